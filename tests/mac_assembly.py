@@ -1,0 +1,161 @@
+"""Independent sparse assembly of the discrete operators, used only to pin the oracle.
+
+The oracle applies its stencils point by point; this module builds the same operators as
+sparse matrices from 1D factors combined with Kronecker products (the structure of Eq (14)).
+A mistake in either (a wrong index, sign, spacing or interpolation weight) makes them differ.
+Padded layout (nz+2, ny+2, nx+2), x fastest, so a 3D operator is kron(Mz, My, Mx).
+"""
+import numpy as np
+import scipy.sparse as sp
+
+
+def positions(n, face):
+    """Node coordinates of indices 0..n+1 along one axis."""
+    if face:
+        p = np.arange(n + 2) / n
+        p[n + 1] = 1.0 + 1.0 / n  # padding, never used by an interior row
+        return p
+    p = (np.arange(n + 2) - 0.5) / n
+    p[0], p[n + 1] = 0.0, 1.0
+    return p
+
+
+def interior_rows(n, face):
+    return np.arange(1, n) if face else np.arange(1, n + 1)
+
+
+def d2_1d(n, face):
+    p, h = positions(n, face), 1.0 / n
+    M = sp.lil_matrix((n + 2, n + 2))
+    for t in interior_rows(n, face):
+        wl, wr = 1.0 / (p[t] - p[t - 1]), 1.0 / (p[t + 1] - p[t])
+        M[t, t - 1] += wl / h
+        M[t, t + 1] += wr / h
+        M[t, t] -= (wl + wr) / h
+    return M.tocsr()
+
+
+def d1_1d(n, face):
+    p = positions(n, face)
+    M = sp.lil_matrix((n + 2, n + 2))
+    for t in interior_rows(n, face):
+        dm, dp = p[t] - p[t - 1], p[t + 1] - p[t]
+        den = dm * dp * (dm + dp)
+        M[t, t + 1] += dm * dm / den
+        M[t, t - 1] -= dp * dp / den
+        M[t, t] += (dp * dp - dm * dm) / den
+    return M.tocsr()
+
+
+def face_to_cell(n):
+    """Row t (cell-like node) = mean of faces t-1 and t."""
+    M = sp.lil_matrix((n + 2, n + 2))
+    for t in range(1, n + 1):
+        M[t, t - 1] = 0.5
+        M[t, t] = 0.5
+    return M.tocsr()
+
+
+def cell_to_face(n):
+    """Row t (face node) = mean of cell-like nodes t and t+1."""
+    M = sp.lil_matrix((n + 2, n + 2))
+    for t in range(0, n + 1):
+        M[t, t] = 0.5
+        M[t, t + 1] = 0.5
+    return M.tocsr()
+
+
+class MacOps:
+    def __init__(self, nx, ny, nz):
+        self.n = (nx, ny, nz)
+        self.P = (nx + 2) * (ny + 2) * (nz + 2)
+
+    def kron3(self, mats):
+        """mats = (Mx, My, Mz) -> operator on the flattened padded array."""
+        Mx, My, Mz = mats
+        return sp.kron(sp.kron(Mz, My), Mx).tocsr()
+
+    def eye(self, a):
+        return sp.identity(self.n[a] + 2, format="csr")
+
+    def along(self, a, M):
+        mats = [self.eye(0), self.eye(1), self.eye(2)]
+        mats[a] = M
+        return self.kron3(mats)
+
+    def laplace(self, F):
+        return sum(self.along(a, d2_1d(self.n[a], F == a)) for a in range(3))
+
+    def deriv(self, F, a):
+        return self.along(a, d1_1d(self.n[a], F == a))
+
+    def interp(self, c, F):
+        """Velocity component c (faces normal to axis c) to the nodes of field F (3 = cell)."""
+        if c == F:
+            return sp.identity(self.P, format="csr")
+        mats = [self.eye(0), self.eye(1), self.eye(2)]
+        mats[c] = face_to_cell(self.n[c])
+        if F < 3:
+            mats[F] = cell_to_face(self.n[F])
+        return self.kron3(mats)
+
+    def dof_mask(self, F):
+        m = []
+        for a in range(3):
+            v = np.zeros(self.n[a] + 2)
+            v[interior_rows(self.n[a], F == a)] = 1.0
+            m.append(v)
+        return np.kron(np.kron(m[2], m[1]), m[0])
+
+    def jacobian(self, base, gr, pr):
+        """Sparse J acting on a packed (u, v, w, T) vector already in Eq (13)'s space."""
+        P = self.P
+        nu, kappa = gr ** -0.5, 1.0 / (pr * gr ** 0.5)
+        Ub = [base[c].ravel() for c in range(3)]
+        Th = base[3].ravel()
+        blocks = [[None] * 4 for _ in range(4)]
+        for F in range(4):
+            diag_adv = sum(sp.diags(self.interp(c, F) @ Ub[c]) @ self.deriv(F, c) for c in range(3))
+            coef = kappa if F == 3 else nu
+            own = coef * self.laplace(F) - diag_adv
+            target = Th if F == 3 else Ub[F]
+            for c in range(3):
+                # -(x . grad) target: the perturbation velocity averaged, times grad of target
+                term = -sp.diags(self.deriv(F, c) @ target) @ self.interp(c, F)
+                blocks[F][c] = term if blocks[F][c] is None else blocks[F][c] + term
+            blocks[F][F] = own if blocks[F][F] is None else blocks[F][F] + own
+            if F == 2:
+                blocks[2][3] = self.along(2, cell_to_face(self.n[2]))
+        for F in range(4):
+            for c in range(4):
+                if blocks[F][c] is None:
+                    blocks[F][c] = sp.csr_matrix((P, P))
+        J = sp.bmat(blocks, format="csr")
+        mask = np.concatenate([self.dof_mask(F) for F in range(4)])
+        return sp.diags(mask) @ J
+
+    def divergence(self):
+        """Cells (padded, interior rows) <- faces; D v with MAC differences."""
+        P = self.P
+        parts = []
+        for a in range(3):
+            n = self.n[a]
+            M = sp.lil_matrix((n + 2, n + 2))
+            for t in range(1, n + 1):
+                M[t, t] = n
+                M[t, t - 1] = -n
+            parts.append(self.along(a, M.tocsr()))
+        D = sp.hstack(parts).tocsr()
+        return sp.diags(self.dof_mask(3)) @ D
+
+    def gradient(self):
+        """Interior faces <- cells; (G phi)_face = (phi_{t+1} - phi_t) / h."""
+        rows = []
+        for a in range(3):
+            n = self.n[a]
+            M = sp.lil_matrix((n + 2, n + 2))
+            for t in range(1, n):
+                M[t, t + 1] = n
+                M[t, t] = -n
+            rows.append(sp.diags(self.dof_mask(a)) @ self.along(a, M.tocsr()))
+        return sp.vstack(rows).tocsr()
