@@ -1,0 +1,327 @@
+#!/usr/bin/env python
+"""Throughput benchmark of the Krylov-vector evaluation (Gelfgat, arXiv 1905.11601, Section 3.1).
+
+One step = one Arnoldi step on the 256^3 grid: the Krylov vector y = (Pi_v (+) P_T) J P_BC x
+(linearised operator stencil, divergence, TPF Poisson solve, velocity correction and temperature
+projection) followed by classical Gram-Schmidt (twice) against the current basis and the
+normalisation; the basis is restarted every --restart vectors. Inputs are seeded synthetic base
+flows and vectors (no dataset), resident in HBM before the timed region; every vector (551 MB)
+is larger than L2, so no L2 flush is needed between steps.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+For N > 1 (launched by torch.distributed.run) every rank runs an independent replica of the
+workload on its own GPU (the method needs no exchange between independent problems); the
+value is the whole-job rate, the time the maximum over ranks. Prints one JSON line on rank 0.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Krylov-vector evals/s at 256^3: mixed vs FP64 plain at 1e-9 rel err; roofline %"
+UNIT = "Krylov-vector evals/s"
+FP64_PEAK_TFLOPS = 1.25  # nominal GB300 FP64 rate (an FMA-loop probe measured 1.20)
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", default="cube256_cc")
+    ap.add_argument("--restart", type=int, default=20)
+    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    hbm, src = 6783.0, "measured copy bandwidth of this pool's GB300 (6783 GB/s)"
+    try:
+        d = json.load(open(path))
+        for key in ("hbm_gbs", "hbm_GBs", "hbm"):
+            if key in d and isinstance(d[key], (int, float)):
+                hbm, src = float(d[key]), "MEASURED_PEAKS.json"
+                break
+    except Exception:
+        pass
+    return hbm, src
+
+
+def workload_desc(w, restart, precision="fp64"):
+    bc = "CC" if w.bc == 0 else "AA"
+    return {"workload": f"{w.name}: {w.nx}x{w.ny}x{w.nz} MAC grid, {bc} spanwise walls, Gr={w.gr:g}, "
+                        f"Pr={w.pr:g}, Arnoldi step (Krylov vector + CGS2), restart {restart}, {precision}",
+            "grid": [w.nx, w.ny, w.nz], "spanwise_bc": bc, "gr": w.gr, "pr": w.pr, "restart": restart,
+            "precision": precision,
+            "l2": "inputs larger than L2 (one packed FP64 vector is "
+                  f"{4 * (w.nx + 2) * (w.ny + 2) * (w.nz + 2) * 8 / 1e6:.0f} MB), no flush"}
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled every 200 ms during the timed region."""
+
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(index), f"--query-gpu={self.QUERY}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.p = None
+
+    def stop(self):
+        if self.p is not None:
+            self.p.terminate()
+            try:
+                self.p.wait(timeout=5)
+            except Exception:
+                self.p.kill()
+        self.f.flush()
+        self.f.seek(0)
+        rows = [r.split(",") for r in self.f.read().splitlines() if r.strip()]
+        self.f.close()
+        os.unlink(self.f.name)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            r = [c.strip() for c in r]
+            try:
+                sm.append(float(r[1]))
+                smax.append(float(r[2]))
+            except (ValueError, IndexError):
+                continue
+            for n, v in zip(names, r[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def source_sha(path):
+    return hashlib.sha256(open(path, "rb").read()).hexdigest()[:16]
+
+
+def traffic_for(kernel):
+    """DRAM bytes per launch of a kernel from a committed ncu summary, if its source is unchanged."""
+    try:
+        d = json.load(open(os.path.join(ROOT, "profiles", "traffic.json")))[kernel]
+        src = os.path.join(ROOT, "paper_1905_11601_gb300", "csrc", d["source"])
+        if source_sha(src) != d["source_sha"]:
+            return None
+        return d["bytes_per_launch"]
+    except Exception:
+        return None
+
+
+def cpu_baseline(workload, evals, warmup, timeout=900):
+    cmd = [sys.executable, "-m", "oracle.bench_cpu", "--workload", workload, "--evals", str(evals),
+           "--warmup", str(warmup)]
+    r = subprocess.run(cmd, cwd=ROOT, capture_output=True, text=True, timeout=timeout)
+    if r.returncode != 0:
+        raise RuntimeError(f"oracle baseline failed: {r.stderr[-2000:]}")
+    return json.loads(r.stdout.strip().splitlines()[-1])
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    from paper_1905_11601_gb300 import synth
+    w = synth.WORKLOADS[args.workload]
+    # each oracle step is one full Krylov-vector evaluation of the same workload on the host
+    # cores; the counts are capped so the run stays within a few minutes
+    steps = max(1, min(args.steps, 8))
+    warm = min(args.warmup, 1)
+    r = cpu_baseline(args.workload, steps, warm)
+    sample = (f"{steps} timed + {warm} warm-up FP64 oracle Krylov-vector evaluations of {w.name} "
+              f"(Arnoldi orthogonalisation not included) on {r['cores']} host threads")
+    out = {"impl": "reference", "metric": METRIC, "value": r["value"], "unit": UNIT, "n_gpus": args.gpus,
+           "steps": steps, "warmup": warm, "ms_per_step": 1000.0 / r["value"], "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": workload_desc(w, args.restart),
+           "cpu_baseline": {"value": r["value"], "unit": UNIT, "cores": r["cores"], "kind": "oracle",
+                            "sample": sample},
+           "e2e": {"value": r["value"], "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    else:
+        dist = None
+        torch.cuda.set_device(local)
+
+    from paper_1905_11601_gb300 import build as kvbuild
+    from paper_1905_11601_gb300 import kv, synth
+
+    kvbuild.build()
+    w = synth.WORKLOADS[args.workload]
+    base_np, x_np = synth.workload_arrays(w)
+    base = torch.from_numpy(np.stack(base_np)).cuda()
+    g = kv.Grid(w.nx, w.ny, w.nz, bc=w.bc, gr=w.gr, pr=w.pr)
+    g.set_base_flow(base)
+    m = args.restart
+    V = torch.zeros((m + 1, 4) + g.shape, dtype=torch.float64, device="cuda")
+    x = torch.from_numpy(x_np[0]).cuda()
+    y0 = g.krylov_vector(x)
+    V[0] = y0 / torch.linalg.vector_norm(y0)
+    del y0
+    state = {"j": 0}
+
+    def step():
+        j = state["j"]
+        if j == m:  # restart the basis from the last vector
+            V[0].copy_(V[m])
+            j = 0
+        g.arnoldi_step(V, j)
+        state["j"] = j + 1
+
+    for _ in range(args.warmup):
+        step()
+    stream = torch.cuda.current_stream()
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local) if rank == 0 else None
+    g.profile_enable(True)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clk = clocks.stop() if clocks else None
+    ms = e0.elapsed_time(e1)
+    prof = g.profile()
+    g.profile_enable(False)
+    if dist:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = world * args.steps / (ms / 1000.0)
+
+    # end to end through the host-buffer entry point (pinned host x and y, copies timed)
+    xh = torch.from_numpy(x_np[0].copy()).pin_memory()
+    yh = torch.empty_like(xh).pin_memory()
+    g.krylov_vector_host(xh, yh)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    t0 = time.perf_counter()
+    for _ in range(args.e2e_steps):
+        g.krylov_vector_host(xh, yh)
+    e2e_s = time.perf_counter() - t0
+    if dist:
+        t = torch.tensor([e2e_s], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    e2e_value = world * args.e2e_steps / e2e_s
+    vec_bytes = xh.numel() * 8
+
+    # roofline of the dominant kernel (largest share of the timed region)
+    n3 = w.nx * w.ny * w.nz
+    phases = {k: {"ms": v[0], "timed": v[1], "launches": v[2]} for k, v in prof.items()}
+    dom = max(phases, key=lambda k: phases[k]["ms"])
+    hbm_peak, hbm_src = measured_peaks()
+    roof = None
+    if dom == "tpd":
+        flops = 2.0 * (n3 * w.nx + n3 * w.ny + n3 * w.nz) / 3.0  # average per contraction launch
+        avg_ms = phases["tpd"]["ms"] / max(phases["tpd"]["timed"], 1)
+        ach = flops / (avg_ms / 1000.0) / 1e12
+        roof = {"kernel": "k_gemm_axis (FP64 per-axis TPF contraction)", "bound": "alu", "achieved": ach,
+                "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": ach / FP64_PEAK_TFLOPS,
+                "traffic": traffic_for("k_gemm_axis"),
+                "peak_source": "nominal GB300 FP64 rate (FMA-loop probe on this pool: 1.20 TFLOP/s)",
+                "algorithmic": f"2 n^4 = {flops:.4g} flop per launch"}
+    elif dom == "stencil":
+        byts = 12.0 * 8.0 * n3
+        avg_ms = phases["stencil"]["ms"] / max(phases["stencil"]["timed"], 1)
+        ach = byts / (avg_ms / 1000.0) / 1e9
+        roof = {"kernel": "k_stencil", "bound": "hbm", "achieved": ach, "peak": hbm_peak, "unit": "GB/s",
+                "frac": ach / hbm_peak, "traffic": traffic_for("k_stencil"), "peak_source": hbm_src,
+                "algorithmic": f"12 fields x 8 B x n^3 = {byts:.4g} B per launch"}
+    else:
+        avg_ms = phases[dom]["ms"] / max(phases[dom]["timed"], 1)
+        roof = {"kernel": dom, "bound": "hbm", "achieved": None, "peak": hbm_peak, "unit": "GB/s",
+                "frac": None, "traffic": None, "peak_source": hbm_src}
+    total_prof = sum(p["ms"] for p in phases.values())
+    for p in phases.values():
+        p["share"] = p["ms"] / total_prof if total_prof else None
+    launches = int(sum(p["launches"] for p in phases.values()))
+
+    if rank != 0:
+        if dist:
+            dist.destroy_process_group()
+        return
+    out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded base flow and vectors)",
+           "config": workload_desc(w, m), "impl": "ours",
+           "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": vec_bytes, "d2h_bytes_per_step": vec_bytes,
+                   "path": "kv_krylov_vector_host (pinned host x and y, copies on the handle's stream)"},
+           "gpu_launches": launches, "roofline": roof, "clocks": clk,
+           "phases": {k: {"ms_per_step": v["ms"] / args.steps, "share": v["share"],
+                          "launches_per_step": v["launches"] / args.steps} for k, v in phases.items()}}
+    if world == 1 and not args.no_cpu_baseline:
+        try:
+            r = cpu_baseline(args.workload, 1, 0)
+            out["cpu_baseline"] = {"value": r["value"], "unit": UNIT, "cores": r["cores"], "kind": "oracle",
+                                   "sample": f"1 FP64 oracle Krylov-vector evaluation of {w.name} "
+                                             f"({r['seconds']:.1f} s on {r['cores']} host threads)"}
+        except Exception as e:  # the baseline is reported, never required
+            out["cpu_baseline"] = {"value": None, "unit": UNIT, "cores": None, "kind": "oracle",
+                                   "sample": f"failed: {e}"[:300]}
+    print(json.dumps(out), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,147 @@
+/*
+ * kv.h -- C ABI of the GB300 (sm_103a) Krylov-vector library.
+ *
+ * The library evaluates one Krylov vector of the Newton / Arnoldi stability method of
+ * Gelfgat, arXiv 1905.11601, Section 3.1, for natural convection in a laterally heated
+ * cube: for a steady state (U, Theta) and a vector x = (u, v, w, T) it computes
+ *
+ *     y = (Pi_v (+) P_T) J(U, Theta) P_BC x
+ *
+ *   P_BC  puts x into the constrained space of Eq (13) (velocity zero outside the interior
+ *         faces, temperature projected onto the homogeneous boundary conditions);
+ *   J     is the right-hand side of Eqs (11)-(12) without the pressure gradient, i.e. the
+ *         linearised operator of Eqs (8)-(9);
+ *   Pi_v  is the SIMPLE / Chorin velocity projection of Section 3.1 (Poisson equation for
+ *         the pressure correction solved by the tensor-product factorisation, Eqs (14)-(18));
+ *   P_T   is the temperature projection of Eqs (19)-(21).
+ *
+ * Grid and memory layout (shared by every array argument):
+ *   - uniform staggered (MAC) grid of the unit cube with nx, ny, nz cells, h_a = 1 / n_a;
+ *   - every field is a padded array of (nx+2)*(ny+2)*(nz+2) doubles, x fastest, element
+ *     (i, j, k) at i + (nx+2) * (j + (ny+2) * k);
+ *   - T and p sit at cell centres (cell index 1..n, wall nodes 0 and n+1 on the walls);
+ *     u / v / w sit on x / y / z faces (face index 0..n along their own axis, index n+1
+ *     unused) and are cell-like along the other two axes;
+ *   - a "packed vector" is four consecutive fields u | v | w | T (4 * field_len doubles);
+ *     a packed state U | V | W | Theta has the same layout.
+ *
+ * Ownership: every pointer argument is owned by the caller and never freed by the library.
+ * Unless a function says otherwise, array pointers are DEVICE pointers (cudaMalloc'ed or
+ * from torch) on the current device, and the work is queued on the handle's stream
+ * (stream-ordered, asynchronous). Functions that return a host scalar synchronise that stream.
+ *
+ * Errors: functions return KV_OK or a negative kv_status; nothing is thrown across the ABI.
+ * kv_last_error() returns a message for the last failed call on a handle (or, for a NULL
+ * handle, for the last failed kv_create_grid on this thread).
+ */
+#ifndef KV_H
+#define KV_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct kv_grid* kv_handle;
+
+typedef enum {
+  KV_OK = 0,
+  KV_ERR_ARG = -1,           /* invalid argument (NULL pointer, size, enum value) */
+  KV_ERR_CUDA = -2,          /* a CUDA call or kernel launch failed */
+  KV_ERR_NOT_CONVERGED = -3, /* SIMPLE / refinement did not reach the tolerance */
+  KV_ERR_STATE = -4,         /* call out of order (e.g. no base flow set) */
+  KV_ERR_NOMEM = -5          /* device allocation failed */
+} kv_status;
+
+/* Spanwise thermal boundary conditions (Section 2). */
+enum { KV_BC_CC = 0 /* conducting, Eq (6) */, KV_BC_AA = 1 /* insulated, Eq (7) */ };
+
+/* Readings of the temperature projection Eq (21) at insulated walls (identical on the
+   conducting walls): orthogonal = Gram-matrix projection onto the boundary-condition
+   subspace (wall pair replaced by its mean); oblique = interior kept, wall node set from
+   the condition. */
+enum { KV_TPROJ_ORTHOGONAL = 0, KV_TPROJ_OBLIQUE = 1 };
+
+/* Arithmetic of the Krylov-vector evaluation. */
+enum { KV_PREC_FP64 = 0 };
+
+typedef struct {
+  int nx, ny, nz;    /* cells per axis, each >= 2 and <= 1024 */
+  int spanwise_bc;   /* KV_BC_CC or KV_BC_AA */
+  int tproj;         /* KV_TPROJ_ORTHOGONAL or KV_TPROJ_OBLIQUE */
+  int precision;     /* KV_PREC_FP64 */
+  double gr, pr;     /* Grashof and Prandtl numbers, > 0 */
+  double tol;        /* SIMPLE stop: max|D v| * h_min / max|v| < tol (0 -> 1e-12) */
+  int max_passes;    /* SIMPLE passes at most (0 -> 1: one exact pass, residual reported) */
+} kv_grid_desc;
+
+typedef struct {
+  int passes;       /* SIMPLE passes performed */
+  double max_div;   /* max |D v| after the last pass (absolute; the paper's pointwise test) */
+  double rel_div;   /* max |D v| * h_min / max |v| */
+} kv_stats;
+
+/* Creates a grid: validates desc, builds the per-axis eigen-decompositions of Eq (15)
+   (computed once, Section 3.1) and allocates the library's device storage (base flow,
+   Poisson scratch). stream: a cudaStream_t (NULL = legacy default stream). */
+kv_status kv_create_grid(const kv_grid_desc* desc, void* stream, kv_handle* out);
+
+/* Frees all device storage of the handle. NULL is accepted. */
+kv_status kv_destroy_grid(kv_handle h);
+
+/* Changes the stream later calls are queued on. */
+kv_status kv_set_stream(kv_handle h, void* stream);
+
+/* Number of doubles in one padded field, (nx+2)(ny+2)(nz+2). */
+kv_status kv_field_len(kv_handle h, size_t* field_len);
+
+/* Copies a packed state U | V | W | Theta (device pointer) into library storage: the steady
+   flow (U, P, Theta) that Eqs (8)-(9) are linearised about. Theta carries its wall values. */
+kv_status kv_set_base_flow(kv_handle h, const double* base);
+
+/* One Krylov vector (Eqs (11)-(13), Section 3.1): y = (Pi_v (+) P_T) J P_BC x.
+   x, y: packed vectors (device, must not overlap). p: optional padded cell field that
+   receives the pressure correction sum(phi) (zero mean, walls zero); may be NULL.
+   st: optional host struct; when given, or when desc.max_passes > 1, the call
+   synchronises the stream to read the divergence residual. */
+kv_status kv_krylov_vector(kv_handle h, const double* x, double* y, double* p, kv_stats* st);
+
+/* As kv_krylov_vector, with x and y in HOST memory (pinned or pageable); the host-device
+   copies are queued on the handle's stream and the call returns once y is in host memory. */
+kv_status kv_krylov_vector_host(kv_handle h, const double* x_host, double* y_host, kv_stats* st);
+
+/* One Arnoldi step (Section 3.1, the Krylov basis for the eigenvalue problem Eq (10)):
+   V holds at least j+2 packed vectors (device), V_0..V_j orthonormal; computes
+   w = A V_j, orthogonalises it against V_0..V_j by classical Gram-Schmidt applied twice,
+   stores w / ||w|| in V_{j+1} and writes the Hessenberg column H[0..j+1, j] to the HOST
+   array h_col (j+2 doubles). Synchronises the stream. Inner products run over all stored
+   entries of the four fields. */
+kv_status kv_arnoldi_step(kv_handle h, double* V, int j, double* h_col);
+
+/* Newton step 2 of Section 3.1: the steady residual of Eqs (1)-(2) at the packed state S
+   (device; carries its own inhomogeneous wall values, Eqs (4)-(7)), projected like a
+   Krylov vector (the pressure gradient drops out). F: optional packed output (device);
+   norm_out: optional HOST pointer receiving ||F||_2 (synchronises the stream). */
+kv_status kv_newton_residual(kv_handle h, const double* S, double* F, double* norm_out);
+
+/* Instrumentation (not part of the method): launch counts per phase, always kept, and, when
+   enabled, per-phase CUDA-event timings on the handle's stream. Phases: 0 = linearised
+   operator stencil, 1 = divergence, 2 = TPF Poisson contractions (one timing per per-axis
+   contraction launch), 3 = velocity correction, 4 = Arnoldi reductions.
+   kv_profile_enable synchronises the stream and clears all counters. */
+kv_status kv_profile_enable(kv_handle h, int on);
+/* Synchronises the stream; total_ms / timed_launches: summed event time and number of timed
+   brackets of the phase since the last kv_profile_enable; launches: kernels launched. Each
+   output pointer (host) may be NULL. */
+kv_status kv_profile_get(kv_handle h, int phase, double* total_ms, long long* timed_launches,
+                         long long* launches);
+
+/* Message of the last failed call on h (NULL h: last failed kv_create_grid). */
+const char* kv_last_error(kv_handle h);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* KV_H */

@@ -309,19 +309,22 @@ or_ctx* or_create(const or_grid* g) {
       }
     double* Gi = (double*)malloc(sizeof(double) * n * n);
     gj_inverse(n, G, Gi);
+    /* P_a = E_a G_a^-1 E_a^T, formed as E_a (G_a^-1 E_a^T) */
+    double* GE = (double*)calloc((size_t)n * m2, sizeof(double)); /* n x (n+2) */
+    for (int p = 0; p < n; ++p)
+      for (int q = 0; q < m2; ++q) {
+        double s = 0.0;
+        for (int p2 = 0; p2 < n; ++p2) s += Gi[(size_t)p * n + p2] * Ex[(size_t)q * n + p2];
+        GE[(size_t)p * m2 + q] = s;
+      }
     c->Pt[a] = (double*)calloc((size_t)m2 * m2, sizeof(double));
     for (int r = 0; r < m2; ++r)
       for (int q = 0; q < m2; ++q) {
         double s = 0.0;
-        for (int p = 0; p < n; ++p) {
-          double er = Ex[(size_t)r * n + p];
-          if (er == 0.0) continue;
-          double t2 = 0.0;
-          for (int p2 = 0; p2 < n; ++p2) t2 += Gi[(size_t)p * n + p2] * Ex[(size_t)q * n + p2];
-          s += er * t2;
-        }
+        for (int p = 0; p < n; ++p) s += Ex[(size_t)r * n + p] * GE[(size_t)p * m2 + q];
         c->Pt[a][(size_t)r * m2 + q] = s;
       }
+    free(GE);
     free(D); free(E); free(lam); free(Ex); free(G); free(Gi);
   }
   return c;

@@ -1,0 +1,446 @@
+// C ABI of libkv: grid handles, the Krylov-vector map, one Arnoldi step and the Newton
+// residual (arXiv 1905.11601, Section 3.1). See include/kv.h for the contract.
+#include <math.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <new>
+#include <string>
+#include <vector>
+
+#include "kv_internal.cuh"
+
+namespace {
+
+thread_local std::string g_create_error;
+
+#define KV_CHECK_CUDA(h, call)                                                              \
+  do {                                                                                      \
+    cudaError_t e_ = (call);                                                                \
+    if (e_ != cudaSuccess) {                                                                \
+      (h)->err = std::string(#call) + ": " + cudaGetErrorString(e_);                        \
+      return e_ == cudaErrorMemoryAllocation ? KV_ERR_NOMEM : KV_ERR_CUDA;                  \
+    }                                                                                       \
+  } while (0)
+
+kv_status fail(kv_grid* h, kv_status st, const std::string& msg) {
+  if (h) h->err = msg;
+  return st;
+}
+
+// Launch-error check after queuing kernels (does not synchronise).
+kv_status check_launch(kv_grid* h, const char* what) {
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return fail(h, KV_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+  return KV_OK;
+}
+
+// Eq (15) for the pressure-correction Laplacian D G with homogeneous Neumann conditions on a
+// uniform axis: eigenvectors alpha_m cos(pi m (t + 1/2) / n), eigenvalues -(4/h^2) sin^2(pi m / 2n).
+// E is orthogonal, so E^-1 = E^T. Computed in long double, rounded once.
+void neumann_axis(int n, std::vector<double>& fwd, std::vector<double>& inv, std::vector<double>& lam) {
+  fwd.assign((size_t)n * n, 0.0);
+  inv.assign((size_t)n * n, 0.0);
+  lam.assign(n, 0.0);
+  const long double pi = 3.141592653589793238462643383279502884L;
+  const long double h = 1.0L / n;
+  for (int m = 0; m < n; ++m) {
+    const long double alpha = sqrtl((m == 0 ? 1.0L : 2.0L) / n);
+    const long double s = sinl(pi * m / (2.0L * n));
+    lam[m] = (double)(-4.0L / (h * h) * s * s);
+    for (int t = 0; t < n; ++t) {
+      const double e = (double)(alpha * cosl(pi * m * (t + 0.5L) / n));
+      fwd[(size_t)m * n + t] = e;  // forward: row = mode, column = node (E^-1 = E^T)
+      inv[(size_t)t * n + m] = e;  // inverse: row = node, column = mode (E)
+    }
+  }
+}
+
+kv_status validate(const kv_grid_desc* d, std::string& msg) {
+  if (!d) { msg = "desc is NULL"; return KV_ERR_ARG; }
+  if (d->nx < 2 || d->ny < 2 || d->nz < 2 || d->nx > 1024 || d->ny > 1024 || d->nz > 1024) {
+    msg = "nx, ny, nz must be in [2, 1024]";
+    return KV_ERR_ARG;
+  }
+  if (d->spanwise_bc != KV_BC_CC && d->spanwise_bc != KV_BC_AA) { msg = "spanwise_bc must be KV_BC_CC or KV_BC_AA"; return KV_ERR_ARG; }
+  if (d->tproj != KV_TPROJ_ORTHOGONAL && d->tproj != KV_TPROJ_OBLIQUE) { msg = "tproj must be KV_TPROJ_ORTHOGONAL or KV_TPROJ_OBLIQUE"; return KV_ERR_ARG; }
+  if (d->precision != KV_PREC_FP64) { msg = "precision must be KV_PREC_FP64"; return KV_ERR_ARG; }
+  if (!(d->gr > 0) || !(d->pr > 0) || !isfinite(d->gr) || !isfinite(d->pr)) { msg = "gr and pr must be finite and > 0"; return KV_ERR_ARG; }
+  if (d->tol < 0 || d->max_passes < 0 || d->max_passes > 100) { msg = "tol must be >= 0 and max_passes in [0, 100]"; return KV_ERR_ARG; }
+  return KV_OK;
+}
+
+void free_all(kv_grid* h) {
+  cudaFree(h->base);
+  cudaFree(h->vstar);
+  cudaFree(h->tpd_a);
+  cudaFree(h->tpd_b);
+  for (int a = 0; a < 6; ++a) cudaFree(h->Wm[a]);
+  for (int a = 0; a < 3; ++a) cudaFree(h->lam[a]);
+  cudaFree(h->red);
+  cudaFree(h->partials);
+  cudaFree(h->hdev);
+  cudaFree(h->stage);
+  cudaFree(h->tmp4);
+}
+
+template <typename T>
+kv_status dalloc(kv_grid* h, T** p, size_t count) {
+  cudaError_t e = cudaMalloc((void**)p, sizeof(T) * (count ? count : 1));
+  if (e != cudaSuccess) {
+    *p = nullptr;
+    return fail(h, KV_ERR_NOMEM, std::string("cudaMalloc: ") + cudaGetErrorString(e));
+  }
+  return KV_OK;
+}
+
+double bits_to_double(unsigned long long b) {
+  double d;
+  memcpy(&d, &b, sizeof d);
+  return d;
+}
+
+// The projection part of the Krylov map for a momentum right-hand side in h->vstar:
+// b = D v*; phi = L^+ b (Eq 18); v = v* - G phi; p = phi; repeated while the SIMPLE test
+// fails and passes remain. Writes the velocity part of y.
+kv_status simple_project(kv_grid* h, double* yvel, double* p, kv_stats* st) {
+  cudaStream_t s = h->s;
+  const int max_passes = h->d.max_passes > 0 ? h->d.max_passes : 1;
+  const bool want = st != nullptr || max_passes > 1;
+  const double tol = h->d.tol > 0 ? h->d.tol : 1e-12;
+  double hmin = fmin(h->g.hx, fmin(h->g.hy, h->g.hz));
+  int pass = 0;
+  double maxdiv = 0, rel = 0;
+  const double* src = h->vstar;
+  for (pass = 1; pass <= max_passes; ++pass) {
+    KV_CHECK_CUDA(h, cudaMemsetAsync(h->red, 0, 2 * sizeof(unsigned long long), s));
+    { KvPhase ph(h, KV_PH_DIV, 1); kv_launch_divergence(h, src, h->tpd_a, s); }
+    kv_launch_poisson(h, h->tpd_a, h->tpd_a, s);
+    { KvPhase ph(h, KV_PH_CORRECT, 1); kv_launch_correct(h, src, h->tpd_a, yvel, p, pass > 1, s); }
+    kv_status ks = check_launch(h, "SIMPLE pass");
+    if (ks != KV_OK) return ks;
+    if (!want) break;
+    unsigned long long r[2];
+    KV_CHECK_CUDA(h, cudaMemcpyAsync(r, h->red, sizeof r, cudaMemcpyDeviceToHost, s));
+    KV_CHECK_CUDA(h, cudaStreamSynchronize(s));
+    maxdiv = bits_to_double(r[0]);
+    const double vmax = bits_to_double(r[1]);
+    rel = vmax > 0 ? maxdiv * hmin / vmax : 0.0;
+    if (rel < tol || pass == max_passes) break;
+    // next pass: project the corrected field again (copy it back as the new v*)
+    KV_CHECK_CUDA(h, cudaMemcpyAsync(h->vstar, yvel, 3 * h->P * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    src = h->vstar;
+  }
+  if (pass > max_passes) pass = max_passes;
+  if (st) {
+    st->passes = pass;
+    st->max_div = maxdiv;
+    st->rel_div = rel;
+  }
+  if (want && max_passes > 1 && !(rel < tol))
+    return fail(h, KV_ERR_NOT_CONVERGED, "SIMPLE did not reach the tolerance in max_passes passes");
+  return KV_OK;
+}
+
+}  // namespace
+
+KvPhase::KvPhase(kv_grid* h_, int phase_, int launches) : h(h_), phase(phase_), n(launches) {
+  if (!h->prof_on) return;
+  if (h->ev_pool.empty()) {
+    if (cudaEventCreate(&a) != cudaSuccess) a = nullptr;
+  } else {
+    a = h->ev_pool.back();
+    h->ev_pool.pop_back();
+  }
+  if (a) cudaEventRecord(a, h->s);
+}
+
+KvPhase::~KvPhase() {
+  h->launches[phase] += n;
+  if (!a) return;
+  cudaEvent_t b = nullptr;
+  if (h->ev_pool.empty()) {
+    if (cudaEventCreate(&b) != cudaSuccess) b = nullptr;
+  } else {
+    b = h->ev_pool.back();
+    h->ev_pool.pop_back();
+  }
+  if (!b) {
+    h->ev_pool.push_back(a);
+    return;
+  }
+  cudaEventRecord(b, h->s);
+  h->pending.push_back({phase, a, b});
+}
+
+extern "C" {
+
+kv_status kv_create_grid(const kv_grid_desc* desc, void* stream, kv_handle* out) {
+  if (!out) {
+    g_create_error = "out is NULL";
+    return KV_ERR_ARG;
+  }
+  *out = nullptr;
+  std::string msg;
+  kv_status st = validate(desc, msg);
+  if (st != KV_OK) {
+    g_create_error = msg;
+    return st;
+  }
+  kv_grid* h = new (std::nothrow) kv_grid();
+  if (!h) {
+    g_create_error = "host allocation failed";
+    return KV_ERR_NOMEM;
+  }
+  h->d = *desc;
+  h->s = (cudaStream_t)stream;
+  cudaGetDevice(&h->dev);
+  KvGeom& g = h->g;
+  g.nx = desc->nx;
+  g.ny = desc->ny;
+  g.nz = desc->nz;
+  g.X = g.nx + 2;
+  g.Y = g.ny + 2;
+  g.Z = g.nz + 2;
+  g.hx = 1.0 / g.nx;
+  g.hy = 1.0 / g.ny;
+  g.hz = 1.0 / g.nz;
+  g.nu = 1.0 / sqrt(desc->gr);
+  g.kappa = 1.0 / (desc->pr * sqrt(desc->gr));
+  g.bc = desc->spanwise_bc;
+  g.tproj = desc->tproj;
+  h->P = (size_t)g.X * g.Y * g.Z;
+  h->Nc = (size_t)g.nx * g.ny * g.nz;
+
+  const int n[3] = {g.nx, g.ny, g.nz};
+  if ((st = dalloc(h, &h->base, 4 * h->P)) || (st = dalloc(h, &h->vstar, 3 * h->P)) ||
+      (st = dalloc(h, &h->tpd_a, h->Nc)) || (st = dalloc(h, &h->tpd_b, h->Nc)) || (st = dalloc(h, &h->red, 2))) {
+    g_create_error = h->err;
+    free_all(h);
+    delete h;
+    return st;
+  }
+  for (int a = 0; a < 3; ++a) {
+    std::vector<double> fwd, inv, lam;
+    neumann_axis(n[a], fwd, inv, lam);
+    if ((st = dalloc(h, &h->Wm[a], fwd.size())) || (st = dalloc(h, &h->Wm[3 + a], inv.size())) ||
+        (st = dalloc(h, &h->lam[a], lam.size()))) {
+      g_create_error = h->err;
+      free_all(h);
+      delete h;
+      return st;
+    }
+    cudaMemcpy(h->Wm[a], fwd.data(), fwd.size() * sizeof(double), cudaMemcpyHostToDevice);
+    cudaMemcpy(h->Wm[3 + a], inv.data(), inv.size() * sizeof(double), cudaMemcpyHostToDevice);
+    cudaMemcpy(h->lam[a], lam.data(), lam.size() * sizeof(double), cudaMemcpyHostToDevice);
+  }
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) {
+    g_create_error = std::string("kv_create_grid: ") + cudaGetErrorString(e);
+    free_all(h);
+    delete h;
+    return KV_ERR_CUDA;
+  }
+  *out = h;
+  return KV_OK;
+}
+
+kv_status kv_destroy_grid(kv_handle h) {
+  if (!h) return KV_OK;
+  cudaStreamSynchronize(h->s);
+  for (auto& p : h->pending) {
+    cudaEventDestroy(p.a);
+    cudaEventDestroy(p.b);
+  }
+  for (auto e : h->ev_pool) cudaEventDestroy(e);
+  free_all(h);
+  delete h;
+  return KV_OK;
+}
+
+kv_status kv_set_stream(kv_handle h, void* stream) {
+  if (!h) return KV_ERR_ARG;
+  h->s = (cudaStream_t)stream;
+  return KV_OK;
+}
+
+kv_status kv_field_len(kv_handle h, size_t* field_len) {
+  if (!h || !field_len) return fail(h, KV_ERR_ARG, "kv_field_len: NULL argument");
+  *field_len = h->P;
+  return KV_OK;
+}
+
+kv_status kv_set_base_flow(kv_handle h, const double* base) {
+  if (!h) return KV_ERR_ARG;
+  if (!base) return fail(h, KV_ERR_ARG, "kv_set_base_flow: base is NULL");
+  KV_CHECK_CUDA(h, cudaMemcpyAsync(h->base, base, 4 * h->P * sizeof(double), cudaMemcpyDeviceToDevice, h->s));
+  h->has_base = true;
+  return KV_OK;
+}
+
+kv_status kv_krylov_vector(kv_handle h, const double* x, double* y, double* p, kv_stats* st) {
+  if (!h) return KV_ERR_ARG;
+  if (!x || !y) return fail(h, KV_ERR_ARG, "kv_krylov_vector: x and y must be non-NULL");
+  if (!h->has_base) return fail(h, KV_ERR_STATE, "kv_krylov_vector: no base flow set");
+  const size_t L = 4 * h->P;
+  if ((x < y + L && y < x + L)) return fail(h, KV_ERR_ARG, "kv_krylov_vector: x and y overlap");
+  // J P_BC x: momentum right-hand side to vstar, projected temperature straight into y
+  { KvPhase ph(h, KV_PH_STENCIL, 1); kv_launch_stencil(h, 0, h->base, x, h->vstar, y + 3 * h->P, h->s); }
+  kv_status ks = check_launch(h, "stencil");
+  if (ks != KV_OK) return ks;
+  return simple_project(h, y, p, st);
+}
+
+kv_status kv_krylov_vector_host(kv_handle h, const double* x_host, double* y_host, kv_stats* st) {
+  if (!h) return KV_ERR_ARG;
+  if (!x_host || !y_host) return fail(h, KV_ERR_ARG, "kv_krylov_vector_host: NULL argument");
+  const size_t L = 4 * h->P;
+  if (!h->stage) {
+    kv_status s = dalloc(h, &h->stage, 2 * L);
+    if (s != KV_OK) return s;
+  }
+  KV_CHECK_CUDA(h, cudaMemcpyAsync(h->stage, x_host, L * sizeof(double), cudaMemcpyHostToDevice, h->s));
+  kv_status s = kv_krylov_vector(h, h->stage, h->stage + L, nullptr, st);
+  if (s != KV_OK) return s;
+  KV_CHECK_CUDA(h, cudaMemcpyAsync(y_host, h->stage + L, L * sizeof(double), cudaMemcpyDeviceToHost, h->s));
+  KV_CHECK_CUDA(h, cudaStreamSynchronize(h->s));
+  return KV_OK;
+}
+
+kv_status kv_arnoldi_step(kv_handle h, double* V, int j, double* h_col) {
+  if (!h) return KV_ERR_ARG;
+  if (!V || !h_col || j < 0 || j > 4095) return fail(h, KV_ERR_ARG, "kv_arnoldi_step: bad argument");
+  const size_t L = 4 * h->P;
+  const int nq = j + 1;
+  const size_t need_p = (size_t)(nq + 1) * kv_reduce_blocks();
+  if (h->partials_cap < need_p) {
+    cudaFree(h->partials);
+    h->partials = nullptr;
+    h->partials_cap = 0;
+    kv_status s = dalloc(h, &h->partials, need_p);
+    if (s != KV_OK) return s;
+    h->partials_cap = need_p;
+  }
+  const size_t need_h = 2 * (size_t)nq + 1;
+  if (h->hdev_cap < need_h) {
+    cudaFree(h->hdev);
+    h->hdev = nullptr;
+    h->hdev_cap = 0;
+    kv_status s = dalloc(h, &h->hdev, need_h);
+    if (s != KV_OK) return s;
+    h->hdev_cap = need_h;
+  }
+  double* w = V + (size_t)(j + 1) * L;
+  kv_status s = kv_krylov_vector(h, V + (size_t)j * L, w, nullptr, nullptr);
+  if (s != KV_OK) return s;
+  double* h1 = h->hdev;
+  double* h2 = h->hdev + nq;
+  double* nrm = h->hdev + 2 * nq;
+  // classical Gram-Schmidt, twice
+  {
+    const int md = (nq + 7) / 8 + 1;  // multidot sweeps + finalize
+    KvPhase ph(h, KV_PH_ARNOLDI, 2 * md + 2 + 2 + 1);
+    kv_launch_multidot(V, L, nq, w, L, h->partials, h1, 0, h->s);
+    kv_launch_update(V, L, nq, h1, w, L, h->s);
+    kv_launch_multidot(V, L, nq, w, L, h->partials, h2, 0, h->s);
+    kv_launch_update(V, L, nq, h2, w, L, h->s);
+    kv_launch_norm2(w, L, h->partials, nrm, h->s);
+    kv_launch_scale_inv_sqrt(w, L, nrm, h->s);
+  }
+  s = check_launch(h, "arnoldi");
+  if (s != KV_OK) return s;
+  std::vector<double> hh(2 * (size_t)nq + 1);
+  KV_CHECK_CUDA(h, cudaMemcpyAsync(hh.data(), h->hdev, hh.size() * sizeof(double), cudaMemcpyDeviceToHost, h->s));
+  KV_CHECK_CUDA(h, cudaStreamSynchronize(h->s));
+  for (int q = 0; q < nq; ++q) h_col[q] = hh[q] + hh[nq + q];
+  h_col[nq] = sqrt(hh[2 * nq]);
+  return KV_OK;
+}
+
+kv_status kv_newton_residual(kv_handle h, const double* S, double* F, double* norm_out) {
+  if (!h) return KV_ERR_ARG;
+  if (!S) return fail(h, KV_ERR_ARG, "kv_newton_residual: S is NULL");
+  const size_t L = 4 * h->P;
+  double* out = F;
+  if (!out) {
+    if (!h->tmp4) {
+      kv_status s = dalloc(h, &h->tmp4, L);
+      if (s != KV_OK) return s;
+    }
+    out = h->tmp4;
+  }
+  if (S < out + L && out < S + L) return fail(h, KV_ERR_ARG, "kv_newton_residual: S and F overlap");
+  { KvPhase ph(h, KV_PH_STENCIL, 1); kv_launch_stencil(h, 1, S, S, h->vstar, out + 3 * h->P, h->s); }
+  kv_status s = check_launch(h, "residual stencil");
+  if (s != KV_OK) return s;
+  s = simple_project(h, out, nullptr, nullptr);
+  if (s != KV_OK) return s;
+  if (norm_out) {
+    const size_t need_p = 2 * (size_t)kv_reduce_blocks();
+    if (h->partials_cap < need_p) {
+      cudaFree(h->partials);
+      h->partials = nullptr;
+      h->partials_cap = 0;
+      s = dalloc(h, &h->partials, need_p);
+      if (s != KV_OK) return s;
+      h->partials_cap = need_p;
+    }
+    if (h->hdev_cap < 1) {
+      s = dalloc(h, &h->hdev, 3);
+      if (s != KV_OK) return s;
+      h->hdev_cap = 3;
+    }
+    { KvPhase ph(h, KV_PH_ARNOLDI, 2); kv_launch_norm2(out, L, h->partials, h->hdev, h->s); }
+    s = check_launch(h, "residual norm");
+    if (s != KV_OK) return s;
+    double n2 = 0;
+    KV_CHECK_CUDA(h, cudaMemcpyAsync(&n2, h->hdev, sizeof n2, cudaMemcpyDeviceToHost, h->s));
+    KV_CHECK_CUDA(h, cudaStreamSynchronize(h->s));
+    *norm_out = sqrt(n2);
+  }
+  return KV_OK;
+}
+
+kv_status kv_profile_enable(kv_handle h, int on) {
+  if (!h) return KV_ERR_ARG;
+  KV_CHECK_CUDA(h, cudaStreamSynchronize(h->s));
+  for (auto& p : h->pending) {
+    h->ev_pool.push_back(p.a);
+    h->ev_pool.push_back(p.b);
+  }
+  h->pending.clear();
+  for (int q = 0; q < KV_NPHASE; ++q) {
+    h->prof_ms[q] = 0;
+    h->prof_n[q] = 0;
+    h->launches[q] = 0;
+  }
+  h->prof_on = on != 0;
+  return KV_OK;
+}
+
+kv_status kv_profile_get(kv_handle h, int phase, double* total_ms, long long* timed_launches, long long* launches) {
+  if (!h) return KV_ERR_ARG;
+  if (phase < 0 || phase >= KV_NPHASE) return fail(h, KV_ERR_ARG, "kv_profile_get: bad phase");
+  KV_CHECK_CUDA(h, cudaStreamSynchronize(h->s));
+  for (auto& p : h->pending) {
+    float ms = 0;
+    if (cudaEventElapsedTime(&ms, p.a, p.b) == cudaSuccess) {
+      h->prof_ms[p.phase] += ms;
+      h->prof_n[p.phase] += 1;
+    }
+    h->ev_pool.push_back(p.a);
+    h->ev_pool.push_back(p.b);
+  }
+  h->pending.clear();
+  if (total_ms) *total_ms = h->prof_ms[phase];
+  if (timed_launches) *timed_launches = h->prof_n[phase];
+  if (launches) *launches = h->launches[phase];
+  return KV_OK;
+}
+
+const char* kv_last_error(kv_handle h) {
+  if (!h) return g_create_error.c_str();
+  return h->err.c_str();
+}
+
+}  // extern "C"

@@ -1,0 +1,99 @@
+// Internal declarations shared by the CUDA translation units of libkv.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "kv.h"
+
+// timed phases (kv_profile_get)
+enum { KV_PH_STENCIL = 0, KV_PH_DIV = 1, KV_PH_TPD = 2, KV_PH_CORRECT = 3, KV_PH_ARNOLDI = 4, KV_NPHASE = 8 };
+
+// Device-side description of the uniform MAC grid.
+struct KvGeom {
+  int nx, ny, nz;   // cells per axis
+  int X, Y, Z;      // padded extents n+2
+  double hx, hy, hz;
+  double nu, kappa; // Gr^-1/2 and (Pr Gr^1/2)^-1 (Eqs (1)-(2) scaling)
+  int bc;           // KV_BC_CC / KV_BC_AA
+  int tproj;        // KV_TPROJ_*
+};
+
+struct kv_grid {
+  kv_grid_desc d;
+  KvGeom g;
+  cudaStream_t s = nullptr;
+  int dev = 0;
+  size_t P = 0;   // padded field length
+  size_t Nc = 0;  // nx*ny*nz
+  bool has_base = false;
+
+  double* base = nullptr;   // 4P: U | V | W | Theta
+  double* vstar = nullptr;  // 3P: momentum right-hand side before the projection
+  double* tpd_a = nullptr;  // Nc: divergence / Poisson ping-pong buffers
+  double* tpd_b = nullptr;  // Nc
+  double* Wm[6] = {};       // per-axis GEMM operands: forward E_a^-1 (a = 0..2), inverse E_a
+  double* lam[3] = {};      // eigenvalues of the 1D Neumann Laplacians (Eq 15)
+  unsigned long long* red = nullptr;  // [0] max|D v| bits, [1] max|v| bits
+  double* partials = nullptr;         // Arnoldi block partial sums
+  size_t partials_cap = 0;            // in doubles
+  double* hdev = nullptr;             // Arnoldi coefficients on the device
+  size_t hdev_cap = 0;
+  double* stage = nullptr;            // 8P: staging for the host-buffer entry point
+  double* tmp4 = nullptr;             // 4P: residual right-hand side scratch
+
+  // launch counting (always) and per-phase CUDA-event timing (when profiling is on)
+  long long launches[KV_NPHASE] = {};
+  bool prof_on = false;
+  std::vector<cudaEvent_t> ev_pool;
+  struct Pending { int phase; cudaEvent_t a, b; };
+  std::vector<Pending> pending;
+  double prof_ms[KV_NPHASE] = {};
+  long long prof_n[KV_NPHASE] = {};
+
+  std::string err;
+};
+
+// Phase timer: counts the launches of one phase and, with profiling on, brackets them with
+// a pair of CUDA events on the handle's stream (resolved in kv_profile_get). Defined in kv_api.cu.
+struct KvPhase {
+  kv_grid* h;
+  int phase, n;
+  cudaEvent_t a = nullptr;
+  KvPhase(kv_grid* h, int phase, int launches);
+  ~KvPhase();
+};
+
+// kv_stencil.cu
+// mode 0: y* = J P_BC x (Eqs (11)-(12)); mode 1: y* = F(S) (steady residual, x = base = S).
+// Writes the three momentum fields (interior faces, zero elsewhere) to vstar and the
+// projected temperature (all padded entries) to tout.
+void kv_launch_stencil(const kv_grid* h, int mode, const double* base, const double* x, double* vstar,
+                       double* tout, cudaStream_t s);
+
+// kv_project.cu
+void kv_launch_divergence(const kv_grid* h, const double* vel, double* b, cudaStream_t s);
+// out_vel = vstar - G phi on interior faces (0 elsewhere); p (nullable) = phi (+ p if accumulate);
+// reduces max |D out_vel| and max |out_vel| into h->red.
+void kv_launch_correct(const kv_grid* h, const double* vstar, const double* phi, double* out_vel,
+                       double* p, int accumulate_p, cudaStream_t s);
+
+// kv_tpd.cu: phi = L^+ b by Eq (18), six per-axis contractions; b and phi compact n^3
+// (x fastest). b is overwritten (used as scratch).
+void kv_launch_poisson(kv_grid* h, double* b, double* phi, cudaStream_t s);
+
+// kv_reduce.cu
+// partial sums of <V_q, w> for q = 0..nq-1 (vectors of length len, stride between V_q = ld),
+// then out[q] = sum of partials. If accumulate, out[q] += result.
+int kv_reduce_blocks();
+void kv_launch_multidot(const double* V, size_t ld, int nq, const double* w, size_t len, double* partials,
+                        double* out, int accumulate, cudaStream_t s);
+// w -= sum_q c[q] V_q
+void kv_launch_update(const double* V, size_t ld, int nq, const double* c, double* w, size_t len,
+                      cudaStream_t s);
+// out[0] = ||w||^2 (via partials); then w /= sqrt(out[0]) if scale
+void kv_launch_norm2(const double* w, size_t len, double* partials, double* out, cudaStream_t s);
+void kv_launch_scale_inv_sqrt(double* w, size_t len, const double* nrm2, cudaStream_t s);

@@ -1,0 +1,251 @@
+// The linearised Boussinesq operator of Eqs (8)-(9) as used by Eqs (11)-(12), and the
+// steady residual of Eqs (1)-(2), on the uniform MAC grid (FP64).
+//
+// Discrete operators (the paper defers its schemes to its reference [11]; these are the
+// readings this library implements):
+//   diffusion  flux form ((f+ - f)/(x+ - x) - (f - f-)/(x - x-)) / h, wall nodes at h/2;
+//   advection  (a . grad) b in advective form: 3-point central derivative of b at b's node
+//              (non-uniform next to a wall node), times a averaged (2 or 4 points) there;
+//   buoyancy   T e_z on a w-face: mean of the two adjacent cell temperatures.
+// One thread per padded index (i, j, k) writes the u, v and w entries at that index (the
+// momentum right-hand side on interior faces, 0 elsewhere) and the projected temperature.
+#include "kv_internal.cuh"
+
+namespace {
+
+struct W3 {
+  double m, c, p;
+};
+
+// first / second derivative weights at a cell-like index t = 1..n (wall nodes at h/2)
+__device__ __forceinline__ W3 d1_cell(int t, int n, double ih) {
+  if (t == 1) return {-4.0 / 3.0 * ih, ih, 1.0 / 3.0 * ih};
+  if (t == n) return {-1.0 / 3.0 * ih, -ih, 4.0 / 3.0 * ih};
+  return {-0.5 * ih, 0.0, 0.5 * ih};
+}
+__device__ __forceinline__ W3 d2_cell(int t, int n, double ih2) {
+  if (t == 1) return {2.0 * ih2, -3.0 * ih2, ih2};
+  if (t == n) return {ih2, -3.0 * ih2, 2.0 * ih2};
+  return {ih2, -2.0 * ih2, ih2};
+}
+__device__ __forceinline__ W3 d1_face(double ih) { return {-0.5 * ih, 0.0, 0.5 * ih}; }
+__device__ __forceinline__ W3 d2_face(double ih2) { return {ih2, -2.0 * ih2, ih2}; }
+
+__device__ __forceinline__ double ap(const W3& w, double fm, double f0, double fp) {
+  return fma(w.m, fm, fma(w.c, f0, w.p * fp));
+}
+
+struct Grid {
+  KvGeom g;
+  __device__ __forceinline__ int at(int i, int j, int k) const { return i + g.X * (j + g.Y * k); }
+  __device__ __forceinline__ bool dof_u(int i, int j, int k) const {
+    return i >= 1 && i <= g.nx - 1 && j >= 1 && j <= g.ny && k >= 1 && k <= g.nz;
+  }
+  __device__ __forceinline__ bool dof_v(int i, int j, int k) const {
+    return i >= 1 && i <= g.nx && j >= 1 && j <= g.ny - 1 && k >= 1 && k <= g.nz;
+  }
+  __device__ __forceinline__ bool dof_w(int i, int j, int k) const {
+    return i >= 1 && i <= g.nx && j >= 1 && j <= g.ny && k >= 1 && k <= g.nz - 1;
+  }
+};
+
+// Loads of the input vector. PROJ: apply P_BC on the fly (velocity zero outside the interior
+// faces; temperature projected onto the homogeneous BCs); otherwise raw.
+template <bool PROJ>
+struct Loader {
+  Grid G;
+  const double* __restrict__ u;
+  const double* __restrict__ v;
+  const double* __restrict__ w;
+  const double* __restrict__ T;
+  __device__ __forceinline__ double lu(int i, int j, int k) const {
+    if (PROJ && !G.dof_u(i, j, k)) return 0.0;
+    return __ldg(u + G.at(i, j, k));
+  }
+  __device__ __forceinline__ double lv(int i, int j, int k) const {
+    if (PROJ && !G.dof_v(i, j, k)) return 0.0;
+    return __ldg(v + G.at(i, j, k));
+  }
+  __device__ __forceinline__ double lw(int i, int j, int k) const {
+    if (PROJ && !G.dof_w(i, j, k)) return 0.0;
+    return __ldg(w + G.at(i, j, k));
+  }
+  __device__ __forceinline__ double lT(int i, int j, int k) const {
+    if (!PROJ) return __ldg(T + G.at(i, j, k));
+    const KvGeom& g = G.g;
+    if (i < 1 || i > g.nx || k < 1 || k > g.nz) return 0.0;
+    if (g.bc == KV_BC_CC) {
+      if (j < 1 || j > g.ny) return 0.0;
+      return __ldg(T + G.at(i, j, k));
+    }
+    int jw, jn;  // wall node and its interior neighbour
+    if (j <= 1) {
+      jw = 0;
+      jn = 1;
+    } else if (j >= g.ny) {
+      jw = g.ny + 1;
+      jn = g.ny;
+    } else {
+      return __ldg(T + G.at(i, j, k));
+    }
+    double tn = __ldg(T + G.at(i, jn, k));
+    if (g.tproj == KV_TPROJ_OBLIQUE) return tn;
+    return 0.5 * (tn + __ldg(T + G.at(i, jw, k)));
+  }
+};
+
+// MODE 0: J P_BC x with (U, Theta) = base. MODE 1: steady residual F(S), S = base = x.
+template <int MODE>
+__global__ void __launch_bounds__(256) k_stencil(KvGeom g, const double* __restrict__ base,
+                                                 const double* __restrict__ x, size_t P,
+                                                 double* __restrict__ vstar, double* __restrict__ tout) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = blockIdx.y * blockDim.y + threadIdx.y;
+  const int k = blockIdx.z;
+  if (i >= g.X || j >= g.Y || k >= g.Z) return;
+  constexpr bool PROJ = (MODE == 0);
+  Grid G{g};
+  const int e = G.at(i, j, k);
+  // base flow (raw) and input (projected in MODE 0)
+  Loader<false> B{G, base, base + P, base + 2 * P, base + 3 * P};
+  Loader<PROJ> Xl{G, x, x + P, x + 2 * P, x + 3 * P};
+  const double ihx = 1.0 / g.hx, ihy = 1.0 / g.hy, ihz = 1.0 / g.hz;
+  const double ihx2 = ihx * ihx, ihy2 = ihy * ihy, ihz2 = ihz * ihz;
+
+  // ---- u on the x-face (i, j, k) ----
+  double ru = 0.0;
+  if (G.dof_u(i, j, k)) {
+    const W3 dx1 = d1_face(ihx), dx2 = d2_face(ihx2);
+    const W3 dy1 = d1_cell(j, g.ny, ihy), dy2 = d2_cell(j, g.ny, ihy2);
+    const W3 dz1 = d1_cell(k, g.nz, ihz), dz2 = d2_cell(k, g.nz, ihz2);
+    const double c = Xl.lu(i, j, k);
+    const double xm = Xl.lu(i - 1, j, k), xp = Xl.lu(i + 1, j, k);
+    const double ym = Xl.lu(i, j - 1, k), yp = Xl.lu(i, j + 1, k);
+    const double zm = Xl.lu(i, j, k - 1), zp = Xl.lu(i, j, k + 1);
+    const double lap = ap(dx2, xm, c, xp) + ap(dy2, ym, c, yp) + ap(dz2, zm, c, zp);
+    const double Ua = B.lu(i, j, k);
+    const double Va = 0.25 * (B.lv(i, j - 1, k) + B.lv(i, j, k) + B.lv(i + 1, j - 1, k) + B.lv(i + 1, j, k));
+    const double Wa = 0.25 * (B.lw(i, j, k - 1) + B.lw(i, j, k) + B.lw(i + 1, j, k - 1) + B.lw(i + 1, j, k));
+    double r = g.nu * lap - (Ua * ap(dx1, xm, c, xp) + Va * ap(dy1, ym, c, yp) + Wa * ap(dz1, zm, c, zp));
+    if (MODE == 0) {
+      const double va = 0.25 * (Xl.lv(i, j - 1, k) + Xl.lv(i, j, k) + Xl.lv(i + 1, j - 1, k) + Xl.lv(i + 1, j, k));
+      const double wa = 0.25 * (Xl.lw(i, j, k - 1) + Xl.lw(i, j, k) + Xl.lw(i + 1, j, k - 1) + Xl.lw(i + 1, j, k));
+      const double gx = ap(dx1, B.lu(i - 1, j, k), Ua, B.lu(i + 1, j, k));
+      const double gy = ap(dy1, B.lu(i, j - 1, k), Ua, B.lu(i, j + 1, k));
+      const double gz = ap(dz1, B.lu(i, j, k - 1), Ua, B.lu(i, j, k + 1));
+      r -= c * gx + va * gy + wa * gz;
+    }
+    ru = r;
+  }
+  vstar[e] = ru;
+
+  // ---- v on the y-face (i, j, k) ----
+  double rv = 0.0;
+  if (G.dof_v(i, j, k)) {
+    const W3 dx1 = d1_cell(i, g.nx, ihx), dx2 = d2_cell(i, g.nx, ihx2);
+    const W3 dy1 = d1_face(ihy), dy2 = d2_face(ihy2);
+    const W3 dz1 = d1_cell(k, g.nz, ihz), dz2 = d2_cell(k, g.nz, ihz2);
+    const double c = Xl.lv(i, j, k);
+    const double xm = Xl.lv(i - 1, j, k), xp = Xl.lv(i + 1, j, k);
+    const double ym = Xl.lv(i, j - 1, k), yp = Xl.lv(i, j + 1, k);
+    const double zm = Xl.lv(i, j, k - 1), zp = Xl.lv(i, j, k + 1);
+    const double lap = ap(dx2, xm, c, xp) + ap(dy2, ym, c, yp) + ap(dz2, zm, c, zp);
+    const double Ua = 0.25 * (B.lu(i - 1, j, k) + B.lu(i, j, k) + B.lu(i - 1, j + 1, k) + B.lu(i, j + 1, k));
+    const double Va = B.lv(i, j, k);
+    const double Wa = 0.25 * (B.lw(i, j, k - 1) + B.lw(i, j, k) + B.lw(i, j + 1, k - 1) + B.lw(i, j + 1, k));
+    double r = g.nu * lap - (Ua * ap(dx1, xm, c, xp) + Va * ap(dy1, ym, c, yp) + Wa * ap(dz1, zm, c, zp));
+    if (MODE == 0) {
+      const double ua = 0.25 * (Xl.lu(i - 1, j, k) + Xl.lu(i, j, k) + Xl.lu(i - 1, j + 1, k) + Xl.lu(i, j + 1, k));
+      const double wa = 0.25 * (Xl.lw(i, j, k - 1) + Xl.lw(i, j, k) + Xl.lw(i, j + 1, k - 1) + Xl.lw(i, j + 1, k));
+      const double gx = ap(dx1, B.lv(i - 1, j, k), Va, B.lv(i + 1, j, k));
+      const double gy = ap(dy1, B.lv(i, j - 1, k), Va, B.lv(i, j + 1, k));
+      const double gz = ap(dz1, B.lv(i, j, k - 1), Va, B.lv(i, j, k + 1));
+      r -= ua * gx + c * gy + wa * gz;
+    }
+    rv = r;
+  }
+  vstar[P + e] = rv;
+
+  // ---- w on the z-face (i, j, k), with the buoyancy term T e_z ----
+  double rw = 0.0;
+  if (G.dof_w(i, j, k)) {
+    const W3 dx1 = d1_cell(i, g.nx, ihx), dx2 = d2_cell(i, g.nx, ihx2);
+    const W3 dy1 = d1_cell(j, g.ny, ihy), dy2 = d2_cell(j, g.ny, ihy2);
+    const W3 dz1 = d1_face(ihz), dz2 = d2_face(ihz2);
+    const double c = Xl.lw(i, j, k);
+    const double xm = Xl.lw(i - 1, j, k), xp = Xl.lw(i + 1, j, k);
+    const double ym = Xl.lw(i, j - 1, k), yp = Xl.lw(i, j + 1, k);
+    const double zm = Xl.lw(i, j, k - 1), zp = Xl.lw(i, j, k + 1);
+    const double lap = ap(dx2, xm, c, xp) + ap(dy2, ym, c, yp) + ap(dz2, zm, c, zp);
+    const double Ua = 0.25 * (B.lu(i - 1, j, k) + B.lu(i, j, k) + B.lu(i - 1, j, k + 1) + B.lu(i, j, k + 1));
+    const double Va = 0.25 * (B.lv(i, j - 1, k) + B.lv(i, j, k) + B.lv(i, j - 1, k + 1) + B.lv(i, j, k + 1));
+    const double Wa = B.lw(i, j, k);
+    double r = g.nu * lap - (Ua * ap(dx1, xm, c, xp) + Va * ap(dy1, ym, c, yp) + Wa * ap(dz1, zm, c, zp));
+    if (MODE == 0) {
+      const double ua = 0.25 * (Xl.lu(i - 1, j, k) + Xl.lu(i, j, k) + Xl.lu(i - 1, j, k + 1) + Xl.lu(i, j, k + 1));
+      const double va = 0.25 * (Xl.lv(i, j - 1, k) + Xl.lv(i, j, k) + Xl.lv(i, j - 1, k + 1) + Xl.lv(i, j, k + 1));
+      const double gx = ap(dx1, B.lw(i - 1, j, k), Wa, B.lw(i + 1, j, k));
+      const double gy = ap(dy1, B.lw(i, j - 1, k), Wa, B.lw(i, j + 1, k));
+      const double gz = ap(dz1, B.lw(i, j, k - 1), Wa, B.lw(i, j, k + 1));
+      r -= ua * gx + va * gy + c * gz;
+      r += 0.5 * (Xl.lT(i, j, k) + Xl.lT(i, j, k + 1));
+    } else {
+      r += 0.5 * (B.lT(i, j, k) + B.lT(i, j, k + 1));
+    }
+    rw = r;
+  }
+  vstar[2 * P + e] = rw;
+
+  // ---- T at the cell (i, j, k), then the temperature projection of Eq (21) ----
+  const bool cell = i >= 1 && i <= g.nx && j >= 1 && j <= g.ny && k >= 1 && k <= g.nz;
+  if (cell) {
+    const W3 dx1 = d1_cell(i, g.nx, ihx), dx2 = d2_cell(i, g.nx, ihx2);
+    const W3 dy1 = d1_cell(j, g.ny, ihy), dy2 = d2_cell(j, g.ny, ihy2);
+    const W3 dz1 = d1_cell(k, g.nz, ihz), dz2 = d2_cell(k, g.nz, ihz2);
+    const double c = Xl.lT(i, j, k);
+    const double xm = Xl.lT(i - 1, j, k), xp = Xl.lT(i + 1, j, k);
+    const double ym = Xl.lT(i, j - 1, k), yp = Xl.lT(i, j + 1, k);
+    const double zm = Xl.lT(i, j, k - 1), zp = Xl.lT(i, j, k + 1);
+    const double lap = ap(dx2, xm, c, xp) + ap(dy2, ym, c, yp) + ap(dz2, zm, c, zp);
+    const double Ua = 0.5 * (B.lu(i - 1, j, k) + B.lu(i, j, k));
+    const double Va = 0.5 * (B.lv(i, j - 1, k) + B.lv(i, j, k));
+    const double Wa = 0.5 * (B.lw(i, j, k - 1) + B.lw(i, j, k));
+    double r = g.kappa * lap - (Ua * ap(dx1, xm, c, xp) + Va * ap(dy1, ym, c, yp) + Wa * ap(dz1, zm, c, zp));
+    if (MODE == 0) {
+      const double ua = 0.5 * (Xl.lu(i - 1, j, k) + Xl.lu(i, j, k));
+      const double va = 0.5 * (Xl.lv(i, j - 1, k) + Xl.lv(i, j, k));
+      const double wa = 0.5 * (Xl.lw(i, j, k - 1) + Xl.lw(i, j, k));
+      const double th = B.lT(i, j, k);
+      const double gx = ap(dx1, B.lT(i - 1, j, k), th, B.lT(i + 1, j, k));
+      const double gy = ap(dy1, B.lT(i, j - 1, k), th, B.lT(i, j + 1, k));
+      const double gz = ap(dz1, B.lT(i, j, k - 1), th, B.lT(i, j, k + 1));
+      r -= ua * gx + va * gy + wa * gz;
+    }
+    if (g.bc == KV_BC_AA && (j == 1 || j == g.ny)) {
+      // insulated wall pair: the wall node carries no equation (0 before the projection)
+      const double t = (g.tproj == KV_TPROJ_OBLIQUE) ? r : 0.5 * r;
+      tout[e] = t;
+      tout[G.at(i, j == 1 ? 0 : g.ny + 1, k)] = t;
+    } else {
+      tout[e] = r;
+    }
+  } else {
+    // walls, edges and corners: zero, except insulated wall nodes written by their neighbour
+    const bool aa_wall = g.bc == KV_BC_AA && (j == 0 || j == g.ny + 1) && i >= 1 && i <= g.nx && k >= 1 &&
+                         k <= g.nz;
+    if (!aa_wall) tout[e] = 0.0;
+  }
+}
+
+}  // namespace
+
+void kv_launch_stencil(const kv_grid* h, int mode, const double* base, const double* x, double* vstar,
+                       double* tout, cudaStream_t s) {
+  const KvGeom& g = h->g;
+  dim3 block(32, 8, 1);
+  dim3 grid((g.X + 31) / 32, (g.Y + 7) / 8, g.Z);
+  if (mode == 0)
+    k_stencil<0><<<grid, block, 0, s>>>(g, base, x, h->P, vstar, tout);
+  else
+    k_stencil<1><<<grid, block, 0, s>>>(g, base, x, h->P, vstar, tout);
+}

@@ -1,0 +1,199 @@
+"""Python binding of libkv (include/kv.h): argument marshalling only.
+
+Every step of the Krylov-vector evaluation runs in the CUDA kernels of libkv.so; torch is
+used for device memory and streams. There is no CPU fallback: if the library is missing or
+no CUDA device is present, the calls raise.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libkv.so")
+
+KV_BC_CC, KV_BC_AA = 0, 1
+KV_TPROJ_ORTHOGONAL, KV_TPROJ_OBLIQUE = 0, 1
+KV_PREC_FP64 = 0
+
+_STATUS = {0: "KV_OK", -1: "KV_ERR_ARG", -2: "KV_ERR_CUDA", -3: "KV_ERR_NOT_CONVERGED", -4: "KV_ERR_STATE",
+           -5: "KV_ERR_NOMEM"}
+
+# every symbol include/kv.h declares
+EXPORTS = ("kv_create_grid", "kv_destroy_grid", "kv_set_stream", "kv_field_len", "kv_set_base_flow",
+           "kv_krylov_vector", "kv_krylov_vector_host", "kv_arnoldi_step", "kv_newton_residual", "kv_last_error",
+           "kv_profile_enable", "kv_profile_get")
+PHASES = {"stencil": 0, "divergence": 1, "tpd": 2, "correct": 3, "arnoldi": 4}
+
+
+class KvError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{_STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class GridDesc(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int),
+                ("spanwise_bc", ctypes.c_int), ("tproj", ctypes.c_int), ("precision", ctypes.c_int),
+                ("gr", ctypes.c_double), ("pr", ctypes.c_double), ("tol", ctypes.c_double),
+                ("max_passes", ctypes.c_int)]
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [("passes", ctypes.c_int), ("max_div", ctypes.c_double), ("rel_div", ctypes.c_double)]
+
+
+_lib = None
+
+
+def load_library(path: str = LIB_PATH):
+    """Loads libkv.so and declares its signatures (no CUDA call is made)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"libkv.so not built ({path}); run paper_1905_11601_gb300.build.build()")
+    lib = ctypes.CDLL(path)
+    H = ctypes.c_void_p
+    D = ctypes.c_void_p  # device or host pointer (int address)
+    lib.kv_create_grid.argtypes = [ctypes.POINTER(GridDesc), ctypes.c_void_p, ctypes.POINTER(H)]
+    lib.kv_destroy_grid.argtypes = [H]
+    lib.kv_set_stream.argtypes = [H, ctypes.c_void_p]
+    lib.kv_field_len.argtypes = [H, ctypes.POINTER(ctypes.c_size_t)]
+    lib.kv_set_base_flow.argtypes = [H, D]
+    lib.kv_krylov_vector.argtypes = [H, D, D, D, ctypes.POINTER(Stats)]
+    lib.kv_krylov_vector_host.argtypes = [H, D, D, ctypes.POINTER(Stats)]
+    lib.kv_arnoldi_step.argtypes = [H, D, ctypes.c_int, ctypes.POINTER(ctypes.c_double)]
+    lib.kv_newton_residual.argtypes = [H, D, D, ctypes.POINTER(ctypes.c_double)]
+    lib.kv_profile_enable.argtypes = [H, ctypes.c_int]
+    lib.kv_profile_get.argtypes = [H, ctypes.c_int, ctypes.POINTER(ctypes.c_double),
+                                   ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_longlong)]
+    lib.kv_last_error.argtypes = [H]
+    lib.kv_last_error.restype = ctypes.c_char_p
+    for name in EXPORTS:
+        if name != "kv_last_error":
+            getattr(lib, name).restype = ctypes.c_int
+    _lib = lib
+    return lib
+
+
+def _dev_ptr(t, torch, name, numel=None):
+    if t is None:
+        return None
+    if not isinstance(t, torch.Tensor) or not t.is_cuda or t.dtype != torch.float64 or not t.is_contiguous():
+        raise ValueError(f"{name}: expected a contiguous float64 CUDA tensor")
+    if numel is not None and t.numel() < numel:
+        raise ValueError(f"{name}: needs at least {numel} elements, got {t.numel()}")
+    return t.data_ptr()
+
+
+class Grid:
+    """A grid handle: kv_create_grid / kv_destroy_grid around the calls of include/kv.h."""
+
+    def __init__(self, nx, ny, nz, bc=KV_BC_CC, gr=1.0e6, pr=0.71, tproj=KV_TPROJ_ORTHOGONAL,
+                 precision=KV_PREC_FP64, tol=0.0, max_passes=0):
+        import torch
+
+        self.torch = torch
+        if not torch.cuda.is_available():
+            raise RuntimeError("libkv needs a CUDA device")
+        self.lib = load_library()
+        self.nx, self.ny, self.nz = nx, ny, nz
+        self.desc = GridDesc(nx, ny, nz, bc, tproj, precision, gr, pr, tol, max_passes)
+        h = ctypes.c_void_p()
+        st = self.lib.kv_create_grid(ctypes.byref(self.desc), ctypes.c_void_p(self._stream()), ctypes.byref(h))
+        if st != 0:
+            raise KvError(st, self.lib.kv_last_error(None).decode())
+        self.h = h
+        n = ctypes.c_size_t()
+        self._check(self.lib.kv_field_len(self.h, ctypes.byref(n)))
+        self.field_len = n.value
+        self.shape = (nz + 2, ny + 2, nx + 2)
+
+    def _stream(self):
+        return self.torch.cuda.current_stream().cuda_stream
+
+    def _check(self, st):
+        if st != 0:
+            raise KvError(st, self.lib.kv_last_error(self.h).decode())
+
+    def _sync_stream(self):
+        self._check(self.lib.kv_set_stream(self.h, ctypes.c_void_p(self._stream())))
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.kv_destroy_grid(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def empty(self, *lead):
+        return self.torch.zeros(tuple(lead) + self.shape, dtype=self.torch.float64, device="cuda")
+
+    def set_base_flow(self, base):
+        self._sync_stream()
+        self._check(self.lib.kv_set_base_flow(self.h, _dev_ptr(base, self.torch, "base", 4 * self.field_len)))
+
+    def krylov_vector(self, x, y=None, p=None, stats=False):
+        self._sync_stream()
+        if y is None:
+            y = self.empty(4)
+        st = Stats()
+        self._check(self.lib.kv_krylov_vector(self.h, _dev_ptr(x, self.torch, "x", 4 * self.field_len),
+                                              _dev_ptr(y, self.torch, "y", 4 * self.field_len),
+                                              _dev_ptr(p, self.torch, "p", self.field_len),
+                                              ctypes.byref(st) if stats else None))
+        return (y, st) if stats else y
+
+    def krylov_vector_host(self, x_host, y_host, stats=False):
+        """x_host, y_host: host float64 arrays/tensors (pinned recommended), 4 packed fields."""
+        self._sync_stream()
+
+        def hp(a, name):
+            if isinstance(a, np.ndarray):
+                assert a.dtype == np.float64 and a.flags.c_contiguous and a.size >= 4 * self.field_len, name
+                return a.ctypes.data
+            assert not a.is_cuda and a.dtype == self.torch.float64 and a.is_contiguous(), name
+            assert a.numel() >= 4 * self.field_len, name
+            return a.data_ptr()
+
+        st = Stats()
+        self._check(self.lib.kv_krylov_vector_host(self.h, hp(x_host, "x_host"), hp(y_host, "y_host"),
+                                                   ctypes.byref(st) if stats else None))
+        return st if stats else None
+
+    def arnoldi_step(self, V, j):
+        self._sync_stream()
+        L = 4 * self.field_len
+        hcol = (ctypes.c_double * (j + 2))()
+        self._check(self.lib.kv_arnoldi_step(self.h, _dev_ptr(V, self.torch, "V", (j + 2) * L), j, hcol))
+        return np.array(hcol[:])
+
+    def profile_enable(self, on=True):
+        self._sync_stream()
+        self._check(self.lib.kv_profile_enable(self.h, 1 if on else 0))
+
+    def profile(self):
+        """{phase: (total_ms, timed_brackets, launches)} since the last profile_enable."""
+        out = {}
+        for name, ph in PHASES.items():
+            ms, nt, nl = ctypes.c_double(), ctypes.c_longlong(), ctypes.c_longlong()
+            self._check(self.lib.kv_profile_get(self.h, ph, ctypes.byref(ms), ctypes.byref(nt), ctypes.byref(nl)))
+            out[name] = (ms.value, nt.value, nl.value)
+        return out
+
+    def newton_residual(self, S, F=None):
+        self._sync_stream()
+        if F is None:
+            F = self.empty(4)
+        nrm = ctypes.c_double()
+        self._check(self.lib.kv_newton_residual(self.h, _dev_ptr(S, self.torch, "S", 4 * self.field_len),
+                                                _dev_ptr(F, self.torch, "F", 4 * self.field_len),
+                                                ctypes.byref(nrm)))
+        return F, nrm.value

@@ -83,11 +83,12 @@ def base_temperature(nx, ny, nz, bc, rng) -> np.ndarray:
     q = rng.integers(1, 5, size=8)
     r = rng.integers(1, 5, size=8)
     xc, yc, zc = cell_coords(nx), cell_coords(ny), cell_coords(nz)
-    Z, Y, X = _grid(xc, yc, zc)
-    th = 1.0 - X
-    for m in range(8):
-        sy = np.sin(q[m] * np.pi * Y) if bc == CC else np.cos(q[m] * np.pi * Y)
-        th = th + 0.05 * a[m] * np.sin(p[m] * np.pi * X) * sy * np.sin(r[m] * np.pi * Z)
+    th = np.broadcast_to(1.0 - xc[None, None, :], padded_shape(nx, ny, nz)).copy()
+    for m in range(8):  # separable products, evaluated as outer products of 1D factors
+        sx = np.sin(p[m] * np.pi * xc)
+        sy = np.sin(q[m] * np.pi * yc) if bc == CC else np.cos(q[m] * np.pi * yc)
+        sz = np.sin(r[m] * np.pi * zc)
+        th += (0.05 * a[m]) * sz[:, None, None] * sy[None, :, None] * sx[None, None, :]
     # wall values: Eq (4) on x walls, Eq (5) on z walls, Eq (6) (CC) or a discrete Eq (7) (AA)
     th[:, :, 0] = 1.0
     th[:, :, nx + 1] = 0.0
@@ -121,13 +122,14 @@ def base_velocity(nx, ny, nz, rng, umax=0.1):
     freq = rng.integers(0, 3, size=(3, 4, 3))
 
     def potential(comp, xs, ys, zs):
-        Z, Y, X = _grid(xs, ys, zs)
-        s = np.sin(np.pi * X) ** 2 * np.sin(np.pi * Y) ** 2 * np.sin(np.pi * Z) ** 2
-        acc = np.zeros_like(X)
+        # s(x)s(y)s(z) * sum_m c_m Re(exp(i a pi x) exp(i b pi y) exp(i g pi z)): separable
+        acc = np.zeros((len(zs), len(ys), len(xs)))
         for m in range(4):
             al, be, ga = freq[comp, m]
-            acc += coef[comp, m] * np.cos(al * np.pi * X + be * np.pi * Y + ga * np.pi * Z)
-        return s * acc
+            ex, ey, ez = np.exp(1j * al * np.pi * xs), np.exp(1j * be * np.pi * ys), np.exp(1j * ga * np.pi * zs)
+            acc += coef[comp, m] * (ez[:, None, None] * ey[None, :, None] * ex[None, None, :]).real
+        sx, sy, sz = np.sin(np.pi * xs) ** 2, np.sin(np.pi * ys) ** 2, np.sin(np.pi * zs) ** 2
+        return acc * (sz[:, None, None] * sy[None, :, None] * sx[None, None, :])
 
     Ax = potential(0, xc, yf, zf)  # [k face, j face, i cell]
     Ay = potential(1, xf, yc, zf)  # [k face, j cell, i face]
