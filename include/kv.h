@@ -63,23 +63,30 @@ enum { KV_BC_CC = 0 /* conducting, Eq (6) */, KV_BC_AA = 1 /* insulated, Eq (7) 
    the condition. */
 enum { KV_TPROJ_ORTHOGONAL = 0, KV_TPROJ_OBLIQUE = 1 };
 
-/* Arithmetic of the Krylov-vector evaluation. */
-enum { KV_PREC_FP64 = 0 };
+/* Arithmetic of the Krylov-vector evaluation. FP64: every step in FP64. MIXED: the
+   pressure-correction Poisson solve runs its per-axis contractions on the tensor cores
+   (BF16 slices, FP32 accumulation) and is refined to FP64 accuracy with an FP64 residual;
+   the other steps stay FP64. */
+enum { KV_PREC_FP64 = 0, KV_PREC_MIXED = 1 };
 
 typedef struct {
   int nx, ny, nz;    /* cells per axis, each >= 2 and <= 1024 */
   int spanwise_bc;   /* KV_BC_CC or KV_BC_AA */
   int tproj;         /* KV_TPROJ_ORTHOGONAL or KV_TPROJ_OBLIQUE */
-  int precision;     /* KV_PREC_FP64 */
+  int precision;     /* KV_PREC_FP64 or KV_PREC_MIXED */
   double gr, pr;     /* Grashof and Prandtl numbers, > 0 */
   double tol;        /* SIMPLE stop: max|D v| * h_min / max|v| < tol (0 -> 1e-12) */
   int max_passes;    /* SIMPLE passes at most (0 -> 1: one exact pass, residual reported) */
+  int refine_sweeps; /* KV_PREC_MIXED: tensor-core solves per Poisson solve, each followed by an
+                        FP64 residual (0 -> 2) */
 } kv_grid_desc;
 
 typedef struct {
   int passes;       /* SIMPLE passes performed */
   double max_div;   /* max |D v| after the last pass (absolute; the paper's pointwise test) */
   double rel_div;   /* max |D v| * h_min / max |v| */
+  double refine_residual; /* KV_PREC_MIXED: max |b - L phi| before the last tensor-core sweep */
+  int device_error; /* nonzero: a bounded wait inside a tensor-core kernel expired */
 } kv_stats;
 
 /* Creates a grid: validates desc, builds the per-axis eigen-decompositions of Eq (15)
@@ -128,7 +135,8 @@ kv_status kv_newton_residual(kv_handle h, const double* S, double* F, double* no
 /* Instrumentation (not part of the method): launch counts per phase, always kept, and, when
    enabled, per-phase CUDA-event timings on the handle's stream. Phases: 0 = linearised
    operator stencil, 1 = divergence, 2 = TPF Poisson contractions (one timing per per-axis
-   contraction launch), 3 = velocity correction, 4 = Arnoldi reductions.
+   contraction launch), 3 = velocity correction, 4 = Arnoldi reductions, 5 = FP64 refinement
+   residuals of the mixed-precision Poisson solve.
    kv_profile_enable synchronises the stream and clears all counters. */
 kv_status kv_profile_enable(kv_handle h, int on);
 /* Synchronises the stream; total_ms / timed_launches: summed event time and number of timed

@@ -64,7 +64,8 @@ kv_status validate(const kv_grid_desc* d, std::string& msg) {
   }
   if (d->spanwise_bc != KV_BC_CC && d->spanwise_bc != KV_BC_AA) { msg = "spanwise_bc must be KV_BC_CC or KV_BC_AA"; return KV_ERR_ARG; }
   if (d->tproj != KV_TPROJ_ORTHOGONAL && d->tproj != KV_TPROJ_OBLIQUE) { msg = "tproj must be KV_TPROJ_ORTHOGONAL or KV_TPROJ_OBLIQUE"; return KV_ERR_ARG; }
-  if (d->precision != KV_PREC_FP64) { msg = "precision must be KV_PREC_FP64"; return KV_ERR_ARG; }
+  if (d->precision != KV_PREC_FP64 && d->precision != KV_PREC_MIXED) { msg = "precision must be KV_PREC_FP64 or KV_PREC_MIXED"; return KV_ERR_ARG; }
+  if (d->refine_sweeps < 0 || d->refine_sweeps > 20) { msg = "refine_sweeps must be in [0, 20]"; return KV_ERR_ARG; }
   if (!(d->gr > 0) || !(d->pr > 0) || !isfinite(d->gr) || !isfinite(d->pr)) { msg = "gr and pr must be finite and > 0"; return KV_ERR_ARG; }
   if (d->tol < 0 || d->max_passes < 0 || d->max_passes > 100) { msg = "tol must be >= 0 and max_passes in [0, 100]"; return KV_ERR_ARG; }
   return KV_OK;
@@ -82,6 +83,7 @@ void free_all(kv_grid* h) {
   cudaFree(h->hdev);
   cudaFree(h->stage);
   cudaFree(h->tmp4);
+  kv_mixed_free(h);
 }
 
 template <typename T>
@@ -112,11 +114,16 @@ kv_status simple_project(kv_grid* h, double* yvel, double* p, kv_stats* st) {
   int pass = 0;
   double maxdiv = 0, rel = 0;
   const double* src = h->vstar;
+  const bool mixed = h->d.precision == KV_PREC_MIXED;
+  double* phi = mixed ? h->tpd_b : h->tpd_a;
   for (pass = 1; pass <= max_passes; ++pass) {
     KV_CHECK_CUDA(h, cudaMemsetAsync(h->red, 0, 2 * sizeof(unsigned long long), s));
     { KvPhase ph(h, KV_PH_DIV, 1); kv_launch_divergence(h, src, h->tpd_a, s); }
-    kv_launch_poisson(h, h->tpd_a, h->tpd_a, s);
-    { KvPhase ph(h, KV_PH_CORRECT, 1); kv_launch_correct(h, src, h->tpd_a, yvel, p, pass > 1, s); }
+    if (mixed)
+      kv_launch_poisson_mixed(h, h->tpd_a, phi, s);
+    else
+      kv_launch_poisson(h, h->tpd_a, h->tpd_a, s);
+    { KvPhase ph(h, KV_PH_CORRECT, 1); kv_launch_correct(h, src, phi, yvel, p, pass > 1, s); }
     kv_status ks = check_launch(h, "SIMPLE pass");
     if (ks != KV_OK) return ks;
     if (!want) break;
@@ -136,6 +143,18 @@ kv_status simple_project(kv_grid* h, double* yvel, double* p, kv_stats* st) {
     st->passes = pass;
     st->max_div = maxdiv;
     st->rel_div = rel;
+    st->refine_residual = 0;
+    st->device_error = 0;
+    if (mixed) {
+      unsigned long long rm = 0;
+      unsigned int de = 0;
+      KV_CHECK_CUDA(h, cudaMemcpyAsync(&rm, h->rmax, sizeof rm, cudaMemcpyDeviceToHost, s));
+      KV_CHECK_CUDA(h, cudaMemcpyAsync(&de, h->derr, sizeof de, cudaMemcpyDeviceToHost, s));
+      KV_CHECK_CUDA(h, cudaStreamSynchronize(s));
+      st->refine_residual = bits_to_double(rm);
+      st->device_error = (int)de;
+      if (de) return fail(h, KV_ERR_CUDA, "a bounded wait in a tensor-core kernel expired");
+    }
   }
   if (want && max_passes > 1 && !(rel < tol))
     return fail(h, KV_ERR_NOT_CONVERGED, "SIMPLE did not reach the tolerance in max_passes passes");
@@ -205,6 +224,9 @@ kv_status kv_create_grid(const kv_grid_desc* desc, void* stream, kv_handle* out)
   g.hx = 1.0 / g.nx;
   g.hy = 1.0 / g.ny;
   g.hz = 1.0 / g.nz;
+  g.ihx = (double)g.nx;
+  g.ihy = (double)g.ny;
+  g.ihz = (double)g.nz;
   g.nu = 1.0 / sqrt(desc->gr);
   g.kappa = 1.0 / (desc->pr * sqrt(desc->gr));
   g.bc = desc->spanwise_bc;
@@ -220,8 +242,11 @@ kv_status kv_create_grid(const kv_grid_desc* desc, void* stream, kv_handle* out)
     delete h;
     return st;
   }
+  std::vector<double> fwdm[3], invm[3];
   for (int a = 0; a < 3; ++a) {
-    std::vector<double> fwd, inv, lam;
+    std::vector<double>& fwd = fwdm[a];
+    std::vector<double>& inv = invm[a];
+    std::vector<double> lam;
     neumann_axis(n[a], fwd, inv, lam);
     if ((st = dalloc(h, &h->Wm[a], fwd.size())) || (st = dalloc(h, &h->Wm[3 + a], inv.size())) ||
         (st = dalloc(h, &h->lam[a], lam.size()))) {
@@ -240,6 +265,17 @@ kv_status kv_create_grid(const kv_grid_desc* desc, void* stream, kv_handle* out)
     free_all(h);
     delete h;
     return KV_ERR_CUDA;
+  }
+  if (desc->precision == KV_PREC_MIXED) {
+    const double* f3[3] = {fwdm[0].data(), fwdm[1].data(), fwdm[2].data()};
+    const double* i3[3] = {invm[0].data(), invm[1].data(), invm[2].data()};
+    st = kv_mixed_setup(h, f3, i3);
+    if (st != KV_OK) {
+      g_create_error = h->err;
+      free_all(h);
+      delete h;
+      return st;
+    }
   }
   *out = h;
   return KV_OK;

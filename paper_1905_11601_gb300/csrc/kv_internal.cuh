@@ -1,6 +1,8 @@
 // Internal declarations shared by the CUDA translation units of libkv.
 #pragma once
 
+#include <cuda.h>
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -10,13 +12,14 @@
 #include "kv.h"
 
 // timed phases (kv_profile_get)
-enum { KV_PH_STENCIL = 0, KV_PH_DIV = 1, KV_PH_TPD = 2, KV_PH_CORRECT = 3, KV_PH_ARNOLDI = 4, KV_NPHASE = 8 };
+enum { KV_PH_STENCIL = 0, KV_PH_DIV = 1, KV_PH_TPD = 2, KV_PH_CORRECT = 3, KV_PH_ARNOLDI = 4, KV_PH_REFINE = 5, KV_NPHASE = 8 };
 
 // Device-side description of the uniform MAC grid.
 struct KvGeom {
   int nx, ny, nz;   // cells per axis
   int X, Y, Z;      // padded extents n+2
   double hx, hy, hz;
+  double ihx, ihy, ihz;  // 1/h per axis (no FP64 division in the kernels)
   double nu, kappa; // Gr^-1/2 and (Pr Gr^1/2)^-1 (Eqs (1)-(2) scaling)
   int bc;           // KV_BC_CC / KV_BC_AA
   int tproj;        // KV_TPROJ_*
@@ -45,6 +48,17 @@ struct kv_grid {
   double* stage = nullptr;            // 8P: staging for the host-buffer entry point
   double* tmp4 = nullptr;             // 4P: residual right-hand side scratch
 
+  // mixed precision (KV_PREC_MIXED): BF16 slices of the six per-axis matrices, two ping-pong
+  // slice buffers for the data, FP32 eigenvalues, the tensor maps of the six contractions
+  int refine = 0;                        // Poisson refinement sweeps
+  __nv_bfloat16* wsl[6] = {};
+  __nv_bfloat16* xs[2] = {};
+  size_t xs_slice = 0;                   // elements per data slice
+  float* lamf[3] = {};
+  CUtensorMap mapA[6], mapB[6];
+  unsigned int* derr = nullptr;          // device error flag (bounded waits that expired)
+  unsigned long long* rmax = nullptr;    // max |r| of the last refinement residual (bits)
+
   // launch counting (always) and per-phase CUDA-event timing (when profiling is on)
   long long launches[KV_NPHASE] = {};
   bool prof_on = false;
@@ -66,6 +80,32 @@ struct KvPhase {
   KvPhase(kv_grid* h, int phase, int launches);
   ~KvPhase();
 };
+
+// kv_umma.cu
+struct KvUmmaEpi {
+  int mode;          // 0: BF16 slices of D; 1: slices of D / Lambda (Eq 17); 2: phi64 += D
+  int M, R;          // output rows / columns
+  int nb, na;        // r = a * nb + b; output address (m * na + a) * pitch + b
+  int pitch;         // padded fastest extent of the output layout
+  size_t slice;      // elements between output slices
+  __nv_bfloat16* out;
+  double* phi;       // mode 2
+  const float* lz;   // mode 1: eigenvalues of the contracted (m) axis, then of a and b
+  const float* la;
+  const float* lb;
+};
+bool kv_make_slice_map(CUtensorMap* map, const void* base, int cols, int rows, int pitch, size_t slice_elems,
+                       int box_rows);
+int kv_umma_box_rows_a();
+int kv_umma_box_rows_b();
+cudaError_t kv_launch_umma_axis(const CUtensorMap* mapA, const CUtensorMap* mapB, int K, const KvUmmaEpi& ep,
+                                unsigned int* err, cudaStream_t s);
+
+// kv_mixed.cu
+kv_status kv_mixed_setup(kv_grid* h, const double* const fwd[3], const double* const inv[3]);
+void kv_mixed_free(kv_grid* h);
+// phi = L^+ b to FP64 accuracy: BF16-split tensor-core TPF solve + FP64 residual refinement
+void kv_launch_poisson_mixed(kv_grid* h, const double* b, double* phi, cudaStream_t s);
 
 // kv_stencil.cu
 // mode 0: y* = J P_BC x (Eqs (11)-(12)); mode 1: y* = F(S) (steady residual, x = base = S).

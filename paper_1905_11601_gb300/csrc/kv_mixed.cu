@@ -1,0 +1,178 @@
+// Mixed-precision pressure-correction solve: phi = L^+ b (Eqs (14)-(18)) with the six per-axis
+// contractions on the tensor cores (BF16 slices, FP32 accumulation; kv_umma.cu), won back to
+// FP64 accuracy by iterative refinement with an FP64 residual:
+//
+//   phi = 0;  r = b
+//   repeat S times:  phi += TPF(r)   (six tcgen05 contractions, the last one adds into phi)
+//                    r = b - L phi   (FP64 7-point Neumann Laplacian, written as BF16 slices)
+//
+// Each sweep reduces the error by roughly the FP32 accuracy of one tensor-core solve.
+#include <math.h>
+
+#include <algorithm>
+#include <string>
+#include <vector>
+
+#include "kv_internal.cuh"
+
+namespace {
+
+int pad8(int n) { return (n + 7) & ~7; }
+
+// r = b - L phi (L = D G with homogeneous Neumann walls), FP64, then three BF16 slices of r
+// into the first contraction's input layout [k][j][i_pad]. phi == nullptr means phi = 0.
+__global__ void __launch_bounds__(256) k_residual_slices(KvGeom g, const double* __restrict__ b,
+                                                         const double* __restrict__ phi, __nv_bfloat16* __restrict__ xs,
+                                                         size_t slice, int pitch, unsigned long long* rmax) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = blockIdx.y * blockDim.y + threadIdx.y;
+  const int k = blockIdx.z;
+  double rv = 0.0;
+  if (i < g.nx && j < g.ny) {
+    const size_t sx = 1, sy = g.nx, sz = (size_t)g.nx * g.ny;
+    const size_t e = i + sy * j + sz * k;
+    double r = __ldg(b + e);
+    if (phi) {
+      const double c = __ldg(phi + e);
+      double lx = 0.0, ly = 0.0, lz = 0.0;
+      if (i > 0) lx += __ldg(phi + e - sx) - c;
+      if (i < g.nx - 1) lx += __ldg(phi + e + sx) - c;
+      if (j > 0) ly += __ldg(phi + e - sy) - c;
+      if (j < g.ny - 1) ly += __ldg(phi + e + sy) - c;
+      if (k > 0) lz += __ldg(phi + e - sz) - c;
+      if (k < g.nz - 1) lz += __ldg(phi + e + sz) - c;
+      r -= lx * (g.ihx * g.ihx) + ly * (g.ihy * g.ihy) + lz * (g.ihz * g.ihz);
+    }
+    rv = fabs(r);
+    const float rf = (float)r;
+    const __nv_bfloat16 s1 = __float2bfloat16_rn(rf);
+    const float r1 = rf - __bfloat162float(s1);
+    const __nv_bfloat16 s2 = __float2bfloat16_rn(r1);
+    const __nv_bfloat16 s3 = __float2bfloat16_rn(r1 - __bfloat162float(s2));
+    const size_t o = ((size_t)k * g.ny + j) * pitch + i;
+    xs[o] = s1;
+    xs[slice + o] = s2;
+    xs[2 * slice + o] = s3;
+  }
+  if (rmax) {
+    for (int off = 16; off > 0; off >>= 1) rv = fmax(rv, __shfl_xor_sync(0xffffffffu, rv, off));
+    if ((threadIdx.x & 31) == 0) atomicMax(rmax, (unsigned long long)__double_as_longlong(rv));
+  }
+}
+
+// Three BF16 slices of an M x K FP64 matrix, rows padded to pitch (zero padding).
+void split_matrix(const double* W, int M, int K, std::vector<__nv_bfloat16>& out) {
+  const int pitch = pad8(K);
+  const size_t slice = (size_t)M * pitch;
+  out.assign(3 * slice, __float2bfloat16(0.0f));
+  for (int m = 0; m < M; ++m)
+    for (int k = 0; k < K; ++k) {
+      double rem = W[(size_t)m * K + k];
+      for (int s = 0; s < 3; ++s) {
+        const __nv_bfloat16 v = __float2bfloat16_rn((float)rem);
+        out[s * slice + (size_t)m * pitch + k] = v;
+        rem -= (double)__bfloat162float(v);
+      }
+    }
+}
+
+struct PassSpec {
+  int axis;  // contracted axis (0 = x, 1 = y, 2 = z)
+  int a, b;  // axes of the output column index r = a * n_b + b
+};
+// forward x, y, z then inverse x, y, z; see kv_tpd.cu for the rotation of the axes
+const PassSpec kPass[6] = {{0, 2, 1}, {1, 0, 2}, {2, 1, 0}, {0, 2, 1}, {1, 0, 2}, {2, 1, 0}};
+
+}  // namespace
+
+kv_status kv_mixed_setup(kv_grid* h, const double* const fwd[3], const double* const inv[3]) {
+  const int n[3] = {h->g.nx, h->g.ny, h->g.nz};
+  h->refine = h->d.refine_sweeps > 0 ? h->d.refine_sweeps : 2;
+  // data slice buffers: the largest of the six layouts (rows x padded fastest extent)
+  size_t cap = 0;
+  for (int a = 0; a < 3; ++a) cap = std::max(cap, h->Nc / n[a] * (size_t)pad8(n[a]));
+  h->xs_slice = cap;
+  cudaError_t e;
+  for (int q = 0; q < 2; ++q)
+    if ((e = cudaMalloc(&h->xs[q], 3 * cap * sizeof(__nv_bfloat16))) != cudaSuccess) goto fail;
+  for (int p = 0; p < 6; ++p) {
+    const int a = kPass[p].axis;
+    const double* W = p < 3 ? fwd[a] : inv[a];
+    std::vector<__nv_bfloat16> sl;
+    split_matrix(W, n[a], n[a], sl);
+    if ((e = cudaMalloc(&h->wsl[p], sl.size() * sizeof(__nv_bfloat16))) != cudaSuccess) goto fail;
+    if ((e = cudaMemcpy(h->wsl[p], sl.data(), sl.size() * sizeof(__nv_bfloat16), cudaMemcpyHostToDevice)) !=
+        cudaSuccess)
+      goto fail;
+  }
+  for (int a = 0; a < 3; ++a) {
+    std::vector<double> lam(n[a]);
+    if ((e = cudaMemcpy(lam.data(), h->lam[a], n[a] * sizeof(double), cudaMemcpyDeviceToHost)) != cudaSuccess)
+      goto fail;
+    std::vector<float> lf(lam.begin(), lam.end());
+    if ((e = cudaMalloc(&h->lamf[a], n[a] * sizeof(float))) != cudaSuccess) goto fail;
+    if ((e = cudaMemcpy(h->lamf[a], lf.data(), n[a] * sizeof(float), cudaMemcpyHostToDevice)) != cudaSuccess) goto fail;
+  }
+  if ((e = cudaMalloc(&h->derr, sizeof(unsigned int))) != cudaSuccess) goto fail;
+  if ((e = cudaMemset(h->derr, 0, sizeof(unsigned int))) != cudaSuccess) goto fail;
+  if ((e = cudaMalloc(&h->rmax, sizeof(unsigned long long))) != cudaSuccess) goto fail;
+  for (int p = 0; p < 6; ++p) {
+    const int a = kPass[p].axis;
+    const int K = n[a], M = n[a];
+    const int R = (int)(h->Nc / n[a]);
+    const __nv_bfloat16* in = h->xs[p % 2];
+    if (!kv_make_slice_map(&h->mapA[p], h->wsl[p], K, M, pad8(K), (size_t)M * pad8(K), kv_umma_box_rows_a()) ||
+        !kv_make_slice_map(&h->mapB[p], in, K, R, pad8(K), h->xs_slice, kv_umma_box_rows_b())) {
+      h->err = "cuTensorMapEncodeTiled failed";
+      return KV_ERR_CUDA;
+    }
+  }
+  return KV_OK;
+fail:
+  h->err = std::string("mixed-precision set-up: ") + cudaGetErrorString(e);
+  return e == cudaErrorMemoryAllocation ? KV_ERR_NOMEM : KV_ERR_CUDA;
+}
+
+void kv_mixed_free(kv_grid* h) {
+  for (int q = 0; q < 2; ++q) cudaFree(h->xs[q]);
+  for (int p = 0; p < 6; ++p) cudaFree(h->wsl[p]);
+  for (int a = 0; a < 3; ++a) cudaFree(h->lamf[a]);
+  cudaFree(h->derr);
+  cudaFree(h->rmax);
+}
+
+void kv_launch_poisson_mixed(kv_grid* h, const double* b, double* phi, cudaStream_t s) {
+  const KvGeom& g = h->g;
+  const int n[3] = {g.nx, g.ny, g.nz};
+  dim3 rb(32, 8, 1), rg((g.nx + 31) / 32, (g.ny + 7) / 8, g.nz);
+  cudaMemsetAsync(phi, 0, h->Nc * sizeof(double), s);
+  cudaMemsetAsync(h->rmax, 0, sizeof(unsigned long long), s);
+  {
+    KvPhase ph(h, KV_PH_REFINE, 1);
+    k_residual_slices<<<rg, rb, 0, s>>>(g, b, nullptr, h->xs[0], h->xs_slice, pad8(g.nx), nullptr);
+  }
+  for (int sweep = 0; sweep < h->refine; ++sweep) {
+    for (int p = 0; p < 6; ++p) {
+      const PassSpec& ps = kPass[p];
+      KvUmmaEpi ep{};
+      ep.M = n[ps.axis];
+      ep.R = (int)(h->Nc / n[ps.axis]);
+      ep.na = n[ps.a];
+      ep.nb = n[ps.b];
+      ep.pitch = pad8(n[ps.b]);
+      ep.slice = h->xs_slice;
+      ep.out = h->xs[(p + 1) % 2];
+      ep.mode = (p == 2) ? 1 : (p == 5 ? 2 : 0);
+      ep.phi = phi;
+      ep.lz = h->lamf[ps.axis];
+      ep.la = h->lamf[ps.a];
+      ep.lb = h->lamf[ps.b];
+      KvPhase ph(h, KV_PH_TPD, 1);
+      kv_launch_umma_axis(&h->mapA[p], &h->mapB[p], n[ps.axis], ep, h->derr, s);
+    }
+    if (sweep + 1 < h->refine) {
+      KvPhase ph(h, KV_PH_REFINE, 1);
+      k_residual_slices<<<rg, rb, 0, s>>>(g, b, phi, h->xs[0], h->xs_slice, pad8(g.nx), h->rmax);
+    }
+  }
+}

@@ -15,8 +15,8 @@ __global__ void __launch_bounds__(256) k_divergence(KvGeom g, const double* __re
   const double* v = vel + P;
   const double* w = vel + 2 * P;
   const int e = i + g.X * (j + g.Y * k);
-  const double d = (__ldg(u + e) - __ldg(u + e - 1)) / g.hx + (__ldg(v + e) - __ldg(v + e - g.X)) / g.hy +
-                   (__ldg(w + e) - __ldg(w + e - g.X * g.Y)) / g.hz;
+  const double d = (__ldg(u + e) - __ldg(u + e - 1)) * g.ihx + (__ldg(v + e) - __ldg(v + e - g.X)) * g.ihy +
+                   (__ldg(w + e) - __ldg(w + e - g.X * g.Y)) * g.ihz;
   b[(i - 1) + (size_t)g.nx * ((j - 1) + (size_t)g.ny * (k - 1))] = d;
 }
 
@@ -35,15 +35,15 @@ struct Corr {
   __device__ __forceinline__ int at(int i, int j, int k) const { return i + g.X * (j + g.Y * k); }
   __device__ __forceinline__ double u(int i, int j, int k) const {
     if (!(i >= 1 && i <= g.nx - 1 && j >= 1 && j <= g.ny && k >= 1 && k <= g.nz)) return 0.0;
-    return __ldg(vs + at(i, j, k)) - (ph(i + 1, j, k) - ph(i, j, k)) / g.hx;
+    return __ldg(vs + at(i, j, k)) - (ph(i + 1, j, k) - ph(i, j, k)) * g.ihx;
   }
   __device__ __forceinline__ double v(int i, int j, int k) const {
     if (!(i >= 1 && i <= g.nx && j >= 1 && j <= g.ny - 1 && k >= 1 && k <= g.nz)) return 0.0;
-    return __ldg(vs + P + at(i, j, k)) - (ph(i, j + 1, k) - ph(i, j, k)) / g.hy;
+    return __ldg(vs + P + at(i, j, k)) - (ph(i, j + 1, k) - ph(i, j, k)) * g.ihy;
   }
   __device__ __forceinline__ double w(int i, int j, int k) const {
     if (!(i >= 1 && i <= g.nx && j >= 1 && j <= g.ny && k >= 1 && k <= g.nz - 1)) return 0.0;
-    return __ldg(vs + 2 * P + at(i, j, k)) - (ph(i, j, k + 1) - ph(i, j, k)) / g.hz;
+    return __ldg(vs + 2 * P + at(i, j, k)) - (ph(i, j, k + 1) - ph(i, j, k)) * g.ihz;
   }
 };
 
@@ -65,7 +65,7 @@ __global__ void __launch_bounds__(256) k_correct(KvGeom g, const double* __restr
     vmax = fmax(fabs(ur), fmax(fabs(vr), fabs(wr)));
     const bool cell = i >= 1 && i <= g.nx && j >= 1 && j <= g.ny && k >= 1 && k <= g.nz;
     if (cell) {
-      const double d = (ur - C.u(i - 1, j, k)) / g.hx + (vr - C.v(i, j - 1, k)) / g.hy + (wr - C.w(i, j, k - 1)) / g.hz;
+      const double d = (ur - C.u(i - 1, j, k)) * g.ihx + (vr - C.v(i, j - 1, k)) * g.ihy + (wr - C.w(i, j, k - 1)) * g.ihz;
       dmax = fabs(d);
     }
     if (p) {

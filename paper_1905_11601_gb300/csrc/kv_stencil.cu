@@ -109,7 +109,7 @@ __global__ void __launch_bounds__(256) k_stencil(KvGeom g, const double* __restr
   // base flow (raw) and input (projected in MODE 0)
   Loader<false> B{G, base, base + P, base + 2 * P, base + 3 * P};
   Loader<PROJ> Xl{G, x, x + P, x + 2 * P, x + 3 * P};
-  const double ihx = 1.0 / g.hx, ihy = 1.0 / g.hy, ihz = 1.0 / g.hz;
+  const double ihx = g.ihx, ihy = g.ihy, ihz = g.ihz;
   const double ihx2 = ihx * ihx, ihy2 = ihy * ihy, ihz2 = ihz * ihz;
 
   // ---- u on the x-face (i, j, k) ----

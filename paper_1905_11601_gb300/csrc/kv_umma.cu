@@ -1,0 +1,304 @@
+// Mixed-precision TPF Poisson solve (Eqs (14)-(18)) on the 5th-generation tensor cores.
+//
+// Each per-axis contraction D[m][r] = sum_k W[m][k] X[r][k] runs as a BF16 x BF16 -> FP32
+// tcgen05 GEMM: W (the FP64 1D eigenvector matrix) and X (the data) are each split into
+// three BF16 slices (x = x1 + x2 + x3, x1 = bf16(x), x2 = bf16(x - x1), x3 = bf16(x - x1 - x2),
+// about 24 significant bits), and the six slice products with i + j <= 4 are accumulated in
+// one FP32 TMEM accumulator, which gives about FP32 accuracy. The FP64 accuracy of the solve
+// is won back by iterative refinement with an FP64 residual r = b - L phi (kv_mixed.cu).
+//
+// Kernel structure (one 128 x 256 output tile per CTA, cta_group::1):
+//   warp 0      TMA producer: per stage one 128 x 64 tile of W_i and one 256 x 64 tile of X_j
+//               (128-byte swizzle), completion on a full[] mbarrier;
+//   warp 1      allocates 256 TMEM columns; lane 0 issues tcgen05.mma (M=128, N=256, K=16) and
+//               tcgen05.commit to the empty[] barrier of each stage and, last, to acc_full;
+//   warps 2-5   epilogue: tcgen05.ld of the accumulator, transposed through shared memory so
+//               that stores run along r, then either the next pass's three BF16 slices (with
+//               the 1 / Lambda scaling of Eq (17) in the third forward pass) or phi += D (FP64).
+// Every mbarrier wait has an iteration limit; on expiry the kernel sets an error flag and
+// leaves without hanging.
+#include <cuda.h>
+#include <cuda_bf16.h>
+
+#include "kv_internal.cuh"
+
+namespace {
+
+constexpr int UM = 128, UN = 256, UK = 64;  // CTA tile; UK = one 128-byte swizzle row of BF16
+constexpr int STAGES = 4;
+constexpr int A_BYTES = UM * UK * 2;        // 16 KB
+constexpr int B_BYTES = UN * UK * 2;        // 32 KB
+constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
+constexpr int EPI_WARPS = 4;
+constexpr int EPI_STRIDE = 33;              // floats per transposed row (bank-conflict free)
+constexpr int SMEM_BYTES = 1024 /*alignment slack*/ + STAGES * STAGE_BYTES +
+                           EPI_WARPS * 32 * EPI_STRIDE * 4 + 256 /*barriers + tmem slot*/;
+constexpr uint32_t WAIT_LIMIT = 1u << 24;
+constexpr int NPAIRS = 6;
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+// Bounded wait for the phase with the given parity; false (and the error flag set) on expiry.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, unsigned int* err) {
+  for (uint32_t it = 0; it < WAIT_LIMIT; ++it) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    if (ok) return true;
+  }
+  atomicOr(err, 1u);
+  return false;
+}
+
+__device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap* map, int c0, int c1, int c2,
+                                            uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], "
+      "[%5];" ::"r"(dst),
+      "l"((uint64_t)map), "r"(c0), "r"(c1), "r"(c2), "r"(bar)
+      : "memory");
+}
+
+// Shared-memory matrix descriptor (K-major operand, 128-byte swizzle, 8-row groups of 1024 B).
+__device__ __forceinline__ uint64_t sdesc(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);  // start address
+  d |= (uint64_t)1 << 16;                    // leading byte offset (unused for swizzled K-major)
+  d |= (uint64_t)(1024 >> 4) << 32;          // stride byte offset: next 8-row group
+  d |= (uint64_t)1 << 46;                    // descriptor version
+  d |= (uint64_t)2 << 61;                    // 128-byte swizzle
+  return d;
+}
+
+// Instruction descriptor, kind::f16: BF16 A and B (K-major), FP32 accumulator, M = 128, N = 256.
+constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(UN >> 3) << 17) |
+                           ((uint32_t)(UM >> 4) << 24);
+
+__device__ __forceinline__ void umma_bf16(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem_d),
+      "l"(a), "l"(b), "r"(IDESC), "r"(accumulate)
+      : "memory");
+}
+__device__ __forceinline__ void umma_commit(uint32_t bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
+               : "memory");
+}
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
+  uint32_t r[32];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+      "%15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+        "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+        "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int q = 0; q < 32; ++q) v[q] = __uint_as_float(r[q]);
+}
+
+// three-way BF16 split of an FP32 value
+__device__ __forceinline__ void split3(float x, __nv_bfloat16& s1, __nv_bfloat16& s2, __nv_bfloat16& s3) {
+  s1 = __float2bfloat16_rn(x);
+  const float r1 = x - __bfloat162float(s1);
+  s2 = __float2bfloat16_rn(r1);
+  const float r2 = r1 - __bfloat162float(s2);
+  s3 = __float2bfloat16_rn(r2);
+}
+
+// Slice pairs (i, j), 0-based, with i + j <= 2, smallest products first.
+__constant__ int kPairA[NPAIRS] = {2, 1, 0, 1, 0, 0};
+__constant__ int kPairB[NPAIRS] = {0, 1, 2, 0, 1, 0};
+
+}  // namespace
+
+
+namespace {
+
+__global__ void __launch_bounds__(192, 1)
+    k_umma_axis(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB, int K,
+                KvUmmaEpi ep, unsigned int* err) {
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  float* epi = (float*)(smem + STAGES * STAGE_BYTES);
+  uint64_t* bars = (uint64_t*)(epi + EPI_WARPS * 32 * EPI_STRIDE);
+  uint32_t* tmem_slot = (uint32_t*)(bars + 2 * STAGES + 1);
+  const uint32_t full0 = smem_u32(bars), empty0 = smem_u32(bars + STAGES), accb = smem_u32(bars + 2 * STAGES);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int m0 = blockIdx.y * UM, r0 = blockIdx.x * UN;
+  const int kchunks = (K + UK - 1) / UK;
+  const int iters = NPAIRS * kchunks;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < STAGES; ++s) {
+      mbar_init(full0 + 8 * s, 1);
+      mbar_init(empty0 + 8 * s, 1);
+    }
+    mbar_init(accb, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                 "r"(UN)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+
+  if (warp == 0) {
+    if (lane == 0) {
+      asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)&mapA) : "memory");
+      asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)&mapB) : "memory");
+      for (int it = 0; it < iters; ++it) {
+        const int s = it % STAGES;
+        const uint32_t ph = (uint32_t)(it / STAGES) & 1u;
+        if (!mbar_wait(empty0 + 8 * s, ph ^ 1u, err)) break;
+        const int pair = it / kchunks, kc = it % kchunks;
+        const uint32_t a = smem_u32(smem + s * STAGE_BYTES), b = a + A_BYTES;
+        mbar_expect_tx(full0 + 8 * s, STAGE_BYTES);
+        tma_load_3d(a, &mapA, kc * UK, m0, kPairA[pair], full0 + 8 * s);
+        tma_load_3d(b, &mapB, kc * UK, r0, kPairB[pair], full0 + 8 * s);
+      }
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      bool ok = true;
+      for (int it = 0; it < iters && ok; ++it) {
+        const int s = it % STAGES;
+        const uint32_t ph = (uint32_t)(it / STAGES) & 1u;
+        ok = mbar_wait(full0 + 8 * s, ph, err);
+        if (!ok) break;
+        tc_fence_after();
+        const uint32_t a = smem_u32(smem + s * STAGE_BYTES), b = a + A_BYTES;
+#pragma unroll
+        for (int kk = 0; kk < UK / 16; ++kk)
+          umma_bf16(tmem, sdesc(a + kk * 32), sdesc(b + kk * 32), (it > 0 || kk > 0) ? 1u : 0u);
+        umma_commit(empty0 + 8 * s);
+      }
+      umma_commit(accb);  // arrives once every MMA issued above has completed
+    }
+  } else {
+    // epilogue warps 2..5 -> TMEM lane quarter (warp % 4)
+    const int q = warp & 3;
+    float* tb = epi + (warp - 2) * 32 * EPI_STRIDE;
+    if (mbar_wait(accb, 0, err)) {
+      tc_fence_after();
+      const int mrow0 = m0 + 32 * q;
+      for (int c = 0; c < UN; c += 32) {
+        float v[32];
+        tmem_ld32(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)c, v);
+        // transpose: tb[col][row]
+#pragma unroll
+        for (int t = 0; t < 32; ++t) tb[t * EPI_STRIDE + lane] = v[t];
+        __syncwarp();
+        const int r = r0 + c + lane;
+        if (r < ep.R) {
+          int a = 0, bcol = r;
+          if (ep.mode != 2) {
+            a = r / ep.nb;
+            bcol = r - a * ep.nb;
+          }
+          for (int row = 0; row < 32; ++row) {
+            const int m = mrow0 + row;
+            if (m >= ep.M) break;
+            float d = tb[lane * EPI_STRIDE + row];
+            if (ep.mode == 2) {
+              ep.phi[(size_t)m * ep.R + r] += (double)d;
+            } else {
+              if (ep.mode == 1) {
+                const float lam = ep.lz[m] + ep.la[a] + ep.lb[bcol];
+                d = (m == 0 && r == 0) ? 0.0f : __fdividef(d, lam);
+              }
+              __nv_bfloat16 s1, s2, s3;
+              split3(d, s1, s2, s3);
+              const size_t o = ((size_t)m * ep.na + a) * ep.pitch + bcol;
+              ep.out[o] = s1;
+              ep.out[ep.slice + o] = s2;
+              ep.out[2 * ep.slice + o] = s3;
+            }
+          }
+        }
+        __syncwarp();
+      }
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(UN) : "memory");
+  }
+}
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encode_fn() {
+  static EncodeTiledFn fn = nullptr;
+  if (!fn) {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = (EncodeTiledFn)p;
+  }
+  return fn;
+}
+
+}  // namespace
+
+// 3D BF16 tensor map over `slices` arrays of rows x cols (row pitch `pitch` elements), box
+// 64 x box_rows x 1, 128-byte swizzle, zero fill outside [0, cols) x [0, rows).
+bool kv_make_slice_map(CUtensorMap* map, const void* base, int cols, int rows, int pitch, size_t slice_elems,
+                       int box_rows) {
+  EncodeTiledFn fn = encode_fn();
+  if (!fn) return false;
+  cuuint64_t dims[3] = {(cuuint64_t)cols, (cuuint64_t)rows, 3};
+  cuuint64_t strides[2] = {(cuuint64_t)pitch * 2, (cuuint64_t)slice_elems * 2};
+  cuuint32_t box[3] = {(cuuint32_t)UK, (cuuint32_t)box_rows, 1};
+  cuuint32_t estr[3] = {1, 1, 1};
+  CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<void*>(base), dims, strides, box, estr,
+                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS;
+}
+
+int kv_umma_box_rows_a() { return UM; }
+int kv_umma_box_rows_b() { return UN; }
+
+cudaError_t kv_launch_umma_axis(const CUtensorMap* mapA, const CUtensorMap* mapB, int K, const KvUmmaEpi& ep,
+                                unsigned int* err, cudaStream_t s) {
+  static bool attr = false;
+  if (!attr) {
+    cudaError_t e = cudaFuncSetAttribute(k_umma_axis, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  dim3 grid((ep.R + UN - 1) / UN, (ep.M + UM - 1) / UM);
+  k_umma_axis<<<grid, 192, SMEM_BYTES, s>>>(*mapA, *mapB, K, ep, err);
+  return cudaGetLastError();
+}

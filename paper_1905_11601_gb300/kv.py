@@ -16,7 +16,7 @@ LIB_PATH = os.path.join(_PKG, "libkv.so")
 
 KV_BC_CC, KV_BC_AA = 0, 1
 KV_TPROJ_ORTHOGONAL, KV_TPROJ_OBLIQUE = 0, 1
-KV_PREC_FP64 = 0
+KV_PREC_FP64, KV_PREC_MIXED = 0, 1
 
 _STATUS = {0: "KV_OK", -1: "KV_ERR_ARG", -2: "KV_ERR_CUDA", -3: "KV_ERR_NOT_CONVERGED", -4: "KV_ERR_STATE",
            -5: "KV_ERR_NOMEM"}
@@ -25,7 +25,7 @@ _STATUS = {0: "KV_OK", -1: "KV_ERR_ARG", -2: "KV_ERR_CUDA", -3: "KV_ERR_NOT_CONV
 EXPORTS = ("kv_create_grid", "kv_destroy_grid", "kv_set_stream", "kv_field_len", "kv_set_base_flow",
            "kv_krylov_vector", "kv_krylov_vector_host", "kv_arnoldi_step", "kv_newton_residual", "kv_last_error",
            "kv_profile_enable", "kv_profile_get")
-PHASES = {"stencil": 0, "divergence": 1, "tpd": 2, "correct": 3, "arnoldi": 4}
+PHASES = {"stencil": 0, "divergence": 1, "tpd": 2, "correct": 3, "arnoldi": 4, "refine": 5}
 
 
 class KvError(RuntimeError):
@@ -38,11 +38,12 @@ class GridDesc(ctypes.Structure):
     _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int),
                 ("spanwise_bc", ctypes.c_int), ("tproj", ctypes.c_int), ("precision", ctypes.c_int),
                 ("gr", ctypes.c_double), ("pr", ctypes.c_double), ("tol", ctypes.c_double),
-                ("max_passes", ctypes.c_int)]
+                ("max_passes", ctypes.c_int), ("refine_sweeps", ctypes.c_int)]
 
 
 class Stats(ctypes.Structure):
-    _fields_ = [("passes", ctypes.c_int), ("max_div", ctypes.c_double), ("rel_div", ctypes.c_double)]
+    _fields_ = [("passes", ctypes.c_int), ("max_div", ctypes.c_double), ("rel_div", ctypes.c_double),
+                ("refine_residual", ctypes.c_double), ("device_error", ctypes.c_int)]
 
 
 _lib = None
@@ -93,7 +94,7 @@ class Grid:
     """A grid handle: kv_create_grid / kv_destroy_grid around the calls of include/kv.h."""
 
     def __init__(self, nx, ny, nz, bc=KV_BC_CC, gr=1.0e6, pr=0.71, tproj=KV_TPROJ_ORTHOGONAL,
-                 precision=KV_PREC_FP64, tol=0.0, max_passes=0):
+                 precision=KV_PREC_FP64, tol=0.0, max_passes=0, refine_sweeps=0):
         import torch
 
         self.torch = torch
@@ -101,7 +102,7 @@ class Grid:
             raise RuntimeError("libkv needs a CUDA device")
         self.lib = load_library()
         self.nx, self.ny, self.nz = nx, ny, nz
-        self.desc = GridDesc(nx, ny, nz, bc, tproj, precision, gr, pr, tol, max_passes)
+        self.desc = GridDesc(nx, ny, nz, bc, tproj, precision, gr, pr, tol, max_passes, refine_sweeps)
         h = ctypes.c_void_p()
         st = self.lib.kv_create_grid(ctypes.byref(self.desc), ctypes.c_void_p(self._stream()), ctypes.byref(h))
         if st != 0:
