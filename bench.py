@@ -4,7 +4,10 @@
 One step = one Arnoldi step on the 256^3 grid: the Krylov vector y = (Pi_v (+) P_T) J P_BC x
 (linearised operator stencil, divergence, TPF Poisson solve, velocity correction and temperature
 projection) followed by classical Gram-Schmidt (twice) against the current basis and the
-normalisation; the basis is restarted every --restart vectors. Inputs are seeded synthetic base
+normalisation; the basis is restarted every --restart vectors. The headline value is the
+mixed-precision path (tensor-core Poisson contractions refined to FP64 accuracy); the plain FP64
+path is timed on the same workload and reported beside it, with the mixed result's relative
+error against it. Inputs are seeded synthetic base
 flows and vectors (no dataset), resident in HBM before the timed region; every vector (551 MB)
 is larger than L2, so no L2 flush is needed between steps.
 
@@ -32,6 +35,10 @@ sys.path.insert(0, ROOT)
 METRIC = "Krylov-vector evals/s at 256^3: mixed vs FP64 plain at 1e-9 rel err; roofline %"
 UNIT = "Krylov-vector evals/s"
 FP64_PEAK_TFLOPS = 1.25  # nominal GB300 FP64 rate (an FMA-loop probe measured 1.20)
+FP64_PEAK_SRC = "nominal GB300 FP64 rate (FMA-loop probe on this pool: 1.20 TFLOP/s)"
+# The assembled Jacobian J has 60 nonzeros per cell: 15 per velocity face (7 own-field points, 4 + 4
+# cross-component points), 13 per temperature cell (7 + 2 + 2 + 2) and 2 for the buoyancy term.
+STENCIL_FLOPS_PER_CELL = 2 * 60
 
 
 def parse_args():
@@ -44,6 +51,8 @@ def parse_args():
     ap.add_argument("--restart", type=int, default=20)
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--single", choices=["fp64", "mixed"], default=None,
+                    help="profiling case: two untimed Krylov-vector evaluations, no JSON line")
     return ap.parse_args()
 
 
@@ -125,6 +134,19 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+def bf16_peak():
+    """Dense BF16 tensor peak (TFLOP/s) for a kernel timed inside a long step: the sustained figure."""
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        d = json.load(open(path))
+        for key in ("bf16_tflops_sustained", "bf16_sustained_tflops"):
+            if key in d and isinstance(d[key], (int, float)):
+                return float(d[key]), "MEASURED_PEAKS.json (sustained)"
+    except Exception:
+        pass
+    return 1730.0, "measured sustained cuBLAS BF16 on this pool's GB300 (1730 TFLOP/s)"
+
+
 def source_sha(path):
     return hashlib.sha256(open(path, "rb").read()).hexdigest()[:16]
 
@@ -166,11 +188,91 @@ def run_reference(args):
     out = {"impl": "reference", "metric": METRIC, "value": r["value"], "unit": UNIT, "n_gpus": args.gpus,
            "steps": steps, "warmup": warm, "ms_per_step": 1000.0 / r["value"], "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-           "config": workload_desc(w, args.restart),
+           "config": workload_desc(w, args.restart, "mixed"),
            "cpu_baseline": {"value": r["value"], "unit": UNIT, "cores": r["cores"], "kind": "oracle",
                             "sample": sample},
            "e2e": {"value": r["value"], "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out), flush=True)
+
+
+def arnoldi_run(g, V, m, steps, warmup, dist, clocks_index=None):
+    """Times `steps` Arnoldi steps (after `warmup`) on the current stream; restart every m."""
+    import torch
+
+    state = {"j": 0}
+
+    def step():
+        j = state["j"]
+        if j == m:  # restart the basis from the last vector
+            V[0].copy_(V[m])
+            j = 0
+        g.arnoldi_step(V, j)
+        state["j"] = j + 1
+
+    for _ in range(warmup):
+        step()
+    stream = torch.cuda.current_stream()
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(clocks_index) if clocks_index is not None else None
+    g.profile_enable(True)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clk = clocks.stop() if clocks else None
+    ms = e0.elapsed_time(e1)
+    prof = g.profile()
+    g.profile_enable(False)
+    if dist:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    phases = {k: {"ms": v[0], "timed": v[1], "launches": v[2]} for k, v in prof.items()}
+    total = sum(p["ms"] for p in phases.values())
+    for p in phases.values():
+        p["share"] = p["ms"] / total if total else None
+    return ms, phases, clk
+
+
+def roofline(phases, w, precision, steps):
+    """Roofline of the dominant kernel (largest share of the timed region)."""
+    n3 = w.nx * w.ny * w.nz
+    dom = max(phases, key=lambda k: phases[k]["ms"])
+    hbm_peak, hbm_src = measured_peaks()
+    avg_ms = phases[dom]["ms"] / max(phases[dom]["timed"], 1)
+    if dom == "tpd" and precision == "fp64":
+        flops = 2.0 * (n3 * w.nx + n3 * w.ny + n3 * w.nz) / 3.0
+        ach = flops / (avg_ms / 1e3) / 1e12
+        return {"kernel": "k_gemm_axis (FP64 per-axis TPF contraction)", "bound": "alu", "achieved": ach,
+                "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": ach / FP64_PEAK_TFLOPS,
+                "traffic": traffic_for("k_gemm_axis"), "peak_source": FP64_PEAK_SRC,
+                "algorithmic": f"2 n^4 = {flops:.4g} flop per launch"}
+    if dom == "tpd":
+        flops = 6 * 2.0 * (n3 * w.nx + n3 * w.ny + n3 * w.nz) / 3.0
+        peak, src = bf16_peak()
+        ach = flops / (avg_ms / 1e3) / 1e12
+        return {"kernel": "k_umma_axis (tcgen05 BF16-slice TPF contraction)", "bound": "tensor", "achieved": ach,
+                "peak": peak, "unit": "TFLOP/s", "frac": ach / peak, "traffic": traffic_for("k_umma_axis"),
+                "peak_source": src, "algorithmic": f"6 slice products x 2 n^4 = {flops:.4g} flop per launch"}
+    if dom == "stencil":
+        flops = STENCIL_FLOPS_PER_CELL * n3
+        ach = flops / (avg_ms / 1e3) / 1e12
+        return {"kernel": "k_stencil (FP64 linearised operator)", "bound": "alu", "achieved": ach,
+                "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": ach / FP64_PEAK_TFLOPS,
+                "traffic": traffic_for("k_stencil"), "peak_source": FP64_PEAK_SRC,
+                "algorithmic": f"{STENCIL_FLOPS_PER_CELL} flop per cell (2 per Jacobian nonzero) = {flops:.4g} per launch"}
+    byts = {"arnoldi": None, "divergence": 4 * 8.0 * n3, "correct": 11 * 8.0 * n3, "refine": 5 * 8.0 * n3}.get(dom)
+    ach = byts / (avg_ms / 1e3) / 1e9 if byts else None
+    return {"kernel": dom, "bound": "hbm", "achieved": ach, "peak": hbm_peak, "unit": "GB/s",
+            "frac": ach / hbm_peak if ach else None, "traffic": None, "peak_source": hbm_src}
 
 
 def run_ours(args):
@@ -193,52 +295,35 @@ def run_ours(args):
     w = synth.WORKLOADS[args.workload]
     base_np, x_np = synth.workload_arrays(w)
     base = torch.from_numpy(np.stack(base_np)).cuda()
-    g = kv.Grid(w.nx, w.ny, w.nz, bc=w.bc, gr=w.gr, pr=w.pr)
-    g.set_base_flow(base)
-    m = args.restart
-    V = torch.zeros((m + 1, 4) + g.shape, dtype=torch.float64, device="cuda")
     x = torch.from_numpy(x_np[0]).cuda()
-    y0 = g.krylov_vector(x)
-    V[0] = y0 / torch.linalg.vector_norm(y0)
-    del y0
-    state = {"j": 0}
+    m = args.restart
+    results = {}
+    y_ref = None
+    for prec in ("fp64", "mixed"):
+        g = kv.Grid(w.nx, w.ny, w.nz, bc=w.bc, gr=w.gr, pr=w.pr,
+                    precision=kv.KV_PREC_MIXED if prec == "mixed" else kv.KV_PREC_FP64)
+        g.set_base_flow(base)
+        y0, st = g.krylov_vector(x, stats=True)
+        if prec == "fp64":
+            y_ref = y0.clone()
+            err = 0.0
+        else:
+            err = (torch.linalg.vector_norm(y0 - y_ref) / torch.linalg.vector_norm(y_ref)).item()
+            assert st.device_error == 0
+        V = torch.zeros((m + 1, 4) + g.shape, dtype=torch.float64, device="cuda")
+        V[0] = y0 / torch.linalg.vector_norm(y0)
+        del y0
+        ms, phases, clk = arnoldi_run(g, V, m, args.steps, args.warmup, dist,
+                                      clocks_index=local if (rank == 0 and prec == "mixed") else None)
+        results[prec] = {"g": g, "ms": ms, "phases": phases, "clocks": clk, "err": err,
+                         "rel_div": st.rel_div, "value": world * args.steps / (ms / 1000.0)}
+        del V
+        if prec == "fp64":
+            del g
+            results[prec].pop("g")
+            torch.cuda.empty_cache()
 
-    def step():
-        j = state["j"]
-        if j == m:  # restart the basis from the last vector
-            V[0].copy_(V[m])
-            j = 0
-        g.arnoldi_step(V, j)
-        state["j"] = j + 1
-
-    for _ in range(args.warmup):
-        step()
-    stream = torch.cuda.current_stream()
-    torch.cuda.synchronize()
-    if dist:
-        dist.barrier()
-    torch.cuda.synchronize()
-    clocks = ClockSampler(local) if rank == 0 else None
-    g.profile_enable(True)
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    for _ in range(args.steps):
-        step()
-    e1.record(stream)
-    torch.cuda.synchronize()
-    if dist:
-        dist.barrier()
-    torch.cuda.synchronize()
-    clk = clocks.stop() if clocks else None
-    ms = e0.elapsed_time(e1)
-    prof = g.profile()
-    g.profile_enable(False)
-    if dist:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    value = world * args.steps / (ms / 1000.0)
-
+    g = results["mixed"]["g"]
     # end to end through the host-buffer entry point (pinned host x and y, copies timed)
     xh = torch.from_numpy(x_np[0].copy()).pin_memory()
     yh = torch.empty_like(xh).pin_memory()
@@ -257,50 +342,31 @@ def run_ours(args):
     e2e_value = world * args.e2e_steps / e2e_s
     vec_bytes = xh.numel() * 8
 
-    # roofline of the dominant kernel (largest share of the timed region)
-    n3 = w.nx * w.ny * w.nz
-    phases = {k: {"ms": v[0], "timed": v[1], "launches": v[2]} for k, v in prof.items()}
-    dom = max(phases, key=lambda k: phases[k]["ms"])
-    hbm_peak, hbm_src = measured_peaks()
-    roof = None
-    if dom == "tpd":
-        flops = 2.0 * (n3 * w.nx + n3 * w.ny + n3 * w.nz) / 3.0  # average per contraction launch
-        avg_ms = phases["tpd"]["ms"] / max(phases["tpd"]["timed"], 1)
-        ach = flops / (avg_ms / 1000.0) / 1e12
-        roof = {"kernel": "k_gemm_axis (FP64 per-axis TPF contraction)", "bound": "alu", "achieved": ach,
-                "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": ach / FP64_PEAK_TFLOPS,
-                "traffic": traffic_for("k_gemm_axis"),
-                "peak_source": "nominal GB300 FP64 rate (FMA-loop probe on this pool: 1.20 TFLOP/s)",
-                "algorithmic": f"2 n^4 = {flops:.4g} flop per launch"}
-    elif dom == "stencil":
-        byts = 12.0 * 8.0 * n3
-        avg_ms = phases["stencil"]["ms"] / max(phases["stencil"]["timed"], 1)
-        ach = byts / (avg_ms / 1000.0) / 1e9
-        roof = {"kernel": "k_stencil", "bound": "hbm", "achieved": ach, "peak": hbm_peak, "unit": "GB/s",
-                "frac": ach / hbm_peak, "traffic": traffic_for("k_stencil"), "peak_source": hbm_src,
-                "algorithmic": f"12 fields x 8 B x n^3 = {byts:.4g} B per launch"}
-    else:
-        avg_ms = phases[dom]["ms"] / max(phases[dom]["timed"], 1)
-        roof = {"kernel": dom, "bound": "hbm", "achieved": None, "peak": hbm_peak, "unit": "GB/s",
-                "frac": None, "traffic": None, "peak_source": hbm_src}
-    total_prof = sum(p["ms"] for p in phases.values())
-    for p in phases.values():
-        p["share"] = p["ms"] / total_prof if total_prof else None
-    launches = int(sum(p["launches"] for p in phases.values()))
-
+    mx = results["mixed"]
+    fp = results["fp64"]
+    roof = roofline(mx["phases"], w, "mixed", args.steps)
+    launches = int(sum(p["launches"] for p in mx["phases"].values()))
     if rank != 0:
         if dist:
             dist.destroy_process_group()
         return
-    out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-           "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
-           "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded base flow and vectors)",
-           "config": workload_desc(w, m), "impl": "ours",
-           "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": vec_bytes, "d2h_bytes_per_step": vec_bytes,
-                   "path": "kv_krylov_vector_host (pinned host x and y, copies on the handle's stream)"},
-           "gpu_launches": launches, "roofline": roof, "clocks": clk,
+    out = {"metric": METRIC, "value": mx["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": mx["ms"] / args.steps, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+           "data": "synthetic (seeded base flow and vectors)", "config": workload_desc(w, m, "mixed"),
+           "impl": "ours",
+           "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": vec_bytes,
+                   "d2h_bytes_per_step": vec_bytes,
+                   "path": "kv_krylov_vector_host, mixed precision (pinned host x and y, copies on the handle's stream)"},
+           "gpu_launches": launches, "roofline": roof, "clocks": mx["clocks"],
+           "rel_err_vs_fp64": mx["err"],
            "phases": {k: {"ms_per_step": v["ms"] / args.steps, "share": v["share"],
-                          "launches_per_step": v["launches"] / args.steps} for k, v in phases.items()}}
+                          "launches_per_step": v["launches"] / args.steps} for k, v in mx["phases"].items()},
+           "fp64_plain": {"value": fp["value"], "ms_per_step": fp["ms"] / args.steps,
+                          "speedup_of_mixed": mx["value"] / fp["value"],
+                          "roofline": roofline(fp["phases"], w, "fp64", args.steps),
+                          "phases": {k: {"ms_per_step": v["ms"] / args.steps, "share": v["share"]}
+                                     for k, v in fp["phases"].items()}}}
     if world == 1 and not args.no_cpu_baseline:
         try:
             r = cpu_baseline(args.workload, 1, 0)
@@ -315,8 +381,32 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+def run_single(args):
+    """Two Krylov-vector evaluations of the workload (for a profiler's kernel capture)."""
+    import numpy as np
+    import torch
+
+    from paper_1905_11601_gb300 import build as kvbuild
+    from paper_1905_11601_gb300 import kv, synth
+
+    kvbuild.build()
+    w = synth.WORKLOADS[args.workload]
+    base_np, x_np = synth.workload_arrays(w)
+    g = kv.Grid(w.nx, w.ny, w.nz, bc=w.bc, gr=w.gr, pr=w.pr,
+                precision=kv.KV_PREC_MIXED if args.single == "mixed" else kv.KV_PREC_FP64)
+    g.set_base_flow(torch.from_numpy(np.stack(base_np)).cuda())
+    x = torch.from_numpy(x_np[0]).cuda()
+    for _ in range(2):
+        y, st = g.krylov_vector(x, stats=True)
+    torch.cuda.synchronize()
+    print(f"single {args.single} {w.name}: rel_div {st.rel_div:.2e} device_error {st.device_error}")
+
+
 def main():
     args = parse_args()
+    if args.single:
+        run_single(args)
+        return
     if args.impl == "reference":
         run_reference(args)
     else:
