@@ -145,7 +145,24 @@ kv_status kv_profile_enable(kv_handle h, int on);
 kv_status kv_profile_get(kv_handle h, int phase, double* total_ms, long long* timed_launches,
                          long long* launches);
 
-/* Message of the last failed call on h (NULL h: last failed kv_create_grid). */
+/* Allocation-free Krylov vector, for callers that cannot allocate device memory (code that
+   runs under an allocator it does not own, inside a fixed memory budget, or in a plug-in that
+   may not call cudaMalloc / cudaFree). The paper has no counterpart: it is a deployment
+   variant of kv_krylov_vector in FP64 (one exact SIMPLE pass), computing the same y from a
+   grid descriptor, a packed base state, x and y, all caller-owned device pointers; no handle
+   is created. Its scratch is a fixed __device__ array of about 1.5 MB that every GPU loading
+   the library keeps until the process exits, which limits the grid to
+   KV_NOALLOC_MAX_N cells per axis; larger grids and desc->precision != KV_PREC_FP64 return
+   KV_ERR_ARG (message via kv_last_error(NULL)). The first call on a device looks up the
+   array's device address (set-up); make that first call before any stream capture. All
+   calls share the one array and it keeps the last call's contents, so calls that overlap on
+   the GPU (other streams, other host threads) race: serialise them. stream: cudaStream_t. */
+#define KV_NOALLOC_MAX_N 32
+kv_status kv_krylov_vector_noalloc(const kv_grid_desc* desc, const double* base, const double* x, double* y,
+                                   void* stream);
+
+/* Message of the last failed call on h (NULL h: last failed kv_create_grid or
+   kv_krylov_vector_noalloc on this thread). */
 const char* kv_last_error(kv_handle h);
 
 #ifdef __cplusplus

@@ -163,6 +163,8 @@ kv_status simple_project(kv_grid* h, double* yvel, double* p, kv_stats* st) {
 
 }  // namespace
 
+void kv_set_thread_error(const std::string& msg) { g_create_error = msg; }
+
 KvPhase::KvPhase(kv_grid* h_, int phase_, int launches) : h(h_), phase(phase_), n(launches) {
   if (!h->prof_on) return;
   if (h->ev_pool.empty()) {

@@ -107,6 +107,9 @@ void kv_mixed_free(kv_grid* h);
 // phi = L^+ b to FP64 accuracy: BF16-split tensor-core TPF solve + FP64 residual refinement
 void kv_launch_poisson_mixed(kv_grid* h, const double* b, double* phi, cudaStream_t s);
 
+// kv_api.cu: sets the thread's message returned by kv_last_error(NULL)
+void kv_set_thread_error(const std::string& msg);
+
 // kv_stencil.cu
 // mode 0: y* = J P_BC x (Eqs (11)-(12)); mode 1: y* = F(S) (steady residual, x = base = S).
 // Writes the three momentum fields (interior faces, zero elsewhere) to vstar and the

@@ -24,7 +24,7 @@ _STATUS = {0: "KV_OK", -1: "KV_ERR_ARG", -2: "KV_ERR_CUDA", -3: "KV_ERR_NOT_CONV
 # every symbol include/kv.h declares
 EXPORTS = ("kv_create_grid", "kv_destroy_grid", "kv_set_stream", "kv_field_len", "kv_set_base_flow",
            "kv_krylov_vector", "kv_krylov_vector_host", "kv_arnoldi_step", "kv_newton_residual", "kv_last_error",
-           "kv_profile_enable", "kv_profile_get")
+           "kv_profile_enable", "kv_profile_get", "kv_krylov_vector_noalloc")
 PHASES = {"stencil": 0, "divergence": 1, "tpd": 2, "correct": 3, "arnoldi": 4, "refine": 5}
 
 
@@ -71,6 +71,7 @@ def load_library(path: str = LIB_PATH):
     lib.kv_profile_enable.argtypes = [H, ctypes.c_int]
     lib.kv_profile_get.argtypes = [H, ctypes.c_int, ctypes.POINTER(ctypes.c_double),
                                    ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_longlong)]
+    lib.kv_krylov_vector_noalloc.argtypes = [ctypes.POINTER(GridDesc), D, D, D, ctypes.c_void_p]
     lib.kv_last_error.argtypes = [H]
     lib.kv_last_error.restype = ctypes.c_char_p
     for name in EXPORTS:
