@@ -447,13 +447,25 @@ void or_project_input(const or_ctx* c, const double* x, double* out) {
      T* = (Pr Gr^1/2)^-1 Lap T - (U.grad) T - (v.grad) Theta          (cells)
      v* = Gr^-1/2 Lap v - (U.grad) v - (v.grad) U + T e_z              (interior faces)
    Entries outside the interior are written as 0 (SIMPLE step 3 done before step 1). */
-void or_jx_raw(const or_ctx* c, const double* base, const double* xp, double* ystar) {
+static double jx_point(const or_ctx* c, const double* base, const double* xp, int F, int i, int j, int k) {
   size_t P = plen(c);
   double nu = 1.0 / sqrt(c->g.gr), kappa = 1.0 / (c->g.pr * sqrt(c->g.gr));
   const double* Ub[3] = {base, base + P, base + 2 * P};
   const double* Th = base + 3 * P;
   const double* xv[3] = {xp, xp + P, xp + 2 * P};
   const double* xT = xp + 3 * P;
+  double r;
+  if (F == FT) {
+    r = kappa * laplace(c, xT, FT, i, j, k) - advect(c, Ub, xT, FT, i, j, k) - advect(c, xv, Th, FT, i, j, k);
+  } else {
+    r = nu * laplace(c, xv[F], F, i, j, k) - advect(c, Ub, xv[F], F, i, j, k) - advect(c, xv, Ub[F], F, i, j, k);
+    if (F == FW) r += 0.5 * (at(c, xT, i, j, k) + at(c, xT, i, j, k + 1));
+  }
+  return r;
+}
+
+void or_jx_raw(const or_ctx* c, const double* base, const double* xp, double* ystar) {
+  size_t P = plen(c);
   memset(ystar, 0, sizeof(double) * 4 * P);
   for (int F = 0; F < 4; ++F) {
 #pragma omp parallel for
@@ -461,16 +473,7 @@ void or_jx_raw(const or_ctx* c, const double* base, const double* xp, double* ys
       for (int j = 1; j <= c->n[1]; ++j)
         for (int i = 1; i <= c->n[0]; ++i) {
           if (!is_dof(c, F, i, j, k)) continue;
-          double r;
-          if (F == FT) {
-            r = kappa * laplace(c, xT, FT, i, j, k) - advect(c, Ub, xT, FT, i, j, k) -
-                advect(c, xv, Th, FT, i, j, k);
-          } else {
-            r = nu * laplace(c, xv[F], F, i, j, k) - advect(c, Ub, xv[F], F, i, j, k) -
-                advect(c, xv, Ub[F], F, i, j, k);
-            if (F == FW) r += 0.5 * (at(c, xT, i, j, k) + at(c, xT, i, j, k + 1));
-          }
-          ystar[F * P + pidx(c, i, j, k)] = r;
+          ystar[F * P + pidx(c, i, j, k)] = jx_point(c, base, xp, F, i, j, k);
         }
   }
 }
@@ -691,4 +694,114 @@ void or_arnoldi_step(const or_ctx* c, const double* base, double* V, int j, doub
   if (beta > 0)
     for (size_t e = 0; e < L; ++e) w[e] /= beta;
   free(hh);
+}
+
+/* ---------------------------------------------------------------------------------------- */
+/* adjoint (transpose) of the Krylov map and the gradient of <y, A x> with respect to the   */
+/* base state; entries are formed one by one from the definition of J (no transposed        */
+/* stencil is written by hand)                                                               */
+
+/* z = J_raw^T ys, where J_raw is the map xp -> or_jx_raw(base, xp) on all 4 padded fields:
+   z[F', p] = sum over interior outputs (F, o) within one cell of p of ys[F, o] J[(F,o),(F',p)],
+   each entry J[(F,o),(F',p)] = (J e_{F',p})[F, o] evaluated pointwise. */
+void or_jt_raw(const or_ctx* c, const double* base, const double* ys, double* z) {
+  size_t P = plen(c);
+  int X = c->n[0] + 2, Y = c->n[1] + 2, Z = c->n[2] + 2;
+  memset(z, 0, sizeof(double) * 4 * P);
+#pragma omp parallel
+  {
+    double* unit = (double*)calloc(4 * P, sizeof(double));
+#pragma omp for
+    for (int k = 0; k < Z; ++k)
+      for (int j = 0; j < Y; ++j)
+        for (int i = 0; i < X; ++i)
+          for (int Fp = 0; Fp < 4; ++Fp) {
+            size_t q = Fp * P + pidx(c, i, j, k);
+            unit[q] = 1.0;
+            double acc = 0.0;
+            for (int F = 0; F < 4; ++F)
+              for (int dk = -1; dk <= 1; ++dk)
+                for (int dj = -1; dj <= 1; ++dj)
+                  for (int di = -1; di <= 1; ++di) {
+                    int oi = i + di, oj = j + dj, ok = k + dk;
+                    if (!is_dof(c, F, oi, oj, ok)) continue;
+                    double yo = ys[F * P + pidx(c, oi, oj, ok)];
+                    if (yo == 0.0) continue;
+                    acc += yo * jx_point(c, base, unit, F, oi, oj, ok);
+                  }
+            unit[q] = 0.0;
+            z[q] = acc;
+          }
+    free(unit);
+  }
+}
+
+/* Transpose of the Krylov map (orthogonal reading of the temperature projection, in which
+   P_BC, Pi_v and P_T are all symmetric): z = P_BC J_raw^T (Pi_v (+) P_T) y. */
+void or_krylov_adjoint(const or_ctx* c, const double* base, const double* y, double* z, double tol, int max_passes) {
+  size_t P = plen(c);
+  double* yh = (double*)malloc(sizeof(double) * 4 * P);
+  double* g = (double*)malloc(sizeof(double) * 4 * P);
+  memcpy(yh, y, sizeof(double) * 3 * P);
+  simple_loop(c, yh, NULL, tol, max_passes, NULL); /* masks (step 3) and projects */
+  tproj(c, y + 3 * P, yh + 3 * P);
+  or_jt_raw(c, base, yh, g);
+  or_project_input(c, g, z);
+  free(yh);
+  free(g);
+}
+
+/* gb[q] = d <ys, J(base) xp> / d base[q] for every entry q of the packed base state. J is
+   affine in the base state, so the derivative is the exact difference J(e_q) - J(0) applied
+   to xp, evaluated at the interior outputs within one cell of q. */
+void or_grad_base(const or_ctx* c, const double* xp, const double* ys, double* gb) {
+  size_t P = plen(c);
+  int X = c->n[0] + 2, Y = c->n[1] + 2, Z = c->n[2] + 2;
+  memset(gb, 0, sizeof(double) * 4 * P);
+#pragma omp parallel
+  {
+    double* unit = (double*)calloc(4 * P, sizeof(double));
+    double* zero = (double*)calloc(4 * P, sizeof(double));
+#pragma omp for
+    for (int k = 0; k < Z; ++k)
+      for (int j = 0; j < Y; ++j)
+        for (int i = 0; i < X; ++i)
+          for (int Fb = 0; Fb < 4; ++Fb) {
+            size_t q = Fb * P + pidx(c, i, j, k);
+            unit[q] = 1.0;
+            double acc = 0.0;
+            for (int F = 0; F < 4; ++F)
+              for (int dk = -1; dk <= 1; ++dk)
+                for (int dj = -1; dj <= 1; ++dj)
+                  for (int di = -1; di <= 1; ++di) {
+                    int oi = i + di, oj = j + dj, ok = k + dk;
+                    if (!is_dof(c, F, oi, oj, ok)) continue;
+                    double yo = ys[F * P + pidx(c, oi, oj, ok)];
+                    if (yo == 0.0) continue;
+                    acc += yo * (jx_point(c, unit, xp, F, oi, oj, ok) - jx_point(c, zero, xp, F, oi, oj, ok));
+                  }
+            unit[q] = 0.0;
+            gb[q] = acc;
+          }
+    free(unit);
+    free(zero);
+  }
+}
+
+/* d <ys, J xp> / d Gr: J depends on Gr through nu = Gr^-1/2 and kappa = (Pr Gr^1/2)^-1. */
+double or_grad_gr(const or_ctx* c, const double* xp, const double* ys) {
+  size_t P = plen(c);
+  double sv = 0.0, st = 0.0;
+  const double* xv[3] = {xp, xp + P, xp + 2 * P};
+  for (int F = 0; F < 4; ++F)
+    for (int k = 1; k <= c->n[2]; ++k)
+      for (int j = 1; j <= c->n[1]; ++j)
+        for (int i = 1; i <= c->n[0]; ++i) {
+          if (!is_dof(c, F, i, j, k)) continue;
+          double yo = ys[F * P + pidx(c, i, j, k)];
+          if (F == FT) st += yo * laplace(c, xp + 3 * P, FT, i, j, k);
+          else sv += yo * laplace(c, xv[F], F, i, j, k);
+        }
+  double d = -0.5 * pow(c->g.gr, -1.5);
+  return d * sv + d / c->g.pr * st;
 }

@@ -61,6 +61,11 @@ def _load():
         lib.or_newton_residual.restype = ctypes.c_double
         lib.or_newton_residual.argtypes = [P, D, D, ctypes.c_double, ctypes.c_int]
         lib.or_arnoldi_step.argtypes = [P, D, D, ctypes.c_int, D, ctypes.c_double, ctypes.c_int]
+        lib.or_jt_raw.argtypes = [P, D, D, D]
+        lib.or_krylov_adjoint.argtypes = [P, D, D, D, ctypes.c_double, ctypes.c_int]
+        lib.or_grad_base.argtypes = [P, D, D, D]
+        lib.or_grad_gr.restype = ctypes.c_double
+        lib.or_grad_gr.argtypes = [P, D, D]
         _lib = lib
     return _lib
 
@@ -191,3 +196,29 @@ class Oracle:
         self.lib.or_arnoldi_step(self._c, _ptr(base), _ptr(V), j, _ptr(h), self.tol,
                                  self.max_passes)
         return h
+
+    # adjoint ------------------------------------------------------------------------
+    def jt_raw(self, base, ys):
+        base, ys = self._c64(base), self._c64(ys)
+        z = self._new(4)
+        self.lib.or_jt_raw(self._c, _ptr(base), _ptr(ys), _ptr(z))
+        return z
+
+    def krylov_adjoint(self, base, y):
+        """z = A^T y (orthogonal reading of the temperature projection)."""
+        assert self.tproj == 0, "the transpose is defined for the orthogonal reading"
+        base, y = self._c64(base), self._c64(y)
+        z = self._new(4)
+        self.lib.or_krylov_adjoint(self._c, _ptr(base), _ptr(y), _ptr(z), self.tol, self.max_passes)
+        return z
+
+    def grad_base(self, xp, ys):
+        """d <ys, J(base) xp> / d base, a packed (U, V, W, Theta) array."""
+        xp, ys = self._c64(xp), self._c64(ys)
+        g = self._new(4)
+        self.lib.or_grad_base(self._c, _ptr(xp), _ptr(ys), _ptr(g))
+        return g
+
+    def grad_gr(self, xp, ys):
+        xp, ys = self._c64(xp), self._c64(ys)
+        return self.lib.or_grad_gr(self._c, _ptr(xp), _ptr(ys))

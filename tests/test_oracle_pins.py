@@ -12,6 +12,7 @@ import scipy.linalg as sla
 from oracle import Oracle
 from paper_1905_11601_gb300 import synth
 from tests.mac_assembly import MacOps
+from tests.oracle_helpers import project_output_side
 
 GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
 
@@ -368,3 +369,81 @@ def test_arnoldi_relation_and_orthonormality():
     assert np.abs(Vm @ Vm.T - np.eye(k + 1)).max() < 1e-13
     AV = np.stack([o.krylov_vector(base, V[j]) for j in range(k)]).reshape(k, -1)
     assert np.linalg.norm(AV.T - Vm.T @ H) < 1e-12 * np.linalg.norm(AV)
+
+
+# --- the transpose of the Krylov map and the base-flow gradient (adjoint eigenmodes, sensitivity) --
+@pytest.mark.parametrize("n,bc", [((6, 5, 7), synth.CC), ((5, 6, 4), synth.AA)])
+def test_adjoint_dot_product(n, bc):
+    """<y, J x> = <J^T y, x> and <y, A x> = <A^T y, x> (the definition of the transpose)."""
+    o = Oracle(*n, bc=bc, gr=2e6)
+    base = packed_base(*n, bc, 71)
+    x = synth.krylov_input(*n, 72, 2)
+    xp = o.project_input(x[0])
+    lhs, rhs = np.vdot(x[1], o.jx_raw(base, xp)), np.vdot(o.jt_raw(base, x[1]), xp)
+    assert abs(lhs - rhs) < 1e-13 * np.linalg.norm(x[1]) * np.linalg.norm(o.jx_raw(base, xp))
+    A = o.krylov_vector(base, x[0])
+    lhs, rhs = np.vdot(x[1], A), np.vdot(o.krylov_adjoint(base, x[1]), x[0])
+    assert abs(lhs - rhs) < 1e-13 * np.linalg.norm(x[1]) * np.linalg.norm(A)
+
+
+def test_jt_matches_transpose_of_kronecker_assembly():
+    n = (5, 4, 6)
+    o = Oracle(*n, gr=2e6)
+    base = packed_base(*n, synth.CC, 73)
+    ys = rand_vec(*n, 74)
+    J = MacOps(*n).jacobian(base, 2e6, 0.71)
+    z_asm = (J.T @ ys.ravel()).reshape(ys.shape)
+    z = o.jt_raw(base, ys)
+    assert np.allclose(z, z_asm, rtol=0, atol=1e-12 * np.abs(z_asm).max())
+
+
+@pytest.mark.parametrize("bc", [synth.CC, synth.AA])
+def test_base_gradient_matches_central_differences(bc):
+    """<y, J(b) x> is affine in the base state b, so a central difference is exact up to rounding."""
+    n = (6, 5, 4)
+    o = Oracle(*n, bc=bc, gr=2e6)
+    base = packed_base(*n, bc, 75)
+    x = synth.krylov_input(*n, 76, 2)
+    xp, ys = o.project_input(x[0]), x[1]
+    g = o.grad_base(xp, ys)
+    rng = np.random.default_rng(77)
+    for _ in range(3):
+        d = rng.standard_normal(base.shape)
+        h = 1e-3
+        fp = np.vdot(ys, o.jx_raw(base + h * d, xp))
+        fm = np.vdot(ys, o.jx_raw(base - h * d, xp))
+        assert abs((fp - fm) / (2 * h) - np.vdot(g, d)) < 1e-10 * abs(np.vdot(g, d)) + 1e-12
+    # entries no stencil reads (edges and corners of the padded box) have zero gradient
+    assert np.all(g[:, 0, 0, :] == 0) and np.all(g[:, -1, :, 0] == 0)
+
+
+def test_grashof_derivative_matches_central_differences():
+    n = (5, 5, 6)
+    base = packed_base(*n, synth.CC, 78)
+    x = synth.krylov_input(*n, 79, 2)
+    gr, h = 2e6, 1e2
+    o = Oracle(*n, gr=gr)
+    xp, ys = o.project_input(x[0]), x[1]
+    d = o.grad_gr(xp, ys)
+    fp = np.vdot(ys, Oracle(*n, gr=gr + h).jx_raw(base, xp))
+    fm = np.vdot(ys, Oracle(*n, gr=gr - h).jx_raw(base, xp))
+    assert abs((fp - fm) / (2 * h) - d) < 1e-6 * abs(d)
+
+
+def test_rayleigh_quotient_gradient_in_theta():
+    """R = <y, A x> / <y, x>: its gradient in Theta is grad_base(P_BC x, (Pi (+) P_T) y) / <y, x>,
+    checked against central differences with h = 1e-6."""
+    n = (6, 6, 5)
+    o = Oracle(*n, gr=2e6)
+    base = packed_base(*n, synth.CC, 80)
+    x = synth.krylov_input(*n, 81, 2)
+    yx = np.vdot(x[1], x[0])
+    R = lambda b: np.vdot(x[1], o.krylov_vector(b, x[0])) / yx  # noqa: E731
+    xp = o.project_input(x[0])
+    yhat = project_output_side(o, x[1])  # the (symmetric) output projections of A applied to y
+    gb = o.grad_base(xp, yhat) / yx
+    d = np.zeros_like(base)
+    d[3] = np.random.default_rng(82).standard_normal(base.shape[1:])
+    h = 1e-6
+    fd = (R(base + h * d) - R(base - h * d)) / (2 * h)
+    assert abs(fd - np.vdot(gb, d)) < 1e-7 * abs(np.vdot(gb, d))
