@@ -51,6 +51,8 @@ def parse_args():
     ap.add_argument("--restart", type=int, default=20)
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the 16-vector block and the 12-grid plan measurements")
     ap.add_argument("--single", choices=["fp64", "mixed"], default=None,
                     help="profiling case: two untimed Krylov-vector evaluations, no JSON line")
     return ap.parse_args()
@@ -195,11 +197,26 @@ def run_reference(args):
     print(json.dumps(out), flush=True)
 
 
+def max_over_ranks(x, dist, device="cuda"):
+    """Maximum of a per-rank scalar over all ranks (the job's time is the slowest replica's)."""
+    if not dist:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(units_per_rank, world, seconds_max):
+    """Units processed by all replicas divided by the slowest replica's time (weak scaling)."""
+    return world * units_per_rank / seconds_max
+
+
 def arnoldi_run(g, V, m, steps, warmup, dist, clocks_index=None):
     """Times `steps` Arnoldi steps (after `warmup`) on the current stream; restart every m."""
     import torch
 
-    state = {"j": 0}
+    state = {"j": 0, "nq": []}
 
     def step():
         j = state["j"]
@@ -207,10 +224,12 @@ def arnoldi_run(g, V, m, steps, warmup, dist, clocks_index=None):
             V[0].copy_(V[m])
             j = 0
         g.arnoldi_step(V, j)
+        state["nq"].append(j + 1)
         state["j"] = j + 1
 
     for _ in range(warmup):
         step()
+    state["nq"].clear()
     stream = torch.cuda.current_stream()
     torch.cuda.synchronize()
     if dist:
@@ -228,23 +247,20 @@ def arnoldi_run(g, V, m, steps, warmup, dist, clocks_index=None):
         dist.barrier()
     torch.cuda.synchronize()
     clk = clocks.stop() if clocks else None
-    ms = e0.elapsed_time(e1)
+    ms = max_over_ranks(e0.elapsed_time(e1), dist)
     prof = g.profile()
     g.profile_enable(False)
-    if dist:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
     phases = {k: {"ms": v[0], "timed": v[1], "launches": v[2]} for k, v in prof.items()}
     total = sum(p["ms"] for p in phases.values())
     for p in phases.values():
         p["share"] = p["ms"] / total if total else None
-    return ms, phases, clk
+    return ms, phases, clk, list(state["nq"])
 
 
-def roofline(phases, w, precision, steps):
+def roofline(phases, w, precision, steps, nqs=()):
     """Roofline of the dominant kernel (largest share of the timed region)."""
     n3 = w.nx * w.ny * w.nz
+    L = 4 * (w.nx + 2) * (w.ny + 2) * (w.nz + 2)
     dom = max(phases, key=lambda k: phases[k]["ms"])
     hbm_peak, hbm_src = measured_peaks()
     avg_ms = phases[dom]["ms"] / max(phases[dom]["timed"], 1)
@@ -269,10 +285,76 @@ def roofline(phases, w, precision, steps):
                 "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": ach / FP64_PEAK_TFLOPS,
                 "traffic": traffic_for("k_stencil"), "peak_source": FP64_PEAK_SRC,
                 "algorithmic": f"{STENCIL_FLOPS_PER_CELL} flop per cell (2 per Jacobian nonzero) = {flops:.4g} per launch"}
+    if dom in ("gs_update", "gs_dots") and nqs:
+        # per element: first sweep nq + 1 multiply-adds (inner products and ||w||^2); fused sweep
+        # 2 nq + 1 (update, second-pass inner products, ||w||^2); FP64
+        per = [(nq + 1) if dom == "gs_dots" else (2 * nq + 1) for nq in nqs]
+        flops = 2.0 * L * sum(per)
+        ach = flops / (phases[dom]["ms"] / 1e3) / 1e12
+        name = "k_dots (Gram-Schmidt inner products)" if dom == "gs_dots" else \
+            "k_update_dot (Gram-Schmidt update fused with second-pass inner products)"
+        return {"kernel": name, "bound": "alu", "achieved": ach, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "frac": ach / FP64_PEAK_TFLOPS, "traffic": None, "peak_source": FP64_PEAK_SRC,
+                "algorithmic": f"2 x (2 nq + 1) flop per vector entry per launch, nq = basis size, "
+                               f"mean nq {sum(nqs) / len(nqs):.1f}"}
     byts = {"arnoldi": None, "divergence": 4 * 8.0 * n3, "correct": 11 * 8.0 * n3, "refine": 5 * 8.0 * n3}.get(dom)
     ach = byts / (avg_ms / 1e3) / 1e9 if byts else None
     return {"kernel": dom, "bound": "hbm", "achieved": ach, "peak": hbm_peak, "unit": "GB/s",
             "frac": ach / hbm_peak if ach else None, "traffic": None, "peak_source": hbm_src}
+
+
+def timed(fn, reps, warm=1):
+    """Seconds per call of fn on the current stream (CUDA events)."""
+    import torch
+    for _ in range(warm):
+        fn()
+    s = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(s)
+    for _ in range(reps):
+        fn()
+    e1.record(s)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / 1e3 / reps
+
+
+def extras(base_np, x_np, w, kv, synth):
+    """The batched forms: a block of 16 right-hand sides at 256^3 replayed from one CUDA graph,
+    and a plan of 12 grids {100^3 x4, 128^3 x4, 200^3 x2, 256^3 x2} (Gr in [1e6, 4e6], both
+    spanwise boundary types) evaluated by one graph launch. Mixed precision."""
+    import numpy as np
+    import torch
+
+    out = {}
+    g = kv.Grid(w.nx, w.ny, w.nz, bc=w.bc, gr=w.gr, pr=w.pr, precision=kv.KV_PREC_MIXED)
+    g.set_base_flow(torch.from_numpy(np.stack(base_np)).cuda())
+    X = torch.from_numpy(synth.krylov_input(w.nx, w.ny, w.nz, w.seed + 100, count=16)).cuda()
+    Y = torch.empty_like(X)
+    t = timed(lambda: g.krylov_vector_batch(X, Y), reps=3)
+    out["block16"] = {"workload": f"{w.name}, 16 seeded N(0,1) right-hand sides, one CUDA graph",
+                      "value": 16 / t, "unit": UNIT, "ms_per_block": t * 1e3}
+    del X, Y, g
+    torch.cuda.empty_cache()
+    specs = [(100, 0, 1.0e6), (100, 1, 1.6e6), (100, 0, 2.2e6), (100, 1, 2.8e6), (128, 0, 1.4e6), (128, 1, 2.0e6),
+             (128, 0, 2.6e6), (128, 1, 3.2e6), (200, 0, 3.4e6), (200, 1, 3.6e6), (256, 0, 3.8e6), (256, 1, 4.0e6)]
+    plan = kv.Plan()
+    keep = []
+    for q, (n, bc, gr) in enumerate(specs):
+        gq = kv.Grid(n, n, n, bc=bc, gr=gr, pr=0.71, precision=kv.KV_PREC_MIXED)
+        gq.set_base_flow(torch.from_numpy(np.stack(synth.base_flow(n, n, n, bc, 11700 + q))).cuda())
+        xq = torch.from_numpy(synth.krylov_input(n, n, n, 11800 + q)[0]).cuda()
+        yq = gq.empty(4)
+        plan.add(gq, xq, yq)
+        keep.append((gq, xq, yq))
+    t = timed(plan.launch, reps=3)
+    out["plan12"] = {"workload": "12 grids {100^3 x4, 128^3 x4, 200^3 x2, 256^3 x2}, Gr 1e6..4e6, CC and AA, "
+                                 "one CUDA graph with a branch per grid",
+                     "value": len(specs) / t, "unit": UNIT, "ms_per_launch": t * 1e3}
+    plan.close()
+    del keep
+    torch.cuda.empty_cache()
+    return out
 
 
 def run_ours(args):
@@ -313,10 +395,10 @@ def run_ours(args):
         V = torch.zeros((m + 1, 4) + g.shape, dtype=torch.float64, device="cuda")
         V[0] = y0 / torch.linalg.vector_norm(y0)
         del y0
-        ms, phases, clk = arnoldi_run(g, V, m, args.steps, args.warmup, dist,
-                                      clocks_index=local if (rank == 0 and prec == "mixed") else None)
-        results[prec] = {"g": g, "ms": ms, "phases": phases, "clocks": clk, "err": err,
-                         "rel_div": st.rel_div, "value": world * args.steps / (ms / 1000.0)}
+        ms, phases, clk, nqs = arnoldi_run(g, V, m, args.steps, args.warmup, dist,
+                                           clocks_index=local if (rank == 0 and prec == "mixed") else None)
+        results[prec] = {"g": g, "ms": ms, "phases": phases, "clocks": clk, "err": err, "nq": nqs,
+                         "rel_div": st.rel_div, "value": whole_job_rate(args.steps, world, ms / 1000.0)}
         del V
         if prec == "fp64":
             del g
@@ -334,17 +416,13 @@ def run_ours(args):
     t0 = time.perf_counter()
     for _ in range(args.e2e_steps):
         g.krylov_vector_host(xh, yh)
-    e2e_s = time.perf_counter() - t0
-    if dist:
-        t = torch.tensor([e2e_s], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
-    e2e_value = world * args.e2e_steps / e2e_s
+    e2e_s = max_over_ranks(time.perf_counter() - t0, dist)
+    e2e_value = whole_job_rate(args.e2e_steps, world, e2e_s)
     vec_bytes = xh.numel() * 8
 
     mx = results["mixed"]
     fp = results["fp64"]
-    roof = roofline(mx["phases"], w, "mixed", args.steps)
+    roof = roofline(mx["phases"], w, "mixed", args.steps, mx["nq"])
     launches = int(sum(p["launches"] for p in mx["phases"].values()))
     if rank != 0:
         if dist:
@@ -364,9 +442,11 @@ def run_ours(args):
                           "launches_per_step": v["launches"] / args.steps} for k, v in mx["phases"].items()},
            "fp64_plain": {"value": fp["value"], "ms_per_step": fp["ms"] / args.steps,
                           "speedup_of_mixed": mx["value"] / fp["value"],
-                          "roofline": roofline(fp["phases"], w, "fp64", args.steps),
+                          "roofline": roofline(fp["phases"], w, "fp64", args.steps, fp["nq"]),
                           "phases": {k: {"ms_per_step": v["ms"] / args.steps, "share": v["share"]}
                                      for k, v in fp["phases"].items()}}}
+    if not args.no_extras:
+        out.update(extras(base_np, x_np, w, kv, synth))
     if world == 1 and not args.no_cpu_baseline:
         try:
             r = cpu_baseline(args.workload, 1, 0)

@@ -79,6 +79,9 @@ typedef struct {
   int max_passes;    /* SIMPLE passes at most (0 -> 1: one exact pass, residual reported) */
   int refine_sweeps; /* KV_PREC_MIXED: tensor-core solves per Poisson solve, each followed by an
                         FP64 residual (0 -> 2) */
+  int cgs_passes;    /* kv_arnoldi_step: 0 = classical Gram-Schmidt with the DGKS test (a second
+                        pass only when the first removes more than half of ||w||^2, as ARPACK's
+                        Arnoldi does); 2 = always two passes */
 } kv_grid_desc;
 
 typedef struct {
@@ -104,7 +107,11 @@ kv_status kv_set_stream(kv_handle h, void* stream);
 kv_status kv_field_len(kv_handle h, size_t* field_len);
 
 /* Copies a packed state U | V | W | Theta (device pointer) into library storage: the steady
-   flow (U, P, Theta) that Eqs (8)-(9) are linearised about. Theta carries its wall values. */
+   flow (U, P, Theta) that Eqs (8)-(9) are linearised about. Theta carries its wall values.
+   Also forms the coefficients of the linearised operator for this state (37 padded fields:
+   15 per velocity face, 13 per cell plus the fixed buoyancy weights), so that each Krylov
+   vector is a fixed-coefficient 15/13-point product; a grid therefore holds about
+   (4 + 37 + 3) padded fields plus two n^3 buffers of device memory. */
 kv_status kv_set_base_flow(kv_handle h, const double* base);
 
 /* One Krylov vector (Eqs (11)-(13), Section 3.1): y = (Pi_v (+) P_T) J P_BC x.
@@ -118,13 +125,50 @@ kv_status kv_krylov_vector(kv_handle h, const double* x, double* y, double* p, k
    copies are queued on the handle's stream and the call returns once y is in host memory. */
 kv_status kv_krylov_vector_host(kv_handle h, const double* x_host, double* y_host, kv_stats* st);
 
+/* A block of Krylov vectors: Y_b = A X_b for b = 0..nb-1 (X, Y: nb consecutive packed vectors,
+   device, not overlapping). The evaluation sequence is captured once into a CUDA graph, cached
+   per (X, Y, nb) on the handle (up to 8 entries), and replayed with one graph launch on the
+   handle's stream; results equal nb calls of kv_krylov_vector. Requires desc.max_passes <= 1
+   (the graph contains no host-side SIMPLE test). The first call for a (X, Y, nb) captures, so
+   make it outside any capture of your own. */
+kv_status kv_krylov_vector_batch(kv_handle h, const double* X, double* Y, int nb);
+
+/* Multi-grid plans: several grids (sizes, Grashof numbers, boundary types) evaluated by one
+   graph launch. kv_plan_add queues y = A_h x for the grid h (its base flow must be set); the
+   first kv_plan_launch captures every queued evaluation into one CUDA graph with one parallel
+   branch per grid (evaluations of the same grid stay in order, since they share its scratch),
+   later launches replay it on `stream` (cudaStream_t). Plans are immutable after the first
+   launch. A plan does not own the grids; destroy the plan before its grids. */
+typedef struct kv_plan* kv_plan_handle;
+kv_status kv_plan_create(kv_plan_handle* out);
+kv_status kv_plan_add(kv_plan_handle p, kv_handle h, const double* x, double* y);
+kv_status kv_plan_launch(kv_plan_handle p, void* stream);
+kv_status kv_plan_destroy(kv_plan_handle p);
+const char* kv_plan_last_error(kv_plan_handle p);
+
 /* One Arnoldi step (Section 3.1, the Krylov basis for the eigenvalue problem Eq (10)):
    V holds at least j+2 packed vectors (device), V_0..V_j orthonormal; computes
-   w = A V_j, orthogonalises it against V_0..V_j by classical Gram-Schmidt applied twice,
+   w = A V_j, orthogonalises it against V_0..V_j by classical Gram-Schmidt (a second pass by
+   the DGKS test or always, desc.cgs_passes; always two passes beyond 24 basis vectors),
    stores w / ||w|| in V_{j+1} and writes the Hessenberg column H[0..j+1, j] to the HOST
    array h_col (j+2 doubles). Synchronises the stream. Inner products run over all stored
    entries of the four fields. */
 kv_status kv_arnoldi_step(kv_handle h, double* V, int j, double* h_col);
+
+/* Transpose of the Krylov map: z = A^T y with A = (Pi_v (+) P_T) J P_BC (the adjoint eigenvalue
+   problem of Eq (10) uses it). With the orthogonal reading of Eq (21) the three projections are
+   symmetric, so A^T = P_BC J^T (Pi_v (+) P_T); J^T is applied from the same assembled
+   coefficients as J. y, z: packed vectors (device, must not overlap). Requires
+   KV_TPROJ_ORTHOGONAL (else KV_ERR_ARG) and a base flow (else KV_ERR_STATE). */
+kv_status kv_krylov_vector_adjoint(kv_handle h, const double* y, double* z);
+
+/* Sensitivity of <y, A x> to the base state and the Grashof number (with y the adjoint and x
+   the direct eigenvector this gives the sensitivity of an eigenvalue of Eq (10)):
+   g_theta (device, one padded field, nullable) = d<y, A x>/d Theta, from the term
+   -(v . grad) Theta of Eq (8); dgr (host, nullable) = d<y, A x>/d Gr, from the scalings
+   Gr^-1/2 and (Pr Gr^1/2)^-1 of Eqs (1)-(2). x, y: packed vectors (device). Synchronises the
+   stream when dgr is given. Same requirements as kv_krylov_vector_adjoint. */
+kv_status kv_base_flow_gradient(kv_handle h, const double* x, const double* y, double* g_theta, double* dgr);
 
 /* Newton step 2 of Section 3.1: the steady residual of Eqs (1)-(2) at the packed state S
    (device; carries its own inhomogeneous wall values, Eqs (4)-(7)), projected like a
@@ -135,8 +179,9 @@ kv_status kv_newton_residual(kv_handle h, const double* S, double* F, double* no
 /* Instrumentation (not part of the method): launch counts per phase, always kept, and, when
    enabled, per-phase CUDA-event timings on the handle's stream. Phases: 0 = linearised
    operator stencil, 1 = divergence, 2 = TPF Poisson contractions (one timing per per-axis
-   contraction launch), 3 = velocity correction, 4 = Arnoldi reductions, 5 = FP64 refinement
-   residuals of the mixed-precision Poisson solve.
+   contraction launch), 3 = velocity correction, 4 = Arnoldi normalisation (and third
+   Gram-Schmidt sweep), 5 = FP64 refinement residuals of the mixed-precision Poisson solve,
+   6 = first Gram-Schmidt sweep (inner products), 7 = fused update + second-pass inner products.
    kv_profile_enable synchronises the stream and clears all counters. */
 kv_status kv_profile_enable(kv_handle h, int on);
 /* Synchronises the stream; total_ms / timed_launches: summed event time and number of timed

@@ -68,7 +68,8 @@ def build(force: bool = False, verbose: bool = False) -> str:
             sys.stderr.write(log)
     objs = [o for o, _ in results]
     tmp = LIB + f".tmp{os.getpid()}"
-    r = subprocess.run([cc] + ARCH + ["-shared", "-o", tmp] + objs + ["-lcuda"], capture_output=True, text=True)
+    r = subprocess.run([cc] + ARCH + ["-shared", "-Xlinker", "--no-undefined", "-o", tmp] + objs,
+                       capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
     os.replace(tmp, LIB)

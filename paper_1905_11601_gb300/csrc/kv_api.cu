@@ -66,6 +66,7 @@ kv_status validate(const kv_grid_desc* d, std::string& msg) {
   if (d->tproj != KV_TPROJ_ORTHOGONAL && d->tproj != KV_TPROJ_OBLIQUE) { msg = "tproj must be KV_TPROJ_ORTHOGONAL or KV_TPROJ_OBLIQUE"; return KV_ERR_ARG; }
   if (d->precision != KV_PREC_FP64 && d->precision != KV_PREC_MIXED) { msg = "precision must be KV_PREC_FP64 or KV_PREC_MIXED"; return KV_ERR_ARG; }
   if (d->refine_sweeps < 0 || d->refine_sweeps > 20) { msg = "refine_sweeps must be in [0, 20]"; return KV_ERR_ARG; }
+  if (d->cgs_passes != 0 && d->cgs_passes != 2) { msg = "cgs_passes must be 0 or 2"; return KV_ERR_ARG; }
   if (!(d->gr > 0) || !(d->pr > 0) || !isfinite(d->gr) || !isfinite(d->pr)) { msg = "gr and pr must be finite and > 0"; return KV_ERR_ARG; }
   if (d->tol < 0 || d->max_passes < 0 || d->max_passes > 100) { msg = "tol must be >= 0 and max_passes in [0, 100]"; return KV_ERR_ARG; }
   return KV_OK;
@@ -73,6 +74,7 @@ kv_status validate(const kv_grid_desc* d, std::string& msg) {
 
 void free_all(kv_grid* h) {
   cudaFree(h->base);
+  cudaFree(h->coef);
   cudaFree(h->vstar);
   cudaFree(h->tpd_a);
   cudaFree(h->tpd_b);
@@ -83,6 +85,11 @@ void free_all(kv_grid* h) {
   cudaFree(h->hdev);
   cudaFree(h->stage);
   cudaFree(h->tmp4);
+  cudaFree(h->adj);
+  cudaFree(h->adjsum);
+  for (auto& ge : h->graphs) cudaGraphExecDestroy(ge.exec);
+  h->graphs.clear();
+  if (h->cap) cudaStreamDestroy(h->cap);
   kv_mixed_free(h);
 }
 
@@ -123,7 +130,7 @@ kv_status simple_project(kv_grid* h, double* yvel, double* p, kv_stats* st) {
       kv_launch_poisson_mixed(h, h->tpd_a, phi, s);
     else
       kv_launch_poisson(h, h->tpd_a, h->tpd_a, s);
-    { KvPhase ph(h, KV_PH_CORRECT, 1); kv_launch_correct(h, src, phi, yvel, p, pass > 1, s); }
+    { KvPhase ph(h, KV_PH_CORRECT, 1); kv_launch_correct(h, src, phi, yvel, p, pass > 1, s, want ? 1 : 0); }
     kv_status ks = check_launch(h, "SIMPLE pass");
     if (ks != KV_OK) return ks;
     if (!want) break;
@@ -159,6 +166,50 @@ kv_status simple_project(kv_grid* h, double* yvel, double* p, kv_stats* st) {
   if (want && max_passes > 1 && !(rel < tol))
     return fail(h, KV_ERR_NOT_CONVERGED, "SIMPLE did not reach the tolerance in max_passes passes");
   return KV_OK;
+}
+
+// Block-shape autotuner for the linearised-operator kernel: times each candidate shape on this
+// grid's coefficients (the base state stands in for x; v* and a scratch vector take the output)
+// and keeps the fastest. Runs once per handle, at the first kv_set_base_flow.
+kv_status autotune_apply(kv_grid* h) {
+  static const int cand[][2] = {{32, 8}, {64, 4}, {128, 2}, {32, 4}, {16, 16}, {256, 1}};  // <= 256 threads
+  if (!h->tmp4) {  // one padded field of scratch for the temperature output
+    kv_status s = dalloc(h, &h->tmp4, 4 * h->P);
+    if (s != KV_OK) return s;
+  }
+  cudaEvent_t e0, e1;
+  KV_CHECK_CUDA(h, cudaEventCreate(&e0));
+  KV_CHECK_CUDA(h, cudaEventCreate(&e1));
+  float best = 1e30f;
+  int bx = 32, by = 8;
+  for (auto& c : cand) {
+    h->apply_bx = c[0];
+    h->apply_by = c[1];
+    kv_launch_apply(h, h->coef, h->base, h->vstar, h->tmp4, h->s);  // warm-up
+    if (cudaGetLastError() != cudaSuccess) continue;                // shape not launchable here
+    cudaEventRecord(e0, h->s);
+    for (int r = 0; r < 3; ++r) kv_launch_apply(h, h->coef, h->base, h->vstar, h->tmp4, h->s);
+    cudaEventRecord(e1, h->s);
+    cudaError_t e = cudaEventSynchronize(e1);
+    float ms = 0;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+    if (e != cudaSuccess) {
+      cudaEventDestroy(e0);
+      cudaEventDestroy(e1);
+      return fail(h, KV_ERR_CUDA, std::string("autotune: ") + cudaGetErrorString(e));
+    }
+    if (ms < best) {
+      best = ms;
+      bx = c[0];
+      by = c[1];
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  h->apply_bx = bx;
+  h->apply_by = by;
+  h->tuned = true;
+  return check_launch(h, "autotune");
 }
 
 }  // namespace
@@ -237,7 +288,8 @@ kv_status kv_create_grid(const kv_grid_desc* desc, void* stream, kv_handle* out)
   h->Nc = (size_t)g.nx * g.ny * g.nz;
 
   const int n[3] = {g.nx, g.ny, g.nz};
-  if ((st = dalloc(h, &h->base, 4 * h->P)) || (st = dalloc(h, &h->vstar, 3 * h->P)) ||
+  if ((st = dalloc(h, &h->base, 4 * h->P)) || (st = dalloc(h, &h->coef, (size_t)KV_NCOEF * h->P)) ||
+      (st = dalloc(h, &h->vstar, 3 * h->P)) ||
       (st = dalloc(h, &h->tpd_a, h->Nc)) || (st = dalloc(h, &h->tpd_b, h->Nc)) || (st = dalloc(h, &h->red, 2))) {
     g_create_error = h->err;
     free_all(h);
@@ -312,7 +364,11 @@ kv_status kv_set_base_flow(kv_handle h, const double* base) {
   if (!h) return KV_ERR_ARG;
   if (!base) return fail(h, KV_ERR_ARG, "kv_set_base_flow: base is NULL");
   KV_CHECK_CUDA(h, cudaMemcpyAsync(h->base, base, 4 * h->P * sizeof(double), cudaMemcpyDeviceToDevice, h->s));
+  kv_launch_assemble(h, h->base, h->coef, h->s);
+  kv_status ks = check_launch(h, "assemble");
+  if (ks != KV_OK) return ks;
   h->has_base = true;
+  if (!h->tuned) return autotune_apply(h);
   return KV_OK;
 }
 
@@ -323,7 +379,7 @@ kv_status kv_krylov_vector(kv_handle h, const double* x, double* y, double* p, k
   const size_t L = 4 * h->P;
   if ((x < y + L && y < x + L)) return fail(h, KV_ERR_ARG, "kv_krylov_vector: x and y overlap");
   // J P_BC x: momentum right-hand side to vstar, projected temperature straight into y
-  { KvPhase ph(h, KV_PH_STENCIL, 1); kv_launch_stencil(h, 0, h->base, x, h->vstar, y + 3 * h->P, h->s); }
+  { KvPhase ph(h, KV_PH_STENCIL, 1); kv_launch_apply(h, h->coef, x, h->vstar, y + 3 * h->P, h->s); }
   kv_status ks = check_launch(h, "stencil");
   if (ks != KV_OK) return ks;
   return simple_project(h, y, p, st);
@@ -359,7 +415,7 @@ kv_status kv_arnoldi_step(kv_handle h, double* V, int j, double* h_col) {
     if (s != KV_OK) return s;
     h->partials_cap = need_p;
   }
-  const size_t need_h = 2 * (size_t)nq + 1;
+  const size_t need_h = 2 * (size_t)nq + 4;
   if (h->hdev_cap < need_h) {
     cudaFree(h->hdev);
     h->hdev = nullptr;
@@ -371,11 +427,41 @@ kv_status kv_arnoldi_step(kv_handle h, double* V, int j, double* h_col) {
   double* w = V + (size_t)(j + 1) * L;
   kv_status s = kv_krylov_vector(h, V + (size_t)j * L, w, nullptr, nullptr);
   if (s != KV_OK) return s;
-  double* h1 = h->hdev;
-  double* h2 = h->hdev + nq;
-  double* nrm = h->hdev + 2 * nq;
-  // classical Gram-Schmidt, twice
-  {
+  double* h1 = h->hdev;               // [0, nq): first pass; [nq]: ||w||^2 before
+  double* h2 = h->hdev + nq + 1;      // [nq+1, 2nq+1): second pass; [2nq+1]: ||w||^2 after pass 1
+  double* nrm = h->hdev + 2 * nq + 2; // ||w||^2 after the second update
+  std::vector<double> hh(2 * (size_t)nq + 3, 0.0);
+  if (nq <= kv_fused_cgs_max()) {
+    // Classical Gram-Schmidt. Sweep 1: h1 = V^T w and ||w||^2. Sweep 2: w -= V h1 fused with the
+    // second pass's h2 = V^T w and ||w||^2. The DGKS test (as in ARPACK's Arnoldi) then decides
+    // whether sweep 3 (w -= V h2) is needed: only when sweep 2 removed more than half of ||w||^2.
+    {
+      KvPhase ph(h, KV_PH_GS_DOTS, 2);
+      kv_launch_dots_norm(V, L, nq, w, L, h->partials, h1, h1 + nq, h->s);
+    }
+    {
+      KvPhase ph(h, KV_PH_GS_UPDATE, 2);
+      kv_launch_update_dot(V, L, nq, h1, w, L, h->partials, h2, h->s);
+    }
+    s = check_launch(h, "arnoldi");
+    if (s != KV_OK) return s;
+    KV_CHECK_CUDA(h, cudaMemcpyAsync(hh.data(), h->hdev, hh.size() * sizeof(double), cudaMemcpyDeviceToHost, h->s));
+    KV_CHECK_CUDA(h, cudaStreamSynchronize(h->s));
+    const double before = hh[nq], after = hh[2 * nq + 1];
+    const bool reorth = h->d.cgs_passes == 2 || !(after > 0.5 * before);
+    {
+      KvPhase ph(h, KV_PH_ARNOLDI, reorth ? 3 : 1);
+      if (reorth) kv_launch_update_small_norm(V, L, nq, h2, w, L, h->partials, nrm, h->s);
+      kv_launch_scale_inv_sqrt(w, L, reorth ? nrm : h2 + nq, h->s);
+    }
+    s = check_launch(h, "arnoldi");
+    if (s != KV_OK) return s;
+    if (!reorth) {
+      for (int q = 0; q < nq; ++q) h_col[q] = hh[q];
+      h_col[nq] = sqrt(after);
+      return KV_OK;
+    }
+  } else {
     const int md = (nq + 7) / 8 + 1;  // multidot sweeps + finalize
     KvPhase ph(h, KV_PH_ARNOLDI, 2 * md + 2 + 2 + 1);
     kv_launch_multidot(V, L, nq, w, L, h->partials, h1, 0, h->s);
@@ -387,11 +473,10 @@ kv_status kv_arnoldi_step(kv_handle h, double* V, int j, double* h_col) {
   }
   s = check_launch(h, "arnoldi");
   if (s != KV_OK) return s;
-  std::vector<double> hh(2 * (size_t)nq + 1);
   KV_CHECK_CUDA(h, cudaMemcpyAsync(hh.data(), h->hdev, hh.size() * sizeof(double), cudaMemcpyDeviceToHost, h->s));
   KV_CHECK_CUDA(h, cudaStreamSynchronize(h->s));
-  for (int q = 0; q < nq; ++q) h_col[q] = hh[q] + hh[nq + q];
-  h_col[nq] = sqrt(hh[2 * nq]);
+  for (int q = 0; q < nq; ++q) h_col[q] = hh[q] + hh[nq + 1 + q];
+  h_col[nq] = sqrt(hh[2 * nq + 2]);
   return KV_OK;
 }
 
@@ -437,6 +522,60 @@ kv_status kv_newton_residual(kv_handle h, const double* S, double* F, double* no
     *norm_out = sqrt(n2);
   }
   return KV_OK;
+}
+
+// (Pi_v (+) P_T) y into h->adj: the output-side projections of the Krylov map, which are
+// symmetric (orthogonal reading), applied to y.
+static kv_status project_output_side(kv_grid* h, const double* y) {
+  if (!h->adj) {
+    kv_status s = dalloc(h, &h->adj, 4 * h->P);
+    if (s != KV_OK) return s;
+  }
+  kv_launch_adj_prep(h, y, h->vstar, h->adj + 3 * h->P, h->s);
+  kv_status s = check_launch(h, "adjoint prep");
+  if (s != KV_OK) return s;
+  return simple_project(h, h->adj, nullptr, nullptr);
+}
+
+kv_status kv_krylov_vector_adjoint(kv_handle h, const double* y, double* z) {
+  if (!h) return KV_ERR_ARG;
+  if (!y || !z) return fail(h, KV_ERR_ARG, "kv_krylov_vector_adjoint: y and z must be non-NULL");
+  if (!h->has_base) return fail(h, KV_ERR_STATE, "kv_krylov_vector_adjoint: no base flow set");
+  if (h->d.tproj != KV_TPROJ_ORTHOGONAL)
+    return fail(h, KV_ERR_ARG, "kv_krylov_vector_adjoint: defined for the orthogonal temperature projection");
+  const size_t L = 4 * h->P;
+  if (y < z + L && z < y + L) return fail(h, KV_ERR_ARG, "kv_krylov_vector_adjoint: y and z overlap");
+  kv_status s = project_output_side(h, y);
+  if (s != KV_OK) return s;
+  { KvPhase ph(h, KV_PH_STENCIL, 1); kv_launch_apply_t(h, h->coef, h->adj, z, h->s); }
+  return check_launch(h, "transpose stencil");
+}
+
+kv_status kv_base_flow_gradient(kv_handle h, const double* x, const double* y, double* g_theta, double* dgr) {
+  if (!h) return KV_ERR_ARG;
+  if (!x || !y) return fail(h, KV_ERR_ARG, "kv_base_flow_gradient: x and y must be non-NULL");
+  if (!h->has_base) return fail(h, KV_ERR_STATE, "kv_base_flow_gradient: no base flow set");
+  if (h->d.tproj != KV_TPROJ_ORTHOGONAL)
+    return fail(h, KV_ERR_ARG, "kv_base_flow_gradient: defined for the orthogonal temperature projection");
+  kv_status s = project_output_side(h, y);
+  if (s != KV_OK) return s;
+  if (g_theta) kv_launch_grad_theta(h, x, h->adj + 3 * h->P, g_theta, h->s);
+  if (dgr) {
+    if (!h->adjsum) {
+      s = dalloc(h, &h->adjsum, 2);
+      if (s != KV_OK) return s;
+    }
+    KV_CHECK_CUDA(h, cudaMemsetAsync(h->adjsum, 0, 2 * sizeof(double), h->s));
+    kv_launch_lap_dot(h, x, h->adj, h->adjsum, h->s);
+    s = check_launch(h, "Grashof derivative");
+    if (s != KV_OK) return s;
+    double sums[2];
+    KV_CHECK_CUDA(h, cudaMemcpyAsync(sums, h->adjsum, sizeof sums, cudaMemcpyDeviceToHost, h->s));
+    KV_CHECK_CUDA(h, cudaStreamSynchronize(h->s));
+    const double d = -0.5 * pow(h->d.gr, -1.5);
+    *dgr = d * sums[0] + d / h->d.pr * sums[1];
+  }
+  return check_launch(h, "base-flow gradient");
 }
 
 kv_status kv_profile_enable(kv_handle h, int on) {

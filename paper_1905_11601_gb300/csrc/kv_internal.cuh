@@ -12,7 +12,11 @@
 #include "kv.h"
 
 // timed phases (kv_profile_get)
-enum { KV_PH_STENCIL = 0, KV_PH_DIV = 1, KV_PH_TPD = 2, KV_PH_CORRECT = 3, KV_PH_ARNOLDI = 4, KV_PH_REFINE = 5, KV_NPHASE = 8 };
+enum { KV_PH_STENCIL = 0, KV_PH_DIV = 1, KV_PH_TPD = 2, KV_PH_CORRECT = 3, KV_PH_ARNOLDI = 4, KV_PH_REFINE = 5,
+       KV_PH_GS_DOTS = 6, KV_PH_GS_UPDATE = 7, KV_NPHASE = 8 };
+
+// Assembled coefficients of the linearised operator per padded entry (kv_stencil.cu).
+constexpr int KV_NCOEF = 37;
 
 // Device-side description of the uniform MAC grid.
 struct KvGeom {
@@ -35,6 +39,7 @@ struct kv_grid {
   bool has_base = false;
 
   double* base = nullptr;   // 4P: U | V | W | Theta
+  double* coef = nullptr;   // KV_NCOEF * P: assembled coefficients of J (per base flow)
   double* vstar = nullptr;  // 3P: momentum right-hand side before the projection
   double* tpd_a = nullptr;  // Nc: divergence / Poisson ping-pong buffers
   double* tpd_b = nullptr;  // Nc
@@ -46,6 +51,8 @@ struct kv_grid {
   double* hdev = nullptr;             // Arnoldi coefficients on the device
   size_t hdev_cap = 0;
   double* stage = nullptr;            // 8P: staging for the host-buffer entry point
+  double* adj = nullptr;              // 4P: projected output-side vector of the transpose
+  double* adjsum = nullptr;           // 2: reductions of the Grashof derivative
   double* tmp4 = nullptr;             // 4P: residual right-hand side scratch
 
   // mixed precision (KV_PREC_MIXED): BF16 slices of the six per-axis matrices, two ping-pong
@@ -67,6 +74,21 @@ struct kv_grid {
   std::vector<Pending> pending;
   double prof_ms[KV_NPHASE] = {};
   long long prof_n[KV_NPHASE] = {};
+
+  // CUDA graphs of kv_krylov_vector_batch, keyed by (X, Y, nb)
+  struct GraphEntry {
+    const double* X;
+    double* Y;
+    int nb;
+    cudaGraphExec_t exec;
+    long long launches[KV_NPHASE];
+  };
+  std::vector<GraphEntry> graphs;
+  cudaStream_t cap = nullptr;  // capture stream (the handle's stream may be the legacy one)
+
+  // block shape of the linearised-operator kernel, chosen by timing (kv_autotune_apply)
+  int apply_bx = 32, apply_by = 8;
+  bool tuned = false;
 
   std::string err;
 };
@@ -94,6 +116,7 @@ struct KvUmmaEpi {
   const float* la;
   const float* lb;
 };
+cudaError_t kv_umma_init();
 bool kv_make_slice_map(CUtensorMap* map, const void* base, int cols, int rows, int pitch, size_t slice_elems,
                        int box_rows);
 int kv_umma_box_rows_a();
@@ -110,6 +133,12 @@ void kv_launch_poisson_mixed(kv_grid* h, const double* b, double* phi, cudaStrea
 // kv_api.cu: sets the thread's message returned by kv_last_error(NULL)
 void kv_set_thread_error(const std::string& msg);
 
+// kv_adjoint.cu
+void kv_launch_adj_prep(const kv_grid* h, const double* y, double* vel, double* tout, cudaStream_t s);
+void kv_launch_apply_t(const kv_grid* h, const double* coef, const double* yh, double* z, cudaStream_t s);
+void kv_launch_grad_theta(const kv_grid* h, const double* x, const double* yT, double* gt, cudaStream_t s);
+void kv_launch_lap_dot(const kv_grid* h, const double* x, const double* yh, double* sums, cudaStream_t s);
+
 // kv_stencil.cu
 // mode 0: y* = J P_BC x (Eqs (11)-(12)); mode 1: y* = F(S) (steady residual, x = base = S).
 // Writes the three momentum fields (interior faces, zero elsewhere) to vstar and the
@@ -117,12 +146,17 @@ void kv_set_thread_error(const std::string& msg);
 void kv_launch_stencil(const kv_grid* h, int mode, const double* base, const double* x, double* vstar,
                        double* tout, cudaStream_t s);
 
+// Forms the assembled coefficients of J from the base state; then y* = J P_BC x from them.
+void kv_launch_assemble(const kv_grid* h, const double* base, double* coef, cudaStream_t s);
+void kv_launch_apply(const kv_grid* h, const double* coef, const double* x, double* vstar, double* tout,
+                     cudaStream_t s);
+
 // kv_project.cu
 void kv_launch_divergence(const kv_grid* h, const double* vel, double* b, cudaStream_t s);
 // out_vel = vstar - G phi on interior faces (0 elsewhere); p (nullable) = phi (+ p if accumulate);
-// reduces max |D out_vel| and max |out_vel| into h->red.
+// with check != 0 also reduces max |D out_vel| and max |out_vel| into h->red (the SIMPLE test).
 void kv_launch_correct(const kv_grid* h, const double* vstar, const double* phi, double* out_vel,
-                       double* p, int accumulate_p, cudaStream_t s);
+                       double* p, int accumulate_p, cudaStream_t s, int check = 1);
 
 // kv_tpd.cu: phi = L^+ b by Eq (18), six per-axis contractions; b and phi compact n^3
 // (x fastest). b is overwritten (used as scratch).
@@ -140,3 +174,14 @@ void kv_launch_update(const double* V, size_t ld, int nq, const double* c, doubl
 // out[0] = ||w||^2 (via partials); then w /= sqrt(out[0]) if scale
 void kv_launch_norm2(const double* w, size_t len, double* partials, double* out, cudaStream_t s);
 void kv_launch_scale_inv_sqrt(double* w, size_t len, const double* nrm2, cudaStream_t s);
+// Gram-Schmidt building blocks for nq <= kv_fused_cgs_max() vectors (one sweep each):
+// h[q] = <V_q, w> (and h[nq] = ||w||^2 when nrm2 != nullptr, copied to nrm2);
+// w -= V c fused with h2[q] = <V_q, w> and h2[nq] = ||w||^2 (FP64);
+// w -= V c for rounding-size c (product in FP32) with ||w||^2.
+int kv_fused_cgs_max();
+void kv_launch_dots_norm(const double* V, size_t ld, int nq, const double* w, size_t len, double* partials,
+                         double* h, double* nrm2, cudaStream_t s);
+void kv_launch_update_dot(const double* V, size_t ld, int nq, const double* c, double* w, size_t len,
+                          double* partials, double* h2, cudaStream_t s);
+void kv_launch_update_small_norm(const double* V, size_t ld, int nq, const double* c, double* w, size_t len,
+                                 double* partials, double* nrm2, cudaStream_t s);

@@ -33,15 +33,14 @@ __global__ void __launch_bounds__(256) k_residual_slices(KvGeom g, const double*
     const size_t e = i + sy * j + sz * k;
     double r = __ldg(b + e);
     if (phi) {
+      // homogeneous Neumann walls: a missing neighbour contributes as the cell itself
       const double c = __ldg(phi + e);
-      double lx = 0.0, ly = 0.0, lz = 0.0;
-      if (i > 0) lx += __ldg(phi + e - sx) - c;
-      if (i < g.nx - 1) lx += __ldg(phi + e + sx) - c;
-      if (j > 0) ly += __ldg(phi + e - sy) - c;
-      if (j < g.ny - 1) ly += __ldg(phi + e + sy) - c;
-      if (k > 0) lz += __ldg(phi + e - sz) - c;
-      if (k < g.nz - 1) lz += __ldg(phi + e + sz) - c;
-      r -= lx * (g.ihx * g.ihx) + ly * (g.ihy * g.ihy) + lz * (g.ihz * g.ihz);
+      const double xm = i > 0 ? __ldg(phi + e - sx) : c, xp = i < g.nx - 1 ? __ldg(phi + e + sx) : c;
+      const double ym = j > 0 ? __ldg(phi + e - sy) : c, yp = j < g.ny - 1 ? __ldg(phi + e + sy) : c;
+      const double zm = k > 0 ? __ldg(phi + e - sz) : c, zp = k < g.nz - 1 ? __ldg(phi + e + sz) : c;
+      r = fma(-g.ihx * g.ihx, fma(-2.0, c, xm + xp), r);
+      r = fma(-g.ihy * g.ihy, fma(-2.0, c, ym + yp), r);
+      r = fma(-g.ihz * g.ihz, fma(-2.0, c, zm + zp), r);
     }
     rv = fabs(r);
     const float rf = (float)r;
@@ -113,6 +112,7 @@ kv_status kv_mixed_setup(kv_grid* h, const double* const fwd[3], const double* c
     if ((e = cudaMalloc(&h->lamf[a], n[a] * sizeof(float))) != cudaSuccess) goto fail;
     if ((e = cudaMemcpy(h->lamf[a], lf.data(), n[a] * sizeof(float), cudaMemcpyHostToDevice)) != cudaSuccess) goto fail;
   }
+  if ((e = kv_umma_init()) != cudaSuccess) goto fail;
   if ((e = cudaMalloc(&h->derr, sizeof(unsigned int))) != cudaSuccess) goto fail;
   if ((e = cudaMemset(h->derr, 0, sizeof(unsigned int))) != cudaSuccess) goto fail;
   if ((e = cudaMalloc(&h->rmax, sizeof(unsigned long long))) != cudaSuccess) goto fail;

@@ -50,7 +50,7 @@ struct Corr {
 __global__ void __launch_bounds__(256) k_correct(KvGeom g, const double* __restrict__ vs,
                                                  const double* __restrict__ phi, size_t P,
                                                  double* __restrict__ out, double* __restrict__ p, int acc_p,
-                                                 unsigned long long* __restrict__ red) {
+                                                 int check, unsigned long long* __restrict__ red) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   const int j = blockIdx.y * blockDim.y + threadIdx.y;
   const int k = blockIdx.z;
@@ -62,9 +62,9 @@ __global__ void __launch_bounds__(256) k_correct(KvGeom g, const double* __restr
     out[e] = ur;
     out[P + e] = vr;
     out[2 * P + e] = wr;
-    vmax = fmax(fabs(ur), fmax(fabs(vr), fabs(wr)));
     const bool cell = i >= 1 && i <= g.nx && j >= 1 && j <= g.ny && k >= 1 && k <= g.nz;
-    if (cell) {
+    if (check) vmax = fmax(fabs(ur), fmax(fabs(vr), fabs(wr)));
+    if (check && cell) {
       const double d = (ur - C.u(i - 1, j, k)) * g.ihx + (vr - C.v(i, j - 1, k)) * g.ihy + (wr - C.w(i, j, k - 1)) * g.ihz;
       dmax = fabs(d);
     }
@@ -75,6 +75,7 @@ __global__ void __launch_bounds__(256) k_correct(KvGeom g, const double* __restr
         p[e] = 0.0;
     }
   }
+  if (!check) return;
   // block reduction of the two maxima, one atomic each per block
   for (int o = 16; o > 0; o >>= 1) {
     dmax = fmax(dmax, __shfl_xor_sync(0xffffffffu, dmax, o));
@@ -107,8 +108,8 @@ void kv_launch_divergence(const kv_grid* h, const double* vel, double* b, cudaSt
 }
 
 void kv_launch_correct(const kv_grid* h, const double* vstar, const double* phi, double* out_vel, double* p,
-                       int accumulate_p, cudaStream_t s) {
+                       int accumulate_p, cudaStream_t s, int check) {
   const KvGeom& g = h->g;
   dim3 block(32, 8, 1), grid((g.X + 31) / 32, (g.Y + 7) / 8, g.Z);
-  k_correct<<<grid, block, 0, s>>>(g, vstar, phi, h->P, out_vel, p, accumulate_p, h->red);
+  k_correct<<<grid, block, 0, s>>>(g, vstar, phi, h->P, out_vel, p, accumulate_p, check, h->red);
 }

@@ -8,6 +8,7 @@ namespace {
 constexpr int RB = 1216;  // reduction blocks: 8 per SM on 152 SMs
 constexpr int RT = 256;   // threads per block
 constexpr int QB = 8;     // inner products accumulated per sweep over the vector
+constexpr int QF = 24;    // inner products of the fused second Gram-Schmidt pass
 
 __device__ __forceinline__ double warp_sum(double v) {
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -79,9 +80,157 @@ __global__ void __launch_bounds__(RT) k_scale_inv_sqrt(double* __restrict__ w, s
   for (size_t e = (size_t)blockIdx.x * RT + threadIdx.x; e < len; e += (size_t)gridDim.x * RT) w[e] *= f;
 }
 
+// FP32 value of a double from its high word (20 mantissa bits, truncated): integer operations
+// only, so it stays off GB300's narrow FP64 pipe. Zero, denormals and tiny values map to 0.
+// Only for quantities whose own rounding is negligible in the result.
+__device__ __forceinline__ float hi_float(double d) {
+  const unsigned int hi = (unsigned int)__double2hiint(d);
+  const int e = (int)((hi >> 20) & 0x7FFu) - 1023 + 127;
+  const unsigned int bits = (hi & 0x80000000u) | ((unsigned int)e << 23) | ((hi & 0xFFFFFu) << 3);
+  return e > 0 ? __uint_as_float(bits) : 0.0f;
+}
+
+// Inner products <V_q, w> for q < nq (FP64), and with nrm also ||w||^2, in one sweep over w:
+// partials[q * RB + block], the norm's share in partials[nq * RB + block].
+template <int Q>
+__global__ void __launch_bounds__(RT) k_dots(const double* __restrict__ V, size_t ld, int nq,
+                                             const double* __restrict__ w, size_t len, int nrm,
+                                             double* __restrict__ partials) {
+  __shared__ double sm[Q + 1][RT / 32];
+  double acc[Q + 1];
+#pragma unroll
+  for (int q = 0; q <= Q; ++q) acc[q] = 0.0;
+  for (size_t e = (size_t)blockIdx.x * RT + threadIdx.x; e < len; e += (size_t)RB * RT) {
+    const double we = __ldg(w + e);
+#pragma unroll
+    for (int q = 0; q < Q; ++q)
+      if (q < nq) acc[q] = fma(__ldg(V + (size_t)q * ld + e), we, acc[q]);
+    acc[Q] = fma(we, we, acc[Q]);
+  }
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+#pragma unroll
+  for (int q = 0; q <= Q; ++q) {
+    const double t = warp_sum(acc[q]);
+    if (lane == 0) sm[q][warp] = t;
+  }
+  __syncthreads();
+  const int t = threadIdx.x;
+  if (t < nq || (nrm && t == Q)) {
+    double s = 0.0;
+    for (int wv = 0; wv < RT / 32; ++wv) s += sm[t][wv];
+    partials[(size_t)(t < nq ? t : nq) * RB + blockIdx.x] = s;
+  }
+}
+
+// First update fused with the second pass: w -= sum_q c[q] V_q (FP64), then the block's share of
+// <V_q, w> (FP64: inner products of nearly orthogonal vectors need full precision) in
+// partials[q * RB + block] and of the new ||w||^2 in partials[nq * RB + block].
+template <int Q>
+__global__ void __launch_bounds__(RT) k_update_dot(const double* __restrict__ V, size_t ld, int nq,
+                                                   const double* __restrict__ c, double* __restrict__ w, size_t len,
+                                                   double* __restrict__ partials) {
+  __shared__ double cs[Q];
+  __shared__ double sm[Q + 1][RT / 32];
+  if (threadIdx.x < Q) cs[threadIdx.x] = (int)threadIdx.x < nq ? c[threadIdx.x] : 0.0;
+  __syncthreads();
+  double acc[Q + 1];
+#pragma unroll
+  for (int q = 0; q <= Q; ++q) acc[q] = 0.0;
+  for (size_t e = (size_t)blockIdx.x * RT + threadIdx.x; e < len; e += (size_t)RB * RT) {
+    double v[Q];
+    double s = 0.0;
+#pragma unroll
+    for (int q = 0; q < Q; ++q) {
+      v[q] = q < nq ? __ldg(V + (size_t)q * ld + e) : 0.0;
+      s = fma(cs[q], v[q], s);
+    }
+    const double w1 = w[e] - s;
+    w[e] = w1;
+#pragma unroll
+    for (int q = 0; q < Q; ++q)
+      if (q < nq) acc[q] = fma(v[q], w1, acc[q]);
+    acc[Q] = fma(w1, w1, acc[Q]);
+  }
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+#pragma unroll
+  for (int q = 0; q <= Q; ++q) {
+    const double t = warp_sum(acc[q]);
+    if (lane == 0) sm[q][warp] = t;
+  }
+  __syncthreads();
+  const int t = threadIdx.x;
+  if (t < nq || t == Q) {
+    double s = 0.0;
+    for (int wv = 0; wv < RT / 32; ++wv) s += sm[t][wv];
+    partials[(size_t)(t < nq ? t : nq) * RB + blockIdx.x] = s;
+  }
+}
+
+// Second pass, second half: w -= sum_q c[q] V_q. The second-pass coefficients are of rounding
+// size relative to w, so their product with V is formed in FP32 from the high words (its error
+// is ~1e-6 of a rounding-size correction); the subtraction and the block's share of ||w||^2
+// (partials[block]) are FP64.
+__global__ void __launch_bounds__(RT) k_update_small_norm(const double* __restrict__ V, size_t ld, int nq,
+                                                          const double* __restrict__ c, double* __restrict__ w,
+                                                          size_t len, double* __restrict__ partials) {
+  __shared__ float cs[QF];
+  __shared__ double sm[RT / 32];
+  if (threadIdx.x < QF) cs[threadIdx.x] = threadIdx.x < nq ? (float)c[threadIdx.x] : 0.0f;
+  __syncthreads();
+  double nrm = 0.0;
+  for (size_t e = (size_t)blockIdx.x * RT + threadIdx.x; e < len; e += (size_t)RB * RT) {
+    float s = 0.0f;
+#pragma unroll
+    for (int q = 0; q < QF; ++q)
+      if (q < nq) s = fmaf(cs[q], hi_float(__ldg(V + (size_t)q * ld + e)), s);
+    const double w2 = w[e] - (double)s;
+    w[e] = w2;
+    nrm = fma(w2, w2, nrm);
+  }
+  nrm = warp_sum(nrm);
+  if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = nrm;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int wv = 0; wv < RT / 32; ++wv) t += sm[wv];
+    partials[blockIdx.x] = t;
+  }
+}
+
 }  // namespace
 
 int kv_reduce_blocks() { return RB; }
+int kv_fused_cgs_max() { return QF; }
+
+void kv_launch_dots_norm(const double* V, size_t ld, int nq, const double* w, size_t len, double* partials,
+                         double* h, double* nrm2, cudaStream_t s) {
+  const int nrm = nrm2 != nullptr;
+  if (nq <= 8)
+    k_dots<8><<<RB, RT, 0, s>>>(V, ld, nq, w, len, nrm, partials);
+  else if (nq <= 16)
+    k_dots<16><<<RB, RT, 0, s>>>(V, ld, nq, w, len, nrm, partials);
+  else
+    k_dots<QF><<<RB, RT, 0, s>>>(V, ld, nq, w, len, nrm, partials);
+  k_finalize<<<nq + (nrm2 ? 1 : 0), RT, 0, s>>>(partials, h, 0);  // h[nq] = ||w||^2 when asked
+  if (nrm2 && nrm2 != h + nq) cudaMemcpyAsync(nrm2, h + nq, sizeof(double), cudaMemcpyDeviceToDevice, s);
+}
+
+void kv_launch_update_dot(const double* V, size_t ld, int nq, const double* c, double* w, size_t len,
+                          double* partials, double* h2, cudaStream_t s) {
+  if (nq <= 8)
+    k_update_dot<8><<<RB, RT, 0, s>>>(V, ld, nq, c, w, len, partials);
+  else if (nq <= 16)
+    k_update_dot<16><<<RB, RT, 0, s>>>(V, ld, nq, c, w, len, partials);
+  else
+    k_update_dot<QF><<<RB, RT, 0, s>>>(V, ld, nq, c, w, len, partials);
+  k_finalize<<<nq + 1, RT, 0, s>>>(partials, h2, 0);  // h2[nq] = ||w||^2 after the update
+}
+
+void kv_launch_update_small_norm(const double* V, size_t ld, int nq, const double* c, double* w, size_t len,
+                                 double* partials, double* nrm2, cudaStream_t s) {
+  k_update_small_norm<<<RB, RT, 0, s>>>(V, ld, nq, c, w, len, partials);
+  k_finalize<<<1, RT, 0, s>>>(partials, nrm2, 0);
+}
 
 void kv_launch_multidot(const double* V, size_t ld, int nq, const double* w, size_t len, double* partials,
                         double* out, int accumulate, cudaStream_t s) {

@@ -237,6 +237,170 @@ __global__ void __launch_bounds__(256) k_stencil(KvGeom g, const double* __restr
   }
 }
 
+// ---- the linearised operator in assembled-coefficient form -----------------------------
+//
+// J is linear in x and its coefficients depend only on the base flow, so they are formed once
+// per base flow (k_assemble) and every Krylov vector is a 15-point (velocity faces) / 13-point
+// (cells) product (k_apply): 60 FP64 multiply-adds per cell instead of recomputing the
+// interpolated velocities, base gradients and wall weights every time. Coefficient array q
+// (KV_NCOEF of them, each a padded field) at entry e:
+//   u-face  q = 0..6   own-field points (c, x-, x+, y-, y+, z-, z+)
+//           q = 7, 8   factors of the 4-point sums of v and w around the face
+//   v-face  q = 9..15, 16 (sum of u), 17 (sum of w)
+//   w-face  q = 18..24, 25 (sum of u), 26 (sum of v); plus 0.5 (T_k + T_k+1) buoyancy
+//   T-cell  q = 27..33, 34, 35, 36 (factors of the 2-point sums of u, v, w)
+__global__ void __launch_bounds__(256) k_assemble(KvGeom g, const double* __restrict__ base, size_t P,
+                                                  double* __restrict__ coef) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = blockIdx.y * blockDim.y + threadIdx.y;
+  const int k = blockIdx.z;
+  if (i >= g.X || j >= g.Y || k >= g.Z) return;
+  Grid G{g};
+  const int e = G.at(i, j, k);
+  Loader<false> B{G, base, base + P, base + 2 * P, base + 3 * P};
+  double c[KV_NCOEF];
+#pragma unroll
+  for (int q = 0; q < KV_NCOEF; ++q) c[q] = 0.0;
+  const double ihx2 = g.ihx * g.ihx, ihy2 = g.ihy * g.ihy, ihz2 = g.ihz * g.ihz;
+  // own-field coefficients of nu Lap f - (a . grad) f - f_self * g_self
+  auto own = [&](double* o, double diff, const W3& x1, const W3& x2, const W3& y1, const W3& y2, const W3& z1,
+                 const W3& z2, double ax, double ay, double az, double gself) {
+    o[1] = diff * x2.m - ax * x1.m;
+    o[2] = diff * x2.p - ax * x1.p;
+    o[3] = diff * y2.m - ay * y1.m;
+    o[4] = diff * y2.p - ay * y1.p;
+    o[5] = diff * z2.m - az * z1.m;
+    o[6] = diff * z2.p - az * z1.p;
+    o[0] = diff * (x2.c + y2.c + z2.c) - (ax * x1.c + ay * y1.c + az * z1.c) - gself;
+  };
+  if (G.dof_u(i, j, k)) {
+    const W3 dx1 = d1_face(g.ihx), dx2 = d2_face(ihx2);
+    const W3 dy1 = d1_cell(j, g.ny, g.ihy), dy2 = d2_cell(j, g.ny, ihy2);
+    const W3 dz1 = d1_cell(k, g.nz, g.ihz), dz2 = d2_cell(k, g.nz, ihz2);
+    const double Ua = B.lu(i, j, k);
+    const double Va = 0.25 * (B.lv(i, j - 1, k) + B.lv(i, j, k) + B.lv(i + 1, j - 1, k) + B.lv(i + 1, j, k));
+    const double Wa = 0.25 * (B.lw(i, j, k - 1) + B.lw(i, j, k) + B.lw(i + 1, j, k - 1) + B.lw(i + 1, j, k));
+    const double gx = ap(dx1, B.lu(i - 1, j, k), Ua, B.lu(i + 1, j, k));
+    const double gy = ap(dy1, B.lu(i, j - 1, k), Ua, B.lu(i, j + 1, k));
+    const double gz = ap(dz1, B.lu(i, j, k - 1), Ua, B.lu(i, j, k + 1));
+    own(c + 0, g.nu, dx1, dx2, dy1, dy2, dz1, dz2, Ua, Va, Wa, gx);
+    c[7] = -0.25 * gy;
+    c[8] = -0.25 * gz;
+  }
+  if (G.dof_v(i, j, k)) {
+    const W3 dx1 = d1_cell(i, g.nx, g.ihx), dx2 = d2_cell(i, g.nx, ihx2);
+    const W3 dy1 = d1_face(g.ihy), dy2 = d2_face(ihy2);
+    const W3 dz1 = d1_cell(k, g.nz, g.ihz), dz2 = d2_cell(k, g.nz, ihz2);
+    const double Ua = 0.25 * (B.lu(i - 1, j, k) + B.lu(i, j, k) + B.lu(i - 1, j + 1, k) + B.lu(i, j + 1, k));
+    const double Va = B.lv(i, j, k);
+    const double Wa = 0.25 * (B.lw(i, j, k - 1) + B.lw(i, j, k) + B.lw(i, j + 1, k - 1) + B.lw(i, j + 1, k));
+    const double gx = ap(dx1, B.lv(i - 1, j, k), Va, B.lv(i + 1, j, k));
+    const double gy = ap(dy1, B.lv(i, j - 1, k), Va, B.lv(i, j + 1, k));
+    const double gz = ap(dz1, B.lv(i, j, k - 1), Va, B.lv(i, j, k + 1));
+    own(c + 9, g.nu, dx1, dx2, dy1, dy2, dz1, dz2, Ua, Va, Wa, gy);
+    c[16] = -0.25 * gx;
+    c[17] = -0.25 * gz;
+  }
+  if (G.dof_w(i, j, k)) {
+    const W3 dx1 = d1_cell(i, g.nx, g.ihx), dx2 = d2_cell(i, g.nx, ihx2);
+    const W3 dy1 = d1_cell(j, g.ny, g.ihy), dy2 = d2_cell(j, g.ny, ihy2);
+    const W3 dz1 = d1_face(g.ihz), dz2 = d2_face(ihz2);
+    const double Ua = 0.25 * (B.lu(i - 1, j, k) + B.lu(i, j, k) + B.lu(i - 1, j, k + 1) + B.lu(i, j, k + 1));
+    const double Va = 0.25 * (B.lv(i, j - 1, k) + B.lv(i, j, k) + B.lv(i, j - 1, k + 1) + B.lv(i, j, k + 1));
+    const double Wa = B.lw(i, j, k);
+    const double gx = ap(dx1, B.lw(i - 1, j, k), Wa, B.lw(i + 1, j, k));
+    const double gy = ap(dy1, B.lw(i, j - 1, k), Wa, B.lw(i, j + 1, k));
+    const double gz = ap(dz1, B.lw(i, j, k - 1), Wa, B.lw(i, j, k + 1));
+    own(c + 18, g.nu, dx1, dx2, dy1, dy2, dz1, dz2, Ua, Va, Wa, gz);
+    c[25] = -0.25 * gx;
+    c[26] = -0.25 * gy;
+  }
+  if (i >= 1 && i <= g.nx && j >= 1 && j <= g.ny && k >= 1 && k <= g.nz) {
+    const W3 dx1 = d1_cell(i, g.nx, g.ihx), dx2 = d2_cell(i, g.nx, ihx2);
+    const W3 dy1 = d1_cell(j, g.ny, g.ihy), dy2 = d2_cell(j, g.ny, ihy2);
+    const W3 dz1 = d1_cell(k, g.nz, g.ihz), dz2 = d2_cell(k, g.nz, ihz2);
+    const double Ua = 0.5 * (B.lu(i - 1, j, k) + B.lu(i, j, k));
+    const double Va = 0.5 * (B.lv(i, j - 1, k) + B.lv(i, j, k));
+    const double Wa = 0.5 * (B.lw(i, j, k - 1) + B.lw(i, j, k));
+    const double th = B.lT(i, j, k);
+    const double gx = ap(dx1, B.lT(i - 1, j, k), th, B.lT(i + 1, j, k));
+    const double gy = ap(dy1, B.lT(i, j - 1, k), th, B.lT(i, j + 1, k));
+    const double gz = ap(dz1, B.lT(i, j, k - 1), th, B.lT(i, j, k + 1));
+    own(c + 27, g.kappa, dx1, dx2, dy1, dy2, dz1, dz2, Ua, Va, Wa, 0.0);
+    c[34] = -0.5 * gx;
+    c[35] = -0.5 * gy;
+    c[36] = -0.5 * gz;
+  }
+#pragma unroll
+  for (int q = 0; q < KV_NCOEF; ++q) coef[(size_t)q * P + e] = c[q];
+}
+
+__device__ __forceinline__ double cf(const double* __restrict__ coef, size_t P, int q, int e) {
+  return __ldg(coef + (size_t)q * P + e);
+}
+
+// y* = J P_BC x with the assembled coefficients; output as k_stencil<0>.
+__global__ void __launch_bounds__(256) k_apply(KvGeom g, const double* __restrict__ coef,
+                                               const double* __restrict__ x, size_t P, double* __restrict__ vstar,
+                                               double* __restrict__ tout) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = blockIdx.y * blockDim.y + threadIdx.y;
+  const int k = blockIdx.z;
+  if (i >= g.X || j >= g.Y || k >= g.Z) return;
+  Grid G{g};
+  const int e = G.at(i, j, k);
+  Loader<true> X{G, x, x + P, x + 2 * P, x + 3 * P};
+  double ru = 0.0, rv = 0.0, rw = 0.0;
+  if (G.dof_u(i, j, k)) {
+    ru = cf(coef, P, 0, e) * X.lu(i, j, k) + cf(coef, P, 1, e) * X.lu(i - 1, j, k) +
+         cf(coef, P, 2, e) * X.lu(i + 1, j, k) + cf(coef, P, 3, e) * X.lu(i, j - 1, k) +
+         cf(coef, P, 4, e) * X.lu(i, j + 1, k) + cf(coef, P, 5, e) * X.lu(i, j, k - 1) +
+         cf(coef, P, 6, e) * X.lu(i, j, k + 1) +
+         cf(coef, P, 7, e) * (X.lv(i, j - 1, k) + X.lv(i, j, k) + X.lv(i + 1, j - 1, k) + X.lv(i + 1, j, k)) +
+         cf(coef, P, 8, e) * (X.lw(i, j, k - 1) + X.lw(i, j, k) + X.lw(i + 1, j, k - 1) + X.lw(i + 1, j, k));
+  }
+  vstar[e] = ru;
+  if (G.dof_v(i, j, k)) {
+    rv = cf(coef, P, 9, e) * X.lv(i, j, k) + cf(coef, P, 10, e) * X.lv(i - 1, j, k) +
+         cf(coef, P, 11, e) * X.lv(i + 1, j, k) + cf(coef, P, 12, e) * X.lv(i, j - 1, k) +
+         cf(coef, P, 13, e) * X.lv(i, j + 1, k) + cf(coef, P, 14, e) * X.lv(i, j, k - 1) +
+         cf(coef, P, 15, e) * X.lv(i, j, k + 1) +
+         cf(coef, P, 16, e) * (X.lu(i - 1, j, k) + X.lu(i, j, k) + X.lu(i - 1, j + 1, k) + X.lu(i, j + 1, k)) +
+         cf(coef, P, 17, e) * (X.lw(i, j, k - 1) + X.lw(i, j, k) + X.lw(i, j + 1, k - 1) + X.lw(i, j + 1, k));
+  }
+  vstar[P + e] = rv;
+  if (G.dof_w(i, j, k)) {
+    rw = cf(coef, P, 18, e) * X.lw(i, j, k) + cf(coef, P, 19, e) * X.lw(i - 1, j, k) +
+         cf(coef, P, 20, e) * X.lw(i + 1, j, k) + cf(coef, P, 21, e) * X.lw(i, j - 1, k) +
+         cf(coef, P, 22, e) * X.lw(i, j + 1, k) + cf(coef, P, 23, e) * X.lw(i, j, k - 1) +
+         cf(coef, P, 24, e) * X.lw(i, j, k + 1) +
+         cf(coef, P, 25, e) * (X.lu(i - 1, j, k) + X.lu(i, j, k) + X.lu(i - 1, j, k + 1) + X.lu(i, j, k + 1)) +
+         cf(coef, P, 26, e) * (X.lv(i, j - 1, k) + X.lv(i, j, k) + X.lv(i, j - 1, k + 1) + X.lv(i, j, k + 1)) +
+         0.5 * (X.lT(i, j, k) + X.lT(i, j, k + 1));
+  }
+  vstar[2 * P + e] = rw;
+  const bool cell = i >= 1 && i <= g.nx && j >= 1 && j <= g.ny && k >= 1 && k <= g.nz;
+  if (cell) {
+    const double r = cf(coef, P, 27, e) * X.lT(i, j, k) + cf(coef, P, 28, e) * X.lT(i - 1, j, k) +
+                     cf(coef, P, 29, e) * X.lT(i + 1, j, k) + cf(coef, P, 30, e) * X.lT(i, j - 1, k) +
+                     cf(coef, P, 31, e) * X.lT(i, j + 1, k) + cf(coef, P, 32, e) * X.lT(i, j, k - 1) +
+                     cf(coef, P, 33, e) * X.lT(i, j, k + 1) + cf(coef, P, 34, e) * (X.lu(i - 1, j, k) + X.lu(i, j, k)) +
+                     cf(coef, P, 35, e) * (X.lv(i, j - 1, k) + X.lv(i, j, k)) +
+                     cf(coef, P, 36, e) * (X.lw(i, j, k - 1) + X.lw(i, j, k));
+    if (g.bc == KV_BC_AA && (j == 1 || j == g.ny)) {
+      const double t = (g.tproj == KV_TPROJ_OBLIQUE) ? r : 0.5 * r;
+      tout[e] = t;
+      tout[G.at(i, j == 1 ? 0 : g.ny + 1, k)] = t;
+    } else {
+      tout[e] = r;
+    }
+  } else {
+    const bool aa_wall = g.bc == KV_BC_AA && (j == 0 || j == g.ny + 1) && i >= 1 && i <= g.nx && k >= 1 &&
+                         k <= g.nz;
+    if (!aa_wall) tout[e] = 0.0;
+  }
+}
+
 }  // namespace
 
 void kv_launch_stencil(const kv_grid* h, int mode, const double* base, const double* x, double* vstar,
@@ -248,4 +412,18 @@ void kv_launch_stencil(const kv_grid* h, int mode, const double* base, const dou
     k_stencil<0><<<grid, block, 0, s>>>(g, base, x, h->P, vstar, tout);
   else
     k_stencil<1><<<grid, block, 0, s>>>(g, base, x, h->P, vstar, tout);
+}
+
+void kv_launch_assemble(const kv_grid* h, const double* base, double* coef, cudaStream_t s) {
+  const KvGeom& g = h->g;
+  dim3 block(32, 8, 1), grid((g.X + 31) / 32, (g.Y + 7) / 8, g.Z);
+  k_assemble<<<grid, block, 0, s>>>(g, base, h->P, coef);
+}
+
+void kv_launch_apply(const kv_grid* h, const double* coef, const double* x, double* vstar, double* tout,
+                     cudaStream_t s) {
+  const KvGeom& g = h->g;
+  const int bx = h->apply_bx, by = h->apply_by;
+  dim3 block(bx, by, 1), grid((g.X + bx - 1) / bx, (g.Y + by - 1) / by, g.Z);
+  k_apply<<<grid, block, 0, s>>>(g, coef, x, h->P, vstar, tout);
 }

@@ -10,7 +10,7 @@
 // Kernel structure (one 128 x 256 output tile per CTA, cta_group::1):
 //   warp 0      TMA producer: per stage one 128 x 64 tile of W_i and one 256 x 64 tile of X_j
 //               (128-byte swizzle), completion on a full[] mbarrier;
-//   warp 1      allocates 256 TMEM columns; lane 0 issues tcgen05.mma (M=128, N=256, K=16) and
+//   warp 1      allocates 256 TMEM columns (two CTAs per SM use all 512); lane 0 issues tcgen05.mma (M=128, N=256, K=16) and
 //               tcgen05.commit to the empty[] barrier of each stage and, last, to acc_full;
 //   warps 2-5   epilogue: tcgen05.ld of the accumulator, transposed through shared memory so
 //               that stores run along r, then either the next pass's three BF16 slices (with
@@ -25,14 +25,16 @@
 namespace {
 
 constexpr int UM = 128, UN = 256, UK = 64;  // CTA tile; UK = one 128-byte swizzle row of BF16
-constexpr int STAGES = 4;
+constexpr int STAGES = 2;  // two CTAs share an SM: one's epilogue overlaps the other's MMAs
 constexpr int A_BYTES = UM * UK * 2;        // 16 KB
 constexpr int B_BYTES = UN * UK * 2;        // 32 KB
 constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
 constexpr int EPI_WARPS = 4;
 constexpr int EPI_STRIDE = 33;              // floats per transposed row (bank-conflict free)
-constexpr int SMEM_BYTES = 1024 /*alignment slack*/ + STAGES * STAGE_BYTES +
-                           EPI_WARPS * 32 * EPI_STRIDE * 4 + 256 /*barriers + tmem slot*/;
+// The epilogue's transpose buffer reuses the stage buffers: it is touched only after the
+// accumulator barrier, when every TMA load has been consumed and every MMA has completed.
+constexpr int SMEM_BYTES = 1024 /*alignment slack*/ + STAGES * STAGE_BYTES + 256 /*barriers + tmem slot*/;
+static_assert(EPI_WARPS * 32 * EPI_STRIDE * 4 <= STAGES * STAGE_BYTES, "epilogue buffer must fit the stages");
 constexpr uint32_t WAIT_LIMIT = 1u << 24;
 constexpr int NPAIRS = 6;
 
@@ -133,13 +135,13 @@ __constant__ int kPairB[NPAIRS] = {0, 1, 2, 0, 1, 0};
 
 namespace {
 
-__global__ void __launch_bounds__(192, 1)
+__global__ void __launch_bounds__(192, 2)
     k_umma_axis(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB, int K,
                 KvUmmaEpi ep, unsigned int* err) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-  float* epi = (float*)(smem + STAGES * STAGE_BYTES);
-  uint64_t* bars = (uint64_t*)(epi + EPI_WARPS * 32 * EPI_STRIDE);
+  float* epi = (float*)smem;  // aliases the stages (used after the last MMA only)
+  uint64_t* bars = (uint64_t*)(smem + STAGES * STAGE_BYTES);
   uint32_t* tmem_slot = (uint32_t*)(bars + 2 * STAGES + 1);
   const uint32_t full0 = smem_u32(bars), empty0 = smem_u32(bars + STAGES), accb = smem_u32(bars + 2 * STAGES);
 
@@ -290,14 +292,21 @@ bool kv_make_slice_map(CUtensorMap* map, const void* base, int cols, int rows, i
 int kv_umma_box_rows_a() { return UM; }
 int kv_umma_box_rows_b() { return UN; }
 
-cudaError_t kv_launch_umma_axis(const CUtensorMap* mapA, const CUtensorMap* mapB, int K, const KvUmmaEpi& ep,
-                                unsigned int* err, cudaStream_t s) {
+// Raises the kernel's dynamic shared-memory limit (once per process, before any launch or capture).
+cudaError_t kv_umma_init() {
   static bool attr = false;
   if (!attr) {
     cudaError_t e = cudaFuncSetAttribute(k_umma_axis, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
     if (e != cudaSuccess) return e;
     attr = true;
   }
+  return cudaSuccess;
+}
+
+cudaError_t kv_launch_umma_axis(const CUtensorMap* mapA, const CUtensorMap* mapB, int K, const KvUmmaEpi& ep,
+                                unsigned int* err, cudaStream_t s) {
+  cudaError_t e0 = kv_umma_init();
+  if (e0 != cudaSuccess) return e0;
   dim3 grid((ep.R + UN - 1) / UN, (ep.M + UM - 1) / UM);
   k_umma_axis<<<grid, 192, SMEM_BYTES, s>>>(*mapA, *mapB, K, ep, err);
   return cudaGetLastError();

@@ -24,8 +24,11 @@ _STATUS = {0: "KV_OK", -1: "KV_ERR_ARG", -2: "KV_ERR_CUDA", -3: "KV_ERR_NOT_CONV
 # every symbol include/kv.h declares
 EXPORTS = ("kv_create_grid", "kv_destroy_grid", "kv_set_stream", "kv_field_len", "kv_set_base_flow",
            "kv_krylov_vector", "kv_krylov_vector_host", "kv_arnoldi_step", "kv_newton_residual", "kv_last_error",
-           "kv_profile_enable", "kv_profile_get", "kv_krylov_vector_noalloc")
-PHASES = {"stencil": 0, "divergence": 1, "tpd": 2, "correct": 3, "arnoldi": 4, "refine": 5}
+           "kv_profile_enable", "kv_profile_get", "kv_krylov_vector_noalloc", "kv_krylov_vector_adjoint",
+           "kv_base_flow_gradient", "kv_krylov_vector_batch", "kv_plan_create", "kv_plan_add", "kv_plan_launch",
+           "kv_plan_destroy", "kv_plan_last_error")
+PHASES = {"stencil": 0, "divergence": 1, "tpd": 2, "correct": 3, "arnoldi": 4, "refine": 5, "gs_dots": 6,
+          "gs_update": 7}
 
 
 class KvError(RuntimeError):
@@ -38,7 +41,7 @@ class GridDesc(ctypes.Structure):
     _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int),
                 ("spanwise_bc", ctypes.c_int), ("tproj", ctypes.c_int), ("precision", ctypes.c_int),
                 ("gr", ctypes.c_double), ("pr", ctypes.c_double), ("tol", ctypes.c_double),
-                ("max_passes", ctypes.c_int), ("refine_sweeps", ctypes.c_int)]
+                ("max_passes", ctypes.c_int), ("refine_sweeps", ctypes.c_int), ("cgs_passes", ctypes.c_int)]
 
 
 class Stats(ctypes.Structure):
@@ -71,11 +74,20 @@ def load_library(path: str = LIB_PATH):
     lib.kv_profile_enable.argtypes = [H, ctypes.c_int]
     lib.kv_profile_get.argtypes = [H, ctypes.c_int, ctypes.POINTER(ctypes.c_double),
                                    ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_longlong)]
+    lib.kv_krylov_vector_adjoint.argtypes = [H, D, D]
+    lib.kv_base_flow_gradient.argtypes = [H, D, D, D, ctypes.POINTER(ctypes.c_double)]
+    lib.kv_krylov_vector_batch.argtypes = [H, D, D, ctypes.c_int]
+    lib.kv_plan_create.argtypes = [ctypes.POINTER(ctypes.c_void_p)]
+    lib.kv_plan_add.argtypes = [ctypes.c_void_p, H, D, D]
+    lib.kv_plan_launch.argtypes = [ctypes.c_void_p, ctypes.c_void_p]
+    lib.kv_plan_destroy.argtypes = [ctypes.c_void_p]
+    lib.kv_plan_last_error.argtypes = [ctypes.c_void_p]
+    lib.kv_plan_last_error.restype = ctypes.c_char_p
     lib.kv_krylov_vector_noalloc.argtypes = [ctypes.POINTER(GridDesc), D, D, D, ctypes.c_void_p]
     lib.kv_last_error.argtypes = [H]
     lib.kv_last_error.restype = ctypes.c_char_p
     for name in EXPORTS:
-        if name != "kv_last_error":
+        if name not in ("kv_last_error", "kv_plan_last_error"):
             getattr(lib, name).restype = ctypes.c_int
     _lib = lib
     return lib
@@ -95,7 +107,7 @@ class Grid:
     """A grid handle: kv_create_grid / kv_destroy_grid around the calls of include/kv.h."""
 
     def __init__(self, nx, ny, nz, bc=KV_BC_CC, gr=1.0e6, pr=0.71, tproj=KV_TPROJ_ORTHOGONAL,
-                 precision=KV_PREC_FP64, tol=0.0, max_passes=0, refine_sweeps=0):
+                 precision=KV_PREC_FP64, tol=0.0, max_passes=0, refine_sweeps=0, cgs_passes=0):
         import torch
 
         self.torch = torch
@@ -103,7 +115,7 @@ class Grid:
             raise RuntimeError("libkv needs a CUDA device")
         self.lib = load_library()
         self.nx, self.ny, self.nz = nx, ny, nz
-        self.desc = GridDesc(nx, ny, nz, bc, tproj, precision, gr, pr, tol, max_passes, refine_sweeps)
+        self.desc = GridDesc(nx, ny, nz, bc, tproj, precision, gr, pr, tol, max_passes, refine_sweeps, cgs_passes)
         h = ctypes.c_void_p()
         st = self.lib.kv_create_grid(ctypes.byref(self.desc), ctypes.c_void_p(self._stream()), ctypes.byref(h))
         if st != 0:
@@ -177,6 +189,36 @@ class Grid:
         self._check(self.lib.kv_arnoldi_step(self.h, _dev_ptr(V, self.torch, "V", (j + 2) * L), j, hcol))
         return np.array(hcol[:])
 
+    def krylov_vector_batch(self, X, Y=None):
+        """Y[b] = A X[b] for a block X of shape (nb, 4, nz+2, ny+2, nx+2), replayed from a CUDA graph."""
+        self._sync_stream()
+        nb = X.shape[0]
+        if Y is None:
+            Y = self.empty(nb, 4)
+        self._check(self.lib.kv_krylov_vector_batch(self.h, _dev_ptr(X, self.torch, "X", nb * 4 * self.field_len),
+                                                    _dev_ptr(Y, self.torch, "Y", nb * 4 * self.field_len), nb))
+        return Y
+
+    def krylov_vector_adjoint(self, y, z=None):
+        """z = A^T y (transpose of the Krylov map)."""
+        self._sync_stream()
+        if z is None:
+            z = self.empty(4)
+        self._check(self.lib.kv_krylov_vector_adjoint(self.h, _dev_ptr(y, self.torch, "y", 4 * self.field_len),
+                                                      _dev_ptr(z, self.torch, "z", 4 * self.field_len)))
+        return z
+
+    def base_flow_gradient(self, x, y, want_theta=True, want_gr=True):
+        """(d<y, A x>/d Theta as a padded field or None, d<y, A x>/d Gr or None)."""
+        self._sync_stream()
+        gt = self.empty() if want_theta else None
+        dgr = ctypes.c_double()
+        self._check(self.lib.kv_base_flow_gradient(self.h, _dev_ptr(x, self.torch, "x", 4 * self.field_len),
+                                                   _dev_ptr(y, self.torch, "y", 4 * self.field_len),
+                                                   _dev_ptr(gt, self.torch, "g_theta", self.field_len),
+                                                   ctypes.byref(dgr) if want_gr else None))
+        return gt, (dgr.value if want_gr else None)
+
     def profile_enable(self, on=True):
         self._sync_stream()
         self._check(self.lib.kv_profile_enable(self.h, 1 if on else 0))
@@ -199,3 +241,42 @@ class Grid:
                                                 _dev_ptr(F, self.torch, "F", 4 * self.field_len),
                                                 ctypes.byref(nrm)))
         return F, nrm.value
+
+
+class Plan:
+    """Several grids' Krylov vectors evaluated by one CUDA-graph launch (kv_plan_*)."""
+
+    def __init__(self):
+        import torch
+
+        self.torch = torch
+        self.lib = load_library()
+        p = ctypes.c_void_p()
+        st = self.lib.kv_plan_create(ctypes.byref(p))
+        if st != 0:
+            raise KvError(st, "kv_plan_create")
+        self.p = p
+        self._keep = []
+
+    def add(self, grid, x, y):
+        st = self.lib.kv_plan_add(self.p, grid.h, _dev_ptr(x, self.torch, "x", 4 * grid.field_len),
+                                  _dev_ptr(y, self.torch, "y", 4 * grid.field_len))
+        if st != 0:
+            raise KvError(st, self.lib.kv_plan_last_error(self.p).decode())
+        self._keep.append((grid, x, y))
+
+    def launch(self):
+        st = self.lib.kv_plan_launch(self.p, ctypes.c_void_p(self.torch.cuda.current_stream().cuda_stream))
+        if st != 0:
+            raise KvError(st, self.lib.kv_plan_last_error(self.p).decode())
+
+    def close(self):
+        if getattr(self, "p", None):
+            self.lib.kv_plan_destroy(self.p)
+            self.p = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,64 @@
+"""Batched evaluation replayed from a CUDA graph, and multi-grid plans (several grids, Grashof
+numbers and boundary types in one graph launch): results equal the single-vector path."""
+import numpy as np
+import pytest
+
+from paper_1905_11601_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1905_11601_gb300 import build
+    build.build()
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_batch_equals_single_calls_and_replays(precision):
+    from paper_1905_11601_gb300 import kv
+    n = (24, 20, 18)
+    g = kv.Grid(*n, gr=2e6, precision=precision)
+    g.set_base_flow(torch.from_numpy(np.stack(synth.base_flow(*n, synth.CC, 101))).cuda())
+    X = torch.from_numpy(synth.krylov_input(*n, 102, count=5)).cuda()
+    ref = torch.stack([g.krylov_vector(X[b].contiguous()) for b in range(5)])
+    Y = g.krylov_vector_batch(X)
+    torch.cuda.synchronize()
+    assert torch.equal(Y, ref)
+    # replay with new contents of the same buffers
+    X.copy_(torch.from_numpy(synth.krylov_input(*n, 103, count=5)))
+    g.krylov_vector_batch(X, Y)
+    ref = torch.stack([g.krylov_vector(X[b].contiguous()) for b in range(5)])
+    torch.cuda.synchronize()
+    assert torch.equal(Y, ref)
+
+
+def test_plan_over_mixed_grids():
+    """Grids of different sizes, boundary types, Grashof numbers and precisions in one graph."""
+    from paper_1905_11601_gb300 import kv
+    specs = [((16, 16, 16), synth.CC, 1e6, 0), ((20, 12, 18), synth.AA, 4e6, 0), ((32, 32, 32), synth.CC, 2e6, 1),
+             ((24, 24, 24), synth.AA, 3e6, 1)]
+    plan = kv.Plan()
+    grids, xs, ys, refs = [], [], [], []
+    for q, (n, bc, gr, prec) in enumerate(specs):
+        g = kv.Grid(*n, bc=bc, gr=gr, precision=prec)
+        g.set_base_flow(torch.from_numpy(np.stack(synth.base_flow(*n, bc, 110 + q))).cuda())
+        for r in range(2):  # two vectors per grid: ordered on its branch
+            x = torch.from_numpy(synth.krylov_input(*n, 120 + 2 * q + r)[0]).cuda()
+            y = g.empty(4)
+            plan.add(g, x, y)
+            xs.append(x)
+            ys.append(y)
+            refs.append((g, x))
+        grids.append(g)
+    for _ in range(2):  # capture, then replay
+        for y in ys:
+            y.fill_(float("nan"))
+        plan.launch()
+        torch.cuda.synchronize()
+        for y, (g, x) in zip(ys, refs):
+            assert torch.equal(y, g.krylov_vector(x))
+    plan.close()

@@ -107,6 +107,31 @@ def test_arnoldi_steps_match_oracle():
     assert np.abs(G - np.eye(k + 1)).max() < 1e-12
 
 
+@pytest.mark.parametrize("prec,cgs", [(0, 0), (1, 0), (1, 2)])
+def test_arnoldi_orthogonality_over_a_long_basis(prec, cgs):
+    """Both Gram-Schmidt code paths (fused for <= 24 vectors, unfused beyond) keep the basis
+    orthonormal to rounding."""
+    from paper_1905_11601_gb300 import kv
+    n = (20, 18, 16)
+    base = np.stack(synth.base_flow(*n, synth.CC, 61))
+    g = kv.Grid(*n, gr=1e6, precision=prec, cgs_passes=cgs)
+    g.set_base_flow(torch.from_numpy(base).cuda())
+    k = 30
+    V = torch.zeros((k + 1, 4) + g.shape, dtype=torch.float64, device="cuda")
+    y = g.krylov_vector(torch.from_numpy(synth.krylov_input(*n, 62)[0]).cuda())
+    V[0] = y / torch.linalg.vector_norm(y)
+    H = np.zeros((k + 1, k))
+    for j in range(k):
+        H[: j + 2, j] = g.arnoldi_step(V, j)
+    Vm = V.reshape(k + 1, -1)
+    G = (Vm @ Vm.T).cpu().numpy()
+    assert np.abs(G - np.eye(k + 1)).max() < 1e-12
+    # Arnoldi relation A V_k = V_{k+1} H
+    AV = torch.stack([g.krylov_vector(V[j].contiguous()) for j in range(k)]).reshape(k, -1)
+    R = AV.T - Vm.T @ torch.from_numpy(H).cuda()
+    assert (torch.linalg.matrix_norm(R) / torch.linalg.matrix_norm(AV)).item() < 1e-12
+
+
 def test_host_buffer_entry_point_matches_device_path():
     n = (18, 16, 14)
     g, base, x = setup(n, synth.CC, 1e6, 9)

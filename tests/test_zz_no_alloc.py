@@ -24,7 +24,7 @@ def built():
 
 
 def _desc(kv, n, bc, gr, precision=0):
-    return kv.GridDesc(n[0], n[1], n[2], bc, 0, precision, gr, 0.71, 0.0, 0, 0)
+    return kv.GridDesc(n[0], n[1], n[2], bc, 0, precision, gr, 0.71, 0.0, 0, 0, 0)
 
 
 @pytest.mark.parametrize("n,bc", [((20, 17, 24), synth.CC), ((32, 9, 30), synth.AA)])
