@@ -53,8 +53,9 @@ def parse_args():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the 16-vector block and the 12-grid plan measurements")
-    ap.add_argument("--single", choices=["fp64", "mixed"], default=None,
-                    help="profiling case: two untimed Krylov-vector evaluations, no JSON line")
+    ap.add_argument("--single", choices=["fp64", "mixed", "mixed-arnoldi"], default=None,
+                    help="profiling case: two untimed Krylov-vector evaluations (or 8 Arnoldi steps), "
+                         "no JSON line")
     return ap.parse_args()
 
 
@@ -473,11 +474,16 @@ def run_single(args):
     w = synth.WORKLOADS[args.workload]
     base_np, x_np = synth.workload_arrays(w)
     g = kv.Grid(w.nx, w.ny, w.nz, bc=w.bc, gr=w.gr, pr=w.pr,
-                precision=kv.KV_PREC_MIXED if args.single == "mixed" else kv.KV_PREC_FP64)
+                precision=kv.KV_PREC_FP64 if args.single == "fp64" else kv.KV_PREC_MIXED)
     g.set_base_flow(torch.from_numpy(np.stack(base_np)).cuda())
     x = torch.from_numpy(x_np[0]).cuda()
     for _ in range(2):
         y, st = g.krylov_vector(x, stats=True)
+    if args.single == "mixed-arnoldi":
+        V = torch.zeros((9, 4) + g.shape, dtype=torch.float64, device="cuda")
+        V[0] = y / torch.linalg.vector_norm(y)
+        for j in range(8):
+            g.arnoldi_step(V, j)
     torch.cuda.synchronize()
     print(f"single {args.single} {w.name}: rel_div {st.rel_div:.2e} device_error {st.device_error}")
 

@@ -164,11 +164,13 @@ kv_status kv_krylov_vector_adjoint(kv_handle h, const double* y, double* z);
 
 /* Sensitivity of <y, A x> to the base state and the Grashof number (with y the adjoint and x
    the direct eigenvector this gives the sensitivity of an eigenvalue of Eq (10)):
-   g_theta (device, one padded field, nullable) = d<y, A x>/d Theta, from the term
-   -(v . grad) Theta of Eq (8); dgr (host, nullable) = d<y, A x>/d Gr, from the scalings
-   Gr^-1/2 and (Pr Gr^1/2)^-1 of Eqs (1)-(2). x, y: packed vectors (device). Synchronises the
-   stream when dgr is given. Same requirements as kv_krylov_vector_adjoint. */
-kv_status kv_base_flow_gradient(kv_handle h, const double* x, const double* y, double* g_theta, double* dgr);
+   g_base (device, packed U | V | W | Theta layout, nullable) = d<y, A x>/d(U, V, W, Theta):
+   the velocity part from the advecting velocities and the velocity gradients of Eqs (8)-(9),
+   the Theta part from the term -(v . grad) Theta of Eq (8); dgr (host, nullable) =
+   d<y, A x>/d Gr, from the scalings Gr^-1/2 and (Pr Gr^1/2)^-1 of Eqs (1)-(2). x, y: packed
+   vectors (device). Synchronises the stream when dgr is given. Same requirements as
+   kv_krylov_vector_adjoint. */
+kv_status kv_base_flow_gradient(kv_handle h, const double* x, const double* y, double* g_base, double* dgr);
 
 /* Newton step 2 of Section 3.1: the steady residual of Eqs (1)-(2) at the packed state S
    (device; carries its own inhomogeneous wall values, Eqs (4)-(7)), projected like a

@@ -17,7 +17,13 @@ _LIB = os.path.join(_HERE, "libkv_oracle.so")
 
 
 def build_oracle(force: bool = False) -> str:
-    """Compile kv_oracle.c with gcc (OpenMP) into oracle/libkv_oracle.so."""
+    """Compile kv_oracle.c with gcc (OpenMP) into oracle/libkv_oracle.so.
+
+    KV_ORACLE_LIB names another build of the same source to load instead (the mutation tests
+    load deliberately broken copies this way)."""
+    override = os.environ.get("KV_ORACLE_LIB")
+    if override:
+        return override
     if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
         tmp = _LIB + f".tmp{os.getpid()}"
         subprocess.check_call(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-fopenmp",

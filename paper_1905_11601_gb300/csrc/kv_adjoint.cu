@@ -190,6 +190,120 @@ __global__ void __launch_bounds__(256) k_grad_theta(KvGeom g, const double* __re
   gt[i + g.X * (j + g.Y * k)] = -s;
 }
 
+// P_BC x's temperature read on the fly (as in the forward stencil)
+__device__ __forceinline__ double xT_proj(const KvGeom& g, const double* __restrict__ T, int i, int j, int k) {
+  if (i < 1 || i > g.nx || k < 1 || k > g.nz) return 0.0;
+  if (g.bc == KV_BC_CC) return (j < 1 || j > g.ny) ? 0.0 : __ldg(T + i + g.X * (j + g.Y * k));
+  if (j <= 1 || j >= g.ny) {
+    const int jw = j <= 1 ? 0 : g.ny + 1, jn = j <= 1 ? 1 : g.ny;
+    return 0.5 * (__ldg(T + i + g.X * (jw + g.Y * k)) + __ldg(T + i + g.X * (jn + g.Y * k)));
+  }
+  return __ldg(T + i + g.X * (j + g.Y * k));
+}
+
+__device__ __forceinline__ bool dof(const KvGeom& g, int F, const int o[3]) {
+  const int n[3] = {g.nx, g.ny, g.nz};
+  for (int a = 0; a < 3; ++a) {
+    const int hi = (F == a) ? n[a] - 1 : n[a];
+    if (o[a] < 1 || o[a] > hi) return false;
+  }
+  return true;
+}
+
+// value of P_BC x for field F at o (velocity masked, temperature projected)
+__device__ __forceinline__ double xval(const KvGeom& g, const double* __restrict__ x, size_t P, int F, const int o[3]) {
+  if (F == 3) return xT_proj(g, x + 3 * P, o[0], o[1], o[2]);
+  return xmask(g, x + (size_t)F * P, F, o[0], o[1], o[2]);
+}
+
+// first-derivative weights along axis a at index t for a field that is face-like along a or not
+__device__ __forceinline__ void d1w_any(bool face, int t, int n, double ih, double& m, double& c, double& p) {
+  if (face) { m = -0.5 * ih; c = 0.0; p = 0.5 * ih; }
+  else d1w(t, n, ih, m, c, p);
+}
+
+// D1 along axis a of (P_BC x)_F at the node o of field F
+__device__ __forceinline__ double d1x(const KvGeom& g, const double* __restrict__ x, size_t P, int F, int a,
+                                      const int o[3]) {
+  const int n[3] = {g.nx, g.ny, g.nz};
+  const double ih[3] = {g.ihx, g.ihy, g.ihz};
+  double m, c, p;
+  d1w_any(F == a, o[a], n[a], ih[a], m, c, p);
+  int lo[3] = {o[0], o[1], o[2]}, hi[3] = {o[0], o[1], o[2]};
+  lo[a] -= 1;
+  hi[a] += 1;
+  return m * xval(g, x, P, F, lo) + c * xval(g, x, P, F, o) + p * xval(g, x, P, F, hi);
+}
+
+// (P_BC x)_{cp} averaged to the node o of the velocity field c (cp != c): 4 points
+__device__ __forceinline__ double interp4(const KvGeom& g, const double* __restrict__ x, size_t P, int cp, int c,
+                                          const int o[3]) {
+  double s = 0.0;
+  for (int dc = -1; dc <= 0; ++dc)
+    for (int dF = 0; dF <= 1; ++dF) {
+      int t[3] = {o[0], o[1], o[2]};
+      t[cp] += dc;
+      t[c] += dF;
+      s += xval(g, x, P, cp, t);
+    }
+  return 0.25 * s;
+}
+
+// d <yh, J x> / d U_c(q) for the three base velocity components c at the padded entry q:
+// (A) J's advecting-velocity factors I_{c->F}(U_c) in every equation F, (B) the gradients
+// D1(U_c) of the c-momentum equation's term -(v . grad) U_c.
+__global__ void __launch_bounds__(256) k_grad_vel(KvGeom g, const double* __restrict__ x,
+                                                  const double* __restrict__ yh, size_t P, double* __restrict__ gv) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = blockIdx.y * blockDim.y + threadIdx.y;
+  const int k = blockIdx.z;
+  if (i >= g.X || j >= g.Y || k >= g.Z) return;
+  const int q[3] = {i, j, k};
+  const int n[3] = {g.nx, g.ny, g.nz};
+  const double ih[3] = {g.ihx, g.ihy, g.ihz};
+  const int e = i + g.X * (j + g.Y * k);
+  auto yv = [&](int F, const int o[3]) { return __ldg(yh + (size_t)F * P + o[0] + g.X * (o[1] + g.Y * o[2])); };
+  for (int c = 0; c < 3; ++c) {
+    double s = 0.0;
+    // (A) U_c(q) as advecting velocity
+    for (int F = 0; F < 4; ++F) {
+      if (F == c) {
+        if (dof(g, c, q)) s -= d1x(g, x, P, c, c, q) * yv(c, q);
+      } else if (F < 3) {
+        // F-face o reads U_c at (o_c - 1, o_c) x (o_F, o_F + 1)
+        for (int dc = 0; dc <= 1; ++dc)
+          for (int dF = -1; dF <= 0; ++dF) {
+            int o[3] = {q[0], q[1], q[2]};
+            o[c] += dc;
+            o[F] += dF;
+            if (dof(g, F, o)) s -= 0.25 * d1x(g, x, P, F, c, o) * yv(F, o);
+          }
+      } else {
+        // cell o reads U_c at o_c - 1 and o_c
+        for (int dc = 0; dc <= 1; ++dc) {
+          int o[3] = {q[0], q[1], q[2]};
+          o[c] += dc;
+          if (dof(g, 3, o)) s -= 0.5 * d1x(g, x, P, 3, c, o) * yv(3, o);
+        }
+      }
+    }
+    // (B) U_c(q) inside D1_{cp}(U_c) at the c-faces o = q + off e_cp
+    for (int cp = 0; cp < 3; ++cp)
+      for (int off = -1; off <= 1; ++off) {
+        int o[3] = {q[0], q[1], q[2]};
+        o[cp] += off;
+        if (!dof(g, c, o)) continue;
+        double m, cc, p;
+        d1w_any(cp == c, o[cp], n[cp], ih[cp], m, cc, p);
+        const double w = off == 1 ? m : (off == 0 ? cc : p);
+        if (w == 0.0) continue;
+        const double a = (cp == c) ? xval(g, x, P, c, o) : interp4(g, x, P, cp, c, o);
+        s -= a * yv(c, o) * w;
+      }
+    gv[(size_t)c * P + e] = s;
+  }
+}
+
 __device__ __forceinline__ double warp_sum(double v) {
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
   return v;
@@ -280,6 +394,12 @@ void kv_launch_grad_theta(const kv_grid* h, const double* x, const double* yT, d
   const KvGeom& g = h->g;
   dim3 block(32, 8, 1), grid((g.X + 31) / 32, (g.Y + 7) / 8, g.Z);
   k_grad_theta<<<grid, block, 0, s>>>(g, x, yT, h->P, gt);
+}
+
+void kv_launch_grad_vel(const kv_grid* h, const double* x, const double* yh, double* gv, cudaStream_t s) {
+  const KvGeom& g = h->g;
+  dim3 block(32, 8, 1), grid((g.X + 31) / 32, (g.Y + 7) / 8, g.Z);
+  k_grad_vel<<<grid, block, 0, s>>>(g, x, yh, h->P, gv);
 }
 
 void kv_launch_lap_dot(const kv_grid* h, const double* x, const double* yh, double* sums, cudaStream_t s) {

@@ -75,6 +75,7 @@ kv_status validate(const kv_grid_desc* d, std::string& msg) {
 void free_all(kv_grid* h) {
   cudaFree(h->base);
   cudaFree(h->coef);
+  cudaFree(h->coef_df);
   cudaFree(h->vstar);
   cudaFree(h->tpd_a);
   cudaFree(h->tpd_b);
@@ -365,6 +366,13 @@ kv_status kv_set_base_flow(kv_handle h, const double* base) {
   if (!base) return fail(h, KV_ERR_ARG, "kv_set_base_flow: base is NULL");
   KV_CHECK_CUDA(h, cudaMemcpyAsync(h->base, base, 4 * h->P * sizeof(double), cudaMemcpyDeviceToDevice, h->s));
   kv_launch_assemble(h, h->base, h->coef, h->s);
+  if (h->d.precision == KV_PREC_MIXED) {
+    if (!h->coef_df) {
+      kv_status s = dalloc(h, &h->coef_df, (size_t)KV_NCOEF * h->P);
+      if (s != KV_OK) return s;
+    }
+    kv_launch_coef_df(h, h->coef, h->coef_df, h->s);
+  }
   kv_status ks = check_launch(h, "assemble");
   if (ks != KV_OK) return ks;
   h->has_base = true;
@@ -379,7 +387,13 @@ kv_status kv_krylov_vector(kv_handle h, const double* x, double* y, double* p, k
   const size_t L = 4 * h->P;
   if ((x < y + L && y < x + L)) return fail(h, KV_ERR_ARG, "kv_krylov_vector: x and y overlap");
   // J P_BC x: momentum right-hand side to vstar, projected temperature straight into y
-  { KvPhase ph(h, KV_PH_STENCIL, 1); kv_launch_apply(h, h->coef, x, h->vstar, y + 3 * h->P, h->s); }
+  {
+    KvPhase ph(h, KV_PH_STENCIL, 1);
+    if (h->d.precision == KV_PREC_MIXED)
+      kv_launch_apply_df(h, h->coef_df, x, h->vstar, y + 3 * h->P, h->s);
+    else
+      kv_launch_apply(h, h->coef, x, h->vstar, y + 3 * h->P, h->s);
+  }
   kv_status ks = check_launch(h, "stencil");
   if (ks != KV_OK) return ks;
   return simple_project(h, y, p, st);
@@ -450,9 +464,11 @@ kv_status kv_arnoldi_step(kv_handle h, double* V, int j, double* h_col) {
     const double before = hh[nq], after = hh[2 * nq + 1];
     const bool reorth = h->d.cgs_passes == 2 || !(after > 0.5 * before);
     {
-      KvPhase ph(h, KV_PH_ARNOLDI, reorth ? 3 : 1);
-      if (reorth) kv_launch_update_small_norm(V, L, nq, h2, w, L, h->partials, nrm, h->s);
-      kv_launch_scale_inv_sqrt(w, L, reorth ? nrm : h2 + nq, h->s);
+      KvPhase ph(h, KV_PH_ARNOLDI, 1);
+      if (reorth)
+        kv_launch_update_small_scale(V, L, nq, h2, w, L, h->s);
+      else
+        kv_launch_scale_inv_sqrt(w, L, h2 + nq, h->s);
     }
     s = check_launch(h, "arnoldi");
     if (s != KV_OK) return s;
@@ -461,6 +477,15 @@ kv_status kv_arnoldi_step(kv_handle h, double* V, int j, double* h_col) {
       h_col[nq] = sqrt(after);
       return KV_OK;
     }
+    // beta^2 = ||w1||^2 - ||h2||^2 (V orthonormal), the factor the fused sweep applied
+    double h2n = 0.0;
+    for (int q = 0; q < nq; ++q) {
+      h_col[q] = hh[q] + hh[nq + 1 + q];
+      h2n += hh[nq + 1 + q] * hh[nq + 1 + q];
+    }
+    const double b2 = after - h2n;
+    h_col[nq] = b2 > 0.0 ? sqrt(b2) : 0.0;
+    return KV_OK;
   } else {
     const int md = (nq + 7) / 8 + 1;  // multidot sweeps + finalize
     KvPhase ph(h, KV_PH_ARNOLDI, 2 * md + 2 + 2 + 1);
@@ -551,7 +576,7 @@ kv_status kv_krylov_vector_adjoint(kv_handle h, const double* y, double* z) {
   return check_launch(h, "transpose stencil");
 }
 
-kv_status kv_base_flow_gradient(kv_handle h, const double* x, const double* y, double* g_theta, double* dgr) {
+kv_status kv_base_flow_gradient(kv_handle h, const double* x, const double* y, double* g_base, double* dgr) {
   if (!h) return KV_ERR_ARG;
   if (!x || !y) return fail(h, KV_ERR_ARG, "kv_base_flow_gradient: x and y must be non-NULL");
   if (!h->has_base) return fail(h, KV_ERR_STATE, "kv_base_flow_gradient: no base flow set");
@@ -559,7 +584,10 @@ kv_status kv_base_flow_gradient(kv_handle h, const double* x, const double* y, d
     return fail(h, KV_ERR_ARG, "kv_base_flow_gradient: defined for the orthogonal temperature projection");
   kv_status s = project_output_side(h, y);
   if (s != KV_OK) return s;
-  if (g_theta) kv_launch_grad_theta(h, x, h->adj + 3 * h->P, g_theta, h->s);
+  if (g_base) {
+    kv_launch_grad_vel(h, x, h->adj, g_base, h->s);
+    kv_launch_grad_theta(h, x, h->adj + 3 * h->P, g_base + 3 * h->P, h->s);
+  }
   if (dgr) {
     if (!h->adjsum) {
       s = dalloc(h, &h->adjsum, 2);

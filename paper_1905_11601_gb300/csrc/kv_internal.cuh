@@ -40,6 +40,7 @@ struct kv_grid {
 
   double* base = nullptr;   // 4P: U | V | W | Theta
   double* coef = nullptr;   // KV_NCOEF * P: assembled coefficients of J (per base flow)
+  float2* coef_df = nullptr; // KV_PREC_MIXED: the same coefficients as FP32 pairs
   double* vstar = nullptr;  // 3P: momentum right-hand side before the projection
   double* tpd_a = nullptr;  // Nc: divergence / Poisson ping-pong buffers
   double* tpd_b = nullptr;  // Nc
@@ -138,6 +139,7 @@ void kv_launch_adj_prep(const kv_grid* h, const double* y, double* vel, double* 
 void kv_launch_apply_t(const kv_grid* h, const double* coef, const double* yh, double* z, cudaStream_t s);
 void kv_launch_grad_theta(const kv_grid* h, const double* x, const double* yT, double* gt, cudaStream_t s);
 void kv_launch_lap_dot(const kv_grid* h, const double* x, const double* yh, double* sums, cudaStream_t s);
+void kv_launch_grad_vel(const kv_grid* h, const double* x, const double* yh, double* gv, cudaStream_t s);
 
 // kv_stencil.cu
 // mode 0: y* = J P_BC x (Eqs (11)-(12)); mode 1: y* = F(S) (steady residual, x = base = S).
@@ -150,6 +152,10 @@ void kv_launch_stencil(const kv_grid* h, int mode, const double* base, const dou
 void kv_launch_assemble(const kv_grid* h, const double* base, double* coef, cudaStream_t s);
 void kv_launch_apply(const kv_grid* h, const double* coef, const double* x, double* vstar, double* tout,
                      cudaStream_t s);
+// mixed precision: FP32-pair copy of the coefficients, and J P_BC x in double-float on the FP32 pipe
+void kv_launch_coef_df(const kv_grid* h, const double* coef, float2* cdf, cudaStream_t s);
+void kv_launch_apply_df(const kv_grid* h, const float2* cdf, const double* x, double* vstar, double* tout,
+                        cudaStream_t s);
 
 // kv_project.cu
 void kv_launch_divergence(const kv_grid* h, const double* vel, double* b, cudaStream_t s);
@@ -177,11 +183,11 @@ void kv_launch_scale_inv_sqrt(double* w, size_t len, const double* nrm2, cudaStr
 // Gram-Schmidt building blocks for nq <= kv_fused_cgs_max() vectors (one sweep each):
 // h[q] = <V_q, w> (and h[nq] = ||w||^2 when nrm2 != nullptr, copied to nrm2);
 // w -= V c fused with h2[q] = <V_q, w> and h2[nq] = ||w||^2 (FP64);
-// w -= V c for rounding-size c (product in FP32) with ||w||^2.
+// w = (w - V c) / sqrt(c[nq] - ||c||^2) for rounding-size c = V^T w (product in FP32).
 int kv_fused_cgs_max();
 void kv_launch_dots_norm(const double* V, size_t ld, int nq, const double* w, size_t len, double* partials,
                          double* h, double* nrm2, cudaStream_t s);
 void kv_launch_update_dot(const double* V, size_t ld, int nq, const double* c, double* w, size_t len,
                           double* partials, double* h2, cudaStream_t s);
-void kv_launch_update_small_norm(const double* V, size_t ld, int nq, const double* c, double* w, size_t len,
-                                 double* partials, double* nrm2, cudaStream_t s);
+void kv_launch_update_small_scale(const double* V, size_t ld, int nq, const double* c, double* w, size_t len,
+                                  cudaStream_t s);

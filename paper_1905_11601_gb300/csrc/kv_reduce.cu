@@ -8,7 +8,10 @@ namespace {
 constexpr int RB = 1216;  // reduction blocks: 8 per SM on 152 SMs
 constexpr int RT = 256;   // threads per block
 constexpr int QB = 8;     // inner products accumulated per sweep over the vector
-constexpr int QF = 24;    // inner products of the fused second Gram-Schmidt pass
+constexpr int QF = 24;    // largest basis handled by the fused Gram-Schmidt kernels
+#define KV_FOR_EACH_NQ(X)                                                                                  \
+  X(1) X(2) X(3) X(4) X(5) X(6) X(7) X(8) X(9) X(10) X(11) X(12) X(13) X(14) X(15) X(16) X(17) X(18) X(19) \
+      X(20) X(21) X(22) X(23) X(24)
 
 __device__ __forceinline__ double warp_sum(double v) {
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -103,8 +106,7 @@ __global__ void __launch_bounds__(RT) k_dots(const double* __restrict__ V, size_
   for (size_t e = (size_t)blockIdx.x * RT + threadIdx.x; e < len; e += (size_t)RB * RT) {
     const double we = __ldg(w + e);
 #pragma unroll
-    for (int q = 0; q < Q; ++q)
-      if (q < nq) acc[q] = fma(__ldg(V + (size_t)q * ld + e), we, acc[q]);
+    for (int q = 0; q < Q; ++q) acc[q] = fma(__ldg(V + (size_t)q * ld + e), we, acc[q]);
     acc[Q] = fma(we, we, acc[Q]);
   }
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -141,14 +143,13 @@ __global__ void __launch_bounds__(RT) k_update_dot(const double* __restrict__ V,
     double s = 0.0;
 #pragma unroll
     for (int q = 0; q < Q; ++q) {
-      v[q] = q < nq ? __ldg(V + (size_t)q * ld + e) : 0.0;
+      v[q] = __ldg(V + (size_t)q * ld + e);
       s = fma(cs[q], v[q], s);
     }
     const double w1 = w[e] - s;
     w[e] = w1;
 #pragma unroll
-    for (int q = 0; q < Q; ++q)
-      if (q < nq) acc[q] = fma(v[q], w1, acc[q]);
+    for (int q = 0; q < Q; ++q) acc[q] = fma(v[q], w1, acc[q]);
     acc[Q] = fma(w1, w1, acc[Q]);
   }
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -166,34 +167,31 @@ __global__ void __launch_bounds__(RT) k_update_dot(const double* __restrict__ V,
   }
 }
 
-// Second pass, second half: w -= sum_q c[q] V_q. The second-pass coefficients are of rounding
-// size relative to w, so their product with V is formed in FP32 from the high words (its error
-// is ~1e-6 of a rounding-size correction); the subtraction and the block's share of ||w||^2
-// (partials[block]) are FP64.
-__global__ void __launch_bounds__(RT) k_update_small_norm(const double* __restrict__ V, size_t ld, int nq,
-                                                          const double* __restrict__ c, double* __restrict__ w,
-                                                          size_t len, double* __restrict__ partials) {
+// Second pass, second half, fused with the normalisation: w = (w - sum_q c[q] V_q) / beta. The
+// second-pass coefficients are of rounding size relative to w, so their product with V is formed
+// in FP32 from the high words (its error is ~1e-6 of a rounding-size correction) and subtracted
+// in FP64. With V orthonormal and c = V^T w, beta^2 = ||w||^2 - ||c||^2 (c[nq] holds ||w||^2),
+// which needs no further pass over w.
+__global__ void __launch_bounds__(RT) k_update_small_scale(const double* __restrict__ V, size_t ld, int nq,
+                                                           const double* __restrict__ c, double* __restrict__ w,
+                                                           size_t len) {
   __shared__ float cs[QF];
-  __shared__ double sm[RT / 32];
-  if (threadIdx.x < QF) cs[threadIdx.x] = threadIdx.x < nq ? (float)c[threadIdx.x] : 0.0f;
+  __shared__ double finv;
+  if (threadIdx.x < QF) cs[threadIdx.x] = (int)threadIdx.x < nq ? (float)c[threadIdx.x] : 0.0f;
+  if (threadIdx.x == 0) {
+    double s = 0.0;
+    for (int q = 0; q < nq; ++q) s = fma(c[q], c[q], s);
+    const double b2 = c[nq] - s;
+    finv = b2 > 0.0 ? 1.0 / sqrt(b2) : 0.0;
+  }
   __syncthreads();
-  double nrm = 0.0;
+  const double f = finv;
   for (size_t e = (size_t)blockIdx.x * RT + threadIdx.x; e < len; e += (size_t)RB * RT) {
     float s = 0.0f;
 #pragma unroll
     for (int q = 0; q < QF; ++q)
       if (q < nq) s = fmaf(cs[q], hi_float(__ldg(V + (size_t)q * ld + e)), s);
-    const double w2 = w[e] - (double)s;
-    w[e] = w2;
-    nrm = fma(w2, w2, nrm);
-  }
-  nrm = warp_sum(nrm);
-  if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = nrm;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    double t = 0.0;
-    for (int wv = 0; wv < RT / 32; ++wv) t += sm[wv];
-    partials[blockIdx.x] = t;
+    w[e] = (w[e] - (double)s) * f;
   }
 }
 
@@ -205,31 +203,35 @@ int kv_fused_cgs_max() { return QF; }
 void kv_launch_dots_norm(const double* V, size_t ld, int nq, const double* w, size_t len, double* partials,
                          double* h, double* nrm2, cudaStream_t s) {
   const int nrm = nrm2 != nullptr;
-  if (nq <= 8)
-    k_dots<8><<<RB, RT, 0, s>>>(V, ld, nq, w, len, nrm, partials);
-  else if (nq <= 16)
-    k_dots<16><<<RB, RT, 0, s>>>(V, ld, nq, w, len, nrm, partials);
-  else
-    k_dots<QF><<<RB, RT, 0, s>>>(V, ld, nq, w, len, nrm, partials);
+  // one instantiation per basis size, so no predicated-off multiply-adds occupy the FP64 pipe
+  switch (nq) {
+#define KV_DOTS_CASE(Qn) \
+  case Qn:               \
+    k_dots<Qn><<<RB, RT, 0, s>>>(V, ld, nq, w, len, nrm, partials); \
+    break;
+    KV_FOR_EACH_NQ(KV_DOTS_CASE)
+#undef KV_DOTS_CASE
+  }
   k_finalize<<<nq + (nrm2 ? 1 : 0), RT, 0, s>>>(partials, h, 0);  // h[nq] = ||w||^2 when asked
   if (nrm2 && nrm2 != h + nq) cudaMemcpyAsync(nrm2, h + nq, sizeof(double), cudaMemcpyDeviceToDevice, s);
 }
 
 void kv_launch_update_dot(const double* V, size_t ld, int nq, const double* c, double* w, size_t len,
                           double* partials, double* h2, cudaStream_t s) {
-  if (nq <= 8)
-    k_update_dot<8><<<RB, RT, 0, s>>>(V, ld, nq, c, w, len, partials);
-  else if (nq <= 16)
-    k_update_dot<16><<<RB, RT, 0, s>>>(V, ld, nq, c, w, len, partials);
-  else
-    k_update_dot<QF><<<RB, RT, 0, s>>>(V, ld, nq, c, w, len, partials);
+  switch (nq) {
+#define KV_UPD_CASE(Qn) \
+  case Qn:              \
+    k_update_dot<Qn><<<RB, RT, 0, s>>>(V, ld, nq, c, w, len, partials); \
+    break;
+    KV_FOR_EACH_NQ(KV_UPD_CASE)
+#undef KV_UPD_CASE
+  }
   k_finalize<<<nq + 1, RT, 0, s>>>(partials, h2, 0);  // h2[nq] = ||w||^2 after the update
 }
 
-void kv_launch_update_small_norm(const double* V, size_t ld, int nq, const double* c, double* w, size_t len,
-                                 double* partials, double* nrm2, cudaStream_t s) {
-  k_update_small_norm<<<RB, RT, 0, s>>>(V, ld, nq, c, w, len, partials);
-  k_finalize<<<1, RT, 0, s>>>(partials, nrm2, 0);
+void kv_launch_update_small_scale(const double* V, size_t ld, int nq, const double* c, double* w, size_t len,
+                                  cudaStream_t s) {
+  k_update_small_scale<<<RB, RT, 0, s>>>(V, ld, nq, c, w, len);
 }
 
 void kv_launch_multidot(const double* V, size_t ld, int nq, const double* w, size_t len, double* partials,

@@ -401,6 +401,195 @@ __global__ void __launch_bounds__(256) k_apply(KvGeom g, const double* __restric
   }
 }
 
+// ---- the same operator on the FP32 pipe (mixed precision) ----------------------------------
+//
+// GB300's FP64 pipe runs at 1/60 of its FP32 rate, so the mixed path evaluates J x in
+// double-float arithmetic: every coefficient is stored as an FP32 pair c = ch + cl (|cl| <=
+// 2^-24 |ch|), every FP64 input is split into xh (its leading 21 bits, exact) and xl (the rest,
+// rounded to FP32) with integer operations only, and each product is accumulated as an exact
+// FP32 product ch*xh (FMA error term), an exact running sum (TwoSum) and a small FP32
+// correction. The result carries about 2^-44 of the sum of the term magnitudes; the only FP64
+// instruction per output is the final addition of the two FP32 halves.
+
+struct DF {
+  float h, l;
+};
+
+// x = xh + xl: xh from the high word (sign, exponent, 20 mantissa bits), xl = the low 32
+// mantissa bits times 2^(e-52), converted with two exact 16-bit pieces. |x| < 2^-74 maps to 0.
+__device__ __forceinline__ DF split_d(double x) {
+  const unsigned int hi = (unsigned int)__double2hiint(x), lo = (unsigned int)__double2loint(x);
+  const int E = (int)((hi >> 20) & 0x7FFu);
+  const unsigned int sign = hi & 0x80000000u;
+  DF r{0.0f, 0.0f};
+  if (E - 1023 + 127 <= 0) return r;
+  r.h = __uint_as_float(sign | ((unsigned int)(E - 1023 + 127) << 23) | ((hi & 0xFFFFFu) << 3));
+  if (E - 948 <= 0 || lo == 0u) return r;
+  const float fa = __fsub_rn(__uint_as_float(0x4B000000u | (lo >> 16)), 8388608.0f);      // exact
+  const float fb = __fsub_rn(__uint_as_float(0x4B000000u | (lo & 0xFFFFu)), 8388608.0f);  // exact
+  const float lf = __fmaf_rn(fa, 65536.0f, fb);                                           // one rounding
+  const float sc = __uint_as_float((unsigned int)(E - 948) << 23);                        // 2^(E-1075)
+  r.l = __uint_as_float(__float_as_uint(__fmul_rn(lf, sc)) ^ sign);
+  return r;
+}
+
+// exact FP32 -> FP64 by bit manipulation (no FP64 instruction); denormals map to 0
+__device__ __forceinline__ double f2d(float f) {
+  const unsigned int b = __float_as_uint(f);
+  const unsigned int fe = (b >> 23) & 0xFFu;
+  if (fe == 0u) return 0.0;
+  const unsigned int hi = (b & 0x80000000u) | ((fe - 127u + 1023u) << 20) | ((b & 0x7FFFFFu) >> 3);
+  const unsigned int lo = (b & 0x7u) << 29;
+  return __hiloint2double((int)hi, (int)lo);
+}
+
+struct Acc {
+  float S = 0.0f, C = 0.0f;
+  __device__ __forceinline__ void add(const float2 c, const DF x) {
+    const float p = __fmul_rn(c.x, x.h);
+    const float e = __fmaf_rn(c.x, x.h, -p);
+    const float small = __fmaf_rn(c.x, x.l, __fmaf_rn(c.y, x.h, e));
+    const float s = __fadd_rn(S, p);
+    const float bp = __fsub_rn(s, S);
+    const float err = __fadd_rn(__fsub_rn(S, __fsub_rn(s, bp)), __fsub_rn(p, bp));
+    S = s;
+    C = __fadd_rn(C, __fadd_rn(err, small));
+  }
+  __device__ __forceinline__ double value() const { return f2d(S) + f2d(C); }
+};
+
+template <bool PROJ>
+struct DFLoader {
+  Loader<PROJ> L;
+  __device__ __forceinline__ DF u(int i, int j, int k) const { return split_d(L.lu(i, j, k)); }
+  __device__ __forceinline__ DF v(int i, int j, int k) const { return split_d(L.lv(i, j, k)); }
+  __device__ __forceinline__ DF w(int i, int j, int k) const { return split_d(L.lw(i, j, k)); }
+  __device__ __forceinline__ DF T(int i, int j, int k) const { return split_d(L.lT(i, j, k)); }
+};
+
+__device__ __forceinline__ float2 cf2(const float2* __restrict__ coef, size_t P, int q, int e) {
+  return __ldg(coef + (size_t)q * P + e);
+}
+
+// y* = J P_BC x with the FP32-pair coefficients (output as k_apply).
+__global__ void __launch_bounds__(256) k_apply_df(KvGeom g, const float2* __restrict__ coef,
+                                                  const double* __restrict__ x, size_t P, double* __restrict__ vstar,
+                                                  double* __restrict__ tout) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = blockIdx.y * blockDim.y + threadIdx.y;
+  const int k = blockIdx.z;
+  if (i >= g.X || j >= g.Y || k >= g.Z) return;
+  Grid G{g};
+  const int e = G.at(i, j, k);
+  DFLoader<true> X{Loader<true>{G, x, x + P, x + 2 * P, x + 3 * P}};
+  double ru = 0.0, rv = 0.0, rw = 0.0;
+  if (G.dof_u(i, j, k)) {
+    Acc a;
+    a.add(cf2(coef, P, 0, e), X.u(i, j, k));
+    a.add(cf2(coef, P, 1, e), X.u(i - 1, j, k));
+    a.add(cf2(coef, P, 2, e), X.u(i + 1, j, k));
+    a.add(cf2(coef, P, 3, e), X.u(i, j - 1, k));
+    a.add(cf2(coef, P, 4, e), X.u(i, j + 1, k));
+    a.add(cf2(coef, P, 5, e), X.u(i, j, k - 1));
+    a.add(cf2(coef, P, 6, e), X.u(i, j, k + 1));
+    const float2 c7 = cf2(coef, P, 7, e), c8 = cf2(coef, P, 8, e);
+    a.add(c7, X.v(i, j - 1, k));
+    a.add(c7, X.v(i, j, k));
+    a.add(c7, X.v(i + 1, j - 1, k));
+    a.add(c7, X.v(i + 1, j, k));
+    a.add(c8, X.w(i, j, k - 1));
+    a.add(c8, X.w(i, j, k));
+    a.add(c8, X.w(i + 1, j, k - 1));
+    a.add(c8, X.w(i + 1, j, k));
+    ru = a.value();
+  }
+  vstar[e] = ru;
+  if (G.dof_v(i, j, k)) {
+    Acc a;
+    a.add(cf2(coef, P, 9, e), X.v(i, j, k));
+    a.add(cf2(coef, P, 10, e), X.v(i - 1, j, k));
+    a.add(cf2(coef, P, 11, e), X.v(i + 1, j, k));
+    a.add(cf2(coef, P, 12, e), X.v(i, j - 1, k));
+    a.add(cf2(coef, P, 13, e), X.v(i, j + 1, k));
+    a.add(cf2(coef, P, 14, e), X.v(i, j, k - 1));
+    a.add(cf2(coef, P, 15, e), X.v(i, j, k + 1));
+    const float2 c16 = cf2(coef, P, 16, e), c17 = cf2(coef, P, 17, e);
+    a.add(c16, X.u(i - 1, j, k));
+    a.add(c16, X.u(i, j, k));
+    a.add(c16, X.u(i - 1, j + 1, k));
+    a.add(c16, X.u(i, j + 1, k));
+    a.add(c17, X.w(i, j, k - 1));
+    a.add(c17, X.w(i, j, k));
+    a.add(c17, X.w(i, j + 1, k - 1));
+    a.add(c17, X.w(i, j + 1, k));
+    rv = a.value();
+  }
+  vstar[P + e] = rv;
+  if (G.dof_w(i, j, k)) {
+    Acc a;
+    a.add(cf2(coef, P, 18, e), X.w(i, j, k));
+    a.add(cf2(coef, P, 19, e), X.w(i - 1, j, k));
+    a.add(cf2(coef, P, 20, e), X.w(i + 1, j, k));
+    a.add(cf2(coef, P, 21, e), X.w(i, j - 1, k));
+    a.add(cf2(coef, P, 22, e), X.w(i, j + 1, k));
+    a.add(cf2(coef, P, 23, e), X.w(i, j, k - 1));
+    a.add(cf2(coef, P, 24, e), X.w(i, j, k + 1));
+    const float2 c25 = cf2(coef, P, 25, e), c26 = cf2(coef, P, 26, e);
+    a.add(c25, X.u(i - 1, j, k));
+    a.add(c25, X.u(i, j, k));
+    a.add(c25, X.u(i - 1, j, k + 1));
+    a.add(c25, X.u(i, j, k + 1));
+    a.add(c26, X.v(i, j - 1, k));
+    a.add(c26, X.v(i, j, k));
+    a.add(c26, X.v(i, j - 1, k + 1));
+    a.add(c26, X.v(i, j, k + 1));
+    const float2 half = make_float2(0.5f, 0.0f);
+    a.add(half, X.T(i, j, k));
+    a.add(half, X.T(i, j, k + 1));
+    rw = a.value();
+  }
+  vstar[2 * P + e] = rw;
+  const bool cell = i >= 1 && i <= g.nx && j >= 1 && j <= g.ny && k >= 1 && k <= g.nz;
+  if (cell) {
+    Acc a;
+    a.add(cf2(coef, P, 27, e), X.T(i, j, k));
+    a.add(cf2(coef, P, 28, e), X.T(i - 1, j, k));
+    a.add(cf2(coef, P, 29, e), X.T(i + 1, j, k));
+    a.add(cf2(coef, P, 30, e), X.T(i, j - 1, k));
+    a.add(cf2(coef, P, 31, e), X.T(i, j + 1, k));
+    a.add(cf2(coef, P, 32, e), X.T(i, j, k - 1));
+    a.add(cf2(coef, P, 33, e), X.T(i, j, k + 1));
+    const float2 c34 = cf2(coef, P, 34, e), c35 = cf2(coef, P, 35, e), c36 = cf2(coef, P, 36, e);
+    a.add(c34, X.u(i - 1, j, k));
+    a.add(c34, X.u(i, j, k));
+    a.add(c35, X.v(i, j - 1, k));
+    a.add(c35, X.v(i, j, k));
+    a.add(c36, X.w(i, j, k - 1));
+    a.add(c36, X.w(i, j, k));
+    const double r = a.value();
+    if (g.bc == KV_BC_AA && (j == 1 || j == g.ny)) {
+      const double t = (g.tproj == KV_TPROJ_OBLIQUE) ? r : 0.5 * r;
+      tout[e] = t;
+      tout[G.at(i, j == 1 ? 0 : g.ny + 1, k)] = t;
+    } else {
+      tout[e] = r;
+    }
+  } else {
+    const bool aa_wall = g.bc == KV_BC_AA && (j == 0 || j == g.ny + 1) && i >= 1 && i <= g.nx && k >= 1 &&
+                         k <= g.nz;
+    if (!aa_wall) tout[e] = 0.0;
+  }
+}
+
+// FP32-pair copy of the FP64 coefficients: ch = fp32(c), cl = fp32(c - ch).
+__global__ void __launch_bounds__(256) k_coef_df(const double* __restrict__ coef, float2* __restrict__ cdf, size_t n) {
+  for (size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += (size_t)gridDim.x * blockDim.x) {
+    const double c = coef[t];
+    const float h = __double2float_rn(c);
+    cdf[t] = make_float2(h, __double2float_rn(c - (double)h));
+  }
+}
+
 }  // namespace
 
 void kv_launch_stencil(const kv_grid* h, int mode, const double* base, const double* x, double* vstar,
@@ -426,4 +615,16 @@ void kv_launch_apply(const kv_grid* h, const double* coef, const double* x, doub
   const int bx = h->apply_bx, by = h->apply_by;
   dim3 block(bx, by, 1), grid((g.X + bx - 1) / bx, (g.Y + by - 1) / by, g.Z);
   k_apply<<<grid, block, 0, s>>>(g, coef, x, h->P, vstar, tout);
+}
+
+void kv_launch_coef_df(const kv_grid* h, const double* coef, float2* cdf, cudaStream_t s) {
+  k_coef_df<<<4 * 152, 256, 0, s>>>(coef, cdf, (size_t)KV_NCOEF * h->P);
+}
+
+void kv_launch_apply_df(const kv_grid* h, const float2* cdf, const double* x, double* vstar, double* tout,
+                        cudaStream_t s) {
+  const KvGeom& g = h->g;
+  const int bx = h->apply_bx, by = h->apply_by;
+  dim3 block(bx, by, 1), grid((g.X + bx - 1) / bx, (g.Y + by - 1) / by, g.Z);
+  k_apply_df<<<grid, block, 0, s>>>(g, cdf, x, h->P, vstar, tout);
 }

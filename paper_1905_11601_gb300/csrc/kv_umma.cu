@@ -7,14 +7,17 @@
 // one FP32 TMEM accumulator, which gives about FP32 accuracy. The FP64 accuracy of the solve
 // is won back by iterative refinement with an FP64 residual r = b - L phi (kv_mixed.cu).
 //
-// Kernel structure (one 128 x 256 output tile per CTA, cta_group::1):
+// Kernel structure (persistent, one CTA per SM, 128 x 256 output tiles, cta_group::1):
 //   warp 0      TMA producer: per stage one 128 x 64 tile of W_i and one 256 x 64 tile of X_j
 //               (128-byte swizzle), completion on a full[] mbarrier;
-//   warp 1      allocates 256 TMEM columns (two CTAs per SM use all 512); lane 0 issues tcgen05.mma (M=128, N=256, K=16) and
-//               tcgen05.commit to the empty[] barrier of each stage and, last, to acc_full;
-//   warps 2-5   epilogue: tcgen05.ld of the accumulator, transposed through shared memory so
+//   warp 1      allocates 512 TMEM columns (two 128 x 256 FP32 accumulators); lane 0 issues
+//               tcgen05.mma (M=128, N=256, K=16), tcgen05.commit to each stage's empty[] barrier
+//               and, after a tile's last MMA, to that accumulator's full barrier;
+//   warps 2-9   epilogue (two warps per TMEM lane quarter): tcgen05.ld of the accumulator, transposed through shared memory so
 //               that stores run along r, then either the next pass's three BF16 slices (with
-//               the 1 / Lambda scaling of Eq (17) in the third forward pass) or phi += D (FP64).
+//               the 1 / Lambda scaling of Eq (17) in the third forward pass) or phi += D (FP64);
+//               then they release the accumulator, so the epilogue of one tile overlaps the
+//               MMAs of the next.
 // Every mbarrier wait has an iteration limit; on expiry the kernel sets an error flag and
 // leaves without hanging.
 #include <cuda.h>
@@ -25,16 +28,16 @@
 namespace {
 
 constexpr int UM = 128, UN = 256, UK = 64;  // CTA tile; UK = one 128-byte swizzle row of BF16
-constexpr int STAGES = 2;  // two CTAs share an SM: one's epilogue overlaps the other's MMAs
+constexpr int STAGES = 3;
 constexpr int A_BYTES = UM * UK * 2;        // 16 KB
 constexpr int B_BYTES = UN * UK * 2;        // 32 KB
 constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
-constexpr int EPI_WARPS = 4;
+constexpr int EPI_WARPS = 8;  // two per TMEM lane quarter, each taking half of the columns
+constexpr int THREADS = 64 + 32 * EPI_WARPS;
 constexpr int EPI_STRIDE = 33;              // floats per transposed row (bank-conflict free)
-// The epilogue's transpose buffer reuses the stage buffers: it is touched only after the
-// accumulator barrier, when every TMA load has been consumed and every MMA has completed.
-constexpr int SMEM_BYTES = 1024 /*alignment slack*/ + STAGES * STAGE_BYTES + 256 /*barriers + tmem slot*/;
-static_assert(EPI_WARPS * 32 * EPI_STRIDE * 4 <= STAGES * STAGE_BYTES, "epilogue buffer must fit the stages");
+constexpr int EPI_BYTES = EPI_WARPS * 32 * EPI_STRIDE * 4;
+constexpr int SMEM_BYTES = 1024 /*alignment slack*/ + STAGES * STAGE_BYTES + EPI_BYTES + 256 /*barriers + slot*/;
+constexpr int TMEM_COLS = 2 * UN;  // two accumulators: the epilogue of one tile overlaps the next tile's MMAs
 constexpr uint32_t WAIT_LIMIT = 1u << 24;
 constexpr int NPAIRS = 6;
 
@@ -42,6 +45,9 @@ __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)_
 
 __device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
   asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
 }
 __device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
   asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
@@ -135,18 +141,21 @@ __constant__ int kPairB[NPAIRS] = {0, 1, 2, 0, 1, 0};
 
 namespace {
 
-__global__ void __launch_bounds__(192, 2)
+// Persistent: CTA b handles tiles b, b + gridDim.x, ...; tile t covers rows m0 = (t % ntm) * 128
+// and columns r0 = (t / ntm) * 256, so CTAs that run together share their X tiles in L2.
+__global__ void __launch_bounds__(THREADS, 1)
     k_umma_axis(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB, int K,
                 KvUmmaEpi ep, unsigned int* err) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-  float* epi = (float*)smem;  // aliases the stages (used after the last MMA only)
-  uint64_t* bars = (uint64_t*)(smem + STAGES * STAGE_BYTES);
-  uint32_t* tmem_slot = (uint32_t*)(bars + 2 * STAGES + 1);
-  const uint32_t full0 = smem_u32(bars), empty0 = smem_u32(bars + STAGES), accb = smem_u32(bars + 2 * STAGES);
+  float* epi = (float*)(smem + STAGES * STAGE_BYTES);
+  uint64_t* bars = (uint64_t*)(smem + STAGES * STAGE_BYTES + EPI_BYTES);
+  uint32_t* tmem_slot = (uint32_t*)(bars + 2 * STAGES + 4);
+  const uint32_t full0 = smem_u32(bars), empty0 = smem_u32(bars + STAGES);
+  const uint32_t accf0 = smem_u32(bars + 2 * STAGES), acce0 = smem_u32(bars + 2 * STAGES + 2);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int m0 = blockIdx.y * UM, r0 = blockIdx.x * UN;
+  const int ntm = (ep.M + UM - 1) / UM, ntr = (ep.R + UN - 1) / UN, ntiles = ntm * ntr;
   const int kchunks = (K + UK - 1) / UK;
   const int iters = NPAIRS * kchunks;
 
@@ -155,12 +164,15 @@ __global__ void __launch_bounds__(192, 2)
       mbar_init(full0 + 8 * s, 1);
       mbar_init(empty0 + 8 * s, 1);
     }
-    mbar_init(accb, 1);
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(accf0 + 8 * b, 1);                  // tcgen05.commit after a tile's last MMA
+      mbar_init(acce0 + 8 * b, EPI_WARPS * 32);     // every epilogue thread, after reading it
+    }
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (warp == 1) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
-                 "r"(UN)
+                 "r"(TMEM_COLS)
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
@@ -173,47 +185,67 @@ __global__ void __launch_bounds__(192, 2)
     if (lane == 0) {
       asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)&mapA) : "memory");
       asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)&mapB) : "memory");
-      for (int it = 0; it < iters; ++it) {
-        const int s = it % STAGES;
-        const uint32_t ph = (uint32_t)(it / STAGES) & 1u;
-        if (!mbar_wait(empty0 + 8 * s, ph ^ 1u, err)) break;
-        const int pair = it / kchunks, kc = it % kchunks;
-        const uint32_t a = smem_u32(smem + s * STAGE_BYTES), b = a + A_BYTES;
-        mbar_expect_tx(full0 + 8 * s, STAGE_BYTES);
-        tma_load_3d(a, &mapA, kc * UK, m0, kPairA[pair], full0 + 8 * s);
-        tma_load_3d(b, &mapB, kc * UK, r0, kPairB[pair], full0 + 8 * s);
+      uint32_t g = 0;  // stage counter across tiles
+      bool ok = true;
+      for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+        const int m0 = (t % ntm) * UM, r0 = (t / ntm) * UN;
+        for (int it = 0; it < iters; ++it, ++g) {
+          const int s = g % STAGES;
+          const uint32_t ph = (g / STAGES) & 1u;
+          if (!(ok = mbar_wait(empty0 + 8 * s, ph ^ 1u, err))) break;
+          const int pair = it / kchunks, kc = it % kchunks;
+          const uint32_t a = smem_u32(smem + s * STAGE_BYTES), b = a + A_BYTES;
+          mbar_expect_tx(full0 + 8 * s, STAGE_BYTES);
+          tma_load_3d(a, &mapA, kc * UK, m0, kPairA[pair], full0 + 8 * s);
+          tma_load_3d(b, &mapB, kc * UK, r0, kPairB[pair], full0 + 8 * s);
+        }
       }
     }
   } else if (warp == 1) {
     if (lane == 0) {
+      uint32_t g = 0;
+      int lt = 0;
       bool ok = true;
-      for (int it = 0; it < iters && ok; ++it) {
-        const int s = it % STAGES;
-        const uint32_t ph = (uint32_t)(it / STAGES) & 1u;
-        ok = mbar_wait(full0 + 8 * s, ph, err);
-        if (!ok) break;
+      for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x, ++lt) {
+        const int buf = lt & 1;
+        const uint32_t use = (uint32_t)(lt >> 1);
+        // the epilogue must have drained this accumulator (its previous tile)
+        if (!(ok = mbar_wait(acce0 + 8 * buf, (use & 1u) ^ 1u, err))) break;
         tc_fence_after();
-        const uint32_t a = smem_u32(smem + s * STAGE_BYTES), b = a + A_BYTES;
+        const uint32_t acc = tmem + (uint32_t)(buf * UN);
+        for (int it = 0; it < iters; ++it, ++g) {
+          const int s = g % STAGES;
+          const uint32_t ph = (g / STAGES) & 1u;
+          if (!(ok = mbar_wait(full0 + 8 * s, ph, err))) break;
+          tc_fence_after();
+          const uint32_t a = smem_u32(smem + s * STAGE_BYTES), b = a + A_BYTES;
 #pragma unroll
-        for (int kk = 0; kk < UK / 16; ++kk)
-          umma_bf16(tmem, sdesc(a + kk * 32), sdesc(b + kk * 32), (it > 0 || kk > 0) ? 1u : 0u);
-        umma_commit(empty0 + 8 * s);
+          for (int kk = 0; kk < UK / 16; ++kk)
+            umma_bf16(acc, sdesc(a + kk * 32), sdesc(b + kk * 32), (it > 0 || kk > 0) ? 1u : 0u);
+          umma_commit(empty0 + 8 * s);
+        }
+        umma_commit(accf0 + 8 * buf);  // arrives once every MMA of this tile has completed
       }
-      umma_commit(accb);  // arrives once every MMA issued above has completed
     }
   } else {
-    // epilogue warps 2..5 -> TMEM lane quarter (warp % 4)
+    // epilogue warps 2..9 -> TMEM lane quarter (warp % 4), column half (warp - 2) / 4
     const int q = warp & 3;
+    const int c0 = ((warp - 2) / 4) * (UN / 2);
     float* tb = epi + (warp - 2) * 32 * EPI_STRIDE;
-    if (mbar_wait(accb, 0, err)) {
+    int lt = 0;
+    for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++lt) {
+      const int buf = lt & 1;
+      const uint32_t use = (uint32_t)(lt >> 1);
+      if (!mbar_wait(accf0 + 8 * buf, use & 1u, err)) break;
       tc_fence_after();
+      const int m0 = (t % ntm) * UM, r0 = (t / ntm) * UN;
       const int mrow0 = m0 + 32 * q;
-      for (int c = 0; c < UN; c += 32) {
+      for (int c = c0; c < c0 + UN / 2; c += 32) {
         float v[32];
-        tmem_ld32(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)c, v);
+        tmem_ld32(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(buf * UN + c), v);
         // transpose: tb[col][row]
 #pragma unroll
-        for (int t = 0; t < 32; ++t) tb[t * EPI_STRIDE + lane] = v[t];
+        for (int t2 = 0; t2 < 32; ++t2) tb[t2 * EPI_STRIDE + lane] = v[t2];
         __syncwarp();
         const int r = r0 + c + lane;
         if (r < ep.R) {
@@ -244,13 +276,16 @@ __global__ void __launch_bounds__(192, 2)
         }
         __syncwarp();
       }
+      // the accumulator may be overwritten by the tile after next
+      tc_fence_before();
+      mbar_arrive(acce0 + 8 * buf);
     }
   }
   tc_fence_before();
   __syncthreads();
   if (warp == 1) {
     tc_fence_after();
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(UN) : "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS) : "memory");
   }
 }
 
@@ -307,7 +342,14 @@ cudaError_t kv_launch_umma_axis(const CUtensorMap* mapA, const CUtensorMap* mapB
                                 unsigned int* err, cudaStream_t s) {
   cudaError_t e0 = kv_umma_init();
   if (e0 != cudaSuccess) return e0;
-  dim3 grid((ep.R + UN - 1) / UN, (ep.M + UM - 1) / UM);
-  k_umma_axis<<<grid, 192, SMEM_BYTES, s>>>(*mapA, *mapB, K, ep, err);
+  static int sms = 0;
+  if (!sms) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (sms <= 0) sms = 1;
+  }
+  const int tiles = ((ep.R + UN - 1) / UN) * ((ep.M + UM - 1) / UM);
+  k_umma_axis<<<tiles < sms ? tiles : sms, THREADS, SMEM_BYTES, s>>>(*mapA, *mapB, K, ep, err);
   return cudaGetLastError();
 }

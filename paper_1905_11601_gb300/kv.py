@@ -208,14 +208,14 @@ class Grid:
                                                       _dev_ptr(z, self.torch, "z", 4 * self.field_len)))
         return z
 
-    def base_flow_gradient(self, x, y, want_theta=True, want_gr=True):
-        """(d<y, A x>/d Theta as a padded field or None, d<y, A x>/d Gr or None)."""
+    def base_flow_gradient(self, x, y, want_base=True, want_gr=True):
+        """(d<y, A x>/d(U, V, W, Theta) as a packed state or None, d<y, A x>/d Gr or None)."""
         self._sync_stream()
-        gt = self.empty() if want_theta else None
+        gt = self.empty(4) if want_base else None
         dgr = ctypes.c_double()
         self._check(self.lib.kv_base_flow_gradient(self.h, _dev_ptr(x, self.torch, "x", 4 * self.field_len),
                                                    _dev_ptr(y, self.torch, "y", 4 * self.field_len),
-                                                   _dev_ptr(gt, self.torch, "g_theta", self.field_len),
+                                                   _dev_ptr(gt, self.torch, "g_base", 4 * self.field_len),
                                                    ctypes.byref(dgr) if want_gr else None))
         return gt, (dgr.value if want_gr else None)
 

@@ -55,7 +55,10 @@ def test_base_flow_gradient_matches_oracle(n, bc, gr):
     o = Oracle(*n, bc=bc, gr=gr)
     xp, yh = o.project_input(x[0]), project_output_side(o, x[1])
     gb = o.grad_base(xp, yh)
-    assert rel(gt.cpu().numpy(), gb[3]) < RTOL
+    gt = gt.cpu().numpy()
+    assert rel(gt[3], gb[3]) < RTOL
+    for c in range(3):  # the base velocity components
+        assert rel(gt[c], gb[c]) < RTOL, c
     assert abs(dgr - o.grad_gr(xp, yh)) < RTOL * abs(dgr) * 10
 
 
@@ -97,6 +100,17 @@ def test_rayleigh_quotient_gradient_autograd_at_160():
         Rm = torch.vdot(y.flatten(), krylov_map(x, base[3] - h * d, g, vel).flatten()) / yx
     fd = ((Rp - Rm) / (2 * h)).item()
     an = torch.vdot(grad.flatten(), d.flatten()).item()
+    assert abs(fd - an) < 1e-6 * abs(an)
+    # the base-velocity gradient along a random direction (A is affine in U as well)
+    velr = vel.clone().requires_grad_(True)
+    R3 = torch.vdot(y.flatten(), krylov_map(x, base[3], g, velr).flatten()) / yx
+    R3.backward()
+    du = torch.from_numpy(np.random.default_rng(98).standard_normal(tuple(vel.shape))).cuda()
+    with torch.no_grad():
+        Rp = torch.vdot(y.flatten(), krylov_map(x, base[3], g, (vel + h * du).contiguous()).flatten()) / yx
+        Rm = torch.vdot(y.flatten(), krylov_map(x, base[3], g, (vel - h * du).contiguous()).flatten()) / yx
+    fd = ((Rp - Rm) / (2 * h)).item()
+    an = torch.vdot(velr.grad.flatten(), du.flatten()).item()
     assert abs(fd - an) < 1e-6 * abs(an)
     # the x gradient of R is A^T y / <y, x> (through the same function)
     xr = x.clone().requires_grad_(True)

@@ -1,0 +1,42 @@
+"""The pins catch plausible mistakes: each test plants one mistake in a copy of the oracle's C
+source (a wrong index, a swapped weight, a dropped term, a wrong sign), builds it, and runs the
+oracle pins against it in a fresh process; at least one pin must fail. CPU only."""
+import os
+import subprocess
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+SRC = os.path.join(ROOT, "oracle", "kv_oracle.c")
+
+MUTANTS = {
+    "interp_offset": ("for (int dc = -1; dc <= 0; ++dc)", "for (int dc = 0; dc <= 1; ++dc)"),
+    "nonuniform_weights_swapped": ("return (dm * dm * (fp - f0) + dp * dp * (f0 - fm))",
+                                   "return (dp * dp * (fp - f0) + dm * dm * (f0 - fm))"),
+    "buoyancy_neighbour": ("if (F == FW) r += 0.5 * (at(c, xT, i, j, k) + at(c, xT, i, j, k + 1));",
+                           "if (F == FW) r += 0.5 * (at(c, xT, i, j, k) + at(c, xT, i, j, k - 1));"),
+    "eigenvalue_not_squared": ("c->lamp[a][m] = -4.0 / (h * h) * s * s;", "c->lamp[a][m] = -4.0 / (h * h) * s;"),
+    "wall_pair_not_averaged": ("*lo0 = *lo1 = ml;", "*lo0 = ml;"),
+    "advection_sign": ("- advect(c, xv, Th, FT, i, j, k);\n  } else {", "+ advect(c, xv, Th, FT, i, j, k);\n  } else {"),
+    "gradient_direction": ("double g = (phi[cidx(c, u[0], u[1], u[2])] - phi[cidx(c, t[0], t[1], t[2])]) / c->h[F];",
+                           "double g = (phi[cidx(c, t[0], t[1], t[2])] - phi[cidx(c, u[0], u[1], u[2])]) / c->h[F];"),
+    "wall_half_spacing_dropped": ("if (t <= 0) return 0.0;", "if (t <= 0) return -0.5 / n;"),
+}
+
+
+@pytest.mark.parametrize("name", sorted(MUTANTS))
+def test_planted_mistake_fails_a_pin(name, tmp_path):
+    old, new = MUTANTS[name]
+    src = open(SRC).read()
+    assert src.count(old) == 1, f"mutation site for {name} not found exactly once"
+    mutated = tmp_path / "kv_oracle_mut.c"
+    mutated.write_text(src.replace(old, new))
+    lib = tmp_path / "libkv_oracle_mut.so"
+    subprocess.check_call(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-fopenmp", "-D_DEFAULT_SOURCE",
+                           "-o", str(lib), str(mutated), "-lm"])
+    env = dict(os.environ, KV_ORACLE_LIB=str(lib), OMP_NUM_THREADS="2")
+    r = subprocess.run([sys.executable, "-m", "pytest", "-q", "-x", "-p", "no:cacheprovider",
+                        os.path.join(ROOT, "tests", "test_oracle_pins.py")],
+                       cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
+    assert r.returncode != 0, f"no pin caught the mutation {name}:\n{r.stdout[-2000:]}"
