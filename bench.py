@@ -49,7 +49,7 @@ def parse_args():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default="cube256_cc")
     ap.add_argument("--restart", type=int, default=20)
-    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the 16-vector block and the 12-grid plan measurements")
@@ -154,13 +154,17 @@ def source_sha(path):
     return hashlib.sha256(open(path, "rb").read()).hexdigest()[:16]
 
 
-def traffic_for(kernel):
-    """DRAM bytes per launch of a kernel from a committed ncu summary, if its source is unchanged."""
+def traffic_for(kernel, units=None):
+    """DRAM bytes per launch of a kernel from a committed ncu summary (profiles/traffic.json), if
+    the kernel's source is unchanged since the capture. Entries either give bytes per launch of
+    this workload, or bytes per unit measured on a smaller case (scaled by `units`)."""
     try:
         d = json.load(open(os.path.join(ROOT, "profiles", "traffic.json")))[kernel]
         src = os.path.join(ROOT, "paper_1905_11601_gb300", "csrc", d["source"])
         if source_sha(src) != d["source_sha"]:
             return None
+        if "bytes_per_unit" in d:
+            return None if units is None else d["bytes_per_unit"] * units
         return d["bytes_per_launch"]
     except Exception:
         return None
@@ -294,8 +298,11 @@ def roofline(phases, w, precision, steps, nqs=()):
         ach = flops / (phases[dom]["ms"] / 1e3) / 1e12
         name = "k_dots (Gram-Schmidt inner products)" if dom == "gs_dots" else \
             "k_update_dot (Gram-Schmidt update fused with second-pass inner products)"
+        # streams per launch: the first sweep reads nq + 1 vectors; the fused sweep reads nq + 1, writes 1
+        units = L * sum((nq + 1) if dom == "gs_dots" else (nq + 2) for nq in nqs) / len(nqs)
+        traffic = traffic_for("k_dots" if dom == "gs_dots" else "k_update_dot", units)
         return {"kernel": name, "bound": "alu", "achieved": ach, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "frac": ach / FP64_PEAK_TFLOPS, "traffic": None, "peak_source": FP64_PEAK_SRC,
+                "frac": ach / FP64_PEAK_TFLOPS, "traffic": traffic, "peak_source": FP64_PEAK_SRC,
                 "algorithmic": f"2 x (2 nq + 1) flop per vector entry per launch, nq = basis size, "
                                f"mean nq {sum(nqs) / len(nqs):.1f}"}
     byts = {"arnoldi": None, "divergence": 4 * 8.0 * n3, "correct": 11 * 8.0 * n3, "refine": 5 * 8.0 * n3}.get(dom)

@@ -169,9 +169,9 @@ kv_status simple_project(kv_grid* h, double* yvel, double* p, kv_stats* st) {
   return KV_OK;
 }
 
-// Block-shape autotuner for the linearised-operator kernel: times each candidate shape on this
-// grid's coefficients (the base state stands in for x; v* and a scratch vector take the output)
-// and keeps the fastest. Runs once per handle, at the first kv_set_base_flow.
+// Autotuner for the linearised-operator kernels: times each candidate block shape (and, for the
+// double-float kernel of the mixed path, each register budget) on this grid's coefficients (the
+// base state stands in for x; v* and a scratch vector take the output) and keeps the fastest. Runs once per handle, at the first kv_set_base_flow.
 kv_status autotune_apply(kv_grid* h) {
   static const int cand[][2] = {{32, 8}, {64, 4}, {128, 2}, {32, 4}, {16, 16}, {256, 1}};  // <= 256 threads
   if (!h->tmp4) {  // one padded field of scratch for the temperature output
@@ -181,34 +181,56 @@ kv_status autotune_apply(kv_grid* h) {
   cudaEvent_t e0, e1;
   KV_CHECK_CUDA(h, cudaEventCreate(&e0));
   KV_CHECK_CUDA(h, cudaEventCreate(&e1));
-  float best = 1e30f;
+  // times one configuration: warm-up, then three launches; false if it cannot launch here
+  auto time_it = [&](bool df, float& ms) -> bool {
+    auto launch = [&]() {
+      if (df)
+        kv_launch_apply_df(h, h->coef_df, h->base, h->vstar, h->tmp4, h->s);
+      else
+        kv_launch_apply(h, h->coef, h->base, h->vstar, h->tmp4, h->s);
+    };
+    launch();
+    if (cudaGetLastError() != cudaSuccess) return false;
+    cudaEventRecord(e0, h->s);
+    for (int r = 0; r < 3; ++r) launch();
+    cudaEventRecord(e1, h->s);
+    if (cudaEventSynchronize(e1) != cudaSuccess) return false;
+    return cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess;
+  };
+  float best = 1e30f, ms = 0;
   int bx = 32, by = 8;
   for (auto& c : cand) {
     h->apply_bx = c[0];
     h->apply_by = c[1];
-    kv_launch_apply(h, h->coef, h->base, h->vstar, h->tmp4, h->s);  // warm-up
-    if (cudaGetLastError() != cudaSuccess) continue;                // shape not launchable here
-    cudaEventRecord(e0, h->s);
-    for (int r = 0; r < 3; ++r) kv_launch_apply(h, h->coef, h->base, h->vstar, h->tmp4, h->s);
-    cudaEventRecord(e1, h->s);
-    cudaError_t e = cudaEventSynchronize(e1);
-    float ms = 0;
-    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
-    if (e != cudaSuccess) {
-      cudaEventDestroy(e0);
-      cudaEventDestroy(e1);
-      return fail(h, KV_ERR_CUDA, std::string("autotune: ") + cudaGetErrorString(e));
-    }
-    if (ms < best) {
+    if (time_it(false, ms) && ms < best) {
       best = ms;
       bx = c[0];
       by = c[1];
     }
   }
-  cudaEventDestroy(e0);
-  cudaEventDestroy(e1);
   h->apply_bx = bx;
   h->apply_by = by;
+  if (h->d.precision == KV_PREC_MIXED) {
+    best = 1e30f;
+    int dbx = 32, dby = 8, dv = 0;
+    for (int v = 0; v < 2; ++v)
+      for (auto& c : cand) {
+        h->df_variant = v;
+        h->df_bx = c[0];
+        h->df_by = c[1];
+        if (time_it(true, ms) && ms < best) {
+          best = ms;
+          dbx = c[0];
+          dby = c[1];
+          dv = v;
+        }
+      }
+    h->df_bx = dbx;
+    h->df_by = dby;
+    h->df_variant = dv;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
   h->tuned = true;
   return check_launch(h, "autotune");
 }
@@ -281,6 +303,9 @@ kv_status kv_create_grid(const kv_grid_desc* desc, void* stream, kv_handle* out)
   g.ihx = (double)g.nx;
   g.ihy = (double)g.ny;
   g.ihz = (double)g.nz;
+  g.ihx2 = g.ihx * g.ihx;
+  g.ihy2 = g.ihy * g.ihy;
+  g.ihz2 = g.ihz * g.ihz;
   g.nu = 1.0 / sqrt(desc->gr);
   g.kappa = 1.0 / (desc->pr * sqrt(desc->gr));
   g.bc = desc->spanwise_bc;

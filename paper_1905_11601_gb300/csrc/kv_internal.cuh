@@ -24,6 +24,7 @@ struct KvGeom {
   int X, Y, Z;      // padded extents n+2
   double hx, hy, hz;
   double ihx, ihy, ihz;  // 1/h per axis (no FP64 division in the kernels)
+  double ihx2, ihy2, ihz2;  // 1/h^2 per axis
   double nu, kappa; // Gr^-1/2 and (Pr Gr^1/2)^-1 (Eqs (1)-(2) scaling)
   int bc;           // KV_BC_CC / KV_BC_AA
   int tproj;        // KV_TPROJ_*
@@ -89,6 +90,7 @@ struct kv_grid {
 
   // block shape of the linearised-operator kernel, chosen by timing (kv_autotune_apply)
   int apply_bx = 32, apply_by = 8;
+  int df_bx = 32, df_by = 8, df_variant = 0;  // the same for the mixed path's double-float kernel
   bool tuned = false;
 
   std::string err;

@@ -38,9 +38,9 @@ __global__ void __launch_bounds__(256) k_residual_slices(KvGeom g, const double*
       const double xm = i > 0 ? __ldg(phi + e - sx) : c, xp = i < g.nx - 1 ? __ldg(phi + e + sx) : c;
       const double ym = j > 0 ? __ldg(phi + e - sy) : c, yp = j < g.ny - 1 ? __ldg(phi + e + sy) : c;
       const double zm = k > 0 ? __ldg(phi + e - sz) : c, zp = k < g.nz - 1 ? __ldg(phi + e + sz) : c;
-      r = fma(-g.ihx * g.ihx, fma(-2.0, c, xm + xp), r);
-      r = fma(-g.ihy * g.ihy, fma(-2.0, c, ym + yp), r);
-      r = fma(-g.ihz * g.ihz, fma(-2.0, c, zm + zp), r);
+      r = fma(-g.ihx2, fma(-2.0, c, xm + xp), r);
+      r = fma(-g.ihy2, fma(-2.0, c, ym + yp), r);
+      r = fma(-g.ihz2, fma(-2.0, c, zm + zp), r);
     }
     rv = fabs(r);
     const float rf = (float)r;

@@ -107,6 +107,9 @@ extern "C" kv_status kv_krylov_vector_noalloc(const kv_grid_desc* desc, const do
   g.ihx = (double)g.nx;
   g.ihy = (double)g.ny;
   g.ihz = (double)g.nz;
+  g.ihx2 = g.ihx * g.ihx;
+  g.ihy2 = g.ihy * g.ihy;
+  g.ihz2 = g.ihz * g.ihz;
   g.nu = 1.0 / sqrt(desc->gr);
   g.kappa = 1.0 / (desc->pr * sqrt(desc->gr));
   g.bc = desc->spanwise_bc;

@@ -471,13 +471,134 @@ __device__ __forceinline__ float2 cf2(const float2* __restrict__ coef, size_t P,
   return __ldg(coef + (size_t)q * P + e);
 }
 
-// y* = J P_BC x with the FP32-pair coefficients (output as k_apply).
-__global__ void __launch_bounds__(256) k_apply_df(KvGeom g, const float2* __restrict__ coef,
+// The interior case of k_apply_df (see there): unmasked loads, each value split once.
+__device__ __forceinline__ void apply_df_interior(const KvGeom& g, const float2* __restrict__ coef,
                                                   const double* __restrict__ x, size_t P, double* __restrict__ vstar,
-                                                  double* __restrict__ tout) {
+                                                  double* __restrict__ tout, int i, int j, int k) {
+  const int sx = 1, sy = g.X, sz = g.X * g.Y;
+  const int e = i + sy * j + sz * k;
+  const double* __restrict__ xu = x;
+  const double* __restrict__ xv = x + P;
+  const double* __restrict__ xw = x + 2 * P;
+  const double* __restrict__ xT = x + 3 * P;
+  auto L = [&](const double* __restrict__ f, int off) { return split_d(__ldg(f + e + off)); };
+  // u: own 7 + (i-1, j+1) + (i-1, k+1)
+  const DF u0 = L(xu, 0), uxm = L(xu, -sx), uxp = L(xu, sx), uym = L(xu, -sy), uyp = L(xu, sy), uzm = L(xu, -sz),
+           uzp = L(xu, sz), uxmyp = L(xu, -sx + sy), uxmzp = L(xu, -sx + sz);
+  // v: own 7 + (i+1, j-1) + (j-1, k+1)
+  const DF v0 = L(xv, 0), vxm = L(xv, -sx), vxp = L(xv, sx), vym = L(xv, -sy), vyp = L(xv, sy), vzm = L(xv, -sz),
+           vzp = L(xv, sz), vxpym = L(xv, sx - sy), vymzp = L(xv, -sy + sz);
+  // w: own 7 + (i+1, k-1) + (j+1, k-1)
+  const DF w0 = L(xw, 0), wxm = L(xw, -sx), wxp = L(xw, sx), wym = L(xw, -sy), wyp = L(xw, sy), wzm = L(xw, -sz),
+           wzp = L(xw, sz), wxpzm = L(xw, sx - sz), wypzm = L(xw, sy - sz);
+  // T: own 7 (the buoyancy reads T(k) and T(k+1))
+  const DF t0 = L(xT, 0), txm = L(xT, -sx), txp = L(xT, sx), tym = L(xT, -sy), typ = L(xT, sy), tzm = L(xT, -sz),
+           tzp = L(xT, sz);
+  {
+    Acc a;
+    a.add(cf2(coef, P, 0, e), u0);
+    a.add(cf2(coef, P, 1, e), uxm);
+    a.add(cf2(coef, P, 2, e), uxp);
+    a.add(cf2(coef, P, 3, e), uym);
+    a.add(cf2(coef, P, 4, e), uyp);
+    a.add(cf2(coef, P, 5, e), uzm);
+    a.add(cf2(coef, P, 6, e), uzp);
+    const float2 c7 = cf2(coef, P, 7, e), c8 = cf2(coef, P, 8, e);
+    a.add(c7, vym);    // v(i, j-1)
+    a.add(c7, v0);     // v(i, j)
+    a.add(c7, vxpym);  // v(i+1, j-1)
+    a.add(c7, vxp);    // v(i+1, j)
+    a.add(c8, wzm);    // w(i, k-1)
+    a.add(c8, w0);     // w(i, k)
+    a.add(c8, wxpzm);  // w(i+1, k-1)
+    a.add(c8, wxp);    // w(i+1, k)
+    vstar[e] = a.value();
+  }
+  {
+    Acc a;
+    a.add(cf2(coef, P, 9, e), v0);
+    a.add(cf2(coef, P, 10, e), vxm);
+    a.add(cf2(coef, P, 11, e), vxp);
+    a.add(cf2(coef, P, 12, e), vym);
+    a.add(cf2(coef, P, 13, e), vyp);
+    a.add(cf2(coef, P, 14, e), vzm);
+    a.add(cf2(coef, P, 15, e), vzp);
+    const float2 c16 = cf2(coef, P, 16, e), c17 = cf2(coef, P, 17, e);
+    a.add(c16, uxm);    // u(i-1, j)
+    a.add(c16, u0);     // u(i, j)
+    a.add(c16, uxmyp);  // u(i-1, j+1)
+    a.add(c16, uyp);    // u(i, j+1)
+    a.add(c17, wzm);    // w(j, k-1)
+    a.add(c17, w0);     // w(j, k)
+    a.add(c17, wypzm);  // w(j+1, k-1)
+    a.add(c17, wyp);    // w(j+1, k)
+    vstar[P + e] = a.value();
+  }
+  {
+    Acc a;
+    a.add(cf2(coef, P, 18, e), w0);
+    a.add(cf2(coef, P, 19, e), wxm);
+    a.add(cf2(coef, P, 20, e), wxp);
+    a.add(cf2(coef, P, 21, e), wym);
+    a.add(cf2(coef, P, 22, e), wyp);
+    a.add(cf2(coef, P, 23, e), wzm);
+    a.add(cf2(coef, P, 24, e), wzp);
+    const float2 c25 = cf2(coef, P, 25, e), c26 = cf2(coef, P, 26, e);
+    a.add(c25, uxm);    // u(i-1, k)
+    a.add(c25, u0);     // u(i, k)
+    a.add(c25, uxmzp);  // u(i-1, k+1)
+    a.add(c25, uzp);    // u(i, k+1)
+    a.add(c26, vym);    // v(j-1, k)
+    a.add(c26, v0);     // v(j, k)
+    a.add(c26, vymzp);  // v(j-1, k+1)
+    a.add(c26, vzp);    // v(j, k+1)
+    const float2 half = make_float2(0.5f, 0.0f);
+    a.add(half, t0);
+    a.add(half, tzp);
+    vstar[2 * P + e] = a.value();
+  }
+  {
+    Acc a;
+    a.add(cf2(coef, P, 27, e), t0);
+    a.add(cf2(coef, P, 28, e), txm);
+    a.add(cf2(coef, P, 29, e), txp);
+    a.add(cf2(coef, P, 30, e), tym);
+    a.add(cf2(coef, P, 31, e), typ);
+    a.add(cf2(coef, P, 32, e), tzm);
+    a.add(cf2(coef, P, 33, e), tzp);
+    const float2 c34 = cf2(coef, P, 34, e), c35 = cf2(coef, P, 35, e), c36 = cf2(coef, P, 36, e);
+    a.add(c34, uxm);
+    a.add(c34, u0);
+    a.add(c35, vym);
+    a.add(c35, v0);
+    a.add(c36, wzm);
+    a.add(c36, w0);
+    tout[e] = a.value();
+  }
+}
+
+// y* = J P_BC x with the FP32-pair coefficients (output as k_apply). MINB: the launch bound's
+// minimum resident blocks, which sets the register budget (more registers, more independent
+// loads in flight; fewer, more resident warps); the autotuner picks the faster.
+template <int MINB>
+__global__ void __launch_bounds__(256, MINB) k_apply_df(KvGeom g, const float2* __restrict__ coef,
+                                                        const double* __restrict__ x, size_t P,
+                                                        double* __restrict__ vstar, double* __restrict__ tout) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   const int j = blockIdx.y * blockDim.y + threadIdx.y;
   const int k = blockIdx.z;
+  // Blocks three or more cells away from every wall: every output is an interior unknown and
+  // every input it reads is one too (and no temperature it reads belongs to an insulated wall
+  // pair), so the loads need no masking; each distinct input value (34 per cell) is loaded and
+  // split once.
+  {
+    const int i0 = blockIdx.x * blockDim.x, j0 = blockIdx.y * blockDim.y;
+    if (i0 >= 3 && i0 + (int)blockDim.x - 1 <= g.nx - 3 && j0 >= 3 && j0 + (int)blockDim.y - 1 <= g.ny - 3 &&
+        k >= 3 && k <= g.nz - 3) {
+      apply_df_interior(g, coef, x, P, vstar, tout, i, j, k);
+      return;
+    }
+  }
   if (i >= g.X || j >= g.Y || k >= g.Z) return;
   Grid G{g};
   const int e = G.at(i, j, k);
@@ -624,7 +745,10 @@ void kv_launch_coef_df(const kv_grid* h, const double* coef, float2* cdf, cudaSt
 void kv_launch_apply_df(const kv_grid* h, const float2* cdf, const double* x, double* vstar, double* tout,
                         cudaStream_t s) {
   const KvGeom& g = h->g;
-  const int bx = h->apply_bx, by = h->apply_by;
+  const int bx = h->df_bx, by = h->df_by;
   dim3 block(bx, by, 1), grid((g.X + bx - 1) / bx, (g.Y + by - 1) / by, g.Z);
-  k_apply_df<<<grid, block, 0, s>>>(g, cdf, x, h->P, vstar, tout);
+  if (h->df_variant == 0)
+    k_apply_df<4><<<grid, block, 0, s>>>(g, cdf, x, h->P, vstar, tout);
+  else
+    k_apply_df<1><<<grid, block, 0, s>>>(g, cdf, x, h->P, vstar, tout);
 }

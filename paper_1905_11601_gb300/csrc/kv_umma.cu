@@ -13,7 +13,7 @@
 //   warp 1      allocates 512 TMEM columns (two 128 x 256 FP32 accumulators); lane 0 issues
 //               tcgen05.mma (M=128, N=256, K=16), tcgen05.commit to each stage's empty[] barrier
 //               and, after a tile's last MMA, to that accumulator's full barrier;
-//   warps 2-9   epilogue (two warps per TMEM lane quarter): tcgen05.ld of the accumulator, transposed through shared memory so
+//   warps 2-17  epilogue (four warps per TMEM lane quarter): tcgen05.ld of the accumulator, transposed through shared memory so
 //               that stores run along r, then either the next pass's three BF16 slices (with
 //               the 1 / Lambda scaling of Eq (17) in the third forward pass) or phi += D (FP64);
 //               then they release the accumulator, so the epilogue of one tile overlaps the
@@ -32,7 +32,8 @@ constexpr int STAGES = 3;
 constexpr int A_BYTES = UM * UK * 2;        // 16 KB
 constexpr int B_BYTES = UN * UK * 2;        // 32 KB
 constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
-constexpr int EPI_WARPS = 8;  // two per TMEM lane quarter, each taking half of the columns
+constexpr int EPI_WARPS = 16;  // four per TMEM lane quarter, each taking a quarter of the columns
+constexpr int EPI_COLS = UN / (EPI_WARPS / 4);
 constexpr int THREADS = 64 + 32 * EPI_WARPS;
 constexpr int EPI_STRIDE = 33;              // floats per transposed row (bank-conflict free)
 constexpr int EPI_BYTES = EPI_WARPS * 32 * EPI_STRIDE * 4;
@@ -228,9 +229,9 @@ __global__ void __launch_bounds__(THREADS, 1)
       }
     }
   } else {
-    // epilogue warps 2..9 -> TMEM lane quarter (warp % 4), column half (warp - 2) / 4
+    // epilogue warps 2..17 -> TMEM lane quarter (warp % 4), column block (warp - 2) / 4
     const int q = warp & 3;
-    const int c0 = ((warp - 2) / 4) * (UN / 2);
+    const int c0 = ((warp - 2) / 4) * EPI_COLS;
     float* tb = epi + (warp - 2) * 32 * EPI_STRIDE;
     int lt = 0;
     for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++lt) {
@@ -240,7 +241,7 @@ __global__ void __launch_bounds__(THREADS, 1)
       tc_fence_after();
       const int m0 = (t % ntm) * UM, r0 = (t / ntm) * UN;
       const int mrow0 = m0 + 32 * q;
-      for (int c = c0; c < c0 + UN / 2; c += 32) {
+      for (int c = c0; c < c0 + EPI_COLS; c += 32) {
         float v[32];
         tmem_ld32(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(buf * UN + c), v);
         // transpose: tb[col][row]
