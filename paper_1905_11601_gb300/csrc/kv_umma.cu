@@ -233,6 +233,9 @@ __global__ void __launch_bounds__(THREADS, 1)
     const int q = warp & 3;
     const int c0 = ((warp - 2) / 4) * EPI_COLS;
     float* tb = epi + (warp - 2) * 32 * EPI_STRIDE;
+    // groups of 4 outputs are contiguous and 8-byte aligned (slices) or 32-byte aligned (phi)
+    // when the inner extent and R are multiples of 4 (and the slice pitch and size are)
+    const bool vec4 = (ep.R % 4 == 0) && (ep.mode == 2 || (ep.nb % 4 == 0 && ep.pitch % 4 == 0 && ep.slice % 4 == 0));
     int lt = 0;
     for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++lt) {
       const int buf = lt & 1;
@@ -248,30 +251,76 @@ __global__ void __launch_bounds__(THREADS, 1)
 #pragma unroll
         for (int t2 = 0; t2 < 32; ++t2) tb[t2 * EPI_STRIDE + lane] = v[t2];
         __syncwarp();
-        const int r = r0 + c + lane;
-        if (r < ep.R) {
-          int a = 0, bcol = r;
-          if (ep.mode != 2) {
-            a = r / ep.nb;
-            bcol = r - a * ep.nb;
-          }
-          for (int row = 0; row < 32; ++row) {
-            const int m = mrow0 + row;
-            if (m >= ep.M) break;
-            float d = tb[lane * EPI_STRIDE + row];
-            if (ep.mode == 2) {
-              ep.phi[(size_t)m * ep.R + r] += (double)d;
-            } else {
-              if (ep.mode == 1) {
-                const float lam = ep.lz[m] + ep.la[a] + ep.lb[bcol];
-                d = (m == 0 && r == 0) ? 0.0f : __fdividef(d, lam);
+        if (vec4) {
+          // lane: 4 consecutive columns (4 (lane % 8) ..) of rows 4 it + lane / 8; 8-byte stores
+          const int cc = 4 * (lane & 7);
+          const int r = r0 + c + cc;
+          if (r < ep.R) {  // R is a multiple of 4 here, so r < R covers all four columns
+            int a = 0, bcol = r;
+            if (ep.mode != 2) {
+              a = r / ep.nb;
+              bcol = r - a * ep.nb;
+            }
+            for (int it = 0; it < 8; ++it) {
+              const int row = 4 * it + (lane >> 3);
+              const int m = mrow0 + row;
+              if (m >= ep.M) break;
+              float d[4];
+#pragma unroll
+              for (int t2 = 0; t2 < 4; ++t2) d[t2] = tb[(cc + t2) * EPI_STRIDE + row];
+              if (ep.mode == 2) {
+                double2* p = reinterpret_cast<double2*>(ep.phi + (size_t)m * ep.R + r);
+                double2 p0 = p[0], p1 = p[1];
+                p0.x += (double)d[0];
+                p0.y += (double)d[1];
+                p1.x += (double)d[2];
+                p1.y += (double)d[3];
+                p[0] = p0;
+                p[1] = p1;
+              } else {
+                if (ep.mode == 1) {
+#pragma unroll
+                  for (int t2 = 0; t2 < 4; ++t2) {
+                    const float lam = ep.lz[m] + ep.la[a] + ep.lb[bcol + t2];
+                    d[t2] = (m == 0 && r + t2 == 0) ? 0.0f : __fdividef(d[t2], lam);
+                  }
+                }
+                __nv_bfloat16 s[3][4];
+#pragma unroll
+                for (int t2 = 0; t2 < 4; ++t2) split3(d[t2], s[0][t2], s[1][t2], s[2][t2]);
+                const size_t o = ((size_t)m * ep.na + a) * ep.pitch + bcol;
+#pragma unroll
+                for (int sl = 0; sl < 3; ++sl)
+                  *reinterpret_cast<uint2*>(ep.out + (size_t)sl * ep.slice + o) = *reinterpret_cast<const uint2*>(s[sl]);
               }
-              __nv_bfloat16 s1, s2, s3;
-              split3(d, s1, s2, s3);
-              const size_t o = ((size_t)m * ep.na + a) * ep.pitch + bcol;
-              ep.out[o] = s1;
-              ep.out[ep.slice + o] = s2;
-              ep.out[2 * ep.slice + o] = s3;
+            }
+          }
+        } else {
+          const int r = r0 + c + lane;
+          if (r < ep.R) {
+            int a = 0, bcol = r;
+            if (ep.mode != 2) {
+              a = r / ep.nb;
+              bcol = r - a * ep.nb;
+            }
+            for (int row = 0; row < 32; ++row) {
+              const int m = mrow0 + row;
+              if (m >= ep.M) break;
+              float d = tb[lane * EPI_STRIDE + row];
+              if (ep.mode == 2) {
+                ep.phi[(size_t)m * ep.R + r] += (double)d;
+              } else {
+                if (ep.mode == 1) {
+                  const float lam = ep.lz[m] + ep.la[a] + ep.lb[bcol];
+                  d = (m == 0 && r == 0) ? 0.0f : __fdividef(d, lam);
+                }
+                __nv_bfloat16 s1, s2, s3;
+                split3(d, s1, s2, s3);
+                const size_t o = ((size_t)m * ep.na + a) * ep.pitch + bcol;
+                ep.out[o] = s1;
+                ep.out[ep.slice + o] = s2;
+                ep.out[2 * ep.slice + o] = s3;
+              }
             }
           }
         }
