@@ -208,6 +208,14 @@ kv_status kv_profile_get(kv_handle h, int phase, double* total_ms, long long* ti
 kv_status kv_krylov_vector_noalloc(const kv_grid_desc* desc, const double* base, const double* x, double* y,
                                    void* stream);
 
+/* Failure-detection self-test (not part of the method): runs one tensor-core contraction of a
+   KV_PREC_MIXED grid whose completion barriers expect more bytes than its copies deliver, so
+   every bounded wait in the kernel expires (after a few hundred tries) and the kernel returns
+   with its device error flag set instead of hanging; *device_error receives the flag (nonzero
+   means the expiry was detected) and the flag is cleared. No fault, trap or unbounded wait is
+   involved; the grid stays usable. Synchronises the stream. */
+kv_status kv_selftest_wait_timeout(kv_handle h, int* device_error);
+
 /* Message of the last failed call on h (NULL h: last failed kv_create_grid or
    kv_krylov_vector_noalloc on this thread). */
 const char* kv_last_error(kv_handle h);

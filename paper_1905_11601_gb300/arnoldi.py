@@ -42,3 +42,18 @@ def ritz_vector(V, y):
     yr = torch.from_numpy(np.ascontiguousarray(y.real)).to(Vk)
     yi = torch.from_numpy(np.ascontiguousarray(y.imag)).to(Vk)
     return (yr @ Vk).reshape(V.shape[1:]), (yi @ Vk).reshape(V.shape[1:])
+
+
+def save_state(path, V, H, j):
+    """Checkpoint of an Arnoldi run: the basis V (moved to host memory), H and the step count."""
+    import torch
+
+    torch.save({"V": V.detach().cpu(), "H": np.asarray(H), "j": int(j)}, path)
+
+
+def load_state(path, device="cuda"):
+    """Restores (V, H, j) saved by save_state; V is placed on `device`."""
+    import torch
+
+    d = torch.load(path, weights_only=False)
+    return d["V"].to(device), np.asarray(d["H"]), int(d["j"])

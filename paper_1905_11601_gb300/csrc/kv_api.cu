@@ -8,11 +8,17 @@
 #include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "kv_internal.cuh"
 
 namespace {
 
 thread_local std::string g_create_error;
+
+const char* const kPhaseName[KV_NPHASE] = {"kv:operator", "kv:divergence", "kv:tpf-contraction", "kv:correct",
+                                           "kv:arnoldi-normalise", "kv:refine-residual", "kv:gs-dots",
+                                           "kv:gs-update"};
 
 #define KV_CHECK_CUDA(h, call)                                                              \
   do {                                                                                      \
@@ -240,6 +246,7 @@ kv_status autotune_apply(kv_grid* h) {
 void kv_set_thread_error(const std::string& msg) { g_create_error = msg; }
 
 KvPhase::KvPhase(kv_grid* h_, int phase_, int launches) : h(h_), phase(phase_), n(launches) {
+  nvtxRangePushA(kPhaseName[phase]);  // a no-op unless a profiler is attached
   if (!h->prof_on) return;
   if (h->ev_pool.empty()) {
     if (cudaEventCreate(&a) != cudaSuccess) a = nullptr;
@@ -251,6 +258,7 @@ KvPhase::KvPhase(kv_grid* h_, int phase_, int launches) : h(h_), phase(phase_), 
 }
 
 KvPhase::~KvPhase() {
+  nvtxRangePop();
   h->launches[phase] += n;
   if (!a) return;
   cudaEvent_t b = nullptr;
@@ -666,6 +674,12 @@ kv_status kv_profile_get(kv_handle h, int phase, double* total_ms, long long* ti
   if (timed_launches) *timed_launches = h->prof_n[phase];
   if (launches) *launches = h->launches[phase];
   return KV_OK;
+}
+
+kv_status kv_selftest_wait_timeout(kv_handle h, int* device_error) {
+  if (!h || !device_error) return KV_ERR_ARG;
+  if (h->d.precision != KV_PREC_MIXED) return fail(h, KV_ERR_ARG, "kv_selftest_wait_timeout: needs a mixed grid");
+  return kv_mixed_selftest_timeout(h, device_error);
 }
 
 const char* kv_last_error(kv_handle h) {

@@ -118,6 +118,8 @@ struct KvUmmaEpi {
   const float* lz;   // mode 1: eigenvalues of the contracted (m) axis, then of a and b
   const float* la;
   const float* lb;
+  unsigned int wait_limit;  // iterations of each bounded mbarrier wait (0: the default)
+  unsigned int extra_tx;    // self-test only: bytes expected beyond what TMA delivers (0 normally)
 };
 cudaError_t kv_umma_init();
 bool kv_make_slice_map(CUtensorMap* map, const void* base, int cols, int rows, int pitch, size_t slice_elems,
@@ -132,6 +134,7 @@ kv_status kv_mixed_setup(kv_grid* h, const double* const fwd[3], const double* c
 void kv_mixed_free(kv_grid* h);
 // phi = L^+ b to FP64 accuracy: BF16-split tensor-core TPF solve + FP64 residual refinement
 void kv_launch_poisson_mixed(kv_grid* h, const double* b, double* phi, cudaStream_t s);
+kv_status kv_mixed_selftest_timeout(kv_grid* h, int* device_error);
 
 // kv_api.cu: sets the thread's message returned by kv_last_error(NULL)
 void kv_set_thread_error(const std::string& msg);

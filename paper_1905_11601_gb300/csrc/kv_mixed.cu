@@ -176,3 +176,34 @@ void kv_launch_poisson_mixed(kv_grid* h, const double* b, double* phi, cudaStrea
     }
   }
 }
+
+// Failure-detection self-test (no GPU fault): one contraction whose barriers expect 16 bytes
+// more than the copies deliver, so the bounded waits expire after a few hundred tries; the
+// kernel sets the device error flag and returns. Reads and clears the flag.
+kv_status kv_mixed_selftest_timeout(kv_grid* h, int* device_error) {
+  const int n[3] = {h->g.nx, h->g.ny, h->g.nz};
+  const PassSpec& ps = kPass[0];
+  KvUmmaEpi ep{};
+  ep.M = n[ps.axis];
+  ep.R = (int)(h->Nc / n[ps.axis]);
+  ep.na = n[ps.a];
+  ep.nb = n[ps.b];
+  ep.pitch = pad8(n[ps.b]);
+  ep.slice = h->xs_slice;
+  ep.out = h->xs[1];
+  ep.mode = 0;
+  ep.wait_limit = 256;
+  ep.extra_tx = 16;
+  cudaError_t e = cudaMemsetAsync(h->derr, 0, sizeof(unsigned int), h->s);
+  if (e == cudaSuccess) e = kv_launch_umma_axis(&h->mapA[0], &h->mapB[0], n[ps.axis], ep, h->derr, h->s);
+  unsigned int de = 0;
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&de, h->derr, sizeof de, cudaMemcpyDeviceToHost, h->s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(h->derr, 0, sizeof(unsigned int), h->s);
+  if (e != cudaSuccess) {
+    h->err = std::string("self-test: ") + cudaGetErrorString(e);
+    return KV_ERR_CUDA;
+  }
+  *device_error = (int)de;
+  return KV_OK;
+}

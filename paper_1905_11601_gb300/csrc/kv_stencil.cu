@@ -748,7 +748,7 @@ void kv_launch_apply_df(const kv_grid* h, const float2* cdf, const double* x, do
   const int bx = h->df_bx, by = h->df_by;
   dim3 block(bx, by, 1), grid((g.X + bx - 1) / bx, (g.Y + by - 1) / by, g.Z);
   if (h->df_variant == 0)
-    k_apply_df<4><<<grid, block, 0, s>>>(g, cdf, x, h->P, vstar, tout);
+    k_apply_df<3><<<grid, block, 0, s>>>(g, cdf, x, h->P, vstar, tout);
   else
     k_apply_df<1><<<grid, block, 0, s>>>(g, cdf, x, h->P, vstar, tout);
 }

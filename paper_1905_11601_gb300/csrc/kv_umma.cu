@@ -54,8 +54,9 @@ __device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
   asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
 }
 // Bounded wait for the phase with the given parity; false (and the error flag set) on expiry.
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, unsigned int* err) {
-  for (uint32_t it = 0; it < WAIT_LIMIT; ++it) {
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, unsigned int* err,
+                                          uint32_t limit = WAIT_LIMIT) {
+  for (uint32_t it = 0; it < limit; ++it) {
     uint32_t ok;
     asm volatile(
         "{\n\t.reg .pred p;\n\t"
@@ -157,6 +158,7 @@ __global__ void __launch_bounds__(THREADS, 1)
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int ntm = (ep.M + UM - 1) / UM, ntr = (ep.R + UN - 1) / UN, ntiles = ntm * ntr;
+  const uint32_t lim = ep.wait_limit ? ep.wait_limit : WAIT_LIMIT;
   const int kchunks = (K + UK - 1) / UK;
   const int iters = NPAIRS * kchunks;
 
@@ -193,10 +195,10 @@ __global__ void __launch_bounds__(THREADS, 1)
         for (int it = 0; it < iters; ++it, ++g) {
           const int s = g % STAGES;
           const uint32_t ph = (g / STAGES) & 1u;
-          if (!(ok = mbar_wait(empty0 + 8 * s, ph ^ 1u, err))) break;
+          if (!(ok = mbar_wait(empty0 + 8 * s, ph ^ 1u, err, lim))) break;
           const int pair = it / kchunks, kc = it % kchunks;
           const uint32_t a = smem_u32(smem + s * STAGE_BYTES), b = a + A_BYTES;
-          mbar_expect_tx(full0 + 8 * s, STAGE_BYTES);
+          mbar_expect_tx(full0 + 8 * s, STAGE_BYTES + ep.extra_tx);
           tma_load_3d(a, &mapA, kc * UK, m0, kPairA[pair], full0 + 8 * s);
           tma_load_3d(b, &mapB, kc * UK, r0, kPairB[pair], full0 + 8 * s);
         }
@@ -211,13 +213,13 @@ __global__ void __launch_bounds__(THREADS, 1)
         const int buf = lt & 1;
         const uint32_t use = (uint32_t)(lt >> 1);
         // the epilogue must have drained this accumulator (its previous tile)
-        if (!(ok = mbar_wait(acce0 + 8 * buf, (use & 1u) ^ 1u, err))) break;
+        if (!(ok = mbar_wait(acce0 + 8 * buf, (use & 1u) ^ 1u, err, lim))) break;
         tc_fence_after();
         const uint32_t acc = tmem + (uint32_t)(buf * UN);
         for (int it = 0; it < iters; ++it, ++g) {
           const int s = g % STAGES;
           const uint32_t ph = (g / STAGES) & 1u;
-          if (!(ok = mbar_wait(full0 + 8 * s, ph, err))) break;
+          if (!(ok = mbar_wait(full0 + 8 * s, ph, err, lim))) break;
           tc_fence_after();
           const uint32_t a = smem_u32(smem + s * STAGE_BYTES), b = a + A_BYTES;
 #pragma unroll
@@ -240,7 +242,7 @@ __global__ void __launch_bounds__(THREADS, 1)
     for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++lt) {
       const int buf = lt & 1;
       const uint32_t use = (uint32_t)(lt >> 1);
-      if (!mbar_wait(accf0 + 8 * buf, use & 1u, err)) break;
+      if (!mbar_wait(accf0 + 8 * buf, use & 1u, err, lim)) break;
       tc_fence_after();
       const int m0 = (t % ntm) * UM, r0 = (t / ntm) * UN;
       const int mrow0 = m0 + 32 * q;

@@ -26,7 +26,7 @@ EXPORTS = ("kv_create_grid", "kv_destroy_grid", "kv_set_stream", "kv_field_len",
            "kv_krylov_vector", "kv_krylov_vector_host", "kv_arnoldi_step", "kv_newton_residual", "kv_last_error",
            "kv_profile_enable", "kv_profile_get", "kv_krylov_vector_noalloc", "kv_krylov_vector_adjoint",
            "kv_base_flow_gradient", "kv_krylov_vector_batch", "kv_plan_create", "kv_plan_add", "kv_plan_launch",
-           "kv_plan_destroy", "kv_plan_last_error")
+           "kv_plan_destroy", "kv_plan_last_error", "kv_selftest_wait_timeout")
 PHASES = {"stencil": 0, "divergence": 1, "tpd": 2, "correct": 3, "arnoldi": 4, "refine": 5, "gs_dots": 6,
           "gs_update": 7}
 
@@ -83,6 +83,7 @@ def load_library(path: str = LIB_PATH):
     lib.kv_plan_destroy.argtypes = [ctypes.c_void_p]
     lib.kv_plan_last_error.argtypes = [ctypes.c_void_p]
     lib.kv_plan_last_error.restype = ctypes.c_char_p
+    lib.kv_selftest_wait_timeout.argtypes = [H, ctypes.POINTER(ctypes.c_int)]
     lib.kv_krylov_vector_noalloc.argtypes = [ctypes.POINTER(GridDesc), D, D, D, ctypes.c_void_p]
     lib.kv_last_error.argtypes = [H]
     lib.kv_last_error.restype = ctypes.c_char_p
@@ -218,6 +219,13 @@ class Grid:
                                                    _dev_ptr(gt, self.torch, "g_base", 4 * self.field_len),
                                                    ctypes.byref(dgr) if want_gr else None))
         return gt, (dgr.value if want_gr else None)
+
+    def selftest_wait_timeout(self):
+        """Runs the bounded-wait expiry self-test; returns the device error flag it produced."""
+        self._sync_stream()
+        de = ctypes.c_int()
+        self._check(self.lib.kv_selftest_wait_timeout(self.h, ctypes.byref(de)))
+        return de.value
 
     def profile_enable(self, on=True):
         self._sync_stream()

@@ -62,3 +62,23 @@ def test_plan_over_mixed_grids():
         for y, (g, x) in zip(ys, refs):
             assert torch.equal(y, g.krylov_vector(x))
     plan.close()
+
+
+def test_bounded_wait_expiry_is_reported_and_grid_stays_usable():
+    """Failure detection without a GPU fault: a contraction whose barriers never complete gives
+    up after its bounded waits and reports through the device error flag; afterwards the same
+    grid still computes correct Krylov vectors."""
+    from paper_1905_11601_gb300 import kv
+    n = (24, 20, 18)
+    base = torch.from_numpy(np.stack(synth.base_flow(*n, synth.CC, 131))).cuda()
+    x = torch.from_numpy(synth.krylov_input(*n, 132)[0]).cuda()
+    g64 = kv.Grid(*n, gr=2e6)
+    g64.set_base_flow(base)
+    ref = g64.krylov_vector(x)
+    g = kv.Grid(*n, gr=2e6, precision=kv.KV_PREC_MIXED)
+    g.set_base_flow(base)
+    assert g.selftest_wait_timeout() != 0
+    y, st = g.krylov_vector(x, stats=True)
+    assert st.device_error == 0
+    err = (torch.linalg.vector_norm(y - ref) / torch.linalg.vector_norm(ref)).item()
+    assert err < 1e-9
