@@ -152,7 +152,10 @@ const char* kv_plan_last_error(kv_plan_handle p);
    the DGKS test or always, desc.cgs_passes; always two passes beyond 24 basis vectors),
    stores w / ||w|| in V_{j+1} and writes the Hessenberg column H[0..j+1, j] to the HOST
    array h_col (j+2 doubles). Synchronises the stream. Inner products run over all stored
-   entries of the four fields. */
+   entries of the four fields. With KV_PREC_MIXED and up to 24 basis vectors, the first two
+   Gram-Schmidt sweeps run in double-float arithmetic on the FP32 pipe (relative rounding
+   ~2^-46 instead of 2^-53); entries below 2^-103 in magnitude are then treated as 0, and a new
+   vector with an entry of magnitude >= 2^48, NaN or Inf gives KV_ERR_ARG (V_{j+1} undefined). */
 kv_status kv_arnoldi_step(kv_handle h, double* V, int j, double* h_col);
 
 /* Transpose of the Krylov map: z = A^T y with A = (Pi_v (+) P_T) J P_BC (the adjoint eigenvalue

@@ -4,6 +4,7 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <cmath>
 #include <new>
 #include <string>
 #include <vector>
@@ -82,6 +83,7 @@ void free_all(kv_grid* h) {
   cudaFree(h->base);
   cudaFree(h->coef);
   cudaFree(h->coef_df);
+  cudaFree(h->xsplit);
   cudaFree(h->vstar);
   cudaFree(h->tpd_a);
   cudaFree(h->tpd_b);
@@ -134,7 +136,7 @@ kv_status simple_project(kv_grid* h, double* yvel, double* p, kv_stats* st) {
     KV_CHECK_CUDA(h, cudaMemsetAsync(h->red, 0, 2 * sizeof(unsigned long long), s));
     { KvPhase ph(h, KV_PH_DIV, 1); kv_launch_divergence(h, src, h->tpd_a, s); }
     if (mixed)
-      kv_launch_poisson_mixed(h, h->tpd_a, phi, s);
+      kv_launch_poisson_mixed(h, h->tpd_a, phi, st != nullptr, s);
     else
       kv_launch_poisson(h, h->tpd_a, h->tpd_a, s);
     { KvPhase ph(h, KV_PH_CORRECT, 1); kv_launch_correct(h, src, phi, yvel, p, pass > 1, s, want ? 1 : 0); }
@@ -404,6 +406,10 @@ kv_status kv_set_base_flow(kv_handle h, const double* base) {
       kv_status s = dalloc(h, &h->coef_df, (size_t)KV_NCOEF * h->P);
       if (s != KV_OK) return s;
     }
+    if (!h->xsplit) {
+      kv_status s = dalloc(h, &h->xsplit, 4 * h->P);
+      if (s != KV_OK) return s;
+    }
     kv_launch_coef_df(h, h->coef, h->coef_df, h->s);
   }
   kv_status ks = check_launch(h, "assemble");
@@ -421,7 +427,7 @@ kv_status kv_krylov_vector(kv_handle h, const double* x, double* y, double* p, k
   if ((x < y + L && y < x + L)) return fail(h, KV_ERR_ARG, "kv_krylov_vector: x and y overlap");
   // J P_BC x: momentum right-hand side to vstar, projected temperature straight into y
   {
-    KvPhase ph(h, KV_PH_STENCIL, 1);
+    KvPhase ph(h, KV_PH_STENCIL, h->d.precision == KV_PREC_MIXED ? 2 : 1);  // split + operator
     if (h->d.precision == KV_PREC_MIXED)
       kv_launch_apply_df(h, h->coef_df, x, h->vstar, y + 3 * h->P, h->s);
     else
@@ -479,22 +485,28 @@ kv_status kv_arnoldi_step(kv_handle h, double* V, int j, double* h_col) {
   double* nrm = h->hdev + 2 * nq + 2; // ||w||^2 after the second update
   std::vector<double> hh(2 * (size_t)nq + 3, 0.0);
   if (nq <= kv_fused_cgs_max()) {
+    // mixed precision: sweeps 1 and 2 in double-float on the FP32 pipe
+    const int df = h->d.precision == KV_PREC_MIXED;
     // Classical Gram-Schmidt. Sweep 1: h1 = V^T w and ||w||^2. Sweep 2: w -= V h1 fused with the
     // second pass's h2 = V^T w and ||w||^2. The DGKS test (as in ARPACK's Arnoldi) then decides
     // whether sweep 3 (w -= V h2) is needed: only when sweep 2 removed more than half of ||w||^2.
     {
       KvPhase ph(h, KV_PH_GS_DOTS, 2);
-      kv_launch_dots_norm(V, L, nq, w, L, h->partials, h1, h1 + nq, h->s);
+      kv_launch_dots_norm(V, L, nq, w, L, h->partials, h1, h1 + nq, df, h->s);
     }
     {
       KvPhase ph(h, KV_PH_GS_UPDATE, 2);
-      kv_launch_update_dot(V, L, nq, h1, w, L, h->partials, h2, h->s);
+      kv_launch_update_dot(V, L, nq, h1, w, L, h->partials, h2, df, h->s);
     }
     s = check_launch(h, "arnoldi");
     if (s != KV_OK) return s;
     KV_CHECK_CUDA(h, cudaMemcpyAsync(hh.data(), h->hdev, hh.size() * sizeof(double), cudaMemcpyDeviceToHost, h->s));
     KV_CHECK_CUDA(h, cudaStreamSynchronize(h->s));
     const double before = hh[nq], after = hh[2 * nq + 1];
+    if (df && std::isnan(before))
+      return fail(h, KV_ERR_ARG,
+                  "kv_arnoldi_step: the new vector has entries outside the mixed-precision Gram-Schmidt range "
+                  "(NaN, Inf or |x| >= 2^48); V[j+1] is undefined");
     const bool reorth = h->d.cgs_passes == 2 || !(after > 0.5 * before);
     {
       KvPhase ph(h, KV_PH_ARNOLDI, 1);

@@ -42,6 +42,7 @@ struct kv_grid {
   double* base = nullptr;   // 4P: U | V | W | Theta
   double* coef = nullptr;   // KV_NCOEF * P: assembled coefficients of J (per base flow)
   float2* coef_df = nullptr; // KV_PREC_MIXED: the same coefficients as FP32 pairs
+  float2* xsplit = nullptr;  // KV_PREC_MIXED, 4P: P_BC x split into FP32 pairs (operator input)
   double* vstar = nullptr;  // 3P: momentum right-hand side before the projection
   double* tpd_a = nullptr;  // Nc: divergence / Poisson ping-pong buffers
   double* tpd_b = nullptr;  // Nc
@@ -132,8 +133,9 @@ cudaError_t kv_launch_umma_axis(const CUtensorMap* mapA, const CUtensorMap* mapB
 // kv_mixed.cu
 kv_status kv_mixed_setup(kv_grid* h, const double* const fwd[3], const double* const inv[3]);
 void kv_mixed_free(kv_grid* h);
-// phi = L^+ b to FP64 accuracy: BF16-split tensor-core TPF solve + FP64 residual refinement
-void kv_launch_poisson_mixed(kv_grid* h, const double* b, double* phi, cudaStream_t s);
+// phi = L^+ b to FP64-class accuracy: BF16-split tensor-core TPF solve + double-float residual
+// refinement (stats: also reduce max |r| into h->rmax)
+void kv_launch_poisson_mixed(kv_grid* h, const double* b, double* phi, int stats, cudaStream_t s);
 kv_status kv_mixed_selftest_timeout(kv_grid* h, int* device_error);
 
 // kv_api.cu: sets the thread's message returned by kv_last_error(NULL)
@@ -158,6 +160,7 @@ void kv_launch_assemble(const kv_grid* h, const double* base, double* coef, cuda
 void kv_launch_apply(const kv_grid* h, const double* coef, const double* x, double* vstar, double* tout,
                      cudaStream_t s);
 // mixed precision: FP32-pair copy of the coefficients, and J P_BC x in double-float on the FP32 pipe
+// (P_BC x is first split into h->xsplit)
 void kv_launch_coef_df(const kv_grid* h, const double* coef, float2* cdf, cudaStream_t s);
 void kv_launch_apply_df(const kv_grid* h, const float2* cdf, const double* x, double* vstar, double* tout,
                         cudaStream_t s);
@@ -189,10 +192,12 @@ void kv_launch_scale_inv_sqrt(double* w, size_t len, const double* nrm2, cudaStr
 // h[q] = <V_q, w> (and h[nq] = ||w||^2 when nrm2 != nullptr, copied to nrm2);
 // w -= V c fused with h2[q] = <V_q, w> and h2[nq] = ||w||^2 (FP64);
 // w = (w - V c) / sqrt(c[nq] - ||c||^2) for rounding-size c = V^T w (product in FP32).
+// df != 0 forms the first two sweeps in double-float arithmetic on the FP32 pipe (relative
+// rounding ~2^-46; entries of w at or above 2^48 make h[nq] NaN).
 int kv_fused_cgs_max();
 void kv_launch_dots_norm(const double* V, size_t ld, int nq, const double* w, size_t len, double* partials,
-                         double* h, double* nrm2, cudaStream_t s);
+                         double* h, double* nrm2, int df, cudaStream_t s);
 void kv_launch_update_dot(const double* V, size_t ld, int nq, const double* c, double* w, size_t len,
-                          double* partials, double* h2, cudaStream_t s);
+                          double* partials, double* h2, int df, cudaStream_t s);
 void kv_launch_update_small_scale(const double* V, size_t ld, int nq, const double* c, double* w, size_t len,
                                   cudaStream_t s);

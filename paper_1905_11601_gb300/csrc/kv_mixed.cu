@@ -1,10 +1,10 @@
 // Mixed-precision pressure-correction solve: phi = L^+ b (Eqs (14)-(18)) with the six per-axis
 // contractions on the tensor cores (BF16 slices, FP32 accumulation; kv_umma.cu), won back to
-// FP64 accuracy by iterative refinement with an FP64 residual:
+// FP64-class accuracy by iterative refinement with a double-float residual:
 //
 //   phi = 0;  r = b
 //   repeat S times:  phi += TPF(r)   (six tcgen05 contractions, the last one adds into phi)
-//                    r = b - L phi   (FP64 7-point Neumann Laplacian, written as BF16 slices)
+//                    r = b - L phi   (7-point Neumann Laplacian in double-float, written as BF16 slices)
 //
 // Each sweep reduces the error by roughly the FP32 accuracy of one tensor-core solve.
 #include <math.h>
@@ -13,37 +13,43 @@
 #include <string>
 #include <vector>
 
+#include "kv_df.cuh"
 #include "kv_internal.cuh"
 
 namespace {
 
 int pad8(int n) { return (n + 7) & ~7; }
 
-// r = b - L phi (L = D G with homogeneous Neumann walls), FP64, then three BF16 slices of r
-// into the first contraction's input layout [k][j][i_pad]. phi == nullptr means phi = 0.
+// r = b - L phi (L = D G with homogeneous Neumann walls) in double-float arithmetic on the FP32
+// pipe (kv_df.cuh; about 2^-44 of |b| + |L phi|, far below what one tensor-core sweep resolves),
+// then three BF16 slices of r into the first contraction's input layout [k][j][i_pad].
+// phi == nullptr means phi = 0. With rmax, max |r| is reduced per block into *rmax.
 __global__ void __launch_bounds__(256) k_residual_slices(KvGeom g, const double* __restrict__ b,
                                                          const double* __restrict__ phi, __nv_bfloat16* __restrict__ xs,
                                                          size_t slice, int pitch, unsigned long long* rmax) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   const int j = blockIdx.y * blockDim.y + threadIdx.y;
   const int k = blockIdx.z;
-  double rv = 0.0;
+  float rv = 0.0f;
   if (i < g.nx && j < g.ny) {
     const size_t sx = 1, sy = g.nx, sz = (size_t)g.nx * g.ny;
     const size_t e = i + sy * j + sz * k;
-    double r = __ldg(b + e);
+    DF r = df_split(__ldg(b + e));
     if (phi) {
       // homogeneous Neumann walls: a missing neighbour contributes as the cell itself
-      const double c = __ldg(phi + e);
-      const double xm = i > 0 ? __ldg(phi + e - sx) : c, xp = i < g.nx - 1 ? __ldg(phi + e + sx) : c;
-      const double ym = j > 0 ? __ldg(phi + e - sy) : c, yp = j < g.ny - 1 ? __ldg(phi + e + sy) : c;
-      const double zm = k > 0 ? __ldg(phi + e - sz) : c, zp = k < g.nz - 1 ? __ldg(phi + e + sz) : c;
-      r = fma(-g.ihx2, fma(-2.0, c, xm + xp), r);
-      r = fma(-g.ihy2, fma(-2.0, c, ym + yp), r);
-      r = fma(-g.ihz2, fma(-2.0, c, zm + zp), r);
+      const double cd = __ldg(phi + e);
+      const DF c = df_split(cd);
+      const DF c2 = DF{2.0f * c.h, 2.0f * c.l};  // exact
+      const DF xm = df_split(i > 0 ? __ldg(phi + e - sx) : cd), xp = df_split(i < g.nx - 1 ? __ldg(phi + e + sx) : cd);
+      const DF ym = df_split(j > 0 ? __ldg(phi + e - sy) : cd), yp = df_split(j < g.ny - 1 ? __ldg(phi + e + sy) : cd);
+      const DF zm = df_split(k > 0 ? __ldg(phi + e - sz) : cd), zp = df_split(k < g.nz - 1 ? __ldg(phi + e + sz) : cd);
+      const DF lx = df_mul(df_sub(df_add(xm, xp), c2), df_split(g.ihx2));
+      const DF ly = df_mul(df_sub(df_add(ym, yp), c2), df_split(g.ihy2));
+      const DF lz = df_mul(df_sub(df_add(zm, zp), c2), df_split(g.ihz2));
+      r = df_sub(r, df_add(df_add(lx, ly), lz));
     }
-    rv = fabs(r);
-    const float rf = (float)r;
+    const float rf = __fadd_rn(r.h, r.l);
+    rv = fabsf(rf);
     const __nv_bfloat16 s1 = __float2bfloat16_rn(rf);
     const float r1 = rf - __bfloat162float(s1);
     const __nv_bfloat16 s2 = __float2bfloat16_rn(r1);
@@ -54,8 +60,16 @@ __global__ void __launch_bounds__(256) k_residual_slices(KvGeom g, const double*
     xs[2 * slice + o] = s3;
   }
   if (rmax) {
-    for (int off = 16; off > 0; off >>= 1) rv = fmax(rv, __shfl_xor_sync(0xffffffffu, rv, off));
-    if ((threadIdx.x & 31) == 0) atomicMax(rmax, (unsigned long long)__double_as_longlong(rv));
+    for (int off = 16; off > 0; off >>= 1) rv = fmaxf(rv, __shfl_xor_sync(0xffffffffu, rv, off));
+    __shared__ float sm[32];
+    const int t = threadIdx.x + blockDim.x * threadIdx.y, nw = (blockDim.x * blockDim.y + 31) / 32;
+    if ((t & 31) == 0) sm[t >> 5] = rv;
+    __syncthreads();
+    if (t == 0) {
+      float m = sm[0];
+      for (int q = 1; q < nw; ++q) m = fmaxf(m, sm[q]);
+      atomicMax(rmax, (unsigned long long)__double_as_longlong(df_f2d(m)));
+    }
   }
 }
 
@@ -141,12 +155,12 @@ void kv_mixed_free(kv_grid* h) {
   cudaFree(h->rmax);
 }
 
-void kv_launch_poisson_mixed(kv_grid* h, const double* b, double* phi, cudaStream_t s) {
+void kv_launch_poisson_mixed(kv_grid* h, const double* b, double* phi, int stats, cudaStream_t s) {
   const KvGeom& g = h->g;
   const int n[3] = {g.nx, g.ny, g.nz};
   dim3 rb(32, 8, 1), rg((g.nx + 31) / 32, (g.ny + 7) / 8, g.nz);
   cudaMemsetAsync(phi, 0, h->Nc * sizeof(double), s);
-  cudaMemsetAsync(h->rmax, 0, sizeof(unsigned long long), s);
+  if (stats) cudaMemsetAsync(h->rmax, 0, sizeof(unsigned long long), s);
   {
     KvPhase ph(h, KV_PH_REFINE, 1);
     k_residual_slices<<<rg, rb, 0, s>>>(g, b, nullptr, h->xs[0], h->xs_slice, pad8(g.nx), nullptr);
@@ -172,7 +186,7 @@ void kv_launch_poisson_mixed(kv_grid* h, const double* b, double* phi, cudaStrea
     }
     if (sweep + 1 < h->refine) {
       KvPhase ph(h, KV_PH_REFINE, 1);
-      k_residual_slices<<<rg, rb, 0, s>>>(g, b, phi, h->xs[0], h->xs_slice, pad8(g.nx), h->rmax);
+      k_residual_slices<<<rg, rb, 0, s>>>(g, b, phi, h->xs[0], h->xs_slice, pad8(g.nx), stats ? h->rmax : nullptr);
     }
   }
 }

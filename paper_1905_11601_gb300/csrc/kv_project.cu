@@ -1,6 +1,8 @@
 // Divergence and the fused velocity correction of the SIMPLE / Chorin step (Section 3.1):
 // b = D v* on the cells; v = v* - G phi on the interior faces; p = phi; and the pointwise
-// divergence residual max |D v| used as the SIMPLE stopping test.
+// divergence residual max |D v| used as the SIMPLE stopping test. FP64, and for the mixed
+// precision path the same arithmetic in double-float on the FP32 pipe.
+#include "kv_df.cuh"
 #include "kv_internal.cuh"
 
 namespace {
@@ -99,17 +101,146 @@ __global__ void __launch_bounds__(256) k_correct(KvGeom g, const double* __restr
   }
 }
 
+// ---- the same two kernels in double-float arithmetic (mixed precision; kv_df.cuh) ----------
+
+__global__ void __launch_bounds__(256) k_divergence_df(KvGeom g, const double* __restrict__ vel, size_t P,
+                                                       double* __restrict__ b, float2 ihx, float2 ihy, float2 ihz) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x + 1;
+  const int j = blockIdx.y * blockDim.y + threadIdx.y + 1;
+  const int k = blockIdx.z + 1;
+  if (i > g.nx || j > g.ny) return;
+  const double* u = vel;
+  const double* v = vel + P;
+  const double* w = vel + 2 * P;
+  const int e = i + g.X * (j + g.Y * k);
+  const DF dx = df_mul(df_sub(df_split(__ldg(u + e)), df_split(__ldg(u + e - 1))), DF{ihx.x, ihx.y});
+  const DF dy = df_mul(df_sub(df_split(__ldg(v + e)), df_split(__ldg(v + e - g.X))), DF{ihy.x, ihy.y});
+  const DF dz = df_mul(df_sub(df_split(__ldg(w + e)), df_split(__ldg(w + e - g.X * g.Y))), DF{ihz.x, ihz.y});
+  b[(i - 1) + (size_t)g.nx * ((j - 1) + (size_t)g.ny * (k - 1))] = df_value(df_add(df_add(dx, dy), dz));
+}
+
+struct CorrDF {
+  KvGeom g;
+  const double* __restrict__ vs;
+  const double* __restrict__ phi;
+  size_t P;
+  DF ihx, ihy, ihz;
+  __device__ __forceinline__ DF ph(int i, int j, int k) const {  // padded cell index
+    return df_split(__ldg(phi + (i - 1) + (size_t)g.nx * ((j - 1) + (size_t)g.ny * (k - 1))));
+  }
+  __device__ __forceinline__ int at(int i, int j, int k) const { return i + g.X * (j + g.Y * k); }
+  __device__ __forceinline__ DF u(int i, int j, int k) const {
+    if (!(i >= 1 && i <= g.nx - 1 && j >= 1 && j <= g.ny && k >= 1 && k <= g.nz)) return DF{0.0f, 0.0f};
+    return df_sub(df_split(__ldg(vs + at(i, j, k))), df_mul(df_sub(ph(i + 1, j, k), ph(i, j, k)), ihx));
+  }
+  __device__ __forceinline__ DF v(int i, int j, int k) const {
+    if (!(i >= 1 && i <= g.nx && j >= 1 && j <= g.ny - 1 && k >= 1 && k <= g.nz)) return DF{0.0f, 0.0f};
+    return df_sub(df_split(__ldg(vs + P + at(i, j, k))), df_mul(df_sub(ph(i, j + 1, k), ph(i, j, k)), ihy));
+  }
+  __device__ __forceinline__ DF w(int i, int j, int k) const {
+    if (!(i >= 1 && i <= g.nx && j >= 1 && j <= g.ny && k >= 1 && k <= g.nz - 1)) return DF{0.0f, 0.0f};
+    return df_sub(df_split(__ldg(vs + 2 * P + at(i, j, k))), df_mul(df_sub(ph(i, j, k + 1), ph(i, j, k)), ihz));
+  }
+};
+
+__device__ __forceinline__ float df_abs_hi(const DF a) { return fabsf(__fadd_rn(a.h, a.l)); }
+
+__device__ __forceinline__ DF df_of(const float2 c) { return DF{c.x, c.y}; }
+
+// CHECK = 0: the corrected faces and p only, each input loaded and split once, inverse spacings
+// passed as FP32 pairs (ih). CHECK = 1 adds max |D v| and max |v| for the SIMPLE test.
+template <int CHECK>
+__global__ void __launch_bounds__(256) k_correct_df(KvGeom g, const double* __restrict__ vs,
+                                                    const double* __restrict__ phi, size_t P,
+                                                    double* __restrict__ out, double* __restrict__ p, int acc_p,
+                                                    unsigned long long* __restrict__ red, float2 ihx, float2 ihy,
+                                                    float2 ihz) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = blockIdx.y * blockDim.y + threadIdx.y;
+  const int k = blockIdx.z;
+  double dmax = 0.0, vmax = 0.0;
+  if (i < g.X && j < g.Y) {
+    const int e = i + g.X * (j + g.Y * k);
+    const bool cell = i >= 1 && i <= g.nx && j >= 1 && j <= g.ny && k >= 1 && k <= g.nz;
+    // interior faces (the wall-normal faces i = nx etc. stay 0)
+    const bool du = cell && i <= g.nx - 1, dv = cell && j <= g.ny - 1, dw = cell && k <= g.nz - 1;
+    const size_t c = (size_t)(i - 1) + (size_t)g.nx * ((j - 1) + (size_t)g.ny * (k - 1));
+    const size_t cy = g.nx, cz = (size_t)g.nx * g.ny;
+    const double p0d = cell ? __ldg(phi + c) : 0.0;
+    const DF p0 = df_split(p0d);
+    DF ur{0.0f, 0.0f}, vr{0.0f, 0.0f}, wr{0.0f, 0.0f};
+    if (du) ur = df_sub(df_split(__ldg(vs + e)), df_mul(df_sub(df_split(__ldg(phi + c + 1)), p0), df_of(ihx)));
+    if (dv) vr = df_sub(df_split(__ldg(vs + P + e)), df_mul(df_sub(df_split(__ldg(phi + c + cy)), p0), df_of(ihy)));
+    if (dw) wr = df_sub(df_split(__ldg(vs + 2 * P + e)), df_mul(df_sub(df_split(__ldg(phi + c + cz)), p0), df_of(ihz)));
+    out[e] = df_value(ur);
+    out[P + e] = df_value(vr);
+    out[2 * P + e] = df_value(wr);
+    if (CHECK) {
+      vmax = (double)fmaxf(df_abs_hi(ur), fmaxf(df_abs_hi(vr), df_abs_hi(wr)));
+      if (cell) {
+        const CorrDF C{g, vs, phi, P, df_of(ihx), df_of(ihy), df_of(ihz)};
+        const DF d = df_add(df_add(df_mul(df_sub(ur, C.u(i - 1, j, k)), C.ihx), df_mul(df_sub(vr, C.v(i, j - 1, k)), C.ihy)),
+                            df_mul(df_sub(wr, C.w(i, j, k - 1)), C.ihz));
+        dmax = fabs(df_value(d));
+      }
+    }
+    if (p) {
+      if (cell)
+        p[e] = (acc_p ? p[e] : 0.0) + p0d;
+      else if (!acc_p)
+        p[e] = 0.0;
+    }
+  }
+  if (!CHECK) return;
+  for (int o = 16; o > 0; o >>= 1) {
+    dmax = fmax(dmax, __shfl_xor_sync(0xffffffffu, dmax, o));
+    vmax = fmax(vmax, __shfl_xor_sync(0xffffffffu, vmax, o));
+  }
+  __shared__ double sd[8], sv[8];
+  const int t = threadIdx.x + blockDim.x * threadIdx.y, warp = t >> 5, lane = t & 31;
+  if (lane == 0) {
+    sd[warp] = dmax;
+    sv[warp] = vmax;
+  }
+  __syncthreads();
+  if (t == 0) {
+    double a = sd[0], b = sv[0];
+    for (int q = 1; q < 8; ++q) {
+      a = fmax(a, sd[q]);
+      b = fmax(b, sv[q]);
+    }
+    atomic_max_nonneg(red, a);
+    atomic_max_nonneg(red + 1, b);
+  }
+}
+
+// x as an FP32 pair (host side)
+float2 pair_of(double x) {
+  const float h = (float)x;
+  return make_float2(h, (float)(x - (double)h));
+}
+
 }  // namespace
 
 void kv_launch_divergence(const kv_grid* h, const double* vel, double* b, cudaStream_t s) {
   const KvGeom& g = h->g;
   dim3 block(32, 8, 1), grid((g.nx + 31) / 32, (g.ny + 7) / 8, g.nz);
-  k_divergence<<<grid, block, 0, s>>>(g, vel, h->P, b);
+  if (h->d.precision == KV_PREC_MIXED)
+    k_divergence_df<<<grid, block, 0, s>>>(g, vel, h->P, b, pair_of(g.ihx), pair_of(g.ihy), pair_of(g.ihz));
+  else
+    k_divergence<<<grid, block, 0, s>>>(g, vel, h->P, b);
 }
 
 void kv_launch_correct(const kv_grid* h, const double* vstar, const double* phi, double* out_vel, double* p,
                        int accumulate_p, cudaStream_t s, int check) {
   const KvGeom& g = h->g;
   dim3 block(32, 8, 1), grid((g.X + 31) / 32, (g.Y + 7) / 8, g.Z);
-  k_correct<<<grid, block, 0, s>>>(g, vstar, phi, h->P, out_vel, p, accumulate_p, check, h->red);
+  if (h->d.precision == KV_PREC_MIXED) {
+    const float2 cx = pair_of(g.ihx), cy = pair_of(g.ihy), cz = pair_of(g.ihz);
+    if (check)
+      k_correct_df<1><<<grid, block, 0, s>>>(g, vstar, phi, h->P, out_vel, p, accumulate_p, h->red, cx, cy, cz);
+    else
+      k_correct_df<0><<<grid, block, 0, s>>>(g, vstar, phi, h->P, out_vel, p, accumulate_p, h->red, cx, cy, cz);
+  } else
+    k_correct<<<grid, block, 0, s>>>(g, vstar, phi, h->P, out_vel, p, accumulate_p, check, h->red);
 }

@@ -1,6 +1,7 @@
 // FP64 reductions for the Arnoldi step: several inner products against one vector
 // (classical Gram-Schmidt), the matching update, and the 2-norm. Partial sums per block are
 // combined in a fixed order by a second kernel, so results are deterministic.
+#include "kv_df.cuh"
 #include "kv_internal.cuh"
 
 namespace {
@@ -25,7 +26,7 @@ __global__ void __launch_bounds__(RT) k_multidot(const double* __restrict__ V, s
   double acc[QB];
 #pragma unroll
   for (int q = 0; q < QB; ++q) acc[q] = 0.0;
-  for (size_t e = (size_t)blockIdx.x * RT + threadIdx.x; e < len; e += (size_t)RB * RT) {
+  for (size_t e = (size_t)blockIdx.x * RT + threadIdx.x; e < len; e += (size_t)gridDim.x * RT) {
     const double we = __ldg(w + e);
 #pragma unroll
     for (int q = 0; q < QB; ++q)
@@ -46,12 +47,12 @@ __global__ void __launch_bounds__(RT) k_multidot(const double* __restrict__ V, s
   }
 }
 
-// out[q] (+)= sum_b partials[q * RB + b]; one block per q
-__global__ void __launch_bounds__(RT) k_finalize(const double* __restrict__ partials, double* __restrict__ out,
-                                                 int accumulate) {
+// out[q] (+)= sum_{b < nb} partials[q * RB + b]; one block per q
+__global__ void __launch_bounds__(RT) k_finalize(const double* __restrict__ partials, int nb,
+                                                 double* __restrict__ out, int accumulate) {
   const int q = blockIdx.x;
   double s = 0.0;
-  for (int b = threadIdx.x; b < RB; b += RT) s += partials[(size_t)q * RB + b];
+  for (int b = threadIdx.x; b < nb; b += RT) s += partials[(size_t)q * RB + b];
   s = warp_sum(s);
   __shared__ double sm[RT / 32];
   if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = s;
@@ -103,7 +104,7 @@ __global__ void __launch_bounds__(RT) k_dots(const double* __restrict__ V, size_
   double acc[Q + 1];
 #pragma unroll
   for (int q = 0; q <= Q; ++q) acc[q] = 0.0;
-  for (size_t e = (size_t)blockIdx.x * RT + threadIdx.x; e < len; e += (size_t)RB * RT) {
+  for (size_t e = (size_t)blockIdx.x * RT + threadIdx.x; e < len; e += (size_t)gridDim.x * RT) {
     const double we = __ldg(w + e);
 #pragma unroll
     for (int q = 0; q < Q; ++q) acc[q] = fma(__ldg(V + (size_t)q * ld + e), we, acc[q]);
@@ -138,7 +139,7 @@ __global__ void __launch_bounds__(RT) k_update_dot(const double* __restrict__ V,
   double acc[Q + 1];
 #pragma unroll
   for (int q = 0; q <= Q; ++q) acc[q] = 0.0;
-  for (size_t e = (size_t)blockIdx.x * RT + threadIdx.x; e < len; e += (size_t)RB * RT) {
+  for (size_t e = (size_t)blockIdx.x * RT + threadIdx.x; e < len; e += (size_t)gridDim.x * RT) {
     double v[Q];
     double s = 0.0;
 #pragma unroll
@@ -172,27 +173,197 @@ __global__ void __launch_bounds__(RT) k_update_dot(const double* __restrict__ V,
 // in FP32 from the high words (its error is ~1e-6 of a rounding-size correction) and subtracted
 // in FP64. With V orthonormal and c = V^T w, beta^2 = ||w||^2 - ||c||^2 (c[nq] holds ||w||^2),
 // which needs no further pass over w.
-__global__ void __launch_bounds__(RT) k_update_small_scale(const double* __restrict__ V, size_t ld, int nq,
+template <int Q>
+__global__ void __launch_bounds__(RT) k_update_small_scale(const double* __restrict__ V, size_t ld,
                                                            const double* __restrict__ c, double* __restrict__ w,
                                                            size_t len) {
-  __shared__ float cs[QF];
+  __shared__ float cs[Q];
   __shared__ double finv;
-  if (threadIdx.x < QF) cs[threadIdx.x] = (int)threadIdx.x < nq ? (float)c[threadIdx.x] : 0.0f;
+  if (threadIdx.x < Q) cs[threadIdx.x] = (float)c[threadIdx.x];
   if (threadIdx.x == 0) {
     double s = 0.0;
-    for (int q = 0; q < nq; ++q) s = fma(c[q], c[q], s);
-    const double b2 = c[nq] - s;
+    for (int q = 0; q < Q; ++q) s = fma(c[q], c[q], s);
+    const double b2 = c[Q] - s;
     finv = b2 > 0.0 ? 1.0 / sqrt(b2) : 0.0;
   }
   __syncthreads();
   const double f = finv;
-  for (size_t e = (size_t)blockIdx.x * RT + threadIdx.x; e < len; e += (size_t)RB * RT) {
+  for (size_t e = (size_t)blockIdx.x * RT + threadIdx.x; e < len; e += (size_t)gridDim.x * RT) {
     float s = 0.0f;
 #pragma unroll
-    for (int q = 0; q < QF; ++q)
-      if (q < nq) s = fmaf(cs[q], hi_float(__ldg(V + (size_t)q * ld + e)), s);
-    w[e] = (w[e] - (double)s) * f;
+    for (int q = 0; q < Q; ++q) s = fmaf(cs[q], hi_float(__ldg(V + (size_t)q * ld + e)), s);
+    w[e] = (w[e] - df_f2d(s)) * f;
   }
+}
+
+// ---- double-float Gram-Schmidt sweeps (mixed precision) -------------------------------------
+//
+// GB300's FP64 pipe cannot keep up with HBM in these sweeps (one FP64 multiply-add per 8 bytes
+// read is already 1.4x the memory time), so the mixed-precision Arnoldi step forms the inner
+// products and the first update in double-float arithmetic on the FP32 pipe (kv_df.cuh): the
+// result of a sweep is within ~2^-46 of the sum of the magnitudes of its terms, against ~2^-53
+// for FP64. Entries below 2^-103 in magnitude are flushed to zero (an absolute change of at
+// most 2^-103 per entry); entries at or above 2^48 in the new vector (whose sums of squares
+// could leave the FP32 range), NaN and Inf are reported by a NaN norm, which the host turns
+// into an error.
+
+// the new vector's entries must also satisfy |x| < 2^48: its squared norm, up to 2^31 entries,
+// then stays below 2^127
+__device__ __forceinline__ bool gs_in_range(double x) {
+  const unsigned int ex = ((unsigned int)__double2hiint(x) >> 20) & 0x7FFu;
+  return ex < 1023u + 48u;
+}
+
+// U consecutive entries p[e .. e+U-1] (zero past len), as one 16-byte load when vec (p and e
+// 16-byte aligned)
+template <int U>
+__device__ __forceinline__ void load_u(const double* __restrict__ p, size_t e, size_t len, bool vec,
+                                       double (&out)[U]) {
+  if constexpr (U == 2) {
+    if (vec && e + 1 < len) {
+      const double2 t = __ldg(reinterpret_cast<const double2*>(p + e));
+      out[0] = t.x;
+      out[1] = t.y;
+    } else {
+      out[0] = __ldg(p + e);
+      out[1] = e + 1 < len ? __ldg(p + e + 1) : 0.0;
+    }
+  } else {
+    out[0] = __ldg(p + e);
+  }
+}
+
+// Entries per thread and sweep iteration: two adjacent entries (16-byte loads, twice the loads
+// in flight) while the registers allow it.
+template <int Q>
+__host__ __device__ constexpr int dots_unroll() { return Q <= 12 ? 2 : 1; }
+template <int Q>
+__host__ __device__ constexpr int update_unroll() { return Q <= 8 ? 2 : 1; }
+
+// Block partials of <V_q, w> (q < Q) and ||w||^2 in double-float, as k_dots.
+template <int Q>
+__global__ void __launch_bounds__(RT) k_dots_df(const double* __restrict__ V, size_t ld,
+                                                const double* __restrict__ w, size_t len, int nrm, int vec,
+                                                double* __restrict__ partials) {
+  constexpr int U = dots_unroll<Q>();
+  __shared__ double sm[Q + 1][RT / 32];
+  DFAcc acc[Q + 1];
+  bool bad = false;
+  for (size_t e = ((size_t)blockIdx.x * RT + threadIdx.x) * U; e < len; e += (size_t)gridDim.x * RT * U) {
+    double wd[U];
+    double v[Q][U];
+    load_u<U>(w, e, len, vec, wd);
+#pragma unroll
+    for (int q = 0; q < Q; ++q) load_u<U>(V + (size_t)q * ld, e, len, vec, v[q]);
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      bad |= !gs_in_range(wd[u]);
+      const DF we = df_split(wd[u]);
+#pragma unroll
+      for (int q = 0; q < Q; ++q) acc[q].fma(df_split(v[q][u]), we);
+      acc[Q].fma(we, we);
+    }
+  }
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+#pragma unroll
+  for (int q = 0; q <= Q; ++q) {
+    double x = acc[q].value();
+    if (q == Q && bad) x = __longlong_as_double(0x7FF8000000000000LL);  // NaN: out of range
+    const double t = warp_sum(x);
+    if (lane == 0) sm[q][warp] = t;
+  }
+  __syncthreads();
+  const int t = threadIdx.x;
+  if (t < Q || (nrm && t == Q)) {
+    double s = 0.0;
+    for (int wv = 0; wv < RT / 32; ++wv) s += sm[t][wv];
+    partials[(size_t)t * RB + blockIdx.x] = s;
+  }
+}
+
+// w -= sum_q c[q] V_q in double-float, fused with the block partials of <V_q, w> and ||w||^2 of
+// the updated w, as k_update_dot. The updated w is stored rounded to FP64.
+template <int Q>
+__global__ void __launch_bounds__(RT, 2) k_update_dot_df(const double* __restrict__ V, size_t ld,
+                                                         const double* __restrict__ c, double* __restrict__ w,
+                                                         size_t len, int vec, double* __restrict__ partials) {
+  constexpr int U = update_unroll<Q>();
+  __shared__ DF cs[Q];
+  __shared__ double sm[Q + 1][RT / 32];
+  if (threadIdx.x < Q) {
+    const DF x = df_split(c[threadIdx.x]);
+    cs[threadIdx.x] = DF{-x.h, -x.l};
+  }
+  __syncthreads();
+  DFAcc acc[Q + 1];
+  for (size_t e = ((size_t)blockIdx.x * RT + threadIdx.x) * U; e < len; e += (size_t)gridDim.x * RT * U) {
+    double vd[Q][U];
+    double wd[U];
+#pragma unroll
+    for (int q = 0; q < Q; ++q) load_u<U>(V + (size_t)q * ld, e, len, vec, vd[q]);
+    load_u<U>(w, e, len, vec, wd);
+    double wo[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const DF w0 = df_split(wd[u]);
+      DFAcc a;
+      a.start(w0);
+      DF v[Q];
+#pragma unroll
+      for (int q = 0; q < Q; ++q) {
+        v[q] = df_split(vd[q][u]);
+        a.fma(cs[q], v[q]);
+      }
+      const DF w1 = a.pair();
+      wo[u] = df_f2d(w1.h) + df_f2d(w1.l);
+#pragma unroll
+      for (int q = 0; q < Q; ++q) acc[q].fma(v[q], w1);
+      acc[Q].fma(w1, w1);
+    }
+    if constexpr (U == 2) {
+      if (vec && e + 1 < len) {
+        *reinterpret_cast<double2*>(w + e) = make_double2(wo[0], wo[1]);
+      } else {
+        w[e] = wo[0];
+        if (e + 1 < len) w[e + 1] = wo[1];
+      }
+    } else {
+      w[e] = wo[0];
+    }
+  }
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+#pragma unroll
+  for (int q = 0; q <= Q; ++q) {
+    const double t = warp_sum(acc[q].value());
+    if (lane == 0) sm[q][warp] = t;
+  }
+  __syncthreads();
+  const int t = threadIdx.x;
+  if (t <= Q) {
+    double s = 0.0;
+    for (int wv = 0; wv < RT / 32; ++wv) s += sm[t][wv];
+    partials[(size_t)t * RB + blockIdx.x] = s;
+  }
+}
+
+// Blocks of kernel K that are resident at once on the device (at most RB): the sweeps below
+// launch exactly one wave, so no partly filled second wave trails the memory stream.
+template <auto K>
+int wave_blocks() {
+  static const int nb = [] {
+    int dev = 0, sms = 0, per = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, K, RT, 0);
+    const int n = per * sms;
+    return n > 0 && n < RB ? n : RB;
+  }();
+  return nb;
+}
+
+// V_q and w start on 16-byte boundaries for every q
+int aligned16(const double* V, size_t ld, const double* w) {
+  return ((uintptr_t)V % 16 == 0) && (ld % 2 == 0) && ((uintptr_t)w % 16 == 0);
 }
 
 }  // namespace
@@ -201,51 +372,89 @@ int kv_reduce_blocks() { return RB; }
 int kv_fused_cgs_max() { return QF; }
 
 void kv_launch_dots_norm(const double* V, size_t ld, int nq, const double* w, size_t len, double* partials,
-                         double* h, double* nrm2, cudaStream_t s) {
+                         double* h, double* nrm2, int df, cudaStream_t s) {
   const int nrm = nrm2 != nullptr;
-  // one instantiation per basis size, so no predicated-off multiply-adds occupy the FP64 pipe
-  switch (nq) {
+  int nb = RB;
+  const int vec = aligned16(V, ld, w);
+  // one instantiation per basis size, so no predicated-off multiply-adds occupy the pipes
+  if (df) {
+    switch (nq) {
+#define KV_DOTS_DF_CASE(Qn) \
+  case Qn:                  \
+    nb = wave_blocks<k_dots_df<Qn>>();                               \
+    k_dots_df<Qn><<<nb, RT, 0, s>>>(V, ld, w, len, nrm, vec, partials); \
+    break;
+      KV_FOR_EACH_NQ(KV_DOTS_DF_CASE)
+#undef KV_DOTS_DF_CASE
+    }
+  } else {
+    switch (nq) {
 #define KV_DOTS_CASE(Qn) \
   case Qn:               \
-    k_dots<Qn><<<RB, RT, 0, s>>>(V, ld, nq, w, len, nrm, partials); \
+    nb = wave_blocks<k_dots<Qn>>();                                    \
+    k_dots<Qn><<<nb, RT, 0, s>>>(V, ld, nq, w, len, nrm, partials); \
     break;
-    KV_FOR_EACH_NQ(KV_DOTS_CASE)
+      KV_FOR_EACH_NQ(KV_DOTS_CASE)
 #undef KV_DOTS_CASE
+    }
   }
-  k_finalize<<<nq + (nrm2 ? 1 : 0), RT, 0, s>>>(partials, h, 0);  // h[nq] = ||w||^2 when asked
+  k_finalize<<<nq + (nrm2 ? 1 : 0), RT, 0, s>>>(partials, nb, h, 0);  // h[nq] = ||w||^2 when asked
   if (nrm2 && nrm2 != h + nq) cudaMemcpyAsync(nrm2, h + nq, sizeof(double), cudaMemcpyDeviceToDevice, s);
 }
 
 void kv_launch_update_dot(const double* V, size_t ld, int nq, const double* c, double* w, size_t len,
-                          double* partials, double* h2, cudaStream_t s) {
-  switch (nq) {
+                          double* partials, double* h2, int df, cudaStream_t s) {
+  int nb = RB;
+  const int vec = aligned16(V, ld, w);
+  if (df) {
+    switch (nq) {
+#define KV_UPD_DF_CASE(Qn) \
+  case Qn:                 \
+    nb = wave_blocks<k_update_dot_df<Qn>>();                             \
+    k_update_dot_df<Qn><<<nb, RT, 0, s>>>(V, ld, c, w, len, vec, partials); \
+    break;
+      KV_FOR_EACH_NQ(KV_UPD_DF_CASE)
+#undef KV_UPD_DF_CASE
+    }
+  } else {
+    switch (nq) {
 #define KV_UPD_CASE(Qn) \
   case Qn:              \
-    k_update_dot<Qn><<<RB, RT, 0, s>>>(V, ld, nq, c, w, len, partials); \
+    nb = wave_blocks<k_update_dot<Qn>>();                                  \
+    k_update_dot<Qn><<<nb, RT, 0, s>>>(V, ld, nq, c, w, len, partials); \
     break;
-    KV_FOR_EACH_NQ(KV_UPD_CASE)
+      KV_FOR_EACH_NQ(KV_UPD_CASE)
 #undef KV_UPD_CASE
+    }
   }
-  k_finalize<<<nq + 1, RT, 0, s>>>(partials, h2, 0);  // h2[nq] = ||w||^2 after the update
+  k_finalize<<<nq + 1, RT, 0, s>>>(partials, nb, h2, 0);  // h2[nq] = ||w||^2 after the update
 }
 
 void kv_launch_update_small_scale(const double* V, size_t ld, int nq, const double* c, double* w, size_t len,
                                   cudaStream_t s) {
-  k_update_small_scale<<<RB, RT, 0, s>>>(V, ld, nq, c, w, len);
+  switch (nq) {
+#define KV_SMALL_CASE(Qn) \
+  case Qn:                \
+    k_update_small_scale<Qn><<<wave_blocks<k_update_small_scale<Qn>>(), RT, 0, s>>>(V, ld, c, w, len); \
+    break;
+    KV_FOR_EACH_NQ(KV_SMALL_CASE)
+#undef KV_SMALL_CASE
+  }
 }
 
 void kv_launch_multidot(const double* V, size_t ld, int nq, const double* w, size_t len, double* partials,
                         double* out, int accumulate, cudaStream_t s) {
+  const int nb = wave_blocks<k_multidot>();
   for (int q0 = 0; q0 < nq; q0 += QB) {
     const int nqb = nq - q0 < QB ? nq - q0 : QB;
-    k_multidot<<<RB, RT, 0, s>>>(V, ld, q0, nqb, w, len, partials);
+    k_multidot<<<nb, RT, 0, s>>>(V, ld, q0, nqb, w, len, partials);
   }
-  k_finalize<<<nq, RT, 0, s>>>(partials, out, accumulate);
+  k_finalize<<<nq, RT, 0, s>>>(partials, nb, out, accumulate);
 }
 
 void kv_launch_update(const double* V, size_t ld, int nq, const double* c, double* w, size_t len,
                       cudaStream_t s) {
-  k_update<<<RB, RT, sizeof(double) * (size_t)nq, s>>>(V, ld, nq, c, w, len);
+  k_update<<<wave_blocks<k_update>(), RT, sizeof(double) * (size_t)nq, s>>>(V, ld, nq, c, w, len);
 }
 
 void kv_launch_norm2(const double* w, size_t len, double* partials, double* out, cudaStream_t s) {
@@ -253,5 +462,5 @@ void kv_launch_norm2(const double* w, size_t len, double* partials, double* out,
 }
 
 void kv_launch_scale_inv_sqrt(double* w, size_t len, const double* nrm2, cudaStream_t s) {
-  k_scale_inv_sqrt<<<RB, RT, 0, s>>>(w, len, nrm2);
+  k_scale_inv_sqrt<<<wave_blocks<k_scale_inv_sqrt>(), RT, 0, s>>>(w, len, nrm2);
 }

@@ -9,6 +9,7 @@
 //   buoyancy   T e_z on a w-face: mean of the two adjacent cell temperatures.
 // One thread per padded index (i, j, k) writes the u, v and w entries at that index (the
 // momentum right-hand side on interior faces, 0 elsewhere) and the projected temperature.
+#include "kv_df.cuh"
 #include "kv_internal.cuh"
 
 namespace {
@@ -403,85 +404,70 @@ __global__ void __launch_bounds__(256) k_apply(KvGeom g, const double* __restric
 
 // ---- the same operator on the FP32 pipe (mixed precision) ----------------------------------
 //
-// GB300's FP64 pipe runs at 1/60 of its FP32 rate, so the mixed path evaluates J x in
-// double-float arithmetic: every coefficient is stored as an FP32 pair c = ch + cl (|cl| <=
-// 2^-24 |ch|), every FP64 input is split into xh (its leading 21 bits, exact) and xl (the rest,
-// rounded to FP32) with integer operations only, and each product is accumulated as an exact
-// FP32 product ch*xh (FMA error term), an exact running sum (TwoSum) and a small FP32
+// GB300's FP64 pipe runs at 1/64 of its FP32 rate, so the mixed path evaluates J x in
+// double-float arithmetic (kv_df.cuh): every coefficient is stored as an FP32 pair, the
+// projected input is split into pairs once per evaluation, and each product is accumulated with
+// an exact FP32 product (FMA error term), an exact running sum (TwoSum) and a small FP32
 // correction. The result carries about 2^-44 of the sum of the term magnitudes; the only FP64
 // instruction per output is the final addition of the two FP32 halves.
-
-struct DF {
-  float h, l;
-};
-
-// x = xh + xl: xh from the high word (sign, exponent, 20 mantissa bits), xl = the low 32
-// mantissa bits times 2^(e-52), converted with two exact 16-bit pieces. |x| < 2^-74 maps to 0.
-__device__ __forceinline__ DF split_d(double x) {
-  const unsigned int hi = (unsigned int)__double2hiint(x), lo = (unsigned int)__double2loint(x);
-  const int E = (int)((hi >> 20) & 0x7FFu);
-  const unsigned int sign = hi & 0x80000000u;
-  DF r{0.0f, 0.0f};
-  if (E - 1023 + 127 <= 0) return r;
-  r.h = __uint_as_float(sign | ((unsigned int)(E - 1023 + 127) << 23) | ((hi & 0xFFFFFu) << 3));
-  if (E - 948 <= 0 || lo == 0u) return r;
-  const float fa = __fsub_rn(__uint_as_float(0x4B000000u | (lo >> 16)), 8388608.0f);      // exact
-  const float fb = __fsub_rn(__uint_as_float(0x4B000000u | (lo & 0xFFFFu)), 8388608.0f);  // exact
-  const float lf = __fmaf_rn(fa, 65536.0f, fb);                                           // one rounding
-  const float sc = __uint_as_float((unsigned int)(E - 948) << 23);                        // 2^(E-1075)
-  r.l = __uint_as_float(__float_as_uint(__fmul_rn(lf, sc)) ^ sign);
-  return r;
-}
-
-// exact FP32 -> FP64 by bit manipulation (no FP64 instruction); denormals map to 0
-__device__ __forceinline__ double f2d(float f) {
-  const unsigned int b = __float_as_uint(f);
-  const unsigned int fe = (b >> 23) & 0xFFu;
-  if (fe == 0u) return 0.0;
-  const unsigned int hi = (b & 0x80000000u) | ((fe - 127u + 1023u) << 20) | ((b & 0x7FFFFFu) >> 3);
-  const unsigned int lo = (b & 0x7u) << 29;
-  return __hiloint2double((int)hi, (int)lo);
-}
-
-struct Acc {
-  float S = 0.0f, C = 0.0f;
-  __device__ __forceinline__ void add(const float2 c, const DF x) {
-    const float p = __fmul_rn(c.x, x.h);
-    const float e = __fmaf_rn(c.x, x.h, -p);
-    const float small = __fmaf_rn(c.x, x.l, __fmaf_rn(c.y, x.h, e));
-    const float s = __fadd_rn(S, p);
-    const float bp = __fsub_rn(s, S);
-    const float err = __fadd_rn(__fsub_rn(S, __fsub_rn(s, bp)), __fsub_rn(p, bp));
-    S = s;
-    C = __fadd_rn(C, __fadd_rn(err, small));
-  }
-  __device__ __forceinline__ double value() const { return f2d(S) + f2d(C); }
-};
-
-template <bool PROJ>
-struct DFLoader {
-  Loader<PROJ> L;
-  __device__ __forceinline__ DF u(int i, int j, int k) const { return split_d(L.lu(i, j, k)); }
-  __device__ __forceinline__ DF v(int i, int j, int k) const { return split_d(L.lv(i, j, k)); }
-  __device__ __forceinline__ DF w(int i, int j, int k) const { return split_d(L.lw(i, j, k)); }
-  __device__ __forceinline__ DF T(int i, int j, int k) const { return split_d(L.lT(i, j, k)); }
-};
 
 __device__ __forceinline__ float2 cf2(const float2* __restrict__ coef, size_t P, int q, int e) {
   return __ldg(coef + (size_t)q * P + e);
 }
 
-// The interior case of k_apply_df (see there): unmasked loads, each value split once.
-__device__ __forceinline__ void apply_df_interior(const KvGeom& g, const float2* __restrict__ coef,
-                                                  const double* __restrict__ x, size_t P, double* __restrict__ vstar,
-                                                  double* __restrict__ tout, int i, int j, int k) {
+// P_BC x (the input projection of Eq (13)) at every stored entry, split into FP32 pairs: the
+// operator below then loads each input value as a ready pair, with no masks and no splitting.
+__global__ void __launch_bounds__(256) k_split_input(KvGeom g, const double* __restrict__ x, size_t P,
+                                                     float2* __restrict__ xs) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = blockIdx.y * blockDim.y + threadIdx.y;
+  const int k = blockIdx.z;
+  if (i >= g.X || j >= g.Y || k >= g.Z) return;
+  Grid G{g};
+  const Loader<true> L{G, x, x + P, x + 2 * P, x + 3 * P};
+  const int e = G.at(i, j, k);
+  const DF u = df_split(L.lu(i, j, k)), v = df_split(L.lv(i, j, k)), w = df_split(L.lw(i, j, k)),
+           t = df_split(L.lT(i, j, k));
+  xs[e] = make_float2(u.h, u.l);
+  xs[P + e] = make_float2(v.h, v.l);
+  xs[2 * P + e] = make_float2(w.h, w.l);
+  xs[3 * P + e] = make_float2(t.h, t.l);
+}
+
+// y* = J P_BC x with the FP32-pair coefficients and the split projected input xs (output as
+// k_apply). Every cell thread (1 <= i <= nx, ...) reads its 34 distinct input values (all inside
+// the padded array, projected) once and forms the four equations; outputs that are not
+// unknowns at this position are written as 0. MINB: the launch bound's minimum resident blocks,
+// which sets the register budget (more registers, more independent loads in flight; fewer, more
+// resident warps); the autotuner picks the faster.
+template <int MINB>
+__global__ void __launch_bounds__(256, MINB) k_apply_df(KvGeom g, const float2* __restrict__ coef,
+                                                        const float2* __restrict__ xs, size_t P,
+                                                        double* __restrict__ vstar, double* __restrict__ tout) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = blockIdx.y * blockDim.y + threadIdx.y;
+  const int k = blockIdx.z;
+  if (i >= g.X || j >= g.Y || k >= g.Z) return;
   const int sx = 1, sy = g.X, sz = g.X * g.Y;
   const int e = i + sy * j + sz * k;
-  const double* __restrict__ xu = x;
-  const double* __restrict__ xv = x + P;
-  const double* __restrict__ xw = x + 2 * P;
-  const double* __restrict__ xT = x + 3 * P;
-  auto L = [&](const double* __restrict__ f, int off) { return split_d(__ldg(f + e + off)); };
+  if (!(i >= 1 && i <= g.nx && j >= 1 && j <= g.ny && k >= 1 && k <= g.nz)) {
+    vstar[e] = 0.0;
+    vstar[P + e] = 0.0;
+    vstar[2 * P + e] = 0.0;
+    // the insulated walls' temperature nodes are written by their neighbouring cells
+    const bool aa_wall = g.bc == KV_BC_AA && (j == 0 || j == g.ny + 1) && i >= 1 && i <= g.nx && k >= 1 &&
+                         k <= g.nz;
+    if (!aa_wall) tout[e] = 0.0;
+    return;
+  }
+  const float2* __restrict__ xu = xs;
+  const float2* __restrict__ xv = xs + P;
+  const float2* __restrict__ xw = xs + 2 * P;
+  const float2* __restrict__ xT = xs + 3 * P;
+  auto L = [&](const float2* __restrict__ f, int off) {
+    const float2 t = __ldg(f + e + off);
+    return DF{t.x, t.y};
+  };
   // u: own 7 + (i-1, j+1) + (i-1, k+1)
   const DF u0 = L(xu, 0), uxm = L(xu, -sx), uxp = L(xu, sx), uym = L(xu, -sy), uyp = L(xu, sy), uzm = L(xu, -sz),
            uzp = L(xu, sz), uxmyp = L(xu, -sx + sy), uxmzp = L(xu, -sx + sz);
@@ -495,210 +481,92 @@ __device__ __forceinline__ void apply_df_interior(const KvGeom& g, const float2*
   const DF t0 = L(xT, 0), txm = L(xT, -sx), txp = L(xT, sx), tym = L(xT, -sy), typ = L(xT, sy), tzm = L(xT, -sz),
            tzp = L(xT, sz);
   {
-    Acc a;
-    a.add(cf2(coef, P, 0, e), u0);
-    a.add(cf2(coef, P, 1, e), uxm);
-    a.add(cf2(coef, P, 2, e), uxp);
-    a.add(cf2(coef, P, 3, e), uym);
-    a.add(cf2(coef, P, 4, e), uyp);
-    a.add(cf2(coef, P, 5, e), uzm);
-    a.add(cf2(coef, P, 6, e), uzp);
+    DFAcc a;
+    a.fma(cf2(coef, P, 0, e), u0);
+    a.fma(cf2(coef, P, 1, e), uxm);
+    a.fma(cf2(coef, P, 2, e), uxp);
+    a.fma(cf2(coef, P, 3, e), uym);
+    a.fma(cf2(coef, P, 4, e), uyp);
+    a.fma(cf2(coef, P, 5, e), uzm);
+    a.fma(cf2(coef, P, 6, e), uzp);
     const float2 c7 = cf2(coef, P, 7, e), c8 = cf2(coef, P, 8, e);
-    a.add(c7, vym);    // v(i, j-1)
-    a.add(c7, v0);     // v(i, j)
-    a.add(c7, vxpym);  // v(i+1, j-1)
-    a.add(c7, vxp);    // v(i+1, j)
-    a.add(c8, wzm);    // w(i, k-1)
-    a.add(c8, w0);     // w(i, k)
-    a.add(c8, wxpzm);  // w(i+1, k-1)
-    a.add(c8, wxp);    // w(i+1, k)
-    vstar[e] = a.value();
+    a.fma(c7, vym);    // v(i, j-1)
+    a.fma(c7, v0);     // v(i, j)
+    a.fma(c7, vxpym);  // v(i+1, j-1)
+    a.fma(c7, vxp);    // v(i+1, j)
+    a.fma(c8, wzm);    // w(i, k-1)
+    a.fma(c8, w0);     // w(i, k)
+    a.fma(c8, wxpzm);  // w(i+1, k-1)
+    a.fma(c8, wxp);    // w(i+1, k)
+    vstar[e] = i <= g.nx - 1 ? a.value() : 0.0;
   }
   {
-    Acc a;
-    a.add(cf2(coef, P, 9, e), v0);
-    a.add(cf2(coef, P, 10, e), vxm);
-    a.add(cf2(coef, P, 11, e), vxp);
-    a.add(cf2(coef, P, 12, e), vym);
-    a.add(cf2(coef, P, 13, e), vyp);
-    a.add(cf2(coef, P, 14, e), vzm);
-    a.add(cf2(coef, P, 15, e), vzp);
+    DFAcc a;
+    a.fma(cf2(coef, P, 9, e), v0);
+    a.fma(cf2(coef, P, 10, e), vxm);
+    a.fma(cf2(coef, P, 11, e), vxp);
+    a.fma(cf2(coef, P, 12, e), vym);
+    a.fma(cf2(coef, P, 13, e), vyp);
+    a.fma(cf2(coef, P, 14, e), vzm);
+    a.fma(cf2(coef, P, 15, e), vzp);
     const float2 c16 = cf2(coef, P, 16, e), c17 = cf2(coef, P, 17, e);
-    a.add(c16, uxm);    // u(i-1, j)
-    a.add(c16, u0);     // u(i, j)
-    a.add(c16, uxmyp);  // u(i-1, j+1)
-    a.add(c16, uyp);    // u(i, j+1)
-    a.add(c17, wzm);    // w(j, k-1)
-    a.add(c17, w0);     // w(j, k)
-    a.add(c17, wypzm);  // w(j+1, k-1)
-    a.add(c17, wyp);    // w(j+1, k)
-    vstar[P + e] = a.value();
+    a.fma(c16, uxm);    // u(i-1, j)
+    a.fma(c16, u0);     // u(i, j)
+    a.fma(c16, uxmyp);  // u(i-1, j+1)
+    a.fma(c16, uyp);    // u(i, j+1)
+    a.fma(c17, wzm);    // w(j, k-1)
+    a.fma(c17, w0);     // w(j, k)
+    a.fma(c17, wypzm);  // w(j+1, k-1)
+    a.fma(c17, wyp);    // w(j+1, k)
+    vstar[P + e] = j <= g.ny - 1 ? a.value() : 0.0;
   }
   {
-    Acc a;
-    a.add(cf2(coef, P, 18, e), w0);
-    a.add(cf2(coef, P, 19, e), wxm);
-    a.add(cf2(coef, P, 20, e), wxp);
-    a.add(cf2(coef, P, 21, e), wym);
-    a.add(cf2(coef, P, 22, e), wyp);
-    a.add(cf2(coef, P, 23, e), wzm);
-    a.add(cf2(coef, P, 24, e), wzp);
+    DFAcc a;
+    a.fma(cf2(coef, P, 18, e), w0);
+    a.fma(cf2(coef, P, 19, e), wxm);
+    a.fma(cf2(coef, P, 20, e), wxp);
+    a.fma(cf2(coef, P, 21, e), wym);
+    a.fma(cf2(coef, P, 22, e), wyp);
+    a.fma(cf2(coef, P, 23, e), wzm);
+    a.fma(cf2(coef, P, 24, e), wzp);
     const float2 c25 = cf2(coef, P, 25, e), c26 = cf2(coef, P, 26, e);
-    a.add(c25, uxm);    // u(i-1, k)
-    a.add(c25, u0);     // u(i, k)
-    a.add(c25, uxmzp);  // u(i-1, k+1)
-    a.add(c25, uzp);    // u(i, k+1)
-    a.add(c26, vym);    // v(j-1, k)
-    a.add(c26, v0);     // v(j, k)
-    a.add(c26, vymzp);  // v(j-1, k+1)
-    a.add(c26, vzp);    // v(j, k+1)
+    a.fma(c25, uxm);    // u(i-1, k)
+    a.fma(c25, u0);     // u(i, k)
+    a.fma(c25, uxmzp);  // u(i-1, k+1)
+    a.fma(c25, uzp);    // u(i, k+1)
+    a.fma(c26, vym);    // v(j-1, k)
+    a.fma(c26, v0);     // v(j, k)
+    a.fma(c26, vymzp);  // v(j-1, k+1)
+    a.fma(c26, vzp);    // v(j, k+1)
     const float2 half = make_float2(0.5f, 0.0f);
-    a.add(half, t0);
-    a.add(half, tzp);
-    vstar[2 * P + e] = a.value();
+    a.fma(half, t0);
+    a.fma(half, tzp);
+    vstar[2 * P + e] = k <= g.nz - 1 ? a.value() : 0.0;
   }
   {
-    Acc a;
-    a.add(cf2(coef, P, 27, e), t0);
-    a.add(cf2(coef, P, 28, e), txm);
-    a.add(cf2(coef, P, 29, e), txp);
-    a.add(cf2(coef, P, 30, e), tym);
-    a.add(cf2(coef, P, 31, e), typ);
-    a.add(cf2(coef, P, 32, e), tzm);
-    a.add(cf2(coef, P, 33, e), tzp);
+    DFAcc a;
+    a.fma(cf2(coef, P, 27, e), t0);
+    a.fma(cf2(coef, P, 28, e), txm);
+    a.fma(cf2(coef, P, 29, e), txp);
+    a.fma(cf2(coef, P, 30, e), tym);
+    a.fma(cf2(coef, P, 31, e), typ);
+    a.fma(cf2(coef, P, 32, e), tzm);
+    a.fma(cf2(coef, P, 33, e), tzp);
     const float2 c34 = cf2(coef, P, 34, e), c35 = cf2(coef, P, 35, e), c36 = cf2(coef, P, 36, e);
-    a.add(c34, uxm);
-    a.add(c34, u0);
-    a.add(c35, vym);
-    a.add(c35, v0);
-    a.add(c36, wzm);
-    a.add(c36, w0);
-    tout[e] = a.value();
-  }
-}
-
-// y* = J P_BC x with the FP32-pair coefficients (output as k_apply). MINB: the launch bound's
-// minimum resident blocks, which sets the register budget (more registers, more independent
-// loads in flight; fewer, more resident warps); the autotuner picks the faster.
-template <int MINB>
-__global__ void __launch_bounds__(256, MINB) k_apply_df(KvGeom g, const float2* __restrict__ coef,
-                                                        const double* __restrict__ x, size_t P,
-                                                        double* __restrict__ vstar, double* __restrict__ tout) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  const int j = blockIdx.y * blockDim.y + threadIdx.y;
-  const int k = blockIdx.z;
-  // Blocks three or more cells away from every wall: every output is an interior unknown and
-  // every input it reads is one too (and no temperature it reads belongs to an insulated wall
-  // pair), so the loads need no masking; each distinct input value (34 per cell) is loaded and
-  // split once.
-  {
-    const int i0 = blockIdx.x * blockDim.x, j0 = blockIdx.y * blockDim.y;
-    if (i0 >= 3 && i0 + (int)blockDim.x - 1 <= g.nx - 3 && j0 >= 3 && j0 + (int)blockDim.y - 1 <= g.ny - 3 &&
-        k >= 3 && k <= g.nz - 3) {
-      apply_df_interior(g, coef, x, P, vstar, tout, i, j, k);
-      return;
-    }
-  }
-  if (i >= g.X || j >= g.Y || k >= g.Z) return;
-  Grid G{g};
-  const int e = G.at(i, j, k);
-  DFLoader<true> X{Loader<true>{G, x, x + P, x + 2 * P, x + 3 * P}};
-  double ru = 0.0, rv = 0.0, rw = 0.0;
-  if (G.dof_u(i, j, k)) {
-    Acc a;
-    a.add(cf2(coef, P, 0, e), X.u(i, j, k));
-    a.add(cf2(coef, P, 1, e), X.u(i - 1, j, k));
-    a.add(cf2(coef, P, 2, e), X.u(i + 1, j, k));
-    a.add(cf2(coef, P, 3, e), X.u(i, j - 1, k));
-    a.add(cf2(coef, P, 4, e), X.u(i, j + 1, k));
-    a.add(cf2(coef, P, 5, e), X.u(i, j, k - 1));
-    a.add(cf2(coef, P, 6, e), X.u(i, j, k + 1));
-    const float2 c7 = cf2(coef, P, 7, e), c8 = cf2(coef, P, 8, e);
-    a.add(c7, X.v(i, j - 1, k));
-    a.add(c7, X.v(i, j, k));
-    a.add(c7, X.v(i + 1, j - 1, k));
-    a.add(c7, X.v(i + 1, j, k));
-    a.add(c8, X.w(i, j, k - 1));
-    a.add(c8, X.w(i, j, k));
-    a.add(c8, X.w(i + 1, j, k - 1));
-    a.add(c8, X.w(i + 1, j, k));
-    ru = a.value();
-  }
-  vstar[e] = ru;
-  if (G.dof_v(i, j, k)) {
-    Acc a;
-    a.add(cf2(coef, P, 9, e), X.v(i, j, k));
-    a.add(cf2(coef, P, 10, e), X.v(i - 1, j, k));
-    a.add(cf2(coef, P, 11, e), X.v(i + 1, j, k));
-    a.add(cf2(coef, P, 12, e), X.v(i, j - 1, k));
-    a.add(cf2(coef, P, 13, e), X.v(i, j + 1, k));
-    a.add(cf2(coef, P, 14, e), X.v(i, j, k - 1));
-    a.add(cf2(coef, P, 15, e), X.v(i, j, k + 1));
-    const float2 c16 = cf2(coef, P, 16, e), c17 = cf2(coef, P, 17, e);
-    a.add(c16, X.u(i - 1, j, k));
-    a.add(c16, X.u(i, j, k));
-    a.add(c16, X.u(i - 1, j + 1, k));
-    a.add(c16, X.u(i, j + 1, k));
-    a.add(c17, X.w(i, j, k - 1));
-    a.add(c17, X.w(i, j, k));
-    a.add(c17, X.w(i, j + 1, k - 1));
-    a.add(c17, X.w(i, j + 1, k));
-    rv = a.value();
-  }
-  vstar[P + e] = rv;
-  if (G.dof_w(i, j, k)) {
-    Acc a;
-    a.add(cf2(coef, P, 18, e), X.w(i, j, k));
-    a.add(cf2(coef, P, 19, e), X.w(i - 1, j, k));
-    a.add(cf2(coef, P, 20, e), X.w(i + 1, j, k));
-    a.add(cf2(coef, P, 21, e), X.w(i, j - 1, k));
-    a.add(cf2(coef, P, 22, e), X.w(i, j + 1, k));
-    a.add(cf2(coef, P, 23, e), X.w(i, j, k - 1));
-    a.add(cf2(coef, P, 24, e), X.w(i, j, k + 1));
-    const float2 c25 = cf2(coef, P, 25, e), c26 = cf2(coef, P, 26, e);
-    a.add(c25, X.u(i - 1, j, k));
-    a.add(c25, X.u(i, j, k));
-    a.add(c25, X.u(i - 1, j, k + 1));
-    a.add(c25, X.u(i, j, k + 1));
-    a.add(c26, X.v(i, j - 1, k));
-    a.add(c26, X.v(i, j, k));
-    a.add(c26, X.v(i, j - 1, k + 1));
-    a.add(c26, X.v(i, j, k + 1));
-    const float2 half = make_float2(0.5f, 0.0f);
-    a.add(half, X.T(i, j, k));
-    a.add(half, X.T(i, j, k + 1));
-    rw = a.value();
-  }
-  vstar[2 * P + e] = rw;
-  const bool cell = i >= 1 && i <= g.nx && j >= 1 && j <= g.ny && k >= 1 && k <= g.nz;
-  if (cell) {
-    Acc a;
-    a.add(cf2(coef, P, 27, e), X.T(i, j, k));
-    a.add(cf2(coef, P, 28, e), X.T(i - 1, j, k));
-    a.add(cf2(coef, P, 29, e), X.T(i + 1, j, k));
-    a.add(cf2(coef, P, 30, e), X.T(i, j - 1, k));
-    a.add(cf2(coef, P, 31, e), X.T(i, j + 1, k));
-    a.add(cf2(coef, P, 32, e), X.T(i, j, k - 1));
-    a.add(cf2(coef, P, 33, e), X.T(i, j, k + 1));
-    const float2 c34 = cf2(coef, P, 34, e), c35 = cf2(coef, P, 35, e), c36 = cf2(coef, P, 36, e);
-    a.add(c34, X.u(i - 1, j, k));
-    a.add(c34, X.u(i, j, k));
-    a.add(c35, X.v(i, j - 1, k));
-    a.add(c35, X.v(i, j, k));
-    a.add(c36, X.w(i, j, k - 1));
-    a.add(c36, X.w(i, j, k));
+    a.fma(c34, uxm);
+    a.fma(c34, u0);
+    a.fma(c35, vym);
+    a.fma(c35, v0);
+    a.fma(c36, wzm);
+    a.fma(c36, w0);
     const double r = a.value();
     if (g.bc == KV_BC_AA && (j == 1 || j == g.ny)) {
       const double t = (g.tproj == KV_TPROJ_OBLIQUE) ? r : 0.5 * r;
       tout[e] = t;
-      tout[G.at(i, j == 1 ? 0 : g.ny + 1, k)] = t;
+      tout[i + sy * (j == 1 ? 0 : g.ny + 1) + sz * k] = t;
     } else {
       tout[e] = r;
     }
-  } else {
-    const bool aa_wall = g.bc == KV_BC_AA && (j == 0 || j == g.ny + 1) && i >= 1 && i <= g.nx && k >= 1 &&
-                         k <= g.nz;
-    if (!aa_wall) tout[e] = 0.0;
   }
 }
 
@@ -745,10 +613,14 @@ void kv_launch_coef_df(const kv_grid* h, const double* coef, float2* cdf, cudaSt
 void kv_launch_apply_df(const kv_grid* h, const float2* cdf, const double* x, double* vstar, double* tout,
                         cudaStream_t s) {
   const KvGeom& g = h->g;
+  {
+    dim3 block(32, 8, 1), grid((g.X + 31) / 32, (g.Y + 7) / 8, g.Z);
+    k_split_input<<<grid, block, 0, s>>>(g, x, h->P, h->xsplit);
+  }
   const int bx = h->df_bx, by = h->df_by;
   dim3 block(bx, by, 1), grid((g.X + bx - 1) / bx, (g.Y + by - 1) / by, g.Z);
   if (h->df_variant == 0)
-    k_apply_df<3><<<grid, block, 0, s>>>(g, cdf, x, h->P, vstar, tout);
+    k_apply_df<3><<<grid, block, 0, s>>>(g, cdf, h->xsplit, h->P, vstar, tout);
   else
-    k_apply_df<1><<<grid, block, 0, s>>>(g, cdf, x, h->P, vstar, tout);
+    k_apply_df<2><<<grid, block, 0, s>>>(g, cdf, h->xsplit, h->P, vstar, tout);
 }
