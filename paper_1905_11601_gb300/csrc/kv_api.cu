@@ -136,7 +136,7 @@ kv_status simple_project(kv_grid* h, double* yvel, double* p, kv_stats* st) {
     KV_CHECK_CUDA(h, cudaMemsetAsync(h->red, 0, 2 * sizeof(unsigned long long), s));
     { KvPhase ph(h, KV_PH_DIV, 1); kv_launch_divergence(h, src, h->tpd_a, s); }
     if (mixed)
-      kv_launch_poisson_mixed(h, h->tpd_a, phi, st != nullptr, s);
+      kv_launch_poisson_mixed(h, h->tpd_a, phi, st != nullptr, 1, s);  // slices written by the divergence
     else
       kv_launch_poisson(h, h->tpd_a, h->tpd_a, s);
     { KvPhase ph(h, KV_PH_CORRECT, 1); kv_launch_correct(h, src, phi, yvel, p, pass > 1, s, want ? 1 : 0); }
@@ -219,23 +219,22 @@ kv_status autotune_apply(kv_grid* h) {
   h->apply_bx = bx;
   h->apply_by = by;
   if (h->d.precision == KV_PREC_MIXED) {
+    // the double-float kernel: cells per row x rows per block (four equation rows each, <= 512
+    // threads)
+    static const int dcand[][2] = {{32, 1}, {32, 2}, {64, 1}, {32, 4}, {64, 2}, {128, 1}};
     best = 1e30f;
-    int dbx = 32, dby = 8, dv = 0;
-    for (int v = 0; v < 2; ++v)
-      for (auto& c : cand) {
-        h->df_variant = v;
-        h->df_bx = c[0];
-        h->df_by = c[1];
-        if (time_it(true, ms) && ms < best) {
-          best = ms;
-          dbx = c[0];
-          dby = c[1];
-          dv = v;
-        }
+    int dbx = 32, dby = 2;
+    for (auto& c : dcand) {
+      h->df_bx = c[0];
+      h->df_by = c[1];
+      if (time_it(true, ms) && ms < best) {
+        best = ms;
+        dbx = c[0];
+        dby = c[1];
       }
+    }
     h->df_bx = dbx;
     h->df_by = dby;
-    h->df_variant = dv;
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
@@ -403,7 +402,7 @@ kv_status kv_set_base_flow(kv_handle h, const double* base) {
   kv_launch_assemble(h, h->base, h->coef, h->s);
   if (h->d.precision == KV_PREC_MIXED) {
     if (!h->coef_df) {
-      kv_status s = dalloc(h, &h->coef_df, (size_t)KV_NCOEF * h->P);
+      kv_status s = dalloc(h, &h->coef_df, (size_t)KV_NCOEF_DF * h->P);
       if (s != KV_OK) return s;
     }
     if (!h->xsplit) {

@@ -17,6 +17,9 @@ enum { KV_PH_STENCIL = 0, KV_PH_DIV = 1, KV_PH_TPD = 2, KV_PH_CORRECT = 3, KV_PH
 
 // Assembled coefficients of the linearised operator per padded entry (kv_stencil.cu).
 constexpr int KV_NCOEF = 37;
+// coefficients the double-float operator reads (the plus coefficients of the own-field pairs
+// are affine in the minus ones)
+constexpr int KV_NCOEF_DF = 25;
 
 // Device-side description of the uniform MAC grid.
 struct KvGeom {
@@ -41,7 +44,7 @@ struct kv_grid {
 
   double* base = nullptr;   // 4P: U | V | W | Theta
   double* coef = nullptr;   // KV_NCOEF * P: assembled coefficients of J (per base flow)
-  float2* coef_df = nullptr; // KV_PREC_MIXED: the same coefficients as FP32 pairs
+  float2* coef_df = nullptr; // KV_PREC_MIXED, KV_NCOEF_DF * P: FP32 pairs of the coefficients it reads
   float2* xsplit = nullptr;  // KV_PREC_MIXED, 4P: P_BC x split into FP32 pairs (operator input)
   double* vstar = nullptr;  // 3P: momentum right-hand side before the projection
   double* tpd_a = nullptr;  // Nc: divergence / Poisson ping-pong buffers
@@ -63,6 +66,7 @@ struct kv_grid {
   int refine = 0;                        // Poisson refinement sweeps
   __nv_bfloat16* wsl[6] = {};
   __nv_bfloat16* xs[2] = {};
+  float* phi32 = nullptr;                // Nc: phi after the first tensor-core sweep (exact FP32 values)
   size_t xs_slice = 0;                   // elements per data slice
   float* lamf[3] = {};
   CUtensorMap mapA[6], mapB[6];
@@ -91,7 +95,7 @@ struct kv_grid {
 
   // block shape of the linearised-operator kernel, chosen by timing (kv_autotune_apply)
   int apply_bx = 32, apply_by = 8;
-  int df_bx = 32, df_by = 8, df_variant = 0;  // the same for the mixed path's double-float kernel
+  int df_bx = 32, df_by = 2;  // the mixed path's double-float kernel: cells per row, rows per block
   bool tuned = false;
 
   std::string err;
@@ -109,13 +113,15 @@ struct KvPhase {
 
 // kv_umma.cu
 struct KvUmmaEpi {
-  int mode;          // 0: BF16 slices of D; 1: slices of D / Lambda (Eq 17); 2: phi64 += D
+  int mode;          // 0: BF16 slices of D; 1: slices of D / Lambda (Eq 17); 2: phi64 += D; 3: phi64 = D;
+                     // 4: phi32 = D; 5: phi64 = phi32 + D
   int M, R;          // output rows / columns
   int nb, na;        // r = a * nb + b; output address (m * na + a) * pitch + b
   int pitch;         // padded fastest extent of the output layout
   size_t slice;      // elements between output slices
   __nv_bfloat16* out;
-  double* phi;       // mode 2
+  double* phi;       // modes 2, 3, 5
+  float* phi32;      // modes 4, 5
   const float* lz;   // mode 1: eigenvalues of the contracted (m) axis, then of a and b
   const float* la;
   const float* lb;
@@ -130,12 +136,25 @@ int kv_umma_box_rows_b();
 cudaError_t kv_launch_umma_axis(const CUtensorMap* mapA, const CUtensorMap* mapB, int K, const KvUmmaEpi& ep,
                                 unsigned int* err, cudaStream_t s);
 
+// Three BF16 slices of r (r ~ s1 + s2 + s3 to about 2^-24 |r|) at offset o of slice buffers
+// `slice` elements apart: the tensor-core solve's input format.
+__device__ __forceinline__ void kv_store_bf16x3(__nv_bfloat16* xs, size_t slice, size_t o, float r) {
+  const __nv_bfloat16 s1 = __float2bfloat16_rn(r);
+  const float r1 = r - __bfloat162float(s1);
+  const __nv_bfloat16 s2 = __float2bfloat16_rn(r1);
+  const __nv_bfloat16 s3 = __float2bfloat16_rn(r1 - __bfloat162float(s2));
+  xs[o] = s1;
+  xs[slice + o] = s2;
+  xs[2 * slice + o] = s3;
+}
+
 // kv_mixed.cu
 kv_status kv_mixed_setup(kv_grid* h, const double* const fwd[3], const double* const inv[3]);
 void kv_mixed_free(kv_grid* h);
 // phi = L^+ b to FP64-class accuracy: BF16-split tensor-core TPF solve + double-float residual
 // refinement (stats: also reduce max |r| into h->rmax)
-void kv_launch_poisson_mixed(kv_grid* h, const double* b, double* phi, int stats, cudaStream_t s);
+// slices_ready: the BF16 slices of b are already in h->xs[0] (written by the divergence)
+void kv_launch_poisson_mixed(kv_grid* h, const double* b, double* phi, int stats, int slices_ready, cudaStream_t s);
 kv_status kv_mixed_selftest_timeout(kv_grid* h, int* device_error);
 
 // kv_api.cu: sets the thread's message returned by kv_last_error(NULL)

@@ -2,7 +2,7 @@
 // contractions on the tensor cores (BF16 slices, FP32 accumulation; kv_umma.cu), won back to
 // FP64-class accuracy by iterative refinement with a double-float residual:
 //
-//   phi = 0;  r = b
+//   phi = 0;  r = b   (the divergence writes r's slices; the first sweep stores phi, as FP32)
 //   repeat S times:  phi += TPF(r)   (six tcgen05 contractions, the last one adds into phi)
 //                    r = b - L phi   (7-point Neumann Laplacian in double-float, written as BF16 slices)
 //
@@ -22,11 +22,17 @@ int pad8(int n) { return (n + 7) & ~7; }
 
 // r = b - L phi (L = D G with homogeneous Neumann walls) in double-float arithmetic on the FP32
 // pipe (kv_df.cuh; about 2^-44 of |b| + |L phi|, far below what one tensor-core sweep resolves),
-// then three BF16 slices of r into the first contraction's input layout [k][j][i_pad].
-// phi == nullptr means phi = 0. With rmax, max |r| is reduced per block into *rmax.
+// then three BF16 slices of r into the first contraction's input layout [k][j][i_pad]. PhiT:
+// float for phi after the first sweep (exact FP32 values, no split needed), double after
+// later sweeps. With rmax, max |r| is reduced per block into *rmax.
+__device__ __forceinline__ DF phi_pair(float x) { return DF{x, 0.0f}; }
+__device__ __forceinline__ DF phi_pair(double x) { return df_split(x); }
+
+template <typename PhiT>
 __global__ void __launch_bounds__(256) k_residual_slices(KvGeom g, const double* __restrict__ b,
-                                                         const double* __restrict__ phi, __nv_bfloat16* __restrict__ xs,
-                                                         size_t slice, int pitch, unsigned long long* rmax) {
+                                                         const PhiT* __restrict__ phi, __nv_bfloat16* __restrict__ xs,
+                                                         size_t slice, int pitch, unsigned long long* rmax,
+                                                         float2 ihx2, float2 ihy2, float2 ihz2) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   const int j = blockIdx.y * blockDim.y + threadIdx.y;
   const int k = blockIdx.z;
@@ -34,30 +40,20 @@ __global__ void __launch_bounds__(256) k_residual_slices(KvGeom g, const double*
   if (i < g.nx && j < g.ny) {
     const size_t sx = 1, sy = g.nx, sz = (size_t)g.nx * g.ny;
     const size_t e = i + sy * j + sz * k;
-    DF r = df_split(__ldg(b + e));
-    if (phi) {
-      // homogeneous Neumann walls: a missing neighbour contributes as the cell itself
-      const double cd = __ldg(phi + e);
-      const DF c = df_split(cd);
-      const DF c2 = DF{2.0f * c.h, 2.0f * c.l};  // exact
-      const DF xm = df_split(i > 0 ? __ldg(phi + e - sx) : cd), xp = df_split(i < g.nx - 1 ? __ldg(phi + e + sx) : cd);
-      const DF ym = df_split(j > 0 ? __ldg(phi + e - sy) : cd), yp = df_split(j < g.ny - 1 ? __ldg(phi + e + sy) : cd);
-      const DF zm = df_split(k > 0 ? __ldg(phi + e - sz) : cd), zp = df_split(k < g.nz - 1 ? __ldg(phi + e + sz) : cd);
-      const DF lx = df_mul(df_sub(df_add(xm, xp), c2), df_split(g.ihx2));
-      const DF ly = df_mul(df_sub(df_add(ym, yp), c2), df_split(g.ihy2));
-      const DF lz = df_mul(df_sub(df_add(zm, zp), c2), df_split(g.ihz2));
-      r = df_sub(r, df_add(df_add(lx, ly), lz));
-    }
+    // homogeneous Neumann walls: a missing neighbour contributes as the cell itself
+    const PhiT cv = __ldg(phi + e);
+    const DF c = phi_pair(cv);
+    const DF c2 = DF{2.0f * c.h, 2.0f * c.l};  // exact
+    const DF xm = phi_pair(i > 0 ? __ldg(phi + e - sx) : cv), xp = phi_pair(i < g.nx - 1 ? __ldg(phi + e + sx) : cv);
+    const DF ym = phi_pair(j > 0 ? __ldg(phi + e - sy) : cv), yp = phi_pair(j < g.ny - 1 ? __ldg(phi + e + sy) : cv);
+    const DF zm = phi_pair(k > 0 ? __ldg(phi + e - sz) : cv), zp = phi_pair(k < g.nz - 1 ? __ldg(phi + e + sz) : cv);
+    const DF lx = df_mul(df_sub(df_add(xm, xp), c2), DF{ihx2.x, ihx2.y});
+    const DF ly = df_mul(df_sub(df_add(ym, yp), c2), DF{ihy2.x, ihy2.y});
+    const DF lz = df_mul(df_sub(df_add(zm, zp), c2), DF{ihz2.x, ihz2.y});
+    const DF r = df_sub(df_split(__ldg(b + e)), df_add(df_add(lx, ly), lz));
     const float rf = __fadd_rn(r.h, r.l);
     rv = fabsf(rf);
-    const __nv_bfloat16 s1 = __float2bfloat16_rn(rf);
-    const float r1 = rf - __bfloat162float(s1);
-    const __nv_bfloat16 s2 = __float2bfloat16_rn(r1);
-    const __nv_bfloat16 s3 = __float2bfloat16_rn(r1 - __bfloat162float(s2));
-    const size_t o = ((size_t)k * g.ny + j) * pitch + i;
-    xs[o] = s1;
-    xs[slice + o] = s2;
-    xs[2 * slice + o] = s3;
+    kv_store_bf16x3(xs, slice, ((size_t)k * g.ny + j) * pitch + i, rf);
   }
   if (rmax) {
     for (int off = 16; off > 0; off >>= 1) rv = fmaxf(rv, __shfl_xor_sync(0xffffffffu, rv, off));
@@ -71,6 +67,22 @@ __global__ void __launch_bounds__(256) k_residual_slices(KvGeom g, const double*
       atomicMax(rmax, (unsigned long long)__double_as_longlong(df_f2d(m)));
     }
   }
+}
+
+// b's three BF16 slices (the first sweep's right-hand side, r = b)
+__global__ void __launch_bounds__(256) k_rhs_slices(KvGeom g, const double* __restrict__ b,
+                                                    __nv_bfloat16* __restrict__ xs, size_t slice, int pitch) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = blockIdx.y * blockDim.y + threadIdx.y;
+  const int k = blockIdx.z;
+  if (i >= g.nx || j >= g.ny) return;
+  const DF r = df_split(__ldg(b + i + (size_t)g.nx * (j + (size_t)g.ny * k)));
+  kv_store_bf16x3(xs, slice, ((size_t)k * g.ny + j) * pitch + i, __fadd_rn(r.h, r.l));
+}
+
+float2 host_pair(double x) {
+  const float h = (float)x;
+  return make_float2(h, (float)(x - (double)h));
 }
 
 // Three BF16 slices of an M x K FP64 matrix, rows padded to pitch (zero padding).
@@ -130,6 +142,7 @@ kv_status kv_mixed_setup(kv_grid* h, const double* const fwd[3], const double* c
   if ((e = cudaMalloc(&h->derr, sizeof(unsigned int))) != cudaSuccess) goto fail;
   if ((e = cudaMemset(h->derr, 0, sizeof(unsigned int))) != cudaSuccess) goto fail;
   if ((e = cudaMalloc(&h->rmax, sizeof(unsigned long long))) != cudaSuccess) goto fail;
+  if ((e = cudaMalloc(&h->phi32, h->Nc * sizeof(float))) != cudaSuccess) goto fail;
   for (int p = 0; p < 6; ++p) {
     const int a = kPass[p].axis;
     const int K = n[a], M = n[a];
@@ -153,18 +166,19 @@ void kv_mixed_free(kv_grid* h) {
   for (int a = 0; a < 3; ++a) cudaFree(h->lamf[a]);
   cudaFree(h->derr);
   cudaFree(h->rmax);
+  cudaFree(h->phi32);
 }
 
-void kv_launch_poisson_mixed(kv_grid* h, const double* b, double* phi, int stats, cudaStream_t s) {
+void kv_launch_poisson_mixed(kv_grid* h, const double* b, double* phi, int stats, int slices_ready, cudaStream_t s) {
   const KvGeom& g = h->g;
   const int n[3] = {g.nx, g.ny, g.nz};
   dim3 rb(32, 8, 1), rg((g.nx + 31) / 32, (g.ny + 7) / 8, g.nz);
-  cudaMemsetAsync(phi, 0, h->Nc * sizeof(double), s);
   if (stats) cudaMemsetAsync(h->rmax, 0, sizeof(unsigned long long), s);
-  {
+  if (!slices_ready) {
     KvPhase ph(h, KV_PH_REFINE, 1);
-    k_residual_slices<<<rg, rb, 0, s>>>(g, b, nullptr, h->xs[0], h->xs_slice, pad8(g.nx), nullptr);
+    k_rhs_slices<<<rg, rb, 0, s>>>(g, b, h->xs[0], h->xs_slice, pad8(g.nx));
   }
+  const float2 cx = host_pair(g.ihx2), cy = host_pair(g.ihy2), cz = host_pair(g.ihz2);
   for (int sweep = 0; sweep < h->refine; ++sweep) {
     for (int p = 0; p < 6; ++p) {
       const PassSpec& ps = kPass[p];
@@ -176,8 +190,13 @@ void kv_launch_poisson_mixed(kv_grid* h, const double* b, double* phi, int stats
       ep.pitch = pad8(n[ps.b]);
       ep.slice = h->xs_slice;
       ep.out = h->xs[(p + 1) % 2];
-      ep.mode = (p == 2) ? 1 : (p == 5 ? 2 : 0);
+      // the last contraction writes phi: the first of several sweeps as exact FP32 values (the
+      // residual then reads 4-byte values it need not split), the second as phi32 + D in FP64,
+      // later ones by adding; a single sweep stores FP64 directly
+      const bool single = h->refine == 1;
+      ep.mode = (p == 2) ? 1 : (p == 5 ? (sweep == 0 ? (single ? 3 : 4) : (sweep == 1 ? 5 : 2)) : 0);
       ep.phi = phi;
+      ep.phi32 = h->phi32;
       ep.lz = h->lamf[ps.axis];
       ep.la = h->lamf[ps.a];
       ep.lb = h->lamf[ps.b];
@@ -186,7 +205,11 @@ void kv_launch_poisson_mixed(kv_grid* h, const double* b, double* phi, int stats
     }
     if (sweep + 1 < h->refine) {
       KvPhase ph(h, KV_PH_REFINE, 1);
-      k_residual_slices<<<rg, rb, 0, s>>>(g, b, phi, h->xs[0], h->xs_slice, pad8(g.nx), stats ? h->rmax : nullptr);
+      unsigned long long* rm = stats ? h->rmax : nullptr;
+      if (sweep == 0)
+        k_residual_slices<float><<<rg, rb, 0, s>>>(g, b, h->phi32, h->xs[0], h->xs_slice, pad8(g.nx), rm, cx, cy, cz);
+      else
+        k_residual_slices<double><<<rg, rb, 0, s>>>(g, b, phi, h->xs[0], h->xs_slice, pad8(g.nx), rm, cx, cy, cz);
     }
   }
 }

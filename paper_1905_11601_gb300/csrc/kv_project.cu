@@ -103,8 +103,11 @@ __global__ void __launch_bounds__(256) k_correct(KvGeom g, const double* __restr
 
 // ---- the same two kernels in double-float arithmetic (mixed precision; kv_df.cuh) ----------
 
+// b = D v* in double-float; with xs also b's three BF16 slices in the tensor-core solve's input
+// layout [k][j][i_pad] (the first sweep's right-hand side)
 __global__ void __launch_bounds__(256) k_divergence_df(KvGeom g, const double* __restrict__ vel, size_t P,
-                                                       double* __restrict__ b, float2 ihx, float2 ihy, float2 ihz) {
+                                                       double* __restrict__ b, float2 ihx, float2 ihy, float2 ihz,
+                                                       __nv_bfloat16* __restrict__ xs, size_t slice, int pitch) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x + 1;
   const int j = blockIdx.y * blockDim.y + threadIdx.y + 1;
   const int k = blockIdx.z + 1;
@@ -116,7 +119,9 @@ __global__ void __launch_bounds__(256) k_divergence_df(KvGeom g, const double* _
   const DF dx = df_mul(df_sub(df_split(__ldg(u + e)), df_split(__ldg(u + e - 1))), DF{ihx.x, ihx.y});
   const DF dy = df_mul(df_sub(df_split(__ldg(v + e)), df_split(__ldg(v + e - g.X))), DF{ihy.x, ihy.y});
   const DF dz = df_mul(df_sub(df_split(__ldg(w + e)), df_split(__ldg(w + e - g.X * g.Y))), DF{ihz.x, ihz.y});
-  b[(i - 1) + (size_t)g.nx * ((j - 1) + (size_t)g.ny * (k - 1))] = df_value(df_add(df_add(dx, dy), dz));
+  const DF d = df_add(df_add(dx, dy), dz);
+  b[(i - 1) + (size_t)g.nx * ((j - 1) + (size_t)g.ny * (k - 1))] = df_value(d);
+  if (xs) kv_store_bf16x3(xs, slice, ((size_t)(k - 1) * g.ny + (j - 1)) * pitch + (i - 1), __fadd_rn(d.h, d.l));
 }
 
 struct CorrDF {
@@ -226,7 +231,8 @@ void kv_launch_divergence(const kv_grid* h, const double* vel, double* b, cudaSt
   const KvGeom& g = h->g;
   dim3 block(32, 8, 1), grid((g.nx + 31) / 32, (g.ny + 7) / 8, g.nz);
   if (h->d.precision == KV_PREC_MIXED)
-    k_divergence_df<<<grid, block, 0, s>>>(g, vel, h->P, b, pair_of(g.ihx), pair_of(g.ihy), pair_of(g.ihz));
+    k_divergence_df<<<grid, block, 0, s>>>(g, vel, h->P, b, pair_of(g.ihx), pair_of(g.ihy), pair_of(g.ihz), h->xs[0],
+                                           h->xs_slice, (g.nx + 7) & ~7);
   else
     k_divergence<<<grid, block, 0, s>>>(g, vel, h->P, b);
 }

@@ -237,16 +237,29 @@ __device__ __forceinline__ void load_u(const double* __restrict__ p, size_t e, s
 // in flight) while the registers allow it.
 template <int Q>
 __host__ __device__ constexpr int dots_unroll() { return Q <= 12 ? 2 : 1; }
-template <int Q>
-__host__ __device__ constexpr int update_unroll() { return Q <= 8 ? 2 : 1; }
 
-// Block partials of <V_q, w> (q < Q) and ||w||^2 in double-float, as k_dots.
+// Both pipes at once: the FP64 pipe (2 multiply-adds per SM and clock) keeps up with HBM for
+// about 0.6 multiply-adds per 8-byte entry streamed, so the first K64 basis vectors of a sweep
+// run in plain FP64 and the rest in double-float on the FP32 pipe. The first sweep streams
+// Q + 1 vectors and spends one FP64 multiply-add per FP64 vector; the fused sweep streams Q + 2
+// and spends two.
+template <int Q>
+__host__ __device__ constexpr int dots_k64() { return (3 * (Q + 1)) / 5 < Q ? (3 * (Q + 1)) / 5 : Q; }
+template <int Q>
+__host__ __device__ constexpr int update_k64() { return (3 * (Q + 2)) / 10; }
+
+// Block partials of <V_q, w> (q < Q) and ||w||^2, as k_dots: q < K64 in FP64, the others and
+// the norm in double-float.
 template <int Q>
 __global__ void __launch_bounds__(RT) k_dots_df(const double* __restrict__ V, size_t ld,
                                                 const double* __restrict__ w, size_t len, int nrm, int vec,
                                                 double* __restrict__ partials) {
   constexpr int U = dots_unroll<Q>();
+  constexpr int K64 = dots_k64<Q>();
   __shared__ double sm[Q + 1][RT / 32];
+  double a64[K64 > 0 ? K64 : 1];
+#pragma unroll
+  for (int q = 0; q < K64; ++q) a64[q] = 0.0;
   DFAcc acc[Q + 1];
   bool bad = false;
   for (size_t e = ((size_t)blockIdx.x * RT + threadIdx.x) * U; e < len; e += (size_t)gridDim.x * RT * U) {
@@ -258,16 +271,18 @@ __global__ void __launch_bounds__(RT) k_dots_df(const double* __restrict__ V, si
 #pragma unroll
     for (int u = 0; u < U; ++u) {
       bad |= !gs_in_range(wd[u]);
+#pragma unroll
+      for (int q = 0; q < K64; ++q) a64[q] = fma(v[q][u], wd[u], a64[q]);
       const DF we = df_split(wd[u]);
 #pragma unroll
-      for (int q = 0; q < Q; ++q) acc[q].fma(df_split(v[q][u]), we);
+      for (int q = K64; q < Q; ++q) acc[q].fma(df_split(v[q][u]), we);
       acc[Q].fma(we, we);
     }
   }
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 #pragma unroll
   for (int q = 0; q <= Q; ++q) {
-    double x = acc[q].value();
+    double x = q < K64 ? a64[q < K64 ? q : 0] : acc[q].value();
     if (q == Q && bad) x = __longlong_as_double(0x7FF8000000000000LL);  // NaN: out of range
     const double t = warp_sum(x);
     if (lane == 0) sm[q][warp] = t;
@@ -281,60 +296,80 @@ __global__ void __launch_bounds__(RT) k_dots_df(const double* __restrict__ V, si
   }
 }
 
-// w -= sum_q c[q] V_q in double-float, fused with the block partials of <V_q, w> and ||w||^2 of
-// the updated w, as k_update_dot. The updated w is stored rounded to FP64.
+// w -= sum_q c[q] V_q, fused with the block partials of <V_q, w> and ||w||^2 of the updated w,
+// as k_update_dot: the update and inner products of q < K64 in FP64 (the update first, on the
+// FP64 value of w), the others and the norm in double-float. The updated w is stored rounded
+// to FP64. One entry per thread and iteration; for Q <= 12 the next entry's loads are issued
+// before the current entry's arithmetic (software prefetch), so the memory stream continues
+// while a warp computes.
 template <int Q>
 __global__ void __launch_bounds__(RT, 2) k_update_dot_df(const double* __restrict__ V, size_t ld,
                                                          const double* __restrict__ c, double* __restrict__ w,
-                                                         size_t len, int vec, double* __restrict__ partials) {
-  constexpr int U = update_unroll<Q>();
+                                                         size_t len, double* __restrict__ partials) {
+  constexpr int K64 = update_k64<Q>();
+  constexpr bool PF = Q <= 12;
   __shared__ DF cs[Q];
+  __shared__ double c64[K64 > 0 ? K64 : 1];
   __shared__ double sm[Q + 1][RT / 32];
   if (threadIdx.x < Q) {
     const DF x = df_split(c[threadIdx.x]);
     cs[threadIdx.x] = DF{-x.h, -x.l};
+    if ((int)threadIdx.x < K64) c64[threadIdx.x] = c[threadIdx.x];
   }
   __syncthreads();
+  double a64[K64 > 0 ? K64 : 1];
+#pragma unroll
+  for (int q = 0; q < K64; ++q) a64[q] = 0.0;
   DFAcc acc[Q + 1];
-  for (size_t e = ((size_t)blockIdx.x * RT + threadIdx.x) * U; e < len; e += (size_t)gridDim.x * RT * U) {
-    double vd[Q][U];
-    double wd[U];
+  const size_t stride = (size_t)gridDim.x * RT;
+  size_t e = (size_t)blockIdx.x * RT + threadIdx.x;
+  double vn[Q], wn = 0.0;
+  if (PF && e < len) {
 #pragma unroll
-    for (int q = 0; q < Q; ++q) load_u<U>(V + (size_t)q * ld, e, len, vec, vd[q]);
-    load_u<U>(w, e, len, vec, wd);
-    double wo[U];
+    for (int q = 0; q < Q; ++q) vn[q] = __ldg(V + (size_t)q * ld + e);
+    wn = w[e];
+  }
+  for (; e < len; e += stride) {
+    double vd[Q], wd;
+    if (PF) {
 #pragma unroll
-    for (int u = 0; u < U; ++u) {
-      const DF w0 = df_split(wd[u]);
-      DFAcc a;
-      a.start(w0);
-      DF v[Q];
+      for (int q = 0; q < Q; ++q) vd[q] = vn[q];
+      wd = wn;
+      const size_t en = e + stride;
+      if (en < len) {
 #pragma unroll
-      for (int q = 0; q < Q; ++q) {
-        v[q] = df_split(vd[q][u]);
-        a.fma(cs[q], v[q]);
-      }
-      const DF w1 = a.pair();
-      wo[u] = df_f2d(w1.h) + df_f2d(w1.l);
-#pragma unroll
-      for (int q = 0; q < Q; ++q) acc[q].fma(v[q], w1);
-      acc[Q].fma(w1, w1);
-    }
-    if constexpr (U == 2) {
-      if (vec && e + 1 < len) {
-        *reinterpret_cast<double2*>(w + e) = make_double2(wo[0], wo[1]);
-      } else {
-        w[e] = wo[0];
-        if (e + 1 < len) w[e + 1] = wo[1];
+        for (int q = 0; q < Q; ++q) vn[q] = __ldg(V + (size_t)q * ld + en);
+        wn = w[en];
       }
     } else {
-      w[e] = wo[0];
+#pragma unroll
+      for (int q = 0; q < Q; ++q) vd[q] = __ldg(V + (size_t)q * ld + e);
+      wd = w[e];
     }
+    double w64 = wd;
+#pragma unroll
+    for (int q = 0; q < K64; ++q) w64 = fma(-c64[q], vd[q], w64);
+    DFAcc a;
+    a.start(df_split(w64));
+    DF v[Q];
+#pragma unroll
+    for (int q = K64; q < Q; ++q) {
+      v[q] = df_split(vd[q]);
+      a.fma(cs[q], v[q]);
+    }
+    const DF w1 = a.pair();
+    const double wo = df_f2d(w1.h) + df_f2d(w1.l);
+    w[e] = wo;
+#pragma unroll
+    for (int q = 0; q < K64; ++q) a64[q] = fma(vd[q], wo, a64[q]);
+#pragma unroll
+    for (int q = K64; q < Q; ++q) acc[q].fma(v[q], w1);
+    acc[Q].fma(w1, w1);
   }
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 #pragma unroll
   for (int q = 0; q <= Q; ++q) {
-    const double t = warp_sum(acc[q].value());
+    const double t = warp_sum(q < K64 ? a64[q < K64 ? q : 0] : acc[q].value());
     if (lane == 0) sm[q][warp] = t;
   }
   __syncthreads();
@@ -405,13 +440,12 @@ void kv_launch_dots_norm(const double* V, size_t ld, int nq, const double* w, si
 void kv_launch_update_dot(const double* V, size_t ld, int nq, const double* c, double* w, size_t len,
                           double* partials, double* h2, int df, cudaStream_t s) {
   int nb = RB;
-  const int vec = aligned16(V, ld, w);
   if (df) {
     switch (nq) {
 #define KV_UPD_DF_CASE(Qn) \
   case Qn:                 \
     nb = wave_blocks<k_update_dot_df<Qn>>();                             \
-    k_update_dot_df<Qn><<<nb, RT, 0, s>>>(V, ld, c, w, len, vec, partials); \
+    k_update_dot_df<Qn><<<nb, RT, 0, s>>>(V, ld, c, w, len, partials); \
     break;
       KV_FOR_EACH_NQ(KV_UPD_DF_CASE)
 #undef KV_UPD_DF_CASE

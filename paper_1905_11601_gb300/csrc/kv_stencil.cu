@@ -434,30 +434,65 @@ __global__ void __launch_bounds__(256) k_split_input(KvGeom g, const double* __r
   xs[3 * P + e] = make_float2(t.h, t.l);
 }
 
+// Own-field coefficients in pairs: along one axis, the "plus" coefficient of an equation is an
+// affine function of its "minus" coefficient, c+ = alpha + beta c-, with beta = -1 (interior),
+// -1/4 (first cell next to a wall) or -4 (last cell) and alpha = 2, 3/2 or 6 times diff / h^2
+// (diff = nu for the momentum equations, kappa for the energy equation): both come from the same
+// advecting velocity a through the derivative weights of d1_cell / d2_cell / d1_face / d2_face,
+// c- = diff d2.m - a d1.m and c+ = diff d2.p - a d1.p. So the double-float operator stores c-
+// only and forms c- x- + c+ x+ = c- (x- + beta x+) + alpha x+ (beta is a power of two: the
+// scaled pair is exact). alpha[d][axis][class]: d = 0 momentum, 1 energy; class 0 interior or
+// face axis, 1 first cell, 2 last cell.
+struct DfAlpha {
+  float2 a[2][3][3];
+};
+
+__device__ __forceinline__ int wall_class(int t, int n) { return t == 1 ? 1 : (t == n ? 2 : 0); }
+
+__device__ __forceinline__ float2 alpha_of(const DfAlpha& al, int d, int axis, int cls) {
+  const float2 a0 = al.a[d][axis][0], a1 = al.a[d][axis][1], a2 = al.a[d][axis][2];
+  return cls == 0 ? a0 : (cls == 1 ? a1 : a2);
+}
+
+__device__ __forceinline__ float beta_of(int cls) { return cls == 0 ? -1.0f : (cls == 1 ? -0.25f : -4.0f); }
+
+// a += c- x- + c+ x+ along one axis (see DfAlpha)
+__device__ __forceinline__ void own_axis(DFAcc& a, const float2 cm, const DF xm, const DF xp, const float2 alpha,
+                                         const float beta) {
+  a.fma(cm, df_add(xm, DF{beta * xp.h, beta * xp.l}));
+  a.fma(alpha, xp);
+}
+
+// Double-float coefficient q (KV_NCOEF_DF of them) = assembled coefficient kDfFromFull[q]: per
+// equation the centre, the three minus coefficients and the cross-term factors.
+__constant__ int kDfFromFull[KV_NCOEF_DF] = {0,  1,  3,  5,  7,  8,  9,  10, 12, 14, 16, 17, 18,
+                                             19, 21, 23, 25, 26, 27, 28, 30, 32, 34, 35, 36};
+
 // y* = J P_BC x with the FP32-pair coefficients and the split projected input xs (output as
-// k_apply). Every cell thread (1 <= i <= nx, ...) reads its 34 distinct input values (all inside
-// the padded array, projected) once and forms the four equations; outputs that are not
-// unknowns at this position are written as 0. MINB: the launch bound's minimum resident blocks,
-// which sets the register budget (more registers, more independent loads in flight; fewer, more
-// resident warps); the autotuner picks the faster.
-template <int MINB>
-__global__ void __launch_bounds__(256, MINB) k_apply_df(KvGeom g, const float2* __restrict__ coef,
-                                                        const float2* __restrict__ xs, size_t P,
-                                                        double* __restrict__ vstar, double* __restrict__ tout) {
+// k_apply). One thread per (cell, equation): threadIdx.y = 4 row + eq, eq = 0..3 for u, v, w,
+// T, so each warp forms one equation for consecutive cells (no divergence) and keeps only that
+// equation's inputs (15-17 pairs) and coefficients (6-7 pairs) live; the inputs shared between
+// equations come from L1. Cells are 1 <= i <= nx, ... (every input they read is inside the
+// padded array, projected); outputs that are not unknowns at a position are written as 0.
+__global__ void __launch_bounds__(512) k_apply_df(KvGeom g, const float2* __restrict__ coef,
+                                                  const float2* __restrict__ xs, size_t P,
+                                                  double* __restrict__ vstar, double* __restrict__ tout, DfAlpha al) {
+  const int eq = threadIdx.y & 3;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  const int j = blockIdx.y * blockDim.y + threadIdx.y;
+  const int j = blockIdx.y * (blockDim.y >> 2) + (threadIdx.y >> 2);
   const int k = blockIdx.z;
   if (i >= g.X || j >= g.Y || k >= g.Z) return;
   const int sx = 1, sy = g.X, sz = g.X * g.Y;
   const int e = i + sy * j + sz * k;
   if (!(i >= 1 && i <= g.nx && j >= 1 && j <= g.ny && k >= 1 && k <= g.nz)) {
-    vstar[e] = 0.0;
-    vstar[P + e] = 0.0;
-    vstar[2 * P + e] = 0.0;
-    // the insulated walls' temperature nodes are written by their neighbouring cells
-    const bool aa_wall = g.bc == KV_BC_AA && (j == 0 || j == g.ny + 1) && i >= 1 && i <= g.nx && k >= 1 &&
-                         k <= g.nz;
-    if (!aa_wall) tout[e] = 0.0;
+    if (eq < 3) {
+      vstar[(size_t)eq * P + e] = 0.0;
+    } else {
+      // the insulated walls' temperature nodes are written by their neighbouring cells
+      const bool aa_wall = g.bc == KV_BC_AA && (j == 0 || j == g.ny + 1) && i >= 1 && i <= g.nx && k >= 1 &&
+                           k <= g.nz;
+      if (!aa_wall) tout[e] = 0.0;
+    }
     return;
   }
   const float2* __restrict__ xu = xs;
@@ -468,97 +503,70 @@ __global__ void __launch_bounds__(256, MINB) k_apply_df(KvGeom g, const float2* 
     const float2 t = __ldg(f + e + off);
     return DF{t.x, t.y};
   };
-  // u: own 7 + (i-1, j+1) + (i-1, k+1)
-  const DF u0 = L(xu, 0), uxm = L(xu, -sx), uxp = L(xu, sx), uym = L(xu, -sy), uyp = L(xu, sy), uzm = L(xu, -sz),
-           uzp = L(xu, sz), uxmyp = L(xu, -sx + sy), uxmzp = L(xu, -sx + sz);
-  // v: own 7 + (i+1, j-1) + (j-1, k+1)
-  const DF v0 = L(xv, 0), vxm = L(xv, -sx), vxp = L(xv, sx), vym = L(xv, -sy), vyp = L(xv, sy), vzm = L(xv, -sz),
-           vzp = L(xv, sz), vxpym = L(xv, sx - sy), vymzp = L(xv, -sy + sz);
-  // w: own 7 + (i+1, k-1) + (j+1, k-1)
-  const DF w0 = L(xw, 0), wxm = L(xw, -sx), wxp = L(xw, sx), wym = L(xw, -sy), wyp = L(xw, sy), wzm = L(xw, -sz),
-           wzp = L(xw, sz), wxpzm = L(xw, sx - sz), wypzm = L(xw, sy - sz);
-  // T: own 7 (the buoyancy reads T(k) and T(k+1))
-  const DF t0 = L(xT, 0), txm = L(xT, -sx), txp = L(xT, sx), tym = L(xT, -sy), typ = L(xT, sy), tzm = L(xT, -sz),
-           tzp = L(xT, sz);
-  {
-    DFAcc a;
-    a.fma(cf2(coef, P, 0, e), u0);
-    a.fma(cf2(coef, P, 1, e), uxm);
-    a.fma(cf2(coef, P, 2, e), uxp);
-    a.fma(cf2(coef, P, 3, e), uym);
-    a.fma(cf2(coef, P, 4, e), uyp);
-    a.fma(cf2(coef, P, 5, e), uzm);
-    a.fma(cf2(coef, P, 6, e), uzp);
-    const float2 c7 = cf2(coef, P, 7, e), c8 = cf2(coef, P, 8, e);
-    a.fma(c7, vym);    // v(i, j-1)
-    a.fma(c7, v0);     // v(i, j)
-    a.fma(c7, vxpym);  // v(i+1, j-1)
-    a.fma(c7, vxp);    // v(i+1, j)
-    a.fma(c8, wzm);    // w(i, k-1)
-    a.fma(c8, w0);     // w(i, k)
-    a.fma(c8, wxpzm);  // w(i+1, k-1)
-    a.fma(c8, wxp);    // w(i+1, k)
+  auto C = [&](int q) { return __ldg(coef + (size_t)q * P + e); };
+  // wall classes of this cell along the cell-type axes
+  const int ci = wall_class(i, g.nx), cj = wall_class(j, g.ny), ck = wall_class(k, g.nz);
+  DFAcc a;
+  if (eq == 0) {  // u on x-faces (x is the face axis); cross terms: 4-point sums of v and w
+    const float2 c0 = C(0), cx = C(1), cy = C(2), cz = C(3), c7 = C(4), c8 = C(5);
+    a.fma(c0, L(xu, 0));
+    own_axis(a, cx, L(xu, -sx), L(xu, sx), alpha_of(al, 0, 0, 0), -1.0f);
+    own_axis(a, cy, L(xu, -sy), L(xu, sy), alpha_of(al, 0, 1, cj), beta_of(cj));
+    own_axis(a, cz, L(xu, -sz), L(xu, sz), alpha_of(al, 0, 2, ck), beta_of(ck));
+    a.fma(c7, L(xv, -sy));       // v(i, j-1)
+    a.fma(c7, L(xv, 0));         // v(i, j)
+    a.fma(c7, L(xv, sx - sy));   // v(i+1, j-1)
+    a.fma(c7, L(xv, sx));        // v(i+1, j)
+    a.fma(c8, L(xw, -sz));       // w(i, k-1)
+    a.fma(c8, L(xw, 0));         // w(i, k)
+    a.fma(c8, L(xw, sx - sz));   // w(i+1, k-1)
+    a.fma(c8, L(xw, sx));        // w(i+1, k)
     vstar[e] = i <= g.nx - 1 ? a.value() : 0.0;
-  }
-  {
-    DFAcc a;
-    a.fma(cf2(coef, P, 9, e), v0);
-    a.fma(cf2(coef, P, 10, e), vxm);
-    a.fma(cf2(coef, P, 11, e), vxp);
-    a.fma(cf2(coef, P, 12, e), vym);
-    a.fma(cf2(coef, P, 13, e), vyp);
-    a.fma(cf2(coef, P, 14, e), vzm);
-    a.fma(cf2(coef, P, 15, e), vzp);
-    const float2 c16 = cf2(coef, P, 16, e), c17 = cf2(coef, P, 17, e);
-    a.fma(c16, uxm);    // u(i-1, j)
-    a.fma(c16, u0);     // u(i, j)
-    a.fma(c16, uxmyp);  // u(i-1, j+1)
-    a.fma(c16, uyp);    // u(i, j+1)
-    a.fma(c17, wzm);    // w(j, k-1)
-    a.fma(c17, w0);     // w(j, k)
-    a.fma(c17, wypzm);  // w(j+1, k-1)
-    a.fma(c17, wyp);    // w(j+1, k)
+  } else if (eq == 1) {  // v on y-faces
+    const float2 c0 = C(6), cx = C(7), cy = C(8), cz = C(9), c16 = C(10), c17 = C(11);
+    a.fma(c0, L(xv, 0));
+    own_axis(a, cx, L(xv, -sx), L(xv, sx), alpha_of(al, 0, 0, ci), beta_of(ci));
+    own_axis(a, cy, L(xv, -sy), L(xv, sy), alpha_of(al, 0, 1, 0), -1.0f);
+    own_axis(a, cz, L(xv, -sz), L(xv, sz), alpha_of(al, 0, 2, ck), beta_of(ck));
+    a.fma(c16, L(xu, -sx));      // u(i-1, j)
+    a.fma(c16, L(xu, 0));        // u(i, j)
+    a.fma(c16, L(xu, -sx + sy)); // u(i-1, j+1)
+    a.fma(c16, L(xu, sy));       // u(i, j+1)
+    a.fma(c17, L(xw, -sz));      // w(j, k-1)
+    a.fma(c17, L(xw, 0));        // w(j, k)
+    a.fma(c17, L(xw, sy - sz));  // w(j+1, k-1)
+    a.fma(c17, L(xw, sy));       // w(j+1, k)
     vstar[P + e] = j <= g.ny - 1 ? a.value() : 0.0;
-  }
-  {
-    DFAcc a;
-    a.fma(cf2(coef, P, 18, e), w0);
-    a.fma(cf2(coef, P, 19, e), wxm);
-    a.fma(cf2(coef, P, 20, e), wxp);
-    a.fma(cf2(coef, P, 21, e), wym);
-    a.fma(cf2(coef, P, 22, e), wyp);
-    a.fma(cf2(coef, P, 23, e), wzm);
-    a.fma(cf2(coef, P, 24, e), wzp);
-    const float2 c25 = cf2(coef, P, 25, e), c26 = cf2(coef, P, 26, e);
-    a.fma(c25, uxm);    // u(i-1, k)
-    a.fma(c25, u0);     // u(i, k)
-    a.fma(c25, uxmzp);  // u(i-1, k+1)
-    a.fma(c25, uzp);    // u(i, k+1)
-    a.fma(c26, vym);    // v(j-1, k)
-    a.fma(c26, v0);     // v(j, k)
-    a.fma(c26, vymzp);  // v(j-1, k+1)
-    a.fma(c26, vzp);    // v(j, k+1)
+  } else if (eq == 2) {  // w on z-faces, with the buoyancy 0.5 (T_k + T_k+1)
+    const float2 c0 = C(12), cx = C(13), cy = C(14), cz = C(15), c25 = C(16), c26 = C(17);
+    a.fma(c0, L(xw, 0));
+    own_axis(a, cx, L(xw, -sx), L(xw, sx), alpha_of(al, 0, 0, ci), beta_of(ci));
+    own_axis(a, cy, L(xw, -sy), L(xw, sy), alpha_of(al, 0, 1, cj), beta_of(cj));
+    own_axis(a, cz, L(xw, -sz), L(xw, sz), alpha_of(al, 0, 2, 0), -1.0f);
+    a.fma(c25, L(xu, -sx));      // u(i-1, k)
+    a.fma(c25, L(xu, 0));        // u(i, k)
+    a.fma(c25, L(xu, -sx + sz)); // u(i-1, k+1)
+    a.fma(c25, L(xu, sz));       // u(i, k+1)
+    a.fma(c26, L(xv, -sy));      // v(j-1, k)
+    a.fma(c26, L(xv, 0));        // v(j, k)
+    a.fma(c26, L(xv, -sy + sz)); // v(j-1, k+1)
+    a.fma(c26, L(xv, sz));       // v(j, k+1)
     const float2 half = make_float2(0.5f, 0.0f);
-    a.fma(half, t0);
-    a.fma(half, tzp);
+    a.fma(half, L(xT, 0));
+    a.fma(half, L(xT, sz));
     vstar[2 * P + e] = k <= g.nz - 1 ? a.value() : 0.0;
-  }
-  {
-    DFAcc a;
-    a.fma(cf2(coef, P, 27, e), t0);
-    a.fma(cf2(coef, P, 28, e), txm);
-    a.fma(cf2(coef, P, 29, e), txp);
-    a.fma(cf2(coef, P, 30, e), tym);
-    a.fma(cf2(coef, P, 31, e), typ);
-    a.fma(cf2(coef, P, 32, e), tzm);
-    a.fma(cf2(coef, P, 33, e), tzp);
-    const float2 c34 = cf2(coef, P, 34, e), c35 = cf2(coef, P, 35, e), c36 = cf2(coef, P, 36, e);
-    a.fma(c34, uxm);
-    a.fma(c34, u0);
-    a.fma(c35, vym);
-    a.fma(c35, v0);
-    a.fma(c36, wzm);
-    a.fma(c36, w0);
+  } else {  // T on cells
+    const float2 c0 = C(18), cx = C(19), cy = C(20), cz = C(21), c34 = C(22), c35 = C(23), c36 = C(24);
+    a.fma(c0, L(xT, 0));
+    own_axis(a, cx, L(xT, -sx), L(xT, sx), alpha_of(al, 1, 0, ci), beta_of(ci));
+    own_axis(a, cy, L(xT, -sy), L(xT, sy), alpha_of(al, 1, 1, cj), beta_of(cj));
+    own_axis(a, cz, L(xT, -sz), L(xT, sz), alpha_of(al, 1, 2, ck), beta_of(ck));
+    a.fma(c34, L(xu, -sx));
+    a.fma(c34, L(xu, 0));
+    a.fma(c35, L(xv, -sy));
+    a.fma(c35, L(xv, 0));
+    a.fma(c36, L(xw, -sz));
+    a.fma(c36, L(xw, 0));
     const double r = a.value();
     if (g.bc == KV_BC_AA && (j == 1 || j == g.ny)) {
       const double t = (g.tproj == KV_TPROJ_OBLIQUE) ? r : 0.5 * r;
@@ -570,13 +578,22 @@ __global__ void __launch_bounds__(256, MINB) k_apply_df(KvGeom g, const float2* 
   }
 }
 
-// FP32-pair copy of the FP64 coefficients: ch = fp32(c), cl = fp32(c - ch).
-__global__ void __launch_bounds__(256) k_coef_df(const double* __restrict__ coef, float2* __restrict__ cdf, size_t n) {
+// FP32-pair copy of the assembled coefficients the double-float operator reads
+// (kDfFromFull): ch = fp32(c), cl = fp32(c - ch).
+__global__ void __launch_bounds__(256) k_coef_df(const double* __restrict__ coef, float2* __restrict__ cdf, size_t P) {
+  const size_t n = (size_t)KV_NCOEF_DF * P;
   for (size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += (size_t)gridDim.x * blockDim.x) {
-    const double c = coef[t];
+    const size_t q = t / P, e = t - q * P;
+    const double c = coef[(size_t)kDfFromFull[q] * P + e];
     const float h = __double2float_rn(c);
     cdf[t] = make_float2(h, __double2float_rn(c - (double)h));
   }
+}
+
+// x as an FP32 pair (host side)
+float2 host_pair(double x) {
+  const float h = (float)x;
+  return make_float2(h, (float)(x - (double)h));
 }
 
 }  // namespace
@@ -607,7 +624,7 @@ void kv_launch_apply(const kv_grid* h, const double* coef, const double* x, doub
 }
 
 void kv_launch_coef_df(const kv_grid* h, const double* coef, float2* cdf, cudaStream_t s) {
-  k_coef_df<<<4 * 152, 256, 0, s>>>(coef, cdf, (size_t)KV_NCOEF * h->P);
+  k_coef_df<<<4 * 152, 256, 0, s>>>(coef, cdf, h->P);
 }
 
 void kv_launch_apply_df(const kv_grid* h, const float2* cdf, const double* x, double* vstar, double* tout,
@@ -617,10 +634,15 @@ void kv_launch_apply_df(const kv_grid* h, const float2* cdf, const double* x, do
     dim3 block(32, 8, 1), grid((g.X + 31) / 32, (g.Y + 7) / 8, g.Z);
     k_split_input<<<grid, block, 0, s>>>(g, x, h->P, h->xsplit);
   }
-  const int bx = h->df_bx, by = h->df_by;
-  dim3 block(bx, by, 1), grid((g.X + bx - 1) / bx, (g.Y + by - 1) / by, g.Z);
-  if (h->df_variant == 0)
-    k_apply_df<3><<<grid, block, 0, s>>>(g, cdf, h->xsplit, h->P, vstar, tout);
-  else
-    k_apply_df<2><<<grid, block, 0, s>>>(g, cdf, h->xsplit, h->P, vstar, tout);
+  // alpha = {2, 3/2, 6} diff / h^2 per axis (interior, first cell, last cell)
+  DfAlpha al;
+  const double diff[2] = {g.nu, g.kappa}, ih2[3] = {g.ihx * g.ihx, g.ihy * g.ihy, g.ihz * g.ihz};
+  const double fac[3] = {2.0, 1.5, 6.0};
+  for (int d = 0; d < 2; ++d)
+    for (int ax = 0; ax < 3; ++ax)
+      for (int c = 0; c < 3; ++c) al.a[d][ax][c] = host_pair(fac[c] * diff[d] * ih2[ax]);
+  // df_by rows of cells per block, four equation warps-rows each
+  const int bx = h->df_bx, rows = h->df_by;
+  dim3 block(bx, 4 * rows, 1), grid((g.X + bx - 1) / bx, (g.Y + rows - 1) / rows, g.Z);
+  k_apply_df<<<grid, block, 0, s>>>(g, cdf, h->xsplit, h->P, vstar, tout, al);
 }

@@ -23,6 +23,7 @@
 #include <cuda.h>
 #include <cuda_bf16.h>
 
+#include "kv_df.cuh"
 #include "kv_internal.cuh"
 
 namespace {
@@ -237,7 +238,8 @@ __global__ void __launch_bounds__(THREADS, 1)
     float* tb = epi + (warp - 2) * 32 * EPI_STRIDE;
     // groups of 4 outputs are contiguous and 8-byte aligned (slices) or 32-byte aligned (phi)
     // when the inner extent and R are multiples of 4 (and the slice pitch and size are)
-    const bool vec4 = (ep.R % 4 == 0) && (ep.mode == 2 || (ep.nb % 4 == 0 && ep.pitch % 4 == 0 && ep.slice % 4 == 0));
+    const bool to_phi = ep.mode >= 2;
+    const bool vec4 = (ep.R % 4 == 0) && (to_phi || (ep.nb % 4 == 0 && ep.pitch % 4 == 0 && ep.slice % 4 == 0));
     int lt = 0;
     for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++lt) {
       const int buf = lt & 1;
@@ -259,7 +261,7 @@ __global__ void __launch_bounds__(THREADS, 1)
           const int r = r0 + c + cc;
           if (r < ep.R) {  // R is a multiple of 4 here, so r < R covers all four columns
             int a = 0, bcol = r;
-            if (ep.mode != 2) {
+            if (!to_phi) {
               a = r / ep.nb;
               bcol = r - a * ep.nb;
             }
@@ -270,15 +272,29 @@ __global__ void __launch_bounds__(THREADS, 1)
               float d[4];
 #pragma unroll
               for (int t2 = 0; t2 < 4; ++t2) d[t2] = tb[(cc + t2) * EPI_STRIDE + row];
-              if (ep.mode == 2) {
-                double2* p = reinterpret_cast<double2*>(ep.phi + (size_t)m * ep.R + r);
-                double2 p0 = p[0], p1 = p[1];
-                p0.x += (double)d[0];
-                p0.y += (double)d[1];
-                p1.x += (double)d[2];
-                p1.y += (double)d[3];
-                p[0] = p0;
-                p[1] = p1;
+              if (to_phi) {
+                const size_t o = (size_t)m * ep.R + r;
+                if (ep.mode == 4) {
+                  *reinterpret_cast<float4*>(ep.phi32 + o) = make_float4(d[0], d[1], d[2], d[3]);
+                } else {
+                  double2* p = reinterpret_cast<double2*>(ep.phi + o);
+                  double2 p0 = make_double2(df_f2d(d[0]), df_f2d(d[1])), p1 = make_double2(df_f2d(d[2]), df_f2d(d[3]));
+                  if (ep.mode == 2) {
+                    const double2 q0 = p[0], q1 = p[1];
+                    p0.x += q0.x;
+                    p0.y += q0.y;
+                    p1.x += q1.x;
+                    p1.y += q1.y;
+                  } else if (ep.mode == 5) {
+                    const float4 q = *reinterpret_cast<const float4*>(ep.phi32 + o);
+                    p0.x += df_f2d(q.x);
+                    p0.y += df_f2d(q.y);
+                    p1.x += df_f2d(q.z);
+                    p1.y += df_f2d(q.w);
+                  }
+                  p[0] = p0;
+                  p[1] = p1;
+                }
               } else {
                 if (ep.mode == 1) {
 #pragma unroll
@@ -301,7 +317,7 @@ __global__ void __launch_bounds__(THREADS, 1)
           const int r = r0 + c + lane;
           if (r < ep.R) {
             int a = 0, bcol = r;
-            if (ep.mode != 2) {
+            if (!to_phi) {
               a = r / ep.nb;
               bcol = r - a * ep.nb;
             }
@@ -309,8 +325,14 @@ __global__ void __launch_bounds__(THREADS, 1)
               const int m = mrow0 + row;
               if (m >= ep.M) break;
               float d = tb[lane * EPI_STRIDE + row];
-              if (ep.mode == 2) {
-                ep.phi[(size_t)m * ep.R + r] += (double)d;
+              if (to_phi) {
+                const size_t o = (size_t)m * ep.R + r;
+                if (ep.mode == 4)
+                  ep.phi32[o] = d;
+                else if (ep.mode == 5)
+                  ep.phi[o] = df_f2d(ep.phi32[o]) + df_f2d(d);
+                else
+                  ep.phi[o] = ep.mode == 2 ? ep.phi[o] + df_f2d(d) : df_f2d(d);
               } else {
                 if (ep.mode == 1) {
                   const float lam = ep.lz[m] + ep.la[a] + ep.lb[bcol];
