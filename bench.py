@@ -505,7 +505,7 @@ def run_ours(args):
                    "d2h_bytes_per_step": vec_bytes,
                    "path": "kv_krylov_vector_host, mixed precision (pinned host x and y, copies on the handle's stream)"},
            "gpu_launches": launches, "roofline": roof, "clocks": mx["clocks"],
-           "rel_err_vs_fp64": mx["err"],
+           "rel_err_vs_fp64": mx["err"], "tuning": mx["g"].tuning(),
            "phases": {k: {"ms_per_step": v["ms"] / args.steps, "share": v["share"],
                           "launches_per_step": v["launches"] / args.steps} for k, v in mx["phases"].items()},
            "fp64_plain": {"value": fp["value"], "ms_per_step": fp["ms"] / args.steps,

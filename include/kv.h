@@ -185,7 +185,7 @@ kv_status kv_newton_residual(kv_handle h, const double* S, double* F, double* no
    enabled, per-phase CUDA-event timings on the handle's stream. Phases: 0 = linearised
    operator stencil, 1 = divergence, 2 = TPF Poisson contractions (one timing per per-axis
    contraction launch), 3 = velocity correction, 4 = Arnoldi normalisation (and third
-   Gram-Schmidt sweep), 5 = FP64 refinement residuals of the mixed-precision Poisson solve,
+   Gram-Schmidt sweep), 5 = refinement residuals of the mixed-precision Poisson solve,
    6 = first Gram-Schmidt sweep (inner products), 7 = fused update + second-pass inner products.
    kv_profile_enable synchronises the stream and clears all counters. */
 kv_status kv_profile_enable(kv_handle h, int on);
@@ -194,6 +194,13 @@ kv_status kv_profile_enable(kv_handle h, int on);
    output pointer (host) may be NULL. */
 kv_status kv_profile_get(kv_handle h, int phase, double* total_ms, long long* timed_launches,
                          long long* launches);
+
+/* The configuration the autotuner chose at the first kv_set_base_flow (cfg: host array of 5
+   ints): cfg[0] x cfg[1], the FP64 operator's thread block; for KV_PREC_MIXED the double-float
+   operator: cfg[2] = 0 (split pass, then cfg[3] cells x cfg[4] rows of cells per block) or 1
+   (the 2.5D march, cfg[4] z-planes per block); cfg[2..4] = -1 for KV_PREC_FP64. KV_ERR_STATE
+   before the first base flow. */
+kv_status kv_tuning(kv_handle h, int* cfg);
 
 /* Allocation-free Krylov vector, for callers that cannot allocate device memory (code that
    runs under an allocator it does not own, inside a fixed memory budget, or in a plug-in that

@@ -219,20 +219,24 @@ kv_status autotune_apply(kv_grid* h) {
   h->apply_bx = bx;
   h->apply_by = by;
   if (h->d.precision == KV_PREC_MIXED) {
-    // the double-float kernel: cells per row x rows per block (four equation rows each, <= 512
-    // threads)
-    static const int dcand[][2] = {{32, 1}, {32, 2}, {64, 1}, {32, 4}, {64, 2}, {128, 1}};
+    // the double-float operator: variant 0 (split pass, then cells per row x rows per block, four
+    // equation rows each, <= 512 threads) or variant 1 (the 2.5D march, planes per block)
+    static const int dcand[][3] = {{0, 32, 1}, {0, 32, 2}, {0, 64, 1}, {0, 32, 4}, {0, 64, 2}, {0, 128, 1},
+                                   {1, 0, 16}, {1, 0, 32}, {1, 0, 64}};
     best = 1e30f;
-    int dbx = 32, dby = 2;
+    int dv = 0, dbx = 32, dby = 2;
     for (auto& c : dcand) {
-      h->df_bx = c[0];
-      h->df_by = c[1];
+      h->df_variant = c[0];
+      h->df_bx = c[1];
+      h->df_by = c[2];
       if (time_it(true, ms) && ms < best) {
         best = ms;
-        dbx = c[0];
-        dby = c[1];
+        dv = c[0];
+        dbx = c[1];
+        dby = c[2];
       }
     }
+    h->df_variant = dv;
     h->df_bx = dbx;
     h->df_by = dby;
   }
@@ -664,6 +668,19 @@ kv_status kv_profile_enable(kv_handle h, int on) {
     h->launches[q] = 0;
   }
   h->prof_on = on != 0;
+  return KV_OK;
+}
+
+kv_status kv_tuning(kv_handle h, int* cfg) {
+  if (!h) return KV_ERR_ARG;
+  if (!cfg) return fail(h, KV_ERR_ARG, "kv_tuning: cfg is NULL");
+  if (!h->tuned) return fail(h, KV_ERR_STATE, "kv_tuning: no base flow set yet");
+  const bool mixed = h->d.precision == KV_PREC_MIXED;
+  cfg[0] = h->apply_bx;
+  cfg[1] = h->apply_by;
+  cfg[2] = mixed ? h->df_variant : -1;
+  cfg[3] = mixed ? h->df_bx : -1;
+  cfg[4] = mixed ? h->df_by : -1;
   return KV_OK;
 }
 

@@ -95,7 +95,7 @@ struct kv_grid {
 
   // block shape of the linearised-operator kernel, chosen by timing (kv_autotune_apply)
   int apply_bx = 32, apply_by = 8;
-  int df_bx = 32, df_by = 2;  // the mixed path's double-float kernel: cells per row, rows per block
+  int df_variant = 0, df_bx = 32, df_by = 2;  // the mixed path's double-float operator (kv_stencil.cu)
   bool tuned = false;
 
   std::string err;

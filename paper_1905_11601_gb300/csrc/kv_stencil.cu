@@ -411,10 +411,6 @@ __global__ void __launch_bounds__(256) k_apply(KvGeom g, const double* __restric
 // correction. The result carries about 2^-44 of the sum of the term magnitudes; the only FP64
 // instruction per output is the final addition of the two FP32 halves.
 
-__device__ __forceinline__ float2 cf2(const float2* __restrict__ coef, size_t P, int q, int e) {
-  return __ldg(coef + (size_t)q * P + e);
-}
-
 // P_BC x (the input projection of Eq (13)) at every stored entry, split into FP32 pairs: the
 // operator below then loads each input value as a ready pair, with no masks and no splitting.
 __global__ void __launch_bounds__(256) k_split_input(KvGeom g, const double* __restrict__ x, size_t P,
@@ -578,6 +574,215 @@ __global__ void __launch_bounds__(512) k_apply_df(KvGeom g, const float2* __rest
   }
 }
 
+// ---- the same operator as a 2.5D march (no separate split pass) -----------------------------
+//
+// A block owns a tile of MB_X x MB_Y cells and walks a chunk of kc z-planes. It keeps four
+// planes of the projected input (P_BC x, split into FP32 pairs, with a one-cell halo) in shared
+// memory: at step k it issues the FP64 loads of plane k+2, forms the equations of plane k from
+// planes k-1..k+1 (one thread per cell and equation, as k_apply_df), then projects, splits and
+// stores plane k+2 into the slot plane k-2 used, and synchronises once. Each input value is thus
+// read from HBM once per block (plus a two-plane halo per chunk) and split once, and the
+// coefficients of plane k+1 are prefetched into registers while plane k is computed.
+constexpr int MB_X = 32, MB_Y = 4;
+constexpr int MT_X = MB_X + 2, MT_Y = MB_Y + 2, MPTS = MT_X * MT_Y;
+constexpr int MTHREADS = MB_X * MB_Y * 4;
+constexpr int MVALS = 4 * MPTS;                                 // values per plane (4 fields)
+constexpr int MPER = (MVALS + MTHREADS - 1) / MTHREADS;         // values per thread per plane
+
+struct MarchIn {
+  int f, i, j;  // field, padded i, j of one value this thread loads (f < 0: none)
+};
+
+__device__ __forceinline__ double proj_value(const Loader<true>& L, int f, int i, int j, int k) {
+  return f == 0 ? L.lu(i, j, k) : (f == 1 ? L.lv(i, j, k) : (f == 2 ? L.lw(i, j, k) : L.lT(i, j, k)));
+}
+
+__global__ void __launch_bounds__(MTHREADS, 2) k_apply_df_march(KvGeom g, const float2* __restrict__ coef,
+                                                                const double* __restrict__ x, size_t P,
+                                                                double* __restrict__ vstar,
+                                                                double* __restrict__ tout, DfAlpha al, int kc) {
+  __shared__ float2 xt[4][4][MPTS];  // [slot][field][point]
+  const int tid = threadIdx.x;
+  const int tx = tid & 31, warp = tid >> 5;
+  const int ty = warp % MB_Y, eq = warp / MB_Y;
+  const int i = 1 + blockIdx.x * MB_X + tx, j = 1 + blockIdx.y * MB_Y + ty;
+  const int k0 = 1 + blockIdx.z * kc;
+  const int k1 = min(k0 + kc, g.nz + 1);  // planes k0 .. k1-1
+  const bool active = i <= g.nx && j <= g.ny;
+  Grid G{g};
+  const Loader<true> LD{G, x, x + P, x + 2 * P, x + 3 * P};
+  // the values this thread loads for every plane
+  MarchIn mi[MPER];
+#pragma unroll
+  for (int r = 0; r < MPER; ++r) {
+    const int v = tid + r * MTHREADS;
+    mi[r].f = -1;
+    if (v < MVALS) {
+      const int f = v / MPTS, pt = v - f * MPTS;
+      const int ii = blockIdx.x * MB_X + pt % MT_X, jj = blockIdx.y * MB_Y + pt / MT_X;
+      if (ii <= g.nx + 1 && jj <= g.ny + 1) mi[r] = MarchIn{f, ii, jj};
+    }
+  }
+  auto fetch = [&](int kk, double (&val)[MPER]) {
+#pragma unroll
+    for (int r = 0; r < MPER; ++r) val[r] = mi[r].f >= 0 ? proj_value(LD, mi[r].f, mi[r].i, mi[r].j, kk) : 0.0;
+  };
+  auto put = [&](int slot, const double (&val)[MPER]) {
+#pragma unroll
+    for (int r = 0; r < MPER; ++r) {
+      const int v = tid + r * MTHREADS;
+      if (v < MVALS) {
+        const DF d = df_split(val[r]);
+        xt[slot][v / MPTS][v % MPTS] = make_float2(d.h, d.l);
+      }
+    }
+  };
+  {
+    double val[MPER];
+    for (int kk = k0 - 1; kk <= k0 + 1; ++kk) {
+      fetch(kk, val);
+      put(kk & 3, val);
+    }
+  }
+  __syncthreads();
+  const int ci = wall_class(i, g.nx), cj = wall_class(j, g.ny);
+  const int sy = g.X, sz = g.X * g.Y;
+  const int q0 = eq == 0 ? 0 : (eq == 1 ? 6 : (eq == 2 ? 12 : 18));
+  const int nqe = eq == 3 ? 7 : 6;
+  float2 cn[7];
+  auto coefs = [&](int kk, float2 (&c)[7]) {
+    const size_t e = (size_t)i + (size_t)sy * j + (size_t)sz * kk;
+#pragma unroll
+    for (int q = 0; q < 7; ++q) c[q] = (active && q < nqe) ? __ldg(coef + (size_t)(q0 + q) * P + e) : make_float2(0.f, 0.f);
+  };
+  coefs(k0, cn);
+  const int pc = (ty + 1) * MT_X + (tx + 1);  // this cell's point in the tile
+  for (int k = k0; k < k1; ++k) {
+    const bool more = k + 1 < k1;
+    double nxt[MPER];
+    if (more) fetch(k + 2, nxt);
+    float2 c[7];
+#pragma unroll
+    for (int q = 0; q < 7; ++q) c[q] = cn[q];
+    if (more) coefs(k + 1, cn);
+    if (active) {
+      const int sm = (k - 1) & 3, s0 = k & 3, sp = (k + 1) & 3;
+      // input value of field f at offset (di, dj) in plane slot sl
+      auto X = [&](int sl, int f, int di, int dj) {
+        const float2 t = xt[sl][f][pc + di + MT_X * dj];
+        return DF{t.x, t.y};
+      };
+      const int ck = wall_class(k, g.nz);
+      const size_t e = (size_t)i + (size_t)sy * j + (size_t)sz * k;
+      DFAcc a;
+      if (eq == 0) {
+        a.fma(c[0], X(s0, 0, 0, 0));
+        own_axis(a, c[1], X(s0, 0, -1, 0), X(s0, 0, 1, 0), alpha_of(al, 0, 0, 0), -1.0f);
+        own_axis(a, c[2], X(s0, 0, 0, -1), X(s0, 0, 0, 1), alpha_of(al, 0, 1, cj), beta_of(cj));
+        own_axis(a, c[3], X(sm, 0, 0, 0), X(sp, 0, 0, 0), alpha_of(al, 0, 2, ck), beta_of(ck));
+        a.fma(c[4], X(s0, 1, 0, -1));  // v(i, j-1)
+        a.fma(c[4], X(s0, 1, 0, 0));   // v(i, j)
+        a.fma(c[4], X(s0, 1, 1, -1));  // v(i+1, j-1)
+        a.fma(c[4], X(s0, 1, 1, 0));   // v(i+1, j)
+        a.fma(c[5], X(sm, 2, 0, 0));   // w(i, k-1)
+        a.fma(c[5], X(s0, 2, 0, 0));   // w(i, k)
+        a.fma(c[5], X(sm, 2, 1, 0));   // w(i+1, k-1)
+        a.fma(c[5], X(s0, 2, 1, 0));   // w(i+1, k)
+        vstar[e] = i <= g.nx - 1 ? a.value() : 0.0;
+      } else if (eq == 1) {
+        a.fma(c[0], X(s0, 1, 0, 0));
+        own_axis(a, c[1], X(s0, 1, -1, 0), X(s0, 1, 1, 0), alpha_of(al, 0, 0, ci), beta_of(ci));
+        own_axis(a, c[2], X(s0, 1, 0, -1), X(s0, 1, 0, 1), alpha_of(al, 0, 1, 0), -1.0f);
+        own_axis(a, c[3], X(sm, 1, 0, 0), X(sp, 1, 0, 0), alpha_of(al, 0, 2, ck), beta_of(ck));
+        a.fma(c[4], X(s0, 0, -1, 0));  // u(i-1, j)
+        a.fma(c[4], X(s0, 0, 0, 0));   // u(i, j)
+        a.fma(c[4], X(s0, 0, -1, 1));  // u(i-1, j+1)
+        a.fma(c[4], X(s0, 0, 0, 1));   // u(i, j+1)
+        a.fma(c[5], X(sm, 2, 0, 0));   // w(j, k-1)
+        a.fma(c[5], X(s0, 2, 0, 0));   // w(j, k)
+        a.fma(c[5], X(sm, 2, 0, 1));   // w(j+1, k-1)
+        a.fma(c[5], X(s0, 2, 0, 1));   // w(j+1, k)
+        vstar[P + e] = j <= g.ny - 1 ? a.value() : 0.0;
+      } else if (eq == 2) {
+        a.fma(c[0], X(s0, 2, 0, 0));
+        own_axis(a, c[1], X(s0, 2, -1, 0), X(s0, 2, 1, 0), alpha_of(al, 0, 0, ci), beta_of(ci));
+        own_axis(a, c[2], X(s0, 2, 0, -1), X(s0, 2, 0, 1), alpha_of(al, 0, 1, cj), beta_of(cj));
+        own_axis(a, c[3], X(sm, 2, 0, 0), X(sp, 2, 0, 0), alpha_of(al, 0, 2, 0), -1.0f);
+        a.fma(c[4], X(s0, 0, -1, 0));  // u(i-1, k)
+        a.fma(c[4], X(s0, 0, 0, 0));   // u(i, k)
+        a.fma(c[4], X(sp, 0, -1, 0));  // u(i-1, k+1)
+        a.fma(c[4], X(sp, 0, 0, 0));   // u(i, k+1)
+        a.fma(c[5], X(s0, 1, 0, -1));  // v(j-1, k)
+        a.fma(c[5], X(s0, 1, 0, 0));   // v(j, k)
+        a.fma(c[5], X(sp, 1, 0, -1));  // v(j-1, k+1)
+        a.fma(c[5], X(sp, 1, 0, 0));   // v(j, k+1)
+        const float2 half = make_float2(0.5f, 0.0f);
+        a.fma(half, X(s0, 3, 0, 0));
+        a.fma(half, X(sp, 3, 0, 0));
+        vstar[2 * P + e] = k <= g.nz - 1 ? a.value() : 0.0;
+      } else {
+        a.fma(c[0], X(s0, 3, 0, 0));
+        own_axis(a, c[1], X(s0, 3, -1, 0), X(s0, 3, 1, 0), alpha_of(al, 1, 0, ci), beta_of(ci));
+        own_axis(a, c[2], X(s0, 3, 0, -1), X(s0, 3, 0, 1), alpha_of(al, 1, 1, cj), beta_of(cj));
+        own_axis(a, c[3], X(sm, 3, 0, 0), X(sp, 3, 0, 0), alpha_of(al, 1, 2, ck), beta_of(ck));
+        a.fma(c[4], X(s0, 0, -1, 0));
+        a.fma(c[4], X(s0, 0, 0, 0));
+        a.fma(c[5], X(s0, 1, 0, -1));
+        a.fma(c[5], X(s0, 1, 0, 0));
+        a.fma(c[6], X(sm, 2, 0, 0));
+        a.fma(c[6], X(s0, 2, 0, 0));
+        const double r = a.value();
+        if (g.bc == KV_BC_AA && (j == 1 || j == g.ny)) {
+          const double t = (g.tproj == KV_TPROJ_OBLIQUE) ? r : 0.5 * r;
+          tout[e] = t;
+          tout[(size_t)i + (size_t)sy * (j == 1 ? 0 : g.ny + 1) + (size_t)sz * k] = t;
+        } else {
+          tout[e] = r;
+        }
+      }
+    }
+    if (more) put((k + 2) & 3, nxt);
+    __syncthreads();
+  }
+}
+
+// The padded-boundary entries of v* and T* (walls, edges, corners: 0; the insulated walls'
+// temperature nodes are written by their neighbouring cells), which the march does not visit.
+__global__ void __launch_bounds__(256) k_zero_boundary(KvGeom g, size_t P, double* __restrict__ vstar,
+                                                       double* __restrict__ tout) {
+  // the six boundary planes in turn: k = 0, Z-1 (X*Y each), j = 0, Y-1 (X*(Z-2)), i = 0, X-1 ((Y-2)*(Z-2))
+  const long long nk = (long long)g.X * g.Y, nj = (long long)g.X * (g.Z - 2), ni = (long long)(g.Y - 2) * (g.Z - 2);
+  const long long n = 2 * (nk + nj + ni);
+  for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x) {
+    long long r = t;
+    int i, j, k;
+    if (r < 2 * nk) {
+      k = r < nk ? 0 : g.Z - 1;
+      r %= nk;
+      i = (int)(r % g.X);
+      j = (int)(r / g.X);
+    } else if ((r -= 2 * nk) < 2 * nj) {
+      j = r < nj ? 0 : g.Y - 1;
+      r %= nj;
+      i = (int)(r % g.X);
+      k = 1 + (int)(r / g.X);
+    } else {
+      r -= 2 * nj;
+      i = r < ni ? 0 : g.X - 1;
+      r %= ni;
+      j = 1 + (int)(r % (g.Y - 2));
+      k = 1 + (int)(r / (g.Y - 2));
+    }
+    const size_t e = (size_t)i + (size_t)g.X * ((size_t)j + (size_t)g.Y * k);
+    vstar[e] = 0.0;
+    vstar[P + e] = 0.0;
+    vstar[2 * P + e] = 0.0;
+    const bool aa_wall = g.bc == KV_BC_AA && (j == 0 || j == g.ny + 1) && i >= 1 && i <= g.nx && k >= 1 &&
+                         k <= g.nz;
+    if (!aa_wall) tout[e] = 0.0;
+  }
+}
+
 // FP32-pair copy of the assembled coefficients the double-float operator reads
 // (kDfFromFull): ch = fp32(c), cl = fp32(c - ch).
 __global__ void __launch_bounds__(256) k_coef_df(const double* __restrict__ coef, float2* __restrict__ cdf, size_t P) {
@@ -630,10 +835,6 @@ void kv_launch_coef_df(const kv_grid* h, const double* coef, float2* cdf, cudaSt
 void kv_launch_apply_df(const kv_grid* h, const float2* cdf, const double* x, double* vstar, double* tout,
                         cudaStream_t s) {
   const KvGeom& g = h->g;
-  {
-    dim3 block(32, 8, 1), grid((g.X + 31) / 32, (g.Y + 7) / 8, g.Z);
-    k_split_input<<<grid, block, 0, s>>>(g, x, h->P, h->xsplit);
-  }
   // alpha = {2, 3/2, 6} diff / h^2 per axis (interior, first cell, last cell)
   DfAlpha al;
   const double diff[2] = {g.nu, g.kappa}, ih2[3] = {g.ihx * g.ihx, g.ihy * g.ihy, g.ihz * g.ihz};
@@ -641,6 +842,18 @@ void kv_launch_apply_df(const kv_grid* h, const float2* cdf, const double* x, do
   for (int d = 0; d < 2; ++d)
     for (int ax = 0; ax < 3; ++ax)
       for (int c = 0; c < 3; ++c) al.a[d][ax][c] = host_pair(fac[c] * diff[d] * ih2[ax]);
+  if (h->df_variant == 1) {
+    // the 2.5D march: df_by planes per block
+    k_zero_boundary<<<2 * 152, 256, 0, s>>>(g, h->P, vstar, tout);
+    const int kc = h->df_by;
+    dim3 grid((g.nx + MB_X - 1) / MB_X, (g.ny + MB_Y - 1) / MB_Y, (g.nz + kc - 1) / kc);
+    k_apply_df_march<<<grid, MTHREADS, 0, s>>>(g, cdf, x, h->P, vstar, tout, al, kc);
+    return;
+  }
+  {
+    dim3 block(32, 8, 1), grid((g.X + 31) / 32, (g.Y + 7) / 8, g.Z);
+    k_split_input<<<grid, block, 0, s>>>(g, x, h->P, h->xsplit);
+  }
   // df_by rows of cells per block, four equation warps-rows each
   const int bx = h->df_bx, rows = h->df_by;
   dim3 block(bx, 4 * rows, 1), grid((g.X + bx - 1) / bx, (g.Y + rows - 1) / rows, g.Z);

@@ -8,16 +8,21 @@
 // is won back by iterative refinement with an FP64 residual r = b - L phi (kv_mixed.cu).
 //
 // Kernel structure (persistent, one CTA per SM, 128 x 256 output tiles, cta_group::1):
-//   warp 0      TMA producer: per stage one 128 x 64 tile of W_i and one 256 x 64 tile of X_j
-//               (128-byte swizzle), completion on a full[] mbarrier;
-//   warp 1      allocates 512 TMEM columns (two 128 x 256 FP32 accumulators); lane 0 issues
-//               tcgen05.mma (M=128, N=256, K=16), tcgen05.commit to each stage's empty[] barrier
-//               and, after a tile's last MMA, to that accumulator's full barrier;
-//   warps 2-17  epilogue (four warps per TMEM lane quarter): tcgen05.ld of the accumulator, transposed through shared memory so
-//               that stores run along r, then either the next pass's three BF16 slices (with
-//               the 1 / Lambda scaling of Eq (17) in the third forward pass) or phi += D (FP64);
-//               then they release the accumulator, so the epilogue of one tile overlaps the
-//               MMAs of the next.
+//   warp 0      TMA producer, two phases per tile: per 64-wide k-chunk the three 128 x 64 tiles
+//               of W_0..W_2 into a six-slot ring and the three 256 x 64 tiles of X_0..X_2 into a
+//               three-slot ring (128-byte swizzle; each slot with a full[] mbarrier), so every
+//               slice is loaded once per k-chunk and serves all the products with i + j >= 1;
+//               then W_0 and X_0 again for the leading product (see the MMA warp);
+//   warp 1      allocates 512 TMEM columns (two 128 x 256 FP32 accumulators); lane 0 issues, per
+//               k-chunk and X slice j, the tcgen05.mma (M=128, N=256, K=16) of the pairs (i, j)
+//               with i + j <= 2, releases each slot with tcgen05.commit to its empty[] barrier
+//               and, after a tile's last MMA, commits to that accumulator's full barrier;
+//   warps 2-17  epilogue (four warps per TMEM lane quarter): tcgen05.ld of 16 accumulator
+//               columns at a time, transposed through a swizzled 2 KB shared-memory buffer so that
+//               stores run along r, then either the next pass's three BF16 slices (with the
+//               1 / Lambda scaling of Eq (17) in the third forward pass) or phi (FP64, or FP32
+//               after a first refinement sweep); then they release the accumulator, so the
+//               epilogue of one tile overlaps the MMAs of the next.
 // Every mbarrier wait has an iteration limit; on expiry the kernel sets an error flag and
 // leaves without hanging.
 #include <cuda.h>
@@ -29,19 +34,20 @@
 namespace {
 
 constexpr int UM = 128, UN = 256, UK = 64;  // CTA tile; UK = one 128-byte swizzle row of BF16
-constexpr int STAGES = 3;
+constexpr int AR = 6, BR = 3;               // W-slice ring (two k-chunks of three slices), X-slice ring
 constexpr int A_BYTES = UM * UK * 2;        // 16 KB
 constexpr int B_BYTES = UN * UK * 2;        // 32 KB
-constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
 constexpr int EPI_WARPS = 16;  // four per TMEM lane quarter, each taking a quarter of the columns
 constexpr int EPI_COLS = UN / (EPI_WARPS / 4);
+constexpr int EPI_CHUNK = 16;               // columns per TMEM load and transpose
 constexpr int THREADS = 64 + 32 * EPI_WARPS;
-constexpr int EPI_STRIDE = 33;              // floats per transposed row (bank-conflict free)
-constexpr int EPI_BYTES = EPI_WARPS * 32 * EPI_STRIDE * 4;
-constexpr int SMEM_BYTES = 1024 /*alignment slack*/ + STAGES * STAGE_BYTES + EPI_BYTES + 256 /*barriers + slot*/;
+constexpr int EPI_BYTES = EPI_WARPS * 32 * EPI_CHUNK * 4;
+constexpr int NBARS = 2 * AR + 2 * BR + 4;
+constexpr int SMEM_BYTES = 256 /*barriers + TMEM slot*/ + 1024 /*alignment slack*/ + AR * A_BYTES + BR * B_BYTES + EPI_BYTES;
+static_assert(NBARS * 8 + 4 <= 256, "barrier area");
+static_assert(SMEM_BYTES <= 232448, "shared memory per block");
 constexpr int TMEM_COLS = 2 * UN;  // two accumulators: the epilogue of one tile overlaps the next tile's MMAs
 constexpr uint32_t WAIT_LIMIT = 1u << 24;
-constexpr int NPAIRS = 6;
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -111,19 +117,17 @@ __device__ __forceinline__ void umma_commit(uint32_t bar) {
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
-  uint32_t r[32];
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
+  uint32_t r[16];
   asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
-      "%15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+      "%15}, [%16];"
       : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
-        "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
-        "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
       : "r"(taddr));
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
-  for (int q = 0; q < 32; ++q) v[q] = __uint_as_float(r[q]);
+  for (int q = 0; q < 16; ++q) v[q] = __uint_as_float(r[q]);
 }
 
 // three-way BF16 split of an FP32 value
@@ -135,9 +139,6 @@ __device__ __forceinline__ void split3(float x, __nv_bfloat16& s1, __nv_bfloat16
   s3 = __float2bfloat16_rn(r2);
 }
 
-// Slice pairs (i, j), 0-based, with i + j <= 2, smallest products first.
-__constant__ int kPairA[NPAIRS] = {2, 1, 0, 1, 0, 0};
-__constant__ int kPairB[NPAIRS] = {0, 1, 2, 0, 1, 0};
 
 }  // namespace
 
@@ -150,23 +151,29 @@ __global__ void __launch_bounds__(THREADS, 1)
     k_umma_axis(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB, int K,
                 KvUmmaEpi ep, unsigned int* err) {
   extern __shared__ uint8_t smem_raw[];
-  uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-  float* epi = (float*)(smem + STAGES * STAGE_BYTES);
-  uint64_t* bars = (uint64_t*)(smem + STAGES * STAGE_BYTES + EPI_BYTES);
-  uint32_t* tmem_slot = (uint32_t*)(bars + 2 * STAGES + 4);
-  const uint32_t full0 = smem_u32(bars), empty0 = smem_u32(bars + STAGES);
-  const uint32_t accf0 = smem_u32(bars + 2 * STAGES), acce0 = smem_u32(bars + 2 * STAGES + 2);
+  uint64_t* bars = (uint64_t*)smem_raw;  // fullA[AR] emptyA[AR] fullB[BR] emptyB[BR] accf[2] acce[2], TMEM slot
+  uint32_t* tmem_slot = (uint32_t*)(bars + NBARS);
+  uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 256 + 1023) & ~(uintptr_t)1023);
+  uint8_t* aring = smem;
+  uint8_t* bring = smem + AR * A_BYTES;
+  float* epi = (float*)(bring + BR * B_BYTES);
+  const uint32_t fullA0 = smem_u32(bars), emptyA0 = smem_u32(bars + AR);
+  const uint32_t fullB0 = smem_u32(bars + 2 * AR), emptyB0 = smem_u32(bars + 2 * AR + BR);
+  const uint32_t accf0 = smem_u32(bars + 2 * AR + 2 * BR), acce0 = smem_u32(bars + 2 * AR + 2 * BR + 2);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int ntm = (ep.M + UM - 1) / UM, ntr = (ep.R + UN - 1) / UN, ntiles = ntm * ntr;
   const uint32_t lim = ep.wait_limit ? ep.wait_limit : WAIT_LIMIT;
   const int kchunks = (K + UK - 1) / UK;
-  const int iters = NPAIRS * kchunks;
 
   if (threadIdx.x == 0) {
-    for (int s = 0; s < STAGES; ++s) {
-      mbar_init(full0 + 8 * s, 1);
-      mbar_init(empty0 + 8 * s, 1);
+    for (int s = 0; s < AR; ++s) {
+      mbar_init(fullA0 + 8 * s, 1);
+      mbar_init(emptyA0 + 8 * s, 1);
+    }
+    for (int s = 0; s < BR; ++s) {
+      mbar_init(fullB0 + 8 * s, 1);
+      mbar_init(emptyB0 + 8 * s, 1);
     }
     for (int b = 0; b < 2; ++b) {
       mbar_init(accf0 + 8 * b, 1);                  // tcgen05.commit after a tile's last MMA
@@ -189,25 +196,33 @@ __global__ void __launch_bounds__(THREADS, 1)
     if (lane == 0) {
       asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)&mapA) : "memory");
       asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)&mapB) : "memory");
-      uint32_t g = 0;  // stage counter across tiles
+      uint32_t ga = 0, gb = 0;  // ring positions, continued across tiles
       bool ok = true;
       for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
         const int m0 = (t % ntm) * UM, r0 = (t / ntm) * UN;
-        for (int it = 0; it < iters; ++it, ++g) {
-          const int s = g % STAGES;
-          const uint32_t ph = (g / STAGES) & 1u;
-          if (!(ok = mbar_wait(empty0 + 8 * s, ph ^ 1u, err, lim))) break;
-          const int pair = it / kchunks, kc = it % kchunks;
-          const uint32_t a = smem_u32(smem + s * STAGE_BYTES), b = a + A_BYTES;
-          mbar_expect_tx(full0 + 8 * s, STAGE_BYTES + ep.extra_tx);
-          tma_load_3d(a, &mapA, kc * UK, m0, kPairA[pair], full0 + 8 * s);
-          tma_load_3d(b, &mapB, kc * UK, r0, kPairB[pair], full0 + 8 * s);
+        // phase 0: the slices of the five products with i + j >= 1; phase 1: W_0 and X_0 only
+        for (int ph = 0; ph < 2 && ok; ++ph) {
+          const int ns = ph == 0 ? 3 : 1;
+          for (int kc = 0; kc < kchunks && ok; ++kc) {
+            for (int i = 0; i < ns && ok; ++i, ++ga) {
+              const int s = ga % AR;
+              if (!(ok = mbar_wait(emptyA0 + 8 * s, ((ga / AR) & 1u) ^ 1u, err, lim))) break;
+              mbar_expect_tx(fullA0 + 8 * s, A_BYTES + ep.extra_tx);
+              tma_load_3d(smem_u32(aring + s * A_BYTES), &mapA, kc * UK, m0, i, fullA0 + 8 * s);
+            }
+            for (int j = 0; j < ns && ok; ++j, ++gb) {
+              const int s = gb % BR;
+              if (!(ok = mbar_wait(emptyB0 + 8 * s, ((gb / BR) & 1u) ^ 1u, err, lim))) break;
+              mbar_expect_tx(fullB0 + 8 * s, B_BYTES + ep.extra_tx);
+              tma_load_3d(smem_u32(bring + s * B_BYTES), &mapB, kc * UK, r0, j, fullB0 + 8 * s);
+            }
+          }
         }
       }
     }
   } else if (warp == 1) {
     if (lane == 0) {
-      uint32_t g = 0;
+      uint32_t ga = 0, gb = 0;
       int lt = 0;
       bool ok = true;
       for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x, ++lt) {
@@ -217,16 +232,40 @@ __global__ void __launch_bounds__(THREADS, 1)
         if (!(ok = mbar_wait(acce0 + 8 * buf, (use & 1u) ^ 1u, err, lim))) break;
         tc_fence_after();
         const uint32_t acc = tmem + (uint32_t)(buf * UN);
-        for (int it = 0; it < iters; ++it, ++g) {
-          const int s = g % STAGES;
-          const uint32_t ph = (g / STAGES) & 1u;
-          if (!(ok = mbar_wait(full0 + 8 * s, ph, err, lim))) break;
-          tc_fence_after();
-          const uint32_t a = smem_u32(smem + s * STAGE_BYTES), b = a + A_BYTES;
+        bool first = true;
+        // The FP32 accumulation of the tensor core drops the low bits of products much smaller
+        // than the running sum, so the small slice products (i + j >= 1) are summed over all of
+        // K first (phase 0) and the leading product W_0 X_0 is added last (phase 1).
+        for (int ph = 0; ph < 2 && ok; ++ph) {
+          const int ns = ph == 0 ? 3 : 1;
+          for (int kc = 0; kc < kchunks && ok; ++kc) {
+            uint32_t aA[3];
+            for (int i = 0; i < ns && ok; ++i) {
+              const uint32_t p = ga + i;
+              ok = mbar_wait(fullA0 + 8 * (p % AR), (p / AR) & 1u, err, lim);
+              aA[i] = smem_u32(aring + (p % AR) * A_BYTES);
+            }
+            if (!ok) break;
+            // X slice j meets the W slices i with i + j <= 2 (phase 0: i + j >= 1)
+            for (int j = 0; j < ns && ok; ++j, ++gb) {
+              const int sb = gb % BR;
+              if (!(ok = mbar_wait(fullB0 + 8 * sb, (gb / BR) & 1u, err, lim))) break;
+              tc_fence_after();
+              const uint32_t b = smem_u32(bring + sb * B_BYTES);
+              // phase 0: i = 2 - j .. 0 without (0, 0); phase 1: (0, 0) only
+              for (int i = ph == 0 ? 2 - j : 0; i >= 0; --i) {
+                if (ph == 0 && i + j == 0) continue;
 #pragma unroll
-          for (int kk = 0; kk < UK / 16; ++kk)
-            umma_bf16(acc, sdesc(a + kk * 32), sdesc(b + kk * 32), (it > 0 || kk > 0) ? 1u : 0u);
-          umma_commit(empty0 + 8 * s);
+                for (int kk = 0; kk < UK / 16; ++kk) {
+                  umma_bf16(acc, sdesc(aA[i] + kk * 32), sdesc(b + kk * 32), first ? 0u : 1u);
+                  first = false;
+                }
+              }
+              umma_commit(emptyB0 + 8 * sb);
+            }
+            for (int i = 0; i < ns; ++i) umma_commit(emptyA0 + 8 * ((ga + i) % AR));
+            ga += ns;
+          }
         }
         umma_commit(accf0 + 8 * buf);  // arrives once every MMA of this tile has completed
       }
@@ -235,7 +274,10 @@ __global__ void __launch_bounds__(THREADS, 1)
     // epilogue warps 2..17 -> TMEM lane quarter (warp % 4), column block (warp - 2) / 4
     const int q = warp & 3;
     const int c0 = ((warp - 2) / 4) * EPI_COLS;
-    float* tb = epi + (warp - 2) * 32 * EPI_STRIDE;
+    float* tb = epi + (warp - 2) * 32 * EPI_CHUNK;
+    // tb holds EPI_CHUNK = 16 columns x 32 rows, column-major, the row index XOR-swizzled by
+    // 8 (col / 4): the column writes and the 4-column row reads below are bank-conflict free
+    auto tix = [](int col, int row) { return col * 32 + (row ^ (8 * (col >> 2))); };
     // groups of 4 outputs are contiguous and 8-byte aligned (slices) or 32-byte aligned (phi)
     // when the inner extent and R are multiples of 4 (and the slice pitch and size are)
     const bool to_phi = ep.mode >= 2;
@@ -248,16 +290,16 @@ __global__ void __launch_bounds__(THREADS, 1)
       tc_fence_after();
       const int m0 = (t % ntm) * UM, r0 = (t / ntm) * UN;
       const int mrow0 = m0 + 32 * q;
-      for (int c = c0; c < c0 + EPI_COLS; c += 32) {
-        float v[32];
-        tmem_ld32(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(buf * UN + c), v);
+      for (int c = c0; c < c0 + EPI_COLS; c += EPI_CHUNK) {
+        float v[EPI_CHUNK];
+        tmem_ld16(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(buf * UN + c), v);
         // transpose: tb[col][row]
 #pragma unroll
-        for (int t2 = 0; t2 < 32; ++t2) tb[t2 * EPI_STRIDE + lane] = v[t2];
+        for (int t2 = 0; t2 < EPI_CHUNK; ++t2) tb[tix(t2, lane)] = v[t2];
         __syncwarp();
         if (vec4) {
-          // lane: 4 consecutive columns (4 (lane % 8) ..) of rows 4 it + lane / 8; 8-byte stores
-          const int cc = 4 * (lane & 7);
+          // lane: 4 consecutive columns (4 (lane % 4) ..) of rows 8 it + lane / 4; 8-byte stores
+          const int cc = 4 * (lane & 3);
           const int r = r0 + c + cc;
           if (r < ep.R) {  // R is a multiple of 4 here, so r < R covers all four columns
             int a = 0, bcol = r;
@@ -265,13 +307,13 @@ __global__ void __launch_bounds__(THREADS, 1)
               a = r / ep.nb;
               bcol = r - a * ep.nb;
             }
-            for (int it = 0; it < 8; ++it) {
-              const int row = 4 * it + (lane >> 3);
+            for (int it = 0; it < 4; ++it) {
+              const int row = 8 * it + (lane >> 2);
               const int m = mrow0 + row;
               if (m >= ep.M) break;
               float d[4];
 #pragma unroll
-              for (int t2 = 0; t2 < 4; ++t2) d[t2] = tb[(cc + t2) * EPI_STRIDE + row];
+              for (int t2 = 0; t2 < 4; ++t2) d[t2] = tb[tix(cc + t2, row)];
               if (to_phi) {
                 const size_t o = (size_t)m * ep.R + r;
                 if (ep.mode == 4) {
@@ -314,17 +356,20 @@ __global__ void __launch_bounds__(THREADS, 1)
             }
           }
         } else {
-          const int r = r0 + c + lane;
+          // lane: column lane % 16 of rows 16 (lane / 16) ..
+          const int col = lane & (EPI_CHUNK - 1);
+          const int r = r0 + c + col;
           if (r < ep.R) {
             int a = 0, bcol = r;
             if (!to_phi) {
               a = r / ep.nb;
               bcol = r - a * ep.nb;
             }
-            for (int row = 0; row < 32; ++row) {
+            for (int rr = 0; rr < 16; ++rr) {
+              const int row = 16 * (lane >> 4) + rr;
               const int m = mrow0 + row;
               if (m >= ep.M) break;
-              float d = tb[lane * EPI_STRIDE + row];
+              float d = tb[tix(col, row)];
               if (to_phi) {
                 const size_t o = (size_t)m * ep.R + r;
                 if (ep.mode == 4)

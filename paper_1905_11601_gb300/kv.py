@@ -26,7 +26,7 @@ EXPORTS = ("kv_create_grid", "kv_destroy_grid", "kv_set_stream", "kv_field_len",
            "kv_krylov_vector", "kv_krylov_vector_host", "kv_arnoldi_step", "kv_newton_residual", "kv_last_error",
            "kv_profile_enable", "kv_profile_get", "kv_krylov_vector_noalloc", "kv_krylov_vector_adjoint",
            "kv_base_flow_gradient", "kv_krylov_vector_batch", "kv_plan_create", "kv_plan_add", "kv_plan_launch",
-           "kv_plan_destroy", "kv_plan_last_error", "kv_selftest_wait_timeout")
+           "kv_plan_destroy", "kv_plan_last_error", "kv_selftest_wait_timeout", "kv_tuning")
 PHASES = {"stencil": 0, "divergence": 1, "tpd": 2, "correct": 3, "arnoldi": 4, "refine": 5, "gs_dots": 6,
           "gs_update": 7}
 
@@ -74,6 +74,7 @@ def load_library(path: str = LIB_PATH):
     lib.kv_profile_enable.argtypes = [H, ctypes.c_int]
     lib.kv_profile_get.argtypes = [H, ctypes.c_int, ctypes.POINTER(ctypes.c_double),
                                    ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_longlong)]
+    lib.kv_tuning.argtypes = [H, ctypes.POINTER(ctypes.c_int)]
     lib.kv_krylov_vector_adjoint.argtypes = [H, D, D]
     lib.kv_base_flow_gradient.argtypes = [H, D, D, D, ctypes.POINTER(ctypes.c_double)]
     lib.kv_krylov_vector_batch.argtypes = [H, D, D, ctypes.c_int]
@@ -230,6 +231,13 @@ class Grid:
     def profile_enable(self, on=True):
         self._sync_stream()
         self._check(self.lib.kv_profile_enable(self.h, 1 if on else 0))
+
+    def tuning(self):
+        """The autotuner's choice: {"apply_block": (bx, by), "df_variant": 0 split + per-equation
+        kernel | 1 march | -1 (FP64 grid), "df_block": (cells, rows) | (-1, planes per block)}."""
+        cfg = (ctypes.c_int * 5)()
+        self._check(self.lib.kv_tuning(self.h, cfg))
+        return {"apply_block": (cfg[0], cfg[1]), "df_variant": cfg[2], "df_block": (cfg[3], cfg[4])}
 
     def profile(self):
         """{phase: (total_ms, timed_brackets, launches)} since the last profile_enable."""
