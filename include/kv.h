@@ -79,9 +79,11 @@ typedef struct {
   int max_passes;    /* SIMPLE passes at most (0 -> 1: one exact pass, residual reported) */
   int refine_sweeps; /* KV_PREC_MIXED: tensor-core solves per Poisson solve, each followed by an
                         FP64 residual (0 -> 2) */
-  int cgs_passes;    /* kv_arnoldi_step: 0 = classical Gram-Schmidt with the DGKS test (a second
-                        pass only when the first removes more than half of ||w||^2, as ARPACK's
-                        Arnoldi does); 2 = always two passes */
+  int cgs_passes;    /* kv_arnoldi_step: 0 = classical Gram-Schmidt whose second pass measures the
+                        remaining components h2 = V^T w (fused with the first update) and applies
+                        w -= V h2 only when ||h2|| exceeds the sweeps' rounding level (2^-46 ||w||
+                        for KV_PREC_MIXED's double-float sweeps, 2^-50 ||w|| in FP64); 2 = always
+                        apply it */
 } kv_grid_desc;
 
 typedef struct {
@@ -148,8 +150,9 @@ const char* kv_plan_last_error(kv_plan_handle p);
 
 /* One Arnoldi step (Section 3.1, the Krylov basis for the eigenvalue problem Eq (10)):
    V holds at least j+2 packed vectors (device), V_0..V_j orthonormal; computes
-   w = A V_j, orthogonalises it against V_0..V_j by classical Gram-Schmidt (a second pass by
-   the DGKS test or always, desc.cgs_passes; always two passes beyond 24 basis vectors),
+   w = A V_j, orthogonalises it against V_0..V_j by classical Gram-Schmidt (the second pass's
+   correction when its measured coefficients exceed the rounding level, or always:
+   desc.cgs_passes; always two passes beyond 24 basis vectors),
    stores w / ||w|| in V_{j+1} and writes the Hessenberg column H[0..j+1, j] to the HOST
    array h_col (j+2 doubles). Synchronises the stream. Inner products run over all stored
    entries of the four fields. With KV_PREC_MIXED and up to 24 basis vectors, the first two

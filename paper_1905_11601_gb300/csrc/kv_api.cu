@@ -491,8 +491,11 @@ kv_status kv_arnoldi_step(kv_handle h, double* V, int j, double* h_col) {
     // mixed precision: sweeps 1 and 2 in double-float on the FP32 pipe
     const int df = h->d.precision == KV_PREC_MIXED;
     // Classical Gram-Schmidt. Sweep 1: h1 = V^T w and ||w||^2. Sweep 2: w -= V h1 fused with the
-    // second pass's h2 = V^T w and ||w||^2. The DGKS test (as in ARPACK's Arnoldi) then decides
-    // whether sweep 3 (w -= V h2) is needed: only when sweep 2 removed more than half of ||w||^2.
+    // second pass's h2 = V^T w and ||w||^2, i.e. the components along V that remain after the
+    // first update, measured. Sweep 3 (w -= V h2) is applied when they exceed the rounding level
+    // of the sweep arithmetic relative to ||w|| (2^-46 for the double-float sweeps, 2^-50 in
+    // FP64); below it the second update cannot improve the orthogonality. (ARPACK's DGKS test
+    // decides from ||w|| alone because it has not computed h2; here sweep 2 has.)
     {
       KvPhase ph(h, KV_PH_GS_DOTS, 2);
       kv_launch_dots_norm(V, L, nq, w, L, h->partials, h1, h1 + nq, df, h->s);
@@ -510,7 +513,10 @@ kv_status kv_arnoldi_step(kv_handle h, double* V, int j, double* h_col) {
       return fail(h, KV_ERR_ARG,
                   "kv_arnoldi_step: the new vector has entries outside the mixed-precision Gram-Schmidt range "
                   "(NaN, Inf or |x| >= 2^48); V[j+1] is undefined");
-    const bool reorth = h->d.cgs_passes == 2 || !(after > 0.5 * before);
+    double h2n = 0.0;
+    for (int q = 0; q < nq; ++q) h2n += hh[nq + 1 + q] * hh[nq + 1 + q];
+    const double theta = df ? 0x1p-46 : 0x1p-50;
+    const bool reorth = h->d.cgs_passes == 2 || !(h2n <= theta * theta * after);
     {
       KvPhase ph(h, KV_PH_ARNOLDI, 1);
       if (reorth)
@@ -526,11 +532,7 @@ kv_status kv_arnoldi_step(kv_handle h, double* V, int j, double* h_col) {
       return KV_OK;
     }
     // beta^2 = ||w1||^2 - ||h2||^2 (V orthonormal), the factor the fused sweep applied
-    double h2n = 0.0;
-    for (int q = 0; q < nq; ++q) {
-      h_col[q] = hh[q] + hh[nq + 1 + q];
-      h2n += hh[nq + 1 + q] * hh[nq + 1 + q];
-    }
+    for (int q = 0; q < nq; ++q) h_col[q] = hh[q] + hh[nq + 1 + q];
     const double b2 = after - h2n;
     h_col[nq] = b2 > 0.0 ? sqrt(b2) : 0.0;
     return KV_OK;

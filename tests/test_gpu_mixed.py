@@ -167,3 +167,31 @@ def test_refinement_sweeps_converge():
     assert errs[0] < 1e-3, errs
     assert errs[1] < RTOL_MIXED and errs[2] < RTOL_MIXED, errs
     assert errs[1] < 1e-3 * errs[0], errs
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_second_update_criterion_matches_forced_reorthogonalisation(prec):
+    """The second Gram-Schmidt update is applied only when the measured second-pass coefficients
+    exceed the sweeps' rounding level; the basis and Hessenberg matrix then agree to rounding
+    with the ones built when it is always applied (cgs_passes = 2)."""
+    from paper_1905_11601_gb300 import kv
+    n = (36, 30, 34)
+    base = np.stack(synth.base_flow(*n, synth.CC, 41))
+    x = synth.krylov_input(*n, 42)[0]
+    k = 16
+    out = []
+    for cgs in (0, 2):
+        g = kv.Grid(*n, gr=2e6, pr=0.71, precision=prec, cgs_passes=cgs)
+        g.set_base_flow(torch.from_numpy(base).cuda())
+        V = torch.zeros((k + 1, 4) + g.shape, dtype=torch.float64, device="cuda")
+        y = g.krylov_vector(torch.from_numpy(x).cuda())
+        V[0] = y / torch.linalg.vector_norm(y)
+        H = np.zeros((k + 1, k))
+        for j in range(k):
+            H[: j + 2, j] = g.arnoldi_step(V, j)
+        out.append((H, V.reshape(k + 1, -1).cpu().numpy()))
+    (H0, V0), (H2, V2) = out
+    assert np.abs(H0 - H2).max() < 1e-12 * np.abs(H2).max()
+    assert np.abs(V0 - V2).max() < 1e-10
+    G = V0 @ V0.T
+    assert np.abs(G - np.eye(k + 1)).max() < 1e-13
