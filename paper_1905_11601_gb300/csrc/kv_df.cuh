@@ -3,8 +3,10 @@
 // the FP32 rate and cannot keep up with HBM in the streaming kernels of the Krylov step).
 //
 // An FP64 value is split with integer operations only: the head is its leading 24 significant
-// bits (exact), the tail the next 23 bits (exact), so the pair carries the value to within 2^-46
-// of its magnitude. Values below 2^-103 in magnitude become 0 (an absolute change of at most
+// bits (exact), the remaining 29 bits rounded to 23 (half up), so the pair carries the value to
+// within 2^-48 of its magnitude without a systematic bias (a truncated tail would scale every
+// value by 1 - O(2^-47), and those errors add up over a long inner product instead of averaging
+// out). Values below 2^-103 in magnitude become 0 (an absolute change of at most
 // 2^-103); values at or above 2^128 are outside the pair's range (callers bound their inputs).
 // Products are formed as head*head (exact, with the FMA error term) plus the two cross terms,
 // and sums with an exact TwoSum on the leading words, so each operation carries a relative
@@ -25,11 +27,13 @@ __device__ __forceinline__ DF df_split(double x) {
   if (ex - 920u <= 230u) {
     // head: FP32 exponent rebiased in place, then 23 fraction bits (20 from hi, 3 from lo)
     const unsigned int hb = __funnelshift_l(lo, hi - (896u << 20), 3) | (hi & 0x80000000u);
-    // tail: the next 23 fraction bits (lo bits 28..6) as 2^k (1 + m 2^-23) - 2^k, k the weight
-    // of lo bit 28 plus one; the subtraction is exact
+    // tail: lo bits 28..0 rounded (half up) to the 23 bits 28..6, m, as 2^k (1 + m 2^-23) - 2^k,
+    // k the weight of lo bit 28 plus one (m = 2^23 after rounding up carries into the exponent:
+    // 2^(k+1) - 2^k); the subtraction is exact
     const unsigned int eb = (hb & 0xFF800000u) - (23u << 23);
+    const unsigned int m = ((lo & 0x1FFFFFFFu) + 0x20u) >> 6;
     r.h = __uint_as_float(hb);
-    r.l = __fsub_rn(__uint_as_float(eb | ((lo >> 6) & 0x7FFFFFu)), __uint_as_float(eb));
+    r.l = __fsub_rn(__uint_as_float(eb + m), __uint_as_float(eb));
   }
   return r;
 }
