@@ -49,7 +49,7 @@ def parse_args():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default="cube256_cc")
     ap.add_argument("--restart", type=int, default=20)
-    ap.add_argument("--e2e-steps", type=int, default=5)
+    ap.add_argument("--e2e-steps", type=int, default=8)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the 16-vector block and the 12-grid plan measurements")
@@ -479,18 +479,27 @@ def run_ours(args):
             torch.cuda.empty_cache()
 
     g = results["mixed"]["g"]
-    # end to end through the host-buffer entry point (pinned host x and y, copies timed)
-    xh = torch.from_numpy(x_np[0].copy()).pin_memory()
-    yh = torch.empty_like(xh).pin_memory()
-    g.krylov_vector_host(xh, yh)
+    # End to end through the host-buffer entry points (pinned host memory, every vector's copies
+    # inside the timed region): the streamed form (copies overlapping the evaluations) is the
+    # e2e value; one kv_krylov_vector_host call per vector is reported beside it.
+    ne = args.e2e_steps
+    Xh = torch.from_numpy(np.stack([x_np[0]] * ne).reshape(ne, -1)).pin_memory()
+    Yh = torch.empty_like(Xh).pin_memory()
+    g.krylov_vector_host_stream(Xh[:2], Yh[:2])
     torch.cuda.synchronize()
     if dist:
         dist.barrier()
     t0 = time.perf_counter()
-    for _ in range(args.e2e_steps):
-        g.krylov_vector_host(xh, yh)
+    g.krylov_vector_host_stream(Xh, Yh)
     e2e_s = max_over_ranks(time.perf_counter() - t0, dist)
-    e2e_value = whole_job_rate(args.e2e_steps, world, e2e_s)
+    e2e_value = whole_job_rate(ne, world, e2e_s)
+    xh, yh = Xh[0], Yh[0]
+    g.krylov_vector_host(xh, yh)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(ne):
+        g.krylov_vector_host(xh, yh)
+    e2e_single = whole_job_rate(ne, world, max_over_ranks(time.perf_counter() - t0, dist))
     vec_bytes = xh.numel() * 8
 
     mx = results["mixed"]
@@ -508,7 +517,9 @@ def run_ours(args):
            "impl": "ours",
            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": vec_bytes,
                    "d2h_bytes_per_step": vec_bytes,
-                   "path": "kv_krylov_vector_host, mixed precision (pinned host x and y, copies on the handle's stream)"},
+                   "path": f"kv_krylov_vector_host_stream over {ne} vectors, mixed precision (pinned host X and Y; "
+                           f"copy-in of the next and copy-out of the previous vector overlap each evaluation)",
+                   "single_call_value": e2e_single},
            "gpu_launches": launches, "roofline": roof, "clocks": mx["clocks"],
            "rel_err_vs_fp64": mx["err"], "tuning": mx["g"].tuning(),
            "phases": {k: {"ms_per_step": v["ms"] / args.steps, "share": v["share"],

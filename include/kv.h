@@ -127,6 +127,17 @@ kv_status kv_krylov_vector(kv_handle h, const double* x, double* y, double* p, k
    copies are queued on the handle's stream and the call returns once y is in host memory. */
 kv_status kv_krylov_vector_host(kv_handle h, const double* x_host, double* y_host, kv_stats* st);
 
+/* A sequence of Krylov vectors between host buffers: Y_i = A X_i for i = 0..nb-1 (X_host,
+   Y_host: nb consecutive packed vectors in host memory, page-locked for the copies to overlap).
+   The same map as kv_krylov_vector, evaluated in order on the handle's stream from two device
+   staging slots (4 packed vectors, allocated at the first call and kept by the handle), with the
+   host-to-device copy of X_{i+1} and the device-to-host copy of Y_{i-1} on two copy streams of
+   the handle, overlapping the evaluation of X_i (Section 3.1's many Krylov vectors per Newton or
+   Arnoldi run come from the host in this form when they do not fit the device). Returns once
+   every Y_i is in host memory; results equal nb calls of kv_krylov_vector_host. nb = 0 does
+   nothing; KV_ERR_STATE without a base flow. */
+kv_status kv_krylov_vector_host_stream(kv_handle h, const double* X_host, double* Y_host, int nb);
+
 /* A block of Krylov vectors: Y_b = A X_b for b = 0..nb-1 (X, Y: nb consecutive packed vectors,
    device, not overlapping). The evaluation sequence is captured once into a CUDA graph, cached
    per (X, Y, nb) on the handle (up to 8 entries), and replayed with one graph launch on the

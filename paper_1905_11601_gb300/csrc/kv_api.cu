@@ -93,6 +93,11 @@ void free_all(kv_grid* h) {
   cudaFree(h->partials);
   cudaFree(h->hdev);
   cudaFree(h->stage);
+  cudaFree(h->pipe);
+  for (auto& e : h->pev)
+    if (e) cudaEventDestroy(e);
+  if (h->cs_in) cudaStreamDestroy(h->cs_in);
+  if (h->cs_out) cudaStreamDestroy(h->cs_out);
   cudaFree(h->tmp4);
   cudaFree(h->adj);
   cudaFree(h->adjsum);
@@ -454,6 +459,60 @@ kv_status kv_krylov_vector_host(kv_handle h, const double* x_host, double* y_hos
   if (s != KV_OK) return s;
   KV_CHECK_CUDA(h, cudaMemcpyAsync(y_host, h->stage + L, L * sizeof(double), cudaMemcpyDeviceToHost, h->s));
   KV_CHECK_CUDA(h, cudaStreamSynchronize(h->s));
+  return KV_OK;
+}
+
+kv_status kv_krylov_vector_host_stream(kv_handle h, const double* X_host, double* Y_host, int nb) {
+  if (!h) return KV_ERR_ARG;
+  if (nb == 0) return KV_OK;
+  if (!X_host || !Y_host || nb < 0) return fail(h, KV_ERR_ARG, "kv_krylov_vector_host_stream: bad argument");
+  if (!h->has_base) return fail(h, KV_ERR_STATE, "kv_krylov_vector_host_stream: no base flow set");
+  const size_t L = 4 * h->P;
+  if (!h->pipe) {
+    kv_status s = dalloc(h, &h->pipe, 4 * L);
+    if (s != KV_OK) return s;
+  }
+  if (!h->cs_in) {
+    KV_CHECK_CUDA(h, cudaStreamCreateWithFlags(&h->cs_in, cudaStreamNonBlocking));
+    KV_CHECK_CUDA(h, cudaStreamCreateWithFlags(&h->cs_out, cudaStreamNonBlocking));
+    for (auto& e : h->pev) KV_CHECK_CUDA(h, cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+  }
+  cudaEvent_t* loaded = h->pev;
+  cudaEvent_t* computed = h->pev + 2;
+  cudaEvent_t* drained = h->pev + 4;
+  // vector i: copied in on cs_in into x slot i % 2 (free once vector i - 2 is computed), computed
+  // on the handle's stream into y slot i % 2 (free once vector i - 2 is copied out), copied out on
+  // cs_out. The copy-in of i + 1 is queued before the evaluation of i, so it and the copy-out of
+  // i - 1 overlap that evaluation.
+  auto load = [&](int i) -> kv_status {
+    const int b = i & 1;
+    if (i >= 2) KV_CHECK_CUDA(h, cudaStreamWaitEvent(h->cs_in, computed[b], 0));
+    KV_CHECK_CUDA(h, cudaMemcpyAsync(h->pipe + (size_t)b * L, X_host + (size_t)i * L, L * sizeof(double),
+                                     cudaMemcpyHostToDevice, h->cs_in));
+    KV_CHECK_CUDA(h, cudaEventRecord(loaded[b], h->cs_in));
+    return KV_OK;
+  };
+  kv_status s = load(0);
+  for (int i = 0; i < nb && s == KV_OK; ++i) {
+    const int b = i & 1;
+    double* xb = h->pipe + (size_t)b * L;
+    double* yb = h->pipe + (size_t)(2 + b) * L;
+    if (i + 1 < nb && (s = load(i + 1)) != KV_OK) break;
+    KV_CHECK_CUDA(h, cudaStreamWaitEvent(h->s, loaded[b], 0));
+    if (i >= 2) KV_CHECK_CUDA(h, cudaStreamWaitEvent(h->s, drained[b], 0));
+    if ((s = kv_krylov_vector(h, xb, yb, nullptr, nullptr)) != KV_OK) break;
+    KV_CHECK_CUDA(h, cudaEventRecord(computed[b], h->s));
+    KV_CHECK_CUDA(h, cudaStreamWaitEvent(h->cs_out, computed[b], 0));
+    KV_CHECK_CUDA(h, cudaMemcpyAsync(Y_host + (size_t)i * L, yb, L * sizeof(double), cudaMemcpyDeviceToHost, h->cs_out));
+    KV_CHECK_CUDA(h, cudaEventRecord(drained[b], h->cs_out));
+  }
+  if (s != KV_OK) {
+    cudaStreamSynchronize(h->cs_in);
+    cudaStreamSynchronize(h->cs_out);
+    return s;
+  }
+  KV_CHECK_CUDA(h, cudaStreamSynchronize(h->cs_out));
+  KV_CHECK_CUDA(h, cudaStreamSynchronize(h->cs_in));
   return KV_OK;
 }
 

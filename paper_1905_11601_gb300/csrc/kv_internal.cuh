@@ -57,6 +57,9 @@ struct kv_grid {
   double* hdev = nullptr;             // Arnoldi coefficients on the device
   size_t hdev_cap = 0;
   double* stage = nullptr;            // 8P: staging for the host-buffer entry point
+  double* pipe = nullptr;             // 16P: two x and two y staging vectors of the streamed host entry point
+  cudaStream_t cs_in = nullptr, cs_out = nullptr;  // its copy streams (host to device, device to host)
+  cudaEvent_t pev[6] = {};            // loaded[2], computed[2], drained[2]
   double* adj = nullptr;              // 4P: projected output-side vector of the transpose
   double* adjsum = nullptr;           // 2: reductions of the Grashof derivative
   double* tmp4 = nullptr;             // 4P: residual right-hand side scratch

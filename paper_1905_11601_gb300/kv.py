@@ -26,7 +26,8 @@ EXPORTS = ("kv_create_grid", "kv_destroy_grid", "kv_set_stream", "kv_field_len",
            "kv_krylov_vector", "kv_krylov_vector_host", "kv_arnoldi_step", "kv_newton_residual", "kv_last_error",
            "kv_profile_enable", "kv_profile_get", "kv_krylov_vector_noalloc", "kv_krylov_vector_adjoint",
            "kv_base_flow_gradient", "kv_krylov_vector_batch", "kv_plan_create", "kv_plan_add", "kv_plan_launch",
-           "kv_plan_destroy", "kv_plan_last_error", "kv_selftest_wait_timeout", "kv_tuning")
+           "kv_plan_destroy", "kv_plan_last_error", "kv_selftest_wait_timeout", "kv_tuning",
+           "kv_krylov_vector_host_stream")
 PHASES = {"stencil": 0, "divergence": 1, "tpd": 2, "correct": 3, "arnoldi": 4, "refine": 5, "gs_dots": 6,
           "gs_update": 7}
 
@@ -75,6 +76,7 @@ def load_library(path: str = LIB_PATH):
     lib.kv_profile_get.argtypes = [H, ctypes.c_int, ctypes.POINTER(ctypes.c_double),
                                    ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_longlong)]
     lib.kv_tuning.argtypes = [H, ctypes.POINTER(ctypes.c_int)]
+    lib.kv_krylov_vector_host_stream.argtypes = [H, D, D, ctypes.c_int]
     lib.kv_krylov_vector_adjoint.argtypes = [H, D, D]
     lib.kv_base_flow_gradient.argtypes = [H, D, D, D, ctypes.POINTER(ctypes.c_double)]
     lib.kv_krylov_vector_batch.argtypes = [H, D, D, ctypes.c_int]
@@ -183,6 +185,25 @@ class Grid:
         self._check(self.lib.kv_krylov_vector_host(self.h, hp(x_host, "x_host"), hp(y_host, "y_host"),
                                                    ctypes.byref(st) if stats else None))
         return st if stats else None
+
+    def krylov_vector_host_stream(self, X_host, Y_host):
+        """Y[i] = A X[i] for host float64 tensors/arrays of shape (nb, 4 packed fields) (pinned
+        for the copies to overlap the evaluations)."""
+        self._sync_stream()
+        L = 4 * self.field_len
+
+        def hp(a, name):
+            if isinstance(a, np.ndarray):
+                assert a.dtype == np.float64 and a.flags.c_contiguous and a.size % L == 0, name
+                return a.ctypes.data, a.size // L
+            assert not a.is_cuda and a.dtype == self.torch.float64 and a.is_contiguous(), name
+            assert a.numel() % L == 0, name
+            return a.data_ptr(), a.numel() // L
+
+        px, nb = hp(X_host, "X_host")
+        py, nby = hp(Y_host, "Y_host")
+        assert nb == nby, "X_host and Y_host hold different numbers of vectors"
+        self._check(self.lib.kv_krylov_vector_host_stream(self.h, px, py, nb))
 
     def arnoldi_step(self, V, j):
         self._sync_stream()

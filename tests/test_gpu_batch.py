@@ -82,3 +82,24 @@ def test_bounded_wait_expiry_is_reported_and_grid_stays_usable():
     assert st.device_error == 0
     err = (torch.linalg.vector_norm(y - ref) / torch.linalg.vector_norm(ref)).item()
     assert err < 1e-9
+
+
+def test_host_stream_matches_single_host_calls():
+    """The streamed host-buffer entry point (copies overlapping the evaluations, two staging
+    slots) gives the same vectors as one kv_krylov_vector_host call per vector, for an odd count
+    that cycles both slots, in both precisions."""
+    from paper_1905_11601_gb300 import kv
+    n = (24, 20, 18)
+    base = np.stack(synth.base_flow(*n, synth.CC, 51))
+    X = np.stack([synth.krylov_input(*n, 52 + i)[0] for i in range(5)])
+    for prec in (kv.KV_PREC_FP64, kv.KV_PREC_MIXED):
+        g = kv.Grid(*n, gr=2e6, pr=0.71, precision=prec)
+        g.set_base_flow(torch.from_numpy(base).cuda())
+        Xh = torch.from_numpy(X.reshape(5, -1).copy()).pin_memory()
+        Yh = torch.zeros_like(Xh).pin_memory()
+        g.krylov_vector_host_stream(Xh, Yh)
+        for i in range(5):
+            y1 = torch.zeros(Xh.shape[1], dtype=torch.float64).pin_memory()
+            g.krylov_vector_host(Xh[i].contiguous(), y1)
+            assert torch.equal(Yh[i], y1), (prec, i)
+        g.krylov_vector_host_stream(Xh[:0], Yh[:0])  # nb = 0 does nothing
