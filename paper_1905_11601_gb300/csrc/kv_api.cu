@@ -231,6 +231,7 @@ kv_status autotune_apply(kv_grid* h) {
     best = 1e30f;
     int dv = 0, dbx = 32, dby = 2;
     for (auto& c : dcand) {
+      if (c[0] == 1 && 4 * h->P >= (size_t(1) << 31)) continue;  // the march indexes x with 32 bits
       h->df_variant = c[0];
       h->df_bx = c[1];
       h->df_by = c[2];

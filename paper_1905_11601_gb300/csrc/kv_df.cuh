@@ -64,6 +64,16 @@ __device__ __forceinline__ DF df_add(const DF a, const DF b) {
 
 __device__ __forceinline__ DF df_sub(const DF a, const DF b) { return df_add(a, df_neg(b)); }
 
+// a + b left unnormalised: the head is fl(a.h + b.h), the tail carries the exact TwoSum error of
+// the heads plus both tails (|tail| may exceed ulp(head)/2 by a few ulps; the pair still holds
+// the sum to about 2^-47 of |a| + |b|). For operands of products (DFAcc::fma takes such pairs).
+__device__ __forceinline__ DF df_add_lazy(const DF a, const DF b) {
+  const float s = __fadd_rn(a.h, b.h);
+  const float bp = __fsub_rn(s, a.h);
+  const float e = __fadd_rn(__fsub_rn(a.h, __fsub_rn(s, bp)), __fsub_rn(b.h, bp));
+  return DF{s, __fadd_rn(e, __fadd_rn(a.l, b.l))};
+}
+
 // a * c for an FP32 constant c (exact head product via FMA, tail product rounded)
 __device__ __forceinline__ DF df_mul_f(const DF a, float c) {
   const float p = __fmul_rn(a.h, c);

@@ -455,8 +455,14 @@ __device__ __forceinline__ float beta_of(int cls) { return cls == 0 ? -1.0f : (c
 // a += c- x- + c+ x+ along one axis (see DfAlpha)
 __device__ __forceinline__ void own_axis(DFAcc& a, const float2 cm, const DF xm, const DF xp, const float2 alpha,
                                          const float beta) {
-  a.fma(cm, df_add(xm, DF{beta * xp.h, beta * xp.l}));
+  a.fma(cm, df_add_lazy(xm, DF{beta * xp.h, beta * xp.l}));
   a.fma(alpha, xp);
+}
+
+// Inputs that share a coefficient (the cross terms' 2- and 4-point sums, the buoyancy average)
+// are summed before the one product.
+__device__ __forceinline__ DF sum4(const DF a, const DF b, const DF c, const DF d) {
+  return df_add_lazy(df_add_lazy(df_add_lazy(a, b), c), d);
 }
 
 // Double-float coefficient q (KV_NCOEF_DF of them) = assembled coefficient kDfFromFull[q]: per
@@ -509,14 +515,9 @@ __global__ void __launch_bounds__(512) k_apply_df(KvGeom g, const float2* __rest
     own_axis(a, cx, L(xu, -sx), L(xu, sx), alpha_of(al, 0, 0, 0), -1.0f);
     own_axis(a, cy, L(xu, -sy), L(xu, sy), alpha_of(al, 0, 1, cj), beta_of(cj));
     own_axis(a, cz, L(xu, -sz), L(xu, sz), alpha_of(al, 0, 2, ck), beta_of(ck));
-    a.fma(c7, L(xv, -sy));       // v(i, j-1)
-    a.fma(c7, L(xv, 0));         // v(i, j)
-    a.fma(c7, L(xv, sx - sy));   // v(i+1, j-1)
-    a.fma(c7, L(xv, sx));        // v(i+1, j)
-    a.fma(c8, L(xw, -sz));       // w(i, k-1)
-    a.fma(c8, L(xw, 0));         // w(i, k)
-    a.fma(c8, L(xw, sx - sz));   // w(i+1, k-1)
-    a.fma(c8, L(xw, sx));        // w(i+1, k)
+    // v(i, j-1), v(i, j), v(i+1, j-1), v(i+1, j); w(i, k-1), w(i, k), w(i+1, k-1), w(i+1, k)
+    a.fma(c7, sum4(L(xv, -sy), L(xv, 0), L(xv, sx - sy), L(xv, sx)));
+    a.fma(c8, sum4(L(xw, -sz), L(xw, 0), L(xw, sx - sz), L(xw, sx)));
     vstar[e] = i <= g.nx - 1 ? a.value() : 0.0;
   } else if (eq == 1) {  // v on y-faces
     const float2 c0 = C(6), cx = C(7), cy = C(8), cz = C(9), c16 = C(10), c17 = C(11);
@@ -524,14 +525,9 @@ __global__ void __launch_bounds__(512) k_apply_df(KvGeom g, const float2* __rest
     own_axis(a, cx, L(xv, -sx), L(xv, sx), alpha_of(al, 0, 0, ci), beta_of(ci));
     own_axis(a, cy, L(xv, -sy), L(xv, sy), alpha_of(al, 0, 1, 0), -1.0f);
     own_axis(a, cz, L(xv, -sz), L(xv, sz), alpha_of(al, 0, 2, ck), beta_of(ck));
-    a.fma(c16, L(xu, -sx));      // u(i-1, j)
-    a.fma(c16, L(xu, 0));        // u(i, j)
-    a.fma(c16, L(xu, -sx + sy)); // u(i-1, j+1)
-    a.fma(c16, L(xu, sy));       // u(i, j+1)
-    a.fma(c17, L(xw, -sz));      // w(j, k-1)
-    a.fma(c17, L(xw, 0));        // w(j, k)
-    a.fma(c17, L(xw, sy - sz));  // w(j+1, k-1)
-    a.fma(c17, L(xw, sy));       // w(j+1, k)
+    // u(i-1, j), u(i, j), u(i-1, j+1), u(i, j+1); w(j, k-1), w(j, k), w(j+1, k-1), w(j+1, k)
+    a.fma(c16, sum4(L(xu, -sx), L(xu, 0), L(xu, -sx + sy), L(xu, sy)));
+    a.fma(c17, sum4(L(xw, -sz), L(xw, 0), L(xw, sy - sz), L(xw, sy)));
     vstar[P + e] = j <= g.ny - 1 ? a.value() : 0.0;
   } else if (eq == 2) {  // w on z-faces, with the buoyancy 0.5 (T_k + T_k+1)
     const float2 c0 = C(12), cx = C(13), cy = C(14), cz = C(15), c25 = C(16), c26 = C(17);
@@ -539,17 +535,10 @@ __global__ void __launch_bounds__(512) k_apply_df(KvGeom g, const float2* __rest
     own_axis(a, cx, L(xw, -sx), L(xw, sx), alpha_of(al, 0, 0, ci), beta_of(ci));
     own_axis(a, cy, L(xw, -sy), L(xw, sy), alpha_of(al, 0, 1, cj), beta_of(cj));
     own_axis(a, cz, L(xw, -sz), L(xw, sz), alpha_of(al, 0, 2, 0), -1.0f);
-    a.fma(c25, L(xu, -sx));      // u(i-1, k)
-    a.fma(c25, L(xu, 0));        // u(i, k)
-    a.fma(c25, L(xu, -sx + sz)); // u(i-1, k+1)
-    a.fma(c25, L(xu, sz));       // u(i, k+1)
-    a.fma(c26, L(xv, -sy));      // v(j-1, k)
-    a.fma(c26, L(xv, 0));        // v(j, k)
-    a.fma(c26, L(xv, -sy + sz)); // v(j-1, k+1)
-    a.fma(c26, L(xv, sz));       // v(j, k+1)
-    const float2 half = make_float2(0.5f, 0.0f);
-    a.fma(half, L(xT, 0));
-    a.fma(half, L(xT, sz));
+    // u(i-1, k), u(i, k), u(i-1, k+1), u(i, k+1); v(j-1, k), v(j, k), v(j-1, k+1), v(j, k+1)
+    a.fma(c25, sum4(L(xu, -sx), L(xu, 0), L(xu, -sx + sz), L(xu, sz)));
+    a.fma(c26, sum4(L(xv, -sy), L(xv, 0), L(xv, -sy + sz), L(xv, sz)));
+    a.fma(make_float2(0.5f, 0.0f), df_add_lazy(L(xT, 0), L(xT, sz)));
     vstar[2 * P + e] = k <= g.nz - 1 ? a.value() : 0.0;
   } else {  // T on cells
     const float2 c0 = C(18), cx = C(19), cy = C(20), cz = C(21), c34 = C(22), c35 = C(23), c36 = C(24);
@@ -557,12 +546,9 @@ __global__ void __launch_bounds__(512) k_apply_df(KvGeom g, const float2* __rest
     own_axis(a, cx, L(xT, -sx), L(xT, sx), alpha_of(al, 1, 0, ci), beta_of(ci));
     own_axis(a, cy, L(xT, -sy), L(xT, sy), alpha_of(al, 1, 1, cj), beta_of(cj));
     own_axis(a, cz, L(xT, -sz), L(xT, sz), alpha_of(al, 1, 2, ck), beta_of(ck));
-    a.fma(c34, L(xu, -sx));
-    a.fma(c34, L(xu, 0));
-    a.fma(c35, L(xv, -sy));
-    a.fma(c35, L(xv, 0));
-    a.fma(c36, L(xw, -sz));
-    a.fma(c36, L(xw, 0));
+    a.fma(c34, df_add_lazy(L(xu, -sx), L(xu, 0)));
+    a.fma(c35, df_add_lazy(L(xv, -sy), L(xv, 0)));
+    a.fma(c36, df_add_lazy(L(xw, -sz), L(xw, 0)));
     const double r = a.value();
     if (g.bc == KV_BC_AA && (j == 1 || j == g.ny)) {
       const double t = (g.tproj == KV_TPROJ_OBLIQUE) ? r : 0.5 * r;
@@ -589,10 +575,6 @@ constexpr int MTHREADS = MB_X * MB_Y * 4;
 constexpr int MVALS = 4 * MPTS;                                 // values per plane (4 fields)
 constexpr int MPER = (MVALS + MTHREADS - 1) / MTHREADS;         // values per thread per plane
 
-struct MarchIn {
-  int f, i, j;  // field, padded i, j of one value this thread loads (f < 0: none)
-};
-
 __device__ __forceinline__ double proj_value(const Loader<true>& L, int f, int i, int j, int k) {
   return f == 0 ? L.lu(i, j, k) : (f == 1 ? L.lv(i, j, k) : (f == 2 ? L.lw(i, j, k) : L.lT(i, j, k)));
 }
@@ -602,6 +584,7 @@ __global__ void __launch_bounds__(MTHREADS, 2) k_apply_df_march(KvGeom g, const 
                                                                 double* __restrict__ vstar,
                                                                 double* __restrict__ tout, DfAlpha al, int kc) {
   __shared__ float2 xt[4][4][MPTS];  // [slot][field][point]
+  float2* const xflat = &xt[0][0][0];
   const int tid = threadIdx.x;
   const int tx = tid & 31, warp = tid >> 5;
   const int ty = warp % MB_Y, eq = warp / MB_Y;
@@ -609,23 +592,51 @@ __global__ void __launch_bounds__(MTHREADS, 2) k_apply_df_march(KvGeom g, const 
   const int k0 = 1 + blockIdx.z * kc;
   const int k1 = min(k0 + kc, g.nz + 1);  // planes k0 .. k1-1
   const bool active = i <= g.nx && j <= g.ny;
+  const int sy = g.X, sz = g.X * g.Y;
   Grid G{g};
   const Loader<true> LD{G, x, x + P, x + 2 * P, x + 3 * P};
-  // the values this thread loads for every plane
-  MarchIn mi[MPER];
+  // The values this thread stages for every plane: value v = tid + r MTHREADS of a plane is
+  // field f = v / MPTS at tile point v % MPTS, stored at xt[slot][0][v]. P_BC x there is
+  // x_f(i, j, k) for 1 <= k <= lim[r] and 0 for other planes (col[r]: the (f, i, j) column of x;
+  // lim[r] = 0: always 0), except the temperature rows next to insulated walls (lim[r] < 0),
+  // which proj_value projects (the wall node and its neighbour combine). Offsets into the packed
+  // vector fit 32 bits (the variant is taken only for 4 P < 2^31).
+  unsigned int col[MPER];
+  int lim[MPER];
 #pragma unroll
   for (int r = 0; r < MPER; ++r) {
     const int v = tid + r * MTHREADS;
-    mi[r].f = -1;
+    col[r] = 0;
+    lim[r] = 0;
     if (v < MVALS) {
       const int f = v / MPTS, pt = v - f * MPTS;
       const int ii = blockIdx.x * MB_X + pt % MT_X, jj = blockIdx.y * MB_Y + pt / MT_X;
-      if (ii <= g.nx + 1 && jj <= g.ny + 1) mi[r] = MarchIn{f, ii, jj};
+      if (ii <= g.nx + 1 && jj <= g.ny + 1) {
+        col[r] = (unsigned int)((size_t)f * P + ii + (size_t)sy * jj);
+        const bool in_i = ii >= 1 && ii <= g.nx, in_j = jj >= 1 && jj <= g.ny;
+        if (f == 0)
+          lim[r] = (ii >= 1 && ii <= g.nx - 1 && in_j) ? g.nz : 0;
+        else if (f == 1)
+          lim[r] = (in_i && jj >= 1 && jj <= g.ny - 1) ? g.nz : 0;
+        else if (f == 2)
+          lim[r] = (in_i && in_j) ? g.nz - 1 : 0;
+        else if (g.bc == KV_BC_CC)
+          lim[r] = (in_i && in_j) ? g.nz : 0;
+        else
+          lim[r] = !in_i ? 0 : ((jj >= 2 && jj <= g.ny - 1) ? g.nz : -1);
+      }
     }
   }
   auto fetch = [&](int kk, double (&val)[MPER]) {
 #pragma unroll
-    for (int r = 0; r < MPER; ++r) val[r] = mi[r].f >= 0 ? proj_value(LD, mi[r].f, mi[r].i, mi[r].j, kk) : 0.0;
+    for (int r = 0; r < MPER; ++r) {
+      // lim < 0 compares as a large unsigned limit: the load stays inside the column
+      val[r] = (unsigned)(kk - 1) < (unsigned)lim[r] ? __ldg(x + (col[r] + (unsigned int)(sz * kk))) : 0.0;
+      if (lim[r] < 0) {
+        const int pt = tid + r * MTHREADS - 3 * MPTS;
+        val[r] = proj_value(LD, 3, blockIdx.x * MB_X + pt % MT_X, blockIdx.y * MB_Y + pt / MT_X, kk);
+      }
+    }
   };
   auto put = [&](int slot, const double (&val)[MPER]) {
 #pragma unroll
@@ -633,7 +644,7 @@ __global__ void __launch_bounds__(MTHREADS, 2) k_apply_df_march(KvGeom g, const 
       const int v = tid + r * MTHREADS;
       if (v < MVALS) {
         const DF d = df_split(val[r]);
-        xt[slot][v / MPTS][v % MPTS] = make_float2(d.h, d.l);
+        xflat[slot * MVALS + v] = make_float2(d.h, d.l);
       }
     }
   };
@@ -646,14 +657,16 @@ __global__ void __launch_bounds__(MTHREADS, 2) k_apply_df_march(KvGeom g, const 
   }
   __syncthreads();
   const int ci = wall_class(i, g.nx), cj = wall_class(j, g.ny);
-  const int sy = g.X, sz = g.X * g.Y;
   const int q0 = eq == 0 ? 0 : (eq == 1 ? 6 : (eq == 2 ? 12 : 18));
   const int nqe = eq == 3 ? 7 : 6;
+  // coefficient column of this thread's cell (clamped into the grid for threads past its edge)
+  const float2* const ccol =
+      coef + (size_t)q0 * P + (size_t)min(i, g.nx) + (size_t)sy * min(j, g.ny);
   float2 cn[7];
   auto coefs = [&](int kk, float2 (&c)[7]) {
-    const size_t e = (size_t)i + (size_t)sy * j + (size_t)sz * kk;
+    const float2* const cp = ccol + (size_t)sz * kk;
 #pragma unroll
-    for (int q = 0; q < 7; ++q) c[q] = (active && q < nqe) ? __ldg(coef + (size_t)(q0 + q) * P + e) : make_float2(0.f, 0.f);
+    for (int q = 0; q < 7; ++q) c[q] = q < nqe ? __ldg(cp + (size_t)q * P) : make_float2(0.f, 0.f);
   };
   coefs(k0, cn);
   const int pc = (ty + 1) * MT_X + (tx + 1);  // this cell's point in the tile
@@ -680,57 +693,37 @@ __global__ void __launch_bounds__(MTHREADS, 2) k_apply_df_march(KvGeom g, const 
         own_axis(a, c[1], X(s0, 0, -1, 0), X(s0, 0, 1, 0), alpha_of(al, 0, 0, 0), -1.0f);
         own_axis(a, c[2], X(s0, 0, 0, -1), X(s0, 0, 0, 1), alpha_of(al, 0, 1, cj), beta_of(cj));
         own_axis(a, c[3], X(sm, 0, 0, 0), X(sp, 0, 0, 0), alpha_of(al, 0, 2, ck), beta_of(ck));
-        a.fma(c[4], X(s0, 1, 0, -1));  // v(i, j-1)
-        a.fma(c[4], X(s0, 1, 0, 0));   // v(i, j)
-        a.fma(c[4], X(s0, 1, 1, -1));  // v(i+1, j-1)
-        a.fma(c[4], X(s0, 1, 1, 0));   // v(i+1, j)
-        a.fma(c[5], X(sm, 2, 0, 0));   // w(i, k-1)
-        a.fma(c[5], X(s0, 2, 0, 0));   // w(i, k)
-        a.fma(c[5], X(sm, 2, 1, 0));   // w(i+1, k-1)
-        a.fma(c[5], X(s0, 2, 1, 0));   // w(i+1, k)
+        // v(i, j-1), v(i, j), v(i+1, j-1), v(i+1, j); w(i, k-1), w(i, k), w(i+1, k-1), w(i+1, k)
+        a.fma(c[4], sum4(X(s0, 1, 0, -1), X(s0, 1, 0, 0), X(s0, 1, 1, -1), X(s0, 1, 1, 0)));
+        a.fma(c[5], sum4(X(sm, 2, 0, 0), X(s0, 2, 0, 0), X(sm, 2, 1, 0), X(s0, 2, 1, 0)));
         vstar[e] = i <= g.nx - 1 ? a.value() : 0.0;
       } else if (eq == 1) {
         a.fma(c[0], X(s0, 1, 0, 0));
         own_axis(a, c[1], X(s0, 1, -1, 0), X(s0, 1, 1, 0), alpha_of(al, 0, 0, ci), beta_of(ci));
         own_axis(a, c[2], X(s0, 1, 0, -1), X(s0, 1, 0, 1), alpha_of(al, 0, 1, 0), -1.0f);
         own_axis(a, c[3], X(sm, 1, 0, 0), X(sp, 1, 0, 0), alpha_of(al, 0, 2, ck), beta_of(ck));
-        a.fma(c[4], X(s0, 0, -1, 0));  // u(i-1, j)
-        a.fma(c[4], X(s0, 0, 0, 0));   // u(i, j)
-        a.fma(c[4], X(s0, 0, -1, 1));  // u(i-1, j+1)
-        a.fma(c[4], X(s0, 0, 0, 1));   // u(i, j+1)
-        a.fma(c[5], X(sm, 2, 0, 0));   // w(j, k-1)
-        a.fma(c[5], X(s0, 2, 0, 0));   // w(j, k)
-        a.fma(c[5], X(sm, 2, 0, 1));   // w(j+1, k-1)
-        a.fma(c[5], X(s0, 2, 0, 1));   // w(j+1, k)
+        // u(i-1, j), u(i, j), u(i-1, j+1), u(i, j+1); w(j, k-1), w(j, k), w(j+1, k-1), w(j+1, k)
+        a.fma(c[4], sum4(X(s0, 0, -1, 0), X(s0, 0, 0, 0), X(s0, 0, -1, 1), X(s0, 0, 0, 1)));
+        a.fma(c[5], sum4(X(sm, 2, 0, 0), X(s0, 2, 0, 0), X(sm, 2, 0, 1), X(s0, 2, 0, 1)));
         vstar[P + e] = j <= g.ny - 1 ? a.value() : 0.0;
       } else if (eq == 2) {
         a.fma(c[0], X(s0, 2, 0, 0));
         own_axis(a, c[1], X(s0, 2, -1, 0), X(s0, 2, 1, 0), alpha_of(al, 0, 0, ci), beta_of(ci));
         own_axis(a, c[2], X(s0, 2, 0, -1), X(s0, 2, 0, 1), alpha_of(al, 0, 1, cj), beta_of(cj));
         own_axis(a, c[3], X(sm, 2, 0, 0), X(sp, 2, 0, 0), alpha_of(al, 0, 2, 0), -1.0f);
-        a.fma(c[4], X(s0, 0, -1, 0));  // u(i-1, k)
-        a.fma(c[4], X(s0, 0, 0, 0));   // u(i, k)
-        a.fma(c[4], X(sp, 0, -1, 0));  // u(i-1, k+1)
-        a.fma(c[4], X(sp, 0, 0, 0));   // u(i, k+1)
-        a.fma(c[5], X(s0, 1, 0, -1));  // v(j-1, k)
-        a.fma(c[5], X(s0, 1, 0, 0));   // v(j, k)
-        a.fma(c[5], X(sp, 1, 0, -1));  // v(j-1, k+1)
-        a.fma(c[5], X(sp, 1, 0, 0));   // v(j, k+1)
-        const float2 half = make_float2(0.5f, 0.0f);
-        a.fma(half, X(s0, 3, 0, 0));
-        a.fma(half, X(sp, 3, 0, 0));
+        // u(i-1, k), u(i, k), u(i-1, k+1), u(i, k+1); v(j-1, k), v(j, k), v(j-1, k+1), v(j, k+1)
+        a.fma(c[4], sum4(X(s0, 0, -1, 0), X(s0, 0, 0, 0), X(sp, 0, -1, 0), X(sp, 0, 0, 0)));
+        a.fma(c[5], sum4(X(s0, 1, 0, -1), X(s0, 1, 0, 0), X(sp, 1, 0, -1), X(sp, 1, 0, 0)));
+        a.fma(make_float2(0.5f, 0.0f), df_add_lazy(X(s0, 3, 0, 0), X(sp, 3, 0, 0)));
         vstar[2 * P + e] = k <= g.nz - 1 ? a.value() : 0.0;
       } else {
         a.fma(c[0], X(s0, 3, 0, 0));
         own_axis(a, c[1], X(s0, 3, -1, 0), X(s0, 3, 1, 0), alpha_of(al, 1, 0, ci), beta_of(ci));
         own_axis(a, c[2], X(s0, 3, 0, -1), X(s0, 3, 0, 1), alpha_of(al, 1, 1, cj), beta_of(cj));
         own_axis(a, c[3], X(sm, 3, 0, 0), X(sp, 3, 0, 0), alpha_of(al, 1, 2, ck), beta_of(ck));
-        a.fma(c[4], X(s0, 0, -1, 0));
-        a.fma(c[4], X(s0, 0, 0, 0));
-        a.fma(c[5], X(s0, 1, 0, -1));
-        a.fma(c[5], X(s0, 1, 0, 0));
-        a.fma(c[6], X(sm, 2, 0, 0));
-        a.fma(c[6], X(s0, 2, 0, 0));
+        a.fma(c[4], df_add_lazy(X(s0, 0, -1, 0), X(s0, 0, 0, 0)));
+        a.fma(c[5], df_add_lazy(X(s0, 1, 0, -1), X(s0, 1, 0, 0)));
+        a.fma(c[6], df_add_lazy(X(sm, 2, 0, 0), X(s0, 2, 0, 0)));
         const double r = a.value();
         if (g.bc == KV_BC_AA && (j == 1 || j == g.ny)) {
           const double t = (g.tproj == KV_TPROJ_OBLIQUE) ? r : 0.5 * r;
