@@ -572,6 +572,7 @@ __global__ void __launch_bounds__(512) k_apply_df(KvGeom g, const float2* __rest
 constexpr int MB_X = 32, MB_Y = 4;
 constexpr int MT_X = MB_X + 2, MT_Y = MB_Y + 2, MPTS = MT_X * MT_Y;
 constexpr int MTHREADS = MB_X * MB_Y * 4;
+static_assert((MTHREADS & (MTHREADS - 1)) == 0, "the staging order below rotates thread indices mod MTHREADS");
 constexpr int MVALS = 4 * MPTS;                                 // values per plane (4 fields)
 constexpr int MPER = (MVALS + MTHREADS - 1) / MTHREADS;         // values per thread per plane
 
@@ -595,7 +596,11 @@ __global__ void __launch_bounds__(MTHREADS, 2) k_apply_df_march(KvGeom g, const 
   const int sy = g.X, sz = g.X * g.Y;
   Grid G{g};
   const Loader<true> LD{G, x, x + P, x + 2 * P, x + 3 * P};
-  // The values this thread stages for every plane: value v = tid + r MTHREADS of a plane is
+  // Staging order: ft = (tid + 128) mod 512, so the 304 threads that stage a second value per
+  // plane are the temperature warps (the fewest products) and the first momentum warps; the
+  // w warps (buoyancy terms) stage one.
+  const int ft = (tid + 128) & (MTHREADS - 1);
+  // The values this thread stages for every plane: value v = ft + r MTHREADS of a plane is
   // field f = v / MPTS at tile point v % MPTS, stored at xt[slot][0][v]. P_BC x there is
   // x_f(i, j, k) for 1 <= k <= lim[r] and 0 for other planes (col[r]: the (f, i, j) column of x;
   // lim[r] = 0: always 0), except the temperature rows next to insulated walls (lim[r] < 0),
@@ -605,7 +610,7 @@ __global__ void __launch_bounds__(MTHREADS, 2) k_apply_df_march(KvGeom g, const 
   int lim[MPER];
 #pragma unroll
   for (int r = 0; r < MPER; ++r) {
-    const int v = tid + r * MTHREADS;
+    const int v = ft + r * MTHREADS;
     col[r] = 0;
     lim[r] = 0;
     if (v < MVALS) {
@@ -633,7 +638,7 @@ __global__ void __launch_bounds__(MTHREADS, 2) k_apply_df_march(KvGeom g, const 
       // lim < 0 compares as a large unsigned limit: the load stays inside the column
       val[r] = (unsigned)(kk - 1) < (unsigned)lim[r] ? __ldg(x + (col[r] + (unsigned int)(sz * kk))) : 0.0;
       if (lim[r] < 0) {
-        const int pt = tid + r * MTHREADS - 3 * MPTS;
+        const int pt = ft + r * MTHREADS - 3 * MPTS;
         val[r] = proj_value(LD, 3, blockIdx.x * MB_X + pt % MT_X, blockIdx.y * MB_Y + pt / MT_X, kk);
       }
     }
@@ -641,7 +646,7 @@ __global__ void __launch_bounds__(MTHREADS, 2) k_apply_df_march(KvGeom g, const 
   auto put = [&](int slot, const double (&val)[MPER]) {
 #pragma unroll
     for (int r = 0; r < MPER; ++r) {
-      const int v = tid + r * MTHREADS;
+      const int v = ft + r * MTHREADS;
       if (v < MVALS) {
         const DF d = df_split(val[r]);
         xflat[slot * MVALS + v] = make_float2(d.h, d.l);
