@@ -61,3 +61,5 @@ def test_null_arguments_rejected(lib):
     assert lib.kv_arnoldi_step(None, None, 0, None) == -1
     assert lib.kv_newton_residual(None, None, None, None) == -1
     assert lib.kv_set_base_flow(None, None) == -1
+    assert lib.kv_krylov_vector_host(None, None, None, None) == -1
+    assert lib.kv_krylov_vector_host_stream(None, None, None, 1) == -1
