@@ -1,0 +1,130 @@
+"""Pins of the oracle's Krylov solvers and Newton iteration (oracle/solvers.py) against facts fixed
+by linear algebra: a direct dense solve, the least-squares characterisation of a GMRES cycle,
+the finite termination of BiCG for a matrix with two distinct eigenvalues, manufactured
+solutions on the Krylov-vector map, and the quadratic convergence of Newton's method (Section 2,
+steps 1-4). CPU only."""
+import importlib.util
+import os
+
+import numpy as np
+import pytest
+
+from oracle.oracle import Oracle
+from paper_1905_11601_gb300 import synth
+
+# the solvers under test: oracle/solvers.py, or a copy with a planted mistake
+# (tests/test_oracle_solver_mutations.py sets KV_SOLVERS_PATH)
+_path = os.environ.get("KV_SOLVERS_PATH")
+if _path:
+    _spec = importlib.util.spec_from_file_location("kv_solvers_under_test", _path)
+    _solvers = importlib.util.module_from_spec(_spec)
+    _spec.loader.exec_module(_solvers)
+else:
+    from oracle import solvers as _solvers
+bicgstab2, gmres, newton = _solvers.bicgstab2, _solvers.gmres, _solvers.newton
+
+
+def dense_system(n, seed):
+    rng = np.random.default_rng(seed)
+    A = 4.0 * np.eye(n) + rng.standard_normal((n, n)) * 0.5 / np.sqrt(n) \
+        + np.triu(rng.standard_normal((n, n)), 1) * 0.3 / np.sqrt(n)
+    return A, rng.standard_normal(n)
+
+
+def test_gmres_dense_matches_direct_solve():
+    A, b = dense_system(60, 1)
+    xt = np.linalg.solve(A, b)
+    x, info = gmres(lambda v: A @ v, b, np.zeros(60), m=10, max_restarts=50, tol=1e-12)
+    assert info["converged"] and info["restarts"] >= 2  # restarted, not one full cycle
+    assert np.linalg.norm(x - xt) < 1e-10 * np.linalg.norm(xt)
+    assert np.linalg.norm(b - A @ x) <= 1e-12 * np.linalg.norm(b) * 1.01
+
+
+def test_gmres_cycle_is_least_squares_minimiser_over_krylov_space():
+    """One cycle of GMRES(k) from x0 = 0 returns argmin ||b - A x|| over span{b, Ab, ..,
+    A^(k-1) b}; the minimiser is recomputed here from a QR-orthonormalised power basis and
+    numpy's least squares, independently of the Arnoldi/Givens path."""
+    A, b = dense_system(40, 2)
+    k = 7
+    x, info = gmres(lambda v: A @ v, b, np.zeros(40), m=k, max_restarts=1, tol=0.0)
+    assert info["iterations"] == k and info["restarts"] == 1
+    K = np.stack([np.linalg.matrix_power(A, i) @ b for i in range(k)], axis=1)
+    Q, _ = np.linalg.qr(K)
+    y, *_ = np.linalg.lstsq(A @ Q, b, rcond=None)
+    assert np.linalg.norm(x - Q @ y) < 1e-10 * np.linalg.norm(x)
+
+
+def test_gmres_saturation_stops_restarts():
+    """A cycle that cannot reduce the residual (m = 1 on a rotation) is reported as saturated."""
+    A = np.array([[0.0, 1.0], [-1.0, 0.0]])
+    b = np.array([1.0, 0.0])
+    x, info = gmres(lambda v: A @ v, b, np.zeros(2), m=1, max_restarts=10, tol=1e-12, sat=0.99)
+    assert info["saturated"] and not info["converged"] and info["restarts"] == 1
+
+
+def test_bicgstab2_dense_matches_direct_solve():
+    A, b = dense_system(60, 3)
+    xt = np.linalg.solve(A, b)
+    x, info = bicgstab2(lambda v: A @ v, b, np.zeros(60), max_iter=200, tol=1e-12)
+    assert info["converged"] and not info["breakdown"]
+    assert info["matvecs"] == 4 * info["iterations"] + 2
+    assert np.linalg.norm(x - xt) < 1e-10 * np.linalg.norm(xt)
+
+
+def test_bicgstab2_terminates_for_two_distinct_eigenvalues():
+    """A = Q diag(2, .., 2, 5, .., 5) Q^T has a degree-2 minimal polynomial, so the two BiCG steps
+    of the first BiCGstab(2) iteration already give the exact solution."""
+    rng = np.random.default_rng(4)
+    Q, _ = np.linalg.qr(rng.standard_normal((30, 30)))
+    A = Q @ np.diag([2.0] * 13 + [5.0] * 17) @ Q.T
+    b = rng.standard_normal(30)
+    x, info = bicgstab2(lambda v: A @ v, b, np.zeros(30), max_iter=1, tol=0.0)
+    assert info["iterations"] == 1
+    assert np.linalg.norm(x - np.linalg.solve(A, b)) < 1e-12 * np.linalg.norm(x)
+
+
+def _operator_case(gr=1e4):
+    n = (6, 6, 6)
+    o = Oracle(*n, gr=gr)
+    S = np.stack(synth.base_flow(*n, synth.CC, 41))
+    z = o.project_input(synth.krylov_input(*n, 7)[0])
+    x_true = o.krylov_vector(S, z)           # inside the space the Krylov vectors span
+    b = o.krylov_vector(S, x_true)
+    return o, S, x_true, b
+
+
+def test_gmres_recovers_manufactured_solution_of_krylov_map():
+    o, S, x_true, b = _operator_case()
+    x, info = gmres(lambda v: o.krylov_vector(S, v), b, np.zeros_like(b), m=30, max_restarts=20, tol=1e-12)
+    assert info["converged"]
+    assert np.linalg.norm(x - x_true) < 1e-9 * np.linalg.norm(x_true)
+
+
+def test_bicgstab2_recovers_manufactured_solution_of_krylov_map():
+    o, S, x_true, b = _operator_case()
+    x, info = bicgstab2(lambda v: o.krylov_vector(S, v), b, np.zeros_like(b), max_iter=200, tol=1e-12)
+    assert info["converged"]
+    assert np.linalg.norm(x - x_true) < 1e-9 * np.linalg.norm(x_true)
+
+
+@pytest.mark.parametrize("bc", [synth.CC, synth.AA])
+def test_newton_converges_quadratically_to_a_steady_state(bc):
+    """Steps 1-4 of Section 2 from the synthetic base flow at Gr = 1e4: the residual falls to
+    rounding, each of the last steps roughly squares it, and the returned state's residual,
+    recomputed, is at rounding level."""
+    n = (6, 6, 6)
+    o = Oracle(*n, bc=bc, gr=1e4)
+    S0 = np.stack(synth.base_flow(*n, bc, 41))
+    S, info = newton(o, S0, max_newton=10, tol=1e-10, m=30, max_restarts=20, lin_tol=1e-11, sat=0.99,
+                     bicg_max_iter=300)
+    r = info["res_norms"]
+    assert info["converged"] and 4 <= info["iterations"] <= 8
+    # quadratic phase: ||F_{k+1}|| <= C ||F_k||^2 with a modest C once ||F_k|| < 1e-2
+    tail = [(a, c) for a, c in zip(r[:-1], r[1:]) if a < 1e-2 and c > 1e-13]
+    assert tail and all(c <= 10.0 * a * a for a, c in tail)
+    _, nrm = o.newton_residual(S)
+    assert nrm < 1e-10
+    # the wall values of the state (inhomogeneous boundary conditions) are untouched
+    wall = np.zeros(S.shape, dtype=bool)
+    wall[3, :, :, 0] = wall[3, :, :, -1] = True  # the isothermal walls x = 0, 1 of Theta
+    assert np.array_equal(S[wall], S0[wall])
