@@ -369,7 +369,8 @@ def timed(fn, reps, warm=1):
 def extras(base_np, x_np, w, kv, synth):
     """The batched forms: a block of 16 right-hand sides at 256^3 replayed from one CUDA graph,
     and a plan of 12 grids {100^3 x4, 128^3 x4, 200^3 x2, 256^3 x2} (Gr in [1e6, 4e6], both
-    spanwise boundary types) evaluated by one graph launch. Mixed precision."""
+    spanwise boundary types) evaluated by one graph launch; a 100-step Arnoldi run at 256^3; and
+    Newton's method for a steady state at 64^3. Mixed precision."""
     import numpy as np
     import torch
 
@@ -426,6 +427,31 @@ def extras(base_np, x_np, w, kv, synth):
                          "rightmost_ritz": [[float(z.real), float(z.imag)] for z in theta],
                          "ritz_residual": [float(r) for r in res]}
     del V, Vm, g
+    torch.cuda.empty_cache()
+    # Newton's method (Section 2) for a steady state at 64^3 (CC, Gr = 1e4) from the synthetic
+    # base flow: GMRES(100) restarted until it converges or saturates, then BiCGstab(2) from its
+    # result (Section 3.1), mixed precision; stop at ||F|| < 1e-9 ||F_0||
+    n = 64
+    gq = kv.Grid(n, n, n, bc=synth.CC, gr=1e4, pr=0.71, precision=kv.KV_PREC_MIXED)
+    S = torch.from_numpy(np.stack(synth.base_flow(n, n, n, synth.CC, 11900))).cuda()
+    _, f0 = gq.newton_residual(S)
+    V = torch.empty((101, 4) + gq.shape, dtype=torch.float64, device="cuda")
+    work = torch.empty((10, 4) + gq.shape, dtype=torch.float64, device="cuda")
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    st = gq.newton(S, V, work, max_newton=12, tol=1e-9 * f0, gmres_m=100, gmres_max_restarts=100, lin_tol=1e-10,
+                   gmres_sat=0.99, bicg_max_iter=300)
+    torch.cuda.synchronize()
+    t = time.perf_counter() - t0
+    out["newton64"] = {"workload": "64^3 CC, Gr = 1e4, Pr = 0.71: steady state by Newton's method from the synthetic "
+                                   "base flow; GMRES(100) restarted until converged or saturated, then BiCGstab(2) "
+                                   "(at most 300 iterations); mixed precision",
+                       "value": st.matvecs / t, "unit": "Krylov-vector evals/s inside the solves", "seconds": t,
+                       "newton_iterations": st.iterations, "converged": bool(st.converged), "matvecs": st.matvecs,
+                       "gmres_restarts": st.gmres_restarts, "bicg_iterations": st.bicg_iterations,
+                       "bicg_rejected": st.bicg_rejected,
+                       "res_norms": [float(r) for r in st.res_norm[:st.n_res]]}
+    del V, work, S, gq
     torch.cuda.empty_cache()
     return out
 

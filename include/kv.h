@@ -195,6 +195,78 @@ kv_status kv_base_flow_gradient(kv_handle h, const double* x, const double* y, d
    norm_out: optional HOST pointer receiving ||F||_2 (synchronises the stream). */
 kv_status kv_newton_residual(kv_handle h, const double* S, double* F, double* norm_out);
 
+/* ---- Newton-Krylov: the method's steps either side of the path ----------------------------
+   Section 2 (Newton steps 1-4) and Section 3.1: the Jacobian systems are solved by GMRES
+   restarted after every m Krylov vectors (m = 100 in the paper) until it saturates, then by
+   BiCGstab(2) from GMRES's last approximation. The products with the Jacobian are
+   kv_krylov_vector at the handle's base flow (A = projected J, Eqs (11)-(13)), so b, x and
+   every vector below are packed vectors (device) in the space of Krylov vectors. Solvers:
+   GMRES(m) of Saad and Schultz (1986); BiCGstab(l) of Sleijpen and Fokkema (1993), l = 2 (the
+   paper defers both to its reference [17]). The host drives the iterations; every call
+   synchronises the stream. */
+typedef struct {
+  int iterations;      /* GMRES: Arnoldi steps in all cycles; BiCGstab(2): iterations (two BiCG
+                          steps = 4 Krylov vectors, then the minimal-residual update) */
+  int restarts;        /* GMRES: cycles run */
+  int matvecs;         /* Krylov-vector evaluations (products with A) */
+  int converged;       /* rel_residual <= tol */
+  int saturated;       /* GMRES: stopped because a cycle began with a residual above sat times
+                          the previous cycle's */
+  int breakdown;       /* BiCGstab(2): stopped on a zero or non-finite denominator; x is the last
+                          complete iterate */
+  double rel_residual; /* ||b - A x|| / ||b|| of the returned x, recomputed */
+} kv_solve_stats;
+
+/* Restarted GMRES(m) for A x = b, starting from x (in-out). V: caller-owned device workspace of
+   m + 1 packed vectors (the Arnoldi basis; kv_arnoldi_step builds it). A cycle starts from
+   r = b - A x, stops early once the Givens-rotated least-squares residual is at most tol ||b||,
+   and adds the minimiser V y to x. Cycles repeat until converged, saturated (the cycle's starting
+   residual above sat times the previous cycle's; the paper's hand-over to BiCGstab(2)) or
+   max_restarts cycles. b = 0 gives x = 0. st (host, nullable) receives the statistics.
+   KV_ERR_ARG for NULL or overlapping vectors, m outside 1..4095, max_restarts < 1, tol < 0,
+   sat <= 0; KV_ERR_STATE without a base flow. */
+kv_status kv_gmres(kv_handle h, const double* b, double* x, double* V, int m, int max_restarts, double tol,
+                   double sat, kv_solve_stats* st);
+
+/* BiCGstab(2) for A x = b, starting from x (in-out), shadow residual = the initial residual.
+   work: caller-owned device workspace of 8 packed vectors. Stops when ||r|| <= tol ||b||, after
+   max_iter iterations, or on a breakdown (see kv_solve_stats). b = 0 gives x = 0. Errors as
+   kv_gmres. */
+kv_status kv_bicgstab2(kv_handle h, const double* b, double* x, double* work, int max_iter, double tol,
+                       kv_solve_stats* st);
+
+#define KV_NEWTON_HISTORY 64
+typedef struct {
+  int max_newton;         /* Newton corrections at most (0..KV_NEWTON_HISTORY - 1) */
+  double tol;             /* stop once ||F(S)|| < tol (the projected residual, as kv_newton_residual) */
+  int gmres_m;            /* Krylov vectors per GMRES cycle (the paper: 100) */
+  int gmres_max_restarts; /* GMRES cycles per Newton step at most */
+  double lin_tol;         /* relative residual of each linear solve */
+  double gmres_sat;       /* GMRES saturation factor (e.g. 0.99) */
+  int bicg_max_iter;      /* BiCGstab(2) iterations after an unconverged GMRES (0: none) */
+} kv_newton_params;
+
+typedef struct {
+  int iterations;      /* Newton corrections applied */
+  int matvecs;         /* Krylov-vector evaluations in the linear solves */
+  int gmres_restarts;  /* GMRES cycles in all */
+  int bicg_iterations; /* BiCGstab(2) iterations in all */
+  int bicg_rejected;   /* BiCGstab(2) corrections not taken (recomputed residual not below GMRES's) */
+  int converged;       /* ||F(S)|| < tol at exit */
+  int n_res;           /* entries of res_norm */
+  double res_norm[KV_NEWTON_HISTORY]; /* ||F|| at the start of each Newton step */
+} kv_newton_stats;
+
+/* Newton's method (Section 2, steps 1-4) for the steady state S (device packed state, in-out,
+   with its inhomogeneous wall values, which the corrections leave unchanged): F = the projected
+   residual of S; stop once ||F|| < tol; set the base flow to S (the Jacobian at S) and solve
+   A d = F with kv_gmres from d = 0, then kv_bicgstab2 from GMRES's result if GMRES did not
+   converge, keeping the correction with the smaller recomputed residual; S <- S - d. V: m + 1 packed vectors; work: 10 packed vectors (device, caller-owned).
+   Leaves the handle's base flow at the last S that took a correction. st: host, nullable.
+   KV_ERR_ARG for NULL or overlapping buffers or parameters outside their ranges. */
+kv_status kv_newton(kv_handle h, double* S, double* V, double* work, const kv_newton_params* prm,
+                    kv_newton_stats* st);
+
 /* Instrumentation (not part of the method): launch counts per phase, always kept, and, when
    enabled, per-phase CUDA-event timings on the handle's stream. Phases: 0 = linearised
    operator stencil, 1 = divergence, 2 = TPF Poisson contractions (one timing per per-axis

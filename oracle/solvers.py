@@ -200,12 +200,13 @@ def newton(oracle, S0, max_newton, tol, m, max_restarts, lin_tol, sat, bicg_max_
     """The Newton method of Section 2 on the oracle's discretisation: F = the projected steady
     residual of S (oracle.newton_residual); stop once ||F|| < tol; solve A d = F, A the Krylov
     map at the base S, by GMRES(m) restarted until it converges or saturates, then BiCGstab(2)
-    from GMRES's last approximation if it has not converged; S <- S - d.
+    from GMRES's last approximation if it has not converged, keeping whichever correction has the
+    smaller recomputed residual; S <- S - d.
 
     Returns (S, info): iterations, matvecs, res_norms (||F|| at each Newton step start),
-    converged."""
+    converged, bicg_rejected (BiCGstab(2) results not taken)."""
     S = np.array(S0, dtype=np.float64, copy=True)
-    info = dict(iterations=0, matvecs=0, res_norms=[], converged=False)
+    info = dict(iterations=0, matvecs=0, res_norms=[], converged=False, bicg_rejected=0)
     for _ in range(max_newton + 1):
         F, nrm = oracle.newton_residual(S)
         info["res_norms"].append(nrm)
@@ -221,8 +222,14 @@ def newton(oracle, S0, max_newton, tol, m, max_restarts, lin_tol, sat, bicg_max_
         d, gi = gmres(matvec, F, np.zeros_like(F), m, max_restarts, lin_tol, sat)
         info["matvecs"] += gi["matvecs"]
         if not gi["converged"]:
-            d, bi = bicgstab2(matvec, F, d, bicg_max_iter, lin_tol)
+            d2, bi = bicgstab2(matvec, F, d, bicg_max_iter, lin_tol)
             info["matvecs"] += bi["matvecs"]
+            # BiCGstab(2) replaces GMRES's correction only with a smaller recomputed residual
+            # (started at the rounding level of the Krylov vectors it can stagnate or diverge)
+            if bi["rel_residual"] < gi["rel_residual"]:
+                d = d2
+            else:
+                info["bicg_rejected"] += 1
         S = S - d
         info["iterations"] += 1
     return S, info

@@ -92,6 +92,7 @@ void free_all(kv_grid* h) {
   cudaFree(h->red);
   cudaFree(h->partials);
   cudaFree(h->hdev);
+  cudaFree(h->solve_buf);
   cudaFree(h->stage);
   cudaFree(h->pipe);
   for (auto& e : h->pev)

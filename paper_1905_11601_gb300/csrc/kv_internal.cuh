@@ -56,6 +56,8 @@ struct kv_grid {
   size_t partials_cap = 0;            // in doubles
   double* hdev = nullptr;             // Arnoldi coefficients on the device
   size_t hdev_cap = 0;
+  double* solve_buf = nullptr;        // Krylov solvers: inner-product partials and small arrays
+  size_t solve_cap = 0;
   double* stage = nullptr;            // 8P: staging for the host-buffer entry point
   double* pipe = nullptr;             // 16P: two x and two y staging vectors of the streamed host entry point
   cudaStream_t cs_in = nullptr, cs_out = nullptr;  // its copy streams (host to device, device to host)

@@ -27,7 +27,7 @@ EXPORTS = ("kv_create_grid", "kv_destroy_grid", "kv_set_stream", "kv_field_len",
            "kv_profile_enable", "kv_profile_get", "kv_krylov_vector_noalloc", "kv_krylov_vector_adjoint",
            "kv_base_flow_gradient", "kv_krylov_vector_batch", "kv_plan_create", "kv_plan_add", "kv_plan_launch",
            "kv_plan_destroy", "kv_plan_last_error", "kv_selftest_wait_timeout", "kv_tuning",
-           "kv_krylov_vector_host_stream")
+           "kv_krylov_vector_host_stream", "kv_gmres", "kv_bicgstab2", "kv_newton")
 PHASES = {"stencil": 0, "divergence": 1, "tpd": 2, "correct": 3, "arnoldi": 4, "refine": 5, "gs_dots": 6,
           "gs_update": 7}
 
@@ -48,6 +48,29 @@ class GridDesc(ctypes.Structure):
 class Stats(ctypes.Structure):
     _fields_ = [("passes", ctypes.c_int), ("max_div", ctypes.c_double), ("rel_div", ctypes.c_double),
                 ("refine_residual", ctypes.c_double), ("device_error", ctypes.c_int)]
+
+
+class SolveStats(ctypes.Structure):
+    """kv_solve_stats of kv_gmres / kv_bicgstab2."""
+    _fields_ = [("iterations", ctypes.c_int), ("restarts", ctypes.c_int), ("matvecs", ctypes.c_int),
+                ("converged", ctypes.c_int), ("saturated", ctypes.c_int), ("breakdown", ctypes.c_int),
+                ("rel_residual", ctypes.c_double)]
+
+
+NEWTON_HISTORY = 64
+
+
+class NewtonParams(ctypes.Structure):
+    _fields_ = [("max_newton", ctypes.c_int), ("tol", ctypes.c_double), ("gmres_m", ctypes.c_int),
+                ("gmres_max_restarts", ctypes.c_int), ("lin_tol", ctypes.c_double), ("gmres_sat", ctypes.c_double),
+                ("bicg_max_iter", ctypes.c_int)]
+
+
+class NewtonStats(ctypes.Structure):
+    _fields_ = [("iterations", ctypes.c_int), ("matvecs", ctypes.c_int), ("gmres_restarts", ctypes.c_int),
+                ("bicg_iterations", ctypes.c_int), ("bicg_rejected", ctypes.c_int), ("converged", ctypes.c_int),
+                ("n_res", ctypes.c_int),
+                ("res_norm", ctypes.c_double * NEWTON_HISTORY)]
 
 
 _lib = None
@@ -77,6 +100,10 @@ def load_library(path: str = LIB_PATH):
                                    ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_longlong)]
     lib.kv_tuning.argtypes = [H, ctypes.POINTER(ctypes.c_int)]
     lib.kv_krylov_vector_host_stream.argtypes = [H, D, D, ctypes.c_int]
+    lib.kv_gmres.argtypes = [H, D, D, D, ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double,
+                             ctypes.POINTER(SolveStats)]
+    lib.kv_bicgstab2.argtypes = [H, D, D, D, ctypes.c_int, ctypes.c_double, ctypes.POINTER(SolveStats)]
+    lib.kv_newton.argtypes = [H, D, D, D, ctypes.POINTER(NewtonParams), ctypes.POINTER(NewtonStats)]
     lib.kv_krylov_vector_adjoint.argtypes = [H, D, D]
     lib.kv_base_flow_gradient.argtypes = [H, D, D, D, ctypes.POINTER(ctypes.c_double)]
     lib.kv_krylov_vector_batch.argtypes = [H, D, D, ctypes.c_int]
@@ -204,6 +231,42 @@ class Grid:
         py, nby = hp(Y_host, "Y_host")
         assert nb == nby, "X_host and Y_host hold different numbers of vectors"
         self._check(self.lib.kv_krylov_vector_host_stream(self.h, px, py, nb))
+
+    def gmres(self, b, x, V, m, max_restarts, tol, sat=0.99):
+        """Restarted GMRES(m) for A x = b (kv_gmres): x in-out, V an (m + 1)-vector workspace
+        (CUDA float64 tensors). Returns SolveStats."""
+        self._sync_stream()
+        L = 4 * self.field_len
+        st = SolveStats()
+        self._check(self.lib.kv_gmres(self.h, _dev_ptr(b, self.torch, "b", L), _dev_ptr(x, self.torch, "x", L),
+                                      _dev_ptr(V, self.torch, "V", (m + 1) * L), m, max_restarts, tol, sat,
+                                      ctypes.byref(st)))
+        return st
+
+    def bicgstab2(self, b, x, work, max_iter, tol):
+        """BiCGstab(2) for A x = b (kv_bicgstab2): x in-out, work an 8-vector workspace. Returns
+        SolveStats."""
+        self._sync_stream()
+        L = 4 * self.field_len
+        st = SolveStats()
+        self._check(self.lib.kv_bicgstab2(self.h, _dev_ptr(b, self.torch, "b", L), _dev_ptr(x, self.torch, "x", L),
+                                          _dev_ptr(work, self.torch, "work", 8 * L), max_iter, tol,
+                                          ctypes.byref(st)))
+        return st
+
+    def newton(self, S, V, work, max_newton=10, tol=1e-10, gmres_m=100, gmres_max_restarts=40, lin_tol=1e-10,
+               gmres_sat=0.99, bicg_max_iter=1000):
+        """Newton's method for the steady state (kv_newton): S in-out (packed state with its wall
+        values), V an (m + 1)-vector and work a 10-vector workspace. Returns NewtonStats."""
+        self._sync_stream()
+        L = 4 * self.field_len
+        prm = NewtonParams(max_newton, tol, gmres_m, gmres_max_restarts, lin_tol, gmres_sat, bicg_max_iter)
+        st = NewtonStats()
+        self._check(self.lib.kv_newton(self.h, _dev_ptr(S, self.torch, "S", L),
+                                       _dev_ptr(V, self.torch, "V", (gmres_m + 1) * L),
+                                       _dev_ptr(work, self.torch, "work", 10 * L), ctypes.byref(prm),
+                                       ctypes.byref(st)))
+        return st
 
     def arnoldi_step(self, V, j):
         self._sync_stream()

@@ -1,0 +1,181 @@
+"""GPU parity of the Newton-Krylov layer (kv_gmres, kv_bicgstab2, kv_newton) against the oracle's
+solvers (oracle/solvers.py) on the same seeded inputs, through the C ABI.
+
+Tolerances: a GMRES cycle or a few BiCGstab(2) iterations are fixed functions of the products
+with A, which the FP64 path reproduces to ~1e-13; the solution after a cycle inherits that times
+the conditioning of the small least-squares problem, so 1e-9 relative. Converged solves and
+Newton states are compared with the manufactured solution or the oracle's converged state at the
+solver tolerance times a conditioning allowance (1e-8 FP64, 1e-7 mixed precision)."""
+import numpy as np
+import pytest
+
+from oracle import Oracle
+from oracle.solvers import bicgstab2, gmres, newton
+from paper_1905_11601_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1905_11601_gb300 import build
+    build.build()
+
+
+def kvmod():
+    from paper_1905_11601_gb300 import kv
+    return kv
+
+
+def rel(a, b):
+    return np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300)
+
+
+def case(n, bc, gr, precision=0):
+    """Grid with the synthetic base flow; oracle; a manufactured system b = A x_true with x_true
+    a Krylov vector (oracle-computed)."""
+    kv = kvmod()
+    S = np.stack(synth.base_flow(*n, bc, 41))
+    g = kv.Grid(*n, bc=bc, gr=gr, pr=0.71, precision=precision)
+    g.set_base_flow(torch.from_numpy(S).cuda())
+    o = Oracle(*n, bc=bc, gr=gr, pr=0.71)
+    z = o.project_input(synth.krylov_input(*n, 7)[0])
+    x_true = o.krylov_vector(S, z)
+    b = o.krylov_vector(S, x_true)
+    return g, o, S, x_true, b
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+@pytest.mark.parametrize("bc", [synth.CC, synth.AA])
+def test_gmres_cycle_matches_oracle(bc):
+    n, m = (8, 8, 8), 12
+    g, o, S, x_true, b = case(n, bc, 1e4)
+    x_ref, info = gmres(lambda v: o.krylov_vector(S, v), b, np.zeros_like(b), m, 1, 0.0)
+    x = torch.zeros_like(dev(b))
+    V = torch.empty((m + 1,) + x.shape, dtype=torch.float64, device="cuda")
+    st = g.gmres(dev(b), x, V, m, 1, 0.0)
+    assert st.restarts == 1 and st.iterations == m and st.matvecs == info["matvecs"] == m + 2
+    assert rel(x.cpu().numpy(), x_ref) < 1e-9
+    assert abs(st.rel_residual - info["rel_residual"]) < 1e-9 * max(info["rel_residual"], 1e-3)
+
+
+@pytest.mark.parametrize("precision,tol,bar", [(0, 1e-11, 1e-8), (1, 1e-10, 1e-7)])
+def test_gmres_restarted_solves_manufactured_system(precision, tol, bar):
+    n = (16, 16, 16) if precision else (8, 8, 8)
+    g, o, S, x_true, b = case(n, synth.CC, 1e4, precision)
+    x = torch.zeros_like(dev(b))
+    V = torch.empty((31,) + x.shape, dtype=torch.float64, device="cuda")
+    st = g.gmres(dev(b), x, V, 30, 40, tol)
+    assert st.converged and st.restarts >= 2 and st.rel_residual <= tol
+    assert rel(x.cpu().numpy(), x_true) < bar
+
+
+@pytest.mark.parametrize("bc", [synth.CC, synth.AA])
+def test_bicgstab2_iterations_match_oracle(bc):
+    n, k = (8, 8, 8), 3
+    g, o, S, x_true, b = case(n, bc, 1e4)
+    x_ref, info = bicgstab2(lambda v: o.krylov_vector(S, v), b, np.zeros_like(b), k, 0.0)
+    x = torch.zeros_like(dev(b))
+    work = torch.empty((8,) + x.shape, dtype=torch.float64, device="cuda")
+    st = g.bicgstab2(dev(b), x, work, k, 0.0)
+    assert st.iterations == k and st.matvecs == info["matvecs"] and not st.breakdown
+    assert rel(x.cpu().numpy(), x_ref) < 1e-9
+
+
+@pytest.mark.parametrize("precision,tol,bar", [(0, 1e-11, 1e-8), (1, 1e-10, 1e-7)])
+def test_bicgstab2_solves_manufactured_system(precision, tol, bar):
+    n = (16, 16, 16) if precision else (8, 8, 8)
+    g, o, S, x_true, b = case(n, synth.CC, 1e4, precision)
+    x = torch.zeros_like(dev(b))
+    work = torch.empty((8,) + x.shape, dtype=torch.float64, device="cuda")
+    st = g.bicgstab2(dev(b), x, work, 300, tol)
+    assert st.converged and st.rel_residual <= tol
+    assert rel(x.cpu().numpy(), x_true) < bar
+
+
+_NEWTON_REF = {}
+
+
+def oracle_newton(n, bc):
+    """The oracle's Newton run from the synthetic state at Gr = 1e4 (cached per case)."""
+    if (n, bc) not in _NEWTON_REF:
+        S0 = np.stack(synth.base_flow(*n, bc, 41))
+        o = Oracle(*n, bc=bc, gr=1e4, pr=0.71)
+        S_ref, info = newton(o, S0, 10, 1e-10, 30, 20, 1e-11, 0.99, 300)
+        _NEWTON_REF[(n, bc)] = (S0, o, S_ref, info)
+    return _NEWTON_REF[(n, bc)]
+
+
+@pytest.mark.parametrize("bc", [synth.CC, synth.AA])
+def test_newton_matches_oracle(bc):
+    """Section 2's Newton steps on the GPU and in the oracle from the same synthetic state at
+    Gr = 1e4 (8^3, FP64): same number of corrections, residual histories and converged state."""
+    n = (8, 8, 8)
+    kv = kvmod()
+    S0, o, S_ref, info = oracle_newton(n, bc)
+    g = kv.Grid(*n, bc=bc, gr=1e4, pr=0.71)
+    S = dev(S0)
+    V = torch.empty((31,) + S.shape, dtype=torch.float64, device="cuda")
+    work = torch.empty((10,) + S.shape, dtype=torch.float64, device="cuda")
+    st = g.newton(S, V, work, max_newton=10, tol=1e-10, gmres_m=30, gmres_max_restarts=20, lin_tol=1e-11,
+                  gmres_sat=0.99, bicg_max_iter=300)
+    assert st.converged and info["converged"] and st.iterations == info["iterations"]
+    hist = np.array(st.res_norm[:st.n_res])
+    ref = np.array(info["res_norms"])
+    assert len(hist) == len(ref)
+    # before the quadratic phase the residuals agree closely (later ones carry the linear
+    # solves' tolerance relative to much smaller values)
+    big = ref > 1e-3
+    assert big.sum() >= 2 and np.all(np.abs(hist[big] - ref[big]) <= 1e-6 * ref[big])
+    Sg = S.cpu().numpy()
+    assert rel(Sg, S_ref) < 1e-10
+    _, nrm = o.newton_residual(Sg)  # the GPU state is a steady state of the oracle's equations
+    assert nrm < 1e-9
+
+
+@pytest.mark.parametrize("bc", [synth.CC, synth.AA])
+def test_newton_mixed_precision_reaches_oracle_steady_state(bc):
+    n = (8, 8, 8)
+    kv = kvmod()
+    S0, o, S_ref, info = oracle_newton(n, bc)
+    assert info["converged"]
+    g = kv.Grid(*n, bc=bc, gr=1e4, pr=0.71, precision=kv.KV_PREC_MIXED)
+    S = dev(S0)
+    V = torch.empty((31,) + S.shape, dtype=torch.float64, device="cuda")
+    work = torch.empty((10,) + S.shape, dtype=torch.float64, device="cuda")
+    st = g.newton(S, V, work, max_newton=10, tol=1e-9, gmres_m=30, gmres_max_restarts=20, lin_tol=1e-10,
+                  gmres_sat=0.99, bicg_max_iter=300)
+    assert st.converged
+    assert rel(S.cpu().numpy(), S_ref) < 1e-8
+
+
+def test_solver_edge_cases_and_errors():
+    kv = kvmod()
+    n = (6, 5, 4)
+    g, o, S, x_true, b = case(n, synth.CC, 1e4)
+    L = 4 * g.field_len
+    x = torch.ones(L, dtype=torch.float64, device="cuda")
+    V = torch.empty((5, L), dtype=torch.float64, device="cuda")
+    work = torch.empty((8, L), dtype=torch.float64, device="cuda")
+    zero = torch.zeros(L, dtype=torch.float64, device="cuda")
+    st = g.gmres(zero, x, V, 4, 3, 1e-12)  # b = 0: x = 0
+    assert st.converged and torch.count_nonzero(x).item() == 0
+    x.fill_(1.0)
+    st = g.bicgstab2(zero, x, work, 5, 1e-12)
+    assert st.converged and torch.count_nonzero(x).item() == 0
+    with pytest.raises(kv.KvError):
+        g.gmres(dev(b), x, V, 0, 3, 1e-12)  # m = 0
+    with pytest.raises(kv.KvError):
+        g.gmres(dev(b), V[0], V, 4, 3, 1e-12)  # x inside the basis workspace
+    with pytest.raises(kv.KvError):
+        g.bicgstab2(dev(b), x, work, -1, 1e-12)
+    fresh = kv.Grid(*n, bc=synth.CC, gr=1e4, pr=0.71)  # no base flow yet
+    with pytest.raises(kv.KvError):
+        fresh.gmres(dev(b), x, V, 4, 3, 1e-12)
