@@ -233,3 +233,134 @@ def newton(oracle, S0, max_newton, tol, m, max_restarts, lin_tol, sat, bicg_max_
         S = S - d
         info["iterations"] += 1
     return S, info
+
+
+# ---- Chebyshev-preconditioned Arnoldi for the rightmost eigenvalues (Eq (10)) ----------------
+#
+# Section 3.1 computes the leading eigenvalues of the Jacobian by the Chebyshev-preconditioned
+# Arnoldi iteration (the paper uses ARPACK or HSL's EB13). Restated from Saad's Arnoldi-Chebyshev
+# method (Math. Comp. 42, 1984): m Arnoldi steps give Ritz values; the unwanted ones are
+# enclosed in an ellipse centred on the real axis; the next starting vector is the wanted Ritz
+# vectors' real and imaginary parts filtered by the Chebyshev polynomial T_k((A - d) / c) of that
+# ellipse, normalised at the rightmost wanted Ritz value, which damps the unwanted part of the
+# spectrum; repeat until the wanted Ritz pairs' residuals are small. The filtered vector is
+# multiplied by A once more: the Krylov map is singular on the full packed vector (its input
+# projection zeroes the wall entries, its output projection the gradient fields), and for a
+# stable spectrum that eigenvalue 0 lies right of the wanted eigenvalues, where the filter
+# amplifies; the product removes those rounding-level components.
+
+
+def ritz_pairs(H):
+    """Ritz values of the Arnoldi matrix H ((k+1) x k), sorted by decreasing real part, their
+    coefficient vectors and the residual norms |h_{k+1,k}| |y_k| / ||y|| (Arnoldi relation)."""
+    k = H.shape[1]
+    theta, Y = np.linalg.eig(H[:k, :k])
+    order = np.argsort(-theta.real, kind="stable")
+    theta, Y = theta[order], Y[:, order]
+    res = np.abs(H[k, k - 1]) * np.abs(Y[k - 1, :]) / np.linalg.norm(Y, axis=0)
+    return theta, Y, res
+
+
+def wanted_count(theta, nev):
+    """nev, plus one when the nev-th Ritz value is complex and its conjugate comes next (a
+    conjugate pair is kept together)."""
+    n = min(nev, len(theta))
+    if n < len(theta) and theta[n - 1].imag != 0.0 and abs(theta[n] - np.conj(theta[n - 1])) <= \
+            1e-12 * max(abs(theta[n - 1]), 1e-300):
+        n += 1
+    return n
+
+
+def enclosing_ellipse(points):
+    """The ellipse centred on the real axis with axes along the coordinate axes that encloses the
+    points: its centre d and the square of its focal distance c2 = a^2 - b^2 (a: real semi-axis,
+    b: imaginary semi-axis; c2 < 0 for an ellipse taller than wide). Semi-axes start at half the
+    real extent and the largest |imaginary part| and grow by a common factor until every point is
+    inside."""
+    re, im = points.real, np.abs(points.imag)
+    d = 0.5 * (re.max() + re.min())
+    span = max(re.max() - re.min(), im.max(), 1e-300)
+    a = max(0.5 * (re.max() - re.min()), 1e-8 * span)
+    b = max(im.max(), 1e-8 * span)
+    s = max(1.0, float(np.max(((re - d) / a) ** 2 + (im / b) ** 2)))
+    a, b = a * np.sqrt(s), b * np.sqrt(s)
+    return d, a * a - b * b
+
+
+def chebyshev_filter(matvec, v, k, d, c2, lam):
+    """T_k((A - d) / c) v / T_k((lam - d) / c) for real d, lam (lam > d) and real c2 = c^2, by the
+    three-term recurrence written with the real quantities tau_j = sigma_j / c, where
+    sigma_1 = c / (lam - d) and sigma_{j+1} = 1 / (2 (lam - d) / c - sigma_j):
+    y_1 = tau_1 (A - d) y_0, y_{j+1} = 2 tau_{j+1} (A - d) y_j - tau_j tau_{j+1} c2 y_{j-1}."""
+    e = lam - d
+    tau = 1.0 / e
+    y_prev = v
+    y = tau * (matvec(v) - d * v)
+    for _ in range(1, k):
+        tau_next = 1.0 / (2.0 * e - tau * c2)
+        y_next = 2.0 * tau_next * (matvec(y) - d * y) - tau * tau_next * c2 * y_prev
+        y_prev, y, tau = y, y_next, tau_next
+    return y
+
+
+def arnoldi_chebyshev(matvec, v0, m, nev, k, tol, max_cycles):
+    """Rightmost eigenvalues of A: cycles of m Arnoldi steps (classical Gram-Schmidt twice), each
+    restarted from the wanted Ritz vectors filtered by a degree-k Chebyshev polynomial.
+    Converged when every wanted Ritz pair has residual <= tol |theta|. nev = 1 asks for the
+    leading eigenvalue (with its conjugate when complex), the case Section 3.1 computes; for
+    nev > 1 on a non-normal A the later wanted values can be spurious (no locking of converged
+    Schur vectors here).
+
+    A cycle stops early once the new subdiagonal entry of H is at most tol times its column's
+    norm (after at least nev steps; at once when it is exactly 0): the Krylov space then holds an
+    invariant subspace to within tol, whose Ritz values are the answer. Otherwise the Ritz values
+    of the rest of the space, which for a non-normal A lie anywhere in its field of values, could
+    pass for rightmost eigenvalues.
+
+    Returns (theta, res, info): the wanted Ritz values and residuals of the last cycle; info:
+    cycles, matvecs, converged, ellipses (d, c2) used."""
+    info = dict(cycles=0, matvecs=0, converged=False, ellipses=[])
+    v = np.array(v0, dtype=np.float64, copy=True)
+    shape = v.shape
+    theta = res = None
+    for _ in range(max_cycles):
+        info["cycles"] += 1
+        V = np.zeros((m + 1,) + shape)
+        V[0] = v / _norm(v)
+        H = np.zeros((m + 1, m))
+        kk = m
+        for j in range(m):
+            H[: j + 2, j] = arnoldi_cgs2(matvec, V, j)
+            info["matvecs"] += 1
+            # the space holds an invariant subspace to within tol (after at least nev steps), or
+            # exactly: stop the cycle there
+            hn, col = H[j + 1, j], np.linalg.norm(H[: j + 2, j])
+            if hn == 0.0 or (hn <= tol * col and j + 1 >= nev):
+                kk = j + 1
+                break
+        th, Y, rs = ritz_pairs(H[: kk + 1, :kk])
+        nw = wanted_count(th, nev)
+        theta, res = th[:nw], rs[:nw]
+        if np.all(res <= tol * np.abs(theta)):
+            info["converged"] = True
+            break
+        # restart vector: the wanted Ritz vectors' real and imaginary parts, each normalised
+        coef = np.zeros(kk)
+        for i in range(nw):
+            y = Y[:, i] / np.linalg.norm(Y[:, i])
+            coef += y.real + y.imag
+        v = np.tensordot(coef, V[:kk], axes=1)
+        # Chebyshev filter over the ellipse of the unwanted Ritz values
+        if nw >= kk:
+            continue
+        d, c2 = enclosing_ellipse(th[nw:])
+        lam = theta[0].real
+        if lam > d:
+            info["ellipses"].append((d, c2))
+            v = chebyshev_filter(matvec, v, k, d, c2, lam)
+            # one product with A: the Krylov map's null space (entries outside its range, where
+            # the filter's polynomial is large when the spectrum is stable) holds rounding-level
+            # components of the filtered vector; A removes them
+            v = matvec(v)
+            info["matvecs"] += k + 1
+    return theta, res, info

@@ -1,6 +1,7 @@
 """The solver pins catch plausible mistakes: each test plants one mistake in a copy of
 oracle/solvers.py (a sign in a Givens rotation or in the minimal-residual update, an index in
-the back substitution or the BiCG residual update, the direction of the Newton update) and runs
+the back substitution or the BiCG residual update, the direction of the Newton update, the
+Chebyshev recurrence's coefficient or shift, the enclosing ellipse's centre) and runs
 tests/test_oracle_solvers.py against it in a fresh process; at least one pin must fail. CPU only."""
 import os
 import subprocess
@@ -18,6 +19,9 @@ MUTANTS = {
     "bicg_residual_index": ("rh[i] = rh[i] - alpha * uh[i + 1]", "rh[i] = rh[i] - alpha * uh[i]"),
     "mr_tau_sign": ("g1 = g1p - tau12 * g2", "g1 = g1p + tau12 * g2"),
     "newton_direction": ("S = S - d", "S = S + d"),
+    "chebyshev_tau_update": ("tau_next = 1.0 / (2.0 * e - tau * c2)", "tau_next = 1.0 / (2.0 * e + tau * c2)"),
+    "chebyshev_shift_sign": ("y_next = 2.0 * tau_next * (matvec(y) - d * y)", "y_next = 2.0 * tau_next * (matvec(y) + d * y)"),
+    "ellipse_centre": ("d = 0.5 * (re.max() + re.min())", "d = 0.5 * (re.max() - re.min())"),
 }
 
 

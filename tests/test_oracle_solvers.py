@@ -128,3 +128,100 @@ def test_newton_converges_quadratically_to_a_steady_state(bc):
     wall = np.zeros(S.shape, dtype=bool)
     wall[3, :, :, 0] = wall[3, :, :, -1] = True  # the isothermal walls x = 0, 1 of Theta
     assert np.array_equal(S[wall], S0[wall])
+
+
+# --- Chebyshev-preconditioned Arnoldi (Section 3.1, the eigenvalue problem Eq (10)) ------------
+chebyshev_filter = _solvers.chebyshev_filter
+enclosing_ellipse = _solvers.enclosing_ellipse
+arnoldi_chebyshev = _solvers.arnoldi_chebyshev
+
+
+@pytest.mark.parametrize("c2", [2.25, -0.81])
+def test_chebyshev_filter_equals_polynomial_ratio(c2):
+    """On A = diag(l_i) the filter multiplies component i by T_k((l_i - d)/c) / T_k((lam - d)/c);
+    the ratio is evaluated here with numpy's Chebyshev series in complex arithmetic (c imaginary
+    when c2 < 0), independently of the real three-term recurrence."""
+    rng = np.random.default_rng(6)
+    lam_i = np.concatenate([[1.5], -3.0 + 2.5 * rng.random(30)])
+    v = rng.standard_normal(31)
+    d, lam, k = -1.7, 1.5, 9
+    y = chebyshev_filter(lambda x: lam_i * x, v, k, d, c2, lam)
+    c = np.sqrt(complex(c2))
+    Tk = np.polynomial.chebyshev.Chebyshev.basis(k)
+    ratio = Tk((lam_i - d) / c) / Tk((lam - d) / c)
+    assert np.max(np.abs(ratio.imag)) < 1e-12 * np.max(np.abs(ratio))
+    assert np.allclose(y, ratio.real * v, rtol=1e-11, atol=1e-13)
+    assert abs(y[0] - v[0]) < 1e-12 * abs(v[0])  # normalised at lam
+
+
+def test_enclosing_ellipse_contains_points():
+    rng = np.random.default_rng(7)
+    pts = -2.0 + rng.standard_normal(40) + 1j * rng.standard_normal(40) * 3.0
+    pts = np.concatenate([pts, pts.conj()])
+    d, c2 = enclosing_ellipse(pts)
+    # the ellipse with foci d +- c (c imaginary when c2 < 0) contains z iff the distances to the
+    # foci sum to at most twice its major semi-axis; semi-axes recovered from the points' extent
+    re, im = pts.real, np.abs(pts.imag)
+    assert abs(d - 0.5 * (re.max() + re.min())) < 1e-12
+    a0, b0 = 0.5 * (re.max() - re.min()), im.max()
+    s = np.max(((re - d) / a0) ** 2 + (im / b0) ** 2)
+    assert abs(c2 - s * (a0 * a0 - b0 * b0)) < 1e-9 * s * (a0 * a0 + b0 * b0)
+    c = np.sqrt(complex(c2))
+    major = np.sqrt(s) * max(a0, b0)
+    assert np.all(np.abs(pts - d - c) + np.abs(pts - d + c) <= 2 * major * (1 + 1e-12))
+    assert np.max(np.abs(pts - d - c) + np.abs(pts - d + c)) > 2 * major * (1 - 1e-9)  # and touches
+
+
+def _dense_with_spectrum(blocks, rest, seed):
+    """A real matrix S D S^-1 with D = diag(2x2 rotation blocks for complex pairs, real rest)."""
+    rng = np.random.default_rng(seed)
+    n = 2 * len(blocks) + len(rest)
+    D = np.zeros((n, n))
+    for q, (re, im) in enumerate(blocks):
+        D[2 * q:2 * q + 2, 2 * q:2 * q + 2] = [[re, im], [-im, re]]
+    for i, lam in enumerate(rest):
+        D[2 * len(blocks) + i, 2 * len(blocks) + i] = lam
+    Q, _ = np.linalg.qr(rng.standard_normal((n, n)))
+    S = Q @ np.diag(1.0 + 0.2 * rng.random(n))
+    return S @ D @ np.linalg.inv(S), rng.standard_normal(n)
+
+
+def test_arnoldi_chebyshev_finds_rightmost_complex_pair():
+    rng = np.random.default_rng(8)
+    A, v0 = _dense_with_spectrum([(-0.1, 2.0), (-1.5, 3.0)], -1.0 - 4.0 * rng.random(196), 8)
+    theta, res, info = arnoldi_chebyshev(lambda x: A @ x, v0, 20, 2, 15, 1e-10, 30)
+    assert info["converged"] and len(theta) == 2 and info["ellipses"]
+    assert np.allclose(sorted(theta, key=lambda z: z.imag), [-0.1 - 2.0j, -0.1 + 2.0j], atol=1e-9)
+
+
+def test_arnoldi_chebyshev_rightmost_real_with_complex_cloud():
+    """Rightmost eigenvalue real, the unwanted ones a complex cloud taller than wide (c2 < 0)."""
+    rng = np.random.default_rng(9)
+    blocks = [(-2.0 - rng.random(), 1.0 + 5.0 * rng.random()) for _ in range(60)]
+    A, v0 = _dense_with_spectrum(blocks, [-0.3, -2.5, -2.8], 9)
+    theta, res, info = arnoldi_chebyshev(lambda x: A @ x, v0, 25, 1, 20, 1e-10, 40)
+    assert info["converged"] and abs(theta[0] - (-0.3)) < 1e-9
+    assert any(c2 < 0 for _, c2 in info["ellipses"])
+
+
+def test_arnoldi_chebyshev_matches_dense_spectrum_of_krylov_map():
+    """The rightmost eigenvalues of the Krylov map on its range (the space of Krylov vectors),
+    from a dense eigen-decomposition of the map restricted to an orthonormal basis of that range,
+    against the Chebyshev-preconditioned Arnoldi iteration (4^3, CC, Gr = 1e4)."""
+    n = (4, 4, 4)
+    o = Oracle(*n, gr=1e4)
+    S = np.stack(synth.base_flow(*n, synth.CC, 41))
+    N = 4 * int(np.prod([m + 2 for m in n]))
+    M = np.zeros((N, N))
+    for i in range(N):
+        e = np.zeros(N)
+        e[i] = 1.0
+        M[:, i] = o.krylov_vector(S, e.reshape((4,) + o.shape)).ravel()
+    U, sv, _ = np.linalg.svd(M)
+    Q = U[:, sv > 1e-10 * sv[0]]
+    ev = np.linalg.eigvals(Q.T @ M @ Q)
+    ev = ev[np.argsort(-ev.real, kind="stable")]
+    v0 = o.krylov_vector(S, synth.krylov_input(*n, 3)[0])
+    theta, res, info = arnoldi_chebyshev(lambda x: o.krylov_vector(S, x), v0, 30, 1, 12, 1e-10, 60)
+    assert info["converged"] and len(theta) == 1
+    assert abs(theta[0] - ev[0]) < 1e-8 * max(1.0, abs(ev[0]))
