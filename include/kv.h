@@ -235,6 +235,15 @@ kv_status kv_gmres(kv_handle h, const double* b, double* x, double* V, int m, in
 kv_status kv_bicgstab2(kv_handle h, const double* b, double* x, double* work, int max_iter, double tol,
                        kv_solve_stats* st);
 
+/* Vector operations of the Krylov solvers and the eigenvalue driver, on packed vectors
+   (device), stream-ordered: y = a x + b y (x may be y; b = 0 does not read y; a, b finite) and
+   y = sum_{i<k} c[i] V_i (V: k consecutive packed vectors, c: HOST array of k finite values;
+   y outside V; synchronises the stream). KV_ERR_ARG for NULL or overlapping vectors. */
+kv_status kv_axpby(kv_handle h, double a, const double* x, double b, double* y);
+kv_status kv_combine(kv_handle h, const double* V, int k, const double* c, double* y);
+/* *out (HOST) = <x, y> over the packed entries (FP64; synchronises the stream). */
+kv_status kv_dot(kv_handle h, const double* x, const double* y, double* out);
+
 #define KV_NEWTON_HISTORY 64
 typedef struct {
   int max_newton;         /* Newton corrections at most (0..KV_NEWTON_HISTORY - 1) */

@@ -317,12 +317,14 @@ def arnoldi_chebyshev(matvec, v0, m, nev, k, tol, max_cycles):
     of the rest of the space, which for a non-normal A lie anywhere in its field of values, could
     pass for rightmost eigenvalues.
 
-    Returns (theta, res, info): the wanted Ritz values and residuals of the last cycle; info:
-    cycles, matvecs, converged, ellipses (d, c2) used."""
+    Returns (theta, res, info): the wanted Ritz values and residuals of the cycle with the
+    smallest largest relative residual; info: cycles, matvecs, converged, ellipses (d, c2)
+    used."""
     info = dict(cycles=0, matvecs=0, converged=False, ellipses=[])
     v = np.array(v0, dtype=np.float64, copy=True)
     shape = v.shape
     theta = res = None
+    best = (np.inf, None, None)  # the wanted set with the smallest largest relative residual
     for _ in range(max_cycles):
         info["cycles"] += 1
         V = np.zeros((m + 1,) + shape)
@@ -341,7 +343,10 @@ def arnoldi_chebyshev(matvec, v0, m, nev, k, tol, max_cycles):
         th, Y, rs = ritz_pairs(H[: kk + 1, :kk])
         nw = wanted_count(th, nev)
         theta, res = th[:nw], rs[:nw]
-        if np.all(res <= tol * np.abs(theta)):
+        score = float(np.max(res / np.maximum(np.abs(theta), 1e-300)))
+        if score < best[0]:
+            best = (score, theta, res)
+        if score <= tol:
             info["converged"] = True
             break
         # restart vector: the wanted Ritz vectors' real and imaginary parts, each normalised
@@ -363,4 +368,9 @@ def arnoldi_chebyshev(matvec, v0, m, nev, k, tol, max_cycles):
             # components of the filtered vector; A removes them
             v = matvec(v)
             info["matvecs"] += k + 1
+    # once the wanted eigenvector has converged as far as rounding allows, the next Krylov
+    # directions are rounding noise and later cycles can rank a spurious Ritz value first:
+    # return the best wanted set seen
+    if best[1] is not None:
+        theta, res = best[1], best[2]
     return theta, res, info

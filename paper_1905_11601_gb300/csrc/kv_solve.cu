@@ -361,3 +361,37 @@ extern "C" kv_status kv_newton(kv_handle h, double* S, double* V, double* work, 
   if (st) *st = N;
   return KV_OK;
 }
+
+extern "C" kv_status kv_axpby(kv_handle h, double a, const double* x, double b, double* y) {
+  if (!h) return KV_ERR_ARG;
+  if (!x || !y || !isfinite(a) || !isfinite(b)) return sfail(h, KV_ERR_ARG, "kv_axpby: bad argument");
+  const size_t L = 4 * h->P;
+  if (x != y && overlaps(x, L, y, L)) return sfail(h, KV_ERR_ARG, "kv_axpby: x and y overlap");
+  return axpby(h, a, x, b, y);
+}
+
+extern "C" kv_status kv_combine(kv_handle h, const double* V, int k, const double* c, double* y) {
+  if (!h) return KV_ERR_ARG;
+  if (!V || !c || !y || k < 1 || k > 4096) return sfail(h, KV_ERR_ARG, "kv_combine: bad argument");
+  const size_t L = 4 * h->P;
+  if (overlaps(y, L, V, (size_t)k * L)) return sfail(h, KV_ERR_ARG, "kv_combine: y overlaps V");
+  for (int i = 0; i < k; ++i)
+    if (!isfinite(c[i])) return sfail(h, KV_ERR_ARG, "kv_combine: non-finite coefficient");
+  KV_SOLVE_TRY(scratch(h, (size_t)k + 8));
+  // y = 0, then y -= V (-c) (kv_launch_update forms w -= V c)
+  std::vector<double> nc(k);
+  for (int i = 0; i < k; ++i) nc[i] = -c[i];
+  KV_SOLVE_CUDA(h, cudaMemsetAsync(y, 0, L * sizeof(double), h->s));
+  KV_SOLVE_CUDA(h, cudaMemcpyAsync(small_buf(h), nc.data(), k * sizeof(double), cudaMemcpyHostToDevice, h->s));
+  kv_launch_update(V, L, k, small_buf(h), y, L, h->s);
+  KV_SOLVE_TRY(launched(h, "combine"));
+  KV_SOLVE_CUDA(h, cudaStreamSynchronize(h->s));
+  return KV_OK;
+}
+
+extern "C" kv_status kv_dot(kv_handle h, const double* x, const double* y, double* out) {
+  if (!h) return KV_ERR_ARG;
+  if (!x || !y || !out) return sfail(h, KV_ERR_ARG, "kv_dot: bad argument");
+  KV_SOLVE_TRY(scratch(h, 8));
+  return dots(h, x, 0, 1, y, out);
+}

@@ -27,7 +27,7 @@ EXPORTS = ("kv_create_grid", "kv_destroy_grid", "kv_set_stream", "kv_field_len",
            "kv_profile_enable", "kv_profile_get", "kv_krylov_vector_noalloc", "kv_krylov_vector_adjoint",
            "kv_base_flow_gradient", "kv_krylov_vector_batch", "kv_plan_create", "kv_plan_add", "kv_plan_launch",
            "kv_plan_destroy", "kv_plan_last_error", "kv_selftest_wait_timeout", "kv_tuning",
-           "kv_krylov_vector_host_stream", "kv_gmres", "kv_bicgstab2", "kv_newton")
+           "kv_krylov_vector_host_stream", "kv_gmres", "kv_bicgstab2", "kv_newton", "kv_axpby", "kv_combine", "kv_dot")
 PHASES = {"stencil": 0, "divergence": 1, "tpd": 2, "correct": 3, "arnoldi": 4, "refine": 5, "gs_dots": 6,
           "gs_update": 7}
 
@@ -104,6 +104,9 @@ def load_library(path: str = LIB_PATH):
                              ctypes.POINTER(SolveStats)]
     lib.kv_bicgstab2.argtypes = [H, D, D, D, ctypes.c_int, ctypes.c_double, ctypes.POINTER(SolveStats)]
     lib.kv_newton.argtypes = [H, D, D, D, ctypes.POINTER(NewtonParams), ctypes.POINTER(NewtonStats)]
+    lib.kv_axpby.argtypes = [H, ctypes.c_double, D, ctypes.c_double, D]
+    lib.kv_combine.argtypes = [H, D, ctypes.c_int, ctypes.POINTER(ctypes.c_double), D]
+    lib.kv_dot.argtypes = [H, D, D, ctypes.POINTER(ctypes.c_double)]
     lib.kv_krylov_vector_adjoint.argtypes = [H, D, D]
     lib.kv_base_flow_gradient.argtypes = [H, D, D, D, ctypes.POINTER(ctypes.c_double)]
     lib.kv_krylov_vector_batch.argtypes = [H, D, D, ctypes.c_int]
@@ -267,6 +270,31 @@ class Grid:
                                        _dev_ptr(work, self.torch, "work", 10 * L), ctypes.byref(prm),
                                        ctypes.byref(st)))
         return st
+
+    def axpby(self, a, x, b, y):
+        """y = a x + b y on packed vectors (kv_axpby)."""
+        self._sync_stream()
+        L = 4 * self.field_len
+        self._check(self.lib.kv_axpby(self.h, float(a), _dev_ptr(x, self.torch, "x", L), float(b),
+                                      _dev_ptr(y, self.torch, "y", L)))
+
+    def dot(self, x, y):
+        """<x, y> over the packed entries (kv_dot)."""
+        self._sync_stream()
+        L = 4 * self.field_len
+        out = ctypes.c_double()
+        self._check(self.lib.kv_dot(self.h, _dev_ptr(x, self.torch, "x", L), _dev_ptr(y, self.torch, "y", L),
+                                    ctypes.byref(out)))
+        return out.value
+
+    def combine(self, V, c, y):
+        """y = sum_i c[i] V[i] over the first len(c) packed vectors of V (kv_combine)."""
+        self._sync_stream()
+        L = 4 * self.field_len
+        c = np.ascontiguousarray(c, dtype=np.float64)
+        self._check(self.lib.kv_combine(self.h, _dev_ptr(V, self.torch, "V", len(c) * L), len(c),
+                                        c.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                        _dev_ptr(y, self.torch, "y", L)))
 
     def arnoldi_step(self, V, j):
         self._sync_stream()

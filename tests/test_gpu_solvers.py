@@ -179,3 +179,51 @@ def test_solver_edge_cases_and_errors():
     fresh = kv.Grid(*n, bc=synth.CC, gr=1e4, pr=0.71)  # no base flow yet
     with pytest.raises(kv.KvError):
         fresh.gmres(dev(b), x, V, 4, 3, 1e-12)
+
+
+# --- the leading eigenvalue by the Chebyshev-preconditioned Arnoldi iteration (Section 3.1) ----
+def dense_leading_eigenvalue(n, bc, gr):
+    """Rightmost eigenvalue of the oracle's Krylov map on its range (dense, small grids)."""
+    o = Oracle(*n, bc=bc, gr=gr, pr=0.71)
+    S = np.stack(synth.base_flow(*n, bc, 41))
+    N = 4 * int(np.prod([m + 2 for m in n]))
+    M = np.zeros((N, N))
+    for i in range(N):
+        e = np.zeros(N)
+        e[i] = 1.0
+        M[:, i] = o.krylov_vector(S, e.reshape((4,) + o.shape)).ravel()
+    U, sv, _ = np.linalg.svd(M)
+    Q = U[:, sv > 1e-10 * sv[0]]
+    ev = np.linalg.eigvals(Q.T @ M @ Q)
+    return ev[np.argmax(ev.real)]
+
+
+# mixed precision: the wanted pair's residual levels off near 1e-7 at 4^3 (double-float
+# orthogonalisation and projection noise), so that is its tolerance
+@pytest.mark.parametrize("precision,tol,bar", [(0, 1e-10, 1e-8), (1, 1e-7, 1e-6)])
+def test_arnoldi_chebyshev_leading_eigenvalue_matches_dense_spectrum(precision, tol, bar):
+    from paper_1905_11601_gb300.arnoldi import arnoldi_chebyshev
+    n = (4, 4, 4)
+    lead = dense_leading_eigenvalue(n, synth.CC, 1e4)
+    g, o, S, x_true, b = case(n, synth.CC, 1e4, precision)
+    theta, res, info = arnoldi_chebyshev(g, dev(x_true), m=30, nev=1, k=12, tol=tol, max_cycles=80)
+    assert info["converged"] and info["ellipses"]
+    assert abs(theta[0] - lead) < bar * max(1.0, abs(lead))
+
+
+def test_arnoldi_chebyshev_matches_oracle_iteration():
+    from oracle.solvers import arnoldi_chebyshev as oracle_ac
+    from paper_1905_11601_gb300.arnoldi import arnoldi_chebyshev
+    n = (6, 6, 6)
+    g, o, S, x_true, b = case(n, synth.AA, 1e4)
+    th_ref, res_ref, info_ref = oracle_ac(lambda v: o.krylov_vector(S, v), x_true, 24, 1, 10, 1e-10, 80)
+    theta, res, info = arnoldi_chebyshev(g, dev(x_true), m=24, nev=1, k=10, tol=1e-10, max_cycles=80)
+    assert info["converged"] and info_ref["converged"]
+    assert len(theta) == len(th_ref)
+    assert np.allclose(np.sort_complex(theta), np.sort_complex(th_ref), rtol=1e-8, atol=1e-10)
+    # the GPU's Ritz vector is an eigenvector of the oracle's map
+    from paper_1905_11601_gb300.arnoldi import ritz_vector
+    xr, xi = ritz_vector(info["V"], info["Y"][:, 0])
+    X = xr.cpu().numpy() + 1j * xi.cpu().numpy()
+    AX = o.krylov_vector(S, X.real) + 1j * o.krylov_vector(S, X.imag)
+    assert np.linalg.norm(AX - theta[0] * X) < 1e-8 * abs(theta[0]) * np.linalg.norm(X)
