@@ -63,3 +63,10 @@ def test_null_arguments_rejected(lib):
     assert lib.kv_set_base_flow(None, None) == -1
     assert lib.kv_krylov_vector_host(None, None, None, None) == -1
     assert lib.kv_krylov_vector_host_stream(None, None, None, 1) == -1
+    assert lib.kv_gmres(None, None, None, None, 10, 1, 1e-10, 0.99, None) == -1
+    assert lib.kv_bicgstab2(None, None, None, None, 10, 1e-10, None) == -1
+    assert lib.kv_newton(None, None, None, None, None, None) == -1
+    assert lib.kv_axpby(None, 1.0, None, 1.0, None) == -1
+    assert lib.kv_combine(None, None, 1, None, None) == -1
+    out = ctypes.c_double()
+    assert lib.kv_dot(None, None, None, ctypes.byref(out)) == -1
