@@ -53,9 +53,9 @@ def parse_args():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the 16-vector block and the 12-grid plan measurements")
-    ap.add_argument("--single", choices=["fp64", "mixed", "mixed-arnoldi"], default=None,
-                    help="profiling case: two untimed Krylov-vector evaluations (or 8 Arnoldi steps), "
-                         "no JSON line")
+    ap.add_argument("--single", choices=["fp64", "mixed", "mixed-arnoldi", "mixed-newton"], default=None,
+                    help="profiling case: two untimed Krylov-vector evaluations (or 8 Arnoldi steps, or two "
+                         "Newton corrections at 64^3 with one GMRES(30) cycle each), no JSON line")
     return ap.parse_args()
 
 
@@ -581,6 +581,17 @@ def run_single(args):
     from paper_1905_11601_gb300 import kv, synth
 
     kvbuild.build()
+    if args.single == "mixed-newton":
+        n = 64
+        g = kv.Grid(n, n, n, bc=synth.CC, gr=1e4, pr=0.71, precision=kv.KV_PREC_MIXED)
+        S = torch.from_numpy(np.stack(synth.base_flow(n, n, n, synth.CC, 11900))).cuda()
+        V = torch.empty((31, 4) + g.shape, dtype=torch.float64, device="cuda")
+        work = torch.empty((10, 4) + g.shape, dtype=torch.float64, device="cuda")
+        st = g.newton(S, V, work, max_newton=2, tol=0.0, gmres_m=30, gmres_max_restarts=1, lin_tol=1e-10,
+                      gmres_sat=0.99, bicg_max_iter=2)
+        torch.cuda.synchronize()
+        print(f"single mixed-newton 64^3: {st.iterations} corrections, {st.matvecs} Krylov vectors")
+        return
     w = synth.WORKLOADS[args.workload]
     base_np, x_np = synth.workload_arrays(w)
     g = kv.Grid(w.nx, w.ny, w.nz, bc=w.bc, gr=w.gr, pr=w.pr,

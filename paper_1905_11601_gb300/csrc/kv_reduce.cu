@@ -34,10 +34,15 @@ __global__ void __launch_bounds__(RT) k_multidot(const double* __restrict__ V, s
   }
   __shared__ double sm[QB][RT / 32];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  // only the nqb accumulators in use: each warp-wide FP64 add occupies GB300's FP64 pipe (1/64 of
+  // the FP32 rate) for about 16 cycles, so reducing all QB of them cost more than the sweep itself
+  // on vectors of a few MB
 #pragma unroll
   for (int q = 0; q < QB; ++q) {
-    const double s = warp_sum(acc[q]);
-    if (lane == 0) sm[q][warp] = s;
+    if (q < nqb) {
+      const double s = warp_sum(acc[q]);
+      if (lane == 0) sm[q][warp] = s;
+    }
   }
   __syncthreads();
   if (threadIdx.x < QB && (int)threadIdx.x < nqb) {
