@@ -566,6 +566,18 @@ def run_ours(args):
         except Exception as e:  # the baseline is reported, never required
             out["cpu_baseline"] = {"value": None, "unit": UNIT, "cores": None, "kind": "oracle",
                                    "sample": f"failed: {e}"[:300]}
+        if "newton64" in out:  # the oracle beside the Newton line: one bounded GMRES cycle
+            try:
+                cmd = [sys.executable, "-m", "oracle.bench_cpu", "--newton-cycle", "20"]
+                r = subprocess.run(cmd, cwd=ROOT, capture_output=True, text=True, timeout=600)
+                if r.returncode != 0:
+                    raise RuntimeError(r.stderr[-500:])
+                rc = json.loads(r.stdout.strip().splitlines()[-1])
+                out["newton64"]["cpu_baseline"] = {"value": rc["value"], "unit": rc["unit"], "cores": rc["cores"],
+                                                   "kind": "oracle",
+                                                   "sample": f"{rc['sample']} ({rc['seconds']:.1f} s)"}
+            except Exception as e:
+                out["newton64"]["cpu_baseline"] = {"value": None, "kind": "oracle", "sample": f"failed: {e}"[:300]}
     print(json.dumps(out), flush=True)
     if dist:
         dist.destroy_process_group()

@@ -227,3 +227,21 @@ def test_arnoldi_chebyshev_matches_oracle_iteration():
     X = xr.cpu().numpy() + 1j * xi.cpu().numpy()
     AX = o.krylov_vector(S, X.real) + 1j * o.krylov_vector(S, X.imag)
     assert np.linalg.norm(AX - theta[0] * X) < 1e-8 * abs(theta[0]) * np.linalg.norm(X)
+
+
+@pytest.mark.parametrize("precision,tol,bar", [(0, 1e-11, 1e-9), (1, 1e-7, 1e-6)])
+def test_arnoldi_chebyshev_conduction_closed_form(precision, tol, bar):
+    """The leading eigenvalue at zero base flow and Pr = 10 against its closed form (a Kronecker
+    sum of 1D eigenvalues; tests/test_oracle_solvers.py), independent of both Krylov maps."""
+    from paper_1905_11601_gb300.arnoldi import arnoldi_chebyshev
+    from test_oracle_solvers import conduction_leading_eigenvalue
+    kv = kvmod()
+    n, gr, pr = (5, 6, 4), 1e6, 10.0
+    g = kv.Grid(*n, bc=synth.CC, gr=gr, pr=pr, precision=precision)
+    base = np.zeros((4,) + g.shape)
+    g.set_base_flow(dev(base))
+    v0 = g.krylov_vector(dev(synth.krylov_input(*n, 5)[0]))
+    theta, res, info = arnoldi_chebyshev(g, v0, m=30, nev=1, k=12, tol=tol, max_cycles=60)
+    lead = conduction_leading_eigenvalue(n, gr, pr)
+    assert info["converged"] and len(theta) == 1
+    assert abs(theta[0] - lead) < bar * abs(lead)

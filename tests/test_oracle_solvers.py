@@ -225,3 +225,39 @@ def test_arnoldi_chebyshev_matches_dense_spectrum_of_krylov_map():
     theta, res, info = arnoldi_chebyshev(lambda x: o.krylov_vector(S, x), v0, 30, 1, 12, 1e-10, 60)
     assert info["converged"] and len(theta) == 1
     assert abs(theta[0] - ev[0]) < 1e-8 * max(1.0, abs(ev[0]))
+
+
+def conduction_leading_eigenvalue(n, gr, pr):
+    """U = 0, Theta = 0: the map is block-triangular (T drives v through buoyancy, v does not drive
+    T), so its eigenvalues are those of kappa times the temperature Laplacian with the homogeneous
+    BCs (Kronecker sums of 1D eigenvalues, Eq (17)) and those of the Stokes block. With Pr = 10 the
+    slowest temperature mode decays far more slowly than the slowest Stokes mode, so the leading
+    eigenvalue is kappa times the sum of the largest 1D Dirichlet eigenvalues (wall nodes on the
+    walls: the first and last cells see a half spacing)."""
+    kappa = 1 / (pr * gr ** 0.5)
+
+    def largest_dirichlet_1d(m):
+        h = 1.0 / m
+        M = np.zeros((m, m))
+        for t in range(m):
+            wl = 2.0 if t == 0 else 1.0
+            wr = 2.0 if t == m - 1 else 1.0
+            M[t, t] = -(wl + wr) / h ** 2
+            if t > 0:
+                M[t, t - 1] = 1 / h ** 2
+            if t < m - 1:
+                M[t, t + 1] = 1 / h ** 2
+        return np.linalg.eigvalsh(M).max()
+
+    return kappa * sum(largest_dirichlet_1d(m) for m in n)
+
+
+def test_arnoldi_chebyshev_conduction_closed_form():
+    n, gr, pr = (5, 6, 4), 1e6, 10.0
+    o = Oracle(*n, gr=gr, pr=pr)
+    base = np.zeros((4,) + o.shape)
+    v0 = o.krylov_vector(base, synth.krylov_input(*n, 5)[0])
+    theta, res, info = arnoldi_chebyshev(lambda x: o.krylov_vector(base, x), v0, 30, 1, 12, 1e-11, 60)
+    lead = conduction_leading_eigenvalue(n, gr, pr)
+    assert info["converged"] and len(theta) == 1
+    assert abs(theta[0] - lead) < 1e-9 * abs(lead)
