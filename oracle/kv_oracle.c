@@ -20,17 +20,26 @@
  *
  * Discretisation (the paper reuses the finite-volume schemes of its reference [11], which is
  * not given; the readings below are stated once here and used throughout):
- *   - uniform MAC grid of the unit cube, h_a = 1/n_a; every field stored padded as
- *     (nz+2)(ny+2)(nx+2), x fastest; p and T at cell centres, u/v/w on x/y/z faces;
- *   - along an axis a cell-like index t = 1..n sits at (t-1/2)h, indices 0 and n+1 are wall
- *     nodes on the walls; a face-like index t = 0..n sits at t h (index n+1 is padding);
- *   - diffusion in flux form: ((f+ - f)/(x+ - x) - (f - f-)/(x - x-)) / h;
+ *   - MAC grid of the unit cube; every field stored padded as (nz+2)(ny+2)(nx+2), x fastest;
+ *     p and T at cell centres, u/v/w on x/y/z faces;
+ *   - faces of axis a at x_t = xi_t - s sin(2 pi xi_t), xi_t = t/n_a, t = 0..n_a (Eq 22, the
+ *     stretching parameter s = or_grid.stretch; s = 0 is the uniform grid, h_a = 1/n_a); cell
+ *     centres at the midpoints of their two faces; cell widths dx_t = x_t - x_{t-1};
+ *   - along an axis a cell-like index t = 1..n sits at its cell centre, indices 0 and n+1 are
+ *     wall nodes on the walls; a face-like index t = 0..n sits on face t (index n+1 is padding);
+ *   - diffusion in flux form: ((f+ - f)/(x+ - x) - (f - f-)/(x - x-)) / w, w the width of the
+ *     node's control volume: the cell width at a cell-like node, the distance between the two
+ *     adjacent cell centres at a face-like node (both h on the uniform grid);
  *   - advection (a.grad) b in the advective form of Eqs (8)-(9): a 3-point (non-uniform next
  *     to walls) central first derivative of b at b's node, times the advecting velocity
  *     averaged (2 or 4 nearest stored values) to that node;
  *   - buoyancy T e_z on a w-face: mean of the two adjacent cell temperatures;
- *   - divergence / gradient: the MAC differences; the Poisson operator is D G with the wall
- *     faces excluded (homogeneous Neumann), its zero mode removed (pseudo-inverse);
+ *   - divergence / gradient: the MAC differences (divided by the cell width / the distance
+ *     between the two cell centres); the Poisson operator is D G with the wall faces excluded
+ *     (homogeneous Neumann), its zero mode removed (pseudo-inverse); on a stretched axis the
+ *     1D factor of D G is not symmetric, and its eigenpairs (Eq 15) come from the symmetric
+ *     matrix dx^1/2 (D G) dx^-1/2 and E^-1 from a plain inversion of E;
+ *   - the SIMPLE test's h_min is the smallest cell width;
  *   - temperature projection reading "orthogonal" (tproj = 0): Eq (21) read as
  *     T^ = (P_x (x) P_y (x) P_z) T*, P_a = E_a G_a^-1 E_a^T with E_a the 1D eigenvectors of the
  *     homogeneous-BC temperature operator extended to the wall nodes, G_a = E_a^T E_a;
@@ -49,6 +58,7 @@ typedef struct {
   int bc;    /* 0: conducting spanwise walls (Eq 6); 1: insulated spanwise walls (Eq 7) */
   int tproj; /* 0: orthogonal (Gram) reading of Eq (21); 1: oblique reading */
   double gr, pr;
+  double stretch; /* Eq (22) stretching parameter s, 0 <= s < 1/(2 pi); 0: uniform grid */
 } or_grid;
 
 typedef struct {
@@ -63,6 +73,9 @@ typedef struct {
   or_grid g;
   int n[3];
   double h[3];
+  int stretched;  /* stretch != 0: the coordinates below replace t h */
+  double *xf[3];  /* face coordinates, n+1 per axis (Eq 22) */
+  double *xc[3];  /* cell-like coordinates, n+2 per axis: walls at 0 and 1, centres between */
   /* Neumann pressure Laplacian (Eq 14 for phi): eigenvectors E (n x n, row = node, col = mode),
      E^-1, eigenvalues. */
   double *Ep[3], *Epinv[3], *lamp[3];
@@ -92,10 +105,29 @@ static int face_like(int F, int a) { return F == a; }
 /* Coordinate of index t along axis a for field F. */
 static double coord(const or_ctx* c, int F, int a, int t) {
   int n = c->n[a];
+  if (c->stretched) {
+    if (face_like(F, a)) return c->xf[a][t < n ? t : n];
+    return c->xc[a][t <= 0 ? 0 : (t >= n + 1 ? n + 1 : t)];
+  }
   if (face_like(F, a)) return (double)t / n;
   if (t <= 0) return 0.0;
   if (t >= n + 1) return 1.0;
   return ((double)t - 0.5) / n;
+}
+
+/* Width of cell t (1..n) along axis a. */
+static double cell_width(const or_ctx* c, int a, int t) {
+  return c->stretched ? c->xf[a][t] - c->xf[a][t - 1] : c->h[a];
+}
+
+/* Distance between the centres of cells t and t+1 along axis a (face t, 1..n-1). */
+static double centre_gap(const or_ctx* c, int a, int t) {
+  return c->stretched ? c->xc[a][t + 1] - c->xc[a][t] : c->h[a];
+}
+
+/* Width of the control volume of entry t of field F along axis a. */
+static double cv_width(const or_ctx* c, int F, int a, int t) {
+  return face_like(F, a) ? centre_gap(c, a, t) : cell_width(c, a, t);
 }
 
 /* Is (i,j,k) an unknown (interior) entry of field F? */
@@ -122,7 +154,7 @@ static double d2(const or_ctx* c, const double* f, int F, int a, int i, int j, i
   int t[3] = {i, j, k};
   double xm = coord(c, F, a, t[a] - 1), x0 = coord(c, F, a, t[a]), xp = coord(c, F, a, t[a] + 1);
   double fm = nb(c, f, i, j, k, a, -1), f0 = at(c, f, i, j, k), fp = nb(c, f, i, j, k, a, +1);
-  return ((fp - f0) / (xp - x0) - (f0 - fm) / (x0 - xm)) / c->h[a];
+  return ((fp - f0) / (xp - x0) - (f0 - fm) / (x0 - xm)) / cv_width(c, F, a, t[a]);
 }
 
 /* First derivative along axis a, 3-point central (non-uniform next to walls). */
@@ -252,32 +284,89 @@ static void jacobi_eig(int m, const double* S, double* V, double* lam) {
    linearisation)? x walls: Eq (4); z walls: Eq (5); y walls: Eq (6) (CC) or Eq (7) (AA). */
 static int t_dirichlet(const or_ctx* c, int a) { return !(a == 1 && c->g.bc == 1); }
 
+/* Eq (15) for the Neumann Laplacian D G of phi on a stretched axis a: the 1D matrix
+   A = dx^-1 K (K symmetric: the flux differences with the wall faces excluded, weights 1 / the
+   centre gaps) is similar to the symmetric S = dx^1/2 A dx^-1/2, so A = E Lambda E^-1 with
+   E = dx^-1/2 Q, S = Q Lambda Q^T. Modes sorted by decreasing eigenvalue; mode 0 is the
+   constant vector, whose eigenvalue is exactly 0 (every row of K sums to zero). */
+static void stretched_neumann_axis(or_ctx* c, int a) {
+  int n = c->n[a];
+  double* S = (double*)calloc((size_t)n * n, sizeof(double));
+  double* Q = (double*)malloc(sizeof(double) * n * n);
+  double* lam = (double*)malloc(sizeof(double) * n);
+  for (int t = 1; t <= n; ++t) {
+    double dx = cell_width(c, a, t);
+    if (t < n) {
+      double g = centre_gap(c, a, t);
+      S[(size_t)(t - 1) * n + (t - 1)] -= 1.0 / (g * dx);
+      S[(size_t)(t - 1) * n + t] = 1.0 / (g * sqrt(dx * cell_width(c, a, t + 1)));
+    }
+    if (t > 1) {
+      double g = centre_gap(c, a, t - 1);
+      S[(size_t)(t - 1) * n + (t - 1)] -= 1.0 / (g * dx);
+      S[(size_t)(t - 1) * n + (t - 2)] = 1.0 / (g * sqrt(dx * cell_width(c, a, t - 1)));
+    }
+  }
+  jacobi_eig(n, S, Q, lam);
+  int* order = (int*)malloc(sizeof(int) * n);
+  for (int m = 0; m < n; ++m) order[m] = m;
+  for (int m = 0; m < n; ++m) /* selection sort, largest first */
+    for (int q = m + 1; q < n; ++q)
+      if (lam[order[q]] > lam[order[m]]) { int tmp = order[m]; order[m] = order[q]; order[q] = tmp; }
+  for (int m = 0; m < n; ++m) {
+    c->lamp[a][m] = m == 0 ? 0.0 : lam[order[m]];
+    for (int t = 0; t < n; ++t)
+      c->Ep[a][(size_t)t * n + m] = Q[(size_t)t * n + order[m]] / sqrt(cell_width(c, a, t + 1));
+  }
+  gj_inverse(n, c->Ep[a], c->Epinv[a]);
+  free(S); free(Q); free(lam); free(order);
+}
+
 or_ctx* or_create(const or_grid* g) {
   if (!g || g->nx < 2 || g->ny < 2 || g->nz < 2) return NULL;
+  if (!(g->stretch >= 0.0 && g->stretch < 0.5 / M_PI)) return NULL; /* Eq (22) must stay monotone */
   or_ctx* c = (or_ctx*)calloc(1, sizeof(or_ctx));
   c->g = *g;
   c->n[0] = g->nx;
   c->n[1] = g->ny;
   c->n[2] = g->nz;
+  c->stretched = g->stretch != 0.0;
   for (int a = 0; a < 3; ++a) {
     int n = c->n[a];
     double h = 1.0 / n;
     c->h[a] = h;
-    /* Eq (15) for the Neumann Laplacian of phi: closed-form eigenpairs of the 1D matrix
-       (phi_{t+1} - 2 phi_t + phi_{t-1}) / h^2 with the wall terms dropped (cosine basis). */
+    c->xf[a] = (double*)malloc(sizeof(double) * (n + 1));
+    c->xc[a] = (double*)malloc(sizeof(double) * (n + 2));
+    for (int t = 0; t <= n; ++t) {
+      double xi = (double)t / n;
+      c->xf[a][t] = xi - g->stretch * sin(2.0 * M_PI * xi); /* Eq (22) */
+    }
+    c->xf[a][0] = 0.0;
+    c->xf[a][n] = 1.0;
+    c->xc[a][0] = 0.0;
+    c->xc[a][n + 1] = 1.0;
+    for (int t = 1; t <= n; ++t) c->xc[a][t] = 0.5 * (c->xf[a][t - 1] + c->xf[a][t]);
     c->Ep[a] = (double*)malloc(sizeof(double) * n * n);
     c->Epinv[a] = (double*)malloc(sizeof(double) * n * n);
     c->lamp[a] = (double*)malloc(sizeof(double) * n);
-    for (int m = 0; m < n; ++m) {
-      double alpha = sqrt((m == 0 ? 1.0 : 2.0) / n);
-      double s = sin(M_PI * m / (2.0 * n));
-      c->lamp[a][m] = -4.0 / (h * h) * s * s;
-      for (int t = 0; t < n; ++t) c->Ep[a][(size_t)t * n + m] = alpha * cos(M_PI * m * (t + 0.5) / n);
+    if (c->stretched) {
+      stretched_neumann_axis(c, a);
+    } else {
+      /* Eq (15) for the Neumann Laplacian of phi: closed-form eigenpairs of the 1D matrix
+         (phi_{t+1} - 2 phi_t + phi_{t-1}) / h^2 with the wall terms dropped (cosine basis). */
+      for (int m = 0; m < n; ++m) {
+        double alpha = sqrt((m == 0 ? 1.0 : 2.0) / n);
+        double s = sin(M_PI * m / (2.0 * n));
+        c->lamp[a][m] = -4.0 / (h * h) * s * s;
+        for (int t = 0; t < n; ++t) c->Ep[a][(size_t)t * n + m] = alpha * cos(M_PI * m * (t + 0.5) / n);
+      }
+      gj_inverse(n, c->Ep[a], c->Epinv[a]);
     }
-    gj_inverse(n, c->Ep[a], c->Epinv[a]);
 
     /* Eqs (15), (19)-(21) for the temperature: D_aa with the homogeneous BCs folded in,
-       its eigenvectors E_a, extended to the two wall nodes by the same BCs. */
+       its eigenvectors E_a, extended to the two wall nodes by the same BCs. P_a depends only
+       on the span of the extended E_a (every interior vector, wall nodes set by the BCs), so
+       the uniform-grid D_aa serves a stretched axis as well. */
     double* D = (double*)calloc((size_t)n * n, sizeof(double));
     int dir = t_dirichlet(c, a);
     for (int t = 0; t < n; ++t) {
@@ -334,12 +423,14 @@ void or_destroy(or_ctx* c) {
   if (!c) return;
   for (int a = 0; a < 3; ++a) {
     free(c->Ep[a]); free(c->Epinv[a]); free(c->lamp[a]); free(c->Pt[a]);
+    free(c->xf[a]); free(c->xc[a]);
   }
   free(c);
 }
 
 /* Exposes the 1D matrices for the tests: which = 0 -> E (pressure), 1 -> E^-1, 2 -> lambda,
-   3 -> P_a (temperature projection, (n+2)^2). */
+   3 -> P_a (temperature projection, (n+2)^2), 4 -> face coordinates (n+1), 5 -> cell-like
+   coordinates (n+2, walls included). */
 int or_axis_data(const or_ctx* c, int a, int which, double* out) {
   int n = c->n[a];
   switch (which) {
@@ -347,6 +438,8 @@ int or_axis_data(const or_ctx* c, int a, int which, double* out) {
     case 1: memcpy(out, c->Epinv[a], sizeof(double) * n * n); return 0;
     case 2: memcpy(out, c->lamp[a], sizeof(double) * n); return 0;
     case 3: memcpy(out, c->Pt[a], sizeof(double) * (n + 2) * (n + 2)); return 0;
+    case 4: memcpy(out, c->xf[a], sizeof(double) * (n + 1)); return 0;
+    case 5: memcpy(out, c->xc[a], sizeof(double) * (n + 2)); return 0;
   }
   return -1;
 }
@@ -515,9 +608,9 @@ void or_divergence(const or_ctx* c, const double* vel, double* b) {
   for (int k = 1; k <= c->n[2]; ++k)
     for (int j = 1; j <= c->n[1]; ++j)
       for (int i = 1; i <= c->n[0]; ++i)
-        b[cidx(c, i - 1, j - 1, k - 1)] = (at(c, u, i, j, k) - at(c, u, i - 1, j, k)) / c->h[0] +
-                                          (at(c, v, i, j, k) - at(c, v, i, j - 1, k)) / c->h[1] +
-                                          (at(c, w, i, j, k) - at(c, w, i, j, k - 1)) / c->h[2];
+        b[cidx(c, i - 1, j - 1, k - 1)] = (at(c, u, i, j, k) - at(c, u, i - 1, j, k)) / cell_width(c, 0, i) +
+                                          (at(c, v, i, j, k) - at(c, v, i, j - 1, k)) / cell_width(c, 1, j) +
+                                          (at(c, w, i, j, k) - at(c, w, i, j, k - 1)) / cell_width(c, 2, k);
 }
 
 /* out[..] = sum_q M[t][q] in[.. q ..] along axis a of a compact n^3 array (M is n x n,
@@ -575,7 +668,8 @@ void or_correct(const or_ctx* c, const double* phi, double* vel, double* p) {
           if (!is_dof(c, F, i, j, k)) continue;
           int t[3] = {i - 1, j - 1, k - 1}, u[3] = {i - 1, j - 1, k - 1};
           u[F] += 1;
-          double g = (phi[cidx(c, u[0], u[1], u[2])] - phi[cidx(c, t[0], t[1], t[2])]) / c->h[F];
+          int tf[3] = {i, j, k};
+          double g = (phi[cidx(c, u[0], u[1], u[2])] - phi[cidx(c, t[0], t[1], t[2])]) / centre_gap(c, F, tf[F]);
           vel[F * P + pidx(c, i, j, k)] -= g;
         }
   if (p)
@@ -604,6 +698,12 @@ static void simple_loop(const or_ctx* c, double* vel, double* p, double tol, int
   double hmin = c->h[0];
   if (c->h[1] < hmin) hmin = c->h[1];
   if (c->h[2] < hmin) hmin = c->h[2];
+  if (c->stretched) {
+    hmin = 1.0;
+    for (int a = 0; a < 3; ++a)
+      for (int t = 1; t <= c->n[a]; ++t)
+        if (cell_width(c, a, t) < hmin) hmin = cell_width(c, a, t);
+  }
   int pass = 0;
   double maxdiv = 0.0, rel = 0.0, phin = 0.0;
   for (pass = 1; pass <= max_passes; ++pass) {

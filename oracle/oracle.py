@@ -35,7 +35,8 @@ def build_oracle(force: bool = False) -> str:
 class _Grid(ctypes.Structure):
     _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int),
                 ("bc", ctypes.c_int), ("tproj", ctypes.c_int),
-                ("gr", ctypes.c_double), ("pr", ctypes.c_double)]
+                ("gr", ctypes.c_double), ("pr", ctypes.c_double),
+                ("stretch", ctypes.c_double)]
 
 
 class Stats(ctypes.Structure):
@@ -86,12 +87,13 @@ def _ptr(a):
 class Oracle:
     """One grid's oracle context (Eqs (15)-(20)'s per-axis data computed once)."""
 
-    def __init__(self, nx, ny, nz, bc=0, gr=1e6, pr=0.71, tproj=0, tol=1e-13, max_passes=10):
+    def __init__(self, nx, ny, nz, bc=0, gr=1e6, pr=0.71, tproj=0, tol=1e-13, max_passes=10,
+                 stretch=0.0):
         self.lib = _load()
         self.nx, self.ny, self.nz = nx, ny, nz
         self.bc, self.gr, self.pr, self.tproj = bc, gr, pr, tproj
-        self.tol, self.max_passes = tol, max_passes
-        self._g = _Grid(nx, ny, nz, bc, tproj, gr, pr)
+        self.tol, self.max_passes, self.stretch = tol, max_passes, stretch
+        self._g = _Grid(nx, ny, nz, bc, tproj, gr, pr, stretch)
         self._c = self.lib.or_create(ctypes.byref(self._g))
         if not self._c:
             raise ValueError("oracle: invalid grid")
@@ -115,7 +117,7 @@ class Oracle:
     # per-axis data ------------------------------------------------------------------
     def axis_data(self, axis, which):
         n = (self.nx, self.ny, self.nz)[axis]
-        size = {0: n * n, 1: n * n, 2: n, 3: (n + 2) ** 2}[which]
+        size = {0: n * n, 1: n * n, 2: n, 3: (n + 2) ** 2, 4: n + 1, 5: n + 2}[which]
         out = np.zeros(size)
         self.lib.or_axis_data(self._c, axis, which, _ptr(out))
         if which in (0, 1):

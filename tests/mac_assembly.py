@@ -4,13 +4,32 @@ The oracle applies its stencils point by point; this module builds the same oper
 sparse matrices from 1D factors combined with Kronecker products (the structure of Eq (14)).
 A mistake in either (a wrong index, sign, spacing or interpolation weight) makes them differ.
 Padded layout (nz+2, ny+2, nx+2), x fastest, so a 3D operator is kron(Mz, My, Mx).
+A stretched grid (Eq 22, parameter s) maps the faces xi -> xi - s sin(2 pi xi); cell centres
+are the midpoints of their faces, and each row of the flux-form Laplacian, the divergence and
+the gradient divides by the width it spans (control volume, cell, centre gap).
 """
 import numpy as np
 import scipy.sparse as sp
 
 
-def positions(n, face):
+def stretched_faces(n, s):
+    """Face coordinates 0..n of Eq (22)."""
+    xi = np.arange(n + 1) / n
+    f = xi - s * np.sin(2 * np.pi * xi)
+    f[0], f[n] = 0.0, 1.0
+    return f
+
+
+def positions(n, face, s=0.0):
     """Node coordinates of indices 0..n+1 along one axis."""
+    if s != 0.0:
+        f = stretched_faces(n, s)
+        if face:
+            return np.append(f, 2.0 - f[n - 1])  # padding, never used by an interior row
+        p = np.empty(n + 2)
+        p[0], p[n + 1] = 0.0, 1.0
+        p[1:n + 1] = 0.5 * (f[:-1] + f[1:])
+        return p
     if face:
         p = np.arange(n + 2) / n
         p[n + 1] = 1.0 + 1.0 / n  # padding, never used by an interior row
@@ -24,19 +43,33 @@ def interior_rows(n, face):
     return np.arange(1, n) if face else np.arange(1, n + 1)
 
 
-def d2_1d(n, face):
-    p, h = positions(n, face), 1.0 / n
+def control_volume(n, face, s=0.0):
+    """Width of the control volume of each node 0..n+1 (interior rows only are meaningful)."""
+    if s == 0.0:
+        return np.full(n + 2, 1.0 / n)
+    w = np.ones(n + 2)
+    if face:
+        c = positions(n, False, s)
+        w[1:n] = c[2:n + 1] - c[1:n]
+    else:
+        f = stretched_faces(n, s)
+        w[1:n + 1] = f[1:] - f[:-1]
+    return w
+
+
+def d2_1d(n, face, s=0.0):
+    p, h = positions(n, face, s), control_volume(n, face, s)
     M = sp.lil_matrix((n + 2, n + 2))
     for t in interior_rows(n, face):
         wl, wr = 1.0 / (p[t] - p[t - 1]), 1.0 / (p[t + 1] - p[t])
-        M[t, t - 1] += wl / h
-        M[t, t + 1] += wr / h
-        M[t, t] -= (wl + wr) / h
+        M[t, t - 1] += wl / h[t]
+        M[t, t + 1] += wr / h[t]
+        M[t, t] -= (wl + wr) / h[t]
     return M.tocsr()
 
 
-def d1_1d(n, face):
-    p = positions(n, face)
+def d1_1d(n, face, s=0.0):
+    p = positions(n, face, s)
     M = sp.lil_matrix((n + 2, n + 2))
     for t in interior_rows(n, face):
         dm, dp = p[t] - p[t - 1], p[t + 1] - p[t]
@@ -66,8 +99,9 @@ def cell_to_face(n):
 
 
 class MacOps:
-    def __init__(self, nx, ny, nz):
+    def __init__(self, nx, ny, nz, s=0.0):
         self.n = (nx, ny, nz)
+        self.s = s
         self.P = (nx + 2) * (ny + 2) * (nz + 2)
 
     def kron3(self, mats):
@@ -84,10 +118,10 @@ class MacOps:
         return self.kron3(mats)
 
     def laplace(self, F):
-        return sum(self.along(a, d2_1d(self.n[a], F == a)) for a in range(3))
+        return sum(self.along(a, d2_1d(self.n[a], F == a, self.s)) for a in range(3))
 
     def deriv(self, F, a):
-        return self.along(a, d1_1d(self.n[a], F == a))
+        return self.along(a, d1_1d(self.n[a], F == a, self.s))
 
     def interp(self, c, F):
         """Velocity component c (faces normal to axis c) to the nodes of field F (3 = cell)."""
@@ -140,10 +174,11 @@ class MacOps:
         parts = []
         for a in range(3):
             n = self.n[a]
+            w = control_volume(n, False, self.s)
             M = sp.lil_matrix((n + 2, n + 2))
             for t in range(1, n + 1):
-                M[t, t] = n
-                M[t, t - 1] = -n
+                M[t, t] = 1.0 / w[t]
+                M[t, t - 1] = -1.0 / w[t]
             parts.append(self.along(a, M.tocsr()))
         D = sp.hstack(parts).tocsr()
         return sp.diags(self.dof_mask(3)) @ D
@@ -153,9 +188,10 @@ class MacOps:
         rows = []
         for a in range(3):
             n = self.n[a]
+            w = control_volume(n, True, self.s)
             M = sp.lil_matrix((n + 2, n + 2))
             for t in range(1, n):
-                M[t, t + 1] = n
-                M[t, t] = -n
+                M[t, t + 1] = 1.0 / w[t]
+                M[t, t] = -1.0 / w[t]
             rows.append(sp.diags(self.dof_mask(a)) @ self.along(a, M.tocsr()))
         return sp.vstack(rows).tocsr()

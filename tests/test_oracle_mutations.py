@@ -19,15 +19,34 @@ MUTANTS = {
     "eigenvalue_not_squared": ("c->lamp[a][m] = -4.0 / (h * h) * s * s;", "c->lamp[a][m] = -4.0 / (h * h) * s;"),
     "wall_pair_not_averaged": ("*lo0 = *lo1 = ml;", "*lo0 = ml;"),
     "advection_sign": ("- advect(c, xv, Th, FT, i, j, k);\n  } else {", "+ advect(c, xv, Th, FT, i, j, k);\n  } else {"),
-    "gradient_direction": ("double g = (phi[cidx(c, u[0], u[1], u[2])] - phi[cidx(c, t[0], t[1], t[2])]) / c->h[F];",
-                           "double g = (phi[cidx(c, t[0], t[1], t[2])] - phi[cidx(c, u[0], u[1], u[2])]) / c->h[F];"),
+    "gradient_direction": ("double g = (phi[cidx(c, u[0], u[1], u[2])] - phi[cidx(c, t[0], t[1], t[2])]) /",
+                           "double g = (phi[cidx(c, t[0], t[1], t[2])] - phi[cidx(c, u[0], u[1], u[2])]) /"),
     "wall_half_spacing_dropped": ("if (t <= 0) return 0.0;", "if (t <= 0) return -0.5 / n;"),
 }
 
+# Mistakes that only a stretched grid (Eq 22) can show; run against the stretched-grid pins.
+STRETCH_MUTANTS = {
+    "stretch_sign": ("c->xf[a][t] = xi - g->stretch * sin(2.0 * M_PI * xi);",
+                     "c->xf[a][t] = xi + g->stretch * sin(2.0 * M_PI * xi);"),
+    "stretch_centres_unmapped": ("for (int t = 1; t <= n; ++t) c->xc[a][t] = 0.5 * (c->xf[a][t - 1] + c->xf[a][t]);",
+                                 "for (int t = 1; t <= n; ++t) c->xc[a][t] = ((double)t - 0.5) / n;"),
+    "stretch_face_volume_is_cell_width": ("return face_like(F, a) ? centre_gap(c, a, t) : cell_width(c, a, t);",
+                                          "return cell_width(c, a, t);"),
+    "stretch_gradient_uses_cell_width": ("/ centre_gap(c, F, tf[F]);", "/ cell_width(c, F, tf[F]);"),
+    "stretch_divergence_uses_centre_gap": ("/ cell_width(c, 0, i) +", "/ centre_gap(c, 0, i) +"),
+    "stretch_one_sided_symmetrisation": ("S[(size_t)(t - 1) * n + t] = 1.0 / (g * sqrt(dx * cell_width(c, a, t + 1)));",
+                                         "S[(size_t)(t - 1) * n + t] = 1.0 / (g * dx);"),
+    "stretch_eigenvector_scaling_inverted": ("Q[(size_t)t * n + order[m]] / sqrt(cell_width(c, a, t + 1));",
+                                             "Q[(size_t)t * n + order[m]] * sqrt(cell_width(c, a, t + 1));"),
+}
 
-@pytest.mark.parametrize("name", sorted(MUTANTS))
+CASES = {name: (old, new, "test_oracle_pins.py") for name, (old, new) in MUTANTS.items()}
+CASES.update({name: (old, new, "test_oracle_stretch.py") for name, (old, new) in STRETCH_MUTANTS.items()})
+
+
+@pytest.mark.parametrize("name", sorted(CASES))
 def test_planted_mistake_fails_a_pin(name, tmp_path):
-    old, new = MUTANTS[name]
+    old, new, pins = CASES[name]
     src = open(SRC).read()
     assert src.count(old) == 1, f"mutation site for {name} not found exactly once"
     mutated = tmp_path / "kv_oracle_mut.c"
@@ -37,6 +56,6 @@ def test_planted_mistake_fails_a_pin(name, tmp_path):
                            "-o", str(lib), str(mutated), "-lm"])
     env = dict(os.environ, KV_ORACLE_LIB=str(lib), OMP_NUM_THREADS="2")
     r = subprocess.run([sys.executable, "-m", "pytest", "-q", "-x", "-p", "no:cacheprovider",
-                        os.path.join(ROOT, "tests", "test_oracle_pins.py")],
+                        os.path.join(ROOT, "tests", pins)],
                        cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
     assert r.returncode != 0, f"no pin caught the mutation {name}:\n{r.stdout[-2000:]}"
