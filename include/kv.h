@@ -84,6 +84,12 @@ typedef struct {
                         w -= V h2 only when ||h2|| exceeds the sweeps' rounding level (2^-46 ||w||
                         for KV_PREC_MIXED's double-float sweeps, 2^-50 ||w|| in FP64); 2 = always
                         apply it */
+  double stretch;    /* grid stretching of Eq (22), Section 3.2: the faces of every axis sit at
+                        x = xi - stretch sin(2 pi xi), xi = t/n; cell centres at the midpoints of
+                        their faces. 0 = uniform grid; must be in [0, 1/(2 pi)) so the mapping stays
+                        monotone (the paper uses up to 0.12). Nonzero needs KV_PREC_FP64; the
+                        transpose, the base-flow gradient and kv_krylov_vector_noalloc take the
+                        uniform grid only. */
 } kv_grid_desc;
 
 typedef struct {
@@ -95,8 +101,10 @@ typedef struct {
 } kv_stats;
 
 /* Creates a grid: validates desc, builds the per-axis eigen-decompositions of Eq (15)
-   (computed once, Section 3.1) and allocates the library's device storage (base flow,
-   Poisson scratch). stream: a cudaStream_t (NULL = legacy default stream). */
+   (computed once, Section 3.1; closed form on the uniform grid, a symmetric tridiagonal QL
+   iteration on a stretched one, KV_ERR_NOT_CONVERGED if it fails) and allocates the library's
+   device storage (base flow, Poisson scratch; a stretched grid adds 14 (n_a + 2) doubles of
+   per-axis weights). stream: a cudaStream_t (NULL = legacy default stream). */
 kv_status kv_create_grid(const kv_grid_desc* desc, void* stream, kv_handle* out);
 
 /* Frees all device storage of the handle. NULL is accepted. */
@@ -176,7 +184,8 @@ kv_status kv_arnoldi_step(kv_handle h, double* V, int j, double* h_col);
    problem of Eq (10) uses it). With the orthogonal reading of Eq (21) the three projections are
    symmetric, so A^T = P_BC J^T (Pi_v (+) P_T); J^T is applied from the same assembled
    coefficients as J. y, z: packed vectors (device, must not overlap). Requires
-   KV_TPROJ_ORTHOGONAL (else KV_ERR_ARG) and a base flow (else KV_ERR_STATE). */
+   KV_TPROJ_ORTHOGONAL and the uniform grid (else KV_ERR_ARG: on a stretched grid Pi_v is
+   symmetric only in the volume-weighted product) and a base flow (else KV_ERR_STATE). */
 kv_status kv_krylov_vector_adjoint(kv_handle h, const double* y, double* z);
 
 /* Sensitivity of <y, A x> to the base state and the Grashof number (with y the adjoint and x

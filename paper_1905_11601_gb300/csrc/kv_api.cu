@@ -4,6 +4,7 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <algorithm>
 #include <cmath>
 #include <new>
 #include <string>
@@ -63,6 +64,139 @@ void neumann_axis(int n, std::vector<double>& fwd, std::vector<double>& inv, std
   }
 }
 
+// Eigen-decomposition of a symmetric tridiagonal matrix (diagonal d, off-diagonal e[i]
+// coupling rows i and i+1, e[n-1] unused) by the implicit QL iteration with Wilkinson shifts
+// (Bowdler, Martin, Reinsch and Wilkinson, Numer. Math. 11, 1968). On return d holds the
+// eigenvalues and column c of Z (row-major n x n, set to the identity here) the eigenvector of
+// d[c]. Returns false if an eigenvalue did not converge within 60 QL sweeps.
+bool tridiag_ql(int n, std::vector<double>& d, std::vector<double>& e, std::vector<double>& Z) {
+  Z.assign((size_t)n * n, 0.0);
+  for (int r = 0; r < n; ++r) Z[(size_t)r * n + r] = 1.0;
+  e.resize(n);
+  e[n - 1] = 0.0;
+  for (int l = 0; l < n; ++l) {
+    for (int sweep = 0;; ++sweep) {
+      // the first negligible off-diagonal at or below row l splits the matrix there
+      int m = l;
+      while (m < n - 1 && fabs(e[m]) > 0x1p-53 * (fabs(d[m]) + fabs(d[m + 1]))) ++m;
+      if (m == l) break;
+      if (sweep == 60) return false;
+      // shift: the eigenvalue of the leading 2x2 block nearer to d[l]
+      const double theta = (d[l + 1] - d[l]) / (2.0 * e[l]);
+      const double rho = hypot(theta, 1.0);
+      double x = d[m] - d[l] + e[l] / (theta + copysign(rho, theta));
+      // chase the bulge from row m up to row l with plane rotations
+      double sn = 1.0, cs = 1.0, carry = 0.0;
+      bool split = false;
+      for (int i = m - 1; i >= l; --i) {
+        const double f = sn * e[i], b = cs * e[i];
+        const double r = hypot(f, x);
+        e[i + 1] = r;
+        if (r == 0.0) {  // underflow: the matrix splits at i+1
+          d[i + 1] -= carry;
+          e[m] = 0.0;
+          split = true;
+          break;
+        }
+        sn = f / r;
+        cs = x / r;
+        const double y = d[i + 1] - carry;
+        const double t = (d[i] - y) * sn + 2.0 * cs * b;
+        carry = sn * t;
+        d[i + 1] = y + carry;
+        x = cs * t - b;
+        for (int k = 0; k < n; ++k) {
+          double* zr = &Z[(size_t)k * n];
+          const double z1 = zr[i + 1], z0 = zr[i];
+          zr[i + 1] = sn * z0 + cs * z1;
+          zr[i] = cs * z0 - sn * z1;
+        }
+      }
+      if (split) continue;
+      d[l] -= carry;
+      e[l] = x;
+      e[m] = 0.0;
+    }
+  }
+  return true;
+}
+
+// A stretched axis (Eq 22) with n cells and parameter sp: faces x_t = xi_t - sp sin(2 pi xi_t),
+// cell centres at face midpoints, wall nodes at 0 and 1. Fills the KV_SW_N table rows (n+2
+// each) of the operator weights, divergence and gradient, and the eigen-decomposition of
+// Eq (15) for the pressure-correction Laplacian D G: its 1D factor A = dx^-1 K is similar to
+// the symmetric tridiagonal S = dx^-1/2 K dx^-1/2 = Q Lambda Q^T, so E = dx^-1/2 Q and
+// E^-1 = Q^T dx^1/2. Modes sorted by decreasing eigenvalue; mode 0 (the constants) has
+// eigenvalue exactly 0. Layout of fwd / inv as in neumann_axis.
+bool stretched_axis(int n, double sp, std::vector<double>& tab, std::vector<double>& fwd, std::vector<double>& inv,
+                    std::vector<double>& lam, double& hmin) {
+  const int L = n + 2;
+  const double two_pi = 6.283185307179586476925286766559;
+  std::vector<double> xf(n + 1), xc(n + 2), dx(n + 2, 0.0), gap(n + 2, 0.0);
+  for (int t = 0; t <= n; ++t) {
+    const double xi = (double)t / n;
+    xf[t] = xi - sp * sin(two_pi * xi);
+  }
+  xf[0] = 0.0;
+  xf[n] = 1.0;
+  xc[0] = 0.0;
+  xc[n + 1] = 1.0;
+  for (int t = 1; t <= n; ++t) xc[t] = 0.5 * (xf[t - 1] + xf[t]);
+  for (int t = 1; t <= n; ++t) dx[t] = xf[t] - xf[t - 1];
+  for (int t = 1; t < n; ++t) gap[t] = xc[t + 1] - xc[t];
+  hmin = 1.0;
+  for (int t = 1; t <= n; ++t) hmin = fmin(hmin, dx[t]);
+
+  tab.assign((size_t)KV_SW_N * L, 0.0);
+  auto row = [&](int r, int t) -> double& { return tab[(size_t)r * L + t]; };
+  // 3-point weights at x0 between xm and xp: first derivative (exact for quadratics) and the
+  // flux-form second derivative over a control volume of width w
+  auto put = [&](int r1, int r2, int t, double xm, double x0, double xp, double w) {
+    const double dm = x0 - xm, dp = xp - x0;
+    row(r1, t) = -dp / (dm * (dm + dp));
+    row(r1 + 1, t) = (dp - dm) / (dm * dp);
+    row(r1 + 2, t) = dm / (dp * (dm + dp));
+    const double wm = 1.0 / (dm * w), wp = 1.0 / (dp * w);
+    row(r2, t) = wm;
+    row(r2 + 1, t) = -(wm + wp);
+    row(r2 + 2, t) = wp;
+  };
+  for (int t = 1; t <= n; ++t) {
+    row(KV_SW_IDC, t) = 1.0 / dx[t];
+    put(KV_SW_C1, KV_SW_C2, t, xc[t - 1], xc[t], xc[t + 1], dx[t]);
+  }
+  for (int t = 1; t < n; ++t) {
+    row(KV_SW_IDF, t) = 1.0 / gap[t];
+    put(KV_SW_F1, KV_SW_F2, t, xf[t - 1], xf[t], xf[t + 1], gap[t]);
+  }
+
+  // S on cells c = 0..n-1 (cell t = c + 1)
+  std::vector<double> d(n, 0.0), e(n, 0.0), Q;
+  for (int c = 0; c < n; ++c) {
+    const int t = c + 1;
+    if (t < n) d[c] -= 1.0 / (gap[t] * dx[t]);
+    if (t > 1) d[c] -= 1.0 / (gap[t - 1] * dx[t]);
+    if (t < n) e[c] = 1.0 / (gap[t] * sqrt(dx[t] * dx[t + 1]));
+  }
+  if (!tridiag_ql(n, d, e, Q)) return false;
+  std::vector<int> order(n);
+  for (int m = 0; m < n; ++m) order[m] = m;
+  std::sort(order.begin(), order.end(), [&](int a, int b) { return d[a] > d[b]; });
+  fwd.assign((size_t)n * n, 0.0);
+  inv.assign((size_t)n * n, 0.0);
+  lam.assign(n, 0.0);
+  for (int m = 0; m < n; ++m) {
+    const int q = order[m];
+    lam[m] = m == 0 ? 0.0 : d[q];
+    for (int c = 0; c < n; ++c) {
+      const double z = Q[(size_t)c * n + q], w = sqrt(dx[c + 1]);
+      fwd[(size_t)m * n + c] = z * w;  // E^-1: row = mode, column = node
+      inv[(size_t)c * n + m] = z / w;  // E: row = node, column = mode
+    }
+  }
+  return true;
+}
+
 kv_status validate(const kv_grid_desc* d, std::string& msg) {
   if (!d) { msg = "desc is NULL"; return KV_ERR_ARG; }
   if (d->nx < 2 || d->ny < 2 || d->nz < 2 || d->nx > 1024 || d->ny > 1024 || d->nz > 1024) {
@@ -76,6 +210,8 @@ kv_status validate(const kv_grid_desc* d, std::string& msg) {
   if (d->cgs_passes != 0 && d->cgs_passes != 2) { msg = "cgs_passes must be 0 or 2"; return KV_ERR_ARG; }
   if (!(d->gr > 0) || !(d->pr > 0) || !isfinite(d->gr) || !isfinite(d->pr)) { msg = "gr and pr must be finite and > 0"; return KV_ERR_ARG; }
   if (d->tol < 0 || d->max_passes < 0 || d->max_passes > 100) { msg = "tol must be >= 0 and max_passes in [0, 100]"; return KV_ERR_ARG; }
+  if (!(d->stretch >= 0.0 && d->stretch < 0.15915494309189533)) { msg = "stretch must be in [0, 1/(2 pi))"; return KV_ERR_ARG; }
+  if (d->stretch != 0.0 && d->precision != KV_PREC_FP64) { msg = "a stretched grid needs KV_PREC_FP64"; return KV_ERR_ARG; }
   return KV_OK;
 }
 
@@ -89,6 +225,7 @@ void free_all(kv_grid* h) {
   cudaFree(h->tpd_b);
   for (int a = 0; a < 6; ++a) cudaFree(h->Wm[a]);
   for (int a = 0; a < 3; ++a) cudaFree(h->lam[a]);
+  cudaFree(h->sw);
   cudaFree(h->red);
   cudaFree(h->partials);
   cudaFree(h->hdev);
@@ -132,7 +269,7 @@ kv_status simple_project(kv_grid* h, double* yvel, double* p, kv_stats* st) {
   const int max_passes = h->d.max_passes > 0 ? h->d.max_passes : 1;
   const bool want = st != nullptr || max_passes > 1;
   const double tol = h->d.tol > 0 ? h->d.tol : 1e-12;
-  double hmin = fmin(h->g.hx, fmin(h->g.hy, h->g.hz));
+  const double hmin = h->hmin;
   int pass = 0;
   double maxdiv = 0, rel = 0;
   const double* src = h->vstar;
@@ -342,12 +479,29 @@ kv_status kv_create_grid(const kv_grid_desc* desc, void* stream, kv_handle* out)
     delete h;
     return st;
   }
-  std::vector<double> fwdm[3], invm[3];
+  h->hmin = fmin(g.hx, fmin(g.hy, g.hz));
+  const bool stretched = desc->stretch != 0.0;
+  std::vector<double> fwdm[3], invm[3], tabs;
+  if (stretched) h->hmin = 1.0;
   for (int a = 0; a < 3; ++a) {
     std::vector<double>& fwd = fwdm[a];
     std::vector<double>& inv = invm[a];
     std::vector<double> lam;
-    neumann_axis(n[a], fwd, inv, lam);
+    if (stretched) {
+      std::vector<double> tab;
+      double hm = 1.0;
+      if (!stretched_axis(n[a], desc->stretch, tab, fwd, inv, lam, hm)) {
+        g_create_error = "kv_create_grid: the tridiagonal eigensolver did not converge";
+        free_all(h);
+        delete h;
+        return KV_ERR_NOT_CONVERGED;
+      }
+      h->hmin = fmin(h->hmin, hm);
+      g.swo[a] = (int)tabs.size();
+      tabs.insert(tabs.end(), tab.begin(), tab.end());
+    } else {
+      neumann_axis(n[a], fwd, inv, lam);
+    }
     if ((st = dalloc(h, &h->Wm[a], fwd.size())) || (st = dalloc(h, &h->Wm[3 + a], inv.size())) ||
         (st = dalloc(h, &h->lam[a], lam.size()))) {
       g_create_error = h->err;
@@ -358,6 +512,16 @@ kv_status kv_create_grid(const kv_grid_desc* desc, void* stream, kv_handle* out)
     cudaMemcpy(h->Wm[a], fwd.data(), fwd.size() * sizeof(double), cudaMemcpyHostToDevice);
     cudaMemcpy(h->Wm[3 + a], inv.data(), inv.size() * sizeof(double), cudaMemcpyHostToDevice);
     cudaMemcpy(h->lam[a], lam.data(), lam.size() * sizeof(double), cudaMemcpyHostToDevice);
+  }
+  if (stretched) {
+    if ((st = dalloc(h, &h->sw, tabs.size()))) {
+      g_create_error = h->err;
+      free_all(h);
+      delete h;
+      return st;
+    }
+    cudaMemcpy(h->sw, tabs.data(), tabs.size() * sizeof(double), cudaMemcpyHostToDevice);
+    g.sw = h->sw;
   }
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) {
@@ -679,6 +843,8 @@ kv_status kv_krylov_vector_adjoint(kv_handle h, const double* y, double* z) {
   if (!h->has_base) return fail(h, KV_ERR_STATE, "kv_krylov_vector_adjoint: no base flow set");
   if (h->d.tproj != KV_TPROJ_ORTHOGONAL)
     return fail(h, KV_ERR_ARG, "kv_krylov_vector_adjoint: defined for the orthogonal temperature projection");
+  if (h->g.sw)
+    return fail(h, KV_ERR_ARG, "kv_krylov_vector_adjoint: defined on the uniform grid (the velocity projection of a stretched grid is not symmetric)");
   const size_t L = 4 * h->P;
   if (y < z + L && z < y + L) return fail(h, KV_ERR_ARG, "kv_krylov_vector_adjoint: y and z overlap");
   kv_status s = project_output_side(h, y);
@@ -693,6 +859,8 @@ kv_status kv_base_flow_gradient(kv_handle h, const double* x, const double* y, d
   if (!h->has_base) return fail(h, KV_ERR_STATE, "kv_base_flow_gradient: no base flow set");
   if (h->d.tproj != KV_TPROJ_ORTHOGONAL)
     return fail(h, KV_ERR_ARG, "kv_base_flow_gradient: defined for the orthogonal temperature projection");
+  if (h->g.sw)
+    return fail(h, KV_ERR_ARG, "kv_base_flow_gradient: defined on the uniform grid (the velocity projection of a stretched grid is not symmetric)");
   kv_status s = project_output_side(h, y);
   if (s != KV_OK) return s;
   if (g_base) {

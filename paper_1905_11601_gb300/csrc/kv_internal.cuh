@@ -21,7 +21,15 @@ constexpr int KV_NCOEF = 37;
 // are affine in the minus ones)
 constexpr int KV_NCOEF_DF = 25;
 
-// Device-side description of the uniform MAC grid.
+// Per-axis tables of a stretched grid (Eq 22): KV_SW_N rows of n_a + 2 doubles per axis,
+// indexed by the padded index t along the axis (rows for t outside their range are 0).
+//   IDC      1 / cell width, cells t = 1..n (divergence)
+//   IDF      1 / distance between the centres of cells t and t+1, faces t = 1..n-1 (gradient)
+//   C1, C2   first / second derivative weights (minus, centre, plus) at a cell-like node t
+//   F1, F2   the same at a face-like node t = 1..n-1
+enum { KV_SW_IDC = 0, KV_SW_IDF = 1, KV_SW_C1 = 2, KV_SW_C2 = 5, KV_SW_F1 = 8, KV_SW_F2 = 11, KV_SW_N = 14 };
+
+// Device-side description of the MAC grid.
 struct KvGeom {
   int nx, ny, nz;   // cells per axis
   int X, Y, Z;      // padded extents n+2
@@ -31,6 +39,8 @@ struct KvGeom {
   double nu, kappa; // Gr^-1/2 and (Pr Gr^1/2)^-1 (Eqs (1)-(2) scaling)
   int bc;           // KV_BC_CC / KV_BC_AA
   int tproj;        // KV_TPROJ_*
+  const double* sw = nullptr;  // stretched grid: the KV_SW_* tables (device); nullptr: uniform
+  int swo[3] = {0, 0, 0};      // offset of each axis' tables in sw
 };
 
 struct kv_grid {
@@ -51,6 +61,8 @@ struct kv_grid {
   double* tpd_b = nullptr;  // Nc
   double* Wm[6] = {};       // per-axis GEMM operands: forward E_a^-1 (a = 0..2), inverse E_a
   double* lam[3] = {};      // eigenvalues of the 1D Neumann Laplacians (Eq 15)
+  double* sw = nullptr;     // stretched grid: the KV_SW_* weight tables (g.sw points here)
+  double hmin = 0.0;        // smallest cell width (the SIMPLE test)
   unsigned long long* red = nullptr;  // [0] max|D v| bits, [1] max|v| bits
   double* partials = nullptr;         // Arnoldi block partial sums
   size_t partials_cap = 0;            // in doubles

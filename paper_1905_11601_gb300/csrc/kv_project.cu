@@ -1,11 +1,23 @@
 // Divergence and the fused velocity correction of the SIMPLE / Chorin step (Section 3.1):
 // b = D v* on the cells; v = v* - G phi on the interior faces; p = phi; and the pointwise
-// divergence residual max |D v| used as the SIMPLE stopping test. FP64, and for the mixed
-// precision path the same arithmetic in double-float on the FP32 pipe.
+// divergence residual max |D v| used as the SIMPLE stopping test. FP64 on the uniform or the
+// stretched grid (Eq 22), and for the mixed precision path (uniform grid) the same arithmetic
+// in double-float on the FP32 pipe.
 #include "kv_df.cuh"
 #include "kv_internal.cuh"
 
 namespace {
+
+// 1 / width along axis A at padded index t: 1/h on the uniform grid; on a stretched grid
+// (Eq 22) the table row ROW: KV_SW_IDC (cell widths, cells t = 1..n) or KV_SW_IDF (distances
+// between adjacent cell centres, faces t = 1..n-1).
+template <int A, int ROW>
+__device__ __forceinline__ double inv_w(const KvGeom& g, int t) {
+  const double ih = A == 0 ? g.ihx : (A == 1 ? g.ihy : g.ihz);
+  if (!g.sw) return ih;
+  const int L = (A == 0 ? g.nx : (A == 1 ? g.ny : g.nz)) + 2;
+  return __ldg(g.sw + g.swo[A] + ROW * L + t);
+}
 
 __global__ void __launch_bounds__(256) k_divergence(KvGeom g, const double* __restrict__ vel, size_t P,
                                                     double* __restrict__ b) {
@@ -17,8 +29,9 @@ __global__ void __launch_bounds__(256) k_divergence(KvGeom g, const double* __re
   const double* v = vel + P;
   const double* w = vel + 2 * P;
   const int e = i + g.X * (j + g.Y * k);
-  const double d = (__ldg(u + e) - __ldg(u + e - 1)) * g.ihx + (__ldg(v + e) - __ldg(v + e - g.X)) * g.ihy +
-                   (__ldg(w + e) - __ldg(w + e - g.X * g.Y)) * g.ihz;
+  const double d = (__ldg(u + e) - __ldg(u + e - 1)) * inv_w<0, KV_SW_IDC>(g, i) +
+                   (__ldg(v + e) - __ldg(v + e - g.X)) * inv_w<1, KV_SW_IDC>(g, j) +
+                   (__ldg(w + e) - __ldg(w + e - g.X * g.Y)) * inv_w<2, KV_SW_IDC>(g, k);
   b[(i - 1) + (size_t)g.nx * ((j - 1) + (size_t)g.ny * (k - 1))] = d;
 }
 
@@ -37,15 +50,15 @@ struct Corr {
   __device__ __forceinline__ int at(int i, int j, int k) const { return i + g.X * (j + g.Y * k); }
   __device__ __forceinline__ double u(int i, int j, int k) const {
     if (!(i >= 1 && i <= g.nx - 1 && j >= 1 && j <= g.ny && k >= 1 && k <= g.nz)) return 0.0;
-    return __ldg(vs + at(i, j, k)) - (ph(i + 1, j, k) - ph(i, j, k)) * g.ihx;
+    return __ldg(vs + at(i, j, k)) - (ph(i + 1, j, k) - ph(i, j, k)) * inv_w<0, KV_SW_IDF>(g, i);
   }
   __device__ __forceinline__ double v(int i, int j, int k) const {
     if (!(i >= 1 && i <= g.nx && j >= 1 && j <= g.ny - 1 && k >= 1 && k <= g.nz)) return 0.0;
-    return __ldg(vs + P + at(i, j, k)) - (ph(i, j + 1, k) - ph(i, j, k)) * g.ihy;
+    return __ldg(vs + P + at(i, j, k)) - (ph(i, j + 1, k) - ph(i, j, k)) * inv_w<1, KV_SW_IDF>(g, j);
   }
   __device__ __forceinline__ double w(int i, int j, int k) const {
     if (!(i >= 1 && i <= g.nx && j >= 1 && j <= g.ny && k >= 1 && k <= g.nz - 1)) return 0.0;
-    return __ldg(vs + 2 * P + at(i, j, k)) - (ph(i, j, k + 1) - ph(i, j, k)) * g.ihz;
+    return __ldg(vs + 2 * P + at(i, j, k)) - (ph(i, j, k + 1) - ph(i, j, k)) * inv_w<2, KV_SW_IDF>(g, k);
   }
 };
 
@@ -67,7 +80,9 @@ __global__ void __launch_bounds__(256) k_correct(KvGeom g, const double* __restr
     const bool cell = i >= 1 && i <= g.nx && j >= 1 && j <= g.ny && k >= 1 && k <= g.nz;
     if (check) vmax = fmax(fabs(ur), fmax(fabs(vr), fabs(wr)));
     if (check && cell) {
-      const double d = (ur - C.u(i - 1, j, k)) * g.ihx + (vr - C.v(i, j - 1, k)) * g.ihy + (wr - C.w(i, j, k - 1)) * g.ihz;
+      const double d = (ur - C.u(i - 1, j, k)) * inv_w<0, KV_SW_IDC>(g, i) +
+                       (vr - C.v(i, j - 1, k)) * inv_w<1, KV_SW_IDC>(g, j) +
+                       (wr - C.w(i, j, k - 1)) * inv_w<2, KV_SW_IDC>(g, k);
       dmax = fabs(d);
     }
     if (p) {

@@ -1,9 +1,12 @@
 // The linearised Boussinesq operator of Eqs (8)-(9) as used by Eqs (11)-(12), and the
-// steady residual of Eqs (1)-(2), on the uniform MAC grid (FP64).
+// steady residual of Eqs (1)-(2), on the MAC grid (FP64), uniform or stretched by Eq (22).
 //
 // Discrete operators (the paper defers its schemes to its reference [11]; these are the
 // readings this library implements):
-//   diffusion  flux form ((f+ - f)/(x+ - x) - (f - f-)/(x - x-)) / h, wall nodes at h/2;
+//   diffusion  flux form ((f+ - f)/(x+ - x) - (f - f-)/(x - x-)) / w, w the control-volume
+//              width (h on the uniform grid; the cell width at a cell-like node and the
+//              distance between the adjacent cell centres at a face-like node when stretched);
+//              wall nodes on the walls, cell centres at the midpoints of their faces;
 //   advection  (a . grad) b in advective form: 3-point central derivative of b at b's node
 //              (non-uniform next to a wall node), times a averaged (2 or 4 points) there;
 //   buoyancy   T e_z on a w-face: mean of the two adjacent cell temperatures.
@@ -31,6 +34,43 @@ __device__ __forceinline__ W3 d2_cell(int t, int n, double ih2) {
 }
 __device__ __forceinline__ W3 d1_face(double ih) { return {-0.5 * ih, 0.0, 0.5 * ih}; }
 __device__ __forceinline__ W3 d2_face(double ih2) { return {ih2, -2.0 * ih2, ih2}; }
+
+// Weights at padded index t along axis A: the stretched grid's tables (Eq 22) when present,
+// else the uniform formulas above. The branch is uniform across the grid.
+template <int A>
+__device__ __forceinline__ int ax_n(const KvGeom& g) {
+  return A == 0 ? g.nx : (A == 1 ? g.ny : g.nz);
+}
+template <int A>
+__device__ __forceinline__ double ax_ih(const KvGeom& g) {
+  return A == 0 ? g.ihx : (A == 1 ? g.ihy : g.ihz);
+}
+template <int A>
+__device__ __forceinline__ double ax_ih2(const KvGeom& g) {
+  return A == 0 ? g.ihx2 : (A == 1 ? g.ihy2 : g.ihz2);
+}
+template <int A>
+__device__ __forceinline__ W3 sw3(const KvGeom& g, int row, int t) {
+  const int L = ax_n<A>(g) + 2;
+  const double* p = g.sw + g.swo[A] + row * L + t;
+  return {__ldg(p), __ldg(p + L), __ldg(p + 2 * L)};
+}
+template <int A>
+__device__ __forceinline__ W3 wc1(const KvGeom& g, int t) {
+  return g.sw ? sw3<A>(g, KV_SW_C1, t) : d1_cell(t, ax_n<A>(g), ax_ih<A>(g));
+}
+template <int A>
+__device__ __forceinline__ W3 wc2(const KvGeom& g, int t) {
+  return g.sw ? sw3<A>(g, KV_SW_C2, t) : d2_cell(t, ax_n<A>(g), ax_ih2<A>(g));
+}
+template <int A>
+__device__ __forceinline__ W3 wf1(const KvGeom& g, int t) {
+  return g.sw ? sw3<A>(g, KV_SW_F1, t) : d1_face(ax_ih<A>(g));
+}
+template <int A>
+__device__ __forceinline__ W3 wf2(const KvGeom& g, int t) {
+  return g.sw ? sw3<A>(g, KV_SW_F2, t) : d2_face(ax_ih2<A>(g));
+}
 
 __device__ __forceinline__ double ap(const W3& w, double fm, double f0, double fp) {
   return fma(w.m, fm, fma(w.c, f0, w.p * fp));
@@ -110,15 +150,13 @@ __global__ void __launch_bounds__(256) k_stencil(KvGeom g, const double* __restr
   // base flow (raw) and input (projected in MODE 0)
   Loader<false> B{G, base, base + P, base + 2 * P, base + 3 * P};
   Loader<PROJ> Xl{G, x, x + P, x + 2 * P, x + 3 * P};
-  const double ihx = g.ihx, ihy = g.ihy, ihz = g.ihz;
-  const double ihx2 = ihx * ihx, ihy2 = ihy * ihy, ihz2 = ihz * ihz;
 
   // ---- u on the x-face (i, j, k) ----
   double ru = 0.0;
   if (G.dof_u(i, j, k)) {
-    const W3 dx1 = d1_face(ihx), dx2 = d2_face(ihx2);
-    const W3 dy1 = d1_cell(j, g.ny, ihy), dy2 = d2_cell(j, g.ny, ihy2);
-    const W3 dz1 = d1_cell(k, g.nz, ihz), dz2 = d2_cell(k, g.nz, ihz2);
+    const W3 dx1 = wf1<0>(g, i), dx2 = wf2<0>(g, i);
+    const W3 dy1 = wc1<1>(g, j), dy2 = wc2<1>(g, j);
+    const W3 dz1 = wc1<2>(g, k), dz2 = wc2<2>(g, k);
     const double c = Xl.lu(i, j, k);
     const double xm = Xl.lu(i - 1, j, k), xp = Xl.lu(i + 1, j, k);
     const double ym = Xl.lu(i, j - 1, k), yp = Xl.lu(i, j + 1, k);
@@ -143,9 +181,9 @@ __global__ void __launch_bounds__(256) k_stencil(KvGeom g, const double* __restr
   // ---- v on the y-face (i, j, k) ----
   double rv = 0.0;
   if (G.dof_v(i, j, k)) {
-    const W3 dx1 = d1_cell(i, g.nx, ihx), dx2 = d2_cell(i, g.nx, ihx2);
-    const W3 dy1 = d1_face(ihy), dy2 = d2_face(ihy2);
-    const W3 dz1 = d1_cell(k, g.nz, ihz), dz2 = d2_cell(k, g.nz, ihz2);
+    const W3 dx1 = wc1<0>(g, i), dx2 = wc2<0>(g, i);
+    const W3 dy1 = wf1<1>(g, j), dy2 = wf2<1>(g, j);
+    const W3 dz1 = wc1<2>(g, k), dz2 = wc2<2>(g, k);
     const double c = Xl.lv(i, j, k);
     const double xm = Xl.lv(i - 1, j, k), xp = Xl.lv(i + 1, j, k);
     const double ym = Xl.lv(i, j - 1, k), yp = Xl.lv(i, j + 1, k);
@@ -170,9 +208,9 @@ __global__ void __launch_bounds__(256) k_stencil(KvGeom g, const double* __restr
   // ---- w on the z-face (i, j, k), with the buoyancy term T e_z ----
   double rw = 0.0;
   if (G.dof_w(i, j, k)) {
-    const W3 dx1 = d1_cell(i, g.nx, ihx), dx2 = d2_cell(i, g.nx, ihx2);
-    const W3 dy1 = d1_cell(j, g.ny, ihy), dy2 = d2_cell(j, g.ny, ihy2);
-    const W3 dz1 = d1_face(ihz), dz2 = d2_face(ihz2);
+    const W3 dx1 = wc1<0>(g, i), dx2 = wc2<0>(g, i);
+    const W3 dy1 = wc1<1>(g, j), dy2 = wc2<1>(g, j);
+    const W3 dz1 = wf1<2>(g, k), dz2 = wf2<2>(g, k);
     const double c = Xl.lw(i, j, k);
     const double xm = Xl.lw(i - 1, j, k), xp = Xl.lw(i + 1, j, k);
     const double ym = Xl.lw(i, j - 1, k), yp = Xl.lw(i, j + 1, k);
@@ -200,9 +238,9 @@ __global__ void __launch_bounds__(256) k_stencil(KvGeom g, const double* __restr
   // ---- T at the cell (i, j, k), then the temperature projection of Eq (21) ----
   const bool cell = i >= 1 && i <= g.nx && j >= 1 && j <= g.ny && k >= 1 && k <= g.nz;
   if (cell) {
-    const W3 dx1 = d1_cell(i, g.nx, ihx), dx2 = d2_cell(i, g.nx, ihx2);
-    const W3 dy1 = d1_cell(j, g.ny, ihy), dy2 = d2_cell(j, g.ny, ihy2);
-    const W3 dz1 = d1_cell(k, g.nz, ihz), dz2 = d2_cell(k, g.nz, ihz2);
+    const W3 dx1 = wc1<0>(g, i), dx2 = wc2<0>(g, i);
+    const W3 dy1 = wc1<1>(g, j), dy2 = wc2<1>(g, j);
+    const W3 dz1 = wc1<2>(g, k), dz2 = wc2<2>(g, k);
     const double c = Xl.lT(i, j, k);
     const double xm = Xl.lT(i - 1, j, k), xp = Xl.lT(i + 1, j, k);
     const double ym = Xl.lT(i, j - 1, k), yp = Xl.lT(i, j + 1, k);
@@ -262,7 +300,6 @@ __global__ void __launch_bounds__(256) k_assemble(KvGeom g, const double* __rest
   double c[KV_NCOEF];
 #pragma unroll
   for (int q = 0; q < KV_NCOEF; ++q) c[q] = 0.0;
-  const double ihx2 = g.ihx * g.ihx, ihy2 = g.ihy * g.ihy, ihz2 = g.ihz * g.ihz;
   // own-field coefficients of nu Lap f - (a . grad) f - f_self * g_self
   auto own = [&](double* o, double diff, const W3& x1, const W3& x2, const W3& y1, const W3& y2, const W3& z1,
                  const W3& z2, double ax, double ay, double az, double gself) {
@@ -275,9 +312,9 @@ __global__ void __launch_bounds__(256) k_assemble(KvGeom g, const double* __rest
     o[0] = diff * (x2.c + y2.c + z2.c) - (ax * x1.c + ay * y1.c + az * z1.c) - gself;
   };
   if (G.dof_u(i, j, k)) {
-    const W3 dx1 = d1_face(g.ihx), dx2 = d2_face(ihx2);
-    const W3 dy1 = d1_cell(j, g.ny, g.ihy), dy2 = d2_cell(j, g.ny, ihy2);
-    const W3 dz1 = d1_cell(k, g.nz, g.ihz), dz2 = d2_cell(k, g.nz, ihz2);
+    const W3 dx1 = wf1<0>(g, i), dx2 = wf2<0>(g, i);
+    const W3 dy1 = wc1<1>(g, j), dy2 = wc2<1>(g, j);
+    const W3 dz1 = wc1<2>(g, k), dz2 = wc2<2>(g, k);
     const double Ua = B.lu(i, j, k);
     const double Va = 0.25 * (B.lv(i, j - 1, k) + B.lv(i, j, k) + B.lv(i + 1, j - 1, k) + B.lv(i + 1, j, k));
     const double Wa = 0.25 * (B.lw(i, j, k - 1) + B.lw(i, j, k) + B.lw(i + 1, j, k - 1) + B.lw(i + 1, j, k));
@@ -289,9 +326,9 @@ __global__ void __launch_bounds__(256) k_assemble(KvGeom g, const double* __rest
     c[8] = -0.25 * gz;
   }
   if (G.dof_v(i, j, k)) {
-    const W3 dx1 = d1_cell(i, g.nx, g.ihx), dx2 = d2_cell(i, g.nx, ihx2);
-    const W3 dy1 = d1_face(g.ihy), dy2 = d2_face(ihy2);
-    const W3 dz1 = d1_cell(k, g.nz, g.ihz), dz2 = d2_cell(k, g.nz, ihz2);
+    const W3 dx1 = wc1<0>(g, i), dx2 = wc2<0>(g, i);
+    const W3 dy1 = wf1<1>(g, j), dy2 = wf2<1>(g, j);
+    const W3 dz1 = wc1<2>(g, k), dz2 = wc2<2>(g, k);
     const double Ua = 0.25 * (B.lu(i - 1, j, k) + B.lu(i, j, k) + B.lu(i - 1, j + 1, k) + B.lu(i, j + 1, k));
     const double Va = B.lv(i, j, k);
     const double Wa = 0.25 * (B.lw(i, j, k - 1) + B.lw(i, j, k) + B.lw(i, j + 1, k - 1) + B.lw(i, j + 1, k));
@@ -303,9 +340,9 @@ __global__ void __launch_bounds__(256) k_assemble(KvGeom g, const double* __rest
     c[17] = -0.25 * gz;
   }
   if (G.dof_w(i, j, k)) {
-    const W3 dx1 = d1_cell(i, g.nx, g.ihx), dx2 = d2_cell(i, g.nx, ihx2);
-    const W3 dy1 = d1_cell(j, g.ny, g.ihy), dy2 = d2_cell(j, g.ny, ihy2);
-    const W3 dz1 = d1_face(g.ihz), dz2 = d2_face(ihz2);
+    const W3 dx1 = wc1<0>(g, i), dx2 = wc2<0>(g, i);
+    const W3 dy1 = wc1<1>(g, j), dy2 = wc2<1>(g, j);
+    const W3 dz1 = wf1<2>(g, k), dz2 = wf2<2>(g, k);
     const double Ua = 0.25 * (B.lu(i - 1, j, k) + B.lu(i, j, k) + B.lu(i - 1, j, k + 1) + B.lu(i, j, k + 1));
     const double Va = 0.25 * (B.lv(i, j - 1, k) + B.lv(i, j, k) + B.lv(i, j - 1, k + 1) + B.lv(i, j, k + 1));
     const double Wa = B.lw(i, j, k);
@@ -317,9 +354,9 @@ __global__ void __launch_bounds__(256) k_assemble(KvGeom g, const double* __rest
     c[26] = -0.25 * gy;
   }
   if (i >= 1 && i <= g.nx && j >= 1 && j <= g.ny && k >= 1 && k <= g.nz) {
-    const W3 dx1 = d1_cell(i, g.nx, g.ihx), dx2 = d2_cell(i, g.nx, ihx2);
-    const W3 dy1 = d1_cell(j, g.ny, g.ihy), dy2 = d2_cell(j, g.ny, ihy2);
-    const W3 dz1 = d1_cell(k, g.nz, g.ihz), dz2 = d2_cell(k, g.nz, ihz2);
+    const W3 dx1 = wc1<0>(g, i), dx2 = wc2<0>(g, i);
+    const W3 dy1 = wc1<1>(g, j), dy2 = wc2<1>(g, j);
+    const W3 dz1 = wc1<2>(g, k), dz2 = wc2<2>(g, k);
     const double Ua = 0.5 * (B.lu(i - 1, j, k) + B.lu(i, j, k));
     const double Va = 0.5 * (B.lv(i, j - 1, k) + B.lv(i, j, k));
     const double Wa = 0.5 * (B.lw(i, j, k - 1) + B.lw(i, j, k));

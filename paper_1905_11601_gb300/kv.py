@@ -42,7 +42,8 @@ class GridDesc(ctypes.Structure):
     _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int),
                 ("spanwise_bc", ctypes.c_int), ("tproj", ctypes.c_int), ("precision", ctypes.c_int),
                 ("gr", ctypes.c_double), ("pr", ctypes.c_double), ("tol", ctypes.c_double),
-                ("max_passes", ctypes.c_int), ("refine_sweeps", ctypes.c_int), ("cgs_passes", ctypes.c_int)]
+                ("max_passes", ctypes.c_int), ("refine_sweeps", ctypes.c_int), ("cgs_passes", ctypes.c_int),
+                ("stretch", ctypes.c_double)]
 
 
 class Stats(ctypes.Structure):
@@ -141,7 +142,7 @@ class Grid:
     """A grid handle: kv_create_grid / kv_destroy_grid around the calls of include/kv.h."""
 
     def __init__(self, nx, ny, nz, bc=KV_BC_CC, gr=1.0e6, pr=0.71, tproj=KV_TPROJ_ORTHOGONAL,
-                 precision=KV_PREC_FP64, tol=0.0, max_passes=0, refine_sweeps=0, cgs_passes=0):
+                 precision=KV_PREC_FP64, tol=0.0, max_passes=0, refine_sweeps=0, cgs_passes=0, stretch=0.0):
         import torch
 
         self.torch = torch
@@ -149,7 +150,8 @@ class Grid:
             raise RuntimeError("libkv needs a CUDA device")
         self.lib = load_library()
         self.nx, self.ny, self.nz = nx, ny, nz
-        self.desc = GridDesc(nx, ny, nz, bc, tproj, precision, gr, pr, tol, max_passes, refine_sweeps, cgs_passes)
+        self.desc = GridDesc(nx, ny, nz, bc, tproj, precision, gr, pr, tol, max_passes, refine_sweeps, cgs_passes,
+                             stretch)
         h = ctypes.c_void_p()
         st = self.lib.kv_create_grid(ctypes.byref(self.desc), ctypes.c_void_p(self._stream()), ctypes.byref(h))
         if st != 0:

@@ -39,19 +39,28 @@ def test_exports_every_declared_symbol(lib):
 
 def _desc(**kw):
     d = dict(nx=8, ny=8, nz=8, spanwise_bc=0, tproj=0, precision=0, gr=1e6, pr=0.71, tol=0.0, max_passes=0,
-             refine_sweeps=0, cgs_passes=0)
+             refine_sweeps=0, cgs_passes=0, stretch=0.0)
     d.update(kw)
     return kv.GridDesc(**d)
 
 
 @pytest.mark.parametrize("bad", [dict(nx=1), dict(nz=2000), dict(spanwise_bc=3), dict(tproj=7),
                                  dict(precision=9), dict(gr=-1.0), dict(pr=0.0), dict(max_passes=-1),
-                                 dict(gr=float("nan")), dict(refine_sweeps=-1), dict(refine_sweeps=99), dict(cgs_passes=1)])
+                                 dict(gr=float("nan")), dict(refine_sweeps=-1), dict(refine_sweeps=99), dict(cgs_passes=1),
+                                 dict(stretch=-0.01), dict(stretch=0.16), dict(stretch=float("nan")),
+                                 dict(stretch=0.12, precision=1)])
 def test_invalid_descriptor_rejected_on_host(lib, bad):
     h = ctypes.c_void_p()
     st = lib.kv_create_grid(ctypes.byref(_desc(**bad)), None, ctypes.byref(h))
     assert st == -1 and not h.value
     assert lib.kv_last_error(None)
+
+
+def test_stretched_grid_rejected_by_the_allocation_free_entry(lib):
+    # validated on the host before any device call
+    d = _desc(stretch=0.05)
+    buf = (ctypes.c_double * 8)()
+    assert lib.kv_krylov_vector_noalloc(ctypes.byref(d), buf, buf, buf, None) == -1
 
 
 def test_null_arguments_rejected(lib):

@@ -1,0 +1,158 @@
+"""GPU parity on stretched grids (Eq 22, Section 3.2): the FP64 CUDA path through the C ABI
+against the FP64 oracle on the same seeded inputs.
+
+Tolerance: relative 2-norm error <= 1e-12, as on the uniform grid. Both sides now take the
+eigenpairs of Eq (15) from an FP64 eigensolver (the library a tridiagonal QL iteration, the
+oracle dense Jacobi rotations), whose errors in the lowest modes grow like eps ||S|| / |lambda_1|
+~ eps n^2; on the velocity correction this stays near 2e-13 up to 64^3, and the pressure
+correction phi is compared at sizes where it stays below 1e-12."""
+import numpy as np
+import pytest
+
+from oracle import Oracle
+from oracle.solvers import newton
+from paper_1905_11601_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+RTOL = 1e-12
+S = 0.12  # the steepest stretching used in Section 3.2
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1905_11601_gb300 import build
+    build.build()
+
+
+def kvmod():
+    from paper_1905_11601_gb300 import kv
+    return kv
+
+
+def rel(a, b):
+    return np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300)
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def setup(n, bc, gr, seed, tproj=0, s=S, count=1):
+    base = np.stack(synth.base_flow(*n, bc, seed))
+    x = synth.krylov_input(*n, seed, count)
+    g = kvmod().Grid(*n, bc=bc, gr=gr, pr=0.71, tproj=tproj, stretch=s)
+    g.set_base_flow(dev(base))
+    return g, base, x
+
+
+CASES = [((5, 4, 6), synth.CC, 2e6, 0), ((16, 16, 16), synth.CC, 1e6, 0), ((33, 17, 24), synth.AA, 3e6, 0),
+         ((33, 17, 24), synth.AA, 3e6, 1), ((2, 3, 2), synth.AA, 1e6, 0), ((48, 48, 48), synth.CC, 3.4e6, 0)]
+
+
+@pytest.mark.parametrize("n,bc,gr,tproj", CASES)
+def test_stretched_krylov_vector_matches_oracle(n, bc, gr, tproj):
+    g, base, x = setup(n, bc, gr, 11601, tproj)
+    p = g.empty()
+    y, st = g.krylov_vector(dev(x[0]), p=p, stats=True)
+    o = Oracle(*n, bc=bc, gr=gr, pr=0.71, tproj=tproj, stretch=S)
+    y_ref, p_ref = o.krylov_vector(base, x[0], want_p=True)
+    y_gpu = y.cpu().numpy()
+    assert rel(y_gpu, y_ref) < RTOL
+    for F in range(4):
+        assert rel(y_gpu[F], y_ref[F]) < 10 * RTOL or np.linalg.norm(y_ref[F]) == 0
+    if max(n) <= 33:
+        assert np.abs(p.cpu().numpy() - p_ref).max() < 1e-12 * np.abs(p_ref).max()
+    assert st.passes == 1 and st.rel_div < 1e-13
+
+
+@pytest.mark.parametrize("s", [0.05, 0.1])
+def test_milder_stretchings_match_oracle(s):
+    """Section 3.2 repeats its runs at a = 0.05 and 0.1."""
+    n, bc = (20, 9, 14), synth.AA
+    g, base, x = setup(n, bc, 1e6, 5, s=s)
+    y = g.krylov_vector(dev(x[0]))
+    y_ref = Oracle(*n, bc=bc, gr=1e6, pr=0.71, stretch=s).krylov_vector(base, x[0])
+    assert rel(y.cpu().numpy(), y_ref) < RTOL
+
+
+def test_stretched_batch_and_graph_path_match_single_calls():
+    n = (12, 10, 14)
+    g, base, x = setup(n, synth.CC, 1e6, 3, count=3)
+    X = dev(x)
+    Y = g.krylov_vector_batch(X)
+    o = Oracle(*n, gr=1e6, pr=0.71, stretch=S)
+    for b in range(3):
+        assert rel(Y[b].cpu().numpy(), o.krylov_vector(base, x[b])) < RTOL
+
+
+def test_stretched_newton_residual_matches_oracle():
+    n, bc = (12, 10, 14), synth.CC
+    kv = kvmod()
+    St = np.stack(synth.base_flow(*n, bc, 9))
+    g = kv.Grid(*n, bc=bc, gr=1e5, pr=0.71, stretch=S)
+    F, nrm = g.newton_residual(dev(St))
+    F_ref, nrm_ref = Oracle(*n, bc=bc, gr=1e5, pr=0.71, stretch=S).newton_residual(St)
+    assert rel(F.cpu().numpy(), F_ref) < RTOL
+    assert abs(nrm - nrm_ref) < RTOL * nrm_ref
+
+
+def test_stretched_arnoldi_steps_match_oracle():
+    n, bc, k = (12, 10, 14), synth.AA, 6
+    g, base, x = setup(n, bc, 1e6, 13)
+    o = Oracle(*n, bc=bc, gr=1e6, pr=0.71, stretch=S)
+    v0 = o.project_input(x[0])
+    v0 /= np.linalg.norm(v0)
+    V = torch.zeros((k + 1, 4) + o.shape, dtype=torch.float64, device="cuda")
+    V[0] = dev(v0)
+    Vr = np.zeros((k + 1, 4) + o.shape)
+    Vr[0] = v0
+    for j in range(k):
+        h = g.arnoldi_step(V, j)
+        h_ref = o.arnoldi_step(base, Vr, j)
+        assert np.abs(h - h_ref).max() < 1e-10 * np.abs(h_ref).max(), j
+        Vr[j + 1] = V[j + 1].cpu().numpy()  # feed the oracle the same basis
+    Vm = V.reshape(k + 1, -1)
+    G = (Vm @ Vm.T).cpu().numpy()
+    assert np.abs(G - np.eye(k + 1)).max() < 1e-12
+
+
+def test_stretched_newton_matches_oracle():
+    """Newton's method (Section 2) from the synthetic state at Gr = 1e4 on the stretched 8^3 grid:
+    the same number of corrections and the oracle's steady state."""
+    n, bc = (8, 8, 8), synth.CC
+    kv = kvmod()
+    S0 = np.stack(synth.base_flow(*n, bc, 41))
+    o = Oracle(*n, bc=bc, gr=1e4, pr=0.71, stretch=S)
+    S_ref, info = newton(o, S0, 10, 1e-10, 30, 20, 1e-11, 0.99, 300)
+    g = kv.Grid(*n, bc=bc, gr=1e4, pr=0.71, stretch=S)
+    St = dev(S0)
+    V = torch.empty((31,) + St.shape, dtype=torch.float64, device="cuda")
+    work = torch.empty((10,) + St.shape, dtype=torch.float64, device="cuda")
+    st = g.newton(St, V, work, max_newton=10, tol=1e-10, gmres_m=30, gmres_max_restarts=20, lin_tol=1e-11,
+                  gmres_sat=0.99, bicg_max_iter=300)
+    assert st.converged and info["converged"] and st.iterations == info["iterations"]
+    Sg = St.cpu().numpy()
+    assert rel(Sg, S_ref) < 1e-10
+    _, nrm = o.newton_residual(Sg)
+    assert nrm < 1e-9
+
+
+def test_stretched_grid_restrictions():
+    kv = kvmod()
+    with pytest.raises(kv.KvError):
+        kv.Grid(8, 8, 8, precision=kv.KV_PREC_MIXED, stretch=S)
+    with pytest.raises(kv.KvError):
+        kv.Grid(8, 8, 8, stretch=0.2)
+    g, base, x = setup((6, 6, 6), synth.CC, 1e6, 2)
+    y = dev(x[0])
+    with pytest.raises(kv.KvError):
+        g.krylov_vector_adjoint(y)
+    with pytest.raises(kv.KvError):
+        g.base_flow_gradient(y, y)
+    # the grid stays usable after the refusals
+    assert rel(g.krylov_vector(y).cpu().numpy(),
+               Oracle(6, 6, 6, gr=1e6, pr=0.71, stretch=S).krylov_vector(base, x[0])) < RTOL
