@@ -369,8 +369,9 @@ def timed(fn, reps, warm=1):
 def extras(base_np, x_np, w, kv, synth):
     """The batched forms: a block of 16 right-hand sides at 256^3 replayed from one CUDA graph,
     and a plan of 12 grids {100^3 x4, 128^3 x4, 200^3 x2, 256^3 x2} (Gr in [1e6, 4e6], both
-    spanwise boundary types) evaluated by one graph launch; a 100-step Arnoldi run at 256^3; and
-    Newton's method for a steady state at 64^3. Mixed precision."""
+    spanwise boundary types) evaluated by one graph launch; a 100-step Arnoldi run at 256^3;
+    Newton's method for a steady state at 64^3 (these mixed precision); and one FP64 Krylov vector
+    of the bench workload on the grid stretched by Eq (22)."""
     import numpy as np
     import torch
 
@@ -452,6 +453,17 @@ def extras(base_np, x_np, w, kv, synth):
                        "bicg_rejected": st.bicg_rejected,
                        "res_norms": [float(r) for r in st.res_norm[:st.n_res]]}
     del V, work, S, gq
+    torch.cuda.empty_cache()
+    # the same Krylov vector on the grid stretched by Eq (22) at the steepest a = 0.12 of Section
+    # 3.2 (FP64: per-axis weight tables, numerically computed eigenpairs of Eq (15))
+    g = kv.Grid(w.nx, w.ny, w.nz, bc=w.bc, gr=w.gr, pr=w.pr, precision=kv.KV_PREC_FP64, stretch=0.12)
+    g.set_base_flow(torch.from_numpy(np.stack(base_np)).cuda())
+    x = torch.from_numpy(x_np[0]).cuda()
+    y = g.empty(4)
+    t = timed(lambda: g.krylov_vector(x, y), reps=5)
+    out["stretched_fp64"] = {"workload": f"{w.name} on the grid stretched by Eq (22), a = 0.12; FP64",
+                             "value": 1.0 / t, "unit": UNIT, "ms_per_vector": t * 1e3}
+    del g, x, y
     torch.cuda.empty_cache()
     return out
 
