@@ -87,9 +87,11 @@ typedef struct {
   double stretch;    /* grid stretching of Eq (22), Section 3.2: the faces of every axis sit at
                         x = xi - stretch sin(2 pi xi), xi = t/n; cell centres at the midpoints of
                         their faces. 0 = uniform grid; must be in [0, 1/(2 pi)) so the mapping stays
-                        monotone (the paper uses up to 0.12). Nonzero needs KV_PREC_FP64; the
-                        transpose, the base-flow gradient and kv_krylov_vector_noalloc take the
-                        uniform grid only. */
+                        monotone (the paper uses up to 0.12). Both precisions; a stretched
+                        KV_PREC_MIXED grid stores 12 more coefficient pairs per point (its operator
+                        reads the plus-neighbour coefficients instead of rebuilding them) and
+                        skips the 2.5D-march variant. The transpose, the base-flow gradient and
+                        kv_krylov_vector_noalloc take the uniform grid only. */
 } kv_grid_desc;
 
 typedef struct {

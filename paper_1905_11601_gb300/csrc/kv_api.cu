@@ -211,7 +211,6 @@ kv_status validate(const kv_grid_desc* d, std::string& msg) {
   if (!(d->gr > 0) || !(d->pr > 0) || !isfinite(d->gr) || !isfinite(d->pr)) { msg = "gr and pr must be finite and > 0"; return KV_ERR_ARG; }
   if (d->tol < 0 || d->max_passes < 0 || d->max_passes > 100) { msg = "tol must be >= 0 and max_passes in [0, 100]"; return KV_ERR_ARG; }
   if (!(d->stretch >= 0.0 && d->stretch < 0.15915494309189533)) { msg = "stretch must be in [0, 1/(2 pi))"; return KV_ERR_ARG; }
-  if (d->stretch != 0.0 && d->precision != KV_PREC_FP64) { msg = "a stretched grid needs KV_PREC_FP64"; return KV_ERR_ARG; }
   return KV_OK;
 }
 
@@ -226,6 +225,8 @@ void free_all(kv_grid* h) {
   for (int a = 0; a < 6; ++a) cudaFree(h->Wm[a]);
   for (int a = 0; a < 3; ++a) cudaFree(h->lam[a]);
   cudaFree(h->sw);
+  cudaFree(h->swd);
+  cudaFree(h->coef_dfp);
   cudaFree(h->red);
   cudaFree(h->partials);
   cudaFree(h->hdev);
@@ -370,6 +371,7 @@ kv_status autotune_apply(kv_grid* h) {
     int dv = 0, dbx = 32, dby = 2;
     for (auto& c : dcand) {
       if (c[0] == 1 && 4 * h->P >= (size_t(1) << 31)) continue;  // the march indexes x with 32 bits
+      if (c[0] == 1 && h->str.sw) continue;  // the march rebuilds c+ from c- (uniform grids only)
       h->df_variant = c[0];
       h->df_bx = c[1];
       h->df_by = c[2];
@@ -497,7 +499,7 @@ kv_status kv_create_grid(const kv_grid_desc* desc, void* stream, kv_handle* out)
         return KV_ERR_NOT_CONVERGED;
       }
       h->hmin = fmin(h->hmin, hm);
-      g.swo[a] = (int)tabs.size();
+      h->str.swo[a] = (int)tabs.size();
       tabs.insert(tabs.end(), tab.begin(), tab.end());
     } else {
       neumann_axis(n[a], fwd, inv, lam);
@@ -521,7 +523,39 @@ kv_status kv_create_grid(const kv_grid_desc* desc, void* stream, kv_handle* out)
       return st;
     }
     cudaMemcpy(h->sw, tabs.data(), tabs.size() * sizeof(double), cudaMemcpyHostToDevice);
-    g.sw = h->sw;
+    h->str.sw = h->sw;
+    if (desc->precision == KV_PREC_MIXED) {
+      // the double-float kernels' copy: inverse widths and the Neumann Laplacian's weights as
+      // FP32 pairs (rounded once from FP64)
+      auto pair = [](double x) {
+        const float hi = (float)x;
+        return make_float2(hi, (float)(x - (double)hi));
+      };
+      std::vector<float2> td;
+      for (int a = 0; a < 3; ++a) {
+        const int L = n[a] + 2;
+        const double* tab = tabs.data() + h->str.swo[a];
+        const double* idc = tab + (size_t)KV_SW_IDC * L;
+        const double* idf = tab + (size_t)KV_SW_IDF * L;
+        h->str.swdo[a] = (int)td.size();
+        std::vector<float2> rows((size_t)KV_SWD_N * L, make_float2(0.0f, 0.0f));
+        for (int t = 0; t < L; ++t) {
+          rows[(size_t)KV_SWD_IDC * L + t] = pair(idc[t]);
+          rows[(size_t)KV_SWD_IDF * L + t] = pair(idf[t]);
+          if (t >= 2 && t <= n[a]) rows[(size_t)KV_SWD_LWM * L + t] = pair(idc[t] * idf[t - 1]);
+          if (t >= 1 && t <= n[a] - 1) rows[(size_t)KV_SWD_LWP * L + t] = pair(idc[t] * idf[t]);
+        }
+        td.insert(td.end(), rows.begin(), rows.end());
+      }
+      if ((st = dalloc(h, &h->swd, td.size()))) {
+        g_create_error = h->err;
+        free_all(h);
+        delete h;
+        return st;
+      }
+      cudaMemcpy(h->swd, td.data(), td.size() * sizeof(float2), cudaMemcpyHostToDevice);
+      h->str.swd = h->swd;
+    }
   }
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) {
@@ -582,6 +616,10 @@ kv_status kv_set_base_flow(kv_handle h, const double* base) {
     }
     if (!h->xsplit) {
       kv_status s = dalloc(h, &h->xsplit, 4 * h->P);
+      if (s != KV_OK) return s;
+    }
+    if (h->str.sw && !h->coef_dfp) {
+      kv_status s = dalloc(h, &h->coef_dfp, (size_t)KV_NCOEF_DFP * h->P);
       if (s != KV_OK) return s;
     }
     kv_launch_coef_df(h, h->coef, h->coef_df, h->s);
@@ -843,7 +881,7 @@ kv_status kv_krylov_vector_adjoint(kv_handle h, const double* y, double* z) {
   if (!h->has_base) return fail(h, KV_ERR_STATE, "kv_krylov_vector_adjoint: no base flow set");
   if (h->d.tproj != KV_TPROJ_ORTHOGONAL)
     return fail(h, KV_ERR_ARG, "kv_krylov_vector_adjoint: defined for the orthogonal temperature projection");
-  if (h->g.sw)
+  if (h->str.sw)
     return fail(h, KV_ERR_ARG, "kv_krylov_vector_adjoint: defined on the uniform grid (the velocity projection of a stretched grid is not symmetric)");
   const size_t L = 4 * h->P;
   if (y < z + L && z < y + L) return fail(h, KV_ERR_ARG, "kv_krylov_vector_adjoint: y and z overlap");
@@ -859,7 +897,7 @@ kv_status kv_base_flow_gradient(kv_handle h, const double* x, const double* y, d
   if (!h->has_base) return fail(h, KV_ERR_STATE, "kv_base_flow_gradient: no base flow set");
   if (h->d.tproj != KV_TPROJ_ORTHOGONAL)
     return fail(h, KV_ERR_ARG, "kv_base_flow_gradient: defined for the orthogonal temperature projection");
-  if (h->g.sw)
+  if (h->str.sw)
     return fail(h, KV_ERR_ARG, "kv_base_flow_gradient: defined on the uniform grid (the velocity projection of a stretched grid is not symmetric)");
   kv_status s = project_output_side(h, y);
   if (s != KV_OK) return s;

@@ -28,6 +28,13 @@ constexpr int KV_NCOEF_DF = 25;
 //   C1, C2   first / second derivative weights (minus, centre, plus) at a cell-like node t
 //   F1, F2   the same at a face-like node t = 1..n-1
 enum { KV_SW_IDC = 0, KV_SW_IDF = 1, KV_SW_C1 = 2, KV_SW_C2 = 5, KV_SW_F1 = 8, KV_SW_F2 = 11, KV_SW_N = 14 };
+// The mixed path's copy as FP32 pairs (KV_SWD_N rows of n_a + 2 per axis): IDC and IDF as above,
+// and the Neumann Laplacian's weights towards the lower / upper neighbour of cell t,
+// LWM = IDC_t IDF_{t-1}, LWP = IDC_t IDF_t (0 where the face is a wall).
+enum { KV_SWD_IDC = 0, KV_SWD_IDF = 1, KV_SWD_LWM = 2, KV_SWD_LWP = 3, KV_SWD_N = 4 };
+// Assembled coefficients of the plus neighbours, which a stretched grid's double-float operator
+// reads as well (the uniform one rebuilds them from the minus ones): per equation x+, y+, z+.
+constexpr int KV_NCOEF_DFP = 12;
 
 // Device-side description of the MAC grid.
 struct KvGeom {
@@ -39,8 +46,16 @@ struct KvGeom {
   double nu, kappa; // Gr^-1/2 and (Pr Gr^1/2)^-1 (Eqs (1)-(2) scaling)
   int bc;           // KV_BC_CC / KV_BC_AA
   int tproj;        // KV_TPROJ_*
-  const double* sw = nullptr;  // stretched grid: the KV_SW_* tables (device); nullptr: uniform
-  int swo[3] = {0, 0, 0};      // offset of each axis' tables in sw
+};
+
+// The device tables of a stretched grid (Eq 22); all null on a uniform grid. A separate kernel
+// parameter, passed only to the kernels that read it, so that the uniform kernels' parameters
+// (and their register allocation) are those of a uniform-only build.
+struct KvStretch {
+  const double* sw = nullptr;   // the KV_SW_* tables
+  const float2* swd = nullptr;  // KV_PREC_MIXED: the KV_SWD_* tables
+  int swo[3] = {0, 0, 0};       // offset of each axis' tables in sw
+  int swdo[3] = {0, 0, 0};      // offset of each axis' tables in swd
 };
 
 struct kv_grid {
@@ -61,7 +76,10 @@ struct kv_grid {
   double* tpd_b = nullptr;  // Nc
   double* Wm[6] = {};       // per-axis GEMM operands: forward E_a^-1 (a = 0..2), inverse E_a
   double* lam[3] = {};      // eigenvalues of the 1D Neumann Laplacians (Eq 15)
-  double* sw = nullptr;     // stretched grid: the KV_SW_* weight tables (g.sw points here)
+  KvStretch str;            // stretched grid: views of sw / swd (all null on a uniform grid)
+  double* sw = nullptr;     // stretched grid: the KV_SW_* weight tables
+  float2* swd = nullptr;    // stretched KV_PREC_MIXED grid: the KV_SWD_* tables
+  float2* coef_dfp = nullptr; // stretched KV_PREC_MIXED grid, KV_NCOEF_DFP * P: plus coefficients as pairs
   double hmin = 0.0;        // smallest cell width (the SIMPLE test)
   unsigned long long* red = nullptr;  // [0] max|D v| bits, [1] max|v| bits
   double* partials = nullptr;         // Arnoldi block partial sums

@@ -4,7 +4,8 @@
 //
 //   phi = 0;  r = b   (the divergence writes r's slices; the first sweep stores phi, as FP32)
 //   repeat S times:  phi += TPF(r)   (six tcgen05 contractions, the last one adds into phi)
-//                    r = b - L phi   (7-point Neumann Laplacian in double-float, written as BF16 slices)
+//                    r = b - L phi   (7-point Neumann Laplacian in double-float, written as BF16 slices;
+//                                     per-cell weights on a stretched grid, Eq (22))
 //
 // Each sweep reduces the error by roughly the FP32 accuracy of one tensor-core solve.
 #include <math.h>
@@ -28,8 +29,17 @@ int pad8(int n) { return (n + 7) & ~7; }
 __device__ __forceinline__ DF phi_pair(float x) { return DF{x, 0.0f}; }
 __device__ __forceinline__ DF phi_pair(double x) { return df_split(x); }
 
-template <typename PhiT>
-__global__ void __launch_bounds__(256) k_residual_slices(KvGeom g, const double* __restrict__ b,
+// STR (stretched grid): along each axis L phi = LWP (phi+ - phi) + LWM (phi- - phi) with the
+// KV_SWD_* weights of the cell (a wall neighbour contributes zero flux).
+template <int A>
+__device__ __forceinline__ DF lap_weight(const KvGeom& g, const KvStretch& S, int row, int t) {
+  const int L = (A == 0 ? g.nx : (A == 1 ? g.ny : g.nz)) + 2;
+  const float2 v = __ldg(S.swd + S.swdo[A] + row * L + t);
+  return DF{v.x, v.y};
+}
+
+template <typename PhiT, bool STR>
+__global__ void __launch_bounds__(256) k_residual_slices(KvGeom g, KvStretch S, const double* __restrict__ b,
                                                          const PhiT* __restrict__ phi, __nv_bfloat16* __restrict__ xs,
                                                          size_t slice, int pitch, unsigned long long* rmax,
                                                          float2 ihx2, float2 ihy2, float2 ihz2) {
@@ -47,9 +57,19 @@ __global__ void __launch_bounds__(256) k_residual_slices(KvGeom g, const double*
     const DF xm = phi_pair(i > 0 ? __ldg(phi + e - sx) : cv), xp = phi_pair(i < g.nx - 1 ? __ldg(phi + e + sx) : cv);
     const DF ym = phi_pair(j > 0 ? __ldg(phi + e - sy) : cv), yp = phi_pair(j < g.ny - 1 ? __ldg(phi + e + sy) : cv);
     const DF zm = phi_pair(k > 0 ? __ldg(phi + e - sz) : cv), zp = phi_pair(k < g.nz - 1 ? __ldg(phi + e + sz) : cv);
-    const DF lx = df_mul(df_sub(df_add(xm, xp), c2), DF{ihx2.x, ihx2.y});
-    const DF ly = df_mul(df_sub(df_add(ym, yp), c2), DF{ihy2.x, ihy2.y});
-    const DF lz = df_mul(df_sub(df_add(zm, zp), c2), DF{ihz2.x, ihz2.y});
+    DF lx, ly, lz;
+    if (STR) {  // padded cell index t = compact index + 1
+      lx = df_add(df_mul(df_sub(xp, c), lap_weight<0>(g, S, KV_SWD_LWP, i + 1)),
+                  df_mul(df_sub(xm, c), lap_weight<0>(g, S, KV_SWD_LWM, i + 1)));
+      ly = df_add(df_mul(df_sub(yp, c), lap_weight<1>(g, S, KV_SWD_LWP, j + 1)),
+                  df_mul(df_sub(ym, c), lap_weight<1>(g, S, KV_SWD_LWM, j + 1)));
+      lz = df_add(df_mul(df_sub(zp, c), lap_weight<2>(g, S, KV_SWD_LWP, k + 1)),
+                  df_mul(df_sub(zm, c), lap_weight<2>(g, S, KV_SWD_LWM, k + 1)));
+    } else {
+      lx = df_mul(df_sub(df_add(xm, xp), c2), DF{ihx2.x, ihx2.y});
+      ly = df_mul(df_sub(df_add(ym, yp), c2), DF{ihy2.x, ihy2.y});
+      lz = df_mul(df_sub(df_add(zm, zp), c2), DF{ihz2.x, ihz2.y});
+    }
     const DF r = df_sub(df_split(__ldg(b + e)), df_add(df_add(lx, ly), lz));
     const float rf = __fadd_rn(r.h, r.l);
     rv = fabsf(rf);
@@ -206,10 +226,21 @@ void kv_launch_poisson_mixed(kv_grid* h, const double* b, double* phi, int stats
     if (sweep + 1 < h->refine) {
       KvPhase ph(h, KV_PH_REFINE, 1);
       unsigned long long* rm = stats ? h->rmax : nullptr;
-      if (sweep == 0)
-        k_residual_slices<float><<<rg, rb, 0, s>>>(g, b, h->phi32, h->xs[0], h->xs_slice, pad8(g.nx), rm, cx, cy, cz);
-      else
-        k_residual_slices<double><<<rg, rb, 0, s>>>(g, b, phi, h->xs[0], h->xs_slice, pad8(g.nx), rm, cx, cy, cz);
+      if (sweep == 0) {
+        if (h->str.sw)
+          k_residual_slices<float, true><<<rg, rb, 0, s>>>(g, h->str, b, h->phi32, h->xs[0], h->xs_slice, pad8(g.nx), rm, cx,
+                                                           cy, cz);
+        else
+          k_residual_slices<float, false><<<rg, rb, 0, s>>>(g, h->str, b, h->phi32, h->xs[0], h->xs_slice, pad8(g.nx), rm, cx,
+                                                            cy, cz);
+      } else {
+        if (h->str.sw)
+          k_residual_slices<double, true><<<rg, rb, 0, s>>>(g, h->str, b, phi, h->xs[0], h->xs_slice, pad8(g.nx), rm, cx, cy,
+                                                            cz);
+        else
+          k_residual_slices<double, false><<<rg, rb, 0, s>>>(g, h->str, b, phi, h->xs[0], h->xs_slice, pad8(g.nx), rm, cx, cy,
+                                                             cz);
+      }
     }
   }
 }

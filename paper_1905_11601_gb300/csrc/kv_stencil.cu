@@ -35,8 +35,8 @@ __device__ __forceinline__ W3 d2_cell(int t, int n, double ih2) {
 __device__ __forceinline__ W3 d1_face(double ih) { return {-0.5 * ih, 0.0, 0.5 * ih}; }
 __device__ __forceinline__ W3 d2_face(double ih2) { return {ih2, -2.0 * ih2, ih2}; }
 
-// Weights at padded index t along axis A: the stretched grid's tables (Eq 22) when present,
-// else the uniform formulas above. The branch is uniform across the grid.
+// Weights at padded index t along axis A: the stretched grid's tables (Eq 22) when STR, else the
+// uniform formulas above.
 template <int A>
 __device__ __forceinline__ int ax_n(const KvGeom& g) {
   return A == 0 ? g.nx : (A == 1 ? g.ny : g.nz);
@@ -47,29 +47,29 @@ __device__ __forceinline__ double ax_ih(const KvGeom& g) {
 }
 template <int A>
 __device__ __forceinline__ double ax_ih2(const KvGeom& g) {
-  return A == 0 ? g.ihx2 : (A == 1 ? g.ihy2 : g.ihz2);
+  return ax_ih<A>(g) * ax_ih<A>(g);  // as the host's ihx2 etc.; formed here it keeps k_stencil unspilled
 }
 template <int A>
-__device__ __forceinline__ W3 sw3(const KvGeom& g, int row, int t) {
+__device__ __forceinline__ W3 sw3(const KvGeom& g, const KvStretch& S, int row, int t) {
   const int L = ax_n<A>(g) + 2;
-  const double* p = g.sw + g.swo[A] + row * L + t;
+  const double* p = S.sw + S.swo[A] + row * L + t;
   return {__ldg(p), __ldg(p + L), __ldg(p + 2 * L)};
 }
-template <int A>
-__device__ __forceinline__ W3 wc1(const KvGeom& g, int t) {
-  return g.sw ? sw3<A>(g, KV_SW_C1, t) : d1_cell(t, ax_n<A>(g), ax_ih<A>(g));
+template <int A, bool STR>
+__device__ __forceinline__ W3 wc1(const KvGeom& g, const KvStretch& S, int t) {
+  return STR ? sw3<A>(g, S, KV_SW_C1, t) : d1_cell(t, ax_n<A>(g), ax_ih<A>(g));
 }
-template <int A>
-__device__ __forceinline__ W3 wc2(const KvGeom& g, int t) {
-  return g.sw ? sw3<A>(g, KV_SW_C2, t) : d2_cell(t, ax_n<A>(g), ax_ih2<A>(g));
+template <int A, bool STR>
+__device__ __forceinline__ W3 wc2(const KvGeom& g, const KvStretch& S, int t) {
+  return STR ? sw3<A>(g, S, KV_SW_C2, t) : d2_cell(t, ax_n<A>(g), ax_ih2<A>(g));
 }
-template <int A>
-__device__ __forceinline__ W3 wf1(const KvGeom& g, int t) {
-  return g.sw ? sw3<A>(g, KV_SW_F1, t) : d1_face(ax_ih<A>(g));
+template <int A, bool STR>
+__device__ __forceinline__ W3 wf1(const KvGeom& g, const KvStretch& S, int t) {
+  return STR ? sw3<A>(g, S, KV_SW_F1, t) : d1_face(ax_ih<A>(g));
 }
-template <int A>
-__device__ __forceinline__ W3 wf2(const KvGeom& g, int t) {
-  return g.sw ? sw3<A>(g, KV_SW_F2, t) : d2_face(ax_ih2<A>(g));
+template <int A, bool STR>
+__device__ __forceinline__ W3 wf2(const KvGeom& g, const KvStretch& S, int t) {
+  return STR ? sw3<A>(g, S, KV_SW_F2, t) : d2_face(ax_ih2<A>(g));
 }
 
 __device__ __forceinline__ double ap(const W3& w, double fm, double f0, double fp) {
@@ -136,8 +136,8 @@ struct Loader {
 };
 
 // MODE 0: J P_BC x with (U, Theta) = base. MODE 1: steady residual F(S), S = base = x.
-template <int MODE>
-__global__ void __launch_bounds__(256) k_stencil(KvGeom g, const double* __restrict__ base,
+template <int MODE, bool STR>
+__global__ void __launch_bounds__(256) k_stencil(KvGeom g, KvStretch S, const double* __restrict__ base,
                                                  const double* __restrict__ x, size_t P,
                                                  double* __restrict__ vstar, double* __restrict__ tout) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -154,9 +154,9 @@ __global__ void __launch_bounds__(256) k_stencil(KvGeom g, const double* __restr
   // ---- u on the x-face (i, j, k) ----
   double ru = 0.0;
   if (G.dof_u(i, j, k)) {
-    const W3 dx1 = wf1<0>(g, i), dx2 = wf2<0>(g, i);
-    const W3 dy1 = wc1<1>(g, j), dy2 = wc2<1>(g, j);
-    const W3 dz1 = wc1<2>(g, k), dz2 = wc2<2>(g, k);
+    const W3 dx1 = wf1<0, STR>(g, S, i), dx2 = wf2<0, STR>(g, S, i);
+    const W3 dy1 = wc1<1, STR>(g, S, j), dy2 = wc2<1, STR>(g, S, j);
+    const W3 dz1 = wc1<2, STR>(g, S, k), dz2 = wc2<2, STR>(g, S, k);
     const double c = Xl.lu(i, j, k);
     const double xm = Xl.lu(i - 1, j, k), xp = Xl.lu(i + 1, j, k);
     const double ym = Xl.lu(i, j - 1, k), yp = Xl.lu(i, j + 1, k);
@@ -181,9 +181,9 @@ __global__ void __launch_bounds__(256) k_stencil(KvGeom g, const double* __restr
   // ---- v on the y-face (i, j, k) ----
   double rv = 0.0;
   if (G.dof_v(i, j, k)) {
-    const W3 dx1 = wc1<0>(g, i), dx2 = wc2<0>(g, i);
-    const W3 dy1 = wf1<1>(g, j), dy2 = wf2<1>(g, j);
-    const W3 dz1 = wc1<2>(g, k), dz2 = wc2<2>(g, k);
+    const W3 dx1 = wc1<0, STR>(g, S, i), dx2 = wc2<0, STR>(g, S, i);
+    const W3 dy1 = wf1<1, STR>(g, S, j), dy2 = wf2<1, STR>(g, S, j);
+    const W3 dz1 = wc1<2, STR>(g, S, k), dz2 = wc2<2, STR>(g, S, k);
     const double c = Xl.lv(i, j, k);
     const double xm = Xl.lv(i - 1, j, k), xp = Xl.lv(i + 1, j, k);
     const double ym = Xl.lv(i, j - 1, k), yp = Xl.lv(i, j + 1, k);
@@ -208,9 +208,9 @@ __global__ void __launch_bounds__(256) k_stencil(KvGeom g, const double* __restr
   // ---- w on the z-face (i, j, k), with the buoyancy term T e_z ----
   double rw = 0.0;
   if (G.dof_w(i, j, k)) {
-    const W3 dx1 = wc1<0>(g, i), dx2 = wc2<0>(g, i);
-    const W3 dy1 = wc1<1>(g, j), dy2 = wc2<1>(g, j);
-    const W3 dz1 = wf1<2>(g, k), dz2 = wf2<2>(g, k);
+    const W3 dx1 = wc1<0, STR>(g, S, i), dx2 = wc2<0, STR>(g, S, i);
+    const W3 dy1 = wc1<1, STR>(g, S, j), dy2 = wc2<1, STR>(g, S, j);
+    const W3 dz1 = wf1<2, STR>(g, S, k), dz2 = wf2<2, STR>(g, S, k);
     const double c = Xl.lw(i, j, k);
     const double xm = Xl.lw(i - 1, j, k), xp = Xl.lw(i + 1, j, k);
     const double ym = Xl.lw(i, j - 1, k), yp = Xl.lw(i, j + 1, k);
@@ -238,9 +238,9 @@ __global__ void __launch_bounds__(256) k_stencil(KvGeom g, const double* __restr
   // ---- T at the cell (i, j, k), then the temperature projection of Eq (21) ----
   const bool cell = i >= 1 && i <= g.nx && j >= 1 && j <= g.ny && k >= 1 && k <= g.nz;
   if (cell) {
-    const W3 dx1 = wc1<0>(g, i), dx2 = wc2<0>(g, i);
-    const W3 dy1 = wc1<1>(g, j), dy2 = wc2<1>(g, j);
-    const W3 dz1 = wc1<2>(g, k), dz2 = wc2<2>(g, k);
+    const W3 dx1 = wc1<0, STR>(g, S, i), dx2 = wc2<0, STR>(g, S, i);
+    const W3 dy1 = wc1<1, STR>(g, S, j), dy2 = wc2<1, STR>(g, S, j);
+    const W3 dz1 = wc1<2, STR>(g, S, k), dz2 = wc2<2, STR>(g, S, k);
     const double c = Xl.lT(i, j, k);
     const double xm = Xl.lT(i - 1, j, k), xp = Xl.lT(i + 1, j, k);
     const double ym = Xl.lT(i, j - 1, k), yp = Xl.lT(i, j + 1, k);
@@ -288,7 +288,8 @@ __global__ void __launch_bounds__(256) k_stencil(KvGeom g, const double* __restr
 //   v-face  q = 9..15, 16 (sum of u), 17 (sum of w)
 //   w-face  q = 18..24, 25 (sum of u), 26 (sum of v); plus 0.5 (T_k + T_k+1) buoyancy
 //   T-cell  q = 27..33, 34, 35, 36 (factors of the 2-point sums of u, v, w)
-__global__ void __launch_bounds__(256) k_assemble(KvGeom g, const double* __restrict__ base, size_t P,
+template <bool STR>
+__global__ void __launch_bounds__(256) k_assemble(KvGeom g, KvStretch S, const double* __restrict__ base, size_t P,
                                                   double* __restrict__ coef) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   const int j = blockIdx.y * blockDim.y + threadIdx.y;
@@ -312,9 +313,9 @@ __global__ void __launch_bounds__(256) k_assemble(KvGeom g, const double* __rest
     o[0] = diff * (x2.c + y2.c + z2.c) - (ax * x1.c + ay * y1.c + az * z1.c) - gself;
   };
   if (G.dof_u(i, j, k)) {
-    const W3 dx1 = wf1<0>(g, i), dx2 = wf2<0>(g, i);
-    const W3 dy1 = wc1<1>(g, j), dy2 = wc2<1>(g, j);
-    const W3 dz1 = wc1<2>(g, k), dz2 = wc2<2>(g, k);
+    const W3 dx1 = wf1<0, STR>(g, S, i), dx2 = wf2<0, STR>(g, S, i);
+    const W3 dy1 = wc1<1, STR>(g, S, j), dy2 = wc2<1, STR>(g, S, j);
+    const W3 dz1 = wc1<2, STR>(g, S, k), dz2 = wc2<2, STR>(g, S, k);
     const double Ua = B.lu(i, j, k);
     const double Va = 0.25 * (B.lv(i, j - 1, k) + B.lv(i, j, k) + B.lv(i + 1, j - 1, k) + B.lv(i + 1, j, k));
     const double Wa = 0.25 * (B.lw(i, j, k - 1) + B.lw(i, j, k) + B.lw(i + 1, j, k - 1) + B.lw(i + 1, j, k));
@@ -326,9 +327,9 @@ __global__ void __launch_bounds__(256) k_assemble(KvGeom g, const double* __rest
     c[8] = -0.25 * gz;
   }
   if (G.dof_v(i, j, k)) {
-    const W3 dx1 = wc1<0>(g, i), dx2 = wc2<0>(g, i);
-    const W3 dy1 = wf1<1>(g, j), dy2 = wf2<1>(g, j);
-    const W3 dz1 = wc1<2>(g, k), dz2 = wc2<2>(g, k);
+    const W3 dx1 = wc1<0, STR>(g, S, i), dx2 = wc2<0, STR>(g, S, i);
+    const W3 dy1 = wf1<1, STR>(g, S, j), dy2 = wf2<1, STR>(g, S, j);
+    const W3 dz1 = wc1<2, STR>(g, S, k), dz2 = wc2<2, STR>(g, S, k);
     const double Ua = 0.25 * (B.lu(i - 1, j, k) + B.lu(i, j, k) + B.lu(i - 1, j + 1, k) + B.lu(i, j + 1, k));
     const double Va = B.lv(i, j, k);
     const double Wa = 0.25 * (B.lw(i, j, k - 1) + B.lw(i, j, k) + B.lw(i, j + 1, k - 1) + B.lw(i, j + 1, k));
@@ -340,9 +341,9 @@ __global__ void __launch_bounds__(256) k_assemble(KvGeom g, const double* __rest
     c[17] = -0.25 * gz;
   }
   if (G.dof_w(i, j, k)) {
-    const W3 dx1 = wc1<0>(g, i), dx2 = wc2<0>(g, i);
-    const W3 dy1 = wc1<1>(g, j), dy2 = wc2<1>(g, j);
-    const W3 dz1 = wf1<2>(g, k), dz2 = wf2<2>(g, k);
+    const W3 dx1 = wc1<0, STR>(g, S, i), dx2 = wc2<0, STR>(g, S, i);
+    const W3 dy1 = wc1<1, STR>(g, S, j), dy2 = wc2<1, STR>(g, S, j);
+    const W3 dz1 = wf1<2, STR>(g, S, k), dz2 = wf2<2, STR>(g, S, k);
     const double Ua = 0.25 * (B.lu(i - 1, j, k) + B.lu(i, j, k) + B.lu(i - 1, j, k + 1) + B.lu(i, j, k + 1));
     const double Va = 0.25 * (B.lv(i, j - 1, k) + B.lv(i, j, k) + B.lv(i, j - 1, k + 1) + B.lv(i, j, k + 1));
     const double Wa = B.lw(i, j, k);
@@ -354,9 +355,9 @@ __global__ void __launch_bounds__(256) k_assemble(KvGeom g, const double* __rest
     c[26] = -0.25 * gy;
   }
   if (i >= 1 && i <= g.nx && j >= 1 && j <= g.ny && k >= 1 && k <= g.nz) {
-    const W3 dx1 = wc1<0>(g, i), dx2 = wc2<0>(g, i);
-    const W3 dy1 = wc1<1>(g, j), dy2 = wc2<1>(g, j);
-    const W3 dz1 = wc1<2>(g, k), dz2 = wc2<2>(g, k);
+    const W3 dx1 = wc1<0, STR>(g, S, i), dx2 = wc2<0, STR>(g, S, i);
+    const W3 dy1 = wc1<1, STR>(g, S, j), dy2 = wc2<1, STR>(g, S, j);
+    const W3 dz1 = wc1<2, STR>(g, S, k), dz2 = wc2<2, STR>(g, S, k);
     const double Ua = 0.5 * (B.lu(i - 1, j, k) + B.lu(i, j, k));
     const double Va = 0.5 * (B.lv(i, j - 1, k) + B.lv(i, j, k));
     const double Wa = 0.5 * (B.lw(i, j, k - 1) + B.lw(i, j, k));
@@ -377,7 +378,7 @@ __device__ __forceinline__ double cf(const double* __restrict__ coef, size_t P, 
   return __ldg(coef + (size_t)q * P + e);
 }
 
-// y* = J P_BC x with the assembled coefficients; output as k_stencil<0>.
+// y* = J P_BC x with the assembled coefficients; output as k_stencil<0, STR>.
 __global__ void __launch_bounds__(256) k_apply(KvGeom g, const double* __restrict__ coef,
                                                const double* __restrict__ x, size_t P, double* __restrict__ vstar,
                                                double* __restrict__ tout) {
@@ -507,15 +508,22 @@ __device__ __forceinline__ DF sum4(const DF a, const DF b, const DF c, const DF 
 __constant__ int kDfFromFull[KV_NCOEF_DF] = {0,  1,  3,  5,  7,  8,  9,  10, 12, 14, 16, 17, 18,
                                              19, 21, 23, 25, 26, 27, 28, 30, 32, 34, 35, 36};
 
+// Assembled coefficient of each plus neighbour (x+, y+, z+ of u, v, w, T), which the operator of a
+// stretched grid reads directly: there beta is not a power of two, so c+ is not rebuilt from c-.
+__constant__ int kPlusFromFull[KV_NCOEF_DFP] = {2, 4, 6, 11, 13, 15, 20, 22, 24, 29, 31, 33};
+
 // y* = J P_BC x with the FP32-pair coefficients and the split projected input xs (output as
-// k_apply). One thread per (cell, equation): threadIdx.y = 4 row + eq, eq = 0..3 for u, v, w,
+// k_apply). STR (stretched grid): the plus coefficients come from cplus (KV_NCOEF_DFP pairs per
+// point) instead of alpha + beta c-. One thread per (cell, equation): threadIdx.y = 4 row + eq, eq = 0..3 for u, v, w,
 // T, so each warp forms one equation for consecutive cells (no divergence) and keeps only that
 // equation's inputs (15-17 pairs) and coefficients (6-7 pairs) live; the inputs shared between
 // equations come from L1. Cells are 1 <= i <= nx, ... (every input they read is inside the
 // padded array, projected); outputs that are not unknowns at a position are written as 0.
+template <bool STR>
 __global__ void __launch_bounds__(512) k_apply_df(KvGeom g, const float2* __restrict__ coef,
-                                                  const float2* __restrict__ xs, size_t P,
-                                                  double* __restrict__ vstar, double* __restrict__ tout, DfAlpha al) {
+                                                  const float2* __restrict__ cplus, const float2* __restrict__ xs,
+                                                  size_t P, double* __restrict__ vstar, double* __restrict__ tout,
+                                                  DfAlpha al) {
   const int eq = threadIdx.y & 3;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   const int j = blockIdx.y * (blockDim.y >> 2) + (threadIdx.y >> 2);
@@ -546,12 +554,22 @@ __global__ void __launch_bounds__(512) k_apply_df(KvGeom g, const float2* __rest
   // wall classes of this cell along the cell-type axes
   const int ci = wall_class(i, g.nx), cj = wall_class(j, g.ny), ck = wall_class(k, g.nz);
   DFAcc a;
+  // c- x- + c+ x+ along one axis; q = the plus coefficient's index in cplus
+  auto own_axis = [&](DFAcc& acc, const float2 cm, const DF xm, const DF xp, const float2 alpha, const float beta,
+                      int q) {
+    if (STR) {
+      acc.fma(cm, xm);
+      acc.fma(__ldg(cplus + (size_t)q * P + e), xp);
+    } else {
+      ::own_axis(acc, cm, xm, xp, alpha, beta);
+    }
+  };
   if (eq == 0) {  // u on x-faces (x is the face axis); cross terms: 4-point sums of v and w
     const float2 c0 = C(0), cx = C(1), cy = C(2), cz = C(3), c7 = C(4), c8 = C(5);
     a.fma(c0, L(xu, 0));
-    own_axis(a, cx, L(xu, -sx), L(xu, sx), alpha_of(al, 0, 0, 0), -1.0f);
-    own_axis(a, cy, L(xu, -sy), L(xu, sy), alpha_of(al, 0, 1, cj), beta_of(cj));
-    own_axis(a, cz, L(xu, -sz), L(xu, sz), alpha_of(al, 0, 2, ck), beta_of(ck));
+    own_axis(a, cx, L(xu, -sx), L(xu, sx), alpha_of(al, 0, 0, 0), -1.0f, 0);
+    own_axis(a, cy, L(xu, -sy), L(xu, sy), alpha_of(al, 0, 1, cj), beta_of(cj), 1);
+    own_axis(a, cz, L(xu, -sz), L(xu, sz), alpha_of(al, 0, 2, ck), beta_of(ck), 2);
     // v(i, j-1), v(i, j), v(i+1, j-1), v(i+1, j); w(i, k-1), w(i, k), w(i+1, k-1), w(i+1, k)
     a.fma(c7, sum4(L(xv, -sy), L(xv, 0), L(xv, sx - sy), L(xv, sx)));
     a.fma(c8, sum4(L(xw, -sz), L(xw, 0), L(xw, sx - sz), L(xw, sx)));
@@ -559,9 +577,9 @@ __global__ void __launch_bounds__(512) k_apply_df(KvGeom g, const float2* __rest
   } else if (eq == 1) {  // v on y-faces
     const float2 c0 = C(6), cx = C(7), cy = C(8), cz = C(9), c16 = C(10), c17 = C(11);
     a.fma(c0, L(xv, 0));
-    own_axis(a, cx, L(xv, -sx), L(xv, sx), alpha_of(al, 0, 0, ci), beta_of(ci));
-    own_axis(a, cy, L(xv, -sy), L(xv, sy), alpha_of(al, 0, 1, 0), -1.0f);
-    own_axis(a, cz, L(xv, -sz), L(xv, sz), alpha_of(al, 0, 2, ck), beta_of(ck));
+    own_axis(a, cx, L(xv, -sx), L(xv, sx), alpha_of(al, 0, 0, ci), beta_of(ci), 3);
+    own_axis(a, cy, L(xv, -sy), L(xv, sy), alpha_of(al, 0, 1, 0), -1.0f, 4);
+    own_axis(a, cz, L(xv, -sz), L(xv, sz), alpha_of(al, 0, 2, ck), beta_of(ck), 5);
     // u(i-1, j), u(i, j), u(i-1, j+1), u(i, j+1); w(j, k-1), w(j, k), w(j+1, k-1), w(j+1, k)
     a.fma(c16, sum4(L(xu, -sx), L(xu, 0), L(xu, -sx + sy), L(xu, sy)));
     a.fma(c17, sum4(L(xw, -sz), L(xw, 0), L(xw, sy - sz), L(xw, sy)));
@@ -569,9 +587,9 @@ __global__ void __launch_bounds__(512) k_apply_df(KvGeom g, const float2* __rest
   } else if (eq == 2) {  // w on z-faces, with the buoyancy 0.5 (T_k + T_k+1)
     const float2 c0 = C(12), cx = C(13), cy = C(14), cz = C(15), c25 = C(16), c26 = C(17);
     a.fma(c0, L(xw, 0));
-    own_axis(a, cx, L(xw, -sx), L(xw, sx), alpha_of(al, 0, 0, ci), beta_of(ci));
-    own_axis(a, cy, L(xw, -sy), L(xw, sy), alpha_of(al, 0, 1, cj), beta_of(cj));
-    own_axis(a, cz, L(xw, -sz), L(xw, sz), alpha_of(al, 0, 2, 0), -1.0f);
+    own_axis(a, cx, L(xw, -sx), L(xw, sx), alpha_of(al, 0, 0, ci), beta_of(ci), 6);
+    own_axis(a, cy, L(xw, -sy), L(xw, sy), alpha_of(al, 0, 1, cj), beta_of(cj), 7);
+    own_axis(a, cz, L(xw, -sz), L(xw, sz), alpha_of(al, 0, 2, 0), -1.0f, 8);
     // u(i-1, k), u(i, k), u(i-1, k+1), u(i, k+1); v(j-1, k), v(j, k), v(j-1, k+1), v(j, k+1)
     a.fma(c25, sum4(L(xu, -sx), L(xu, 0), L(xu, -sx + sz), L(xu, sz)));
     a.fma(c26, sum4(L(xv, -sy), L(xv, 0), L(xv, -sy + sz), L(xv, sz)));
@@ -580,9 +598,9 @@ __global__ void __launch_bounds__(512) k_apply_df(KvGeom g, const float2* __rest
   } else {  // T on cells
     const float2 c0 = C(18), cx = C(19), cy = C(20), cz = C(21), c34 = C(22), c35 = C(23), c36 = C(24);
     a.fma(c0, L(xT, 0));
-    own_axis(a, cx, L(xT, -sx), L(xT, sx), alpha_of(al, 1, 0, ci), beta_of(ci));
-    own_axis(a, cy, L(xT, -sy), L(xT, sy), alpha_of(al, 1, 1, cj), beta_of(cj));
-    own_axis(a, cz, L(xT, -sz), L(xT, sz), alpha_of(al, 1, 2, ck), beta_of(ck));
+    own_axis(a, cx, L(xT, -sx), L(xT, sx), alpha_of(al, 1, 0, ci), beta_of(ci), 9);
+    own_axis(a, cy, L(xT, -sy), L(xT, sy), alpha_of(al, 1, 1, cj), beta_of(cj), 10);
+    own_axis(a, cz, L(xT, -sz), L(xT, sz), alpha_of(al, 1, 2, ck), beta_of(ck), 11);
     a.fma(c34, df_add_lazy(L(xu, -sx), L(xu, 0)));
     a.fma(c35, df_add_lazy(L(xv, -sy), L(xv, 0)));
     a.fma(c36, df_add_lazy(L(xw, -sz), L(xw, 0)));
@@ -830,6 +848,18 @@ __global__ void __launch_bounds__(256) k_coef_df(const double* __restrict__ coef
   }
 }
 
+// The plus coefficients of a stretched grid as FP32 pairs (KV_NCOEF_DFP of them).
+__global__ void __launch_bounds__(256) k_coef_df_plus(const double* __restrict__ coef, float2* __restrict__ cdf,
+                                                      size_t P) {
+  const size_t n = (size_t)KV_NCOEF_DFP * P;
+  for (size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += (size_t)gridDim.x * blockDim.x) {
+    const size_t q = t / P, e = t - q * P;
+    const double c = coef[(size_t)kPlusFromFull[q] * P + e];
+    const float h = __double2float_rn(c);
+    cdf[t] = make_float2(h, __double2float_rn(c - (double)h));
+  }
+}
+
 // x as an FP32 pair (host side)
 float2 host_pair(double x) {
   const float h = (float)x;
@@ -843,16 +873,24 @@ void kv_launch_stencil(const kv_grid* h, int mode, const double* base, const dou
   const KvGeom& g = h->g;
   dim3 block(32, 8, 1);
   dim3 grid((g.X + 31) / 32, (g.Y + 7) / 8, g.Z);
-  if (mode == 0)
-    k_stencil<0><<<grid, block, 0, s>>>(g, base, x, h->P, vstar, tout);
+  const bool str = h->str.sw != nullptr;
+  if (mode == 0 && str)
+    k_stencil<0, true><<<grid, block, 0, s>>>(g, h->str, base, x, h->P, vstar, tout);
+  else if (mode == 0)
+    k_stencil<0, false><<<grid, block, 0, s>>>(g, h->str, base, x, h->P, vstar, tout);
+  else if (str)
+    k_stencil<1, true><<<grid, block, 0, s>>>(g, h->str, base, x, h->P, vstar, tout);
   else
-    k_stencil<1><<<grid, block, 0, s>>>(g, base, x, h->P, vstar, tout);
+    k_stencil<1, false><<<grid, block, 0, s>>>(g, h->str, base, x, h->P, vstar, tout);
 }
 
 void kv_launch_assemble(const kv_grid* h, const double* base, double* coef, cudaStream_t s) {
   const KvGeom& g = h->g;
   dim3 block(32, 8, 1), grid((g.X + 31) / 32, (g.Y + 7) / 8, g.Z);
-  k_assemble<<<grid, block, 0, s>>>(g, base, h->P, coef);
+  if (h->str.sw)
+    k_assemble<true><<<grid, block, 0, s>>>(g, h->str, base, h->P, coef);
+  else
+    k_assemble<false><<<grid, block, 0, s>>>(g, h->str, base, h->P, coef);
 }
 
 void kv_launch_apply(const kv_grid* h, const double* coef, const double* x, double* vstar, double* tout,
@@ -865,6 +903,7 @@ void kv_launch_apply(const kv_grid* h, const double* coef, const double* x, doub
 
 void kv_launch_coef_df(const kv_grid* h, const double* coef, float2* cdf, cudaStream_t s) {
   k_coef_df<<<4 * 152, 256, 0, s>>>(coef, cdf, h->P);
+  if (h->str.sw) k_coef_df_plus<<<4 * 152, 256, 0, s>>>(coef, h->coef_dfp, h->P);
 }
 
 void kv_launch_apply_df(const kv_grid* h, const float2* cdf, const double* x, double* vstar, double* tout,
@@ -877,7 +916,7 @@ void kv_launch_apply_df(const kv_grid* h, const float2* cdf, const double* x, do
   for (int d = 0; d < 2; ++d)
     for (int ax = 0; ax < 3; ++ax)
       for (int c = 0; c < 3; ++c) al.a[d][ax][c] = host_pair(fac[c] * diff[d] * ih2[ax]);
-  if (h->df_variant == 1) {
+  if (h->df_variant == 1 && !h->str.sw) {
     // the 2.5D march: df_by planes per block
     k_zero_boundary<<<2 * 152, 256, 0, s>>>(g, h->P, vstar, tout);
     const int kc = h->df_by;
@@ -892,5 +931,8 @@ void kv_launch_apply_df(const kv_grid* h, const float2* cdf, const double* x, do
   // df_by rows of cells per block, four equation warps-rows each
   const int bx = h->df_bx, rows = h->df_by;
   dim3 block(bx, 4 * rows, 1), grid((g.X + bx - 1) / bx, (g.Y + rows - 1) / rows, g.Z);
-  k_apply_df<<<grid, block, 0, s>>>(g, cdf, h->xsplit, h->P, vstar, tout, al);
+  if (h->str.sw)
+    k_apply_df<true><<<grid, block, 0, s>>>(g, cdf, h->coef_dfp, h->xsplit, h->P, vstar, tout, al);
+  else
+    k_apply_df<false><<<grid, block, 0, s>>>(g, cdf, nullptr, h->xsplit, h->P, vstar, tout, al);
 }

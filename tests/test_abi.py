@@ -47,8 +47,7 @@ def _desc(**kw):
 @pytest.mark.parametrize("bad", [dict(nx=1), dict(nz=2000), dict(spanwise_bc=3), dict(tproj=7),
                                  dict(precision=9), dict(gr=-1.0), dict(pr=0.0), dict(max_passes=-1),
                                  dict(gr=float("nan")), dict(refine_sweeps=-1), dict(refine_sweeps=99), dict(cgs_passes=1),
-                                 dict(stretch=-0.01), dict(stretch=0.16), dict(stretch=float("nan")),
-                                 dict(stretch=0.12, precision=1)])
+                                 dict(stretch=-0.01), dict(stretch=0.16), dict(stretch=float("nan"))])
 def test_invalid_descriptor_rejected_on_host(lib, bad):
     h = ctypes.c_void_p()
     st = lib.kv_create_grid(ctypes.byref(_desc(**bad)), None, ctypes.byref(h))
