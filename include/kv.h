@@ -332,8 +332,27 @@ kv_status kv_krylov_vector_noalloc(const kv_grid_desc* desc, const double* base,
    involved; the grid stays usable. Synchronises the stream. */
 kv_status kv_selftest_wait_timeout(kv_handle h, int* device_error);
 
-/* Message of the last failed call on h (NULL h: last failed kv_create_grid or
-   kv_krylov_vector_noalloc on this thread). */
+/* Host only (no device call): the per-axis data kv_create_grid builds for one axis of n cells
+   (2 <= n <= 1024) with the Eq (22) stretching parameter `stretch` (as in kv_grid_desc).
+   Eq (15) for the pressure-correction Laplacian D G with homogeneous Neumann walls:
+     E      n x n, row-major, row = cell, column = mode (eigenvectors), nullable;
+     E_inv  n x n, row-major, row = mode, column = cell, nullable;
+     lambda n eigenvalues, mode 0 the constants (exactly 0), then decreasing, nullable.
+   Closed form on the uniform grid (stretch = 0), the tridiagonal QL iteration otherwise.
+   weights (nullable): 14 rows of n + 2 doubles, indexed by the padded index t along the axis,
+   row-major, zero outside each row's range:
+     0      1 / cell width (cells t = 1..n)
+     1      1 / distance between the centres of cells t and t+1 (faces t = 1..n-1)
+     2..4   first-derivative weights (t-1, t, t+1) at a cell-like node t = 1..n
+     5..7   second-derivative (flux form) weights at a cell-like node
+     8..10  first-derivative weights at a face-like node t = 1..n-1
+     11..13 second-derivative weights at a face-like node
+   All buffers are the caller's host memory. KV_ERR_ARG for a bad n or stretch,
+   KV_ERR_NOT_CONVERGED if the eigensolver fails (message via kv_last_error(NULL)). */
+kv_status kv_axis_data(int n, double stretch, double* E, double* E_inv, double* lambda, double* weights);
+
+/* Message of the last failed call on h (NULL h: last failed kv_create_grid,
+   kv_krylov_vector_noalloc or kv_axis_data on this thread). */
 const char* kv_last_error(kv_handle h);
 
 #ifdef __cplusplus

@@ -129,7 +129,7 @@ bool tridiag_ql(int n, std::vector<double>& d, std::vector<double>& e, std::vect
 // E^-1 = Q^T dx^1/2. Modes sorted by decreasing eigenvalue; mode 0 (the constants) has
 // eigenvalue exactly 0. Layout of fwd / inv as in neumann_axis.
 bool stretched_axis(int n, double sp, std::vector<double>& tab, std::vector<double>& fwd, std::vector<double>& inv,
-                    std::vector<double>& lam, double& hmin) {
+                    std::vector<double>& lam, double& hmin, bool want_eigen = true) {
   const int L = n + 2;
   const double two_pi = 6.283185307179586476925286766559;
   std::vector<double> xf(n + 1), xc(n + 2), dx(n + 2, 0.0), gap(n + 2, 0.0);
@@ -170,6 +170,7 @@ bool stretched_axis(int n, double sp, std::vector<double>& tab, std::vector<doub
     put(KV_SW_F1, KV_SW_F2, t, xf[t - 1], xf[t], xf[t + 1], gap[t]);
   }
 
+  if (!want_eigen) return true;
   // S on cells c = 0..n-1 (cell t = c + 1)
   std::vector<double> d(n, 0.0), e(n, 0.0), Q;
   for (int c = 0; c < n; ++c) {
@@ -977,6 +978,28 @@ kv_status kv_selftest_wait_timeout(kv_handle h, int* device_error) {
   if (!h || !device_error) return KV_ERR_ARG;
   if (h->d.precision != KV_PREC_MIXED) return fail(h, KV_ERR_ARG, "kv_selftest_wait_timeout: needs a mixed grid");
   return kv_mixed_selftest_timeout(h, device_error);
+}
+
+kv_status kv_axis_data(int n, double stretch, double* E, double* E_inv, double* lambda, double* weights) {
+  if (n < 2 || n > 1024 || !(stretch >= 0.0 && stretch < 0.15915494309189533)) {
+    g_create_error = "kv_axis_data: n must be in [2, 1024] and stretch in [0, 1/(2 pi))";
+    return KV_ERR_ARG;
+  }
+  std::vector<double> fwd, inv, lam, tab;
+  double hm = 0.0;
+  // the tables by the stretched formulas (at stretch = 0 they are the uniform grid's weights)
+  if (!stretched_axis(n, stretch, tab, fwd, inv, lam, hm, stretch != 0.0)) {
+    g_create_error = "kv_axis_data: the tridiagonal eigensolver did not converge";
+    return KV_ERR_NOT_CONVERGED;
+  }
+  if (stretch == 0.0) neumann_axis(n, fwd, inv, lam);  // the closed form kv_create_grid uses
+  const size_t nn = (size_t)n * n;
+  // fwd: row = mode, column = cell (E^-1); inv: row = cell, column = mode (E)
+  if (E) memcpy(E, inv.data(), nn * sizeof(double));
+  if (E_inv) memcpy(E_inv, fwd.data(), nn * sizeof(double));
+  if (lambda) memcpy(lambda, lam.data(), (size_t)n * sizeof(double));
+  if (weights) memcpy(weights, tab.data(), tab.size() * sizeof(double));
+  return KV_OK;
 }
 
 const char* kv_last_error(kv_handle h) {

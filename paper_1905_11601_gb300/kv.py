@@ -27,9 +27,23 @@ EXPORTS = ("kv_create_grid", "kv_destroy_grid", "kv_set_stream", "kv_field_len",
            "kv_profile_enable", "kv_profile_get", "kv_krylov_vector_noalloc", "kv_krylov_vector_adjoint",
            "kv_base_flow_gradient", "kv_krylov_vector_batch", "kv_plan_create", "kv_plan_add", "kv_plan_launch",
            "kv_plan_destroy", "kv_plan_last_error", "kv_selftest_wait_timeout", "kv_tuning",
-           "kv_krylov_vector_host_stream", "kv_gmres", "kv_bicgstab2", "kv_newton", "kv_axpby", "kv_combine", "kv_dot")
+           "kv_krylov_vector_host_stream", "kv_gmres", "kv_bicgstab2", "kv_newton", "kv_axpby", "kv_combine", "kv_dot",
+           "kv_axis_data")
 PHASES = {"stencil": 0, "divergence": 1, "tpd": 2, "correct": 3, "arnoldi": 4, "refine": 5, "gs_dots": 6,
           "gs_update": 7}
+
+
+def axis_data(n, stretch=0.0):
+    """kv_axis_data on the host (no CUDA call): (E, E_inv, lambda, weights) of one axis of n cells,
+    as numpy arrays of shapes (n, n), (n, n), (n,) and (14, n + 2); see include/kv.h."""
+    lib = load_library()
+    E, Ei = np.zeros((n, n)), np.zeros((n, n))
+    lam, w = np.zeros(n), np.zeros((14, n + 2))
+    P = ctypes.POINTER(ctypes.c_double)
+    st = lib.kv_axis_data(n, stretch, *(a.ctypes.data_as(P) for a in (E, Ei, lam, w)))
+    if st != 0:
+        raise KvError(st, lib.kv_last_error(None).decode())
+    return E, Ei, lam, w
 
 
 class KvError(RuntimeError):
@@ -108,6 +122,8 @@ def load_library(path: str = LIB_PATH):
     lib.kv_axpby.argtypes = [H, ctypes.c_double, D, ctypes.c_double, D]
     lib.kv_combine.argtypes = [H, D, ctypes.c_int, ctypes.POINTER(ctypes.c_double), D]
     lib.kv_dot.argtypes = [H, D, D, ctypes.POINTER(ctypes.c_double)]
+    P = ctypes.POINTER(ctypes.c_double)
+    lib.kv_axis_data.argtypes = [ctypes.c_int, ctypes.c_double, P, P, P, P]
     lib.kv_krylov_vector_adjoint.argtypes = [H, D, D]
     lib.kv_base_flow_gradient.argtypes = [H, D, D, D, ctypes.POINTER(ctypes.c_double)]
     lib.kv_krylov_vector_batch.argtypes = [H, D, D, ctypes.c_int]
