@@ -339,7 +339,8 @@ __global__ void __launch_bounds__(256) k_lap_dot(KvGeom g, const double* __restr
         int a[3] = {i, j, k}, b[3] = {i, j, k};
         a[ax] -= 1;
         b[ax] += 1;
-        lap += m * xmask(g, f, F, a[0], a[1], a[2]) + c * xmask(g, f, F, i, j, k) + p * xmask(g, f, F, b[0], b[1], b[2]);
+        lap += m * xmask(g, f, F, a[0], a[1], a[2]) + c * xmask(g, f, F, i, j, k) +
+               p * xmask(g, f, F, b[0], b[1], b[2]);
       }
       sv += yo * lap;
     }

@@ -199,19 +199,46 @@ bool stretched_axis(int n, double sp, std::vector<double>& tab, std::vector<doub
 }
 
 kv_status validate(const kv_grid_desc* d, std::string& msg) {
-  if (!d) { msg = "desc is NULL"; return KV_ERR_ARG; }
+  if (!d) {
+    msg = "desc is NULL";
+    return KV_ERR_ARG;
+  }
   if (d->nx < 2 || d->ny < 2 || d->nz < 2 || d->nx > 1024 || d->ny > 1024 || d->nz > 1024) {
     msg = "nx, ny, nz must be in [2, 1024]";
     return KV_ERR_ARG;
   }
-  if (d->spanwise_bc != KV_BC_CC && d->spanwise_bc != KV_BC_AA) { msg = "spanwise_bc must be KV_BC_CC or KV_BC_AA"; return KV_ERR_ARG; }
-  if (d->tproj != KV_TPROJ_ORTHOGONAL && d->tproj != KV_TPROJ_OBLIQUE) { msg = "tproj must be KV_TPROJ_ORTHOGONAL or KV_TPROJ_OBLIQUE"; return KV_ERR_ARG; }
-  if (d->precision != KV_PREC_FP64 && d->precision != KV_PREC_MIXED) { msg = "precision must be KV_PREC_FP64 or KV_PREC_MIXED"; return KV_ERR_ARG; }
-  if (d->refine_sweeps < 0 || d->refine_sweeps > 20) { msg = "refine_sweeps must be in [0, 20]"; return KV_ERR_ARG; }
-  if (d->cgs_passes != 0 && d->cgs_passes != 2) { msg = "cgs_passes must be 0 or 2"; return KV_ERR_ARG; }
-  if (!(d->gr > 0) || !(d->pr > 0) || !isfinite(d->gr) || !isfinite(d->pr)) { msg = "gr and pr must be finite and > 0"; return KV_ERR_ARG; }
-  if (d->tol < 0 || d->max_passes < 0 || d->max_passes > 100) { msg = "tol must be >= 0 and max_passes in [0, 100]"; return KV_ERR_ARG; }
-  if (!(d->stretch >= 0.0 && d->stretch < 0.15915494309189533)) { msg = "stretch must be in [0, 1/(2 pi))"; return KV_ERR_ARG; }
+  if (d->spanwise_bc != KV_BC_CC && d->spanwise_bc != KV_BC_AA) {
+    msg = "spanwise_bc must be KV_BC_CC or KV_BC_AA";
+    return KV_ERR_ARG;
+  }
+  if (d->tproj != KV_TPROJ_ORTHOGONAL && d->tproj != KV_TPROJ_OBLIQUE) {
+    msg = "tproj must be KV_TPROJ_ORTHOGONAL or KV_TPROJ_OBLIQUE";
+    return KV_ERR_ARG;
+  }
+  if (d->precision != KV_PREC_FP64 && d->precision != KV_PREC_MIXED) {
+    msg = "precision must be KV_PREC_FP64 or KV_PREC_MIXED";
+    return KV_ERR_ARG;
+  }
+  if (d->refine_sweeps < 0 || d->refine_sweeps > 20) {
+    msg = "refine_sweeps must be in [0, 20]";
+    return KV_ERR_ARG;
+  }
+  if (d->cgs_passes != 0 && d->cgs_passes != 2) {
+    msg = "cgs_passes must be 0 or 2";
+    return KV_ERR_ARG;
+  }
+  if (!(d->gr > 0) || !(d->pr > 0) || !isfinite(d->gr) || !isfinite(d->pr)) {
+    msg = "gr and pr must be finite and > 0";
+    return KV_ERR_ARG;
+  }
+  if (d->tol < 0 || d->max_passes < 0 || d->max_passes > 100) {
+    msg = "tol must be >= 0 and max_passes in [0, 100]";
+    return KV_ERR_ARG;
+  }
+  if (!(d->stretch >= 0.0 && d->stretch < 0.15915494309189533)) {
+    msg = "stretch must be in [0, 1/(2 pi))";
+    return KV_ERR_ARG;
+  }
   return KV_OK;
 }
 
@@ -324,7 +351,8 @@ kv_status simple_project(kv_grid* h, double* yvel, double* p, kv_stats* st) {
 
 // Autotuner for the linearised-operator kernels: times each candidate block shape (and, for the
 // double-float kernel of the mixed path, each register budget) on this grid's coefficients (the
-// base state stands in for x; v* and a scratch vector take the output) and keeps the fastest. Runs once per handle, at the first kv_set_base_flow.
+// base state stands in for x; v* and a scratch vector take the output) and keeps the fastest.
+// Runs once per handle, at the first kv_set_base_flow.
 kv_status autotune_apply(kv_grid* h) {
   static const int cand[][2] = {{32, 8}, {64, 4}, {128, 2}, {32, 4}, {16, 16}, {256, 1}};  // <= 256 threads
   if (!h->tmp4) {  // one padded field of scratch for the temperature output
@@ -708,7 +736,8 @@ kv_status kv_krylov_vector_host_stream(kv_handle h, const double* X_host, double
     if ((s = kv_krylov_vector(h, xb, yb, nullptr, nullptr)) != KV_OK) break;
     KV_CHECK_CUDA(h, cudaEventRecord(computed[b], h->s));
     KV_CHECK_CUDA(h, cudaStreamWaitEvent(h->cs_out, computed[b], 0));
-    KV_CHECK_CUDA(h, cudaMemcpyAsync(Y_host + (size_t)i * L, yb, L * sizeof(double), cudaMemcpyDeviceToHost, h->cs_out));
+    KV_CHECK_CUDA(h, cudaMemcpyAsync(Y_host + (size_t)i * L, yb, L * sizeof(double), cudaMemcpyDeviceToHost,
+                                     h->cs_out));
     KV_CHECK_CUDA(h, cudaEventRecord(drained[b], h->cs_out));
   }
   if (s != KV_OK) {
@@ -883,7 +912,9 @@ kv_status kv_krylov_vector_adjoint(kv_handle h, const double* y, double* z) {
   if (h->d.tproj != KV_TPROJ_ORTHOGONAL)
     return fail(h, KV_ERR_ARG, "kv_krylov_vector_adjoint: defined for the orthogonal temperature projection");
   if (h->str.sw)
-    return fail(h, KV_ERR_ARG, "kv_krylov_vector_adjoint: defined on the uniform grid (the velocity projection of a stretched grid is not symmetric)");
+    return fail(h, KV_ERR_ARG,
+                "kv_krylov_vector_adjoint: defined on the uniform grid (the velocity projection of a stretched "
+                "grid is not symmetric)");
   const size_t L = 4 * h->P;
   if (y < z + L && z < y + L) return fail(h, KV_ERR_ARG, "kv_krylov_vector_adjoint: y and z overlap");
   kv_status s = project_output_side(h, y);
@@ -899,7 +930,9 @@ kv_status kv_base_flow_gradient(kv_handle h, const double* x, const double* y, d
   if (h->d.tproj != KV_TPROJ_ORTHOGONAL)
     return fail(h, KV_ERR_ARG, "kv_base_flow_gradient: defined for the orthogonal temperature projection");
   if (h->str.sw)
-    return fail(h, KV_ERR_ARG, "kv_base_flow_gradient: defined on the uniform grid (the velocity projection of a stretched grid is not symmetric)");
+    return fail(h, KV_ERR_ARG,
+                "kv_base_flow_gradient: defined on the uniform grid (the velocity projection of a stretched "
+                "grid is not symmetric)");
   kv_status s = project_output_side(h, y);
   if (s != KV_OK) return s;
   if (g_base) {

@@ -226,20 +226,13 @@ void kv_launch_poisson_mixed(kv_grid* h, const double* b, double* phi, int stats
     if (sweep + 1 < h->refine) {
       KvPhase ph(h, KV_PH_REFINE, 1);
       unsigned long long* rm = stats ? h->rmax : nullptr;
+      const bool str = h->str.sw != nullptr;
       if (sweep == 0) {
-        if (h->str.sw)
-          k_residual_slices<float, true><<<rg, rb, 0, s>>>(g, h->str, b, h->phi32, h->xs[0], h->xs_slice, pad8(g.nx), rm, cx,
-                                                           cy, cz);
-        else
-          k_residual_slices<float, false><<<rg, rb, 0, s>>>(g, h->str, b, h->phi32, h->xs[0], h->xs_slice, pad8(g.nx), rm, cx,
-                                                            cy, cz);
+        auto kern = str ? k_residual_slices<float, true> : k_residual_slices<float, false>;
+        kern<<<rg, rb, 0, s>>>(g, h->str, b, h->phi32, h->xs[0], h->xs_slice, pad8(g.nx), rm, cx, cy, cz);
       } else {
-        if (h->str.sw)
-          k_residual_slices<double, true><<<rg, rb, 0, s>>>(g, h->str, b, phi, h->xs[0], h->xs_slice, pad8(g.nx), rm, cx, cy,
-                                                            cz);
-        else
-          k_residual_slices<double, false><<<rg, rb, 0, s>>>(g, h->str, b, phi, h->xs[0], h->xs_slice, pad8(g.nx), rm, cx, cy,
-                                                             cz);
+        auto kern = str ? k_residual_slices<double, true> : k_residual_slices<double, false>;
+        kern<<<rg, rb, 0, s>>>(g, h->str, b, phi, h->xs[0], h->xs_slice, pad8(g.nx), rm, cx, cy, cz);
       }
     }
   }

@@ -146,8 +146,10 @@ __global__ void __launch_bounds__(256) k_divergence_df(KvGeom g, KvStretch S, co
   const double* v = vel + P;
   const double* w = vel + 2 * P;
   const int e = i + g.X * (j + g.Y * k);
-  const DF dx = df_mul(df_sub(df_split(__ldg(u + e)), df_split(__ldg(u + e - 1))), inv_w_df<STR, 0, KV_SWD_IDC>(g, S, i, ihx));
-  const DF dy = df_mul(df_sub(df_split(__ldg(v + e)), df_split(__ldg(v + e - g.X))), inv_w_df<STR, 1, KV_SWD_IDC>(g, S, j, ihy));
+  const DF dx = df_mul(df_sub(df_split(__ldg(u + e)), df_split(__ldg(u + e - 1))),
+                       inv_w_df<STR, 0, KV_SWD_IDC>(g, S, i, ihx));
+  const DF dy = df_mul(df_sub(df_split(__ldg(v + e)), df_split(__ldg(v + e - g.X))),
+                       inv_w_df<STR, 1, KV_SWD_IDC>(g, S, j, ihy));
   const DF dz = df_mul(df_sub(df_split(__ldg(w + e)), df_split(__ldg(w + e - g.X * g.Y))),
                        inv_w_df<STR, 2, KV_SWD_IDC>(g, S, k, ihz));
   const DF d = df_add(df_add(dx, dy), dz);
@@ -169,15 +171,18 @@ struct CorrDF {
   __device__ __forceinline__ int at(int i, int j, int k) const { return i + g.X * (j + g.Y * k); }
   __device__ __forceinline__ DF u(int i, int j, int k) const {
     if (!(i >= 1 && i <= g.nx - 1 && j >= 1 && j <= g.ny && k >= 1 && k <= g.nz)) return DF{0.0f, 0.0f};
-    return df_sub(df_split(__ldg(vs + at(i, j, k))), df_mul(df_sub(ph(i + 1, j, k), ph(i, j, k)), inv_w_df<STR, 0, KV_SWD_IDF>(g, S, i, ihx)));
+    return df_sub(df_split(__ldg(vs + at(i, j, k))),
+                  df_mul(df_sub(ph(i + 1, j, k), ph(i, j, k)), inv_w_df<STR, 0, KV_SWD_IDF>(g, S, i, ihx)));
   }
   __device__ __forceinline__ DF v(int i, int j, int k) const {
     if (!(i >= 1 && i <= g.nx && j >= 1 && j <= g.ny - 1 && k >= 1 && k <= g.nz)) return DF{0.0f, 0.0f};
-    return df_sub(df_split(__ldg(vs + P + at(i, j, k))), df_mul(df_sub(ph(i, j + 1, k), ph(i, j, k)), inv_w_df<STR, 1, KV_SWD_IDF>(g, S, j, ihy)));
+    return df_sub(df_split(__ldg(vs + P + at(i, j, k))),
+                  df_mul(df_sub(ph(i, j + 1, k), ph(i, j, k)), inv_w_df<STR, 1, KV_SWD_IDF>(g, S, j, ihy)));
   }
   __device__ __forceinline__ DF w(int i, int j, int k) const {
     if (!(i >= 1 && i <= g.nx && j >= 1 && j <= g.ny && k >= 1 && k <= g.nz - 1)) return DF{0.0f, 0.0f};
-    return df_sub(df_split(__ldg(vs + 2 * P + at(i, j, k))), df_mul(df_sub(ph(i, j, k + 1), ph(i, j, k)), inv_w_df<STR, 2, KV_SWD_IDF>(g, S, k, ihz)));
+    return df_sub(df_split(__ldg(vs + 2 * P + at(i, j, k))),
+                  df_mul(df_sub(ph(i, j, k + 1), ph(i, j, k)), inv_w_df<STR, 2, KV_SWD_IDF>(g, S, k, ihz)));
   }
 };
 
@@ -268,18 +273,14 @@ float2 pair_of(double x) {
 void kv_launch_divergence(const kv_grid* h, const double* vel, double* b, cudaStream_t s) {
   const KvGeom& g = h->g;
   dim3 block(32, 8, 1), grid((g.nx + 31) / 32, (g.ny + 7) / 8, g.nz);
+  const bool str = h->str.sw != nullptr;
   if (h->d.precision == KV_PREC_MIXED) {
-    if (h->str.sw)
-      k_divergence_df<true><<<grid, block, 0, s>>>(g, h->str, vel, h->P, b, pair_of(g.ihx), pair_of(g.ihy), pair_of(g.ihz),
-                                                   h->xs[0], h->xs_slice, (g.nx + 7) & ~7);
-    else
-      k_divergence_df<false><<<grid, block, 0, s>>>(g, h->str, vel, h->P, b, pair_of(g.ihx), pair_of(g.ihy), pair_of(g.ihz),
-                                                    h->xs[0], h->xs_slice, (g.nx + 7) & ~7);
+    auto kern = str ? k_divergence_df<true> : k_divergence_df<false>;
+    kern<<<grid, block, 0, s>>>(g, h->str, vel, h->P, b, pair_of(g.ihx), pair_of(g.ihy), pair_of(g.ihz), h->xs[0],
+                                h->xs_slice, (g.nx + 7) & ~7);
   } else {
-    if (h->str.sw)
-      k_divergence<true><<<grid, block, 0, s>>>(g, h->str, vel, h->P, b);
-    else
-      k_divergence<false><<<grid, block, 0, s>>>(g, h->str, vel, h->P, b);
+    auto kern = str ? k_divergence<true> : k_divergence<false>;
+    kern<<<grid, block, 0, s>>>(g, h->str, vel, h->P, b);
   }
 }
 
@@ -287,22 +288,14 @@ void kv_launch_correct(const kv_grid* h, const double* vstar, const double* phi,
                        int accumulate_p, cudaStream_t s, int check) {
   const KvGeom& g = h->g;
   dim3 block(32, 8, 1), grid((g.X + 31) / 32, (g.Y + 7) / 8, g.Z);
+  const bool str = h->str.sw != nullptr;
   if (h->d.precision == KV_PREC_MIXED) {
     const float2 cx = pair_of(g.ihx), cy = pair_of(g.ihy), cz = pair_of(g.ihz);
-    if (h->str.sw) {
-      if (check)
-        k_correct_df<1, true><<<grid, block, 0, s>>>(g, h->str, vstar, phi, h->P, out_vel, p, accumulate_p, h->red, cx, cy, cz);
-      else
-        k_correct_df<0, true><<<grid, block, 0, s>>>(g, h->str, vstar, phi, h->P, out_vel, p, accumulate_p, h->red, cx, cy, cz);
-    } else {
-      if (check)
-        k_correct_df<1, false><<<grid, block, 0, s>>>(g, h->str, vstar, phi, h->P, out_vel, p, accumulate_p, h->red, cx, cy, cz);
-      else
-        k_correct_df<0, false><<<grid, block, 0, s>>>(g, h->str, vstar, phi, h->P, out_vel, p, accumulate_p, h->red, cx, cy, cz);
-    }
-  } else if (h->str.sw) {
-    k_correct<true><<<grid, block, 0, s>>>(g, h->str, vstar, phi, h->P, out_vel, p, accumulate_p, check, h->red);
+    auto kern = str ? (check ? k_correct_df<1, true> : k_correct_df<0, true>)
+                    : (check ? k_correct_df<1, false> : k_correct_df<0, false>);
+    kern<<<grid, block, 0, s>>>(g, h->str, vstar, phi, h->P, out_vel, p, accumulate_p, h->red, cx, cy, cz);
   } else {
-    k_correct<false><<<grid, block, 0, s>>>(g, h->str, vstar, phi, h->P, out_vel, p, accumulate_p, check, h->red);
+    auto kern = str ? k_correct<true> : k_correct<false>;
+    kern<<<grid, block, 0, s>>>(g, h->str, vstar, phi, h->P, out_vel, p, accumulate_p, check, h->red);
   }
 }
