@@ -89,9 +89,9 @@ typedef struct {
                         their faces. 0 = uniform grid; must be in [0, 1/(2 pi)) so the mapping stays
                         monotone (the paper uses up to 0.12). Both precisions; a stretched
                         KV_PREC_MIXED grid stores 12 more coefficient pairs per point (its operator
-                        reads the plus-neighbour coefficients instead of rebuilding them) and
-                        skips the 2.5D-march variant. The transpose, the base-flow gradient and
-                        kv_krylov_vector_noalloc take the uniform grid only. */
+                        reads the plus-neighbour coefficients instead of rebuilding them). The
+                        transpose, the base-flow gradient and kv_krylov_vector_noalloc take the
+                        uniform grid only. */
 } kv_grid_desc;
 
 typedef struct {

@@ -400,7 +400,6 @@ kv_status autotune_apply(kv_grid* h) {
     int dv = 0, dbx = 32, dby = 2;
     for (auto& c : dcand) {
       if (c[0] == 1 && 4 * h->P >= (size_t(1) << 31)) continue;  // the march indexes x with 32 bits
-      if (c[0] == 1 && h->str.sw) continue;  // the march rebuilds c+ from c- (uniform grids only)
       h->df_variant = c[0];
       h->df_bx = c[1];
       h->df_by = c[2];

@@ -635,10 +635,11 @@ __device__ __forceinline__ double proj_value(const Loader<true>& L, int f, int i
   return f == 0 ? L.lu(i, j, k) : (f == 1 ? L.lv(i, j, k) : (f == 2 ? L.lw(i, j, k) : L.lT(i, j, k)));
 }
 
-__global__ void __launch_bounds__(MTHREADS, 2) k_apply_df_march(KvGeom g, const float2* __restrict__ coef,
-                                                                const double* __restrict__ x, size_t P,
-                                                                double* __restrict__ vstar,
-                                                                double* __restrict__ tout, DfAlpha al, int kc) {
+template <bool STR>
+__device__ __forceinline__ void march_body(const KvGeom& g, const float2* __restrict__ coef,
+                                           const float2* __restrict__ cplus, const double* __restrict__ x, size_t P,
+                                           double* __restrict__ vstar, double* __restrict__ tout, const DfAlpha& al,
+                                           int kc) {
   __shared__ float2 xt[4][4][MPTS];  // [slot][field][point]
   float2* const xflat = &xt[0][0][0];
   const int tid = threadIdx.x;
@@ -748,29 +749,40 @@ __global__ void __launch_bounds__(MTHREADS, 2) k_apply_df_march(KvGeom g, const 
       const int ck = wall_class(k, g.nz);
       const size_t e = (size_t)i + (size_t)sy * j + (size_t)sz * k;
       DFAcc a;
+      // c- x- + c+ x+ along one axis; on a stretched grid (STR) c+ is read from cplus (entry
+      // 3 eq + axis), else rebuilt as alpha + beta c-
+      auto own_axis = [&](DFAcc& acc, const float2 cm, const DF xm, const DF xp, const float2 alpha, const float beta,
+                          int axis) {
+        if (STR) {
+          acc.fma(cm, xm);
+          acc.fma(__ldg(cplus + (size_t)(3 * eq + axis) * P + e), xp);
+        } else {
+          ::own_axis(acc, cm, xm, xp, alpha, beta);
+        }
+      };
       if (eq == 0) {
         a.fma(c[0], X(s0, 0, 0, 0));
-        own_axis(a, c[1], X(s0, 0, -1, 0), X(s0, 0, 1, 0), alpha_of(al, 0, 0, 0), -1.0f);
-        own_axis(a, c[2], X(s0, 0, 0, -1), X(s0, 0, 0, 1), alpha_of(al, 0, 1, cj), beta_of(cj));
-        own_axis(a, c[3], X(sm, 0, 0, 0), X(sp, 0, 0, 0), alpha_of(al, 0, 2, ck), beta_of(ck));
+        own_axis(a, c[1], X(s0, 0, -1, 0), X(s0, 0, 1, 0), alpha_of(al, 0, 0, 0), -1.0f, 0);
+        own_axis(a, c[2], X(s0, 0, 0, -1), X(s0, 0, 0, 1), alpha_of(al, 0, 1, cj), beta_of(cj), 1);
+        own_axis(a, c[3], X(sm, 0, 0, 0), X(sp, 0, 0, 0), alpha_of(al, 0, 2, ck), beta_of(ck), 2);
         // v(i, j-1), v(i, j), v(i+1, j-1), v(i+1, j); w(i, k-1), w(i, k), w(i+1, k-1), w(i+1, k)
         a.fma(c[4], sum4(X(s0, 1, 0, -1), X(s0, 1, 0, 0), X(s0, 1, 1, -1), X(s0, 1, 1, 0)));
         a.fma(c[5], sum4(X(sm, 2, 0, 0), X(s0, 2, 0, 0), X(sm, 2, 1, 0), X(s0, 2, 1, 0)));
         vstar[e] = i <= g.nx - 1 ? a.value() : 0.0;
       } else if (eq == 1) {
         a.fma(c[0], X(s0, 1, 0, 0));
-        own_axis(a, c[1], X(s0, 1, -1, 0), X(s0, 1, 1, 0), alpha_of(al, 0, 0, ci), beta_of(ci));
-        own_axis(a, c[2], X(s0, 1, 0, -1), X(s0, 1, 0, 1), alpha_of(al, 0, 1, 0), -1.0f);
-        own_axis(a, c[3], X(sm, 1, 0, 0), X(sp, 1, 0, 0), alpha_of(al, 0, 2, ck), beta_of(ck));
+        own_axis(a, c[1], X(s0, 1, -1, 0), X(s0, 1, 1, 0), alpha_of(al, 0, 0, ci), beta_of(ci), 0);
+        own_axis(a, c[2], X(s0, 1, 0, -1), X(s0, 1, 0, 1), alpha_of(al, 0, 1, 0), -1.0f, 1);
+        own_axis(a, c[3], X(sm, 1, 0, 0), X(sp, 1, 0, 0), alpha_of(al, 0, 2, ck), beta_of(ck), 2);
         // u(i-1, j), u(i, j), u(i-1, j+1), u(i, j+1); w(j, k-1), w(j, k), w(j+1, k-1), w(j+1, k)
         a.fma(c[4], sum4(X(s0, 0, -1, 0), X(s0, 0, 0, 0), X(s0, 0, -1, 1), X(s0, 0, 0, 1)));
         a.fma(c[5], sum4(X(sm, 2, 0, 0), X(s0, 2, 0, 0), X(sm, 2, 0, 1), X(s0, 2, 0, 1)));
         vstar[P + e] = j <= g.ny - 1 ? a.value() : 0.0;
       } else if (eq == 2) {
         a.fma(c[0], X(s0, 2, 0, 0));
-        own_axis(a, c[1], X(s0, 2, -1, 0), X(s0, 2, 1, 0), alpha_of(al, 0, 0, ci), beta_of(ci));
-        own_axis(a, c[2], X(s0, 2, 0, -1), X(s0, 2, 0, 1), alpha_of(al, 0, 1, cj), beta_of(cj));
-        own_axis(a, c[3], X(sm, 2, 0, 0), X(sp, 2, 0, 0), alpha_of(al, 0, 2, 0), -1.0f);
+        own_axis(a, c[1], X(s0, 2, -1, 0), X(s0, 2, 1, 0), alpha_of(al, 0, 0, ci), beta_of(ci), 0);
+        own_axis(a, c[2], X(s0, 2, 0, -1), X(s0, 2, 0, 1), alpha_of(al, 0, 1, cj), beta_of(cj), 1);
+        own_axis(a, c[3], X(sm, 2, 0, 0), X(sp, 2, 0, 0), alpha_of(al, 0, 2, 0), -1.0f, 2);
         // u(i-1, k), u(i, k), u(i-1, k+1), u(i, k+1); v(j-1, k), v(j, k), v(j-1, k+1), v(j, k+1)
         a.fma(c[4], sum4(X(s0, 0, -1, 0), X(s0, 0, 0, 0), X(sp, 0, -1, 0), X(sp, 0, 0, 0)));
         a.fma(c[5], sum4(X(s0, 1, 0, -1), X(s0, 1, 0, 0), X(sp, 1, 0, -1), X(sp, 1, 0, 0)));
@@ -778,9 +790,9 @@ __global__ void __launch_bounds__(MTHREADS, 2) k_apply_df_march(KvGeom g, const 
         vstar[2 * P + e] = k <= g.nz - 1 ? a.value() : 0.0;
       } else {
         a.fma(c[0], X(s0, 3, 0, 0));
-        own_axis(a, c[1], X(s0, 3, -1, 0), X(s0, 3, 1, 0), alpha_of(al, 1, 0, ci), beta_of(ci));
-        own_axis(a, c[2], X(s0, 3, 0, -1), X(s0, 3, 0, 1), alpha_of(al, 1, 1, cj), beta_of(cj));
-        own_axis(a, c[3], X(sm, 3, 0, 0), X(sp, 3, 0, 0), alpha_of(al, 1, 2, ck), beta_of(ck));
+        own_axis(a, c[1], X(s0, 3, -1, 0), X(s0, 3, 1, 0), alpha_of(al, 1, 0, ci), beta_of(ci), 0);
+        own_axis(a, c[2], X(s0, 3, 0, -1), X(s0, 3, 0, 1), alpha_of(al, 1, 1, cj), beta_of(cj), 1);
+        own_axis(a, c[3], X(sm, 3, 0, 0), X(sp, 3, 0, 0), alpha_of(al, 1, 2, ck), beta_of(ck), 2);
         a.fma(c[4], df_add_lazy(X(s0, 0, -1, 0), X(s0, 0, 0, 0)));
         a.fma(c[5], df_add_lazy(X(s0, 1, 0, -1), X(s0, 1, 0, 0)));
         a.fma(c[6], df_add_lazy(X(sm, 2, 0, 0), X(s0, 2, 0, 0)));
@@ -797,6 +809,24 @@ __global__ void __launch_bounds__(MTHREADS, 2) k_apply_df_march(KvGeom g, const 
     if (more) put((k + 2) & 3, nxt);
     __syncthreads();
   }
+}
+
+// The uniform grid's march: two blocks of 512 threads per SM (64 registers a thread).
+__global__ void __launch_bounds__(MTHREADS, 2) k_apply_df_march(KvGeom g, const float2* __restrict__ coef,
+                                                                const double* __restrict__ x, size_t P,
+                                                                double* __restrict__ vstar,
+                                                                double* __restrict__ tout, DfAlpha al, int kc) {
+  march_body<false>(g, coef, nullptr, x, P, vstar, tout, al, kc);
+}
+
+// A stretched grid's march (Eq 22): the three plus coefficients per equation come from cplus,
+// which needs more registers than two blocks per SM leave.
+__global__ void __launch_bounds__(MTHREADS, 1) k_apply_df_march_str(KvGeom g, const float2* __restrict__ coef,
+                                                                    const float2* __restrict__ cplus,
+                                                                    const double* __restrict__ x, size_t P,
+                                                                    double* __restrict__ vstar,
+                                                                    double* __restrict__ tout, DfAlpha al, int kc) {
+  march_body<true>(g, coef, cplus, x, P, vstar, tout, al, kc);
 }
 
 // The padded-boundary entries of v* and T* (walls, edges, corners: 0; the insulated walls'
@@ -916,12 +946,15 @@ void kv_launch_apply_df(const kv_grid* h, const float2* cdf, const double* x, do
   for (int d = 0; d < 2; ++d)
     for (int ax = 0; ax < 3; ++ax)
       for (int c = 0; c < 3; ++c) al.a[d][ax][c] = host_pair(fac[c] * diff[d] * ih2[ax]);
-  if (h->df_variant == 1 && !h->str.sw) {
+  if (h->df_variant == 1) {
     // the 2.5D march: df_by planes per block
     k_zero_boundary<<<2 * 152, 256, 0, s>>>(g, h->P, vstar, tout);
     const int kc = h->df_by;
     dim3 grid((g.nx + MB_X - 1) / MB_X, (g.ny + MB_Y - 1) / MB_Y, (g.nz + kc - 1) / kc);
-    k_apply_df_march<<<grid, MTHREADS, 0, s>>>(g, cdf, x, h->P, vstar, tout, al, kc);
+    if (h->str.sw)
+      k_apply_df_march_str<<<grid, MTHREADS, 0, s>>>(g, cdf, h->coef_dfp, x, h->P, vstar, tout, al, kc);
+    else
+      k_apply_df_march<<<grid, MTHREADS, 0, s>>>(g, cdf, x, h->P, vstar, tout, al, kc);
     return;
   }
   {

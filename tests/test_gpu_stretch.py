@@ -7,7 +7,8 @@ oracle dense Jacobi rotations), whose errors in the lowest modes grow like eps |
 ~ eps n^2; on the velocity correction this stays near 2e-13 up to 64^3, and the pressure
 correction phi is compared at sizes where it stays below 1e-12. The mixed-precision path
 (tensor-core TPF contractions refined to FP64 class, double-float operator reading the
-plus-neighbour coefficients) is held to the mixed bar, 1e-9."""
+plus-neighbour coefficients, as the split pass or the 2.5D march, whichever the autotuner
+times faster) is held to the mixed bar, 1e-9."""
 import numpy as np
 import pytest
 
@@ -180,8 +181,7 @@ def test_stretched_mixed_krylov_vector_matches_oracle(n, bc, gr, tproj):
     assert st.device_error == 0
     y_ref = Oracle(*n, bc=bc, gr=gr, pr=0.71, tproj=tproj, stretch=S).krylov_vector(base, x[0])
     err = rel(y.cpu().numpy(), y_ref)
-    assert err < RTOL_MIXED, err
-    assert g.tuning()["df_variant"] == 0  # the march rebuilds c+ from c- (uniform grids only)
+    assert err < RTOL_MIXED, (err, g.tuning())
 
 
 def test_stretched_mixed_at_256_matches_fp64_path():
@@ -201,7 +201,7 @@ def test_stretched_mixed_at_256_matches_fp64_path():
     ym, st = gm.krylov_vector(xt, stats=True)
     assert st.device_error == 0
     err = (torch.linalg.vector_norm(ym - y64) / torch.linalg.vector_norm(y64)).item()
-    assert err < RTOL_MIXED, err
+    assert err < RTOL_MIXED, (err, gm.tuning())
 
 
 def test_stretched_mixed_arnoldi_steps():
