@@ -601,6 +601,22 @@ def run_ours(args):
                                                    "sample": f"{rc['sample']} ({rc['seconds']:.1f} s)"}
             except Exception as e:
                 out["newton64"]["cpu_baseline"] = {"value": None, "kind": "oracle", "sample": f"failed: {e}"[:300]}
+        if "stretched_fp64" in out:  # the oracle beside the stretched line: one evaluation
+            try:
+                cmd = [sys.executable, "-m", "oracle.bench_cpu", "--workload", w.name, "--evals", "1",
+                       "--stretch", "0.12"]
+                r = subprocess.run(cmd, cwd=ROOT, capture_output=True, text=True, timeout=120)
+                if r.returncode != 0:
+                    raise RuntimeError(r.stderr[-500:])
+                rc = json.loads(r.stdout.strip().splitlines()[-1])
+                out["stretched_fp64"]["cpu_baseline"] = {
+                    "value": rc["value"], "unit": UNIT, "cores": rc["cores"], "kind": "oracle",
+                    "sample": f"1 FP64 oracle Krylov-vector evaluation of {w.name} stretched by Eq (22), a = 0.12 "
+                              f"({rc['seconds']:.1f} s on {rc['cores']} host threads; the grid set-up, "
+                              f"{rc['setup_seconds']:.1f} s, not timed)"}
+            except Exception as e:
+                out["stretched_fp64"]["cpu_baseline"] = {"value": None, "kind": "oracle",
+                                                         "sample": f"failed: {e}"[:300]}
     print(json.dumps(out), flush=True)
     if dist:
         dist.destroy_process_group()

@@ -1,7 +1,7 @@
 """Times the FP64 CPU oracle on a workload (test infrastructure: the benchmark's CPU
 baseline). Prints one JSON line: Krylov-vector evaluations per second on the host cores.
 
-    python -m oracle.bench_cpu --workload cube256_cc --evals 1 [--warmup 0]
+    python -m oracle.bench_cpu --workload cube256_cc --evals 1 [--warmup 0] [--stretch 0.12]
     python -m oracle.bench_cpu --newton-cycle 20
 """
 import argparse
@@ -43,6 +43,7 @@ def main():
     ap.add_argument("--evals", type=int, default=1)
     ap.add_argument("--warmup", type=int, default=0)
     ap.add_argument("--newton-cycle", type=int, default=0, help="time one GMRES(m) cycle of the Newton line instead")
+    ap.add_argument("--stretch", type=float, default=0.0, help="grid stretching parameter of Eq (22)")
     a = ap.parse_args()
     if a.newton_cycle:
         newton_cycle(a.newton_cycle)
@@ -50,7 +51,9 @@ def main():
     w = synth.WORKLOADS[a.workload]
     base, x = synth.workload_arrays(w)
     base = np.stack(base)
-    o = Oracle(w.nx, w.ny, w.nz, bc=w.bc, gr=w.gr, pr=w.pr)
+    t0 = time.perf_counter()
+    o = Oracle(w.nx, w.ny, w.nz, bc=w.bc, gr=w.gr, pr=w.pr, stretch=a.stretch)
+    setup = time.perf_counter() - t0
     for _ in range(a.warmup):
         o.krylov_vector(base, x[0])
     t0 = time.perf_counter()
@@ -59,7 +62,7 @@ def main():
     dt = time.perf_counter() - t0
     threads = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
     print(json.dumps({"value": a.evals / dt, "unit": "Krylov-vector evals/s", "seconds": dt, "evals": a.evals,
-                      "cores": threads, "workload": a.workload}))
+                      "cores": threads, "workload": a.workload, "stretch": a.stretch, "setup_seconds": setup}))
 
 
 if __name__ == "__main__":
