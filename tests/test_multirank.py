@@ -52,3 +52,39 @@ def test_reference_arm_other_ranks_exit_without_work(monkeypatch, capsys):
         workload, steps, warmup, restart, gpus = "cube16_cc", 1, 0, 20, 2
     bench.run_reference(A())
     assert capsys.readouterr().out == ""
+
+
+def test_reference_arm_rank0_prints_the_contract_line(monkeypatch, capsys):
+    """The reference arm (the oracle on the host cores) prints one JSON line with the keys the
+    benchmark contract names, its e2e equal to its value and no host-device bytes."""
+    import json
+
+    import bench
+    monkeypatch.setenv("RANK", "0")
+    monkeypatch.setenv("WORLD_SIZE", "1")
+
+    class A:
+        workload, steps, warmup, restart, gpus = "cube16_cc", 2, 1, 20, 1
+    bench.run_reference(A())
+    lines = [ln for ln in capsys.readouterr().out.splitlines() if ln.startswith("{")]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    assert d["impl"] == "reference" and d["metric"] == bench.METRIC and d["unit"] == bench.UNIT
+    assert d["value"] > 0 and d["higher_is_better"] is True and d["steps"] == 2 and d["warmup"] == 1
+    assert d["e2e"] == {"value": d["value"], "unit": d["unit"], "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
+    assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["value"] == d["value"]
+    assert d["cpu_baseline"]["cores"] >= 1 and d["config"]["workload"]
+
+
+def test_oracle_timing_on_a_stretched_grid():
+    """The oracle's timing script, as the benchmark calls it beside the stretched line."""
+    import json
+    import subprocess
+    import sys
+
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    r = subprocess.run([sys.executable, "-m", "oracle.bench_cpu", "--workload", "cube16_cc", "--evals", "2",
+                        "--stretch", "0.12"], cwd=root, capture_output=True, text=True, timeout=300)
+    assert r.returncode == 0, r.stderr[-1000:]
+    d = json.loads(r.stdout.strip().splitlines()[-1])
+    assert d["value"] > 0 and d["evals"] == 2 and d["stretch"] == 0.12 and d["setup_seconds"] >= 0
