@@ -265,3 +265,55 @@ def test_small_stretch_approaches_the_uniform_grid():
     b -= b.mean()
     p0, p1 = o0.poisson(b), o1.poisson(b)
     assert np.abs(p1 - p0).max() < 1e-6 * np.abs(p0).max()
+
+
+# --- Section 3.1's special cases on the stretched grid ----------------------------------------------
+def test_stretched_conduction_spectrum_is_kronecker_sum():
+    """U = 0, Theta = 0: the temperature block is kappa times the Laplacian with homogeneous
+    Dirichlet walls (CC), a sum of 1D operators along the three axes, so its eigenvalues are the
+    sums of the 1D eigenvalues (the structure of Eq 17), here for the stretched 1D operators."""
+    n = (4, 5, 3)
+    nx, ny, nz = n
+    gr, pr = 1.0e6, 0.71
+    kappa = 1 / (pr * gr ** 0.5)
+    o = Oracle(*n, gr=gr, pr=pr, stretch=S)
+    base = np.zeros((4,) + o.shape)
+    cols = []
+    for k in range(1, nz + 1):
+        for j in range(1, ny + 1):
+            for i in range(1, nx + 1):
+                x = np.zeros((4,) + o.shape)
+                x[3, k, j, i] = 1.0
+                cols.append(o.krylov_vector(base, x)[3, 1:-1, 1:-1, 1:-1].ravel())
+    ev = np.sort(np.linalg.eigvals(np.array(cols).T).real)
+
+    def dirichlet_1d(m):
+        c, dx = positions(m, False, S), cell_widths(m, S)  # c[0] = 0 and c[m + 1] = 1 are the walls
+        M = np.zeros((m, m))
+        for t in range(1, m + 1):
+            wl, wr = 1 / ((c[t] - c[t - 1]) * dx[t - 1]), 1 / ((c[t + 1] - c[t]) * dx[t - 1])
+            M[t - 1, t - 1] = -(wl + wr)
+            if t > 1:
+                M[t - 1, t - 2] = wl
+            if t < m:
+                M[t - 1, t] = wr
+        return np.linalg.eigvals(M).real
+
+    lx, ly, lz = dirichlet_1d(nx), dirichlet_1d(ny), dirichlet_1d(nz)
+    expect = np.sort((kappa * (lz[:, None, None] + ly[None, :, None] + lx[None, None, :])).ravel())
+    assert np.allclose(ev, expect, rtol=1e-10)
+
+
+@pytest.mark.parametrize("bc", [synth.CC, synth.AA])
+def test_stretched_finite_difference_of_residual_equals_krylov_vector(bc):
+    """The residual of Eqs (1)-(2) is quadratic in the state, so its central difference equals
+    the Krylov vector exactly (up to rounding) on the stretched grid too."""
+    n = (6, 7, 5)
+    o = Oracle(*n, bc=bc, gr=2.0e6, stretch=S)
+    St = packed_base(*n, bc, 41)
+    x = o.project_input(rand_vec(*n, 42))
+    eps = 1e-3
+    Fp, _ = o.newton_residual(St + eps * x)
+    Fm, _ = o.newton_residual(St - eps * x)
+    y = o.krylov_vector(St, x)
+    assert np.linalg.norm((Fp - Fm) / (2 * eps) - y) < 1e-10 * np.linalg.norm(y)
