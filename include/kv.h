@@ -75,7 +75,8 @@ typedef struct {
   int tproj;         /* KV_TPROJ_ORTHOGONAL or KV_TPROJ_OBLIQUE */
   int precision;     /* KV_PREC_FP64 or KV_PREC_MIXED */
   double gr, pr;     /* Grashof and Prandtl numbers, > 0 */
-  double tol;        /* SIMPLE stop: max|D v| * h_min / max|v| < tol (0 -> 1e-12) */
+  double tol;        /* SIMPLE stop: max|D v| * h_min / max|v| < tol (0 -> 1e-12 for KV_PREC_FP64,
+                        1e-11 for KV_PREC_MIXED) */
   int max_passes;    /* SIMPLE passes at most (0 -> 1: one exact pass, residual reported) */
   int refine_sweeps; /* KV_PREC_MIXED: tensor-core solves per Poisson solve, each followed by an
                         FP64 residual (0 -> 2) */
@@ -118,20 +119,52 @@ kv_status kv_set_stream(kv_handle h, void* stream);
 /* Number of doubles in one padded field, (nx+2)(ny+2)(nz+2). */
 kv_status kv_field_len(kv_handle h, size_t* field_len);
 
-/* Copies a packed state U | V | W | Theta (device pointer) into library storage: the steady
-   flow (U, P, Theta) that Eqs (8)-(9) are linearised about. Theta carries its wall values.
-   Also forms the coefficients of the linearised operator for this state (37 padded fields:
-   15 per velocity face, 13 per cell plus the fixed buoyancy weights), so that each Krylov
-   vector is a fixed-coefficient 15/13-point product; a grid therefore holds about
-   (4 + 37 + 3) padded fields plus two n^3 buffers of device memory. */
-kv_status kv_set_base_flow(kv_handle h, const double* base);
+/* Layout query: the number of doubles in each padded field of a vector, u (x-faces), v (y-faces),
+   w (z-faces) and a cell field (T, p). All four use the one padded layout above, so all four are
+   (nx+2)(ny+2)(nz+2); a packed vector is their concatenation. Any output may be NULL (not all). */
+kv_status kv_field_sizes(kv_handle h, size_t* u, size_t* v, size_t* w, size_t* cell);
+
+/* Copies the steady state that Eqs (8)-(9) are linearised about (Section 3.1: the Jacobian at the
+   current Newton iterate or at the converged flow) into library storage: U, V, W (velocity on
+   the x/y/z faces) and Theta (temperature at the cells, with its wall values, Eqs (4)-(7)); four
+   device pointers to padded fields, read on the handle's stream and not kept. Also forms the
+   coefficients of the linearised operator for this state (37 padded fields: 15 per velocity
+   face, 13 per cell plus the fixed buoyancy weights), so that each Krylov vector is a
+   fixed-coefficient 15/13-point product; a grid therefore holds about (4 + 37 + 3) padded
+   fields plus two n^3 buffers of device memory. The first call on a handle also runs the
+   autotuner (unless kv_set_tuning fixed the configuration). */
+kv_status kv_set_base_flow(kv_handle h, const double* U, const double* V, const double* W, const double* Theta);
+
+/* As kv_set_base_flow, for a packed state U | V | W | Theta (one device pointer, 4 padded
+   fields), the layout kv_newton and the state vectors of the solvers use. */
+kv_status kv_set_base_flow_packed(kv_handle h, const double* base);
 
 /* One Krylov vector (Eqs (11)-(13), Section 3.1): y = (Pi_v (+) P_T) J P_BC x.
    x, y: packed vectors (device, must not overlap). p: optional padded cell field that
    receives the pressure correction sum(phi) (zero mean, walls zero); may be NULL.
-   st: optional host struct; when given, or when desc.max_passes > 1, the call
-   synchronises the stream to read the divergence residual. */
+   Every pass evaluates the SIMPLE stopping test of Section 3.1 (max|D v| h_min / max|v| < tol)
+   on the device. With desc.max_passes <= 1 and st == NULL the call does not synchronise: the
+   test's outcome is accumulated in the grid's guard (kv_guard_read). With st, or with
+   desc.max_passes > 1 (the literal loop: repeat while the test fails), the call synchronises
+   the stream after each pass to read it and returns KV_ERR_NOT_CONVERGED when the literal loop
+   ends above tol (y and p then hold the last pass), and KV_ERR_ARG when the velocity or its
+   divergence is not finite (NaN or Inf in x or in the base flow; y is then undefined). */
 kv_status kv_krylov_vector(kv_handle h, const double* x, double* y, double* p, kv_stats* st);
+
+/* The device-side SIMPLE test of the one-pass evaluations (desc.max_passes <= 1) since the grid
+   was created or last reset: every projection of the grid counts (Krylov vectors, also inside
+   the batched, plan, host-buffer and solver calls; Newton residuals; the transpose's input
+   projection). failed: tests at or above tol with finite values; nonfinite: NaN or Inf in the
+   velocity or its divergence; worst_rel_div: the largest finite max|D v| h_min / max|v|. */
+typedef struct {
+  long long checks;
+  long long failed;
+  long long nonfinite;
+  double worst_rel_div;
+} kv_guard;
+
+/* Synchronises the stream and copies the guard into *out (host); reset != 0 then clears it. */
+kv_status kv_guard_read(kv_handle h, kv_guard* out, int reset);
 
 /* As kv_krylov_vector, with x and y in HOST memory (pinned or pageable); the host-device
    copies are queued on the handle's stream and the call returns once y is in host memory. */
@@ -179,7 +212,9 @@ const char* kv_plan_last_error(kv_plan_handle p);
    entries of the four fields. With KV_PREC_MIXED and up to 24 basis vectors, the first two
    Gram-Schmidt sweeps run in double-float arithmetic on the FP32 pipe (relative rounding
    ~2^-46 instead of 2^-53); entries below 2^-103 in magnitude are then treated as 0, and a new
-   vector with an entry of magnitude >= 2^48, NaN or Inf gives KV_ERR_ARG (V_{j+1} undefined). */
+   vector with an entry of magnitude >= 2^48, NaN or Inf gives KV_ERR_ARG (V_{j+1} undefined).
+   Up to 24 basis vectors the decision on the second update is taken on the device and the
+   step synchronises once, to return h_col. */
 kv_status kv_arnoldi_step(kv_handle h, double* V, int j, double* h_col);
 
 /* Transpose of the Krylov map: z = A^T y with A = (Pi_v (+) P_T) J P_BC (the adjoint eigenvalue
@@ -308,6 +343,21 @@ kv_status kv_profile_get(kv_handle h, int phase, double* total_ms, long long* ti
    before the first base flow. */
 kv_status kv_tuning(kv_handle h, int* cfg);
 
+/* Fixes the operator configuration instead of timing the candidates (not part of the method: it
+   lets every compiled variant be run and checked deterministically). cfg (host, 5 ints) as
+   kv_tuning: cfg[0] x cfg[1] the FP64 operator's block (each >= 1, product <= 256 and a multiple
+   of 32); for KV_PREC_MIXED, cfg[2] = 0 with cfg[3] in {32, 64, 128} cells and cfg[4] rows
+   (cfg[3] x 4 x cfg[4] <= 512), or cfg[2] = 1 with cfg[4] in 1..1024 planes per block (only for
+   grids whose packed vector has fewer than 2^31 doubles); cfg[2..4] are ignored for
+   KV_PREC_FP64. Takes effect for the next evaluation; the autotuner does not run afterwards.
+   KV_ERR_ARG for values outside these ranges. */
+kv_status kv_set_tuning(kv_handle h, const int* cfg);
+
+/* Instrumentation: fused Arnoldi steps (basis of at most 24 vectors) since the last
+   kv_profile_enable, and of them those that applied the second Gram-Schmidt update. Host
+   pointers, each nullable. */
+kv_status kv_arnoldi_counts(kv_handle h, long long* steps, long long* second_updates);
+
 /* Allocation-free Krylov vector, for callers that cannot allocate device memory (code that
    runs under an allocator it does not own, inside a fixed memory budget, or in a plug-in that
    may not call cudaMalloc / cudaFree). The paper has no counterpart: it is a deployment
@@ -315,11 +365,13 @@ kv_status kv_tuning(kv_handle h, int* cfg);
    grid descriptor, a packed base state, x and y, all caller-owned device pointers; no handle
    is created. Its scratch is a fixed __device__ array of about 1.5 MB that every GPU loading
    the library keeps until the process exits, which limits the grid to
-   KV_NOALLOC_MAX_N cells per axis; larger grids and desc->precision != KV_PREC_FP64 return
-   KV_ERR_ARG (message via kv_last_error(NULL)). The first call on a device looks up the
-   array's device address (set-up); make that first call before any stream capture. All
-   calls share the one array and it keeps the last call's contents, so calls that overlap on
-   the GPU (other streams, other host threads) race: serialise them. stream: cudaStream_t. */
+   KV_NOALLOC_MAX_N cells per axis; larger grids, a stretched grid and
+   desc->precision != KV_PREC_FP64 return KV_ERR_ARG (message via kv_last_error(NULL)), as do
+   x or base overlapping y. The per-axis tables of Eq (15) are written into the array by a
+   kernel on `stream` at every call. The first call on a device looks up the array's device
+   address (set-up); make that first call before any stream capture. All calls share the one
+   array and it keeps the last call's contents, so calls that overlap on the GPU (other streams,
+   other host threads) race: serialise them. stream: cudaStream_t. */
 #define KV_NOALLOC_MAX_N 32
 kv_status kv_krylov_vector_noalloc(const kv_grid_desc* desc, const double* base, const double* x, double* y,
                                    void* stream);

@@ -1,6 +1,7 @@
 // C ABI of libkv: grid handles, the Krylov-vector map, one Arnoldi step and the Newton
 // residual (arXiv 1905.11601, Section 3.1). See include/kv.h for the contract.
 #include <math.h>
+#include <stddef.h>
 #include <stdio.h>
 #include <string.h>
 
@@ -255,7 +256,8 @@ void free_all(kv_grid* h) {
   cudaFree(h->sw);
   cudaFree(h->swd);
   cudaFree(h->coef_dfp);
-  cudaFree(h->red);
+  cudaFree(h->guard);
+  h->red = nullptr;
   cudaFree(h->partials);
   cudaFree(h->hdev);
   cudaFree(h->solve_buf);
@@ -293,35 +295,49 @@ double bits_to_double(unsigned long long b) {
 // The projection part of the Krylov map for a momentum right-hand side in h->vstar:
 // b = D v*; phi = L^+ b (Eq 18); v = v* - G phi; p = phi; repeated while the SIMPLE test
 // fails and passes remain. Writes the velocity part of y.
+//
+// Every pass evaluates the stopping test of Section 3.1 on the device: the correction kernel
+// reduces max |D v| and max |v|, and a one-thread kernel forms max |D v| h_min / max |v| and
+// records it in the grid's guard (kv_guard_read). One-pass evaluations (max_passes <= 1) stay
+// asynchronous: the guard is read later. The host reads the pass's figures only when it needs
+// them: for st, and in the literal loop (max_passes > 1), which decides on the host whether
+// another pass runs.
 kv_status simple_project(kv_grid* h, double* yvel, double* p, kv_stats* st) {
   cudaStream_t s = h->s;
   const int max_passes = h->d.max_passes > 0 ? h->d.max_passes : 1;
-  const bool want = st != nullptr || max_passes > 1;
-  const double tol = h->d.tol > 0 ? h->d.tol : 1e-12;
-  const double hmin = h->hmin;
+  const bool literal = max_passes > 1;
+  const bool want = st != nullptr || literal;
+  const bool mixed = h->d.precision == KV_PREC_MIXED;
+  // default tolerances: FP64 arithmetic leaves max|D v| h_min / max|v| near 1e-14; the mixed
+  // path's two refinement sweeps leave about 1.4e-12 at 256^3, where an unrefined tensor-core
+  // solve leaves about 1e-7
+  const double tol = h->d.tol > 0 ? h->d.tol : (mixed ? 1e-11 : 1e-12);
   int pass = 0;
   double maxdiv = 0, rel = 0;
+  bool finite = true;
   const double* src = h->vstar;
-  const bool mixed = h->d.precision == KV_PREC_MIXED;
   double* phi = mixed ? h->tpd_b : h->tpd_a;
   for (pass = 1; pass <= max_passes; ++pass) {
-    KV_CHECK_CUDA(h, cudaMemsetAsync(h->red, 0, 2 * sizeof(unsigned long long), s));
     { KvPhase ph(h, KV_PH_DIV, 1); kv_launch_divergence(h, src, h->tpd_a, s); }
     if (mixed)
       kv_launch_poisson_mixed(h, h->tpd_a, phi, st != nullptr, 1, s);  // slices written by the divergence
     else
       kv_launch_poisson(h, h->tpd_a, h->tpd_a, s);
-    { KvPhase ph(h, KV_PH_CORRECT, 1); kv_launch_correct(h, src, phi, yvel, p, pass > 1, s, want ? 1 : 0); }
+    {
+      KvPhase ph(h, KV_PH_CORRECT, 2);
+      kv_launch_correct(h, src, phi, yvel, p, pass > 1, s, 1);
+      kv_launch_guard_close(h, tol, literal ? 0 : 1, s);
+    }
     kv_status ks = check_launch(h, "SIMPLE pass");
     if (ks != KV_OK) return ks;
     if (!want) break;
-    unsigned long long r[2];
-    KV_CHECK_CUDA(h, cudaMemcpyAsync(r, h->red, sizeof r, cudaMemcpyDeviceToHost, s));
+    double last[3];
+    KV_CHECK_CUDA(h, cudaMemcpyAsync(last, &h->guard->last_maxdiv, sizeof last, cudaMemcpyDeviceToHost, s));
     KV_CHECK_CUDA(h, cudaStreamSynchronize(s));
-    maxdiv = bits_to_double(r[0]);
-    const double vmax = bits_to_double(r[1]);
-    rel = vmax > 0 ? maxdiv * hmin / vmax : 0.0;
-    if (rel < tol || pass == max_passes) break;
+    maxdiv = last[0];
+    rel = last[2];
+    finite = std::isfinite(last[0]) && std::isfinite(last[1]) && std::isfinite(last[2]);
+    if (!finite || rel < tol || pass == max_passes) break;
     // next pass: project the corrected field again (copy it back as the new v*)
     KV_CHECK_CUDA(h, cudaMemcpyAsync(h->vstar, yvel, 3 * h->P * sizeof(double), cudaMemcpyDeviceToDevice, s));
     src = h->vstar;
@@ -344,7 +360,10 @@ kv_status simple_project(kv_grid* h, double* yvel, double* p, kv_stats* st) {
       if (de) return fail(h, KV_ERR_CUDA, "a bounded wait in a tensor-core kernel expired");
     }
   }
-  if (want && max_passes > 1 && !(rel < tol))
+  if (want && !finite)
+    return fail(h, KV_ERR_ARG,
+                "non-finite velocity or divergence after the projection (NaN or Inf in x or in the base flow)");
+  if (literal && !(rel < tol))
     return fail(h, KV_ERR_NOT_CONVERGED, "SIMPLE did not reach the tolerance in max_passes passes");
   return KV_OK;
 }
@@ -503,12 +522,14 @@ kv_status kv_create_grid(const kv_grid_desc* desc, void* stream, kv_handle* out)
   const int n[3] = {g.nx, g.ny, g.nz};
   if ((st = dalloc(h, &h->base, 4 * h->P)) || (st = dalloc(h, &h->coef, (size_t)KV_NCOEF * h->P)) ||
       (st = dalloc(h, &h->vstar, 3 * h->P)) ||
-      (st = dalloc(h, &h->tpd_a, h->Nc)) || (st = dalloc(h, &h->tpd_b, h->Nc)) || (st = dalloc(h, &h->red, 2))) {
+      (st = dalloc(h, &h->tpd_a, h->Nc)) || (st = dalloc(h, &h->tpd_b, h->Nc)) || (st = dalloc(h, &h->guard, 1))) {
     g_create_error = h->err;
     free_all(h);
     delete h;
     return st;
   }
+  cudaMemset(h->guard, 0, sizeof(KvGuardDev));
+  h->red = reinterpret_cast<unsigned long long*>(h->guard);  // guard->red, its first member
   h->hmin = fmin(g.hx, fmin(g.hy, g.hz));
   const bool stretched = desc->stretch != 0.0;
   std::vector<double> fwdm[3], invm[3], tabs;
@@ -632,10 +653,19 @@ kv_status kv_field_len(kv_handle h, size_t* field_len) {
   return KV_OK;
 }
 
-kv_status kv_set_base_flow(kv_handle h, const double* base) {
+kv_status kv_field_sizes(kv_handle h, size_t* u, size_t* v, size_t* w, size_t* cell) {
   if (!h) return KV_ERR_ARG;
-  if (!base) return fail(h, KV_ERR_ARG, "kv_set_base_flow: base is NULL");
-  KV_CHECK_CUDA(h, cudaMemcpyAsync(h->base, base, 4 * h->P * sizeof(double), cudaMemcpyDeviceToDevice, h->s));
+  if (!u && !v && !w && !cell) return fail(h, KV_ERR_ARG, "kv_field_sizes: every output is NULL");
+  // one padded layout serves all four fields (the face fields keep their unused index n+1)
+  if (u) *u = h->P;
+  if (v) *v = h->P;
+  if (w) *w = h->P;
+  if (cell) *cell = h->P;
+  return KV_OK;
+}
+
+// The base state is in h->base: assemble the coefficients of J for it (and their FP32 pairs).
+static kv_status base_flow_ready(kv_grid* h) {
   kv_launch_assemble(h, h->base, h->coef, h->s);
   if (h->d.precision == KV_PREC_MIXED) {
     if (!h->coef_df) {
@@ -656,6 +686,81 @@ kv_status kv_set_base_flow(kv_handle h, const double* base) {
   if (ks != KV_OK) return ks;
   h->has_base = true;
   if (!h->tuned) return autotune_apply(h);
+  return KV_OK;
+}
+
+kv_status kv_set_base_flow(kv_handle h, const double* U, const double* V, const double* W, const double* Theta) {
+  if (!h) return KV_ERR_ARG;
+  if (!U || !V || !W || !Theta) return fail(h, KV_ERR_ARG, "kv_set_base_flow: NULL field");
+  const double* f[4] = {U, V, W, Theta};
+  for (int q = 0; q < 4; ++q)
+    KV_CHECK_CUDA(h, cudaMemcpyAsync(h->base + (size_t)q * h->P, f[q], h->P * sizeof(double),
+                                     cudaMemcpyDeviceToDevice, h->s));
+  return base_flow_ready(h);
+}
+
+kv_status kv_set_base_flow_packed(kv_handle h, const double* base) {
+  if (!h) return KV_ERR_ARG;
+  if (!base) return fail(h, KV_ERR_ARG, "kv_set_base_flow_packed: base is NULL");
+  KV_CHECK_CUDA(h, cudaMemcpyAsync(h->base, base, 4 * h->P * sizeof(double), cudaMemcpyDeviceToDevice, h->s));
+  return base_flow_ready(h);
+}
+
+kv_status kv_set_tuning(kv_handle h, const int* cfg) {
+  if (!h) return KV_ERR_ARG;
+  if (!cfg) return fail(h, KV_ERR_ARG, "kv_set_tuning: cfg is NULL");
+  const bool mixed = h->d.precision == KV_PREC_MIXED;
+  const int bx = cfg[0], by = cfg[1];
+  if (bx < 1 || by < 1 || bx * by > 256 || (bx * by) % 32 != 0)
+    return fail(h, KV_ERR_ARG, "kv_set_tuning: the FP64 operator block needs bx, by >= 1, bx * by <= 256 and a "
+                               "multiple of 32");
+  int dv = -1, dbx = -1, dby = -1;
+  if (mixed) {
+    dv = cfg[2];
+    dbx = cfg[3];
+    dby = cfg[4];
+    if (dv == 0) {
+      if ((dbx != 32 && dbx != 64 && dbx != 128) || dby < 1 || dbx * 4 * dby > 512)
+        return fail(h, KV_ERR_ARG, "kv_set_tuning: the split-pass operator needs cells per row 32, 64 or 128 and "
+                                   "cells x 4 x rows <= 512");
+    } else if (dv == 1) {
+      if (dby < 1 || dby > 1024)
+        return fail(h, KV_ERR_ARG, "kv_set_tuning: the march needs 1..1024 planes per block");
+      if (4 * h->P >= (size_t(1) << 31))
+        return fail(h, KV_ERR_ARG, "kv_set_tuning: the march indexes a packed vector with 32 bits; this grid is too "
+                                   "large for it");
+      dbx = 0;
+    } else {
+      return fail(h, KV_ERR_ARG, "kv_set_tuning: cfg[2] (the double-float operator variant) must be 0 or 1");
+    }
+  }
+  h->apply_bx = bx;
+  h->apply_by = by;
+  if (mixed) {
+    h->df_variant = dv;
+    h->df_bx = dbx;
+    h->df_by = dby;
+  }
+  h->tuned = true;
+  h->pinned = true;
+  return KV_OK;
+}
+
+kv_status kv_guard_read(kv_handle h, kv_guard* out, int reset) {
+  if (!h) return KV_ERR_ARG;
+  if (!out) return fail(h, KV_ERR_ARG, "kv_guard_read: out is NULL");
+  KvGuardDev gd;
+  KV_CHECK_CUDA(h, cudaMemcpyAsync(&gd, h->guard, sizeof gd, cudaMemcpyDeviceToHost, h->s));
+  KV_CHECK_CUDA(h, cudaStreamSynchronize(h->s));
+  out->checks = (long long)gd.checks;
+  out->failed = (long long)gd.failed;
+  out->nonfinite = (long long)gd.nonfinite;
+  out->worst_rel_div = gd.worst_rel;
+  if (reset) {
+    // the counters and figures; red belongs to a pass in progress and is cleared by its close
+    KV_CHECK_CUDA(h, cudaMemsetAsync(&h->guard->checks, 0, sizeof(KvGuardDev) - offsetof(KvGuardDev, checks), h->s));
+    KV_CHECK_CUDA(h, cudaStreamSynchronize(h->s));
+  }
   return KV_OK;
 }
 
@@ -763,7 +868,7 @@ kv_status kv_arnoldi_step(kv_handle h, double* V, int j, double* h_col) {
     if (s != KV_OK) return s;
     h->partials_cap = need_p;
   }
-  const size_t need_h = 2 * (size_t)nq + 4;
+  const size_t need_h = 3 * (size_t)nq + 6;
   if (h->hdev_cap < need_h) {
     cudaFree(h->hdev);
     h->hdev = nullptr;
@@ -777,8 +882,10 @@ kv_status kv_arnoldi_step(kv_handle h, double* V, int j, double* h_col) {
   if (s != KV_OK) return s;
   double* h1 = h->hdev;               // [0, nq): first pass; [nq]: ||w||^2 before
   double* h2 = h->hdev + nq + 1;      // [nq+1, 2nq+1): second pass; [2nq+1]: ||w||^2 after pass 1
-  double* nrm = h->hdev + 2 * nq + 2; // ||w||^2 after the second update
-  std::vector<double> hh(2 * (size_t)nq + 3, 0.0);
+  double* nrm = h->hdev + 2 * nq + 2; // ||w||^2 after the second update (unfused path)
+  double* hcol = h->hdev + 2 * nq + 3;  // [2nq+3, 3nq+4): the Hessenberg column (fused path)
+  int* flag = reinterpret_cast<int*>(h->hdev + 3 * nq + 4);  // second update applied (fused path)
+  std::vector<double> hh(need_h, 0.0);
   if (nq <= kv_fused_cgs_max()) {
     // mixed precision: sweeps 1 and 2 in double-float on the FP32 pipe
     const int df = h->d.precision == KV_PREC_MIXED;
@@ -787,7 +894,9 @@ kv_status kv_arnoldi_step(kv_handle h, double* V, int j, double* h_col) {
     // first update, measured. Sweep 3 (w -= V h2) is applied when they exceed the rounding level
     // of the sweep arithmetic relative to ||w|| (2^-46 for the double-float sweeps, 2^-50 in
     // FP64); below it the second update cannot improve the orthogonality. (ARPACK's DGKS test
-    // decides from ||w|| alone because it has not computed h2; here sweep 2 has.)
+    // decides from ||w|| alone because it has not computed h2; here sweep 2 has.) The decision
+    // and the Hessenberg column are formed on the device, so the step synchronises once, at its
+    // end, to return the column.
     {
       KvPhase ph(h, KV_PH_GS_DOTS, 2);
       kv_launch_dots_norm(V, L, nq, w, L, h->partials, h1, h1 + nq, df, h->s);
@@ -796,37 +905,24 @@ kv_status kv_arnoldi_step(kv_handle h, double* V, int j, double* h_col) {
       KvPhase ph(h, KV_PH_GS_UPDATE, 2);
       kv_launch_update_dot(V, L, nq, h1, w, L, h->partials, h2, df, h->s);
     }
+    {
+      KvPhase ph(h, KV_PH_ARNOLDI, 2);
+      kv_launch_gs_decide(h1, h2, nq, df ? 0x1p-46 : 0x1p-50, h->d.cgs_passes == 2, hcol, flag, h->s);
+      kv_launch_update_small_scale(V, L, nq, h2, w, L, h->s, flag);
+    }
     s = check_launch(h, "arnoldi");
     if (s != KV_OK) return s;
-    KV_CHECK_CUDA(h, cudaMemcpyAsync(hh.data(), h->hdev, hh.size() * sizeof(double), cudaMemcpyDeviceToHost, h->s));
+    KV_CHECK_CUDA(h, cudaMemcpyAsync(hh.data(), h->hdev, need_h * sizeof(double), cudaMemcpyDeviceToHost, h->s));
     KV_CHECK_CUDA(h, cudaStreamSynchronize(h->s));
-    const double before = hh[nq], after = hh[2 * nq + 1];
-    if (df && std::isnan(before))
+    if (df && std::isnan(hh[nq]))
       return fail(h, KV_ERR_ARG,
                   "kv_arnoldi_step: the new vector has entries outside the mixed-precision Gram-Schmidt range "
                   "(NaN, Inf or |x| >= 2^48); V[j+1] is undefined");
-    double h2n = 0.0;
-    for (int q = 0; q < nq; ++q) h2n += hh[nq + 1 + q] * hh[nq + 1 + q];
-    const double theta = df ? 0x1p-46 : 0x1p-50;
-    const bool reorth = h->d.cgs_passes == 2 || !(h2n <= theta * theta * after);
-    {
-      KvPhase ph(h, KV_PH_ARNOLDI, 1);
-      if (reorth)
-        kv_launch_update_small_scale(V, L, nq, h2, w, L, h->s);
-      else
-        kv_launch_scale_inv_sqrt(w, L, h2 + nq, h->s);
-    }
-    s = check_launch(h, "arnoldi");
-    if (s != KV_OK) return s;
-    if (!reorth) {
-      for (int q = 0; q < nq; ++q) h_col[q] = hh[q];
-      h_col[nq] = sqrt(after);
-      return KV_OK;
-    }
-    // beta^2 = ||w1||^2 - ||h2||^2 (V orthonormal), the factor the fused sweep applied
-    for (int q = 0; q < nq; ++q) h_col[q] = hh[q] + hh[nq + 1 + q];
-    const double b2 = after - h2n;
-    h_col[nq] = b2 > 0.0 ? sqrt(b2) : 0.0;
+    int upd = 0;
+    memcpy(&upd, &hh[3 * (size_t)nq + 4], sizeof upd);
+    h->gs_steps += 1;
+    h->gs_second += upd != 0;
+    for (int q = 0; q <= nq; ++q) h_col[q] = hh[2 * (size_t)nq + 3 + q];
     return KV_OK;
   } else {
     const int md = (nq + 7) / 8 + 1;  // multidot sweeps + finalize
@@ -969,7 +1065,16 @@ kv_status kv_profile_enable(kv_handle h, int on) {
     h->prof_n[q] = 0;
     h->launches[q] = 0;
   }
+  h->gs_steps = 0;
+  h->gs_second = 0;
   h->prof_on = on != 0;
+  return KV_OK;
+}
+
+kv_status kv_arnoldi_counts(kv_handle h, long long* steps, long long* second_updates) {
+  if (!h) return KV_ERR_ARG;
+  if (steps) *steps = h->gs_steps;
+  if (second_updates) *second_updates = h->gs_second;
   return KV_OK;
 }
 

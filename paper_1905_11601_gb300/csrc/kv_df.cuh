@@ -7,7 +7,8 @@
 // within 2^-48 of its magnitude without a systematic bias (a truncated tail would scale every
 // value by 1 - O(2^-47), and those errors add up over a long inner product instead of averaging
 // out). Values below 2^-103 in magnitude become 0 (an absolute change of at most
-// 2^-103); values at or above 2^128 are outside the pair's range (callers bound their inputs).
+// 2^-103); values at or above 2^128, Inf and NaN are outside the pair's range and become a NaN
+// pair, so that a non-finite input shows up as a non-finite result instead of vanishing.
 // Products are formed as head*head (exact, with the FMA error term) plus the two cross terms,
 // and sums with an exact TwoSum on the leading words, so each operation carries a relative
 // error of about 2^-46 of the magnitudes involved.
@@ -34,16 +35,21 @@ __device__ __forceinline__ DF df_split(double x) {
     const unsigned int m = ((lo & 0x1FFFFFFFu) + 0x20u) >> 6;
     r.h = __uint_as_float(hb);
     r.l = __fsub_rn(__uint_as_float(eb + m), __uint_as_float(eb));
+  } else if (ex >= 1151u) {  // |x| >= 2^128, Inf, NaN
+    r.h = __uint_as_float(0x7FC00000u);
+    r.l = r.h;
   }
   return r;
 }
 
-// exact FP32 -> FP64 by bit manipulation (no FP64 instruction); FP32 denormals map to 0
+// exact FP32 -> FP64 by bit manipulation (no FP64 instruction); FP32 denormals map to 0, Inf
+// and NaN to Inf and NaN
 __device__ __forceinline__ double df_f2d(float f) {
   const unsigned int b = __float_as_uint(f);
   const unsigned int fe = (b >> 23) & 0xFFu;
   if (fe == 0u) return 0.0;
-  const unsigned int hi = (b & 0x80000000u) | ((fe - 127u + 1023u) << 20) | ((b & 0x7FFFFFu) >> 3);
+  const unsigned int eb = fe == 0xFFu ? 0x7FFu : fe - 127u + 1023u;
+  const unsigned int hi = (b & 0x80000000u) | (eb << 20) | ((b & 0x7FFFFFu) >> 3);
   return __hiloint2double((int)hi, (int)((b & 0x7u) << 29));
 }
 

@@ -58,6 +58,18 @@ struct KvStretch {
   int swdo[3] = {0, 0, 0};      // offset of each axis' tables in swd
 };
 
+// The SIMPLE stopping test of every one-pass Krylov vector, evaluated on the device (no host
+// synchronisation) and accumulated until the host reads it (kv_guard_read): the correction
+// kernel reduces max |D v| and max |v| into red (bit patterns of non-negative doubles, so NaN
+// compares above every finite value and Inf), and k_guard_close turns them into the relative
+// residual, counts the check, and clears red for the next one.
+struct KvGuardDev {
+  unsigned long long red[2];  // max |D v|, max |v| of the pass in progress (bits)
+  unsigned long long checks, failed, nonfinite;
+  double worst_rel;           // largest finite max |D v| h_min / max |v|
+  double last_maxdiv, last_vmax, last_rel;  // the last pass closed
+};
+
 struct kv_grid {
   kv_grid_desc d;
   KvGeom g;
@@ -81,7 +93,9 @@ struct kv_grid {
   float2* swd = nullptr;    // stretched KV_PREC_MIXED grid: the KV_SWD_* tables
   float2* coef_dfp = nullptr; // stretched KV_PREC_MIXED grid, KV_NCOEF_DFP * P: plus coefficients as pairs
   double hmin = 0.0;        // smallest cell width (the SIMPLE test)
-  unsigned long long* red = nullptr;  // [0] max|D v| bits, [1] max|v| bits
+  unsigned long long* red = nullptr;  // [0] max|D v| bits, [1] max|v| bits (guard->red, or the
+                                      // allocation-free entry point's own pair)
+  KvGuardDev* guard = nullptr;        // the device-side SIMPLE test (red points into it)
   double* partials = nullptr;         // Arnoldi block partial sums
   size_t partials_cap = 0;            // in doubles
   double* hdev = nullptr;             // Arnoldi coefficients on the device
@@ -110,6 +124,7 @@ struct kv_grid {
 
   // launch counting (always) and per-phase CUDA-event timing (when profiling is on)
   long long launches[KV_NPHASE] = {};
+  long long gs_steps = 0, gs_second = 0;  // fused Arnoldi steps, and of them those with the second update
   bool prof_on = false;
   std::vector<cudaEvent_t> ev_pool;
   struct Pending { int phase; cudaEvent_t a, b; };
@@ -132,6 +147,7 @@ struct kv_grid {
   int apply_bx = 32, apply_by = 8;
   int df_variant = 0, df_bx = 32, df_by = 2;  // the mixed path's double-float operator (kv_stencil.cu)
   bool tuned = false;
+  bool pinned = false;  // kv_set_tuning fixed the configuration: the autotuner does not run
 
   std::string err;
 };
@@ -225,6 +241,10 @@ void kv_launch_divergence(const kv_grid* h, const double* vel, double* b, cudaSt
 // with check != 0 also reduces max |D out_vel| and max |out_vel| into h->red (the SIMPLE test).
 void kv_launch_correct(const kv_grid* h, const double* vstar, const double* phi, double* out_vel,
                        double* p, int accumulate_p, cudaStream_t s, int check = 1);
+// Closes one SIMPLE test on the device: reads h->guard->red, stores the pass's figures in
+// guard->last_*, counts the check when record != 0 (failed: rel >= tol; nonfinite: NaN or Inf),
+// and clears red.
+void kv_launch_guard_close(const kv_grid* h, double tol, int record, cudaStream_t s);
 
 // kv_tpd.cu: phi = L^+ b by Eq (18), six per-axis contractions; b and phi compact n^3
 // (x fastest). b is overwritten (used as scratch).
@@ -254,4 +274,10 @@ void kv_launch_dots_norm(const double* V, size_t ld, int nq, const double* w, si
 void kv_launch_update_dot(const double* V, size_t ld, int nq, const double* c, double* w, size_t len,
                           double* partials, double* h2, int df, cudaStream_t s);
 void kv_launch_update_small_scale(const double* V, size_t ld, int nq, const double* c, double* w, size_t len,
-                                  cudaStream_t s);
+                                  cudaStream_t s, const int* flag = nullptr);
+// The second-update decision of the fused Gram-Schmidt step on the device: from h1 (first pass,
+// h1[nq] = ||w||^2 before it) and h2 (second pass, h2[nq] = ||w||^2 after the first update),
+// *flag = force || ||h2||^2 > theta^2 ||w||^2, and hcol[0..nq] = the Hessenberg column that
+// kv_launch_update_small_scale (given flag) then produces.
+void kv_launch_gs_decide(const double* h1, const double* h2, int nq, double theta, int force, double* hcol,
+                         int* flag, cudaStream_t s);

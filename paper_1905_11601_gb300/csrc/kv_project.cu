@@ -36,8 +36,36 @@ __global__ void __launch_bounds__(256) k_divergence(KvGeom g, KvStretch S, const
   b[(i - 1) + (size_t)g.nx * ((j - 1) + (size_t)g.ny * (k - 1))] = d;
 }
 
-__device__ __forceinline__ void atomic_max_nonneg(unsigned long long* addr, double v) {
-  atomicMax(addr, (unsigned long long)__double_as_longlong(v));
+// |v| as the bit pattern of a non-negative double: these order like the values, with +Inf above
+// every finite value and NaN above +Inf, so a maximum over bit patterns propagates NaN (fmax
+// would drop it)
+__device__ __forceinline__ unsigned long long abs_bits(double v) {
+  return (unsigned long long)__double_as_longlong(fabs(v));
+}
+
+// max over the block of two bit patterns, then one atomicMax each into red[0], red[1]
+__device__ __forceinline__ void block_max2(unsigned long long a, unsigned long long b,
+                                           unsigned long long* __restrict__ red) {
+  for (int o = 16; o > 0; o >>= 1) {
+    a = max(a, __shfl_xor_sync(0xffffffffu, a, o));
+    b = max(b, __shfl_xor_sync(0xffffffffu, b, o));
+  }
+  __shared__ unsigned long long sa[32], sb[32];
+  const int t = threadIdx.x + blockDim.x * threadIdx.y, warp = t >> 5, lane = t & 31;
+  if (lane == 0) {
+    sa[warp] = a;
+    sb[warp] = b;
+  }
+  __syncthreads();
+  if (t == 0) {
+    const int nw = (blockDim.x * blockDim.y + 31) >> 5;
+    for (int q = 1; q < nw; ++q) {
+      a = max(a, sa[q]);
+      b = max(b, sb[q]);
+    }
+    atomicMax(red, a);
+    atomicMax(red + 1, b);
+  }
 }
 
 template <bool STR>
@@ -73,7 +101,7 @@ __global__ void __launch_bounds__(256) k_correct(KvGeom g, KvStretch S, const do
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   const int j = blockIdx.y * blockDim.y + threadIdx.y;
   const int k = blockIdx.z;
-  double dmax = 0.0, vmax = 0.0;
+  unsigned long long dmax = 0, vmax = 0;
   if (i < g.X && j < g.Y) {
     Corr<STR> C{g, S, vs, phi, P};
     const int e = C.at(i, j, k);
@@ -82,12 +110,12 @@ __global__ void __launch_bounds__(256) k_correct(KvGeom g, KvStretch S, const do
     out[P + e] = vr;
     out[2 * P + e] = wr;
     const bool cell = i >= 1 && i <= g.nx && j >= 1 && j <= g.ny && k >= 1 && k <= g.nz;
-    if (check) vmax = fmax(fabs(ur), fmax(fabs(vr), fabs(wr)));
+    if (check) vmax = max(abs_bits(ur), max(abs_bits(vr), abs_bits(wr)));
     if (check && cell) {
       const double d = (ur - C.u(i - 1, j, k)) * inv_w<STR, 0, KV_SW_IDC>(g, S, i) +
                        (vr - C.v(i, j - 1, k)) * inv_w<STR, 1, KV_SW_IDC>(g, S, j) +
                        (wr - C.w(i, j, k - 1)) * inv_w<STR, 2, KV_SW_IDC>(g, S, k);
-      dmax = fabs(d);
+      dmax = abs_bits(d);
     }
     if (p) {
       if (cell)
@@ -97,27 +125,7 @@ __global__ void __launch_bounds__(256) k_correct(KvGeom g, KvStretch S, const do
     }
   }
   if (!check) return;
-  // block reduction of the two maxima, one atomic each per block
-  for (int o = 16; o > 0; o >>= 1) {
-    dmax = fmax(dmax, __shfl_xor_sync(0xffffffffu, dmax, o));
-    vmax = fmax(vmax, __shfl_xor_sync(0xffffffffu, vmax, o));
-  }
-  __shared__ double sd[8], sv[8];
-  const int t = threadIdx.x + blockDim.x * threadIdx.y, warp = t >> 5, lane = t & 31;
-  if (lane == 0) {
-    sd[warp] = dmax;
-    sv[warp] = vmax;
-  }
-  __syncthreads();
-  if (t == 0) {
-    double a = sd[0], b = sv[0];
-    for (int q = 1; q < 8; ++q) {
-      a = fmax(a, sd[q]);
-      b = fmax(b, sv[q]);
-    }
-    atomic_max_nonneg(red, a);
-    atomic_max_nonneg(red + 1, b);
-  }
+  block_max2(dmax, vmax, red);  // one atomic each per block
 }
 
 // ---- the same two kernels in double-float arithmetic (mixed precision; kv_df.cuh) ----------
@@ -157,108 +165,172 @@ __global__ void __launch_bounds__(256) k_divergence_df(KvGeom g, KvStretch S, co
   if (xs) kv_store_bf16x3(xs, slice, ((size_t)(k - 1) * g.ny + (j - 1)) * pitch + (i - 1), __fadd_rn(d.h, d.l));
 }
 
-template <bool STR>
-struct CorrDF {
-  KvGeom g;
-  KvStretch S;
-  const double* __restrict__ vs;
-  const double* __restrict__ phi;
-  size_t P;
-  float2 ihx, ihy, ihz;
-  __device__ __forceinline__ DF ph(int i, int j, int k) const {  // padded cell index
-    return df_split(__ldg(phi + (i - 1) + (size_t)g.nx * ((j - 1) + (size_t)g.ny * (k - 1))));
-  }
-  __device__ __forceinline__ int at(int i, int j, int k) const { return i + g.X * (j + g.Y * k); }
-  __device__ __forceinline__ DF u(int i, int j, int k) const {
-    if (!(i >= 1 && i <= g.nx - 1 && j >= 1 && j <= g.ny && k >= 1 && k <= g.nz)) return DF{0.0f, 0.0f};
-    return df_sub(df_split(__ldg(vs + at(i, j, k))),
-                  df_mul(df_sub(ph(i + 1, j, k), ph(i, j, k)), inv_w_df<STR, 0, KV_SWD_IDF>(g, S, i, ihx)));
-  }
-  __device__ __forceinline__ DF v(int i, int j, int k) const {
-    if (!(i >= 1 && i <= g.nx && j >= 1 && j <= g.ny - 1 && k >= 1 && k <= g.nz)) return DF{0.0f, 0.0f};
-    return df_sub(df_split(__ldg(vs + P + at(i, j, k))),
-                  df_mul(df_sub(ph(i, j + 1, k), ph(i, j, k)), inv_w_df<STR, 1, KV_SWD_IDF>(g, S, j, ihy)));
-  }
-  __device__ __forceinline__ DF w(int i, int j, int k) const {
-    if (!(i >= 1 && i <= g.nx && j >= 1 && j <= g.ny && k >= 1 && k <= g.nz - 1)) return DF{0.0f, 0.0f};
-    return df_sub(df_split(__ldg(vs + 2 * P + at(i, j, k))),
-                  df_mul(df_sub(ph(i, j, k + 1), ph(i, j, k)), inv_w_df<STR, 2, KV_SWD_IDF>(g, S, k, ihz)));
-  }
-};
-
 __device__ __forceinline__ float df_abs_hi(const DF a) { return fabsf(__fadd_rn(a.h, a.l)); }
 
-// CHECK = 0: the corrected faces and p only, each input loaded and split once, inverse spacings
-// passed as FP32 pairs (ih). CHECK = 1 adds max |D v| and max |v| for the SIMPLE test.
-template <int CHECK, bool STR>
+// The corrected faces and p only (no SIMPLE test), each input loaded and split once, inverse
+// spacings passed as FP32 pairs (ih).
+template <bool STR>
 __global__ void __launch_bounds__(256) k_correct_df(KvGeom g, KvStretch S, const double* __restrict__ vs,
                                                     const double* __restrict__ phi, size_t P,
                                                     double* __restrict__ out, double* __restrict__ p, int acc_p,
-                                                    unsigned long long* __restrict__ red, float2 ihx, float2 ihy,
-                                                    float2 ihz) {
+                                                    float2 ihx, float2 ihy, float2 ihz) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   const int j = blockIdx.y * blockDim.y + threadIdx.y;
   const int k = blockIdx.z;
-  double dmax = 0.0, vmax = 0.0;
-  if (i < g.X && j < g.Y) {
-    const int e = i + g.X * (j + g.Y * k);
-    const bool cell = i >= 1 && i <= g.nx && j >= 1 && j <= g.ny && k >= 1 && k <= g.nz;
-    // interior faces (the wall-normal faces i = nx etc. stay 0)
-    const bool du = cell && i <= g.nx - 1, dv = cell && j <= g.ny - 1, dw = cell && k <= g.nz - 1;
-    const size_t c = (size_t)(i - 1) + (size_t)g.nx * ((j - 1) + (size_t)g.ny * (k - 1));
-    const size_t cy = g.nx, cz = (size_t)g.nx * g.ny;
-    const double p0d = cell ? __ldg(phi + c) : 0.0;
-    const DF p0 = df_split(p0d);
-    DF ur{0.0f, 0.0f}, vr{0.0f, 0.0f}, wr{0.0f, 0.0f};
-    if (du)
-      ur = df_sub(df_split(__ldg(vs + e)),
-                  df_mul(df_sub(df_split(__ldg(phi + c + 1)), p0), inv_w_df<STR, 0, KV_SWD_IDF>(g, S, i, ihx)));
-    if (dv)
-      vr = df_sub(df_split(__ldg(vs + P + e)),
-                  df_mul(df_sub(df_split(__ldg(phi + c + cy)), p0), inv_w_df<STR, 1, KV_SWD_IDF>(g, S, j, ihy)));
-    if (dw)
-      wr = df_sub(df_split(__ldg(vs + 2 * P + e)),
-                  df_mul(df_sub(df_split(__ldg(phi + c + cz)), p0), inv_w_df<STR, 2, KV_SWD_IDF>(g, S, k, ihz)));
-    out[e] = df_value(ur);
-    out[P + e] = df_value(vr);
-    out[2 * P + e] = df_value(wr);
-    if (CHECK) {
-      vmax = (double)fmaxf(df_abs_hi(ur), fmaxf(df_abs_hi(vr), df_abs_hi(wr)));
+  if (i >= g.X || j >= g.Y) return;
+  const int e = i + g.X * (j + g.Y * k);
+  const bool cell = i >= 1 && i <= g.nx && j >= 1 && j <= g.ny && k >= 1 && k <= g.nz;
+  // interior faces (the wall-normal faces i = nx etc. stay 0)
+  const bool du = cell && i <= g.nx - 1, dv = cell && j <= g.ny - 1, dw = cell && k <= g.nz - 1;
+  const size_t c = (size_t)(i - 1) + (size_t)g.nx * ((j - 1) + (size_t)g.ny * (k - 1));
+  const size_t cy = g.nx, cz = (size_t)g.nx * g.ny;
+  const double p0d = cell ? __ldg(phi + c) : 0.0;
+  const DF p0 = df_split(p0d);
+  DF ur{0.0f, 0.0f}, vr{0.0f, 0.0f}, wr{0.0f, 0.0f};
+  if (du)
+    ur = df_sub(df_split(__ldg(vs + e)),
+                df_mul(df_sub(df_split(__ldg(phi + c + 1)), p0), inv_w_df<STR, 0, KV_SWD_IDF>(g, S, i, ihx)));
+  if (dv)
+    vr = df_sub(df_split(__ldg(vs + P + e)),
+                df_mul(df_sub(df_split(__ldg(phi + c + cy)), p0), inv_w_df<STR, 1, KV_SWD_IDF>(g, S, j, ihy)));
+  if (dw)
+    wr = df_sub(df_split(__ldg(vs + 2 * P + e)),
+                df_mul(df_sub(df_split(__ldg(phi + c + cz)), p0), inv_w_df<STR, 2, KV_SWD_IDF>(g, S, k, ihz)));
+  out[e] = df_value(ur);
+  out[P + e] = df_value(vr);
+  out[2 * P + e] = df_value(wr);
+  if (p) {
+    if (cell)
+      p[e] = (acc_p ? p[e] : 0.0) + p0d;
+    else if (!acc_p)
+      p[e] = 0.0;
+  }
+}
+
+// The double-float correction with the SIMPLE test, marching in z (the form the one-pass
+// evaluations use). A block of 32 x MC_Y threads owns 31 x (MC_Y - 1) face columns: lane 0 and
+// row 0 are a halo that forms the corrected faces u(i-1) and v(j-1) its neighbours' divergence
+// needs (handed over by warp shuffle and shared memory) and writes nothing; w(k-1) is the
+// previous plane's value, kept in a register. So each corrected face is formed once (plus the
+// halo) and max |D v| costs one double-float divergence per cell, with the same rounding of the
+// faces as the stored velocity. The loads of plane k+1 are issued before plane k is computed.
+// Outputs as k_correct_df.
+constexpr int MC_Y = 16;
+struct CorrIn {
+  double u, v, w, c, cx, cy, cz;  // v* at (i, j, k); phi at the cell and its three plus neighbours
+};
+template <bool STR>
+__global__ void __launch_bounds__(32 * MC_Y) k_correct_df_march(KvGeom g, KvStretch S, const double* __restrict__ vs,
+                                                              const double* __restrict__ phi, size_t P,
+                                                              double* __restrict__ out, double* __restrict__ p,
+                                                              int acc_p, unsigned long long* __restrict__ red,
+                                                              float2 ihx, float2 ihy, float2 ihz, int kc) {
+  __shared__ float2 vsh[2][MC_Y][32];
+  const int tx = threadIdx.x, ty = threadIdx.y;
+  const int i = blockIdx.x * 31 + tx - 1;  // -1 for the first block's halo lane
+  const int j = blockIdx.y * (MC_Y - 1) + ty - 1;
+  const int k0 = blockIdx.z * kc, k1 = min(k0 + kc, g.Z);
+  const bool own = tx >= 1 && ty >= 1 && i < g.X && j < g.Y;
+  const bool col = i >= 1 && i <= g.nx && j >= 1 && j <= g.ny;  // a column of cells
+  const size_t cy = g.nx, cz = (size_t)g.nx * g.ny;
+  const size_t e0 = (size_t)i + (size_t)g.X * (size_t)j;                  // padded index at k = 0
+  const size_t c0 = col ? (size_t)(i - 1) + cy * (size_t)(j - 1) : 0;   // compact index at k = 1, minus cz
+  // the inputs of plane k (zero where the plane has no cell in this column); the loads stay
+  // inside the arrays: phi is read at compact cells and their plus neighbours inside the grid
+  auto load = [&](int k, CorrIn& r) {
+    r = CorrIn{0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+    if (!col || k < 1 || k > g.nz) return;
+    const size_t e = e0 + (size_t)g.X * g.Y * k, c = c0 + cz * (size_t)(k - 1);
+    r.c = __ldg(phi + c);
+    if (i <= g.nx - 1) {
+      r.u = __ldg(vs + e);
+      r.cx = __ldg(phi + c + 1);
+    }
+    if (j <= g.ny - 1) {
+      r.v = __ldg(vs + P + e);
+      r.cy = __ldg(phi + c + cy);
+    }
+    if (k <= g.nz - 1) {
+      r.w = __ldg(vs + 2 * P + e);
+      r.cz = __ldg(phi + c + cz);
+    }
+  };
+  // corrected faces at (i, j, k): zero outside the interior faces
+  auto faces = [&](int k, const CorrIn& r, DF& ur, DF& vr, DF& wr) {
+    ur = vr = wr = DF{0.0f, 0.0f};
+    if (!col || k < 1 || k > g.nz) return;
+    const DF p0 = df_split(r.c);
+    if (i <= g.nx - 1)
+      ur = df_sub(df_split(r.u), df_mul(df_sub(df_split(r.cx), p0), inv_w_df<STR, 0, KV_SWD_IDF>(g, S, i, ihx)));
+    if (j <= g.ny - 1)
+      vr = df_sub(df_split(r.v), df_mul(df_sub(df_split(r.cy), p0), inv_w_df<STR, 1, KV_SWD_IDF>(g, S, j, ihy)));
+    if (k <= g.nz - 1)
+      wr = df_sub(df_split(r.w), df_mul(df_sub(df_split(r.cz), p0), inv_w_df<STR, 2, KV_SWD_IDF>(g, S, k, ihz)));
+  };
+  DF wprev{0.0f, 0.0f};
+  CorrIn cur, nxt;
+  if (k0 >= 1) {
+    DF a, b;
+    load(k0 - 1, cur);
+    faces(k0 - 1, cur, a, b, wprev);
+  }
+  load(k0, cur);
+  unsigned long long dmax = 0, vmax = 0;
+  int buf = 0;
+  for (int k = k0; k < k1; ++k, buf ^= 1) {
+    if (k + 1 < k1) load(k + 1, nxt);
+    DF ur, vr, wr;
+    faces(k, cur, ur, vr, wr);
+    vsh[buf][ty][tx] = make_float2(vr.h, vr.l);
+    const DF um{__shfl_up_sync(0xffffffffu, ur.h, 1), __shfl_up_sync(0xffffffffu, ur.l, 1)};
+    __syncthreads();  // one per plane: vsh is double-buffered
+    if (own) {
+      const size_t e = e0 + (size_t)g.X * g.Y * k;
+      out[e] = df_value(ur);
+      out[P + e] = df_value(vr);
+      out[2 * P + e] = df_value(wr);
+      const unsigned int vb = max(__float_as_uint(df_abs_hi(ur)), max(__float_as_uint(df_abs_hi(vr)),
+                                                                      __float_as_uint(df_abs_hi(wr))));
+      vmax = max(vmax, abs_bits(df_f2d(__uint_as_float(vb))));
+      const bool cell = col && k >= 1 && k <= g.nz;
       if (cell) {
-        const CorrDF<STR> C{g, S, vs, phi, P, ihx, ihy, ihz};
-        const DF d = df_add(df_add(df_mul(df_sub(ur, C.u(i - 1, j, k)), inv_w_df<STR, 0, KV_SWD_IDC>(g, S, i, ihx)),
-                                   df_mul(df_sub(vr, C.v(i, j - 1, k)), inv_w_df<STR, 1, KV_SWD_IDC>(g, S, j, ihy))),
-                            df_mul(df_sub(wr, C.w(i, j, k - 1)), inv_w_df<STR, 2, KV_SWD_IDC>(g, S, k, ihz)));
-        dmax = fabs(df_value(d));
+        const float2 vm = vsh[buf][ty - 1][tx];
+        const DF d = df_add(df_add(df_mul(df_sub(ur, um), inv_w_df<STR, 0, KV_SWD_IDC>(g, S, i, ihx)),
+                                   df_mul(df_sub(vr, DF{vm.x, vm.y}), inv_w_df<STR, 1, KV_SWD_IDC>(g, S, j, ihy))),
+                            df_mul(df_sub(wr, wprev), inv_w_df<STR, 2, KV_SWD_IDC>(g, S, k, ihz)));
+        dmax = max(dmax, abs_bits(df_value(d)));
+      }
+      if (p) {
+        if (cell)
+          p[e] = (acc_p ? p[e] : 0.0) + cur.c;
+        else if (!acc_p)
+          p[e] = 0.0;
       }
     }
-    if (p) {
-      if (cell)
-        p[e] = (acc_p ? p[e] : 0.0) + p0d;
-      else if (!acc_p)
-        p[e] = 0.0;
-    }
+    wprev = wr;
+    cur = nxt;
   }
-  if (!CHECK) return;
-  for (int o = 16; o > 0; o >>= 1) {
-    dmax = fmax(dmax, __shfl_xor_sync(0xffffffffu, dmax, o));
-    vmax = fmax(vmax, __shfl_xor_sync(0xffffffffu, vmax, o));
-  }
-  __shared__ double sd[8], sv[8];
-  const int t = threadIdx.x + blockDim.x * threadIdx.y, warp = t >> 5, lane = t & 31;
-  if (lane == 0) {
-    sd[warp] = dmax;
-    sv[warp] = vmax;
-  }
-  __syncthreads();
-  if (t == 0) {
-    double a = sd[0], b = sv[0];
-    for (int q = 1; q < 8; ++q) {
-      a = fmax(a, sd[q]);
-      b = fmax(b, sv[q]);
-    }
-    atomic_max_nonneg(red, a);
-    atomic_max_nonneg(red + 1, b);
+  block_max2(dmax, vmax, red);
+}
+
+// One SIMPLE test closed on the device (one thread): see KvGuardDev.
+__global__ void k_guard_close(KvGuardDev* __restrict__ gd, double hmin, double tol, int record) {
+  const double md = __longlong_as_double((long long)gd->red[0]);
+  const double vm = __longlong_as_double((long long)gd->red[1]);
+  gd->red[0] = 0ull;
+  gd->red[1] = 0ull;
+  const double rel = vm > 0.0 ? md * hmin / vm : (md > 0.0 ? md : 0.0);
+  const bool finite = isfinite(md) && isfinite(vm) && isfinite(rel);
+  gd->last_maxdiv = md;
+  gd->last_vmax = vm;
+  gd->last_rel = finite ? rel : __longlong_as_double(0x7FF8000000000000LL);
+  if (!record) return;
+  gd->checks += 1ull;
+  if (!finite) {
+    gd->nonfinite += 1ull;
+  } else {
+    if (!(rel < tol)) gd->failed += 1ull;
+    if (rel > gd->worst_rel) gd->worst_rel = rel;
   }
 }
 
@@ -291,11 +363,21 @@ void kv_launch_correct(const kv_grid* h, const double* vstar, const double* phi,
   const bool str = h->str.sw != nullptr;
   if (h->d.precision == KV_PREC_MIXED) {
     const float2 cx = pair_of(g.ihx), cy = pair_of(g.ihy), cz = pair_of(g.ihz);
-    auto kern = str ? (check ? k_correct_df<1, true> : k_correct_df<0, true>)
-                    : (check ? k_correct_df<1, false> : k_correct_df<0, false>);
-    kern<<<grid, block, 0, s>>>(g, h->str, vstar, phi, h->P, out_vel, p, accumulate_p, h->red, cx, cy, cz);
+    if (check) {
+      const int kc = 16;
+      dim3 mb(32, MC_Y, 1), mg((g.X + 30) / 31, (g.Y + MC_Y - 2) / (MC_Y - 1), (g.Z + kc - 1) / kc);
+      auto kern = str ? k_correct_df_march<true> : k_correct_df_march<false>;
+      kern<<<mg, mb, 0, s>>>(g, h->str, vstar, phi, h->P, out_vel, p, accumulate_p, h->red, cx, cy, cz, kc);
+      return;
+    }
+    auto kern = str ? k_correct_df<true> : k_correct_df<false>;
+    kern<<<grid, block, 0, s>>>(g, h->str, vstar, phi, h->P, out_vel, p, accumulate_p, cx, cy, cz);
   } else {
     auto kern = str ? k_correct<true> : k_correct<false>;
     kern<<<grid, block, 0, s>>>(g, h->str, vstar, phi, h->P, out_vel, p, accumulate_p, check, h->red);
   }
+}
+
+void kv_launch_guard_close(const kv_grid* h, double tol, int record, cudaStream_t s) {
+  k_guard_close<<<1, 1, 0, s>>>(h->guard, h->hmin, tol, record);
 }

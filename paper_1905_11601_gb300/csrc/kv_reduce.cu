@@ -178,27 +178,51 @@ __global__ void __launch_bounds__(RT) k_update_dot(const double* __restrict__ V,
 // in FP32 from the high words (its error is ~1e-6 of a rounding-size correction) and subtracted
 // in FP64. With V orthonormal and c = V^T w, beta^2 = ||w||^2 - ||c||^2 (c[nq] holds ||w||^2),
 // which needs no further pass over w.
+// With flag (the device-side decision of k_gs_decide) and *flag == 0 the second update is skipped:
+// w = w / sqrt(c[Q]), without reading V.
 template <int Q>
 __global__ void __launch_bounds__(RT) k_update_small_scale(const double* __restrict__ V, size_t ld,
                                                            const double* __restrict__ c, double* __restrict__ w,
-                                                           size_t len) {
+                                                           size_t len, const int* __restrict__ flag) {
   __shared__ float cs[Q];
   __shared__ double finv;
+  const bool upd = flag == nullptr || *flag != 0;
   if (threadIdx.x < Q) cs[threadIdx.x] = (float)c[threadIdx.x];
   if (threadIdx.x == 0) {
     double s = 0.0;
-    for (int q = 0; q < Q; ++q) s = fma(c[q], c[q], s);
+    if (upd)
+      for (int q = 0; q < Q; ++q) s = fma(c[q], c[q], s);
     const double b2 = c[Q] - s;
-    finv = b2 > 0.0 ? 1.0 / sqrt(b2) : 0.0;
+    finv = b2 > 0.0 || isnan(b2) ? 1.0 / sqrt(b2) : 0.0;
   }
   __syncthreads();
   const double f = finv;
+  if (!upd) {
+    for (size_t e = (size_t)blockIdx.x * RT + threadIdx.x; e < len; e += (size_t)gridDim.x * RT) w[e] *= f;
+    return;
+  }
   for (size_t e = (size_t)blockIdx.x * RT + threadIdx.x; e < len; e += (size_t)gridDim.x * RT) {
     float s = 0.0f;
 #pragma unroll
     for (int q = 0; q < Q; ++q) s = fmaf(cs[q], hi_float(__ldg(V + (size_t)q * ld + e)), s);
     w[e] = (w[e] - df_f2d(s)) * f;
   }
+}
+
+// The second-update decision and the Hessenberg column (one thread; nq <= QF): with
+// h2n = ||h2||^2 (sequential FMA, the order k_update_small_scale uses), the update runs when
+// forced or when h2n > theta^2 h2[nq]; the column is h1 + h2 and sqrt(h2[nq] - h2n) then, else
+// h1 and sqrt(h2[nq]).
+__global__ void k_gs_decide(const double* __restrict__ h1, const double* __restrict__ h2, int nq, double theta2,
+                            int force, double* __restrict__ hcol, int* __restrict__ flag) {
+  double h2n = 0.0;
+  for (int q = 0; q < nq; ++q) h2n = fma(h2[q], h2[q], h2n);
+  const double after = h2[nq];
+  const int upd = force || !(h2n <= theta2 * after);
+  *flag = upd;
+  for (int q = 0; q < nq; ++q) hcol[q] = upd ? h1[q] + h2[q] : h1[q];
+  const double b2 = upd ? after - h2n : after;
+  hcol[nq] = b2 > 0.0 || isnan(b2) ? sqrt(b2) : 0.0;  // a NaN norm stays NaN
 }
 
 // ---- double-float Gram-Schmidt sweeps (mixed precision) -------------------------------------
@@ -469,12 +493,17 @@ void kv_launch_update_dot(const double* V, size_t ld, int nq, const double* c, d
   k_finalize<<<nq + 1, RT, 0, s>>>(partials, nb, h2, 0);  // h2[nq] = ||w||^2 after the update
 }
 
+void kv_launch_gs_decide(const double* h1, const double* h2, int nq, double theta, int force, double* hcol,
+                         int* flag, cudaStream_t s) {
+  k_gs_decide<<<1, 1, 0, s>>>(h1, h2, nq, theta * theta, force, hcol, flag);
+}
+
 void kv_launch_update_small_scale(const double* V, size_t ld, int nq, const double* c, double* w, size_t len,
-                                  cudaStream_t s) {
+                                  cudaStream_t s, const int* flag) {
   switch (nq) {
 #define KV_SMALL_CASE(Qn) \
   case Qn:                \
-    k_update_small_scale<Qn><<<wave_blocks<k_update_small_scale<Qn>>(), RT, 0, s>>>(V, ld, c, w, len); \
+    k_update_small_scale<Qn><<<wave_blocks<k_update_small_scale<Qn>>(), RT, 0, s>>>(V, ld, c, w, len, flag); \
     break;
     KV_FOR_EACH_NQ(KV_SMALL_CASE)
 #undef KV_SMALL_CASE

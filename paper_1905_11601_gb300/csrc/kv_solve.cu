@@ -334,7 +334,7 @@ extern "C" kv_status kv_newton(kv_handle h, double* S, double* V, double* work, 
     }
     if (it == p->max_newton) break;
     // the Jacobian at S, then J d = F: GMRES(m) until it converges or saturates, then BiCGstab(2)
-    KV_SOLVE_TRY(kv_set_base_flow(h, S));
+    KV_SOLVE_TRY(kv_set_base_flow_packed(h, S));
     KV_SOLVE_CUDA(h, cudaMemsetAsync(d, 0, L * sizeof(double), h->s));
     kv_solve_stats gs{};
     KV_SOLVE_TRY(kv_gmres(h, F, d, V, p->gmres_m, p->gmres_max_restarts, p->lin_tol, p->gmres_sat, &gs));

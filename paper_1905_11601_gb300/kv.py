@@ -28,7 +28,8 @@ EXPORTS = ("kv_create_grid", "kv_destroy_grid", "kv_set_stream", "kv_field_len",
            "kv_base_flow_gradient", "kv_krylov_vector_batch", "kv_plan_create", "kv_plan_add", "kv_plan_launch",
            "kv_plan_destroy", "kv_plan_last_error", "kv_selftest_wait_timeout", "kv_tuning",
            "kv_krylov_vector_host_stream", "kv_gmres", "kv_bicgstab2", "kv_newton", "kv_axpby", "kv_combine", "kv_dot",
-           "kv_axis_data")
+           "kv_axis_data", "kv_field_sizes", "kv_set_base_flow_packed", "kv_set_tuning", "kv_guard_read",
+           "kv_arnoldi_counts")
 PHASES = {"stencil": 0, "divergence": 1, "tpd": 2, "correct": 3, "arnoldi": 4, "refine": 5, "gs_dots": 6,
           "gs_update": 7}
 
@@ -58,6 +59,12 @@ class GridDesc(ctypes.Structure):
                 ("gr", ctypes.c_double), ("pr", ctypes.c_double), ("tol", ctypes.c_double),
                 ("max_passes", ctypes.c_int), ("refine_sweeps", ctypes.c_int), ("cgs_passes", ctypes.c_int),
                 ("stretch", ctypes.c_double)]
+
+
+class Guard(ctypes.Structure):
+    """kv_guard: the device-side SIMPLE test of the one-pass evaluations."""
+    _fields_ = [("checks", ctypes.c_longlong), ("failed", ctypes.c_longlong), ("nonfinite", ctypes.c_longlong),
+                ("worst_rel_div", ctypes.c_double)]
 
 
 class Stats(ctypes.Structure):
@@ -105,7 +112,13 @@ def load_library(path: str = LIB_PATH):
     lib.kv_destroy_grid.argtypes = [H]
     lib.kv_set_stream.argtypes = [H, ctypes.c_void_p]
     lib.kv_field_len.argtypes = [H, ctypes.POINTER(ctypes.c_size_t)]
-    lib.kv_set_base_flow.argtypes = [H, D]
+    lib.kv_set_base_flow.argtypes = [H, D, D, D, D]
+    lib.kv_set_base_flow_packed.argtypes = [H, D]
+    S = ctypes.POINTER(ctypes.c_size_t)
+    lib.kv_field_sizes.argtypes = [H, S, S, S, S]
+    lib.kv_set_tuning.argtypes = [H, ctypes.POINTER(ctypes.c_int)]
+    lib.kv_guard_read.argtypes = [H, ctypes.POINTER(Guard), ctypes.c_int]
+    lib.kv_arnoldi_counts.argtypes = [H, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_longlong)]
     lib.kv_krylov_vector.argtypes = [H, D, D, D, ctypes.POINTER(Stats)]
     lib.kv_krylov_vector_host.argtypes = [H, D, D, ctypes.POINTER(Stats)]
     lib.kv_arnoldi_step.argtypes = [H, D, ctypes.c_int, ctypes.POINTER(ctypes.c_double)]
@@ -203,8 +216,47 @@ class Grid:
         return self.torch.zeros(tuple(lead) + self.shape, dtype=self.torch.float64, device="cuda")
 
     def set_base_flow(self, base):
+        """base: a packed state U | V | W | Theta (CUDA float64), passed field by field to
+        kv_set_base_flow."""
         self._sync_stream()
-        self._check(self.lib.kv_set_base_flow(self.h, _dev_ptr(base, self.torch, "base", 4 * self.field_len)))
+        P = self.field_len
+        p = _dev_ptr(base, self.torch, "base", 4 * P)
+        self._check(self.lib.kv_set_base_flow(self.h, p, p + 8 * P, p + 16 * P, p + 24 * P))
+
+    def set_base_flow_fields(self, U, V, W, Theta):
+        """The four fields as separate CUDA float64 tensors of one padded field each."""
+        self._sync_stream()
+        P = self.field_len
+        self._check(self.lib.kv_set_base_flow(self.h, *(_dev_ptr(f, self.torch, n, P) for f, n in
+                                                        ((U, "U"), (V, "V"), (W, "W"), (Theta, "Theta")))))
+
+    def set_base_flow_packed(self, base):
+        self._sync_stream()
+        self._check(self.lib.kv_set_base_flow_packed(self.h, _dev_ptr(base, self.torch, "base", 4 * self.field_len)))
+
+    def field_sizes(self):
+        """kv_field_sizes: padded lengths of the u, v, w and cell fields."""
+        out = [ctypes.c_size_t() for _ in range(4)]
+        self._check(self.lib.kv_field_sizes(self.h, *(ctypes.byref(o) for o in out)))
+        return tuple(o.value for o in out)
+
+    def set_tuning(self, apply_block=(32, 8), df_variant=-1, df_block=(-1, -1)):
+        """kv_set_tuning: fix the operator configuration (same layout as tuning())."""
+        cfg = (ctypes.c_int * 5)(apply_block[0], apply_block[1], df_variant, df_block[0], df_block[1])
+        self._check(self.lib.kv_set_tuning(self.h, cfg))
+
+    def guard(self, reset=False):
+        """kv_guard_read: {checks, failed, nonfinite, worst_rel_div} of the device-side SIMPLE test."""
+        self._sync_stream()
+        g = Guard()
+        self._check(self.lib.kv_guard_read(self.h, ctypes.byref(g), 1 if reset else 0))
+        return {"checks": g.checks, "failed": g.failed, "nonfinite": g.nonfinite, "worst_rel_div": g.worst_rel_div}
+
+    def arnoldi_counts(self):
+        """(fused Arnoldi steps, of them with the second Gram-Schmidt update) since profile_enable."""
+        a, b = ctypes.c_longlong(), ctypes.c_longlong()
+        self._check(self.lib.kv_arnoldi_counts(self.h, ctypes.byref(a), ctypes.byref(b)))
+        return a.value, b.value
 
     def krylov_vector(self, x, y=None, p=None, stats=False):
         self._sync_stream()

@@ -68,7 +68,12 @@ def test_null_arguments_rejected(lib):
     assert lib.kv_krylov_vector(None, None, None, None, None) == -1
     assert lib.kv_arnoldi_step(None, None, 0, None) == -1
     assert lib.kv_newton_residual(None, None, None, None) == -1
-    assert lib.kv_set_base_flow(None, None) == -1
+    assert lib.kv_set_base_flow(None, None, None, None, None) == -1
+    assert lib.kv_set_base_flow_packed(None, None) == -1
+    assert lib.kv_field_sizes(None, None, None, None, None) == -1
+    assert lib.kv_set_tuning(None, None) == -1
+    assert lib.kv_guard_read(None, None, 0) == -1
+    assert lib.kv_arnoldi_counts(None, None, None) == -1
     assert lib.kv_krylov_vector_host(None, None, None, None) == -1
     assert lib.kv_krylov_vector_host_stream(None, None, None, 1) == -1
     assert lib.kv_gmres(None, None, None, None, 10, 1, 1e-10, 0.99, None) == -1
