@@ -9,6 +9,7 @@
 #include <math.h>
 #include <string.h>
 
+#include <atomic>
 #include <string>
 
 #include "kv_internal.cuh"
@@ -32,30 +33,37 @@ constexpr size_t SCRATCH_DOUBLES = OFF_RED + 2;
 static __device__ __align__(256) double g_noalloc_scratch[SCRATCH_DOUBLES];
 
 constexpr int MAX_DEVICES = 64;
-double* g_scratch_addr[MAX_DEVICES] = {};
-
-// host-side eigen data of the last call on this thread (copied to the device each call)
-thread_local double t_w[6][NMAX * NMAX];
-thread_local double t_lam[3][NMAX];
+// the array's device address per device, looked up once (host threads may race to store the
+// same value; the atomic makes that well defined)
+std::atomic<double*> g_scratch_addr[MAX_DEVICES];
 
 kv_status noalloc_fail(kv_status st, const std::string& msg) {
   kv_set_thread_error(msg);  // read back with kv_last_error(NULL)
   return st;
 }
 
-// Eq (15) for the Neumann pressure Laplacian on a uniform axis (closed form, as in kv_api.cu).
-void axis_tables(int n, double* fwd, double* inv, double* lam) {
-  const long double pi = 3.141592653589793238462643383279502884L;
-  const long double h = 1.0L / n;
-  for (int m = 0; m < n; ++m) {
-    const long double alpha = sqrtl((m == 0 ? 1.0L : 2.0L) / n);
-    const long double s = sinl(pi * m / (2.0L * n));
-    lam[m] = (double)(-4.0L / (h * h) * s * s);
-    for (int t = 0; t < n; ++t) {
-      const double e = (double)(alpha * cosl(pi * m * (t + 0.5L) / n));
-      fwd[(size_t)m * n + t] = e;
-      inv[(size_t)t * n + m] = e;
-    }
+// Eq (15) for the Neumann pressure Laplacian on the uniform axes, built on the device straight into
+// the scratch (block a = axis a of n[a] cells): eigenvectors alpha_m cos(pi m (t + 1/2) / n) and
+// eigenvalues -4 n^2 sin^2(pi m / 2n), the closed form kv_create_grid uses. The argument
+// m (2t + 1) / (2n) is reduced exactly in integers (modulo 4n, a period of cos(pi x / 2n)) before
+// cospi, so every entry carries cospi's own rounding only. fwd (E^-1 = E^T): row = mode,
+// column = cell; inv (E): row = cell, column = mode.
+__global__ void k_noalloc_tables(int n0, int n1, int n2, double* __restrict__ W, double* __restrict__ lam) {
+  const int a = blockIdx.x;
+  const int n = a == 0 ? n0 : (a == 1 ? n1 : n2);
+  double* fwd = W + (size_t)a * NMAX * NMAX;
+  double* inv = W + (size_t)(3 + a) * NMAX * NMAX;
+  for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) {
+    const int m = idx / n, t = idx - m * n;
+    const int q = (m * (2 * t + 1)) % (4 * n);
+    const double alpha = sqrt((m == 0 ? 1.0 : 2.0) / n);
+    const double e = alpha * cospi((double)q / (2.0 * n));
+    fwd[(size_t)m * n + t] = e;
+    inv[(size_t)t * n + m] = e;
+  }
+  for (int m = threadIdx.x; m < n; m += blockDim.x) {
+    const double sn = sinpi((double)m / (2.0 * n));
+    lam[(size_t)a * NMAX + m] = -4.0 * (double)n * (double)n * sn * sn;
   }
 }
 
@@ -82,14 +90,15 @@ extern "C" kv_status kv_krylov_vector_noalloc(const kv_grid_desc* desc, const do
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return noalloc_fail(KV_ERR_CUDA, std::string("cudaGetDevice: ") + cudaGetErrorString(e));
   if (dev < 0 || dev >= MAX_DEVICES) return noalloc_fail(KV_ERR_ARG, "kv_krylov_vector_noalloc: device ordinal >= 64");
-  if (!g_scratch_addr[dev]) {  // set-up, once per device, with that device current
+  double* S = g_scratch_addr[dev].load(std::memory_order_acquire);
+  if (!S) {  // set-up, once per device, with that device current
     void* p = nullptr;
     e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
     if (e != cudaSuccess || !p)
       return noalloc_fail(KV_ERR_CUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
-    g_scratch_addr[dev] = (double*)p;
+    S = (double*)p;
+    g_scratch_addr[dev].store(S, std::memory_order_release);
   }
-  double* S = g_scratch_addr[dev];
   cudaStream_t s = (cudaStream_t)stream;
 
   kv_grid h;  // a view over the static scratch; owns nothing
@@ -120,28 +129,22 @@ extern "C" kv_status kv_krylov_vector_noalloc(const kv_grid_desc* desc, const do
   h.P = (size_t)g.X * g.Y * g.Z;
   h.Nc = (size_t)g.nx * g.ny * g.nz;
   if (x < y + 4 * h.P && y < x + 4 * h.P) return noalloc_fail(KV_ERR_ARG, "kv_krylov_vector_noalloc: x and y overlap");
+  // the operator reads base directly (there is no library copy of it here) while y is written
+  if (base < y + 4 * h.P && y < base + 4 * h.P)
+    return noalloc_fail(KV_ERR_ARG, "kv_krylov_vector_noalloc: base and y overlap");
   h.base = const_cast<double*>(base);
   h.vstar = S + OFF_VSTAR;
   h.tpd_a = S + OFF_TPDA;
   h.tpd_b = S + OFF_TPDB;
   h.red = (unsigned long long*)(S + OFF_RED);
 
-  // per-axis eigenvectors / eigenvalues for this size, copied into the scratch each call
-  const int n[3] = {g.nx, g.ny, g.nz};
+  // per-axis eigenvectors / eigenvalues for this size, written into the scratch by a kernel
   for (int a = 0; a < 3; ++a) {
-    axis_tables(n[a], t_w[a], t_w[3 + a], t_lam[a]);
     h.Wm[a] = S + OFF_W + (size_t)a * NMAX * NMAX;
     h.Wm[3 + a] = S + OFF_W + (size_t)(3 + a) * NMAX * NMAX;
     h.lam[a] = S + OFF_LAM + (size_t)a * NMAX;
   }
-  for (int a = 0; a < 3; ++a) {
-    const size_t nn = (size_t)n[a] * n[a] * sizeof(double);
-    if ((e = cudaMemcpyAsync(h.Wm[a], t_w[a], nn, cudaMemcpyHostToDevice, s)) != cudaSuccess ||
-        (e = cudaMemcpyAsync(h.Wm[3 + a], t_w[3 + a], nn, cudaMemcpyHostToDevice, s)) != cudaSuccess ||
-        (e = cudaMemcpyAsync(h.lam[a], t_lam[a], n[a] * sizeof(double), cudaMemcpyHostToDevice, s)) !=
-            cudaSuccess)
-      return noalloc_fail(KV_ERR_CUDA, std::string("cudaMemcpyAsync: ") + cudaGetErrorString(e));
-  }
+  k_noalloc_tables<<<3, 256, 0, s>>>(g.nx, g.ny, g.nz, S + OFF_W, S + OFF_LAM);
   // the divergence reduction must start at zero; everything else is fully overwritten
   if ((e = cudaMemsetAsync(h.red, 0, 2 * sizeof(unsigned long long), s)) != cudaSuccess)
     return noalloc_fail(KV_ERR_CUDA, std::string("cudaMemsetAsync: ") + cudaGetErrorString(e));

@@ -23,20 +23,21 @@ def built():
     build.build()
 
 
-def _desc(kv, n, bc, gr, precision=0):
-    return kv.GridDesc(n[0], n[1], n[2], bc, 0, precision, gr, 0.71, 0.0, 0, 0, 0)
+def _desc(kv, n, bc, gr, precision=0, tproj=0):
+    return kv.GridDesc(n[0], n[1], n[2], bc, tproj, precision, gr, 0.71, 0.0, 0, 0, 0)
 
 
-@pytest.mark.parametrize("n,bc", [((20, 17, 24), synth.CC), ((32, 9, 30), synth.AA)])
-def test_noalloc_matches_handle_path_on_two_calls(n, bc):
+@pytest.mark.parametrize("n,bc,tproj", [((20, 17, 24), synth.CC, 0), ((32, 9, 30), synth.AA, 0),
+                                        ((15, 22, 11), synth.AA, 1)])
+def test_noalloc_matches_handle_path_on_two_calls(n, bc, tproj):
     from paper_1905_11601_gb300 import kv
     lib = kv.load_library()
     gr = 2.0e6
     base = torch.from_numpy(np.stack(synth.base_flow(*n, bc, 31))).cuda()
     xs = torch.from_numpy(synth.krylov_input(*n, 32, count=2)).cuda()
-    g = kv.Grid(*n, bc=bc, gr=gr)
+    g = kv.Grid(*n, bc=bc, gr=gr, tproj=tproj)
     g.set_base_flow(base)
-    desc = _desc(kv, n, bc, gr)
+    desc = _desc(kv, n, bc, gr, tproj=tproj)
     stream = torch.cuda.current_stream().cuda_stream
     for call in range(2):
         x = xs[call].contiguous()
@@ -63,3 +64,10 @@ def test_noalloc_rejects_sizes_beyond_its_scratch():
     st = lib.kv_krylov_vector_noalloc(ctypes.byref(_desc(kv, (8, 8, 8), 0, 1e6, precision=1)), t.data_ptr(),
                                       t.data_ptr(), y.data_ptr(), None)
     assert st == -1
+    # a base state overlapping y is refused (the operator reads base while y is written)
+    n = (8, 8, 8)
+    buf = torch.zeros((2, 4, 10, 10, 10), dtype=torch.float64, device="cuda")
+    st = lib.kv_krylov_vector_noalloc(ctypes.byref(_desc(kv, n, 0, 1e6)), buf[1].data_ptr(), buf[0].data_ptr(),
+                                      buf[1].data_ptr(), None)
+    assert st == -1
+    assert b"overlap" in lib.kv_last_error(None)
