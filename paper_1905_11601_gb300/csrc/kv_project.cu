@@ -208,16 +208,17 @@ __global__ void __launch_bounds__(256) k_correct_df(KvGeom g, KvStretch S, const
 }
 
 // The double-float correction with the SIMPLE test, marching in z (the form the one-pass
-// evaluations use). A block of 32 x MC_Y threads owns 31 x (MC_Y - 1) face columns: lane 0 and
-// row 0 are a halo that forms the corrected faces u(i-1) and v(j-1) its neighbours' divergence
-// needs (handed over by warp shuffle and shared memory) and writes nothing; w(k-1) is the
-// previous plane's value, kept in a register. So each corrected face is formed once (plus the
-// halo) and max |D v| costs one double-float divergence per cell, with the same rounding of the
-// faces as the stored velocity. The loads of plane k+1 are issued before plane k is computed.
+// evaluations use). A warp owns 31 face columns of one row: lane 0 is a halo that forms the
+// corrected face u(i-1) its neighbour's divergence needs (handed over by a warp shuffle) and
+// writes nothing; v(j-1) is formed again by the thread itself (two more loads, no block-wide
+// barrier); w(k-1) is the previous plane's value, kept in a register. So max |D v| costs about
+// one extra corrected face and one double-float divergence per cell, with the same rounding of
+// the faces as the stored velocity. The loads of plane k+1 are issued before plane k is computed.
 // Outputs as k_correct_df.
-constexpr int MC_Y = 16;
+constexpr int MC_Y = 8;
 struct CorrIn {
   double u, v, w, c, cx, cy, cz;  // v* at (i, j, k); phi at the cell and its three plus neighbours
+  double vm, cm;                  // v* at (i, j-1, k) and phi at the cell (i, j-1, k)
 };
 template <bool STR>
 __global__ void __launch_bounds__(32 * MC_Y) k_correct_df_march(KvGeom g, KvStretch S, const double* __restrict__ vs,
@@ -225,20 +226,20 @@ __global__ void __launch_bounds__(32 * MC_Y) k_correct_df_march(KvGeom g, KvStre
                                                               double* __restrict__ out, double* __restrict__ p,
                                                               int acc_p, unsigned long long* __restrict__ red,
                                                               float2 ihx, float2 ihy, float2 ihz, int kc) {
-  __shared__ float2 vsh[2][MC_Y][32];
   const int tx = threadIdx.x, ty = threadIdx.y;
   const int i = blockIdx.x * 31 + tx - 1;  // -1 for the first block's halo lane
-  const int j = blockIdx.y * (MC_Y - 1) + ty - 1;
+  const int j = blockIdx.y * MC_Y + ty;
   const int k0 = blockIdx.z * kc, k1 = min(k0 + kc, g.Z);
-  const bool own = tx >= 1 && ty >= 1 && i < g.X && j < g.Y;
+  const bool own = tx >= 1 && i < g.X && j < g.Y;
   const bool col = i >= 1 && i <= g.nx && j >= 1 && j <= g.ny;  // a column of cells
+  const bool vface_m = col && j >= 2;                            // the face v(i, j-1) is interior
   const size_t cy = g.nx, cz = (size_t)g.nx * g.ny;
   const size_t e0 = (size_t)i + (size_t)g.X * (size_t)j;                  // padded index at k = 0
-  const size_t c0 = col ? (size_t)(i - 1) + cy * (size_t)(j - 1) : 0;   // compact index at k = 1, minus cz
+  const size_t c0 = col ? (size_t)(i - 1) + cy * (size_t)(j - 1) : 0;   // compact index at k = 1
   // the inputs of plane k (zero where the plane has no cell in this column); the loads stay
-  // inside the arrays: phi is read at compact cells and their plus neighbours inside the grid
+  // inside the arrays: phi is read at compact cells and their neighbours inside the grid
   auto load = [&](int k, CorrIn& r) {
-    r = CorrIn{0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+    r = CorrIn{0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
     if (!col || k < 1 || k > g.nz) return;
     const size_t e = e0 + (size_t)g.X * g.Y * k, c = c0 + cz * (size_t)(k - 1);
     r.c = __ldg(phi + c);
@@ -254,10 +255,14 @@ __global__ void __launch_bounds__(32 * MC_Y) k_correct_df_march(KvGeom g, KvStre
       r.w = __ldg(vs + 2 * P + e);
       r.cz = __ldg(phi + c + cz);
     }
+    if (vface_m) {
+      r.vm = __ldg(vs + P + e - g.X);
+      r.cm = __ldg(phi + c - cy);
+    }
   };
-  // corrected faces at (i, j, k): zero outside the interior faces
-  auto faces = [&](int k, const CorrIn& r, DF& ur, DF& vr, DF& wr) {
-    ur = vr = wr = DF{0.0f, 0.0f};
+  // corrected faces at (i, j, k) and v at (i, j-1, k): zero outside the interior faces
+  auto faces = [&](int k, const CorrIn& r, DF& ur, DF& vr, DF& wr, DF& vmr) {
+    ur = vr = wr = vmr = DF{0.0f, 0.0f};
     if (!col || k < 1 || k > g.nz) return;
     const DF p0 = df_split(r.c);
     if (i <= g.nx - 1)
@@ -266,24 +271,23 @@ __global__ void __launch_bounds__(32 * MC_Y) k_correct_df_march(KvGeom g, KvStre
       vr = df_sub(df_split(r.v), df_mul(df_sub(df_split(r.cy), p0), inv_w_df<STR, 1, KV_SWD_IDF>(g, S, j, ihy)));
     if (k <= g.nz - 1)
       wr = df_sub(df_split(r.w), df_mul(df_sub(df_split(r.cz), p0), inv_w_df<STR, 2, KV_SWD_IDF>(g, S, k, ihz)));
+    if (vface_m)
+      vmr = df_sub(df_split(r.vm), df_mul(df_sub(p0, df_split(r.cm)), inv_w_df<STR, 1, KV_SWD_IDF>(g, S, j - 1, ihy)));
   };
   DF wprev{0.0f, 0.0f};
   CorrIn cur, nxt;
   if (k0 >= 1) {
-    DF a, b;
+    DF a, b, d;
     load(k0 - 1, cur);
-    faces(k0 - 1, cur, a, b, wprev);
+    faces(k0 - 1, cur, a, b, wprev, d);
   }
   load(k0, cur);
   unsigned long long dmax = 0, vmax = 0;
-  int buf = 0;
-  for (int k = k0; k < k1; ++k, buf ^= 1) {
+  for (int k = k0; k < k1; ++k) {
     if (k + 1 < k1) load(k + 1, nxt);
-    DF ur, vr, wr;
-    faces(k, cur, ur, vr, wr);
-    vsh[buf][ty][tx] = make_float2(vr.h, vr.l);
+    DF ur, vr, wr, vm;
+    faces(k, cur, ur, vr, wr, vm);
     const DF um{__shfl_up_sync(0xffffffffu, ur.h, 1), __shfl_up_sync(0xffffffffu, ur.l, 1)};
-    __syncthreads();  // one per plane: vsh is double-buffered
     if (own) {
       const size_t e = e0 + (size_t)g.X * g.Y * k;
       out[e] = df_value(ur);
@@ -294,9 +298,8 @@ __global__ void __launch_bounds__(32 * MC_Y) k_correct_df_march(KvGeom g, KvStre
       vmax = max(vmax, abs_bits(df_f2d(__uint_as_float(vb))));
       const bool cell = col && k >= 1 && k <= g.nz;
       if (cell) {
-        const float2 vm = vsh[buf][ty - 1][tx];
         const DF d = df_add(df_add(df_mul(df_sub(ur, um), inv_w_df<STR, 0, KV_SWD_IDC>(g, S, i, ihx)),
-                                   df_mul(df_sub(vr, DF{vm.x, vm.y}), inv_w_df<STR, 1, KV_SWD_IDC>(g, S, j, ihy))),
+                                   df_mul(df_sub(vr, vm), inv_w_df<STR, 1, KV_SWD_IDC>(g, S, j, ihy))),
                             df_mul(df_sub(wr, wprev), inv_w_df<STR, 2, KV_SWD_IDC>(g, S, k, ihz)));
         dmax = max(dmax, abs_bits(df_value(d)));
       }
@@ -365,7 +368,7 @@ void kv_launch_correct(const kv_grid* h, const double* vstar, const double* phi,
     const float2 cx = pair_of(g.ihx), cy = pair_of(g.ihy), cz = pair_of(g.ihz);
     if (check) {
       const int kc = 16;
-      dim3 mb(32, MC_Y, 1), mg((g.X + 30) / 31, (g.Y + MC_Y - 2) / (MC_Y - 1), (g.Z + kc - 1) / kc);
+      dim3 mb(32, MC_Y, 1), mg((g.X + 30) / 31, (g.Y + MC_Y - 1) / MC_Y, (g.Z + kc - 1) / kc);
       auto kern = str ? k_correct_df_march<true> : k_correct_df_march<false>;
       kern<<<mg, mb, 0, s>>>(g, h->str, vstar, phi, h->P, out_vel, p, accumulate_p, h->red, cx, cy, cz, kc);
       return;
