@@ -882,7 +882,6 @@ kv_status kv_arnoldi_step(kv_handle h, double* V, int j, double* h_col) {
   if (s != KV_OK) return s;
   double* h1 = h->hdev;               // [0, nq): first pass; [nq]: ||w||^2 before
   double* h2 = h->hdev + nq + 1;      // [nq+1, 2nq+1): second pass; [2nq+1]: ||w||^2 after pass 1
-  double* nrm = h->hdev + 2 * nq + 2; // ||w||^2 after the second update (unfused path)
   double* hcol = h->hdev + 2 * nq + 3;  // [2nq+3, 3nq+4): the Hessenberg column (fused path)
   int* flag = reinterpret_cast<int*>(h->hdev + 3 * nq + 4);  // second update applied (fused path)
   std::vector<double> hh(need_h, 0.0);
@@ -924,22 +923,44 @@ kv_status kv_arnoldi_step(kv_handle h, double* V, int j, double* h_col) {
     h->gs_second += upd != 0;
     for (int q = 0; q <= nq; ++q) h_col[q] = hh[2 * (size_t)nq + 3 + q];
     return KV_OK;
-  } else {
-    const int md = (nq + 7) / 8 + 1;  // multidot sweeps + finalize
-    KvPhase ph(h, KV_PH_ARNOLDI, 2 * md + 2 + 2 + 1);
-    kv_launch_multidot(V, L, nq, w, L, h->partials, h1, 0, h->s);
-    kv_launch_update(V, L, nq, h1, w, L, h->s);
-    kv_launch_multidot(V, L, nq, w, L, h->partials, h2, 0, h->s);
-    kv_launch_update(V, L, nq, h2, w, L, h->s);
-    kv_launch_norm2(w, L, h->partials, nrm, h->s);
-    kv_launch_scale_inv_sqrt(w, L, nrm, h->s);
+  }
+  // Beyond QF basis vectors: the same classical Gram-Schmidt with its measured second pass, as
+  // separate sweeps: h1 = V^T w and ||w||^2 (chunks of QF vectors), w -= V h1 (one sweep over all
+  // vectors; in mixed precision on both pipes), h2 = V^T w and ||w||^2 (chunks), then the device-side
+  // decision and the third sweep fused with the normalisation.
+  const int df = h->d.precision == KV_PREC_MIXED;
+  {
+    const int chunks = (nq + kv_fused_cgs_max() - 1) / kv_fused_cgs_max();
+    KvPhase ph(h, KV_PH_GS_DOTS, 2 * chunks);
+    kv_launch_dots_chunked(V, L, nq, w, L, h->partials, h1, 1, df, h->s);
+  }
+  {
+    KvPhase ph(h, KV_PH_GS_UPDATE, 1);
+    kv_launch_update_n(V, L, nq, h1, w, L, df, h->s);
+  }
+  {
+    const int chunks = (nq + kv_fused_cgs_max() - 1) / kv_fused_cgs_max();
+    KvPhase ph(h, KV_PH_GS_DOTS, 2 * chunks);
+    kv_launch_dots_chunked(V, L, nq, w, L, h->partials, h2, 1, df, h->s);
+  }
+  {
+    KvPhase ph(h, KV_PH_ARNOLDI, 2);
+    kv_launch_gs_decide(h1, h2, nq, df ? 0x1p-46 : 0x1p-50, h->d.cgs_passes == 2, hcol, flag, h->s);
+    kv_launch_update_small_scale_n(V, L, nq, h2, w, L, h->s, flag);
   }
   s = check_launch(h, "arnoldi");
   if (s != KV_OK) return s;
-  KV_CHECK_CUDA(h, cudaMemcpyAsync(hh.data(), h->hdev, hh.size() * sizeof(double), cudaMemcpyDeviceToHost, h->s));
+  KV_CHECK_CUDA(h, cudaMemcpyAsync(hh.data(), h->hdev, need_h * sizeof(double), cudaMemcpyDeviceToHost, h->s));
   KV_CHECK_CUDA(h, cudaStreamSynchronize(h->s));
-  for (int q = 0; q < nq; ++q) h_col[q] = hh[q] + hh[nq + 1 + q];
-  h_col[nq] = sqrt(hh[2 * nq + 2]);
+  if (df && (std::isnan(hh[nq]) || std::isnan(hh[2 * (size_t)nq + 1])))
+    return fail(h, KV_ERR_ARG,
+                "kv_arnoldi_step: the new vector has entries outside the mixed-precision Gram-Schmidt range "
+                "(NaN, Inf or |x| >= 2^48); V[j+1] is undefined");
+  int upd = 0;
+  memcpy(&upd, &hh[3 * (size_t)nq + 4], sizeof upd);
+  h->gs_steps += 1;
+  h->gs_second += upd != 0;
+  for (int q = 0; q <= nq; ++q) h_col[q] = hh[2 * (size_t)nq + 3 + q];
   return KV_OK;
 }
 

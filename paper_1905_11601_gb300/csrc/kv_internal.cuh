@@ -124,7 +124,7 @@ struct kv_grid {
 
   // launch counting (always) and per-phase CUDA-event timing (when profiling is on)
   long long launches[KV_NPHASE] = {};
-  long long gs_steps = 0, gs_second = 0;  // fused Arnoldi steps, and of them those with the second update
+  long long gs_steps = 0, gs_second = 0;  // Arnoldi steps, and of them those with the second update
   bool prof_on = false;
   std::vector<cudaEvent_t> ev_pool;
   struct Pending { int phase; cudaEvent_t a, b; };
@@ -259,9 +259,8 @@ void kv_launch_multidot(const double* V, size_t ld, int nq, const double* w, siz
 // w -= sum_q c[q] V_q
 void kv_launch_update(const double* V, size_t ld, int nq, const double* c, double* w, size_t len,
                       cudaStream_t s);
-// out[0] = ||w||^2 (via partials); then w /= sqrt(out[0]) if scale
+// out[0] = ||w||^2 (via partials)
 void kv_launch_norm2(const double* w, size_t len, double* partials, double* out, cudaStream_t s);
-void kv_launch_scale_inv_sqrt(double* w, size_t len, const double* nrm2, cudaStream_t s);
 // Gram-Schmidt building blocks for nq <= kv_fused_cgs_max() vectors (one sweep each):
 // h[q] = <V_q, w> (and h[nq] = ||w||^2 when nrm2 != nullptr, copied to nrm2);
 // w -= V c fused with h2[q] = <V_q, w> and h2[nq] = ||w||^2 (FP64);
@@ -281,3 +280,13 @@ void kv_launch_update_small_scale(const double* V, size_t ld, int nq, const doub
 // kv_launch_update_small_scale (given flag) then produces.
 void kv_launch_gs_decide(const double* h1, const double* h2, int nq, double theta, int force, double* hcol,
                          int* flag, cudaStream_t s);
+// The same sweeps for any basis size: inner products in chunks of at most kv_fused_cgs_max()
+// vectors (h[q], and h[nq] = ||w||^2 when nrm); w -= V c over all vectors (df: FP64 for about
+// 3 (nq + 2) / 10 of them, double-float for the others; else FP64); and the third sweep
+// (flag-controlled, as kv_launch_update_small_scale).
+void kv_launch_dots_chunked(const double* V, size_t ld, int nq, const double* w, size_t len, double* partials,
+                            double* h, int nrm, int df, cudaStream_t s);
+void kv_launch_update_n(const double* V, size_t ld, int nq, const double* c, double* w, size_t len, int df,
+                        cudaStream_t s);
+void kv_launch_update_small_scale_n(const double* V, size_t ld, int nq, const double* c, double* w, size_t len,
+                                    cudaStream_t s, const int* flag);

@@ -82,13 +82,6 @@ __global__ void __launch_bounds__(RT) k_update(const double* __restrict__ V, siz
   }
 }
 
-__global__ void __launch_bounds__(RT) k_scale_inv_sqrt(double* __restrict__ w, size_t len,
-                                                       const double* __restrict__ nrm2) {
-  const double n2 = *nrm2;
-  const double f = n2 > 0.0 ? 1.0 / sqrt(n2) : 0.0;
-  for (size_t e = (size_t)blockIdx.x * RT + threadIdx.x; e < len; e += (size_t)gridDim.x * RT) w[e] *= f;
-}
-
 // FP32 value of a double from its high word (20 mantissa bits, truncated): integer operations
 // only, so it stays off GB300's narrow FP64 pipe. Zero, denormals and tiny values map to 0.
 // Only for quantities whose own rounding is negligible in the result.
@@ -410,6 +403,66 @@ __global__ void __launch_bounds__(RT, 2) k_update_dot_df(const double* __restric
   }
 }
 
+// Any basis size (the sweeps beyond QF vectors): w -= sum_q c[q] V_q, the first k64 vectors in FP64
+// on the FP64 pipe and the others in double-float on the FP32 pipe (the dual-pipe split of
+// k_update_dot_df), without inner products; the updated w is stored rounded to FP64. Dynamic shared
+// memory: k64 doubles, then nq - k64 FP32 pairs (the negated coefficients).
+__global__ void __launch_bounds__(RT) k_update_n_df(const double* __restrict__ V, size_t ld, int nq, int k64,
+                                                    const double* __restrict__ c, double* __restrict__ w, size_t len) {
+  extern __shared__ double dyn[];
+  double* c64 = dyn;
+  DF* cs = reinterpret_cast<DF*>(dyn + k64);
+  for (int q = threadIdx.x; q < nq; q += RT) {
+    if (q < k64) {
+      c64[q] = c[q];
+    } else {
+      const DF x = df_split(c[q]);
+      cs[q - k64] = DF{-x.h, -x.l};
+    }
+  }
+  __syncthreads();
+  for (size_t e = (size_t)blockIdx.x * RT + threadIdx.x; e < len; e += (size_t)gridDim.x * RT) {
+    double w64 = w[e];
+#pragma unroll 4
+    for (int q = 0; q < k64; ++q) w64 = fma(-c64[q], __ldg(V + (size_t)q * ld + e), w64);
+    DFAcc a;
+    a.start(df_split(w64));
+#pragma unroll 4
+    for (int q = k64; q < nq; ++q) a.fma(cs[q - k64], df_split(__ldg(V + (size_t)q * ld + e)));
+    const DF w1 = a.pair();
+    w[e] = df_f2d(w1.h) + df_f2d(w1.l);
+  }
+}
+
+// k_update_small_scale for any basis size (coefficients in dynamic shared memory, nq floats).
+__global__ void __launch_bounds__(RT) k_update_small_scale_n(const double* __restrict__ V, size_t ld, int nq,
+                                                             const double* __restrict__ c, double* __restrict__ w,
+                                                             size_t len, const int* __restrict__ flag) {
+  extern __shared__ float csn[];
+  __shared__ double finv;
+  const bool upd = flag == nullptr || *flag != 0;
+  for (int q = threadIdx.x; q < nq; q += RT) csn[q] = (float)c[q];
+  if (threadIdx.x == 0) {
+    double s = 0.0;
+    if (upd)
+      for (int q = 0; q < nq; ++q) s = fma(c[q], c[q], s);
+    const double b2 = c[nq] - s;
+    finv = b2 > 0.0 || isnan(b2) ? 1.0 / sqrt(b2) : 0.0;
+  }
+  __syncthreads();
+  const double f = finv;
+  if (!upd) {
+    for (size_t e = (size_t)blockIdx.x * RT + threadIdx.x; e < len; e += (size_t)gridDim.x * RT) w[e] *= f;
+    return;
+  }
+  for (size_t e = (size_t)blockIdx.x * RT + threadIdx.x; e < len; e += (size_t)gridDim.x * RT) {
+    float acc = 0.0f;
+#pragma unroll 4
+    for (int q = 0; q < nq; ++q) acc = fmaf(csn[q], hi_float(__ldg(V + (size_t)q * ld + e)), acc);
+    w[e] = (w[e] - df_f2d(acc)) * f;
+  }
+}
+
 // Blocks of kernel K that are resident at once on the device (at most RB): the sweeps below
 // launch exactly one wave, so no partly filled second wave trails the memory stream.
 template <auto K>
@@ -510,6 +563,34 @@ void kv_launch_update_small_scale(const double* V, size_t ld, int nq, const doub
   }
 }
 
+void kv_launch_dots_chunked(const double* V, size_t ld, int nq, const double* w, size_t len, double* partials,
+                            double* h, int nrm, int df, cudaStream_t s) {
+  // chunks of at most QF vectors, each one sweep over its vectors and w; ||w||^2 with the last
+  for (int q0 = 0; q0 < nq; q0 += QF) {
+    const int qc = nq - q0 < QF ? nq - q0 : QF;
+    const bool last = q0 + qc == nq;
+    kv_launch_dots_norm(V + (size_t)q0 * ld, ld, qc, w, len, partials, h + q0, (last && nrm) ? h + nq : nullptr, df,
+                        s);
+  }
+}
+
+void kv_launch_update_n(const double* V, size_t ld, int nq, const double* c, double* w, size_t len, int df,
+                        cudaStream_t s) {
+  if (!df) {
+    kv_launch_update(V, ld, nq, c, w, len, s);
+    return;
+  }
+  const int k64 = (3 * (nq + 2)) / 10;
+  const size_t smem = (size_t)k64 * sizeof(double) + (size_t)(nq - k64) * sizeof(DF);
+  k_update_n_df<<<wave_blocks<k_update_n_df>(), RT, smem, s>>>(V, ld, nq, k64, c, w, len);
+}
+
+void kv_launch_update_small_scale_n(const double* V, size_t ld, int nq, const double* c, double* w, size_t len,
+                                    cudaStream_t s, const int* flag) {
+  k_update_small_scale_n<<<wave_blocks<k_update_small_scale_n>(), RT, (size_t)nq * sizeof(float), s>>>(V, ld, nq, c,
+                                                                                                       w, len, flag);
+}
+
 void kv_launch_multidot(const double* V, size_t ld, int nq, const double* w, size_t len, double* partials,
                         double* out, int accumulate, cudaStream_t s) {
   const int nb = wave_blocks<k_multidot>();
@@ -529,6 +610,3 @@ void kv_launch_norm2(const double* w, size_t len, double* partials, double* out,
   kv_launch_multidot(w, 0, 1, w, len, partials, out, 0, s);
 }
 
-void kv_launch_scale_inv_sqrt(double* w, size_t len, const double* nrm2, cudaStream_t s) {
-  k_scale_inv_sqrt<<<wave_blocks<k_scale_inv_sqrt>(), RT, 0, s>>>(w, len, nrm2);
-}

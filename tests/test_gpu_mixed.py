@@ -195,3 +195,36 @@ def test_second_update_criterion_matches_forced_reorthogonalisation(prec):
     assert np.abs(V0 - V2).max() < 1e-10
     G = V0 @ V0.T
     assert np.abs(G - np.eye(k + 1)).max() < 1e-13
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_gram_schmidt_beyond_24_matches_fp64_definition(prec):
+    """Basis sizes beyond the fused kernels (25..52: inner products in chunks of 24 vectors, the
+    update as a sweep of its own, on both pipes in mixed precision) against the FP64 definition
+    applied to the same w = A V_j, as above; then the orthogonality of the whole basis."""
+    from paper_1905_11601_gb300 import kv
+    n = (20, 18, 16)
+    base = np.stack(synth.base_flow(*n, synth.CC, 25))
+    g = kv.Grid(*n, gr=2e6, pr=0.71, precision=prec)
+    g.set_base_flow(torch.from_numpy(base).cuda())
+    k = 52
+    V = torch.zeros((k + 1, 4) + g.shape, dtype=torch.float64, device="cuda")
+    y = g.krylov_vector(torch.from_numpy(synth.krylov_input(*n, 26)[0]).cuda())
+    V[0] = y / torch.linalg.vector_norm(y)
+    bar = 2e-13 if prec == 1 else 1e-14
+    for j in range(k):
+        if j < 24:
+            g.arnoldi_step(V, j)
+            continue
+        w = g.krylov_vector(V[j].contiguous()).reshape(-1).cpu().numpy()
+        Vj = V[: j + 1].reshape(j + 1, -1).cpu().numpy()
+        h_ref, beta_ref, q_ref = _cgs2_fp64(Vj, w)
+        h = g.arnoldi_step(V, j)
+        nw = np.linalg.norm(w)
+        assert np.abs(h[: j + 1] - h_ref).max() < bar * nw, j
+        assert abs(h[j + 1] - beta_ref) < bar * nw, j
+        q = V[j + 1].reshape(-1).cpu().numpy()
+        assert np.linalg.norm(q - q_ref) < 50 * bar * nw / beta_ref, j
+    Vm = V.reshape(k + 1, -1)
+    G = (Vm @ Vm.T).cpu().numpy()
+    assert np.abs(G - np.eye(k + 1)).max() < 1e-13
