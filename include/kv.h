@@ -206,15 +206,17 @@ const char* kv_plan_last_error(kv_plan_handle p);
    V holds at least j+2 packed vectors (device), V_0..V_j orthonormal; computes
    w = A V_j, orthogonalises it against V_0..V_j by classical Gram-Schmidt (the second pass's
    correction when its measured coefficients exceed the rounding level, or always:
-   desc.cgs_passes; always two passes beyond 24 basis vectors),
+   desc.cgs_passes),
    stores w / ||w|| in V_{j+1} and writes the Hessenberg column H[0..j+1, j] to the HOST
    array h_col (j+2 doubles). Synchronises the stream. Inner products run over all stored
    entries of the four fields. With KV_PREC_MIXED and up to 24 basis vectors, the first two
    Gram-Schmidt sweeps run in double-float arithmetic on the FP32 pipe (relative rounding
    ~2^-46 instead of 2^-53); entries below 2^-103 in magnitude are then treated as 0, and a new
    vector with an entry of magnitude >= 2^48, NaN or Inf gives KV_ERR_ARG (V_{j+1} undefined).
-   Up to 24 basis vectors the decision on the second update is taken on the device and the
-   step synchronises once, to return h_col. */
+   The decision on the second update is taken on the device and the step synchronises once, to
+   return h_col. Up to 24 basis vectors the first update is fused with the second pass's inner
+   products; beyond, the inner products run in chunks of 24 vectors and the update (in
+   KV_PREC_MIXED on both the FP64 and FP32 pipes) is a sweep of its own. */
 kv_status kv_arnoldi_step(kv_handle h, double* V, int j, double* h_col);
 
 /* Transpose of the Krylov map: z = A^T y with A = (Pi_v (+) P_T) J P_BC (the adjoint eigenvalue
@@ -306,7 +308,8 @@ typedef struct {
   int matvecs;         /* Krylov-vector evaluations in the linear solves */
   int gmres_restarts;  /* GMRES cycles in all */
   int bicg_iterations; /* BiCGstab(2) iterations in all */
-  int bicg_rejected;   /* BiCGstab(2) corrections not taken (recomputed residual not below GMRES's) */
+  int bicg_rejected;   /* BiCGstab(2) corrections not taken (recomputed residual not below GMRES's, or the
+                          Newton step with it did not decrease ||F||) */
   int converged;       /* ||F(S)|| < tol at exit */
   int n_res;           /* entries of res_norm */
   double res_norm[KV_NEWTON_HISTORY]; /* ||F|| at the start of each Newton step */
@@ -316,7 +319,8 @@ typedef struct {
    with its inhomogeneous wall values, which the corrections leave unchanged): F = the projected
    residual of S; stop once ||F|| < tol; set the base flow to S (the Jacobian at S) and solve
    A d = F with kv_gmres from d = 0, then kv_bicgstab2 from GMRES's result if GMRES did not
-   converge, keeping the correction with the smaller recomputed residual; S <- S - d. V: m + 1 packed vectors; work: 10 packed vectors (device, caller-owned).
+   converge, keeping the correction with the smaller recomputed residual (BiCGstab(2)'s only if
+   the step with it also does not increase ||F||); S <- S - d. V: m + 1 packed vectors; work: 10 packed vectors (device, caller-owned).
    Leaves the handle's base flow at the last S that took a correction. st: host, nullable.
    KV_ERR_ARG for NULL or overlapping buffers or parameters outside their ranges. */
 kv_status kv_newton(kv_handle h, double* S, double* V, double* work, const kv_newton_params* prm,
@@ -353,9 +357,8 @@ kv_status kv_tuning(kv_handle h, int* cfg);
    KV_ERR_ARG for values outside these ranges. */
 kv_status kv_set_tuning(kv_handle h, const int* cfg);
 
-/* Instrumentation: fused Arnoldi steps (basis of at most 24 vectors) since the last
-   kv_profile_enable, and of them those that applied the second Gram-Schmidt update. Host
-   pointers, each nullable. */
+/* Instrumentation: Arnoldi steps since the last kv_profile_enable, and of them those that applied
+   the second Gram-Schmidt update. Host pointers, each nullable. */
 kv_status kv_arnoldi_counts(kv_handle h, long long* steps, long long* second_updates);
 
 /* Allocation-free Krylov vector, for callers that cannot allocate device memory (code that

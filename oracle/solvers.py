@@ -201,7 +201,10 @@ def newton(oracle, S0, max_newton, tol, m, max_restarts, lin_tol, sat, bicg_max_
     residual of S (oracle.newton_residual); stop once ||F|| < tol; solve A d = F, A the Krylov
     map at the base S, by GMRES(m) restarted until it converges or saturates, then BiCGstab(2)
     from GMRES's last approximation if it has not converged, keeping whichever correction has the
-    smaller recomputed residual; S <- S - d.
+    smaller recomputed residual; S <- S - d. A BiCGstab(2) correction preferred that way is still
+    dropped for GMRES's when the Newton step with it does not decrease ||F|| (a correction can
+    have the smaller linear residual and still carry a large part the linear residual does not
+    see, as once happened near convergence in mixed precision).
 
     Returns (S, info): iterations, matvecs, res_norms (||F|| at each Newton step start),
     converged, bicg_rejected (BiCGstab(2) results not taken)."""
@@ -226,7 +229,7 @@ def newton(oracle, S0, max_newton, tol, m, max_restarts, lin_tol, sat, bicg_max_
             info["matvecs"] += bi["matvecs"]
             # BiCGstab(2) replaces GMRES's correction only with a smaller recomputed residual
             # (started at the rounding level of the Krylov vectors it can stagnate or diverge)
-            if bi["rel_residual"] < gi["rel_residual"]:
+            if bi["rel_residual"] < gi["rel_residual"] and oracle.newton_residual(S - d2)[1] <= nrm:
                 d = d2
             else:
                 info["bicg_rejected"] += 1

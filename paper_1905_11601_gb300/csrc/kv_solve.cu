@@ -349,7 +349,19 @@ extern "C" kv_status kv_newton(kv_handle h, double* S, double* V, double* work, 
       KV_SOLVE_TRY(kv_bicgstab2(h, F, d, bw, p->bicg_max_iter, p->lin_tol, &bs));
       N.matvecs += bs.matvecs;
       N.bicg_iterations += bs.iterations;
-      if (!(bs.rel_residual < gs.rel_residual)) {
+      // and, preferred that way, it is still dropped when the Newton step with it does not decrease
+      // ||F|| (a correction can have the smaller linear residual and carry a large part the linear
+      // residual does not see); bw, BiCGstab's workspace, is free again for the trial state
+      bool take = bs.rel_residual < gs.rel_residual;
+      if (take) {
+        double* trial = bw;
+        double ntry = 0.0;
+        KV_SOLVE_CUDA(h, cudaMemcpyAsync(trial, S, L * sizeof(double), cudaMemcpyDeviceToDevice, h->s));
+        KV_SOLVE_TRY(axpby(h, -1.0, d, 1.0, trial));
+        KV_SOLVE_TRY(kv_newton_residual(h, trial, bw + L, &ntry));
+        take = ntry <= nrm;
+      }
+      if (!take) {
         KV_SOLVE_CUDA(h, cudaMemcpyAsync(d, V, L * sizeof(double), cudaMemcpyDeviceToDevice, h->s));
         ++N.bicg_rejected;
       }
