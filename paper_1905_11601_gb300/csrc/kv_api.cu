@@ -308,10 +308,7 @@ kv_status simple_project(kv_grid* h, double* yvel, double* p, kv_stats* st) {
   const bool literal = max_passes > 1;
   const bool want = st != nullptr || literal;
   const bool mixed = h->d.precision == KV_PREC_MIXED;
-  // default tolerances: FP64 arithmetic leaves max|D v| h_min / max|v| near 1e-14; the mixed
-  // path's two refinement sweeps leave about 1.4e-12 at 256^3, where an unrefined tensor-core
-  // solve leaves about 1e-7
-  const double tol = h->d.tol > 0 ? h->d.tol : (mixed ? 1e-11 : 1e-12);
+  const double tol = kv_simple_tol(h);
   int pass = 0;
   double maxdiv = 0, rel = 0;
   bool finite = true;

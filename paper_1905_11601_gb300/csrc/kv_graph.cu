@@ -4,7 +4,9 @@
 // precision). For small grids the launch overhead dominates, and independent problems (a block
 // of right-hand sides, several grids or Grashof numbers) leave the GPU idle between launches.
 // The sequences are captured once into a CUDA graph and replayed: one graph launch per batch,
-// with the evaluations of different grids on parallel branches of the graph.
+// with the evaluations of different grids on parallel branches of the graph. In mixed precision
+// a batch is evaluated in blocks of up to KV_BLOCK_MAX vectors whose tensor-core contractions are
+// one launch per axis for the whole block (kv_block.cu).
 #include <algorithm>
 #include <map>
 #include <string>
@@ -35,6 +37,13 @@ extern "C" kv_status kv_krylov_vector_batch(kv_handle h, const double* X, double
   auto it = std::find_if(h->graphs.begin(), h->graphs.end(), [&](const kv_grid::GraphEntry& g) {
     return g.X == X && g.Y == Y && g.nb == nb;
   });
+  // mixed precision: blocks of up to KV_BLOCK_MAX vectors share each contraction launch (their
+  // buffers are allocated here, before any capture)
+  const bool block = h->d.precision == KV_PREC_MIXED;
+  if (it == h->graphs.end() && block) {
+    const kv_status bs = kv_mixed_block_setup(h, nb < KV_BLOCK_MAX ? nb : KV_BLOCK_MAX);
+    if (bs != KV_OK) return bs;
+  }
   if (it == h->graphs.end()) {
     cudaError_t e;
     if (!h->cap && (e = cudaStreamCreateWithFlags(&h->cap, cudaStreamNonBlocking)) != cudaSuccess)
@@ -52,8 +61,15 @@ extern "C" kv_status kv_krylov_vector_batch(kv_handle h, const double* X, double
     if ((e = cudaStreamBeginCapture(h->cap, cudaStreamCaptureModeThreadLocal)) != cudaSuccess) {
       st = set_err(h, KV_ERR_CUDA, std::string("cudaStreamBeginCapture: ") + cudaGetErrorString(e));
     } else {
-      for (int b = 0; b < nb && st == KV_OK; ++b)
-        st = kv_krylov_vector(h, X + (size_t)b * L, Y + (size_t)b * L, nullptr, nullptr);
+      if (block) {
+        for (int b0 = 0; b0 < nb && st == KV_OK; b0 += h->blk_cap) {
+          const int cnt = nb - b0 < h->blk_cap ? nb - b0 : h->blk_cap;
+          st = kv_krylov_block(h, X + (size_t)b0 * L, Y + (size_t)b0 * L, cnt);
+        }
+      } else {
+        for (int b = 0; b < nb && st == KV_OK; ++b)
+          st = kv_krylov_vector(h, X + (size_t)b * L, Y + (size_t)b * L, nullptr, nullptr);
+      }
       e = cudaStreamEndCapture(h->cap, &graph);
       if (st == KV_OK && e != cudaSuccess)
         st = set_err(h, KV_ERR_CUDA, std::string("cudaStreamEndCapture: ") + cudaGetErrorString(e));

@@ -119,6 +119,17 @@ struct kv_grid {
   size_t xs_slice = 0;                   // elements per data slice
   float* lamf[3] = {};
   CUtensorMap mapA[6], mapB[6];
+
+  // block evaluations (kv_krylov_vector_batch in mixed precision; kv_block.cu): per-vector
+  // buffers for up to blk_cap vectors, allocated at the first block call
+  int blk_cap = 0;
+  double* blk_vstar = nullptr;           // blk_cap x 3P: each vector's momentum right-hand side
+  double* blk_b = nullptr;               // blk_cap x Nc: divergences
+  double* blk_phi = nullptr;             // blk_cap x Nc
+  float* blk_phi32 = nullptr;            // blk_cap x Nc
+  __nv_bfloat16* blk_xs[2] = {};         // 3 slices x blk_cap x xs_slice each: slice s of vector v at
+                                         // s * blk_cap * xs_slice + v * xs_slice
+  CUtensorMap blk_mapB[6];
   unsigned int* derr = nullptr;          // device error flag (bounded waits that expired)
   unsigned long long* rmax = nullptr;    // max |r| of the last refinement residual (bits)
 
@@ -178,10 +189,17 @@ struct KvUmmaEpi {
   const float* lb;
   unsigned int wait_limit;  // iterations of each bounded mbarrier wait (0: the default)
   unsigned int extra_tx;    // self-test only: bytes expected beyond what TMA delivers (0 normally)
+  int nvec;                 // vectors contracted by the launch (block evaluations; 0 or 1: one)
+  size_t vstride_out;       // elements between consecutive vectors' outputs within an output slice
+  size_t vstride_phi;       // elements between consecutive vectors' phi (modes 2-5)
 };
 cudaError_t kv_umma_init();
 bool kv_make_slice_map(CUtensorMap* map, const void* base, int cols, int rows, int pitch, size_t slice_elems,
                        int box_rows);
+// The data operand's map: nvec vectors of `rows` x `cols` BF16 (row pitch `pitch`), vector v's rows
+// `vec_elems` after vector v-1's, three slices `slice_elems` apart (a one-vector map for nvec = 1).
+bool kv_make_data_map(CUtensorMap* map, const void* base, int cols, int rows, int pitch, int nvec, size_t vec_elems,
+                      size_t slice_elems, int box_rows);
 int kv_umma_box_rows_a();
 int kv_umma_box_rows_b();
 cudaError_t kv_launch_umma_axis(const CUtensorMap* mapA, const CUtensorMap* mapB, int K, const KvUmmaEpi& ep,
@@ -207,9 +225,26 @@ void kv_mixed_free(kv_grid* h);
 // slices_ready: the BF16 slices of b are already in h->xs[0] (written by the divergence)
 void kv_launch_poisson_mixed(kv_grid* h, const double* b, double* phi, int stats, int slices_ready, cudaStream_t s);
 kv_status kv_mixed_selftest_timeout(kv_grid* h, int* device_error);
+// The same solve for nb <= h->blk_cap vectors at once (h->blk_* buffers): the divergences have
+// written each vector's b and BF16 slices; each of the 6 contractions per sweep is one launch for
+// the whole block; the residuals run per vector.
+kv_status kv_mixed_block_setup(kv_grid* h, int cap);
+void kv_launch_poisson_mixed_block(kv_grid* h, int nb, cudaStream_t s);
+void kv_mixed_block_free(kv_grid* h);
 
 // kv_api.cu: sets the thread's message returned by kv_last_error(NULL)
 void kv_set_thread_error(const std::string& msg);
+
+// The SIMPLE tolerance of a grid: desc.tol, or the default of its precision. FP64 leaves
+// max|D v| h_min / max|v| near 1e-14; the mixed path's two refinement sweeps leave about 1.4e-12
+// at 256^3, where an unrefined tensor-core solve leaves about 1e-7.
+inline double kv_simple_tol(const kv_grid* h) {
+  return h->d.tol > 0 ? h->d.tol : (h->d.precision == KV_PREC_MIXED ? 1e-11 : 1e-12);
+}
+
+// kv_block.cu: Y_v = A X_v for v < nb <= h->blk_cap, mixed precision, with the block contractions
+constexpr int KV_BLOCK_MAX = 16;
+kv_status kv_krylov_block(kv_grid* h, const double* X, double* Y, int nb);
 
 // kv_adjoint.cu
 void kv_launch_adj_prep(const kv_grid* h, const double* y, double* vel, double* tout, cudaStream_t s);
@@ -237,6 +272,9 @@ void kv_launch_apply_df(const kv_grid* h, const float2* cdf, const double* x, do
 
 // kv_project.cu
 void kv_launch_divergence(const kv_grid* h, const double* vel, double* b, cudaStream_t s);
+// as kv_launch_divergence, with the mixed path's BF16 slices of b written to xs (slices `slice` apart)
+void kv_launch_divergence_to(const kv_grid* h, const double* vel, double* b, __nv_bfloat16* xs, size_t slice,
+                             cudaStream_t s);
 // out_vel = vstar - G phi on interior faces (0 elsewhere); p (nullable) = phi (+ p if accumulate);
 // with check != 0 also reduces max |D out_vel| and max |out_vel| into h->red (the SIMPLE test).
 void kv_launch_correct(const kv_grid* h, const double* vstar, const double* phi, double* out_vel,

@@ -169,7 +169,7 @@ kv_status kv_mixed_setup(kv_grid* h, const double* const fwd[3], const double* c
     const int R = (int)(h->Nc / n[a]);
     const __nv_bfloat16* in = h->xs[p % 2];
     if (!kv_make_slice_map(&h->mapA[p], h->wsl[p], K, M, pad8(K), (size_t)M * pad8(K), kv_umma_box_rows_a()) ||
-        !kv_make_slice_map(&h->mapB[p], in, K, R, pad8(K), h->xs_slice, kv_umma_box_rows_b())) {
+        !kv_make_data_map(&h->mapB[p], in, K, R, pad8(K), 1, h->xs_slice, h->xs_slice, kv_umma_box_rows_b())) {
       h->err = "cuTensorMapEncodeTiled failed";
       return KV_ERR_CUDA;
     }
@@ -187,6 +187,50 @@ void kv_mixed_free(kv_grid* h) {
   cudaFree(h->derr);
   cudaFree(h->rmax);
   cudaFree(h->phi32);
+  kv_mixed_block_free(h);
+}
+
+void kv_mixed_block_free(kv_grid* h) {
+  cudaFree(h->blk_vstar);
+  cudaFree(h->blk_b);
+  cudaFree(h->blk_phi);
+  cudaFree(h->blk_phi32);
+  for (int q = 0; q < 2; ++q) cudaFree(h->blk_xs[q]);
+  h->blk_vstar = h->blk_b = h->blk_phi = nullptr;
+  h->blk_phi32 = nullptr;
+  h->blk_xs[0] = h->blk_xs[1] = nullptr;
+  h->blk_cap = 0;
+}
+
+kv_status kv_mixed_block_setup(kv_grid* h, int cap) {
+  if (h->blk_cap >= cap) return KV_OK;
+  kv_mixed_block_free(h);
+  const int n[3] = {h->g.nx, h->g.ny, h->g.nz};
+  const size_t xsb = (size_t)3 * cap * h->xs_slice;
+  cudaError_t e;
+  if ((e = cudaMalloc(&h->blk_vstar, (size_t)cap * 3 * h->P * sizeof(double))) != cudaSuccess ||
+      (e = cudaMalloc(&h->blk_b, (size_t)cap * h->Nc * sizeof(double))) != cudaSuccess ||
+      (e = cudaMalloc(&h->blk_phi, (size_t)cap * h->Nc * sizeof(double))) != cudaSuccess ||
+      (e = cudaMalloc(&h->blk_phi32, (size_t)cap * h->Nc * sizeof(float))) != cudaSuccess ||
+      (e = cudaMalloc(&h->blk_xs[0], xsb * sizeof(__nv_bfloat16))) != cudaSuccess ||
+      (e = cudaMalloc(&h->blk_xs[1], xsb * sizeof(__nv_bfloat16))) != cudaSuccess) {
+    kv_mixed_block_free(h);
+    h->err = std::string("block buffers: ") + cudaGetErrorString(e);
+    return e == cudaErrorMemoryAllocation ? KV_ERR_NOMEM : KV_ERR_CUDA;
+  }
+  for (int p = 0; p < 6; ++p) {
+    const int a = kPass[p].axis;
+    const int K = n[a];
+    const int R = (int)(h->Nc / n[a]);
+    if (!kv_make_data_map(&h->blk_mapB[p], h->blk_xs[p % 2], K, R, pad8(K), cap, h->xs_slice,
+                          (size_t)cap * h->xs_slice, kv_umma_box_rows_b())) {
+      kv_mixed_block_free(h);
+      h->err = "cuTensorMapEncodeTiled failed (block maps)";
+      return KV_ERR_CUDA;
+    }
+  }
+  h->blk_cap = cap;
+  return KV_OK;
 }
 
 void kv_launch_poisson_mixed(kv_grid* h, const double* b, double* phi, int stats, int slices_ready, cudaStream_t s) {
@@ -233,6 +277,56 @@ void kv_launch_poisson_mixed(kv_grid* h, const double* b, double* phi, int stats
       } else {
         auto kern = str ? k_residual_slices<double, true> : k_residual_slices<double, false>;
         kern<<<rg, rb, 0, s>>>(g, h->str, b, phi, h->xs[0], h->xs_slice, pad8(g.nx), rm, cx, cy, cz);
+      }
+    }
+  }
+}
+
+void kv_launch_poisson_mixed_block(kv_grid* h, int nb, cudaStream_t s) {
+  const KvGeom& g = h->g;
+  const int n[3] = {g.nx, g.ny, g.nz};
+  const size_t bslice = (size_t)h->blk_cap * h->xs_slice;  // elements between slices of the block buffers
+  dim3 rb(32, 8, 1), rg((g.nx + 31) / 32, (g.ny + 7) / 8, g.nz);
+  const float2 cx = host_pair(g.ihx2), cy = host_pair(g.ihy2), cz = host_pair(g.ihz2);
+  const bool str = h->str.sw != nullptr;
+  for (int sweep = 0; sweep < h->refine; ++sweep) {
+    for (int p = 0; p < 6; ++p) {
+      const PassSpec& ps = kPass[p];
+      KvUmmaEpi ep{};
+      ep.M = n[ps.axis];
+      ep.R = (int)(h->Nc / n[ps.axis]);
+      ep.na = n[ps.a];
+      ep.nb = n[ps.b];
+      ep.pitch = pad8(n[ps.b]);
+      ep.slice = bslice;
+      ep.out = h->blk_xs[(p + 1) % 2];
+      const bool single = h->refine == 1;
+      ep.mode = (p == 2) ? 1 : (p == 5 ? (sweep == 0 ? (single ? 3 : 4) : (sweep == 1 ? 5 : 2)) : 0);
+      ep.phi = h->blk_phi;
+      ep.phi32 = h->blk_phi32;
+      ep.lz = h->lamf[ps.axis];
+      ep.la = h->lamf[ps.a];
+      ep.lb = h->lamf[ps.b];
+      ep.nvec = nb;
+      ep.vstride_out = h->xs_slice;
+      ep.vstride_phi = h->Nc;
+      KvPhase ph(h, KV_PH_TPD, 1);
+      kv_launch_umma_axis(&h->mapA[p], &h->blk_mapB[p], n[ps.axis], ep, h->derr, s);
+    }
+    if (sweep + 1 < h->refine) {
+      KvPhase ph(h, KV_PH_REFINE, nb);
+      for (int v = 0; v < nb; ++v) {
+        const double* b = h->blk_b + (size_t)v * h->Nc;
+        __nv_bfloat16* xs = h->blk_xs[0] + (size_t)v * h->xs_slice;
+        if (sweep == 0) {
+          auto kern = str ? k_residual_slices<float, true> : k_residual_slices<float, false>;
+          kern<<<rg, rb, 0, s>>>(g, h->str, b, h->blk_phi32 + (size_t)v * h->Nc, xs, bslice, pad8(g.nx), nullptr, cx,
+                                 cy, cz);
+        } else {
+          auto kern = str ? k_residual_slices<double, true> : k_residual_slices<double, false>;
+          kern<<<rg, rb, 0, s>>>(g, h->str, b, h->blk_phi + (size_t)v * h->Nc, xs, bslice, pad8(g.nx), nullptr, cx,
+                                 cy, cz);
+        }
       }
     }
   }

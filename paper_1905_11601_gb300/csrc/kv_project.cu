@@ -346,13 +346,18 @@ float2 pair_of(double x) {
 }  // namespace
 
 void kv_launch_divergence(const kv_grid* h, const double* vel, double* b, cudaStream_t s) {
+  kv_launch_divergence_to(h, vel, b, h->xs[0], h->xs_slice, s);
+}
+
+void kv_launch_divergence_to(const kv_grid* h, const double* vel, double* b, __nv_bfloat16* xs, size_t slice,
+                             cudaStream_t s) {
   const KvGeom& g = h->g;
   dim3 block(32, 8, 1), grid((g.nx + 31) / 32, (g.ny + 7) / 8, g.nz);
   const bool str = h->str.sw != nullptr;
   if (h->d.precision == KV_PREC_MIXED) {
     auto kern = str ? k_divergence_df<true> : k_divergence_df<false>;
-    kern<<<grid, block, 0, s>>>(g, h->str, vel, h->P, b, pair_of(g.ihx), pair_of(g.ihy), pair_of(g.ihz), h->xs[0],
-                                h->xs_slice, (g.nx + 7) & ~7);
+    kern<<<grid, block, 0, s>>>(g, h->str, vel, h->P, b, pair_of(g.ihx), pair_of(g.ihy), pair_of(g.ihz), xs, slice,
+                                (g.nx + 7) & ~7);
   } else {
     auto kern = str ? k_divergence<true> : k_divergence<false>;
     kern<<<grid, block, 0, s>>>(g, h->str, vel, h->P, b);

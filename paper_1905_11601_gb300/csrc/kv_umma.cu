@@ -86,6 +86,14 @@ __device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap* map
       "l"((uint64_t)map), "r"(c0), "r"(c1), "r"(c2), "r"(bar)
       : "memory");
 }
+__device__ __forceinline__ void tma_load_4d(uint32_t dst, const CUtensorMap* map, int c0, int c1, int c2, int c3,
+                                            uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.4d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5}], "
+      "[%6];" ::"r"(dst),
+      "l"((uint64_t)map), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(bar)
+      : "memory");
+}
 
 // Shared-memory matrix descriptor (K-major operand, 128-byte swizzle, 8-row groups of 1024 B).
 __device__ __forceinline__ uint64_t sdesc(uint32_t saddr) {
@@ -145,8 +153,10 @@ __device__ __forceinline__ void split3(float x, __nv_bfloat16& s1, __nv_bfloat16
 
 namespace {
 
-// Persistent: CTA b handles tiles b, b + gridDim.x, ...; tile t covers rows m0 = (t % ntm) * 128
-// and columns r0 = (t / ntm) * 256, so CTAs that run together share their X tiles in L2.
+// Persistent: CTA b handles tiles b, b + gridDim.x, ...; tile t covers vector t / (ntm ntr), and
+// within it rows m0 = (t % ntm) * 128 and columns r0 = ((t / ntm) % ntr) * 256, so CTAs that run
+// together share their X tiles in L2. A block of vectors is one launch: its tiles fill the GPU
+// evenly where one vector's do not.
 __global__ void __launch_bounds__(THREADS, 1)
     k_umma_axis(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB, int K,
                 KvUmmaEpi ep, unsigned int* err) {
@@ -162,7 +172,8 @@ __global__ void __launch_bounds__(THREADS, 1)
   const uint32_t accf0 = smem_u32(bars + 2 * AR + 2 * BR), acce0 = smem_u32(bars + 2 * AR + 2 * BR + 2);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int ntm = (ep.M + UM - 1) / UM, ntr = (ep.R + UN - 1) / UN, ntiles = ntm * ntr;
+  const int ntm = (ep.M + UM - 1) / UM, ntr = (ep.R + UN - 1) / UN, nvt = ntm * ntr;
+  const int ntiles = nvt * (ep.nvec > 1 ? ep.nvec : 1);
   const uint32_t lim = ep.wait_limit ? ep.wait_limit : WAIT_LIMIT;
   const int kchunks = (K + UK - 1) / UK;
 
@@ -199,7 +210,8 @@ __global__ void __launch_bounds__(THREADS, 1)
       uint32_t ga = 0, gb = 0;  // ring positions, continued across tiles
       bool ok = true;
       for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
-        const int m0 = (t % ntm) * UM, r0 = (t / ntm) * UN;
+        const int vec = t / nvt, tv = t - vec * nvt;
+        const int m0 = (tv % ntm) * UM, r0 = (tv / ntm) * UN;
         // phase 0: the slices of the five products with i + j >= 1; phase 1: W_0 and X_0 only
         for (int ph = 0; ph < 2 && ok; ++ph) {
           const int ns = ph == 0 ? 3 : 1;
@@ -214,7 +226,7 @@ __global__ void __launch_bounds__(THREADS, 1)
               const int s = gb % BR;
               if (!(ok = mbar_wait(emptyB0 + 8 * s, ((gb / BR) & 1u) ^ 1u, err, lim))) break;
               mbar_expect_tx(fullB0 + 8 * s, B_BYTES + ep.extra_tx);
-              tma_load_3d(smem_u32(bring + s * B_BYTES), &mapB, kc * UK, r0, j, fullB0 + 8 * s);
+              tma_load_4d(smem_u32(bring + s * B_BYTES), &mapB, kc * UK, r0, vec, j, fullB0 + 8 * s);
             }
           }
         }
@@ -281,15 +293,22 @@ __global__ void __launch_bounds__(THREADS, 1)
     // groups of 4 outputs are contiguous and 8-byte aligned (slices) or 32-byte aligned (phi)
     // when the inner extent and R are multiples of 4 (and the slice pitch and size are)
     const bool to_phi = ep.mode >= 2;
-    const bool vec4 = (ep.R % 4 == 0) && (to_phi || (ep.nb % 4 == 0 && ep.pitch % 4 == 0 && ep.slice % 4 == 0));
+    // (and the per-vector offsets of a block keep that alignment)
+    const bool vec4 = (ep.R % 4 == 0) && (to_phi || (ep.nb % 4 == 0 && ep.pitch % 4 == 0 && ep.slice % 4 == 0)) &&
+                      (ep.nvec <= 1 || (ep.vstride_out % 4 == 0 && ep.vstride_phi % 4 == 0));
     int lt = 0;
     for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++lt) {
       const int buf = lt & 1;
       const uint32_t use = (uint32_t)(lt >> 1);
       if (!mbar_wait(accf0 + 8 * buf, use & 1u, err, lim)) break;
       tc_fence_after();
-      const int m0 = (t % ntm) * UM, r0 = (t / ntm) * UN;
+      const int vec = t / nvt, tv = t - vec * nvt;
+      const int m0 = (tv % ntm) * UM, r0 = (tv / ntm) * UN;
       const int mrow0 = m0 + 32 * q;
+      // this vector's outputs
+      __nv_bfloat16* const vout = ep.out ? ep.out + (size_t)vec * ep.vstride_out : nullptr;
+      double* const vphi = ep.phi ? ep.phi + (size_t)vec * ep.vstride_phi : nullptr;
+      float* const vphi32 = ep.phi32 ? ep.phi32 + (size_t)vec * ep.vstride_phi : nullptr;
       for (int c = c0; c < c0 + EPI_COLS; c += EPI_CHUNK) {
         float v[EPI_CHUNK];
         tmem_ld16(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(buf * UN + c), v);
@@ -317,9 +336,9 @@ __global__ void __launch_bounds__(THREADS, 1)
               if (to_phi) {
                 const size_t o = (size_t)m * ep.R + r;
                 if (ep.mode == 4) {
-                  *reinterpret_cast<float4*>(ep.phi32 + o) = make_float4(d[0], d[1], d[2], d[3]);
+                  *reinterpret_cast<float4*>(vphi32 + o) = make_float4(d[0], d[1], d[2], d[3]);
                 } else {
-                  double2* p = reinterpret_cast<double2*>(ep.phi + o);
+                  double2* p = reinterpret_cast<double2*>(vphi + o);
                   double2 p0 = make_double2(df_f2d(d[0]), df_f2d(d[1])), p1 = make_double2(df_f2d(d[2]), df_f2d(d[3]));
                   if (ep.mode == 2) {
                     const double2 q0 = p[0], q1 = p[1];
@@ -328,7 +347,7 @@ __global__ void __launch_bounds__(THREADS, 1)
                     p1.x += q1.x;
                     p1.y += q1.y;
                   } else if (ep.mode == 5) {
-                    const float4 q = *reinterpret_cast<const float4*>(ep.phi32 + o);
+                    const float4 q = *reinterpret_cast<const float4*>(vphi32 + o);
                     p0.x += df_f2d(q.x);
                     p0.y += df_f2d(q.y);
                     p1.x += df_f2d(q.z);
@@ -351,7 +370,7 @@ __global__ void __launch_bounds__(THREADS, 1)
                 const size_t o = ((size_t)m * ep.na + a) * ep.pitch + bcol;
 #pragma unroll
                 for (int sl = 0; sl < 3; ++sl)
-                  *reinterpret_cast<uint2*>(ep.out + (size_t)sl * ep.slice + o) = *reinterpret_cast<const uint2*>(s[sl]);
+                  *reinterpret_cast<uint2*>(vout + (size_t)sl * ep.slice + o) = *reinterpret_cast<const uint2*>(s[sl]);
               }
             }
           }
@@ -373,11 +392,11 @@ __global__ void __launch_bounds__(THREADS, 1)
               if (to_phi) {
                 const size_t o = (size_t)m * ep.R + r;
                 if (ep.mode == 4)
-                  ep.phi32[o] = d;
+                  vphi32[o] = d;
                 else if (ep.mode == 5)
-                  ep.phi[o] = df_f2d(ep.phi32[o]) + df_f2d(d);
+                  vphi[o] = df_f2d(vphi32[o]) + df_f2d(d);
                 else
-                  ep.phi[o] = ep.mode == 2 ? ep.phi[o] + df_f2d(d) : df_f2d(d);
+                  vphi[o] = ep.mode == 2 ? vphi[o] + df_f2d(d) : df_f2d(d);
               } else {
                 if (ep.mode == 1) {
                   const float lam = ep.lz[m] + ep.la[a] + ep.lb[bcol];
@@ -386,9 +405,9 @@ __global__ void __launch_bounds__(THREADS, 1)
                 __nv_bfloat16 s1, s2, s3;
                 split3(d, s1, s2, s3);
                 const size_t o = ((size_t)m * ep.na + a) * ep.pitch + bcol;
-                ep.out[o] = s1;
-                ep.out[ep.slice + o] = s2;
-                ep.out[2 * ep.slice + o] = s3;
+                vout[o] = s1;
+                vout[ep.slice + o] = s2;
+                vout[2 * ep.slice + o] = s3;
               }
             }
           }
@@ -443,6 +462,20 @@ bool kv_make_slice_map(CUtensorMap* map, const void* base, int cols, int rows, i
   return r == CUDA_SUCCESS;
 }
 
+bool kv_make_data_map(CUtensorMap* map, const void* base, int cols, int rows, int pitch, int nvec, size_t vec_elems,
+                      size_t slice_elems, int box_rows) {
+  EncodeTiledFn fn = encode_fn();
+  if (!fn) return false;
+  cuuint64_t dims[4] = {(cuuint64_t)cols, (cuuint64_t)rows, (cuuint64_t)nvec, 3};
+  cuuint64_t strides[3] = {(cuuint64_t)pitch * 2, (cuuint64_t)vec_elems * 2, (cuuint64_t)slice_elems * 2};
+  cuuint32_t box[4] = {(cuuint32_t)UK, (cuuint32_t)box_rows, 1, 1};
+  cuuint32_t estr[4] = {1, 1, 1, 1};
+  CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<void*>(base), dims, strides, box, estr,
+                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS;
+}
+
 int kv_umma_box_rows_a() { return UM; }
 int kv_umma_box_rows_b() { return UN; }
 
@@ -468,7 +501,7 @@ cudaError_t kv_launch_umma_axis(const CUtensorMap* mapA, const CUtensorMap* mapB
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (sms <= 0) sms = 1;
   }
-  const int tiles = ((ep.R + UN - 1) / UN) * ((ep.M + UM - 1) / UM);
+  const int tiles = ((ep.R + UN - 1) / UN) * ((ep.M + UM - 1) / UM) * (ep.nvec > 1 ? ep.nvec : 1);
   k_umma_axis<<<tiles < sms ? tiles : sms, THREADS, SMEM_BYTES, s>>>(*mapA, *mapB, K, ep, err);
   return cudaGetLastError();
 }

@@ -103,3 +103,23 @@ def test_host_stream_matches_single_host_calls():
             g.krylov_vector_host(Xh[i].contiguous(), y1)
             assert torch.equal(Yh[i], y1), (prec, i)
         g.krylov_vector_host_stream(Xh[:0], Yh[:0])  # nb = 0 does nothing
+
+
+@pytest.mark.parametrize("n,bc,tproj,count", [((70, 65, 67), synth.CC, 0, 3), ((33, 18, 20), synth.AA, 1, 18)])
+def test_mixed_blocks_equal_single_calls(n, bc, tproj, count):
+    """Mixed-precision batches go through blocks of up to 16 vectors whose tensor-core
+    contractions are one launch per axis for the whole block. Each vector's tiles do the same
+    arithmetic as a single evaluation, so the results equal single calls bit for bit: on a grid
+    whose cell count is not a multiple of 4 (the contraction's epilogue then takes its scalar
+    stores) and for 18 vectors (a block of 16 and one of 2), insulated walls, oblique reading."""
+    from paper_1905_11601_gb300 import kv
+    g = kv.Grid(*n, bc=bc, gr=3e6, tproj=tproj, precision=kv.KV_PREC_MIXED)
+    g.set_base_flow(torch.from_numpy(np.stack(synth.base_flow(*n, bc, 141))).cuda())
+    X = torch.from_numpy(synth.krylov_input(*n, 142, count=count)).cuda()
+    ref = torch.stack([g.krylov_vector(X[b].contiguous()) for b in range(count)])
+    g.guard(reset=True)
+    Y = g.krylov_vector_batch(X)
+    torch.cuda.synchronize()
+    assert torch.equal(Y, ref)
+    gd = g.guard()
+    assert gd["checks"] == count and gd["failed"] == 0 and gd["nonfinite"] == 0, gd
