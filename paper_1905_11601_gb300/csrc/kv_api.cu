@@ -256,6 +256,7 @@ void free_all(kv_grid* h) {
   cudaFree(h->sw);
   cudaFree(h->swd);
   cudaFree(h->coef_dfp);
+  kv_fx_free(h);
   cudaFree(h->guard);
   h->red = nullptr;
   cudaFree(h->partials);
@@ -411,11 +412,13 @@ kv_status autotune_apply(kv_grid* h) {
     // the double-float operator: variant 0 (split pass, then cells per row x rows per block, four
     // equation rows each, <= 512 threads) or variant 1 (the 2.5D march, planes per block)
     static const int dcand[][3] = {{0, 32, 1}, {0, 32, 2}, {0, 64, 1}, {0, 32, 4}, {0, 64, 2}, {0, 128, 1},
-                                   {1, 0, 16}, {1, 0, 32}, {1, 0, 64}};
+                                   {1, 0, 16}, {1, 0, 32}, {1, 0, 64}, {2, 0, 8},  {2, 0, 16}, {2, 0, 32},
+                                   {2, 0, 64}};
     best = 1e30f;
     int dv = 0, dbx = 32, dby = 2;
     for (auto& c : dcand) {
       if (c[0] == 1 && 4 * h->P >= (size_t(1) << 31)) continue;  // the march indexes x with 32 bits
+      if (c[0] == 2 && !h->fx_ok) continue;                        // fixed point: uniform cubic grids
       h->df_variant = c[0];
       h->df_bx = c[1];
       h->df_by = c[2];
@@ -678,6 +681,8 @@ static kv_status base_flow_ready(kv_grid* h) {
       if (s != KV_OK) return s;
     }
     kv_launch_coef_df(h, h->coef, h->coef_df, h->s);
+    kv_status fs = kv_fx_setup(h);
+    if (fs != KV_OK) return fail(h, fs, "kv_set_base_flow: the fixed-point operator's set-up failed");
   }
   kv_status ks = check_launch(h, "assemble");
   if (ks != KV_OK) return ks;
@@ -727,8 +732,15 @@ kv_status kv_set_tuning(kv_handle h, const int* cfg) {
         return fail(h, KV_ERR_ARG, "kv_set_tuning: the march indexes a packed vector with 32 bits; this grid is too "
                                    "large for it");
       dbx = 0;
+    } else if (dv == 2) {
+      if (dby < 1 || dby > 1024)
+        return fail(h, KV_ERR_ARG, "kv_set_tuning: the fixed-point march needs 1..1024 planes per block");
+      if (!kv_fx_eligible(h))
+        return fail(h, KV_ERR_ARG, "kv_set_tuning: the fixed-point operator serves uniform cubic mixed-precision "
+                                   "grids whose packed vectors fit 32-bit offsets");
+      dbx = 0;
     } else {
-      return fail(h, KV_ERR_ARG, "kv_set_tuning: cfg[2] (the double-float operator variant) must be 0 or 1");
+      return fail(h, KV_ERR_ARG, "kv_set_tuning: cfg[2] (the mixed operator variant) must be 0, 1 or 2");
     }
   }
   h->apply_bx = bx;

@@ -10,6 +10,7 @@
 #include <vector>
 
 #include "kv.h"
+#include "kv_fixed.cuh"
 
 // timed phases (kv_profile_get)
 enum { KV_PH_STENCIL = 0, KV_PH_DIV = 1, KV_PH_TPD = 2, KV_PH_CORRECT = 3, KV_PH_ARNOLDI = 4, KV_PH_REFINE = 5,
@@ -130,6 +131,12 @@ struct kv_grid {
   __nv_bfloat16* blk_xs[2] = {};         // 3 slices x blk_cap x xs_slice each: slice s of vector v at
                                          // s * blk_cap * xs_slice + v * xs_slice
   CUtensorMap blk_mapB[6];
+  // the fixed-point operator (kv_fixed.cu; uniform cubic mixed grids): the base state on its
+  // fixed-point grid, the pre-pass maxima ([0] the input's, [1] the base state's), the constants
+  int2* base_fx = nullptr;               // 4P
+  unsigned int* fxmax = nullptr;         // 2
+  FxConst fxk{};
+  bool fx_ok = false;                    // set per base flow by kv_fx_setup
   unsigned int* derr = nullptr;          // device error flag (bounded waits that expired)
   unsigned long long* rmax = nullptr;    // max |r| of the last refinement residual (bits)
 
@@ -156,7 +163,8 @@ struct kv_grid {
 
   // block shape of the linearised-operator kernel, chosen by timing (kv_autotune_apply)
   int apply_bx = 32, apply_by = 8;
-  int df_variant = 0, df_bx = 32, df_by = 2;  // the mixed path's double-float operator (kv_stencil.cu)
+  int df_variant = 0, df_bx = 32, df_by = 2;  // the mixed path's operator: 0, 1 double-float
+                                              // (kv_stencil.cu), 2 fixed point (kv_fixed.cu)
   bool tuned = false;
   bool pinned = false;  // kv_set_tuning fixed the configuration: the autotuner does not run
 
@@ -267,6 +275,11 @@ void kv_launch_apply(const kv_grid* h, const double* coef, const double* x, doub
 // mixed precision: FP32-pair copy of the coefficients, and J P_BC x in double-float on the FP32 pipe
 // (P_BC x is first split into h->xsplit)
 void kv_launch_coef_df(const kv_grid* h, const double* coef, float2* cdf, cudaStream_t s);
+// kv_fixed.cu
+bool kv_fx_eligible(const kv_grid* h);
+kv_status kv_fx_setup(kv_grid* h);
+void kv_fx_free(kv_grid* h);
+void kv_launch_apply_fx(const kv_grid* h, const double* x, double* vstar, double* tout, int kc, cudaStream_t s);
 void kv_launch_apply_df(const kv_grid* h, const float2* cdf, const double* x, double* vstar, double* tout,
                         cudaStream_t s);
 

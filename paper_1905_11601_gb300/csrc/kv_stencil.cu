@@ -946,7 +946,12 @@ void kv_launch_apply_df(const kv_grid* h, const float2* cdf, const double* x, do
   for (int d = 0; d < 2; ++d)
     for (int ax = 0; ax < 3; ++ax)
       for (int c = 0; c < 3; ++c) al.a[d][ax][c] = host_pair(fac[c] * diff[d] * ih2[ax]);
-  if (h->df_variant == 1) {
+  if (h->df_variant == 2 && h->fx_ok) {  // fixed point, df_by planes per block (kv_fixed.cu)
+    kv_launch_apply_fx(h, x, vstar, tout, h->df_by, s);
+    return;
+  }
+  // variant 2 on a base state the fixed-point form does not take (non-finite): the march
+  if (h->df_variant == 1 || h->df_variant == 2) {
     // the 2.5D march: df_by planes per block
     k_zero_boundary<<<2 * 152, 256, 0, s>>>(g, h->P, vstar, tout);
     const int kc = h->df_by;

@@ -24,9 +24,11 @@ torch = pytest.importorskip("torch")
 
 FP64_BLOCKS = [(32, 8), (64, 4), (128, 2), (32, 4), (16, 16), (256, 1)]
 DF_VARIANTS = [(0, 32, 1), (0, 32, 2), (0, 64, 1), (0, 32, 4), (0, 64, 2), (0, 128, 1), (1, 0, 16), (1, 0, 32),
-               (1, 0, 64)]
+               (1, 0, 64), (2, 0, 8), (2, 0, 16), (2, 0, 32), (2, 0, 64)]
 CASES = [((70, 65, 67), synth.CC, 2e6, 0), ((33, 18, 20), synth.AA, 3e6, 0), ((33, 18, 20), synth.AA, 3e6, 1),
          ((9, 130, 12), synth.AA, 3e6, 1)]
+# the fixed-point operator (variant 2) serves cubic grids: ragged cubes against the tiles
+CUBES = [((37, 37, 37), synth.CC, 2e6, 0), ((33, 33, 33), synth.AA, 3e6, 1), ((20, 20, 20), synth.AA, 3e6, 0)]
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -82,7 +84,7 @@ def test_every_fp64_block_shape_matches_oracle(n, bc, gr, tproj):
         check(g.krylov_vector(xt).cpu().numpy(), y_ref, TOL64, blk)
 
 
-@pytest.mark.parametrize("n,bc,gr,tproj", CASES + [((128, 128, 128), synth.AA, 3e6, 0)])
+@pytest.mark.parametrize("n,bc,gr,tproj", CASES + CUBES + [((128, 128, 128), synth.AA, 3e6, 0)])
 def test_every_double_float_variant_matches_oracle(n, bc, gr, tproj):
     kv = kvmod()
     base, x, y_ref = reference(n, bc, gr, tproj)
@@ -90,7 +92,12 @@ def test_every_double_float_variant_matches_oracle(n, bc, gr, tproj):
     g.set_tuning(apply_block=(32, 8), df_variant=1, df_block=(0, 32))
     g.set_base_flow(torch.from_numpy(base).cuda())
     xt = torch.from_numpy(x).cuda()
+    cubic = n[0] == n[1] == n[2]
     for v, bx, by in DF_VARIANTS:
+        if v == 2 and not cubic:
+            with pytest.raises(kv.KvError):
+                g.set_tuning(apply_block=(32, 8), df_variant=v, df_block=(bx, by))
+            continue
         g.set_tuning(apply_block=(32, 8), df_variant=v, df_block=(bx, by))
         t = g.tuning()
         assert t["df_variant"] == v and t["df_block"][1] == by
@@ -257,7 +264,8 @@ def test_field_sizes_and_the_four_pointer_base_flow():
 def test_set_tuning_rejects_bad_configurations():
     kv = kvmod()
     g = kv.Grid(8, 8, 8, precision=kv.KV_PREC_MIXED)
-    for bad in [((0, 8), 1, (0, 32)), ((32, 9), 1, (0, 32)), ((512, 1), 1, (0, 32)), ((32, 8), 2, (0, 32)),
+    for bad in [((0, 8), 1, (0, 32)), ((32, 9), 1, (0, 32)), ((512, 1), 1, (0, 32)), ((32, 8), 3, (0, 32)),
+                ((32, 8), 2, (0, 0)),
                 ((32, 8), 0, (48, 1)), ((32, 8), 0, (128, 2)), ((32, 8), 1, (0, 0))]:
         with pytest.raises(kv.KvError) as e:
             g.set_tuning(*bad)
@@ -292,3 +300,37 @@ def test_arnoldi_counts_and_device_decision_match_forced_updates():
         assert np.abs(G - np.eye(k + 1)).max() < 1e-13
         Hs.append(H)
     assert np.abs(Hs[0] - Hs[1]).max() < 1e-11 * np.abs(Hs[1]).max()
+
+
+@pytest.mark.parametrize("where", ["x", "x_wall", "base"])
+def test_fixed_point_operator_nonfinite_and_zero_inputs(where):
+    """The fixed-point operator (variant 2) takes the input's grid from its largest kept entry: a
+    NaN there makes every result non-finite (reported as the double-float path reports it), a NaN
+    at an entry P_BC discards changes nothing, a zero input gives a zero result, and a non-finite
+    base state falls back to the double-float march."""
+    kv = kvmod()
+    n = (12, 12, 12)
+    base = np.stack(synth.base_flow(*n, synth.CC, 65))
+    x = synth.krylov_input(*n, 66)[0]
+    g = kv.Grid(*n, gr=1e6, precision=kv.KV_PREC_MIXED)
+    g.set_tuning(apply_block=(32, 8), df_variant=2, df_block=(0, 8))
+    bad_base, bad_x = base.copy(), x.copy()
+    if where == "x":
+        bad_x[3, 5, 6, 7] = np.nan
+    elif where == "x_wall":
+        bad_x[0, 4, 5, 0] = np.nan  # u at the wall face i = 0: not a degree of freedom
+    else:
+        bad_base[2, 4, 5, 6] = np.inf
+    g.set_base_flow(torch.from_numpy(bad_base).cuda())
+    xt = torch.from_numpy(bad_x).cuda()
+    y = g.empty(4)
+    st = kv.Stats()
+    rc = g.lib.kv_krylov_vector(g.h, xt.data_ptr(), y.data_ptr(), None, ctypes.byref(st))
+    if where == "x_wall":
+        assert rc == 0
+        check(y.cpu().numpy(), Oracle(*n, gr=1e6).krylov_vector(base, bad_x), TOLMIX, "NaN at a wall face")
+    else:
+        assert rc == -1 and b"non-finite" in g.lib.kv_last_error(g.h)
+    g.set_base_flow(torch.from_numpy(base).cuda())
+    z = g.krylov_vector(torch.zeros_like(xt))
+    assert torch.count_nonzero(z) == 0
