@@ -22,18 +22,6 @@ __device__ __forceinline__ void cp_async8(void* smem, const void* gmem, unsigned
   asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;" ::"r"(d), "l"(gmem), "r"(n) : "memory");
 }
 
-// P_BC keeps x at the interior faces (velocity) and the cells (temperature); with insulated
-// spanwise walls and the orthogonal temperature projection it also reads the wall nodes, which
-// it averages with their neighbours.
-__device__ __forceinline__ bool kept(const KvGeom& g, int f, int i, int j, int k) {
-  const bool ci = i >= 1 && i <= g.nx, cj = j >= 1 && j <= g.ny, ck = k >= 1 && k <= g.nz;
-  if (f == 0) return i >= 1 && i <= g.nx - 1 && cj && ck;
-  if (f == 1) return ci && j >= 1 && j <= g.ny - 1 && ck;
-  if (f == 2) return ci && cj && k >= 1 && k <= g.nz - 1;
-  if (ci && cj && ck) return true;
-  return g.bc == KV_BC_AA && g.tproj != KV_TPROJ_OBLIQUE && ci && ck && (j == 0 || j == g.ny + 1);
-}
-
 __device__ __forceinline__ unsigned int abs_hi(double v) {
   return (unsigned int)(__double2hiint(v)) & 0x7FFFFFFFu;  // monotonic in |v|; NaN above Inf
 }
@@ -41,31 +29,50 @@ __device__ __forceinline__ unsigned int abs_hi(double v) {
 // The largest |x| over the entries P_BC keeps, as the high word of its bit pattern (one atomic
 // max into xmax per block), and the padded-boundary entries of v* and T* (0, except the
 // insulated walls' temperature nodes, which the operator writes from their neighbouring cells).
-// Each warp walks whole x-rows of the padded array.
+// Each warp takes whole x-rows of the padded array; along a row the kept entries of a field are
+// one contiguous range, which each lane reads PF_U entries at a time (independent loads).
+constexpr int PF_U = 9;  // 32 x 9 = 288 >= X for n <= 286; longer rows take further passes
 __global__ void __launch_bounds__(256) k_fx_prepass(KvGeom g, const double* __restrict__ x, size_t P,
                                                     unsigned int* __restrict__ xmax, double* __restrict__ vstar,
                                                     double* __restrict__ tout) {
   __shared__ unsigned int wmax[8];
   const int lane = threadIdx.x & 31;
   const int nwarp = gridDim.x * (blockDim.x >> 5);
+  const bool aa_t = g.bc == KV_BC_AA && g.tproj != KV_TPROJ_OBLIQUE;  // wall T nodes are read
   unsigned int m = 0;
   for (int row = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); row < g.Y * g.Z; row += nwarp) {
     const int j = row % g.Y, k = row / g.Y;
     const size_t e0 = (size_t)g.X * row;
-    const bool row_in = j >= 1 && j <= g.ny && k >= 1 && k <= g.nz;
-    for (int i = lane; i < g.X; i += 32) {
-      const size_t e = e0 + i;
+    const bool jin = j >= 1 && j <= g.ny, kin = k >= 1 && k <= g.nz;
+    // kept range [lo, hi] of each field on this row (empty: hi < lo)
+    int hi_f[4];
+    hi_f[0] = jin && kin ? g.nx - 1 : 0;
+    hi_f[1] = j >= 1 && j <= g.ny - 1 && kin ? g.nx : 0;
+    hi_f[2] = jin && k >= 1 && k <= g.nz - 1 ? g.nx : 0;
+    hi_f[3] = kin && (jin || (aa_t && (j == 0 || j == g.ny + 1))) ? g.nx : 0;
+    for (int i0 = 0; i0 < g.X; i0 += 32 * PF_U) {
 #pragma unroll
-      for (int f = 0; f < 4; ++f)
-        if (kept(g, f, i, j, k)) m = max(m, abs_hi(__ldg(x + (size_t)f * P + e)));
-      if (!(row_in && i >= 1 && i <= g.nx)) {
-        vstar[e] = 0.0;
-        vstar[P + e] = 0.0;
-        vstar[2 * P + e] = 0.0;
-        const bool aa_wall = g.bc == KV_BC_AA && (j == 0 || j == g.ny + 1) && i >= 1 && i <= g.nx && k >= 1 &&
-                             k <= g.nz;
-        if (!aa_wall) tout[e] = 0.0;
+      for (int f = 0; f < 4; ++f) {
+        double vals[PF_U];
+#pragma unroll
+        for (int u = 0; u < PF_U; ++u) {
+          const int i = i0 + lane + 32 * u;
+          vals[u] = (i >= 1 && i <= hi_f[f]) ? __ldg(x + (size_t)f * P + e0 + i) : 0.0;
+        }
+#pragma unroll
+        for (int u = 0; u < PF_U; ++u) m = max(m, abs_hi(vals[u]));
       }
+    }
+    // boundary zeros: whole rows outside the interior, else the two ends of the row
+    const bool row_in = jin && kin;
+    const bool aa_row = g.bc == KV_BC_AA && (j == 0 || j == g.ny + 1) && kin;
+    for (int i = lane; i < g.X; i += 32) {
+      if (row_in && i >= 1 && i <= g.nx) continue;
+      const size_t e = e0 + i;
+      vstar[e] = 0.0;
+      vstar[P + e] = 0.0;
+      vstar[2 * P + e] = 0.0;
+      if (!(aa_row && i >= 1 && i <= g.nx)) tout[e] = 0.0;
     }
   }
   m = __reduce_max_sync(0xFFFFFFFFu, m);

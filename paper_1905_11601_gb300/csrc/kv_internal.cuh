@@ -275,6 +275,8 @@ void kv_launch_apply(const kv_grid* h, const double* coef, const double* x, doub
 // mixed precision: FP32-pair copy of the coefficients, and J P_BC x in double-float on the FP32 pipe
 // (P_BC x is first split into h->xsplit)
 void kv_launch_coef_df(const kv_grid* h, const double* coef, float2* cdf, cudaStream_t s);
+// the padded-boundary entries of v* and T* (kv_stencil.cu)
+void kv_launch_zero_boundary(const kv_grid* h, double* vstar, double* tout, cudaStream_t s);
 // kv_fixed.cu
 bool kv_fx_eligible(const kv_grid* h);
 kv_status kv_fx_setup(kv_grid* h);

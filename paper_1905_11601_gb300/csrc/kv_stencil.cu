@@ -931,6 +931,10 @@ void kv_launch_apply(const kv_grid* h, const double* coef, const double* x, doub
   k_apply<<<grid, block, 0, s>>>(g, coef, x, h->P, vstar, tout);
 }
 
+void kv_launch_zero_boundary(const kv_grid* h, double* vstar, double* tout, cudaStream_t s) {
+  k_zero_boundary<<<2 * 152, 256, 0, s>>>(h->g, h->P, vstar, tout);
+}
+
 void kv_launch_coef_df(const kv_grid* h, const double* coef, float2* cdf, cudaStream_t s) {
   k_coef_df<<<4 * 152, 256, 0, s>>>(coef, cdf, h->P);
   if (h->str.sw) k_coef_df_plus<<<4 * 152, 256, 0, s>>>(coef, h->coef_dfp, h->P);
