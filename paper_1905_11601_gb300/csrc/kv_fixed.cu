@@ -110,7 +110,8 @@ __global__ void __launch_bounds__(256) k_fx_base(const double* __restrict__ a, s
 // eight staged fields (projected input and base state, fixed point, with a one-cell halo): at
 // step k the threads issue the copies of plane k+2, form their cells' equations from planes
 // k-1..k+1 (the first half of the block u and T, the second half v and w), convert and store
-// plane k+2 into the slot plane k-2 used, and synchronise once.
+// plane k+2 into the slot plane k-2 used, and synchronise once. (A deeper ring, three compute
+// slots and two planes in flight, measured slower: it needs a second barrier per plane.)
 constexpr int FB_X = 32, FB_Y = 8;
 constexpr int FT_X = FB_X + 2, FT_Y = FB_Y + 2, FPTS = FT_X * FT_Y;
 constexpr int FCELLS = FB_X * FB_Y;
@@ -251,33 +252,35 @@ __global__ void __launch_bounds__(FTHREADS, 2)
       const size_t e = (size_t)i + (size_t)sy * j + (size_t)sz * k;
       // a non-finite input: every result NaN (scaled by NaN)
       const double fo = nonfinite ? __longlong_as_double(0x7FF8000000000000ll) : fout;
-      // the cell's equations with the derivative weights of its wall classes
-      auto eqs = [&](W3i d1x, W3i d2x, W3i d1y, W3i d2y, W3i d1z, W3i d2z) {
+      // the cell's equations with the derivative weights of its wall classes; fs scales the
+      // result (3 where the interior first-derivative weights run without their factor 3)
+      auto eqs = [&](W3i d1x, W3i d2x, W3i d1y, W3i d2y, W3i d1z, W3i d2z, const FxK& KK, int face,
+                     double fs) {
         if (half == 0) {
-          const long long tu = fx_eq_u(X, B, d1y, d2y, d1z, d2z, K);
-          vstar[e] = i <= g.nx - 1 ? fx_to_double(tu) * fo : 0.0;
-          const double r = fx_to_double(fx_eq_t(X, B, d1x, d2x, d1y, d2y, d1z, d2z, K)) * fo;
+          const long long tu = fx_eq_u(X, B, d1y, d2y, d1z, d2z, KK, face);
+          vstar[e] = i <= g.nx - 1 ? fx_to_double(tu) * fs : 0.0;
+          const double r = fx_to_double(fx_eq_t(X, B, d1x, d2x, d1y, d2y, d1z, d2z, KK, face)) * fs;
           // insulated wall pair: the cell and its wall node (Eq 21's projection for that pair)
           const bool pair = g.bc == KV_BC_AA && (j == 1 || j == g.ny);
           const double t = pair && g.tproj != KV_TPROJ_OBLIQUE ? 0.5 * r : r;
           tout[e] = t;
           if (pair) tout[(size_t)i + (size_t)sy * (j == 1 ? 0 : g.ny + 1) + (size_t)sz * k] = t;
         } else {
-          const long long tv = fx_eq_v(X, B, d1x, d2x, d1z, d2z, K);
-          vstar[Pz + e] = j <= g.ny - 1 ? fx_to_double(tv) * fo : 0.0;
-          const long long tw = fx_eq_w(X, B, d1x, d2x, d1y, d2y, K);
-          vstar[2 * Pz + e] = k <= g.nz - 1 ? fx_to_double(tw) * fo : 0.0;
+          const long long tv = fx_eq_v(X, B, d1x, d2x, d1z, d2z, KK, face);
+          vstar[Pz + e] = j <= g.ny - 1 ? fx_to_double(tv) * fs : 0.0;
+          const long long tw = fx_eq_w(X, B, d1x, d2x, d1y, d2y, KK, face);
+          vstar[2 * Pz + e] = k <= g.nz - 1 ? fx_to_double(tw) * fs : 0.0;
         }
       };
       // interior weights as constants where the whole warp is interior (the weighted sums become
       // differences); the walls' weights per cell elsewhere
-      const W3i I1{-3, 0, 3}, I2{1, -2, 1};
+      const W3i I1{-3, 0, 3}, I2{1, -2, 1}, J1{-1, 0, 1};
       if (cy == 0 && cz == 0 && x_inner)
-        eqs(I1, I2, I1, I2, I1, I2);
+        eqs(J1, I2, J1, I2, J1, I2, K.k3, 4, 3.0 * fo);
       else if (cy == 0 && cz == 0)
-        eqs(fx_d1(cx), fx_d2(cx), I1, I2, I1, I2);
+        eqs(fx_d1(cx), fx_d2(cx), I1, I2, I1, I2, K.k1, 12, fo);
       else
-        eqs(fx_d1(cx), fx_d2(cx), fx_d1(cy), fx_d2(cy), fx_d1(cz), fx_d2(cz));
+        eqs(fx_d1(cx), fx_d2(cx), fx_d1(cy), fx_d2(cy), fx_d1(cz), fx_d2(cz), K.k1, 12, fo);
     }
     if (more) finish(k + 2, (k + 2) & 3);
     __syncthreads();
@@ -330,9 +333,8 @@ kv_status kv_fx_setup(kv_grid* h) {
   for (double c : {kd_m, kd_e, kb}) e = std::max(e, std::ilogb(c) + 1);
   const int r0 = 1026 + e;
   FxConst K;
-  K.kd_m = fx_of(kd_m, r0);
-  K.kd_e = fx_of(kd_e, r0);
-  K.kb = fx_of(kb, r0);
+  K.k1 = FxK{fx_of(kd_m, r0), fx_of(kd_e, r0), fx_of(kb, r0)};
+  K.k3 = FxK{fx_of(kd_m / 3.0, r0), fx_of(kd_e / 3.0, r0), fx_of(kb / 3.0, r0)};
   K.f0 = -n / 24.0 * std::ldexp(1.0, e - 50);
   K.e = e;
   k_fx_base<<<4 * 152, 256, 0, s>>>(h->base, 4 * h->P, r0, h->base_fx);

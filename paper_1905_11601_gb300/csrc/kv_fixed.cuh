@@ -74,14 +74,6 @@ KV_HD double fx_from_bits(unsigned long long b) {
 #endif
 }
 
-KV_HD int fx_clz64(unsigned long long a) {
-#if defined(__CUDA_ARCH__)
-  return __clzll((long long)a);
-#else
-  return a ? __builtin_clzll(a) : 64;
-#endif
-}
-
 // x on the grid of 2^(e - 49), for |x| < 2^e: round(x 2^(49 - e)) as a pair; r0 = 1026 + e.
 // With b the biased exponent of x, the value is its 53-bit significand shifted right by
 // r = r0 - b >= 4, rounded half away from zero. Zero, subnormal values and values below half a
@@ -96,15 +88,13 @@ KV_HD FX fx_of(double x, int r0) {
   return FX{(int)(s >> FX_SPLIT), (int)(s & ((1ll << FX_SPLIT) - 1))};
 }
 
-// An integer as FP64, rounded half up in magnitude (|t| < 2^63), by integer operations only.
+// An integer (|t| < 2^63) as FP64, rounded to nearest
 KV_HD double fx_to_double(long long t) {
-  const unsigned long long sgn = t < 0 ? (1ull << 63) : 0ull;
-  unsigned long long a = t < 0 ? 0ull - (unsigned long long)t : (unsigned long long)t;
-  const int lz = fx_clz64(a | 1ull);  // (t = 0 is selected below)
-  a <<= lz;                           // leading bit at 63
-  const unsigned long long m = (a >> 11) + ((a >> 10) & 1ull);  // 53 bits, may carry into bit 53
-  const unsigned long long e = (unsigned long long)(1086 - lz);  // biased exponent of 2^(63 - lz)
-  return fx_from_bits(t == 0 ? 0ull : sgn | ((e << 52) + m - (1ull << 52)));
+#if defined(__CUDA_ARCH__)
+  return __ll2double_rn(t);
+#else
+  return (double)t;
+#endif
 }
 
 // Derivative weights as small integers. First derivative in units of 1/(6h): interior or face
@@ -125,28 +115,34 @@ KV_HD int fx_class(int t, int n) { return t == 1 ? 1 : (t == n ? 2 : 0); }
 //   v, w alike (w adds Kb (T + T_k+1)); T:  2 S2U D1x(T) + ... + 2 s2u D1x(Theta) + ... + Kd_e L(T)
 // with D1 the first-derivative weights in units of 1/(6h), S4 / S2 the 4- / 2-point sums of the
 // averaged velocities, L the second-derivative weights (units 1/h^2) summed over the axes, and
-// the constants Kd_m = -24 nu n, Kd_e = -24 kappa n, Kb = -12/n on the base state's grid.
+// the constants Kd_m = -24 nu n, Kd_e = -24 kappa n, Kb = -12/n on the base state's grid (K).
 // Accessors: X(f, di, dj, dk) the projected input of field f (u, v, w, T) at the offset,
-// B(f, di, dj, dk) the base state (U, V, W, Theta). d1a, d2a: the derivative weights along axis
+// B(f, di, dj, dk) the base state (U, V, W, Theta). face: 4 x the face axis' first-derivative
+// weight (12, or 4 with the constants K divided by 3). d1a, d2a: the derivative weights along axis
 // a at the cell (fx_d1 / fx_d2 of its wall class; constants for interior cells, so that the
 // weighted sums reduce to differences).
-struct FxConst {
+struct FxK {
   FX kd_m, kd_e, kb;  // on the base state's grid
-  double f0;          // -n/24 x 2^(E - 50): the result of a unit total for x on the grid 2^-49
-  int e;              // base state grid: |values| < 2^E
+};
+// k1: the constants above. k3: the same divided by 3, for cells whose first-derivative weights
+// are all the interior ones, which then run as (-1, 0, 1) (the factor 3 moves to the output).
+struct FxConst {
+  FxK k1, k3;
+  double f0;  // -n/24 x 2^(E - 50): the result of a unit total for x on the grid 2^-49 (k1)
+  int e;      // base state grid: |values| < 2^E
 };
 
 template <class XA, class BA>
-KV_HD long long fx_eq_u(const XA& X, const BA& B, W3i d1y, W3i d2y, W3i d1z, W3i d2z, const FxConst& K) {
+KV_HD long long fx_eq_u(const XA& X, const BA& B, W3i d1y, W3i d2y, W3i d1z, W3i d2z, const FxK& K, int face) {
   const FX u0 = X(0, 0, 0, 0), uxm = X(0, -1, 0, 0), uxp = X(0, 1, 0, 0), uym = X(0, 0, -1, 0),
            uyp = X(0, 0, 1, 0), uzm = X(0, 0, 0, -1), uzp = X(0, 0, 0, 1);
   const FX U0 = B(0, 0, 0, 0);
   FXAcc a, b;
   // x is the face axis: D1 = (-3, 0, 3); the own velocity carries 4 (the others are 4-point sums)
-  a.mac(U0, fx_mul(fx_sub(uxp, uxm), 12));
+  a.mac(U0, fx_mul(fx_sub(uxp, uxm), face));
   b.mac(fx_sum4(B(1, 0, -1, 0), B(1, 0, 0, 0), B(1, 1, -1, 0), B(1, 1, 0, 0)), fx_w3(d1y, uym, u0, uyp));
   a.mac(fx_sum4(B(2, 0, 0, -1), B(2, 0, 0, 0), B(2, 1, 0, -1), B(2, 1, 0, 0)), fx_w3(d1z, uzm, u0, uzp));
-  b.mac(u0, fx_mul(fx_sub(B(0, 1, 0, 0), B(0, -1, 0, 0)), 12));
+  b.mac(u0, fx_mul(fx_sub(B(0, 1, 0, 0), B(0, -1, 0, 0)), face));
   a.mac(fx_sum4(X(1, 0, -1, 0), X(1, 0, 0, 0), X(1, 1, -1, 0), X(1, 1, 0, 0)),
         fx_w3(d1y, B(0, 0, -1, 0), U0, B(0, 0, 1, 0)));
   b.mac(fx_sum4(X(2, 0, 0, -1), X(2, 0, 0, 0), X(2, 1, 0, -1), X(2, 1, 0, 0)),
@@ -157,17 +153,17 @@ KV_HD long long fx_eq_u(const XA& X, const BA& B, W3i d1y, W3i d2y, W3i d1z, W3i
 }
 
 template <class XA, class BA>
-KV_HD long long fx_eq_v(const XA& X, const BA& B, W3i d1x, W3i d2x, W3i d1z, W3i d2z, const FxConst& K) {
+KV_HD long long fx_eq_v(const XA& X, const BA& B, W3i d1x, W3i d2x, W3i d1z, W3i d2z, const FxK& K, int face) {
   const FX v0 = X(1, 0, 0, 0), vxm = X(1, -1, 0, 0), vxp = X(1, 1, 0, 0), vym = X(1, 0, -1, 0),
            vyp = X(1, 0, 1, 0), vzm = X(1, 0, 0, -1), vzp = X(1, 0, 0, 1);
   const FX V0 = B(1, 0, 0, 0);
   FXAcc a, b;
   a.mac(fx_sum4(B(0, -1, 0, 0), B(0, 0, 0, 0), B(0, -1, 1, 0), B(0, 0, 1, 0)), fx_w3(d1x, vxm, v0, vxp));
-  b.mac(V0, fx_mul(fx_sub(vyp, vym), 12));
+  b.mac(V0, fx_mul(fx_sub(vyp, vym), face));
   a.mac(fx_sum4(B(2, 0, 0, -1), B(2, 0, 0, 0), B(2, 0, 1, -1), B(2, 0, 1, 0)), fx_w3(d1z, vzm, v0, vzp));
   b.mac(fx_sum4(X(0, -1, 0, 0), X(0, 0, 0, 0), X(0, -1, 1, 0), X(0, 0, 1, 0)),
         fx_w3(d1x, B(1, -1, 0, 0), V0, B(1, 1, 0, 0)));
-  a.mac(v0, fx_mul(fx_sub(B(1, 0, 1, 0), B(1, 0, -1, 0)), 12));
+  a.mac(v0, fx_mul(fx_sub(B(1, 0, 1, 0), B(1, 0, -1, 0)), face));
   b.mac(fx_sum4(X(2, 0, 0, -1), X(2, 0, 0, 0), X(2, 0, 1, -1), X(2, 0, 1, 0)),
         fx_w3(d1z, B(1, 0, 0, -1), V0, B(1, 0, 0, 1)));
   const W3i d2y{1, -2, 1};
@@ -176,19 +172,19 @@ KV_HD long long fx_eq_v(const XA& X, const BA& B, W3i d1x, W3i d2x, W3i d1z, W3i
 }
 
 template <class XA, class BA>
-KV_HD long long fx_eq_w(const XA& X, const BA& B, W3i d1x, W3i d2x, W3i d1y, W3i d2y, const FxConst& K) {
+KV_HD long long fx_eq_w(const XA& X, const BA& B, W3i d1x, W3i d2x, W3i d1y, W3i d2y, const FxK& K, int face) {
   const FX w0 = X(2, 0, 0, 0), wxm = X(2, -1, 0, 0), wxp = X(2, 1, 0, 0), wym = X(2, 0, -1, 0),
            wyp = X(2, 0, 1, 0), wzm = X(2, 0, 0, -1), wzp = X(2, 0, 0, 1);
   const FX W0 = B(2, 0, 0, 0);
   FXAcc a, b;
   a.mac(fx_sum4(B(0, -1, 0, 0), B(0, 0, 0, 0), B(0, -1, 0, 1), B(0, 0, 0, 1)), fx_w3(d1x, wxm, w0, wxp));
   b.mac(fx_sum4(B(1, 0, -1, 0), B(1, 0, 0, 0), B(1, 0, -1, 1), B(1, 0, 0, 1)), fx_w3(d1y, wym, w0, wyp));
-  a.mac(W0, fx_mul(fx_sub(wzp, wzm), 12));
+  a.mac(W0, fx_mul(fx_sub(wzp, wzm), face));
   b.mac(fx_sum4(X(0, -1, 0, 0), X(0, 0, 0, 0), X(0, -1, 0, 1), X(0, 0, 0, 1)),
         fx_w3(d1x, B(2, -1, 0, 0), W0, B(2, 1, 0, 0)));
   a.mac(fx_sum4(X(1, 0, -1, 0), X(1, 0, 0, 0), X(1, 0, -1, 1), X(1, 0, 0, 1)),
         fx_w3(d1y, B(2, 0, -1, 0), W0, B(2, 0, 1, 0)));
-  b.mac(w0, fx_mul(fx_sub(B(2, 0, 0, 1), B(2, 0, 0, -1)), 12));
+  b.mac(w0, fx_mul(fx_sub(B(2, 0, 0, 1), B(2, 0, 0, -1)), face));
   const W3i d2z{1, -2, 1};
   a.mac(K.kd_m, fx_add(fx_add(fx_w3(d2x, wxm, w0, wxp), fx_w3(d2y, wym, w0, wyp)), fx_w3(d2z, wzm, w0, wzp)));
   b.mac(K.kb, fx_add(X(3, 0, 0, 0), X(3, 0, 0, 1)));  // buoyancy (T_k + T_k+1) / 2
@@ -197,7 +193,7 @@ KV_HD long long fx_eq_w(const XA& X, const BA& B, W3i d1x, W3i d2x, W3i d1y, W3i
 
 template <class XA, class BA>
 KV_HD long long fx_eq_t(const XA& X, const BA& B, W3i d1x, W3i d2x, W3i d1y, W3i d2y, W3i d1z, W3i d2z,
-                        const FxConst& K) {
+                        const FxK& K, int face) {
   const FX t0 = X(3, 0, 0, 0), txm = X(3, -1, 0, 0), txp = X(3, 1, 0, 0), tym = X(3, 0, -1, 0),
            typ = X(3, 0, 1, 0), tzm = X(3, 0, 0, -1), tzp = X(3, 0, 0, 1);
   const FX th0 = B(3, 0, 0, 0);
