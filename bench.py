@@ -56,6 +56,9 @@ def parse_args():
     ap.add_argument("--single", choices=["fp64", "mixed", "mixed-arnoldi", "mixed-newton"], default=None,
                     help="profiling case: two untimed Krylov-vector evaluations (or 8 Arnoldi steps, or two "
                          "Newton corrections at 64^3 with one GMRES(30) cycle each), no JSON line")
+    ap.add_argument("--operator", default=None, metavar="VARIANT,PLANES",
+                    help="with --single: pin the mixed path's operator (kv_set_tuning), e.g. 2,16 for the "
+                         "fixed-point march with 16 planes per block, 1,32 for the double-float march")
     return ap.parse_args()
 
 
@@ -315,8 +318,17 @@ def roofline(phases, w, precision, steps, nqs=(), tuning=None):
         # J x: read x (4 fields) and the base state (4), write v* and T* (4): 12 x 8 B per cell
         byts = 12 * 8.0 * n3
         ach = byts / (avg_ms / 1e3) / 1e9
-        march = bool(tuning) and tuning.get("df_variant") == 1
+        variant = tuning.get("df_variant") if tuning else None
         points = (w.nx + 2) * (w.ny + 2) * (w.nz + 2)
+        if variant == 2:
+            tf = [traffic_for(k, points) for k in ("k_fx_prepass", "k_apply_fx_march")]
+            return {"kernel": "k_fx_prepass + k_apply_fx_march (fixed-point operator from the base state)",
+                    "bound": "hbm", "achieved": ach, "peak": hbm_peak, "unit": "GB/s", "frac": ach / hbm_peak,
+                    "traffic": None if None in tf else sum(tf), "peak_source": hbm_src,
+                    "algorithmic": f"12 fields x 8 B per cell = {byts:.4g} B per evaluation (read x and the base "
+                                   f"state, write v* and T*); traffic: measured DRAM bytes of both kernels per "
+                                   f"evaluation (the pre-pass reads x once more for its largest magnitude)"}
+        march = variant == 1
         name = ("k_zero_boundary + k_apply_df_march (double-float operator, 2.5D march)" if march
                 else "k_split_input + k_apply_df (double-float operator)")
         return {"kernel": name, "bound": "hbm", "achieved": ach, "peak": hbm_peak, "unit": "GB/s",
@@ -646,6 +658,9 @@ def run_ours(args):
                                     "mixed run, timed steps included; read after the timed region")
     out["second_gs_update"] = {"steps": mx["second_updates"][1], "with_second_update": mx["second_updates"][0],
                                "note": "the phase-timing pass over the timed basis sizes"}
+    # the operator phase's own roofline (the line's roofline object is the dominant phase's)
+    out["roofline_operator"] = roofline({"stencil": mx["phases"]["stencil"]}, w, "mixed", args.steps,
+                                        mx["nq"], mx["g"].tuning())
     out["phases"] = {k: {"ms_per_step": v["ms"] / args.steps, "share": v["share"],
                          "launches_per_step": v["launches"] / args.steps} for k, v in mx["phases"].items()}
     out["fp64_plain"] = {"value": fp["value"], "ms_per_step": fp["ms"] / args.steps,
@@ -689,6 +704,9 @@ def run_single(args):
     base_np, x_np = synth.workload_arrays(w)
     g = kv.Grid(w.nx, w.ny, w.nz, bc=w.bc, gr=w.gr, pr=w.pr,
                 precision=kv.KV_PREC_FP64 if args.single == "fp64" else kv.KV_PREC_MIXED)
+    if args.operator and args.single != "fp64":
+        variant, planes = (int(v) for v in args.operator.split(","))
+        g.set_tuning((32, 8), variant, (0 if variant else 32, planes))
     g.set_base_flow(torch.from_numpy(np.stack(base_np)).cuda())
     x = torch.from_numpy(x_np[0]).cuda()
     y, st = g.krylov_vector(x, stats=True)  # statistics for the line printed below
