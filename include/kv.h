@@ -341,21 +341,32 @@ kv_status kv_profile_get(kv_handle h, int phase, double* total_ms, long long* ti
                          long long* launches);
 
 /* The configuration the autotuner chose at the first kv_set_base_flow (cfg: host array of 5
-   ints): cfg[0] x cfg[1], the FP64 operator's thread block; for KV_PREC_MIXED the double-float
-   operator: cfg[2] = 0 (split pass, then cfg[3] cells x cfg[4] rows of cells per block) or 1
-   (the 2.5D march, cfg[4] z-planes per block); cfg[2..4] = -1 for KV_PREC_FP64. KV_ERR_STATE
-   before the first base flow. */
+   ints): cfg[0] x cfg[1], the FP64 operator's thread block; for KV_PREC_MIXED the operator:
+   cfg[2] = 0 (double-float, split pass, then cfg[3] cells x cfg[4] rows of cells per block), 1
+   (double-float 2.5D march, cfg[4] z-planes per block) or 2 (fixed-point 2.5D march from the base
+   state, cfg[4] z-planes per block; uniform cubic grids); cfg[2..4] = -1 for KV_PREC_FP64.
+   KV_ERR_STATE before the first base flow. */
 kv_status kv_tuning(kv_handle h, int* cfg);
 
 /* Fixes the operator configuration instead of timing the candidates (not part of the method: it
    lets every compiled variant be run and checked deterministically). cfg (host, 5 ints) as
    kv_tuning: cfg[0] x cfg[1] the FP64 operator's block (each >= 1, product <= 256 and a multiple
    of 32); for KV_PREC_MIXED, cfg[2] = 0 with cfg[3] in {32, 64, 128} cells and cfg[4] rows
-   (cfg[3] x 4 x cfg[4] <= 512), or cfg[2] = 1 with cfg[4] in 1..1024 planes per block (only for
-   grids whose packed vector has fewer than 2^31 doubles); cfg[2..4] are ignored for
-   KV_PREC_FP64. Takes effect for the next evaluation; the autotuner does not run afterwards.
+   (cfg[3] x 4 x cfg[4] <= 512), or cfg[2] = 1 or 2 with cfg[4] in 1..1024 planes per block (only
+   for grids whose packed vector has fewer than 2^31 doubles; 2 only on uniform grids with
+   nx = ny = nz, and on a base flow with a non-finite value it runs as 1); cfg[2..4] are ignored
+   for KV_PREC_FP64. Takes effect for the next evaluation; the autotuner does not run afterwards.
    KV_ERR_ARG for values outside these ranges. */
 kv_status kv_set_tuning(kv_handle h, const int* cfg);
+
+/* The tile width of the mixed path's tensor-core contractions (Eqs (14)-(18), kv_umma): output
+   columns per tile, 256 or 128. The autotuner times both at the first kv_set_base_flow (one
+   mixed Poisson solve each) unless this call or kv_set_tuning fixed the configuration;
+   narrower tiles give more tiles per contraction, which fills 152 SMs better on small grids.
+   KV_ERR_ARG for another width or a KV_PREC_FP64 grid. kv_contraction_tile reads it (host
+   pointer; -1 for KV_PREC_FP64). */
+kv_status kv_set_contraction_tile(kv_handle h, int columns);
+kv_status kv_contraction_tile(kv_handle h, int* columns);
 
 /* Instrumentation: Arnoldi steps since the last kv_profile_enable, and of them those that applied
    the second Gram-Schmidt update. Host pointers, each nullable. */

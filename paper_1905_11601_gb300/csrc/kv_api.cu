@@ -432,6 +432,27 @@ kv_status autotune_apply(kv_grid* h) {
     h->df_variant = dv;
     h->df_bx = dbx;
     h->df_by = dby;
+    // the tensor-core contractions' tile width: one mixed Poisson solve (b = tpd_a, phi = tpd_b,
+    // their contents are immaterial for the timing) with each
+    if (!h->tile_pinned) {
+      best = 1e30f;
+      int tile = 256;
+      for (int t : {256, 128}) {
+        h->umma_tile = t;
+        auto solve = [&]() { kv_launch_poisson_mixed(h, h->tpd_a, h->tpd_b, 0, 0, h->s); };
+        solve();
+        if (cudaGetLastError() != cudaSuccess) continue;
+        cudaEventRecord(e0, h->s);
+        for (int r = 0; r < 3; ++r) solve();
+        cudaEventRecord(e1, h->s);
+        if (cudaEventSynchronize(e1) == cudaSuccess && cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess &&
+            ms < best) {
+          best = ms;
+          tile = t;
+        }
+      }
+      h->umma_tile = tile;
+    }
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
@@ -752,6 +773,24 @@ kv_status kv_set_tuning(kv_handle h, const int* cfg) {
   }
   h->tuned = true;
   h->pinned = true;
+  return KV_OK;
+}
+
+kv_status kv_set_contraction_tile(kv_handle h, int columns) {
+  if (!h) return KV_ERR_ARG;
+  if (h->d.precision != KV_PREC_MIXED)
+    return fail(h, KV_ERR_ARG, "kv_set_contraction_tile: only the mixed path contracts on the tensor cores");
+  if (columns != 128 && columns != 256)
+    return fail(h, KV_ERR_ARG, "kv_set_contraction_tile: the tile width must be 128 or 256 columns");
+  h->umma_tile = columns;
+  h->tile_pinned = true;
+  return KV_OK;
+}
+
+kv_status kv_contraction_tile(kv_handle h, int* columns) {
+  if (!h) return KV_ERR_ARG;
+  if (!columns) return fail(h, KV_ERR_ARG, "kv_contraction_tile: columns is NULL");
+  *columns = h->d.precision == KV_PREC_MIXED ? h->umma_tile : -1;
   return KV_OK;
 }
 

@@ -120,6 +120,8 @@ struct kv_grid {
   size_t xs_slice = 0;                   // elements per data slice
   float* lamf[3] = {};
   CUtensorMap mapA[6], mapB[6];
+  CUtensorMap mapB128[6];                // the data maps for the 128-column tile
+  int umma_tile = 256;                   // the contractions' tile width (autotuner / kv_set_contraction_tile)
 
   // block evaluations (kv_krylov_vector_batch in mixed precision; kv_block.cu): per-vector
   // buffers for up to blk_cap vectors, allocated at the first block call
@@ -167,6 +169,7 @@ struct kv_grid {
                                               // (kv_stencil.cu), 2 fixed point (kv_fixed.cu)
   bool tuned = false;
   bool pinned = false;  // kv_set_tuning fixed the configuration: the autotuner does not run
+  bool tile_pinned = false;  // kv_set_contraction_tile fixed the contractions' tile width
 
   std::string err;
 };
@@ -209,9 +212,10 @@ bool kv_make_slice_map(CUtensorMap* map, const void* base, int cols, int rows, i
 bool kv_make_data_map(CUtensorMap* map, const void* base, int cols, int rows, int pitch, int nvec, size_t vec_elems,
                       size_t slice_elems, int box_rows);
 int kv_umma_box_rows_a();
-int kv_umma_box_rows_b();
+int kv_umma_box_rows_b();  // rows of the data map's box for the default 256-column tile
+// tile: output columns per tile, 256 (default) or 128; mapB's box must have that many rows
 cudaError_t kv_launch_umma_axis(const CUtensorMap* mapA, const CUtensorMap* mapB, int K, const KvUmmaEpi& ep,
-                                unsigned int* err, cudaStream_t s);
+                                unsigned int* err, cudaStream_t s, int tile = 256);
 
 // Three BF16 slices of r (r ~ s1 + s2 + s3 to about 2^-24 |r|) at offset o of slice buffers
 // `slice` elements apart: the tensor-core solve's input format.

@@ -169,7 +169,8 @@ kv_status kv_mixed_setup(kv_grid* h, const double* const fwd[3], const double* c
     const int R = (int)(h->Nc / n[a]);
     const __nv_bfloat16* in = h->xs[p % 2];
     if (!kv_make_slice_map(&h->mapA[p], h->wsl[p], K, M, pad8(K), (size_t)M * pad8(K), kv_umma_box_rows_a()) ||
-        !kv_make_data_map(&h->mapB[p], in, K, R, pad8(K), 1, h->xs_slice, h->xs_slice, kv_umma_box_rows_b())) {
+        !kv_make_data_map(&h->mapB[p], in, K, R, pad8(K), 1, h->xs_slice, h->xs_slice, kv_umma_box_rows_b()) ||
+        !kv_make_data_map(&h->mapB128[p], in, K, R, pad8(K), 1, h->xs_slice, h->xs_slice, 128)) {
       h->err = "cuTensorMapEncodeTiled failed";
       return KV_ERR_CUDA;
     }
@@ -265,7 +266,9 @@ void kv_launch_poisson_mixed(kv_grid* h, const double* b, double* phi, int stats
       ep.la = h->lamf[ps.a];
       ep.lb = h->lamf[ps.b];
       KvPhase ph(h, KV_PH_TPD, 1);
-      kv_launch_umma_axis(&h->mapA[p], &h->mapB[p], n[ps.axis], ep, h->derr, s);
+      const bool t128 = h->umma_tile == 128;
+      kv_launch_umma_axis(&h->mapA[p], t128 ? &h->mapB128[p] : &h->mapB[p], n[ps.axis], ep, h->derr, s,
+                          h->umma_tile);
     }
     if (sweep + 1 < h->refine) {
       KvPhase ph(h, KV_PH_REFINE, 1);

@@ -33,20 +33,33 @@
 
 namespace {
 
-constexpr int UM = 128, UN = 256, UK = 64;  // CTA tile; UK = one 128-byte swizzle row of BF16
-constexpr int AR = 6, BR = 3;               // W-slice ring (two k-chunks of three slices), X-slice ring
+constexpr int UM = 128, UK = 64;            // CTA tile rows; UK = one 128-byte swizzle row of BF16
+constexpr int AR = 6;                       // W-slice ring (two k-chunks of three slices)
 constexpr int A_BYTES = UM * UK * 2;        // 16 KB
-constexpr int B_BYTES = UN * UK * 2;        // 32 KB
 constexpr int EPI_WARPS = 16;  // four per TMEM lane quarter, each taking a quarter of the columns
-constexpr int EPI_COLS = UN / (EPI_WARPS / 4);
 constexpr int EPI_CHUNK = 16;               // columns per TMEM load and transpose
 constexpr int THREADS = 64 + 32 * EPI_WARPS;
 constexpr int EPI_BYTES = EPI_WARPS * 32 * EPI_CHUNK * 4;
-constexpr int NBARS = 2 * AR + 2 * BR + 4;
-constexpr int SMEM_BYTES = 256 /*barriers + TMEM slot*/ + 1024 /*alignment slack*/ + AR * A_BYTES + BR * B_BYTES + EPI_BYTES;
-static_assert(NBARS * 8 + 4 <= 256, "barrier area");
-static_assert(SMEM_BYTES <= 232448, "shared memory per block");
-constexpr int TMEM_COLS = 2 * UN;  // two accumulators: the epilogue of one tile overlaps the next tile's MMAs
+// Tile width (output columns per tile, the MMA's N): 256 or 128. The X-slice ring holds 96 KB
+// either way (three 32 KB slots, or six 16 KB slots: two k-chunks in flight). Two TMEM
+// accumulators: the epilogue of one tile overlaps the next tile's MMAs.
+template <int UNT>
+struct Tile {
+  static constexpr int N = UNT;
+  static constexpr int BR = 3 * 256 / UNT;
+  static constexpr int B_BYTES = UNT * UK * 2;
+  static constexpr int EPI_COLS = UNT / (EPI_WARPS / 4);
+  static constexpr int NBARS = 2 * AR + 2 * BR + 4;
+  static constexpr int SMEM = 256 /*barriers + TMEM slot*/ + 1024 /*alignment slack*/ + AR * A_BYTES +
+                              BR * B_BYTES + EPI_BYTES;
+  static constexpr int TMEM_COLS = 2 * UNT;
+  // instruction descriptor, kind::f16: BF16 A and B (K-major), FP32 accumulator, M = 128, N = UNT
+  static constexpr uint32_t IDESC =
+      (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(UNT >> 3) << 17) | ((uint32_t)(UM >> 4) << 24);
+  static_assert(NBARS * 8 + 4 <= 256, "barrier area");
+  static_assert(SMEM <= 232448, "shared memory per block");
+  static_assert(EPI_COLS % EPI_CHUNK == 0, "epilogue column blocks");
+};
 constexpr uint32_t WAIT_LIMIT = 1u << 24;
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -106,16 +119,13 @@ __device__ __forceinline__ uint64_t sdesc(uint32_t saddr) {
   return d;
 }
 
-// Instruction descriptor, kind::f16: BF16 A and B (K-major), FP32 accumulator, M = 128, N = 256.
-constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(UN >> 3) << 17) |
-                           ((uint32_t)(UM >> 4) << 24);
-
-__device__ __forceinline__ void umma_bf16(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t accumulate) {
+__device__ __forceinline__ void umma_bf16(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t idesc,
+                                          uint32_t accumulate) {
   asm volatile(
       "{\n\t.reg .pred p;\n\t"
       "setp.ne.b32 p, %4, 0;\n\t"
       "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem_d),
-      "l"(a), "l"(b), "r"(IDESC), "r"(accumulate)
+      "l"(a), "l"(b), "r"(idesc), "r"(accumulate)
       : "memory");
 }
 __device__ __forceinline__ void umma_commit(uint32_t bar) {
@@ -157,9 +167,13 @@ namespace {
 // within it rows m0 = (t % ntm) * 128 and columns r0 = ((t / ntm) % ntr) * 256, so CTAs that run
 // together share their X tiles in L2. A block of vectors is one launch: its tiles fill the GPU
 // evenly where one vector's do not.
+template <int UNT>
 __global__ void __launch_bounds__(THREADS, 1)
     k_umma_axis(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB, int K,
                 KvUmmaEpi ep, unsigned int* err) {
+  using T = Tile<UNT>;
+  constexpr int UN = T::N, BR = T::BR, B_BYTES = T::B_BYTES, EPI_COLS = T::EPI_COLS, NBARS = T::NBARS,
+                TMEM_COLS = T::TMEM_COLS;
   extern __shared__ uint8_t smem_raw[];
   uint64_t* bars = (uint64_t*)smem_raw;  // fullA[AR] emptyA[AR] fullB[BR] emptyB[BR] accf[2] acce[2], TMEM slot
   uint32_t* tmem_slot = (uint32_t*)(bars + NBARS);
@@ -269,7 +283,7 @@ __global__ void __launch_bounds__(THREADS, 1)
                 if (ph == 0 && i + j == 0) continue;
 #pragma unroll
                 for (int kk = 0; kk < UK / 16; ++kk) {
-                  umma_bf16(acc, sdesc(aA[i] + kk * 32), sdesc(b + kk * 32), first ? 0u : 1u);
+                  umma_bf16(acc, sdesc(aA[i] + kk * 32), sdesc(b + kk * 32), T::IDESC, first ? 0u : 1u);
                   first = false;
                 }
               }
@@ -477,13 +491,16 @@ bool kv_make_data_map(CUtensorMap* map, const void* base, int cols, int rows, in
 }
 
 int kv_umma_box_rows_a() { return UM; }
-int kv_umma_box_rows_b() { return UN; }
+int kv_umma_box_rows_b() { return 256; }
 
-// Raises the kernel's dynamic shared-memory limit (once per process, before any launch or capture).
+// Raises the kernels' dynamic shared-memory limit (once per process, before any launch or capture).
 cudaError_t kv_umma_init() {
   static bool attr = false;
   if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(k_umma_axis, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
+    cudaError_t e =
+        cudaFuncSetAttribute(k_umma_axis<256>, cudaFuncAttributeMaxDynamicSharedMemorySize, Tile<256>::SMEM);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(k_umma_axis<128>, cudaFuncAttributeMaxDynamicSharedMemorySize, Tile<128>::SMEM);
     if (e != cudaSuccess) return e;
     attr = true;
   }
@@ -491,7 +508,7 @@ cudaError_t kv_umma_init() {
 }
 
 cudaError_t kv_launch_umma_axis(const CUtensorMap* mapA, const CUtensorMap* mapB, int K, const KvUmmaEpi& ep,
-                                unsigned int* err, cudaStream_t s) {
+                                unsigned int* err, cudaStream_t s, int tile) {
   cudaError_t e0 = kv_umma_init();
   if (e0 != cudaSuccess) return e0;
   static int sms = 0;
@@ -501,7 +518,12 @@ cudaError_t kv_launch_umma_axis(const CUtensorMap* mapA, const CUtensorMap* mapB
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (sms <= 0) sms = 1;
   }
-  const int tiles = ((ep.R + UN - 1) / UN) * ((ep.M + UM - 1) / UM) * (ep.nvec > 1 ? ep.nvec : 1);
-  k_umma_axis<<<tiles < sms ? tiles : sms, THREADS, SMEM_BYTES, s>>>(*mapA, *mapB, K, ep, err);
+  const int un = tile == 128 ? 128 : 256;  // the data map's box must have un rows
+  const int tiles = ((ep.R + un - 1) / un) * ((ep.M + UM - 1) / UM) * (ep.nvec > 1 ? ep.nvec : 1);
+  const int grid = tiles < sms ? tiles : sms;
+  if (un == 128)
+    k_umma_axis<128><<<grid, THREADS, Tile<128>::SMEM, s>>>(*mapA, *mapB, K, ep, err);
+  else
+    k_umma_axis<256><<<grid, THREADS, Tile<256>::SMEM, s>>>(*mapA, *mapB, K, ep, err);
   return cudaGetLastError();
 }

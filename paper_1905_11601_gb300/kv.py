@@ -29,7 +29,7 @@ EXPORTS = ("kv_create_grid", "kv_destroy_grid", "kv_set_stream", "kv_field_len",
            "kv_plan_destroy", "kv_plan_last_error", "kv_selftest_wait_timeout", "kv_tuning",
            "kv_krylov_vector_host_stream", "kv_gmres", "kv_bicgstab2", "kv_newton", "kv_axpby", "kv_combine", "kv_dot",
            "kv_axis_data", "kv_field_sizes", "kv_set_base_flow_packed", "kv_set_tuning", "kv_guard_read",
-           "kv_arnoldi_counts")
+           "kv_arnoldi_counts", "kv_set_contraction_tile", "kv_contraction_tile")
 PHASES = {"stencil": 0, "divergence": 1, "tpd": 2, "correct": 3, "arnoldi": 4, "refine": 5, "gs_dots": 6,
           "gs_update": 7}
 
@@ -117,6 +117,8 @@ def load_library(path: str = LIB_PATH):
     S = ctypes.POINTER(ctypes.c_size_t)
     lib.kv_field_sizes.argtypes = [H, S, S, S, S]
     lib.kv_set_tuning.argtypes = [H, ctypes.POINTER(ctypes.c_int)]
+    lib.kv_set_contraction_tile.argtypes = [H, ctypes.c_int]
+    lib.kv_contraction_tile.argtypes = [H, ctypes.POINTER(ctypes.c_int)]
     lib.kv_guard_read.argtypes = [H, ctypes.POINTER(Guard), ctypes.c_int]
     lib.kv_arnoldi_counts.argtypes = [H, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_longlong)]
     lib.kv_krylov_vector.argtypes = [H, D, D, D, ctypes.POINTER(Stats)]
@@ -416,10 +418,21 @@ class Grid:
 
     def tuning(self):
         """The autotuner's choice: {"apply_block": (bx, by), "df_variant": 0 split + per-equation
-        kernel | 1 march | -1 (FP64 grid), "df_block": (cells, rows) | (-1, planes per block)}."""
+        kernel | 1 double-float march | 2 fixed-point march | -1 (FP64 grid), "df_block": (cells,
+        rows) | (0, planes per block), "contraction_tile": 256 | 128 | -1 (FP64 grid)}."""
         cfg = (ctypes.c_int * 5)()
         self._check(self.lib.kv_tuning(self.h, cfg))
-        return {"apply_block": (cfg[0], cfg[1]), "df_variant": cfg[2], "df_block": (cfg[3], cfg[4])}
+        return {"apply_block": (cfg[0], cfg[1]), "df_variant": cfg[2], "df_block": (cfg[3], cfg[4]),
+                "contraction_tile": self.contraction_tile()}
+
+    def set_contraction_tile(self, columns):
+        """kv_set_contraction_tile: 256 or 128 output columns per tensor-core tile."""
+        self._check(self.lib.kv_set_contraction_tile(self.h, int(columns)))
+
+    def contraction_tile(self):
+        c = ctypes.c_int()
+        self._check(self.lib.kv_contraction_tile(self.h, ctypes.byref(c)))
+        return c.value
 
     def profile(self):
         """{phase: (total_ms, timed_brackets, launches)} since the last profile_enable."""

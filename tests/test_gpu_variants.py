@@ -334,3 +334,35 @@ def test_fixed_point_operator_nonfinite_and_zero_inputs(where):
     g.set_base_flow(torch.from_numpy(base).cuda())
     z = g.krylov_vector(torch.zeros_like(xt))
     assert torch.count_nonzero(z) == 0
+
+
+@pytest.mark.parametrize("n,bc,gr,tproj", [CASES[0], CASES[3], CUBES[1], ((100, 100, 100), synth.CC, 2e6, 0)])
+def test_both_contraction_tiles_match_oracle(n, bc, gr, tproj):
+    """The tensor-core contractions with 256- and 128-column tiles (the autotuner's two widths),
+    each pinned, against the oracle; both widths give the same result to rounding."""
+    kv = kvmod()
+    base, x, y_ref = reference(n, bc, gr, tproj)
+    ys = []
+    for tile in (256, 128):
+        g = kv.Grid(*n, bc=bc, gr=gr, pr=0.71, tproj=tproj, precision=kv.KV_PREC_MIXED)
+        g.set_contraction_tile(tile)
+        g.set_base_flow(torch.from_numpy(base).cuda())
+        assert g.tuning()["contraction_tile"] == tile
+        y, st = g.krylov_vector(torch.from_numpy(x).cuda(), stats=True)
+        assert st.device_error == 0
+        y = y.cpu().numpy()
+        check(y, y_ref, TOLMIX, ("tile", tile))
+        ys.append(y)
+    assert np.linalg.norm(ys[0] - ys[1]) <= 1e-11 * np.linalg.norm(ys[0])
+
+
+def test_contraction_tile_rejects_bad_widths():
+    kv = kvmod()
+    g = kv.Grid(8, 8, 8, precision=kv.KV_PREC_MIXED)
+    for bad in (0, 64, 192, 512):
+        with pytest.raises(kv.KvError):
+            g.set_contraction_tile(bad)
+    g64 = kv.Grid(8, 8, 8, precision=kv.KV_PREC_FP64)
+    assert g64.contraction_tile() == -1
+    with pytest.raises(kv.KvError):
+        g64.set_contraction_tile(128)
