@@ -41,18 +41,28 @@ constexpr int EPI_CHUNK = 16;               // columns per TMEM load and transpo
 constexpr int THREADS = 64 + 32 * EPI_WARPS;
 constexpr int EPI_BYTES = EPI_WARPS * 32 * EPI_CHUNK * 4;
 // Tile width (output columns per tile, the MMA's N): 256 or 128. The X-slice ring holds 96 KB
-// either way (three 32 KB slots, or six 16 KB slots: two k-chunks in flight). Two TMEM
-// accumulators: the epilogue of one tile overlaps the next tile's MMAs.
+// either way (three 32 KB slots, or six 16 KB slots: two k-chunks in flight). Two accumulator
+// buffers: the epilogue of one tile overlaps the next tile's MMAs.
+//
+// The FP32 accumulation of the tensor core drops the low bits of products much smaller than the
+// running sum, so the five small slice products (i + j >= 1) must not be accumulated onto the
+// leading product W_0 X_0. With 256 columns (SPLIT false) the small products are summed over all
+// of K first and W_0 X_0 is added after them, in a second pass over K that loads W_0 and X_0
+// again. With 128 columns (SPLIT true) TMEM holds two accumulators per buffer, one for the small
+// products and one for W_0 X_0, summed in the epilogue: one pass over K, a third fewer loads.
 template <int UNT>
 struct Tile {
   static constexpr int N = UNT;
+  static constexpr bool SPLIT = UNT == 128;
   static constexpr int BR = 3 * 256 / UNT;
   static constexpr int B_BYTES = UNT * UK * 2;
   static constexpr int EPI_COLS = UNT / (EPI_WARPS / 4);
   static constexpr int NBARS = 2 * AR + 2 * BR + 4;
   static constexpr int SMEM = 256 /*barriers + TMEM slot*/ + 1024 /*alignment slack*/ + AR * A_BYTES +
                               BR * B_BYTES + EPI_BYTES;
-  static constexpr int TMEM_COLS = 2 * UNT;
+  static constexpr int ACC_COLS = SPLIT ? 2 * UNT : UNT;  // TMEM columns of one buffer
+  static constexpr int TMEM_COLS = 2 * ACC_COLS;
+  static constexpr int NPH = SPLIT ? 1 : 2;               // passes over K per tile
   // instruction descriptor, kind::f16: BF16 A and B (K-major), FP32 accumulator, M = 128, N = UNT
   static constexpr uint32_t IDESC =
       (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(UNT >> 3) << 17) | ((uint32_t)(UM >> 4) << 24);
@@ -226,8 +236,9 @@ __global__ void __launch_bounds__(THREADS, 1)
       for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
         const int vec = t / nvt, tv = t - vec * nvt;
         const int m0 = (tv % ntm) * UM, r0 = (tv / ntm) * UN;
-        // phase 0: the slices of the five products with i + j >= 1; phase 1: W_0 and X_0 only
-        for (int ph = 0; ph < 2 && ok; ++ph) {
+        // phase 0: the slices of the six products (of the five with i + j >= 1 without SPLIT);
+        // phase 1 (without SPLIT): W_0 and X_0 only
+        for (int ph = 0; ph < T::NPH && ok; ++ph) {
           const int ns = ph == 0 ? 3 : 1;
           for (int kc = 0; kc < kchunks && ok; ++kc) {
             for (int i = 0; i < ns && ok; ++i, ++ga) {
@@ -257,12 +268,10 @@ __global__ void __launch_bounds__(THREADS, 1)
         // the epilogue must have drained this accumulator (its previous tile)
         if (!(ok = mbar_wait(acce0 + 8 * buf, (use & 1u) ^ 1u, err, lim))) break;
         tc_fence_after();
-        const uint32_t acc = tmem + (uint32_t)(buf * UN);
-        bool first = true;
-        // The FP32 accumulation of the tensor core drops the low bits of products much smaller
-        // than the running sum, so the small slice products (i + j >= 1) are summed over all of
-        // K first (phase 0) and the leading product W_0 X_0 is added last (phase 1).
-        for (int ph = 0; ph < 2 && ok; ++ph) {
+        const uint32_t acc = tmem + (uint32_t)(buf * T::ACC_COLS);
+        const uint32_t acc_lead = T::SPLIT ? acc + (uint32_t)UN : acc;  // W_0 X_0 (see Tile)
+        bool first = true, first_lead = true;
+        for (int ph = 0; ph < T::NPH && ok; ++ph) {
           const int ns = ph == 0 ? 3 : 1;
           for (int kc = 0; kc < kchunks && ok; ++kc) {
             uint32_t aA[3];
@@ -272,19 +281,26 @@ __global__ void __launch_bounds__(THREADS, 1)
               aA[i] = smem_u32(aring + (p % AR) * A_BYTES);
             }
             if (!ok) break;
-            // X slice j meets the W slices i with i + j <= 2 (phase 0: i + j >= 1)
+            // X slice j meets the W slices i with i + j <= 2 (without SPLIT, phase 0: i + j >= 1)
             for (int j = 0; j < ns && ok; ++j, ++gb) {
               const int sb = gb % BR;
               if (!(ok = mbar_wait(fullB0 + 8 * sb, (gb / BR) & 1u, err, lim))) break;
               tc_fence_after();
               const uint32_t b = smem_u32(bring + sb * B_BYTES);
-              // phase 0: i = 2 - j .. 0 without (0, 0); phase 1: (0, 0) only
+              // phase 0: i = 2 - j .. 0 (without SPLIT not (0, 0)); phase 1: (0, 0) only
               for (int i = ph == 0 ? 2 - j : 0; i >= 0; --i) {
-                if (ph == 0 && i + j == 0) continue;
+                const bool lead = i + j == 0;
+                if (!T::SPLIT && ph == 0 && lead) continue;
+                const bool to_lead = T::SPLIT && lead;
 #pragma unroll
                 for (int kk = 0; kk < UK / 16; ++kk) {
-                  umma_bf16(acc, sdesc(aA[i] + kk * 32), sdesc(b + kk * 32), T::IDESC, first ? 0u : 1u);
-                  first = false;
+                  const bool f = to_lead ? first_lead : first;
+                  umma_bf16(to_lead ? acc_lead : acc, sdesc(aA[i] + kk * 32), sdesc(b + kk * 32), T::IDESC,
+                            f ? 0u : 1u);
+                  if (to_lead)
+                    first_lead = false;
+                  else
+                    first = false;
                 }
               }
               umma_commit(emptyB0 + 8 * sb);
@@ -325,7 +341,13 @@ __global__ void __launch_bounds__(THREADS, 1)
       float* const vphi32 = ep.phi32 ? ep.phi32 + (size_t)vec * ep.vstride_phi : nullptr;
       for (int c = c0; c < c0 + EPI_COLS; c += EPI_CHUNK) {
         float v[EPI_CHUNK];
-        tmem_ld16(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(buf * UN + c), v);
+        tmem_ld16(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(buf * T::ACC_COLS + c), v);
+        if (T::SPLIT) {  // the small products' sum plus W_0 X_0
+          float vl[EPI_CHUNK];
+          tmem_ld16(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(buf * T::ACC_COLS + UN + c), vl);
+#pragma unroll
+          for (int t2 = 0; t2 < EPI_CHUNK; ++t2) v[t2] = __fadd_rn(v[t2], vl[t2]);
+        }
         // transpose: tb[col][row]
 #pragma unroll
         for (int t2 = 0; t2 < EPI_CHUNK; ++t2) tb[tix(t2, lane)] = v[t2];
