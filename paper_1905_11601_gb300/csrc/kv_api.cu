@@ -773,7 +773,16 @@ kv_status kv_set_tuning(kv_handle h, const int* cfg) {
   }
   h->tuned = true;
   h->pinned = true;
+  for (auto& ge : h->graphs) cudaGraphExecDestroy(ge.exec);
+  h->graphs.clear();
   return KV_OK;
+}
+
+// Captured graphs hold the kernels and launch shapes of the configuration they were captured
+// with: a new configuration drops them (the next batch call captures again).
+static void drop_graphs(kv_grid* h) {
+  for (auto& ge : h->graphs) cudaGraphExecDestroy(ge.exec);
+  h->graphs.clear();
 }
 
 kv_status kv_set_contraction_tile(kv_handle h, int columns) {
@@ -784,6 +793,7 @@ kv_status kv_set_contraction_tile(kv_handle h, int columns) {
     return fail(h, KV_ERR_ARG, "kv_set_contraction_tile: the tile width must be 128 or 256 columns");
   h->umma_tile = columns;
   h->tile_pinned = true;
+  drop_graphs(h);
   return KV_OK;
 }
 

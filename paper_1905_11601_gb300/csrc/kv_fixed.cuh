@@ -37,10 +37,10 @@ KV_HD FX fx_w3(W3i w, FX a, FX b, FX c) {
   return FX{w.m * a.h + w.c * b.h + w.p * c.h, w.m * a.l + w.c * b.l + w.p * c.l};
 }
 
-// Sum of products: H collects the high-word products (weight 2^48), M1 and M2 the two cross
-// products (weight 2^24); the low-word product (weight 1, below 2^-40 of one high-word unit per
-// term) is left out. Three independent chains of multiply-adds; the equations below use two such
-// accumulators in turn, so that no chain is longer than four products.
+// Sum of products: H collects the high-word products (weight 2^48), M1 both cross products
+// (weight 2^24); the low-word product (weight 1, below 2^-40 of one high-word unit per term) is
+// left out. Two chains of multiply-adds; the equations below use two such accumulators in turn,
+// so that the chains stay short.
 struct FXAcc {
   long long H = 0, M1 = 0;
   KV_HD void mac(FX a, FX b) {

@@ -132,7 +132,7 @@ struct kv_grid {
   float* blk_phi32 = nullptr;            // blk_cap x Nc
   __nv_bfloat16* blk_xs[2] = {};         // 3 slices x blk_cap x xs_slice each: slice s of vector v at
                                          // s * blk_cap * xs_slice + v * xs_slice
-  CUtensorMap blk_mapB[6];
+  CUtensorMap blk_mapB[6], blk_mapB128[6];  // for the 256- and 128-column tiles
   // the fixed-point operator (kv_fixed.cu; uniform cubic mixed grids): the base state on its
   // fixed-point grid, the pre-pass maxima ([0] the input's, [1] the base state's), the constants
   int2* base_fx = nullptr;               // 4P

@@ -224,7 +224,9 @@ kv_status kv_mixed_block_setup(kv_grid* h, int cap) {
     const int K = n[a];
     const int R = (int)(h->Nc / n[a]);
     if (!kv_make_data_map(&h->blk_mapB[p], h->blk_xs[p % 2], K, R, pad8(K), cap, h->xs_slice,
-                          (size_t)cap * h->xs_slice, kv_umma_box_rows_b())) {
+                          (size_t)cap * h->xs_slice, kv_umma_box_rows_b()) ||
+        !kv_make_data_map(&h->blk_mapB128[p], h->blk_xs[p % 2], K, R, pad8(K), cap, h->xs_slice,
+                          (size_t)cap * h->xs_slice, 128)) {
       kv_mixed_block_free(h);
       h->err = "cuTensorMapEncodeTiled failed (block maps)";
       return KV_ERR_CUDA;
@@ -314,7 +316,10 @@ void kv_launch_poisson_mixed_block(kv_grid* h, int nb, cudaStream_t s) {
       ep.vstride_out = h->xs_slice;
       ep.vstride_phi = h->Nc;
       KvPhase ph(h, KV_PH_TPD, 1);
-      kv_launch_umma_axis(&h->mapA[p], &h->blk_mapB[p], n[ps.axis], ep, h->derr, s);
+      // the single-vector path's tile width, so that a block equals single calls bit for bit
+      const bool t128 = h->umma_tile == 128;
+      kv_launch_umma_axis(&h->mapA[p], t128 ? &h->blk_mapB128[p] : &h->blk_mapB[p], n[ps.axis], ep, h->derr, s,
+                          h->umma_tile);
     }
     if (sweep + 1 < h->refine) {
       KvPhase ph(h, KV_PH_REFINE, nb);
