@@ -433,11 +433,13 @@ kv_status autotune_apply(kv_grid* h) {
     h->df_bx = dbx;
     h->df_by = dby;
     // the tensor-core contractions' tile width: one mixed Poisson solve (b = tpd_a, phi = tpd_b,
-    // their contents are immaterial for the timing) with each
+    // their contents are immaterial for the timing) with each; 128 columns only if at least 3 %
+    // faster (where the two tie, as at 256^3, the wide tile does better in block evaluations)
     if (!h->tile_pinned) {
       best = 1e30f;
       int tile = 256;
       for (int t : {256, 128}) {
+        if (t == 128) best *= 0.97f;
         h->umma_tile = t;
         auto solve = [&]() { kv_launch_poisson_mixed(h, h->tpd_a, h->tpd_b, 0, 0, h->s); };
         solve();
