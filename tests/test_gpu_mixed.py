@@ -25,6 +25,17 @@ def rel(a, b):
     return np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300)
 
 
+def field_max_ok(y, y_ref, tol):
+    """Per field F: max |y_F - y_ref_F| <= tol * max |y_ref_F| (catches errors confined to a wall
+    or a tile's tail, which a 2-norm over the whole vector can hide)."""
+    for F in range(4):
+        m = np.abs(y_ref[F]).max()
+        e = np.abs(y[F] - y_ref[F]).max()
+        if e > tol * m:
+            return False, F, e / m if m else e
+    return True, None, 0.0
+
+
 def grid(n, bc, gr, tproj=0, sweeps=0):
     from paper_1905_11601_gb300 import kv
     return kv.Grid(*n, bc=bc, gr=gr, pr=0.71, tproj=tproj, precision=kv.KV_PREC_MIXED, refine_sweeps=sweeps)
@@ -43,6 +54,8 @@ def test_mixed_krylov_vector_matches_oracle(n, bc, gr, tproj):
     y_ref = Oracle(*n, bc=bc, gr=gr, pr=0.71, tproj=tproj).krylov_vector(base, x)
     err = rel(y.cpu().numpy(), y_ref)
     assert err < RTOL_MIXED, err
+    ok = field_max_ok(y.cpu().numpy(), y_ref, RTOL_MIXED)
+    assert ok[0], ok
 
 
 def test_mixed_at_128_insulated_matches_oracle():
@@ -56,6 +69,8 @@ def test_mixed_at_128_insulated_matches_oracle():
     assert st.device_error == 0
     y_ref = Oracle(*n, bc=w.bc, gr=w.gr, pr=w.pr).krylov_vector(base, x[0])
     assert rel(y.cpu().numpy(), y_ref) < RTOL_MIXED
+    ok = field_max_ok(y.cpu().numpy(), y_ref, RTOL_MIXED)
+    assert ok[0], ok
 
 
 def test_mixed_at_256_matches_fp64_path():
