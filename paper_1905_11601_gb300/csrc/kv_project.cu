@@ -165,6 +165,65 @@ __global__ void __launch_bounds__(256) k_divergence_df(KvGeom g, KvStretch S, co
   if (xs) kv_store_bf16x3(xs, slice, ((size_t)(k - 1) * g.ny + (j - 1)) * pitch + (i - 1), __fadd_rn(d.h, d.l));
 }
 
+// The same divergence as a march in z: a warp covers 31 cells of a row plus the face to their
+// left (lane 0), so u(i-1) comes by shuffle and each u value is split once; w(k-1) is the
+// previous plane's w, kept in a register; the next plane's loads are issued before this plane's
+// arithmetic. kc planes per block.
+constexpr int MD_Y = 8;
+template <bool STR>
+__global__ void __launch_bounds__(32 * MD_Y) k_divergence_df_march(KvGeom g, KvStretch S,
+                                                                 const double* __restrict__ vel, size_t P,
+                                                                 double* __restrict__ b, float2 ihx, float2 ihy,
+                                                                 float2 ihz, __nv_bfloat16* __restrict__ xs,
+                                                                 size_t slice, int pitch, int kc) {
+  const int tx = threadIdx.x, ty = threadIdx.y;
+  const int i = blockIdx.x * 31 + tx;  // lane 0: the face left of this warp's first cell
+  const int j = blockIdx.y * MD_Y + ty + 1;
+  const int k0 = 1 + blockIdx.z * kc, k1 = min(k0 + kc, g.nz + 1);
+  const bool row = i < g.X && j <= g.ny;       // loads stay inside the padded arrays
+  const bool own = tx >= 1 && i <= g.nx && j <= g.ny;
+  const double* u = vel;
+  const double* v = vel + P;
+  const double* w = vel + 2 * P;
+  const size_t sz = (size_t)g.X * g.Y;
+  const size_t e0 = (size_t)i + (size_t)g.X * j;  // padded index at k = 0
+  struct In {
+    double u, v, vm, w;
+  };
+  auto load = [&](int k, In& r) {
+    r = In{0.0, 0.0, 0.0, 0.0};
+    if (!row) return;
+    const size_t e = e0 + sz * k;
+    r.u = __ldg(u + e);
+    if (tx >= 1) {
+      r.v = __ldg(v + e);
+      r.vm = __ldg(v + e - g.X);
+      r.w = __ldg(w + e);
+    }
+  };
+  DF wprev = (row && tx >= 1) ? df_split(__ldg(w + e0 + sz * (k0 - 1))) : DF{0.0f, 0.0f};
+  In cur, nxt;
+  load(k0, cur);
+  const DF cx = inv_w_df<STR, 0, KV_SWD_IDC>(g, S, own ? i : 1, ihx);
+  const DF cy = inv_w_df<STR, 1, KV_SWD_IDC>(g, S, own ? j : 1, ihy);
+  for (int k = k0; k < k1; ++k) {
+    if (k + 1 < k1) load(k + 1, nxt);
+    const DF su = df_split(cur.u);
+    const DF um{__shfl_up_sync(0xffffffffu, su.h, 1), __shfl_up_sync(0xffffffffu, su.l, 1)};
+    const DF sw = df_split(cur.w);
+    if (own) {
+      const DF dx = df_mul(df_sub(su, um), cx);
+      const DF dy = df_mul(df_sub(df_split(cur.v), df_split(cur.vm)), cy);
+      const DF dz = df_mul(df_sub(sw, wprev), inv_w_df<STR, 2, KV_SWD_IDC>(g, S, k, ihz));
+      const DF d = df_add(df_add(dx, dy), dz);
+      b[(i - 1) + (size_t)g.nx * ((j - 1) + (size_t)g.ny * (k - 1))] = df_value(d);
+      if (xs) kv_store_bf16x3(xs, slice, ((size_t)(k - 1) * g.ny + (j - 1)) * pitch + (i - 1), __fadd_rn(d.h, d.l));
+    }
+    wprev = sw;
+    cur = nxt;
+  }
+}
+
 __device__ __forceinline__ float df_abs_hi(const DF a) { return fabsf(__fadd_rn(a.h, a.l)); }
 
 // The corrected faces and p only (no SIMPLE test), each input loaded and split once, inverse
@@ -355,9 +414,11 @@ void kv_launch_divergence_to(const kv_grid* h, const double* vel, double* b, __n
   dim3 block(32, 8, 1), grid((g.nx + 31) / 32, (g.ny + 7) / 8, g.nz);
   const bool str = h->str.sw != nullptr;
   if (h->d.precision == KV_PREC_MIXED) {
-    auto kern = str ? k_divergence_df<true> : k_divergence_df<false>;
-    kern<<<grid, block, 0, s>>>(g, h->str, vel, h->P, b, pair_of(g.ihx), pair_of(g.ihy), pair_of(g.ihz), xs, slice,
-                                (g.nx + 7) & ~7);
+    const int kc = 16;
+    dim3 mblock(32, MD_Y, 1), mgrid((g.nx + 30) / 31, (g.ny + MD_Y - 1) / MD_Y, (g.nz + kc - 1) / kc);
+    auto kern = str ? k_divergence_df_march<true> : k_divergence_df_march<false>;
+    kern<<<mgrid, mblock, 0, s>>>(g, h->str, vel, h->P, b, pair_of(g.ihx), pair_of(g.ihy), pair_of(g.ihz), xs,
+                                  slice, (g.nx + 7) & ~7, kc);
   } else {
     auto kern = str ? k_divergence<true> : k_divergence<false>;
     kern<<<grid, block, 0, s>>>(g, h->str, vel, h->P, b);
