@@ -131,8 +131,11 @@ kv_status kv_field_sizes(kv_handle h, size_t* u, size_t* v, size_t* w, size_t* c
    coefficients of the linearised operator for this state (37 padded fields: 15 per velocity
    face, 13 per cell plus the fixed buoyancy weights), so that each Krylov vector is a
    fixed-coefficient 15/13-point product; a grid therefore holds about (4 + 37 + 3) padded
-   fields plus two n^3 buffers of device memory. The first call on a handle also runs the
-   autotuner (unless kv_set_tuning fixed the configuration). */
+   fields plus two n^3 buffers of device memory. In KV_PREC_MIXED it adds 25 coefficient fields
+   as FP32 pairs and, on uniform grids with nx = ny = nz, the base state on the fixed-point
+   operator's grid (4 padded fields of 8 bytes; its scale is read back to the host, so the call
+   synchronises the stream). The first call on a handle also runs the autotuner (unless
+   kv_set_tuning fixed the configuration). Not for use inside a stream capture. */
 kv_status kv_set_base_flow(kv_handle h, const double* U, const double* V, const double* W, const double* Theta);
 
 /* As kv_set_base_flow, for a packed state U | V | W | Theta (one device pointer, 4 padded
