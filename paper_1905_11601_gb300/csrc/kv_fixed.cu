@@ -95,7 +95,7 @@ __global__ void __launch_bounds__(256) k_fx_absmax(const double* __restrict__ a,
   if ((threadIdx.x & 31) == 0 && m) atomicMax(out, m);
 }
 
-// the base state on its fixed-point grid (r0 = 1026 + E)
+// the base state on its fixed-point grid (r0 = fx_r0(E))
 __global__ void __launch_bounds__(256) k_fx_base(const double* __restrict__ a, size_t n, int r0,
                                                  int2* __restrict__ out) {
   for (size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += (size_t)gridDim.x * blockDim.x) {
@@ -143,7 +143,7 @@ __global__ void __launch_bounds__(FTHREADS, 2)
   const int eb = (int)((mb >> 20) & 0x7FFu);
   const bool nonfinite = eb == 0x7FF;
   const int ex = eb == 0 ? -1022 : eb - 1022;
-  const int r0 = 1026 + ex;
+  const int r0 = fx_r0(ex);
   const int ea = ex / 2, eb2 = ex - ex / 2;  // 2^ex in two in-range factors
   const double fout = K.f0 * fx_from_bits((unsigned long long)(ea + 1023) << 52) *
                       fx_from_bits((unsigned long long)(eb2 + 1023) << 52);
@@ -327,11 +327,17 @@ kv_status kv_fx_setup(kv_grid* h) {
     return KV_ERR_CUDA;
   const int eb = (int)((mb >> 20) & 0x7FFu);
   if (eb == 0x7FF) return KV_OK;  // a non-finite base state: the double-float operator reports it
+  // the march's shared memory (above the 48 KB default), set here, outside any stream capture
+  if (cudaFuncSetAttribute(k_apply_fx_march, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)FSMEM) !=
+      cudaSuccess) {
+    cudaGetLastError();
+    return KV_OK;  // the double-float operator stays in use
+  }
   const double n = h->g.nx;
   const double kd_m = -24.0 * h->g.nu * n, kd_e = -24.0 * h->g.kappa * n, kb = -12.0 / n;
   int e = eb == 0 ? -1022 : eb - 1022;
   for (double c : {kd_m, kd_e, kb}) e = std::max(e, std::ilogb(c) + 1);
-  const int r0 = 1026 + e;
+  const int r0 = fx_r0(e);
   FxConst K;
   K.k1 = FxK{fx_of(kd_m, r0), fx_of(kd_e, r0), fx_of(kb, r0)};
   K.k3 = FxK{fx_of(kd_m / 3.0, r0), fx_of(kd_e / 3.0, r0), fx_of(kb / 3.0, r0)};
@@ -347,11 +353,6 @@ kv_status kv_fx_setup(kv_grid* h) {
 // J P_BC x by the fixed-point march (kc planes per block): pre-pass (input grid, boundary zeros),
 // then the march. Launches: 2 (plus a 4-byte memset).
 void kv_launch_apply_fx(const kv_grid* h, const double* x, double* vstar, double* tout, int kc, cudaStream_t s) {
-  static bool attr = false;
-  if (!attr) {
-    cudaFuncSetAttribute(k_apply_fx_march, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)FSMEM);
-    attr = true;
-  }
   const KvGeom& g = h->g;
   cudaMemsetAsync(h->fxmax, 0, sizeof(unsigned int), s);
   k_fx_prepass<<<4 * 152, 256, 0, s>>>(g, x, h->P, h->fxmax, vstar, tout);

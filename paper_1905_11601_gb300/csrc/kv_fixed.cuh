@@ -24,6 +24,8 @@ struct FX {
 
 constexpr int FX_BITS = 49;   // converted values: |v| < 2^49 units
 constexpr int FX_SPLIT = 24;  // low word bits
+// fx_of's shift base for a bound |x| < 2^e: r0 = fx_r0(e) (1075 = FP64 exponent bias + 52)
+KV_HD constexpr int fx_r0(int e) { return 1075 - FX_BITS + e; }
 
 KV_HD FX fx_add(FX a, FX b) { return FX{a.h + b.h, a.l + b.l}; }
 KV_HD FX fx_sub(FX a, FX b) { return FX{a.h - b.h, a.l - b.l}; }
@@ -74,7 +76,7 @@ KV_HD double fx_from_bits(unsigned long long b) {
 #endif
 }
 
-// x on the grid of 2^(e - 49), for |x| < 2^e: round(x 2^(49 - e)) as a pair; r0 = 1026 + e.
+// x on the grid of 2^(e - 49), for |x| < 2^e: round(x 2^(49 - e)) as a pair; r0 = fx_r0(e).
 // With b the biased exponent of x, the value is its 53-bit significand shifted right by
 // r = r0 - b >= 4, rounded half away from zero. Zero, subnormal values and values below half a
 // unit give 0. (Non-finite inputs are caught before: the caller's bound e is then meaningless.)
