@@ -663,6 +663,18 @@ def run_ours(args):
                                         mx["nq"], mx["g"].tuning())
     out["phases"] = {k: {"ms_per_step": v["ms"] / args.steps, "share": v["share"],
                          "launches_per_step": v["launches"] / args.steps} for k, v in mx["phases"].items()}
+    # each HBM-bound phase's algorithmic bytes per step over its time, as a fraction of the copy
+    # bandwidth (the bytes of the roofline function; the tensor-core phase is not HBM-bound)
+    hbm_peak = measured_peaks()[0]
+    L = 4 * (w.nx + 2) * (w.ny + 2) * (w.nz + 2)
+    n3 = w.nx * w.ny * w.nz
+    nqm = sum(mx["nq"]) / len(mx["nq"]) if mx["nq"] else 0.0
+    algo = {"stencil": 12 * 8.0 * n3, "divergence": (4 * 8.0 + 6.0) * n3, "correct": 7 * 8.0 * n3,
+            "refine": (2 * 8.0 + 6.0) * n3, "gs_dots": 8.0 * L * (nqm + 1), "gs_update": 8.0 * L * (nqm + 2)}
+    for k, byts in algo.items():
+        ph = out["phases"].get(k)
+        if ph and ph["ms_per_step"] > 0:
+            ph["hbm_frac"] = byts / (ph["ms_per_step"] / 1e3) / 1e9 / hbm_peak
     out["fp64_plain"] = {"value": fp["value"], "ms_per_step": fp["ms"] / args.steps,
                          "krylov_vector_ms": fp["kv_ms"],
                          "roofline": roofline(fp["phases"], w, "fp64", args.steps, fp["nq"]),
