@@ -28,7 +28,8 @@ DF_VARIANTS = [(0, 32, 1), (0, 32, 2), (0, 64, 1), (0, 32, 4), (0, 64, 2), (0, 1
 CASES = [((70, 65, 67), synth.CC, 2e6, 0), ((33, 18, 20), synth.AA, 3e6, 0), ((33, 18, 20), synth.AA, 3e6, 1),
          ((9, 130, 12), synth.AA, 3e6, 1)]
 # the fixed-point operator (variant 2) serves cubic grids: ragged cubes against the tiles
-CUBES = [((37, 37, 37), synth.CC, 2e6, 0), ((33, 33, 33), synth.AA, 3e6, 1), ((20, 20, 20), synth.AA, 3e6, 0)]
+CUBES = [((37, 37, 37), synth.CC, 2e6, 0), ((33, 33, 33), synth.AA, 3e6, 1), ((20, 20, 20), synth.AA, 3e6, 0),
+         ((2, 2, 2), synth.CC, 1e6, 0), ((3, 3, 3), synth.AA, 1e6, 1)]  # every cell next to a wall
 
 
 @pytest.fixture(scope="module", autouse=True)
