@@ -33,6 +33,12 @@
  *   - advection (a.grad) b in the advective form of Eqs (8)-(9): a 3-point (non-uniform next
  *     to walls) central first derivative of b at b's node, times the advecting velocity
  *     averaged (2 or 4 nearest stored values) to that node;
+ *   - optional first-order upwind advection (adv = 1): the derivative of b along each axis is
+ *     the one-sided difference towards the upstream neighbour (the backward difference where
+ *     the selecting velocity, averaged to b's node as above, is >= 0, else the forward one),
+ *     over the actual node gap (h/2 to a wall node). In the linearised operator the base
+ *     velocity selects in both advection terms, (U.grad) v and (v.grad) U, so J is the exact
+ *     derivative of the upwind residual wherever no averaged base velocity changes sign;
  *   - buoyancy T e_z on a w-face: mean of the two adjacent cell temperatures;
  *   - divergence / gradient: the MAC differences (divided by the cell width / the distance
  *     between the two cell centres); the Poisson operator is D G with the wall faces excluded
@@ -59,6 +65,7 @@ typedef struct {
   int tproj; /* 0: orthogonal (Gram) reading of Eq (21); 1: oblique reading */
   double gr, pr;
   double stretch; /* Eq (22) stretching parameter s, 0 <= s < 1/(2 pi); 0: uniform grid */
+  int adv;        /* advection scheme: 0 central (the default reading), 1 first-order upwind */
 } or_grid;
 
 typedef struct {
@@ -186,12 +193,25 @@ static double interp(const or_ctx* c, const double* ac, int comp, int F, int i, 
   return s / cnt;
 }
 
-/* (a . grad) b at entry (i,j,k) of field F; a = (a0, a1, a2) on their faces. */
-static double advect(const or_ctx* c, const double* const a[3], const double* b, int F, int i, int j,
-                     int k) {
+/* One-sided first derivative along axis a: backward (towards index t-1) if up, else forward. */
+static double d1_side(const or_ctx* c, const double* f, int F, int a, int i, int j, int k, int up) {
+  int t[3] = {i, j, k};
+  double x0 = coord(c, F, a, t[a]), f0 = at(c, f, i, j, k);
+  if (up) return (f0 - nb(c, f, i, j, k, a, -1)) / (x0 - coord(c, F, a, t[a] - 1));
+  return (nb(c, f, i, j, k, a, +1) - f0) / (coord(c, F, a, t[a] + 1) - x0);
+}
+
+/* (a . grad) b at entry (i,j,k) of field F; a = (a0, a1, a2) on their faces. Central, or
+   with adv = 1 upwind along each axis by the sign of sel's component averaged to the node. */
+static double advect_sel(const or_ctx* c, const double* const a[3], const double* const sel[3],
+                         const double* b, int F, int i, int j, int k) {
   double s = 0.0;
-  for (int comp = 0; comp < 3; ++comp)
-    s += interp(c, a[comp], comp, F, i, j, k) * d1(c, b, F, comp, i, j, k);
+  for (int comp = 0; comp < 3; ++comp) {
+    double db;
+    if (c->g.adv) db = d1_side(c, b, F, comp, i, j, k, interp(c, sel[comp], comp, F, i, j, k) >= 0.0);
+    else db = d1(c, b, F, comp, i, j, k);
+    s += interp(c, a[comp], comp, F, i, j, k) * db;
+  }
   return s;
 }
 
@@ -325,6 +345,7 @@ static void stretched_neumann_axis(or_ctx* c, int a) {
 or_ctx* or_create(const or_grid* g) {
   if (!g || g->nx < 2 || g->ny < 2 || g->nz < 2) return NULL;
   if (!(g->stretch >= 0.0 && g->stretch < 0.5 / M_PI)) return NULL; /* Eq (22) must stay monotone */
+  if (g->adv != 0 && g->adv != 1) return NULL;
   or_ctx* c = (or_ctx*)calloc(1, sizeof(or_ctx));
   c->g = *g;
   c->n[0] = g->nx;
@@ -549,9 +570,11 @@ static double jx_point(const or_ctx* c, const double* base, const double* xp, in
   const double* xT = xp + 3 * P;
   double r;
   if (F == FT) {
-    r = kappa * laplace(c, xT, FT, i, j, k) - advect(c, Ub, xT, FT, i, j, k) - advect(c, xv, Th, FT, i, j, k);
+    r = kappa * laplace(c, xT, FT, i, j, k) - advect_sel(c, Ub, Ub, xT, FT, i, j, k) -
+        advect_sel(c, xv, Ub, Th, FT, i, j, k);
   } else {
-    r = nu * laplace(c, xv[F], F, i, j, k) - advect(c, Ub, xv[F], F, i, j, k) - advect(c, xv, Ub[F], F, i, j, k);
+    r = nu * laplace(c, xv[F], F, i, j, k) - advect_sel(c, Ub, Ub, xv[F], F, i, j, k) -
+        advect_sel(c, xv, Ub, Ub[F], F, i, j, k);
     if (F == FW) r += 0.5 * (at(c, xT, i, j, k) + at(c, xT, i, j, k + 1));
   }
   return r;
@@ -587,9 +610,9 @@ void or_residual_raw(const or_ctx* c, const double* S, double* F_out) {
           if (!is_dof(c, F, i, j, k)) continue;
           double r;
           if (F == FT) {
-            r = kappa * laplace(c, Th, FT, i, j, k) - advect(c, Us, Th, FT, i, j, k);
+            r = kappa * laplace(c, Th, FT, i, j, k) - advect_sel(c, Us, Us, Th, FT, i, j, k);
           } else {
-            r = nu * laplace(c, Us[F], F, i, j, k) - advect(c, Us, Us[F], F, i, j, k);
+            r = nu * laplace(c, Us[F], F, i, j, k) - advect_sel(c, Us, Us, Us[F], F, i, j, k);
             if (F == FW) r += 0.5 * (at(c, Th, i, j, k) + at(c, Th, i, j, k + 1));
           }
           F_out[F * P + pidx(c, i, j, k)] = r;
@@ -853,10 +876,15 @@ void or_krylov_adjoint(const or_ctx* c, const double* base, const double* y, dou
 
 /* gb[q] = d <ys, J(base) xp> / d base[q] for every entry q of the packed base state. J is
    affine in the base state, so the derivative is the exact difference J(e_q) - J(0) applied
-   to xp, evaluated at the interior outputs within one cell of q. */
+   to xp, evaluated at the interior outputs within one cell of q. Central advection only (with
+   upwinding J is not affine in the base state): NaN everywhere for adv = 1. */
 void or_grad_base(const or_ctx* c, const double* xp, const double* ys, double* gb) {
   size_t P = plen(c);
   int X = c->n[0] + 2, Y = c->n[1] + 2, Z = c->n[2] + 2;
+  if (c->g.adv) {
+    for (size_t q = 0; q < 4 * P; ++q) gb[q] = NAN;
+    return;
+  }
   memset(gb, 0, sizeof(double) * 4 * P);
 #pragma omp parallel
   {

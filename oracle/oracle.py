@@ -36,7 +36,7 @@ class _Grid(ctypes.Structure):
     _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int),
                 ("bc", ctypes.c_int), ("tproj", ctypes.c_int),
                 ("gr", ctypes.c_double), ("pr", ctypes.c_double),
-                ("stretch", ctypes.c_double)]
+                ("stretch", ctypes.c_double), ("adv", ctypes.c_int)]
 
 
 class Stats(ctypes.Structure):
@@ -88,12 +88,12 @@ class Oracle:
     """One grid's oracle context (Eqs (15)-(20)'s per-axis data computed once)."""
 
     def __init__(self, nx, ny, nz, bc=0, gr=1e6, pr=0.71, tproj=0, tol=1e-13, max_passes=10,
-                 stretch=0.0):
+                 stretch=0.0, adv=0):
         self.lib = _load()
         self.nx, self.ny, self.nz = nx, ny, nz
         self.bc, self.gr, self.pr, self.tproj = bc, gr, pr, tproj
-        self.tol, self.max_passes, self.stretch = tol, max_passes, stretch
-        self._g = _Grid(nx, ny, nz, bc, tproj, gr, pr, stretch)
+        self.tol, self.max_passes, self.stretch, self.adv = tol, max_passes, stretch, adv
+        self._g = _Grid(nx, ny, nz, bc, tproj, gr, pr, stretch, adv)
         self._c = self.lib.or_create(ctypes.byref(self._g))
         if not self._c:
             raise ValueError("oracle: invalid grid")

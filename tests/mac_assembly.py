@@ -80,6 +80,22 @@ def d1_1d(n, face, s=0.0):
     return M.tocsr()
 
 
+def d1_side_1d(n, face, backward, s=0.0):
+    """One-sided first difference over the node gap: towards t-1 (backward) or t+1 (forward)."""
+    p = positions(n, face, s)
+    M = sp.lil_matrix((n + 2, n + 2))
+    for t in interior_rows(n, face):
+        if backward:
+            g = p[t] - p[t - 1]
+            M[t, t] += 1.0 / g
+            M[t, t - 1] -= 1.0 / g
+        else:
+            g = p[t + 1] - p[t]
+            M[t, t + 1] += 1.0 / g
+            M[t, t] -= 1.0 / g
+    return M.tocsr()
+
+
 def face_to_cell(n):
     """Row t (cell-like node) = mean of faces t-1 and t."""
     M = sp.lil_matrix((n + 2, n + 2))
@@ -141,21 +157,33 @@ class MacOps:
             m.append(v)
         return np.kron(np.kron(m[2], m[1]), m[0])
 
-    def jacobian(self, base, gr, pr):
-        """Sparse J acting on a packed (u, v, w, T) vector already in Eq (13)'s space."""
+    def upwind_deriv(self, F, a, sel):
+        """First derivative along axis a at the nodes of field F, one-sided towards the
+        upstream node: backward where the node's selecting velocity sel is >= 0."""
+        back = self.along(a, d1_side_1d(self.n[a], F == a, True, self.s))
+        fwd = self.along(a, d1_side_1d(self.n[a], F == a, False, self.s))
+        pos = (sel >= 0.0).astype(float)
+        return sp.diags(pos) @ back + sp.diags(1.0 - pos) @ fwd
+
+    def jacobian(self, base, gr, pr, upwind=False):
+        """Sparse J acting on a packed (u, v, w, T) vector already in Eq (13)'s space. With
+        upwind, each derivative of an advection term is one-sided, chosen by the sign of the
+        base velocity component averaged to the node (in both (U.grad)v and (v.grad)U)."""
         P = self.P
         nu, kappa = gr ** -0.5, 1.0 / (pr * gr ** 0.5)
         Ub = [base[c].ravel() for c in range(3)]
         Th = base[3].ravel()
         blocks = [[None] * 4 for _ in range(4)]
         for F in range(4):
-            diag_adv = sum(sp.diags(self.interp(c, F) @ Ub[c]) @ self.deriv(F, c) for c in range(3))
+            adv = [self.interp(c, F) @ Ub[c] for c in range(3)]
+            D = [self.upwind_deriv(F, c, adv[c]) if upwind else self.deriv(F, c) for c in range(3)]
+            diag_adv = sum(sp.diags(adv[c]) @ D[c] for c in range(3))
             coef = kappa if F == 3 else nu
             own = coef * self.laplace(F) - diag_adv
             target = Th if F == 3 else Ub[F]
             for c in range(3):
                 # -(x . grad) target: the perturbation velocity averaged, times grad of target
-                term = -sp.diags(self.deriv(F, c) @ target) @ self.interp(c, F)
+                term = -sp.diags(D[c] @ target) @ self.interp(c, F)
                 blocks[F][c] = term if blocks[F][c] is None else blocks[F][c] + term
             blocks[F][F] = own if blocks[F][F] is None else blocks[F][F] + own
             if F == 2:

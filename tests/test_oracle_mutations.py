@@ -18,7 +18,7 @@ MUTANTS = {
                            "if (F == FW) r += 0.5 * (at(c, xT, i, j, k) + at(c, xT, i, j, k - 1));"),
     "eigenvalue_not_squared": ("c->lamp[a][m] = -4.0 / (h * h) * s * s;", "c->lamp[a][m] = -4.0 / (h * h) * s;"),
     "wall_pair_not_averaged": ("*lo0 = *lo1 = ml;", "*lo0 = ml;"),
-    "advection_sign": ("- advect(c, xv, Th, FT, i, j, k);\n  } else {", "+ advect(c, xv, Th, FT, i, j, k);\n  } else {"),
+    "advection_sign": ("-\n        advect_sel(c, xv, Ub, Th, FT, i, j, k);", "+\n        advect_sel(c, xv, Ub, Th, FT, i, j, k);"),
     "gradient_direction": ("double g = (phi[cidx(c, u[0], u[1], u[2])] - phi[cidx(c, t[0], t[1], t[2])]) /",
                            "double g = (phi[cidx(c, t[0], t[1], t[2])] - phi[cidx(c, u[0], u[1], u[2])]) /"),
     "wall_half_spacing_dropped": ("if (t <= 0) return 0.0;", "if (t <= 0) return -0.5 / n;"),
@@ -40,7 +40,17 @@ STRETCH_MUTANTS = {
                                              "Q[(size_t)t * n + order[m]] * sqrt(cell_width(c, a, t + 1));"),
 }
 
+# Mistakes in the optional upwind advection; run against its pins.
+UPWIND_MUTANTS = {
+    "upwind_selector_flipped": ("interp(c, sel[comp], comp, F, i, j, k) >= 0.0", "interp(c, sel[comp], comp, F, i, j, k) < 0.0"),
+    "upwind_selected_by_perturbation": ("advect_sel(c, xv, Ub, Ub[F], F, i, j, k)", "advect_sel(c, xv, xv, Ub[F], F, i, j, k)"),
+    "upwind_wall_gap_uniform": ("/ (x0 - coord(c, F, a, t[a] - 1));", "/ c->h[a];"),
+    "upwind_forward_side_swapped": ("return (nb(c, f, i, j, k, a, +1) - f0) / (coord(c, F, a, t[a] + 1) - x0);",
+                                    "return (f0 - nb(c, f, i, j, k, a, -1)) / (coord(c, F, a, t[a] + 1) - x0);"),
+}
+
 CASES = {name: (old, new, "test_oracle_pins.py") for name, (old, new) in MUTANTS.items()}
+CASES.update({name: (old, new, "test_oracle_upwind.py") for name, (old, new) in UPWIND_MUTANTS.items()})
 CASES.update({name: (old, new, "test_oracle_stretch.py") for name, (old, new) in STRETCH_MUTANTS.items()})
 
 
