@@ -63,6 +63,18 @@ enum { KV_BC_CC = 0 /* conducting, Eq (6) */, KV_BC_AA = 1 /* insulated, Eq (7) 
    the condition. */
 enum { KV_TPROJ_ORTHOGONAL = 0, KV_TPROJ_OBLIQUE = 1 };
 
+/* Advection scheme of the linearised operator and the residual. Central: the derivative of
+   the advected field is the 3-point central difference at its node (non-uniform next to a
+   wall node), times the advecting velocity averaged to the node (Section 3's discretisation).
+   Upwind (an option, not from the paper): along each axis the derivative is the one-sided
+   difference towards the upstream neighbour, over the node gap (h/2 to a wall node), chosen
+   by the sign of the base velocity's component averaged to the node (>= 0: backward; the
+   4-point averages summed in the order (t-1 along the velocity's axis, then t; within each,
+   t and t+1 along the node's face axis)). The linearisation keeps the base velocity's choice
+   in both (U.grad)v and (v.grad)U, so it is the derivative of the upwind residual wherever no
+   averaged base velocity is zero. */
+enum { KV_ADV_CENTRAL = 0, KV_ADV_UPWIND = 1 };
+
 /* Arithmetic of the Krylov-vector evaluation. FP64: every step in FP64. MIXED: the
    pressure-correction Poisson solve runs its per-axis contractions on the tensor cores
    (BF16 slices, FP32 accumulation) and is refined to FP64 accuracy with an FP64 residual;
@@ -93,6 +105,13 @@ typedef struct {
                         reads the plus-neighbour coefficients instead of rebuilding them). The
                         transpose, the base-flow gradient and kv_krylov_vector_noalloc take the
                         uniform grid only. */
+  int advection;     /* KV_ADV_CENTRAL (0, the paper's discretisation) or KV_ADV_UPWIND: first-order
+                        upwind derivatives in the advection terms of Eqs (8)-(9) and of the
+                        residual of Eqs (1)-(2). Upwind takes the uniform grid only; a KV_PREC_MIXED
+                        grid then stores 12 more coefficient pairs per point, as a stretched one
+                        does, and its operator runs in double-float arithmetic (the fixed-point
+                        form is central only). kv_base_flow_gradient and kv_krylov_vector_noalloc
+                        take central advection only. */
 } kv_grid_desc;
 
 typedef struct {
@@ -225,7 +244,7 @@ kv_status kv_arnoldi_step(kv_handle h, double* V, int j, double* h_col);
 /* Transpose of the Krylov map: z = A^T y with A = (Pi_v (+) P_T) J P_BC (the adjoint eigenvalue
    problem of Eq (10) uses it). With the orthogonal reading of Eq (21) the three projections are
    symmetric, so A^T = P_BC J^T (Pi_v (+) P_T); J^T is applied from the same assembled
-   coefficients as J. y, z: packed vectors (device, must not overlap). Requires
+   coefficients as J (either advection scheme). y, z: packed vectors (device, must not overlap). Requires
    KV_TPROJ_ORTHOGONAL and the uniform grid (else KV_ERR_ARG: on a stretched grid Pi_v is
    symmetric only in the volume-weighted product) and a base flow (else KV_ERR_STATE). */
 kv_status kv_krylov_vector_adjoint(kv_handle h, const double* y, double* z);
@@ -237,7 +256,8 @@ kv_status kv_krylov_vector_adjoint(kv_handle h, const double* y, double* z);
    the Theta part from the term -(v . grad) Theta of Eq (8); dgr (host, nullable) =
    d<y, A x>/d Gr, from the scalings Gr^-1/2 and (Pr Gr^1/2)^-1 of Eqs (1)-(2). x, y: packed
    vectors (device). Synchronises the stream when dgr is given. Same requirements as
-   kv_krylov_vector_adjoint. */
+   kv_krylov_vector_adjoint, and central advection (KV_ERR_ARG with KV_ADV_UPWIND, for which
+   the operator is not affine in the base state). */
 kv_status kv_base_flow_gradient(kv_handle h, const double* x, const double* y, double* g_base, double* dgr);
 
 /* Newton step 2 of Section 3.1: the steady residual of Eqs (1)-(2) at the packed state S
@@ -382,7 +402,7 @@ kv_status kv_arnoldi_counts(kv_handle h, long long* steps, long long* second_upd
    grid descriptor, a packed base state, x and y, all caller-owned device pointers; no handle
    is created. Its scratch is a fixed __device__ array of about 1.5 MB that every GPU loading
    the library keeps until the process exits, which limits the grid to
-   KV_NOALLOC_MAX_N cells per axis; larger grids, a stretched grid and
+   KV_NOALLOC_MAX_N cells per axis; larger grids, a stretched grid, upwind advection and
    desc->precision != KV_PREC_FP64 return KV_ERR_ARG (message via kv_last_error(NULL)), as do
    x or base overlapping y. The per-axis tables of Eq (15) are written into the array by a
    kernel on `stream` at every call. The first call on a device looks up the array's device

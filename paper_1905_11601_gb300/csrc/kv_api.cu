@@ -240,6 +240,14 @@ kv_status validate(const kv_grid_desc* d, std::string& msg) {
     msg = "stretch must be in [0, 1/(2 pi))";
     return KV_ERR_ARG;
   }
+  if (d->advection != KV_ADV_CENTRAL && d->advection != KV_ADV_UPWIND) {
+    msg = "advection must be KV_ADV_CENTRAL or KV_ADV_UPWIND";
+    return KV_ERR_ARG;
+  }
+  if (d->advection == KV_ADV_UPWIND && d->stretch != 0.0) {
+    msg = "upwind advection takes the uniform grid only (stretch must be 0)";
+    return KV_ERR_ARG;
+  }
   return KV_OK;
 }
 
@@ -539,6 +547,7 @@ kv_status kv_create_grid(const kv_grid_desc* desc, void* stream, kv_handle* out)
   g.kappa = 1.0 / (desc->pr * sqrt(desc->gr));
   g.bc = desc->spanwise_bc;
   g.tproj = desc->tproj;
+  g.adv = desc->advection;
   h->P = (size_t)g.X * g.Y * g.Z;
   h->Nc = (size_t)g.nx * g.ny * g.nz;
 
@@ -699,7 +708,7 @@ static kv_status base_flow_ready(kv_grid* h) {
       kv_status s = dalloc(h, &h->xsplit, 4 * h->P);
       if (s != KV_OK) return s;
     }
-    if (h->str.sw && !h->coef_dfp) {
+    if ((h->str.sw || h->g.adv) && !h->coef_dfp) {
       kv_status s = dalloc(h, &h->coef_dfp, (size_t)KV_NCOEF_DFP * h->P);
       if (s != KV_OK) return s;
     }
@@ -1109,6 +1118,10 @@ kv_status kv_base_flow_gradient(kv_handle h, const double* x, const double* y, d
     return fail(h, KV_ERR_ARG,
                 "kv_base_flow_gradient: defined on the uniform grid (the velocity projection of a stretched "
                 "grid is not symmetric)");
+  if (h->g.adv)
+    return fail(h, KV_ERR_ARG,
+                "kv_base_flow_gradient: defined for central advection (with upwinding the operator is not "
+                "affine in the base flow)");
   kv_status s = project_output_side(h, y);
   if (s != KV_OK) return s;
   if (g_base) {

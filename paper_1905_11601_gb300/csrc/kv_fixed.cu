@@ -289,11 +289,11 @@ __global__ void __launch_bounds__(FTHREADS, 2)
 
 }  // namespace
 
-// Grids the fixed-point operator serves: mixed precision, uniform and cubic (one h on all axes),
-// offsets of a packed vector within 32 bits; kv_fx_setup adds a finite base state whose grid
-// leaves the accumulators their headroom.
+// Grids the fixed-point operator serves: mixed precision, central advection, uniform and cubic
+// (one h on all axes), offsets of a packed vector within 32 bits; kv_fx_setup adds a finite base
+// state whose grid leaves the accumulators their headroom.
 bool kv_fx_eligible(const kv_grid* h) {
-  return h->d.precision == KV_PREC_MIXED && !h->str.sw && h->g.nx == h->g.ny && h->g.ny == h->g.nz &&
+  return h->d.precision == KV_PREC_MIXED && !h->str.sw && !h->g.adv && h->g.nx == h->g.ny && h->g.ny == h->g.nz &&
          4 * h->P < (size_t(1) << 31);
 }
 

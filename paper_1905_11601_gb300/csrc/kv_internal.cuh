@@ -47,6 +47,7 @@ struct KvGeom {
   double nu, kappa; // Gr^-1/2 and (Pr Gr^1/2)^-1 (Eqs (1)-(2) scaling)
   int bc;           // KV_BC_CC / KV_BC_AA
   int tproj;        // KV_TPROJ_*
+  int adv;          // KV_ADV_* (upwind on uniform grids only)
 };
 
 // The device tables of a stretched grid (Eq 22); all null on a uniform grid. A separate kernel
@@ -92,7 +93,7 @@ struct kv_grid {
   KvStretch str;            // stretched grid: views of sw / swd (all null on a uniform grid)
   double* sw = nullptr;     // stretched grid: the KV_SW_* weight tables
   float2* swd = nullptr;    // stretched KV_PREC_MIXED grid: the KV_SWD_* tables
-  float2* coef_dfp = nullptr; // stretched KV_PREC_MIXED grid, KV_NCOEF_DFP * P: plus coefficients as pairs
+  float2* coef_dfp = nullptr; // stretched or upwind KV_PREC_MIXED grid, KV_NCOEF_DFP * P: plus coefficients as pairs
   double hmin = 0.0;        // smallest cell width (the SIMPLE test)
   unsigned long long* red = nullptr;  // [0] max|D v| bits, [1] max|v| bits (guard->red, or the
                                       // allocation-free entry point's own pair)

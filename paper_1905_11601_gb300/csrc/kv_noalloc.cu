@@ -83,6 +83,8 @@ extern "C" kv_status kv_krylov_vector_noalloc(const kv_grid_desc* desc, const do
     return noalloc_fail(KV_ERR_ARG, "kv_krylov_vector_noalloc: only KV_PREC_FP64 is available");
   if (desc->stretch != 0.0)
     return noalloc_fail(KV_ERR_ARG, "kv_krylov_vector_noalloc: the uniform grid only (stretch must be 0)");
+  if (desc->advection != KV_ADV_CENTRAL)
+    return noalloc_fail(KV_ERR_ARG, "kv_krylov_vector_noalloc: central advection only");
   if (!(desc->gr > 0) || !(desc->pr > 0) || !isfinite(desc->gr) || !isfinite(desc->pr))
     return noalloc_fail(KV_ERR_ARG, "kv_krylov_vector_noalloc: gr and pr must be finite and > 0");
 
@@ -125,6 +127,7 @@ extern "C" kv_status kv_krylov_vector_noalloc(const kv_grid_desc* desc, const do
   g.kappa = 1.0 / (desc->pr * sqrt(desc->gr));
   g.bc = desc->spanwise_bc;
   g.tproj = desc->tproj;
+  g.adv = KV_ADV_CENTRAL;
   h.hmin = fmin(g.hx, fmin(g.hy, g.hz));
   h.P = (size_t)g.X * g.Y * g.Z;
   h.Nc = (size_t)g.nx * g.ny * g.nz;

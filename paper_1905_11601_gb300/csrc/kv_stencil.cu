@@ -72,6 +72,37 @@ __device__ __forceinline__ W3 wf2(const KvGeom& g, const KvStretch& S, int t) {
   return STR ? sw3<A>(g, S, KV_SW_F2, t) : d2_face(ax_ih2<A>(g));
 }
 
+// First-order upwind weights on the uniform grid (KvGeom::adv): the one-sided difference towards
+// the upstream node, backward where the selecting velocity s >= 0, over the node gap (h/2 between
+// the first or last cell centre and its wall node, h elsewhere and between faces).
+__device__ __forceinline__ W3 up_cell(int t, int n, double ih, double s) {
+  if (s >= 0.0) {
+    const double w = t == 1 ? 2.0 * ih : ih;
+    return {-w, w, 0.0};
+  }
+  const double w = t == n ? 2.0 * ih : ih;
+  return {0.0, -w, w};
+}
+__device__ __forceinline__ W3 up_face(double ih, double s) {
+  return s >= 0.0 ? W3{-ih, ih, 0.0} : W3{0.0, -ih, ih};
+}
+// The selecting sum of a 4-point average, in a fixed order: the two entries at t-1 along the
+// velocity's own axis, then the two at t (each pair: t, t+1 along the node's face axis). Only its
+// sign is used.
+__device__ __forceinline__ double sel4(double a, double b, double c, double d) { return ((a + b) + c) + d; }
+// First-derivative weights of an advection term along axis A at a cell-like / face-like index t:
+// central, or upwind by the selecting velocity s.
+template <int A, bool STR>
+__device__ __forceinline__ W3 adv_c(const KvGeom& g, const KvStretch& S, int t, double s) {
+  if (!STR && g.adv) return up_cell(t, ax_n<A>(g), ax_ih<A>(g), s);
+  return wc1<A, STR>(g, S, t);
+}
+template <int A, bool STR>
+__device__ __forceinline__ W3 adv_f(const KvGeom& g, const KvStretch& S, int t, double s) {
+  if (!STR && g.adv) return up_face(ax_ih<A>(g), s);
+  return wf1<A, STR>(g, S, t);
+}
+
 __device__ __forceinline__ double ap(const W3& w, double fm, double f0, double fp) {
   return fma(w.m, fm, fma(w.c, f0, w.p * fp));
 }
@@ -154,9 +185,10 @@ __global__ void __launch_bounds__(256) k_stencil(KvGeom g, KvStretch S, const do
   // ---- u on the x-face (i, j, k) ----
   double ru = 0.0;
   if (G.dof_u(i, j, k)) {
-    const W3 dx1 = wf1<0, STR>(g, S, i), dx2 = wf2<0, STR>(g, S, i);
-    const W3 dy1 = wc1<1, STR>(g, S, j), dy2 = wc2<1, STR>(g, S, j);
-    const W3 dz1 = wc1<2, STR>(g, S, k), dz2 = wc2<2, STR>(g, S, k);
+    const W3 dx2 = wf2<0, STR>(g, S, i), dy2 = wc2<1, STR>(g, S, j), dz2 = wc2<2, STR>(g, S, k);
+    const W3 dx1 = adv_f<0, STR>(g, S, i, B.lu(i, j, k));
+    const W3 dy1 = adv_c<1, STR>(g, S, j, sel4(B.lv(i, j - 1, k), B.lv(i + 1, j - 1, k), B.lv(i, j, k), B.lv(i + 1, j, k)));
+    const W3 dz1 = adv_c<2, STR>(g, S, k, sel4(B.lw(i, j, k - 1), B.lw(i + 1, j, k - 1), B.lw(i, j, k), B.lw(i + 1, j, k)));
     const double c = Xl.lu(i, j, k);
     const double xm = Xl.lu(i - 1, j, k), xp = Xl.lu(i + 1, j, k);
     const double ym = Xl.lu(i, j - 1, k), yp = Xl.lu(i, j + 1, k);
@@ -181,9 +213,10 @@ __global__ void __launch_bounds__(256) k_stencil(KvGeom g, KvStretch S, const do
   // ---- v on the y-face (i, j, k) ----
   double rv = 0.0;
   if (G.dof_v(i, j, k)) {
-    const W3 dx1 = wc1<0, STR>(g, S, i), dx2 = wc2<0, STR>(g, S, i);
-    const W3 dy1 = wf1<1, STR>(g, S, j), dy2 = wf2<1, STR>(g, S, j);
-    const W3 dz1 = wc1<2, STR>(g, S, k), dz2 = wc2<2, STR>(g, S, k);
+    const W3 dx2 = wc2<0, STR>(g, S, i), dy2 = wf2<1, STR>(g, S, j), dz2 = wc2<2, STR>(g, S, k);
+    const W3 dx1 = adv_c<0, STR>(g, S, i, sel4(B.lu(i - 1, j, k), B.lu(i - 1, j + 1, k), B.lu(i, j, k), B.lu(i, j + 1, k)));
+    const W3 dy1 = adv_f<1, STR>(g, S, j, B.lv(i, j, k));
+    const W3 dz1 = adv_c<2, STR>(g, S, k, sel4(B.lw(i, j, k - 1), B.lw(i, j + 1, k - 1), B.lw(i, j, k), B.lw(i, j + 1, k)));
     const double c = Xl.lv(i, j, k);
     const double xm = Xl.lv(i - 1, j, k), xp = Xl.lv(i + 1, j, k);
     const double ym = Xl.lv(i, j - 1, k), yp = Xl.lv(i, j + 1, k);
@@ -208,9 +241,10 @@ __global__ void __launch_bounds__(256) k_stencil(KvGeom g, KvStretch S, const do
   // ---- w on the z-face (i, j, k), with the buoyancy term T e_z ----
   double rw = 0.0;
   if (G.dof_w(i, j, k)) {
-    const W3 dx1 = wc1<0, STR>(g, S, i), dx2 = wc2<0, STR>(g, S, i);
-    const W3 dy1 = wc1<1, STR>(g, S, j), dy2 = wc2<1, STR>(g, S, j);
-    const W3 dz1 = wf1<2, STR>(g, S, k), dz2 = wf2<2, STR>(g, S, k);
+    const W3 dx2 = wc2<0, STR>(g, S, i), dy2 = wc2<1, STR>(g, S, j), dz2 = wf2<2, STR>(g, S, k);
+    const W3 dx1 = adv_c<0, STR>(g, S, i, sel4(B.lu(i - 1, j, k), B.lu(i - 1, j, k + 1), B.lu(i, j, k), B.lu(i, j, k + 1)));
+    const W3 dy1 = adv_c<1, STR>(g, S, j, sel4(B.lv(i, j - 1, k), B.lv(i, j - 1, k + 1), B.lv(i, j, k), B.lv(i, j, k + 1)));
+    const W3 dz1 = adv_f<2, STR>(g, S, k, B.lw(i, j, k));
     const double c = Xl.lw(i, j, k);
     const double xm = Xl.lw(i - 1, j, k), xp = Xl.lw(i + 1, j, k);
     const double ym = Xl.lw(i, j - 1, k), yp = Xl.lw(i, j + 1, k);
@@ -238,9 +272,10 @@ __global__ void __launch_bounds__(256) k_stencil(KvGeom g, KvStretch S, const do
   // ---- T at the cell (i, j, k), then the temperature projection of Eq (21) ----
   const bool cell = i >= 1 && i <= g.nx && j >= 1 && j <= g.ny && k >= 1 && k <= g.nz;
   if (cell) {
-    const W3 dx1 = wc1<0, STR>(g, S, i), dx2 = wc2<0, STR>(g, S, i);
-    const W3 dy1 = wc1<1, STR>(g, S, j), dy2 = wc2<1, STR>(g, S, j);
-    const W3 dz1 = wc1<2, STR>(g, S, k), dz2 = wc2<2, STR>(g, S, k);
+    const W3 dx2 = wc2<0, STR>(g, S, i), dy2 = wc2<1, STR>(g, S, j), dz2 = wc2<2, STR>(g, S, k);
+    const W3 dx1 = adv_c<0, STR>(g, S, i, B.lu(i - 1, j, k) + B.lu(i, j, k));
+    const W3 dy1 = adv_c<1, STR>(g, S, j, B.lv(i, j - 1, k) + B.lv(i, j, k));
+    const W3 dz1 = adv_c<2, STR>(g, S, k, B.lw(i, j, k - 1) + B.lw(i, j, k));
     const double c = Xl.lT(i, j, k);
     const double xm = Xl.lT(i - 1, j, k), xp = Xl.lT(i + 1, j, k);
     const double ym = Xl.lT(i, j - 1, k), yp = Xl.lT(i, j + 1, k);
@@ -313,9 +348,10 @@ __global__ void __launch_bounds__(256) k_assemble(KvGeom g, KvStretch S, const d
     o[0] = diff * (x2.c + y2.c + z2.c) - (ax * x1.c + ay * y1.c + az * z1.c) - gself;
   };
   if (G.dof_u(i, j, k)) {
-    const W3 dx1 = wf1<0, STR>(g, S, i), dx2 = wf2<0, STR>(g, S, i);
-    const W3 dy1 = wc1<1, STR>(g, S, j), dy2 = wc2<1, STR>(g, S, j);
-    const W3 dz1 = wc1<2, STR>(g, S, k), dz2 = wc2<2, STR>(g, S, k);
+    const W3 dx2 = wf2<0, STR>(g, S, i), dy2 = wc2<1, STR>(g, S, j), dz2 = wc2<2, STR>(g, S, k);
+    const W3 dx1 = adv_f<0, STR>(g, S, i, B.lu(i, j, k));
+    const W3 dy1 = adv_c<1, STR>(g, S, j, sel4(B.lv(i, j - 1, k), B.lv(i + 1, j - 1, k), B.lv(i, j, k), B.lv(i + 1, j, k)));
+    const W3 dz1 = adv_c<2, STR>(g, S, k, sel4(B.lw(i, j, k - 1), B.lw(i + 1, j, k - 1), B.lw(i, j, k), B.lw(i + 1, j, k)));
     const double Ua = B.lu(i, j, k);
     const double Va = 0.25 * (B.lv(i, j - 1, k) + B.lv(i, j, k) + B.lv(i + 1, j - 1, k) + B.lv(i + 1, j, k));
     const double Wa = 0.25 * (B.lw(i, j, k - 1) + B.lw(i, j, k) + B.lw(i + 1, j, k - 1) + B.lw(i + 1, j, k));
@@ -327,9 +363,10 @@ __global__ void __launch_bounds__(256) k_assemble(KvGeom g, KvStretch S, const d
     c[8] = -0.25 * gz;
   }
   if (G.dof_v(i, j, k)) {
-    const W3 dx1 = wc1<0, STR>(g, S, i), dx2 = wc2<0, STR>(g, S, i);
-    const W3 dy1 = wf1<1, STR>(g, S, j), dy2 = wf2<1, STR>(g, S, j);
-    const W3 dz1 = wc1<2, STR>(g, S, k), dz2 = wc2<2, STR>(g, S, k);
+    const W3 dx2 = wc2<0, STR>(g, S, i), dy2 = wf2<1, STR>(g, S, j), dz2 = wc2<2, STR>(g, S, k);
+    const W3 dx1 = adv_c<0, STR>(g, S, i, sel4(B.lu(i - 1, j, k), B.lu(i - 1, j + 1, k), B.lu(i, j, k), B.lu(i, j + 1, k)));
+    const W3 dy1 = adv_f<1, STR>(g, S, j, B.lv(i, j, k));
+    const W3 dz1 = adv_c<2, STR>(g, S, k, sel4(B.lw(i, j, k - 1), B.lw(i, j + 1, k - 1), B.lw(i, j, k), B.lw(i, j + 1, k)));
     const double Ua = 0.25 * (B.lu(i - 1, j, k) + B.lu(i, j, k) + B.lu(i - 1, j + 1, k) + B.lu(i, j + 1, k));
     const double Va = B.lv(i, j, k);
     const double Wa = 0.25 * (B.lw(i, j, k - 1) + B.lw(i, j, k) + B.lw(i, j + 1, k - 1) + B.lw(i, j + 1, k));
@@ -341,9 +378,10 @@ __global__ void __launch_bounds__(256) k_assemble(KvGeom g, KvStretch S, const d
     c[17] = -0.25 * gz;
   }
   if (G.dof_w(i, j, k)) {
-    const W3 dx1 = wc1<0, STR>(g, S, i), dx2 = wc2<0, STR>(g, S, i);
-    const W3 dy1 = wc1<1, STR>(g, S, j), dy2 = wc2<1, STR>(g, S, j);
-    const W3 dz1 = wf1<2, STR>(g, S, k), dz2 = wf2<2, STR>(g, S, k);
+    const W3 dx2 = wc2<0, STR>(g, S, i), dy2 = wc2<1, STR>(g, S, j), dz2 = wf2<2, STR>(g, S, k);
+    const W3 dx1 = adv_c<0, STR>(g, S, i, sel4(B.lu(i - 1, j, k), B.lu(i - 1, j, k + 1), B.lu(i, j, k), B.lu(i, j, k + 1)));
+    const W3 dy1 = adv_c<1, STR>(g, S, j, sel4(B.lv(i, j - 1, k), B.lv(i, j - 1, k + 1), B.lv(i, j, k), B.lv(i, j, k + 1)));
+    const W3 dz1 = adv_f<2, STR>(g, S, k, B.lw(i, j, k));
     const double Ua = 0.25 * (B.lu(i - 1, j, k) + B.lu(i, j, k) + B.lu(i - 1, j, k + 1) + B.lu(i, j, k + 1));
     const double Va = 0.25 * (B.lv(i, j - 1, k) + B.lv(i, j, k) + B.lv(i, j - 1, k + 1) + B.lv(i, j, k + 1));
     const double Wa = B.lw(i, j, k);
@@ -355,9 +393,10 @@ __global__ void __launch_bounds__(256) k_assemble(KvGeom g, KvStretch S, const d
     c[26] = -0.25 * gy;
   }
   if (i >= 1 && i <= g.nx && j >= 1 && j <= g.ny && k >= 1 && k <= g.nz) {
-    const W3 dx1 = wc1<0, STR>(g, S, i), dx2 = wc2<0, STR>(g, S, i);
-    const W3 dy1 = wc1<1, STR>(g, S, j), dy2 = wc2<1, STR>(g, S, j);
-    const W3 dz1 = wc1<2, STR>(g, S, k), dz2 = wc2<2, STR>(g, S, k);
+    const W3 dx2 = wc2<0, STR>(g, S, i), dy2 = wc2<1, STR>(g, S, j), dz2 = wc2<2, STR>(g, S, k);
+    const W3 dx1 = adv_c<0, STR>(g, S, i, B.lu(i - 1, j, k) + B.lu(i, j, k));
+    const W3 dy1 = adv_c<1, STR>(g, S, j, B.lv(i, j - 1, k) + B.lv(i, j, k));
+    const W3 dz1 = adv_c<2, STR>(g, S, k, B.lw(i, j, k - 1) + B.lw(i, j, k));
     const double Ua = 0.5 * (B.lu(i - 1, j, k) + B.lu(i, j, k));
     const double Va = 0.5 * (B.lv(i, j - 1, k) + B.lv(i, j, k));
     const double Wa = 0.5 * (B.lw(i, j, k - 1) + B.lw(i, j, k));
@@ -509,11 +548,12 @@ __constant__ int kDfFromFull[KV_NCOEF_DF] = {0,  1,  3,  5,  7,  8,  9,  10, 12,
                                              19, 21, 23, 25, 26, 27, 28, 30, 32, 34, 35, 36};
 
 // Assembled coefficient of each plus neighbour (x+, y+, z+ of u, v, w, T), which the operator of a
-// stretched grid reads directly: there beta is not a power of two, so c+ is not rebuilt from c-.
+// stretched grid reads directly (there beta is not a power of two, so c+ is not rebuilt from c-),
+// and so does the operator with upwind advection (its c+ is not alpha + beta c- either).
 __constant__ int kPlusFromFull[KV_NCOEF_DFP] = {2, 4, 6, 11, 13, 15, 20, 22, 24, 29, 31, 33};
 
 // y* = J P_BC x with the FP32-pair coefficients and the split projected input xs (output as
-// k_apply). STR (stretched grid): the plus coefficients come from cplus (KV_NCOEF_DFP pairs per
+// k_apply). STR (stretched grid, or upwind advection): the plus coefficients come from cplus (KV_NCOEF_DFP pairs per
 // point) instead of alpha + beta c-. One thread per (cell, equation): threadIdx.y = 4 row + eq, eq = 0..3 for u, v, w,
 // T, so each warp forms one equation for consecutive cells (no divergence) and keeps only that
 // equation's inputs (15-17 pairs) and coefficients (6-7 pairs) live; the inputs shared between
@@ -749,7 +789,7 @@ __device__ __forceinline__ void march_body(const KvGeom& g, const float2* __rest
       const int ck = wall_class(k, g.nz);
       const size_t e = (size_t)i + (size_t)sy * j + (size_t)sz * k;
       DFAcc a;
-      // c- x- + c+ x+ along one axis; on a stretched grid (STR) c+ is read from cplus (entry
+      // c- x- + c+ x+ along one axis; on a stretched grid or with upwinding (STR) c+ is read from cplus (entry
       // 3 eq + axis), else rebuilt as alpha + beta c-
       auto own_axis = [&](DFAcc& acc, const float2 cm, const DF xm, const DF xp, const float2 alpha, const float beta,
                           int axis) {
@@ -819,8 +859,8 @@ __global__ void __launch_bounds__(MTHREADS, 2) k_apply_df_march(KvGeom g, const 
   march_body<false>(g, coef, nullptr, x, P, vstar, tout, al, kc);
 }
 
-// A stretched grid's march (Eq 22): the three plus coefficients per equation come from cplus,
-// which needs more registers than two blocks per SM leave.
+// The march of a stretched grid (Eq 22) or of upwind advection: the three plus coefficients per
+// equation come from cplus, which needs more registers than two blocks per SM leave.
 __global__ void __launch_bounds__(MTHREADS, 1) k_apply_df_march_str(KvGeom g, const float2* __restrict__ coef,
                                                                     const float2* __restrict__ cplus,
                                                                     const double* __restrict__ x, size_t P,
@@ -878,7 +918,7 @@ __global__ void __launch_bounds__(256) k_coef_df(const double* __restrict__ coef
   }
 }
 
-// The plus coefficients of a stretched grid as FP32 pairs (KV_NCOEF_DFP of them).
+// The plus coefficients of a stretched grid or of upwind advection as FP32 pairs (KV_NCOEF_DFP of them).
 __global__ void __launch_bounds__(256) k_coef_df_plus(const double* __restrict__ coef, float2* __restrict__ cdf,
                                                       size_t P) {
   const size_t n = (size_t)KV_NCOEF_DFP * P;
@@ -937,7 +977,7 @@ void kv_launch_zero_boundary(const kv_grid* h, double* vstar, double* tout, cuda
 
 void kv_launch_coef_df(const kv_grid* h, const double* coef, float2* cdf, cudaStream_t s) {
   k_coef_df<<<4 * 152, 256, 0, s>>>(coef, cdf, h->P);
-  if (h->str.sw) k_coef_df_plus<<<4 * 152, 256, 0, s>>>(coef, h->coef_dfp, h->P);
+  if (h->str.sw || h->g.adv) k_coef_df_plus<<<4 * 152, 256, 0, s>>>(coef, h->coef_dfp, h->P);
 }
 
 void kv_launch_apply_df(const kv_grid* h, const float2* cdf, const double* x, double* vstar, double* tout,
@@ -960,7 +1000,7 @@ void kv_launch_apply_df(const kv_grid* h, const float2* cdf, const double* x, do
     k_zero_boundary<<<2 * 152, 256, 0, s>>>(g, h->P, vstar, tout);
     const int kc = h->df_by;
     dim3 grid((g.nx + MB_X - 1) / MB_X, (g.ny + MB_Y - 1) / MB_Y, (g.nz + kc - 1) / kc);
-    if (h->str.sw)
+    if (h->str.sw || g.adv)  // plus coefficients stored: stretched or upwind
       k_apply_df_march_str<<<grid, MTHREADS, 0, s>>>(g, cdf, h->coef_dfp, x, h->P, vstar, tout, al, kc);
     else
       k_apply_df_march<<<grid, MTHREADS, 0, s>>>(g, cdf, x, h->P, vstar, tout, al, kc);
@@ -973,7 +1013,7 @@ void kv_launch_apply_df(const kv_grid* h, const float2* cdf, const double* x, do
   // df_by rows of cells per block, four equation warps-rows each
   const int bx = h->df_bx, rows = h->df_by;
   dim3 block(bx, 4 * rows, 1), grid((g.X + bx - 1) / bx, (g.Y + rows - 1) / rows, g.Z);
-  if (h->str.sw)
+  if (h->str.sw || g.adv)
     k_apply_df<true><<<grid, block, 0, s>>>(g, cdf, h->coef_dfp, h->xsplit, h->P, vstar, tout, al);
   else
     k_apply_df<false><<<grid, block, 0, s>>>(g, cdf, nullptr, h->xsplit, h->P, vstar, tout, al);

@@ -17,6 +17,7 @@ LIB_PATH = os.path.join(_PKG, "libkv.so")
 KV_BC_CC, KV_BC_AA = 0, 1
 KV_TPROJ_ORTHOGONAL, KV_TPROJ_OBLIQUE = 0, 1
 KV_PREC_FP64, KV_PREC_MIXED = 0, 1
+KV_ADV_CENTRAL, KV_ADV_UPWIND = 0, 1
 
 _STATUS = {0: "KV_OK", -1: "KV_ERR_ARG", -2: "KV_ERR_CUDA", -3: "KV_ERR_NOT_CONVERGED", -4: "KV_ERR_STATE",
            -5: "KV_ERR_NOMEM"}
@@ -58,7 +59,7 @@ class GridDesc(ctypes.Structure):
                 ("spanwise_bc", ctypes.c_int), ("tproj", ctypes.c_int), ("precision", ctypes.c_int),
                 ("gr", ctypes.c_double), ("pr", ctypes.c_double), ("tol", ctypes.c_double),
                 ("max_passes", ctypes.c_int), ("refine_sweeps", ctypes.c_int), ("cgs_passes", ctypes.c_int),
-                ("stretch", ctypes.c_double)]
+                ("stretch", ctypes.c_double), ("advection", ctypes.c_int)]
 
 
 class Guard(ctypes.Structure):
@@ -173,7 +174,8 @@ class Grid:
     """A grid handle: kv_create_grid / kv_destroy_grid around the calls of include/kv.h."""
 
     def __init__(self, nx, ny, nz, bc=KV_BC_CC, gr=1.0e6, pr=0.71, tproj=KV_TPROJ_ORTHOGONAL,
-                 precision=KV_PREC_FP64, tol=0.0, max_passes=0, refine_sweeps=0, cgs_passes=0, stretch=0.0):
+                 precision=KV_PREC_FP64, tol=0.0, max_passes=0, refine_sweeps=0, cgs_passes=0, stretch=0.0,
+                 advection=0):
         import torch
 
         self.torch = torch
@@ -182,7 +184,7 @@ class Grid:
         self.lib = load_library()
         self.nx, self.ny, self.nz = nx, ny, nz
         self.desc = GridDesc(nx, ny, nz, bc, tproj, precision, gr, pr, tol, max_passes, refine_sweeps, cgs_passes,
-                             stretch)
+                             stretch, advection)
         h = ctypes.c_void_p()
         st = self.lib.kv_create_grid(ctypes.byref(self.desc), ctypes.c_void_p(self._stream()), ctypes.byref(h))
         if st != 0:

@@ -47,7 +47,8 @@ def _desc(**kw):
 @pytest.mark.parametrize("bad", [dict(nx=1), dict(nz=2000), dict(spanwise_bc=3), dict(tproj=7),
                                  dict(precision=9), dict(gr=-1.0), dict(pr=0.0), dict(max_passes=-1),
                                  dict(gr=float("nan")), dict(refine_sweeps=-1), dict(refine_sweeps=99), dict(cgs_passes=1),
-                                 dict(stretch=-0.01), dict(stretch=0.16), dict(stretch=float("nan"))])
+                                 dict(stretch=-0.01), dict(stretch=0.16), dict(stretch=float("nan")),
+                                 dict(advection=2), dict(advection=-1), dict(advection=1, stretch=0.05)])
 def test_invalid_descriptor_rejected_on_host(lib, bad):
     h = ctypes.c_void_p()
     st = lib.kv_create_grid(ctypes.byref(_desc(**bad)), None, ctypes.byref(h))
@@ -60,6 +61,13 @@ def test_stretched_grid_rejected_by_the_allocation_free_entry(lib):
     d = _desc(stretch=0.05)
     buf = (ctypes.c_double * 8)()
     assert lib.kv_krylov_vector_noalloc(ctypes.byref(d), buf, buf, buf, None) == -1
+
+
+def test_upwind_rejected_by_the_allocation_free_entry(lib):
+    d = _desc(advection=kv.KV_ADV_UPWIND)
+    buf = (ctypes.c_double * 8)()
+    assert lib.kv_krylov_vector_noalloc(ctypes.byref(d), buf, buf, buf, None) == -1
+    assert b"central" in lib.kv_last_error(None)
 
 
 def test_null_arguments_rejected(lib):
