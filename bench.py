@@ -394,7 +394,8 @@ def extras(base_np, x_np, w, kv, synth):
     and a plan of 12 grids {100^3 x4, 128^3 x4, 200^3 x2, 256^3 x2} (Gr in [1e6, 4e6], both
     spanwise boundary types) evaluated by one graph launch; a 100-step Arnoldi run at 256^3;
     Newton's method for a steady state at 64^3 (these mixed precision); and one Krylov vector of
-    the bench workload on the grid stretched by Eq (22), FP64 and mixed precision."""
+    the bench workload on the grid stretched by Eq (22), FP64 and mixed precision; and one Krylov
+    vector of the bench workload with first-order upwind advection, FP64 and mixed precision."""
     import numpy as np
     import torch
 
@@ -497,6 +498,27 @@ def extras(base_np, x_np, w, kv, synth):
     out["stretched_mixed"] = {"workload": f"{w.name} on the grid stretched by Eq (22), a = 0.12; mixed precision",
                               "value": 1.0 / t, "unit": UNIT, "ms_per_vector": t * 1e3, "rel_err_vs_fp64": err,
                               "tuning": g.tuning()}
+    del g, y64
+    torch.cuda.empty_cache()
+    # the same Krylov vector with first-order upwind advection (the descriptor's option), FP64
+    # and mixed precision (the double-float operator that reads the plus coefficients)
+    g = kv.Grid(w.nx, w.ny, w.nz, bc=w.bc, gr=w.gr, pr=w.pr, precision=kv.KV_PREC_FP64,
+                advection=kv.KV_ADV_UPWIND)
+    g.set_base_flow(torch.from_numpy(np.stack(base_np)).cuda())
+    t = timed(lambda: g.krylov_vector(x, y), reps=5)
+    out["upwind_fp64"] = {"workload": f"{w.name} with first-order upwind advection; FP64",
+                          "value": 1.0 / t, "unit": UNIT, "ms_per_vector": t * 1e3}
+    y64 = y.clone()
+    del g
+    torch.cuda.empty_cache()
+    g = kv.Grid(w.nx, w.ny, w.nz, bc=w.bc, gr=w.gr, pr=w.pr, precision=kv.KV_PREC_MIXED,
+                advection=kv.KV_ADV_UPWIND)
+    g.set_base_flow(torch.from_numpy(np.stack(base_np)).cuda())
+    t = timed(lambda: g.krylov_vector(x, y), reps=5)
+    err = (torch.linalg.vector_norm(y - y64) / torch.linalg.vector_norm(y64)).item()
+    out["upwind_mixed"] = {"workload": f"{w.name} with first-order upwind advection; mixed precision",
+                           "value": 1.0 / t, "unit": UNIT, "ms_per_vector": t * 1e3, "rel_err_vs_fp64": err,
+                           "tuning": g.tuning()}
     del g, x, y, y64
     torch.cuda.empty_cache()
     return out
@@ -505,7 +527,7 @@ def extras(base_np, x_np, w, kv, synth):
 def cpu_baselines(w, out):
     """The oracle on the host cores beside the GPU figures: the benchmark workload on all cores
     (best of 3 after a warm-up), a 100^3 workload on one core (best of 3 after a warm-up), and
-    one bounded sample each beside the Newton and stretched-grid lines (when present in out)."""
+    one bounded sample each beside the Newton, stretched-grid and upwind lines (when present in out)."""
     if "newton64" in out:  # the oracle beside the Newton line: one bounded GMRES cycle
         try:
             cmd = [sys.executable, "-m", "oracle.bench_cpu", "--newton-cycle", "20"]
@@ -527,6 +549,15 @@ def cpu_baselines(w, out):
                           f"{rc['setup_seconds']:.1f} s, not timed)"}
         except Exception as e:
             out["stretched_fp64"]["cpu_baseline"] = {"value": None, "kind": "oracle", "sample": f"failed: {e}"[:300]}
+    if "upwind_fp64" in out:  # the oracle beside the upwind line: one evaluation
+        try:
+            rc = cpu_baseline(w.name, 1, 0, timeout=120, extra=["--adv", "1"])
+            out["upwind_fp64"]["cpu_baseline"] = {
+                "value": rc["value"], "unit": UNIT, "cores": rc["cores"], "kind": "oracle",
+                "sample": f"1 FP64 oracle Krylov-vector evaluation of {w.name} with upwind advection "
+                          f"({rc['seconds']:.1f} s on {rc['cores']} host threads)"}
+        except Exception as e:
+            out["upwind_fp64"]["cpu_baseline"] = {"value": None, "kind": "oracle", "sample": f"failed: {e}"[:300]}
     try:
         r = cpu_baseline(w.name, 1, 1, best_of=3)
         r1 = cpu_baseline("cube100_cc", 1, 1, best_of=3, one_core=True)

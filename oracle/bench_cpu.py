@@ -118,6 +118,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=0)
     ap.add_argument("--newton-cycle", type=int, default=0, help="time one GMRES(m) cycle of the Newton line instead")
     ap.add_argument("--stretch", type=float, default=0.0, help="grid stretching parameter of Eq (22)")
+    ap.add_argument("--adv", type=int, default=0, help="advection scheme: 0 central, 1 first-order upwind")
     ap.add_argument("--best-of", type=int, default=1, help="report the fastest of this many timed repetitions")
     ap.add_argument("--arnoldi", type=int, default=-1, help="time Arnoldi steps from this basis index instead")
     ap.add_argument("--restart", type=int, default=20)
@@ -136,7 +137,7 @@ def main():
     base, x = synth.workload_arrays(w)
     base = np.stack(base)
     t0 = time.perf_counter()
-    o = Oracle(w.nx, w.ny, w.nz, bc=w.bc, gr=w.gr, pr=w.pr, stretch=a.stretch)
+    o = Oracle(w.nx, w.ny, w.nz, bc=w.bc, gr=w.gr, pr=w.pr, stretch=a.stretch, adv=a.adv)
     setup = time.perf_counter() - t0
     for _ in range(a.warmup):
         o.krylov_vector(base, x[0])
@@ -149,7 +150,7 @@ def main():
     dt = min(times)
     print(json.dumps({"value": a.evals / dt, "unit": "Krylov-vector evals/s", "seconds": dt, "evals": a.evals,
                       "best_of": len(times), "all_seconds": times, "warmup": a.warmup, "cores": threads(),
-                      "workload": a.workload, "stretch": a.stretch, "setup_seconds": setup, "host": host_info()}))
+                      "workload": a.workload, "stretch": a.stretch, "adv": a.adv, "setup_seconds": setup, "host": host_info()}))
 
 
 if __name__ == "__main__":
