@@ -59,6 +59,8 @@ def parse_args():
     ap.add_argument("--operator", default=None, metavar="VARIANT,PLANES",
                     help="with --single: pin the mixed path's operator (kv_set_tuning), e.g. 2,16 for the "
                          "fixed-point march with 16 planes per block, 1,32 for the double-float march")
+    ap.add_argument("--advection", choices=["central", "upwind"], default="central",
+                    help="with --single: the advection scheme of the operator (KV_ADV_*)")
     return ap.parse_args()
 
 
@@ -746,7 +748,8 @@ def run_single(args):
     w = synth.WORKLOADS[args.workload]
     base_np, x_np = synth.workload_arrays(w)
     g = kv.Grid(w.nx, w.ny, w.nz, bc=w.bc, gr=w.gr, pr=w.pr,
-                precision=kv.KV_PREC_FP64 if args.single == "fp64" else kv.KV_PREC_MIXED)
+                precision=kv.KV_PREC_FP64 if args.single == "fp64" else kv.KV_PREC_MIXED,
+                advection=kv.KV_ADV_UPWIND if args.advection == "upwind" else kv.KV_ADV_CENTRAL)
     if args.operator and args.single != "fp64":
         variant, planes = (int(v) for v in args.operator.split(","))
         g.set_tuning((32, 8), variant, (0 if variant else 32, planes))
