@@ -107,11 +107,11 @@ typedef struct {
                         uniform grid only. */
   int advection;     /* KV_ADV_CENTRAL (0, the paper's discretisation) or KV_ADV_UPWIND: first-order
                         upwind derivatives in the advection terms of Eqs (8)-(9) and of the
-                        residual of Eqs (1)-(2). Upwind takes the uniform grid only; a KV_PREC_MIXED
-                        grid then stores 12 more coefficient pairs per point, as a stretched one
-                        does, and its operator runs in double-float arithmetic (the fixed-point
-                        form is central only). kv_base_flow_gradient and kv_krylov_vector_noalloc
-                        take central advection only. */
+                        residual of Eqs (1)-(2). Upwind takes the uniform grid only. A KV_PREC_MIXED
+                        upwind grid keeps 2 B of one-sided choices per point for the fixed-point
+                        operator (cubic grids) and stores 12 more coefficient pairs per point, as a
+                        stretched one does, for the double-float operator. kv_base_flow_gradient
+                        and kv_krylov_vector_noalloc take central advection only. */
 } kv_grid_desc;
 
 typedef struct {

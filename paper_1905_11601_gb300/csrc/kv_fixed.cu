@@ -95,6 +95,45 @@ __global__ void __launch_bounds__(256) k_fx_absmax(const double* __restrict__ a,
   if ((threadIdx.x & 31) == 0 && m) atomicMax(out, m);
 }
 
+// Upwind advection: the one-sided choice of each equation along each axis at every cell (bit set:
+// backward, the selecting velocity >= 0), from the FP64 base state: bits 0-2 u (x, y, z), 3-5 v,
+// 6-8 w, 9-11 T. The selecting velocity is the base component averaged to the equation's node,
+// the 4-point sums taken in a fixed order (the two entries at t-1 along the component's axis,
+// then the two at t), as in the coefficient assembly. 0 outside the cells.
+__global__ void __launch_bounds__(256) k_fx_sel(KvGeom g, const double* __restrict__ base, size_t P,
+                                                unsigned short* __restrict__ sel) {
+  const int sy = g.X, sz = g.X * g.Y;
+  for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < P; e += (size_t)gridDim.x * blockDim.x) {
+    const int i = (int)(e % g.X), j = (int)((e / g.X) % g.Y), k = (int)(e / sz);
+    if (i < 1 || i > g.nx || j < 1 || j > g.ny || k < 1 || k > g.nz) {
+      sel[e] = 0;
+      continue;
+    }
+    const double* U = base;
+    const double* V = base + P;
+    const double* W = base + 2 * P;
+    auto s4 = [](double a, double b, double c, double d) { return ((a + b) + c) + d; };
+    unsigned int m = 0;
+    // u on the x-face (i, j, k)
+    m |= (__ldg(U + e) >= 0.0) << 0;
+    m |= (s4(__ldg(V + e - sy), __ldg(V + e + 1 - sy), __ldg(V + e), __ldg(V + e + 1)) >= 0.0) << 1;
+    m |= (s4(__ldg(W + e - sz), __ldg(W + e + 1 - sz), __ldg(W + e), __ldg(W + e + 1)) >= 0.0) << 2;
+    // v on the y-face
+    m |= (s4(__ldg(U + e - 1), __ldg(U + e - 1 + sy), __ldg(U + e), __ldg(U + e + sy)) >= 0.0) << 3;
+    m |= (__ldg(V + e) >= 0.0) << 4;
+    m |= (s4(__ldg(W + e - sz), __ldg(W + e + sy - sz), __ldg(W + e), __ldg(W + e + sy)) >= 0.0) << 5;
+    // w on the z-face
+    m |= (s4(__ldg(U + e - 1), __ldg(U + e - 1 + sz), __ldg(U + e), __ldg(U + e + sz)) >= 0.0) << 6;
+    m |= (s4(__ldg(V + e - sy), __ldg(V + e - sy + sz), __ldg(V + e), __ldg(V + e + sz)) >= 0.0) << 7;
+    m |= (__ldg(W + e) >= 0.0) << 8;
+    // T at the cell (2-point sums)
+    m |= (__ldg(U + e - 1) + __ldg(U + e) >= 0.0) << 9;
+    m |= (__ldg(V + e - sy) + __ldg(V + e) >= 0.0) << 10;
+    m |= (__ldg(W + e - sz) + __ldg(W + e) >= 0.0) << 11;
+    sel[e] = (unsigned short)m;
+  }
+}
+
 // the base state on its fixed-point grid (r0 = fx_r0(E))
 __global__ void __launch_bounds__(256) k_fx_base(const double* __restrict__ a, size_t n, int r0,
                                                  int2* __restrict__ out) {
@@ -124,10 +163,12 @@ constexpr size_t FSMEM = (size_t)4 * FVALS * sizeof(int2) + (size_t)FIN * sizeof
 static_assert(FIN / FTHREADS == 2 && (FIN + FTHREADS - 1) / FTHREADS == 3,
               "values r < 2 of a thread are input, r == 2 either, r > 2 base state");
 
+// UPW: upwind advection, every cell with the one-sided weights its selector bits choose (sel).
+template <bool UPW>
 __global__ void __launch_bounds__(FTHREADS, 2)
     k_apply_fx_march(KvGeom g, const int2* __restrict__ bfx, const double* __restrict__ x, size_t P,
                      double* __restrict__ vstar, double* __restrict__ tout, FxConst K,
-                     const unsigned int* __restrict__ xmax, int kc) {
+                     const unsigned int* __restrict__ xmax, const unsigned short* __restrict__ sel, int kc) {
   extern __shared__ int2 fst[];  // [slot][field][point]
   const int tid = threadIdx.x;
   const int half = tid / FCELLS;  // 0: u and T, 1: v and w (uniform per warp)
@@ -275,7 +316,26 @@ __global__ void __launch_bounds__(FTHREADS, 2)
       // interior weights as constants where the whole warp is interior (the weighted sums become
       // differences); the walls' weights per cell elsewhere
       const W3i I1{-3, 0, 3}, I2{1, -2, 1}, J1{-1, 0, 1};
-      if (cy == 0 && cz == 0 && x_inner)
+      if (UPW) {
+        const unsigned int b = __ldg(sel + e);
+        const W3i dx2 = fx_d2(cx), dy2 = fx_d2(cy), dz2 = fx_d2(cz);
+        if (half == 0) {
+          const long long tu = fx_eq_u(X, B, fx_u1(cy, b & 2u), dy2, fx_u1(cz, b & 4u), dz2, K.k1, fx_u1_face(b & 1u));
+          vstar[e] = i <= g.nx - 1 ? fx_to_double(tu) * fo : 0.0;
+          const double r = fx_to_double(fx_eq_t(X, B, fx_u1(cx, b & 512u), dx2, fx_u1(cy, b & 1024u), dy2,
+                                                fx_u1(cz, b & 2048u), dz2, K.k1, 12)) * fo;
+          const bool pair = g.bc == KV_BC_AA && (j == 1 || j == g.ny);
+          const double t = pair && g.tproj != KV_TPROJ_OBLIQUE ? 0.5 * r : r;
+          tout[e] = t;
+          if (pair) tout[(size_t)i + (size_t)sy * (j == 1 ? 0 : g.ny + 1) + (size_t)sz * k] = t;
+        } else {
+          const long long tv = fx_eq_v(X, B, fx_u1(cx, b & 8u), dx2, fx_u1(cz, b & 32u), dz2, K.k1, fx_u1_face(b & 16u));
+          vstar[Pz + e] = j <= g.ny - 1 ? fx_to_double(tv) * fo : 0.0;
+          const long long tw = fx_eq_w(X, B, fx_u1(cx, b & 64u), dx2, fx_u1(cy, b & 128u), dy2, K.k1,
+                                       fx_u1_face(b & 256u));
+          vstar[2 * Pz + e] = k <= g.nz - 1 ? fx_to_double(tw) * fo : 0.0;
+        }
+      } else if (cy == 0 && cz == 0 && x_inner)
         eqs(J1, I2, J1, I2, J1, I2, K.k3, 4, 3.0 * fo);
       else if (cy == 0 && cz == 0)
         eqs(fx_d1(cx), fx_d2(cx), I1, I2, I1, I2, K.k1, 12, fo);
@@ -289,19 +349,21 @@ __global__ void __launch_bounds__(FTHREADS, 2)
 
 }  // namespace
 
-// Grids the fixed-point operator serves: mixed precision, central advection, uniform and cubic
-// (one h on all axes), offsets of a packed vector within 32 bits; kv_fx_setup adds a finite base
-// state whose grid leaves the accumulators their headroom.
+// Grids the fixed-point operator serves: mixed precision, uniform and cubic (one h on all axes),
+// offsets of a packed vector within 32 bits; kv_fx_setup adds a finite base state whose grid
+// leaves the accumulators their headroom.
 bool kv_fx_eligible(const kv_grid* h) {
-  return h->d.precision == KV_PREC_MIXED && !h->str.sw && !h->g.adv && h->g.nx == h->g.ny && h->g.ny == h->g.nz &&
+  return h->d.precision == KV_PREC_MIXED && !h->str.sw && h->g.nx == h->g.ny && h->g.ny == h->g.nz &&
          4 * h->P < (size_t(1) << 31);
 }
 
 void kv_fx_free(kv_grid* h) {
   cudaFree(h->base_fx);
   cudaFree(h->fxmax);
+  cudaFree(h->fx_sel);
   h->base_fx = nullptr;
   h->fxmax = nullptr;
+  h->fx_sel = nullptr;
   h->fx_ok = false;
 }
 
@@ -312,7 +374,8 @@ kv_status kv_fx_setup(kv_grid* h) {
   if (!kv_fx_eligible(h)) return KV_OK;
   if (!h->base_fx) {
     if (cudaMalloc(&h->base_fx, 4 * h->P * sizeof(int2)) != cudaSuccess ||
-        cudaMalloc(&h->fxmax, 2 * sizeof(unsigned int)) != cudaSuccess) {
+        cudaMalloc(&h->fxmax, 2 * sizeof(unsigned int)) != cudaSuccess ||
+        (h->g.adv && cudaMalloc(&h->fx_sel, h->P * sizeof(unsigned short)) != cudaSuccess)) {
       kv_fx_free(h);
       cudaGetLastError();
       return KV_OK;  // the double-float operator stays in use
@@ -328,8 +391,10 @@ kv_status kv_fx_setup(kv_grid* h) {
   const int eb = (int)((mb >> 20) & 0x7FFu);
   if (eb == 0x7FF) return KV_OK;  // a non-finite base state: the double-float operator reports it
   // the march's shared memory (above the 48 KB default), set here, outside any stream capture
-  if (cudaFuncSetAttribute(k_apply_fx_march, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)FSMEM) !=
-      cudaSuccess) {
+  if (cudaFuncSetAttribute(k_apply_fx_march<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)FSMEM) !=
+          cudaSuccess ||
+      cudaFuncSetAttribute(k_apply_fx_march<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)FSMEM) !=
+          cudaSuccess) {
     cudaGetLastError();
     return KV_OK;  // the double-float operator stays in use
   }
@@ -344,6 +409,7 @@ kv_status kv_fx_setup(kv_grid* h) {
   K.f0 = -n / 24.0 * std::ldexp(1.0, e - 50);
   K.e = e;
   k_fx_base<<<4 * 152, 256, 0, s>>>(h->base, 4 * h->P, r0, h->base_fx);
+  if (h->g.adv) k_fx_sel<<<4 * 152, 256, 0, s>>>(h->g, h->base, h->P, h->fx_sel);
   if (cudaGetLastError() != cudaSuccess) return KV_ERR_CUDA;
   h->fxk = K;
   h->fx_ok = true;
@@ -357,5 +423,10 @@ void kv_launch_apply_fx(const kv_grid* h, const double* x, double* vstar, double
   cudaMemsetAsync(h->fxmax, 0, sizeof(unsigned int), s);
   k_fx_prepass<<<4 * 152, 256, 0, s>>>(g, x, h->P, h->fxmax, vstar, tout);
   dim3 grid((g.nx + FB_X - 1) / FB_X, (g.ny + FB_Y - 1) / FB_Y, (g.nz + kc - 1) / kc);
-  k_apply_fx_march<<<grid, FTHREADS, FSMEM, s>>>(g, h->base_fx, x, h->P, vstar, tout, h->fxk, h->fxmax, kc);
+  if (g.adv)
+    k_apply_fx_march<true><<<grid, FTHREADS, FSMEM, s>>>(g, h->base_fx, x, h->P, vstar, tout, h->fxk, h->fxmax,
+                                                         h->fx_sel, kc);
+  else
+    k_apply_fx_march<false><<<grid, FTHREADS, FSMEM, s>>>(g, h->base_fx, x, h->P, vstar, tout, h->fxk, h->fxmax,
+                                                          nullptr, kc);
 }

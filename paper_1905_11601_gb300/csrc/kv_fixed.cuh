@@ -103,6 +103,19 @@ KV_HD double fx_to_double(long long t) {
 // (-3, 0, 3), first cell next to a wall (-8, 6, 2), last cell (-2, -6, 8); second derivative in
 // units of 1/h^2: (1, -2, 1), (2, -3, 1), (1, -3, 2) (wall nodes at h/2 from the cell centres).
 KV_HD W3i fx_d1(int cls) { return cls == 0 ? W3i{-3, 0, 3} : (cls == 1 ? W3i{-8, 6, 2} : W3i{-2, -6, 8}); }
+// First-order upwind (same units): the one-sided difference towards the upstream node over the
+// node gap, backward where the selecting velocity is >= 0 (back), else forward; the gap to a wall
+// node is h/2 (first cell backward, last cell forward).
+KV_HD W3i fx_u1(int cls, bool back) {
+  if (back) return cls == 1 ? W3i{-12, 12, 0} : W3i{-6, 6, 0};
+  return cls == 2 ? W3i{0, -12, 12} : W3i{0, -6, 6};
+}
+// The face axis' weights of a velocity equation carry 4 (see the equations below): central
+// 4 x (-3, 0, 3) as the multiplier of a difference, upwind 4 x the one-sided weights (faces are
+// h apart everywhere).
+KV_HD W3i fx_u1_face(bool back) { return back ? W3i{-24, 24, 0} : W3i{0, -24, 24}; }
+KV_HD FX fx_face(int face, FX m, FX, FX p) { return fx_mul(fx_sub(p, m), face); }
+KV_HD FX fx_face(W3i w, FX m, FX c, FX p) { return fx_w3(w, m, c, p); }
 KV_HD W3i fx_d2(int cls) { return cls == 0 ? W3i{1, -2, 1} : (cls == 1 ? W3i{2, -3, 1} : W3i{1, -3, 2}); }
 KV_HD int fx_class(int t, int n) { return t == 1 ? 1 : (t == n ? 2 : 0); }
 
@@ -119,10 +132,12 @@ KV_HD int fx_class(int t, int n) { return t == 1 ? 1 : (t == n ? 2 : 0); }
 // averaged velocities, L the second-derivative weights (units 1/h^2) summed over the axes, and
 // the constants Kd_m = -24 nu n, Kd_e = -24 kappa n, Kb = -12/n on the base state's grid (K).
 // Accessors: X(f, di, dj, dk) the projected input of field f (u, v, w, T) at the offset,
-// B(f, di, dj, dk) the base state (U, V, W, Theta). face: 4 x the face axis' first-derivative
-// weight (12, or 4 with the constants K divided by 3). d1a, d2a: the derivative weights along axis
-// a at the cell (fx_d1 / fx_d2 of its wall class; constants for interior cells, so that the
-// weighted sums reduce to differences).
+// B(f, di, dj, dk) the base state (U, V, W, Theta). face: the face axis' first derivative, 4 x its
+// weights: central, an int multiplier of the difference (12, or 4 with the constants K divided by
+// 3); upwind, a W3i (fx_u1_face). d1a, d2a: the derivative weights along axis a at the cell
+// (fx_d1 / fx_d2 of its wall class, or fx_u1 with upwinding; constants for interior cells, so
+// that the weighted sums reduce to differences). With upwinding, each axis' one-sided choice is
+// the base velocity's, shared by the two advection terms that differentiate along that axis.
 struct FxK {
   FX kd_m, kd_e, kb;  // on the base state's grid
 };
@@ -134,17 +149,17 @@ struct FxConst {
   int e;      // base state grid: |values| < 2^E
 };
 
-template <class XA, class BA>
-KV_HD long long fx_eq_u(const XA& X, const BA& B, W3i d1y, W3i d2y, W3i d1z, W3i d2z, const FxK& K, int face) {
+template <class XA, class BA, class FW>
+KV_HD long long fx_eq_u(const XA& X, const BA& B, W3i d1y, W3i d2y, W3i d1z, W3i d2z, const FxK& K, FW face) {
   const FX u0 = X(0, 0, 0, 0), uxm = X(0, -1, 0, 0), uxp = X(0, 1, 0, 0), uym = X(0, 0, -1, 0),
            uyp = X(0, 0, 1, 0), uzm = X(0, 0, 0, -1), uzp = X(0, 0, 0, 1);
   const FX U0 = B(0, 0, 0, 0);
   FXAcc a, b;
   // x is the face axis: D1 = (-3, 0, 3); the own velocity carries 4 (the others are 4-point sums)
-  a.mac(U0, fx_mul(fx_sub(uxp, uxm), face));
+  a.mac(U0, fx_face(face, uxm, u0, uxp));
   b.mac(fx_sum4(B(1, 0, -1, 0), B(1, 0, 0, 0), B(1, 1, -1, 0), B(1, 1, 0, 0)), fx_w3(d1y, uym, u0, uyp));
   a.mac(fx_sum4(B(2, 0, 0, -1), B(2, 0, 0, 0), B(2, 1, 0, -1), B(2, 1, 0, 0)), fx_w3(d1z, uzm, u0, uzp));
-  b.mac(u0, fx_mul(fx_sub(B(0, 1, 0, 0), B(0, -1, 0, 0)), face));
+  b.mac(u0, fx_face(face, B(0, -1, 0, 0), U0, B(0, 1, 0, 0)));
   a.mac(fx_sum4(X(1, 0, -1, 0), X(1, 0, 0, 0), X(1, 1, -1, 0), X(1, 1, 0, 0)),
         fx_w3(d1y, B(0, 0, -1, 0), U0, B(0, 0, 1, 0)));
   b.mac(fx_sum4(X(2, 0, 0, -1), X(2, 0, 0, 0), X(2, 1, 0, -1), X(2, 1, 0, 0)),
@@ -154,18 +169,18 @@ KV_HD long long fx_eq_u(const XA& X, const BA& B, W3i d1y, W3i d2y, W3i d1z, W3i
   return fx_total(a, b);
 }
 
-template <class XA, class BA>
-KV_HD long long fx_eq_v(const XA& X, const BA& B, W3i d1x, W3i d2x, W3i d1z, W3i d2z, const FxK& K, int face) {
+template <class XA, class BA, class FW>
+KV_HD long long fx_eq_v(const XA& X, const BA& B, W3i d1x, W3i d2x, W3i d1z, W3i d2z, const FxK& K, FW face) {
   const FX v0 = X(1, 0, 0, 0), vxm = X(1, -1, 0, 0), vxp = X(1, 1, 0, 0), vym = X(1, 0, -1, 0),
            vyp = X(1, 0, 1, 0), vzm = X(1, 0, 0, -1), vzp = X(1, 0, 0, 1);
   const FX V0 = B(1, 0, 0, 0);
   FXAcc a, b;
   a.mac(fx_sum4(B(0, -1, 0, 0), B(0, 0, 0, 0), B(0, -1, 1, 0), B(0, 0, 1, 0)), fx_w3(d1x, vxm, v0, vxp));
-  b.mac(V0, fx_mul(fx_sub(vyp, vym), face));
+  b.mac(V0, fx_face(face, vym, v0, vyp));
   a.mac(fx_sum4(B(2, 0, 0, -1), B(2, 0, 0, 0), B(2, 0, 1, -1), B(2, 0, 1, 0)), fx_w3(d1z, vzm, v0, vzp));
   b.mac(fx_sum4(X(0, -1, 0, 0), X(0, 0, 0, 0), X(0, -1, 1, 0), X(0, 0, 1, 0)),
         fx_w3(d1x, B(1, -1, 0, 0), V0, B(1, 1, 0, 0)));
-  a.mac(v0, fx_mul(fx_sub(B(1, 0, 1, 0), B(1, 0, -1, 0)), face));
+  a.mac(v0, fx_face(face, B(1, 0, -1, 0), V0, B(1, 0, 1, 0)));
   b.mac(fx_sum4(X(2, 0, 0, -1), X(2, 0, 0, 0), X(2, 0, 1, -1), X(2, 0, 1, 0)),
         fx_w3(d1z, B(1, 0, 0, -1), V0, B(1, 0, 0, 1)));
   const W3i d2y{1, -2, 1};
@@ -173,20 +188,20 @@ KV_HD long long fx_eq_v(const XA& X, const BA& B, W3i d1x, W3i d2x, W3i d1z, W3i
   return fx_total(a, b);
 }
 
-template <class XA, class BA>
-KV_HD long long fx_eq_w(const XA& X, const BA& B, W3i d1x, W3i d2x, W3i d1y, W3i d2y, const FxK& K, int face) {
+template <class XA, class BA, class FW>
+KV_HD long long fx_eq_w(const XA& X, const BA& B, W3i d1x, W3i d2x, W3i d1y, W3i d2y, const FxK& K, FW face) {
   const FX w0 = X(2, 0, 0, 0), wxm = X(2, -1, 0, 0), wxp = X(2, 1, 0, 0), wym = X(2, 0, -1, 0),
            wyp = X(2, 0, 1, 0), wzm = X(2, 0, 0, -1), wzp = X(2, 0, 0, 1);
   const FX W0 = B(2, 0, 0, 0);
   FXAcc a, b;
   a.mac(fx_sum4(B(0, -1, 0, 0), B(0, 0, 0, 0), B(0, -1, 0, 1), B(0, 0, 0, 1)), fx_w3(d1x, wxm, w0, wxp));
   b.mac(fx_sum4(B(1, 0, -1, 0), B(1, 0, 0, 0), B(1, 0, -1, 1), B(1, 0, 0, 1)), fx_w3(d1y, wym, w0, wyp));
-  a.mac(W0, fx_mul(fx_sub(wzp, wzm), face));
+  a.mac(W0, fx_face(face, wzm, w0, wzp));
   b.mac(fx_sum4(X(0, -1, 0, 0), X(0, 0, 0, 0), X(0, -1, 0, 1), X(0, 0, 0, 1)),
         fx_w3(d1x, B(2, -1, 0, 0), W0, B(2, 1, 0, 0)));
   a.mac(fx_sum4(X(1, 0, -1, 0), X(1, 0, 0, 0), X(1, 0, -1, 1), X(1, 0, 0, 1)),
         fx_w3(d1y, B(2, 0, -1, 0), W0, B(2, 0, 1, 0)));
-  b.mac(w0, fx_mul(fx_sub(B(2, 0, 0, 1), B(2, 0, 0, -1)), face));
+  b.mac(w0, fx_face(face, B(2, 0, 0, -1), W0, B(2, 0, 0, 1)));
   const W3i d2z{1, -2, 1};
   a.mac(K.kd_m, fx_add(fx_add(fx_w3(d2x, wxm, w0, wxp), fx_w3(d2y, wym, w0, wyp)), fx_w3(d2z, wzm, w0, wzp)));
   b.mac(K.kb, fx_add(X(3, 0, 0, 0), X(3, 0, 0, 1)));  // buoyancy (T_k + T_k+1) / 2

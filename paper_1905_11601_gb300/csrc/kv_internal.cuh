@@ -138,6 +138,7 @@ struct kv_grid {
   // fixed-point grid, the pre-pass maxima ([0] the input's, [1] the base state's), the constants
   int2* base_fx = nullptr;               // 4P
   unsigned int* fxmax = nullptr;         // 2
+  unsigned short* fx_sel = nullptr;      // P, upwind advection: the one-sided choices per cell
   FxConst fxk{};
   bool fx_ok = false;                    // set per base flow by kv_fx_setup
   unsigned int* derr = nullptr;          // device error flag (bounded waits that expired)

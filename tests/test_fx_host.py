@@ -70,6 +70,31 @@ def test_fixed_point_equations_match_oracle(driver, tmp_path, n, bc, gr, tproj, 
         assert np.abs(g - r).max() <= TOL * m, (F, np.abs(g - r).max() / m)
 
 
+UPWIND_CASES = [(12, synth.CC, 1e6, 0, "random"), (13, synth.AA, 3e6, 1, "random"), (16, synth.AA, 3e6, 0, "smooth"),
+                (2, synth.CC, 1e6, 0, "random"), (3, synth.AA, 1e6, 1, "smooth")]
+
+
+@pytest.mark.parametrize("n,bc,gr,tproj,kind", UPWIND_CASES)
+def test_fixed_point_upwind_equations_match_oracle(driver, tmp_path, n, bc, gr, tproj, kind):
+    """The one-sided weights of the upwind reading (units of 1/(6h)), chosen per equation and axis
+    by the FP64 base velocity, against the oracle's upwind branch."""
+    pr = 0.71
+    base = np.stack(synth.base_flow(n, n, n, bc, 31))
+    x = synth.krylov_input(n, n, n, 32)[0] if kind == "random" else np.stack(synth.base_flow(n, n, n, bc, 33))
+    o = Oracle(n, n, n, bc=bc, gr=gr, pr=pr, tproj=tproj, adv=1)
+    xp = o.project_input(x)
+    ref = o.jx_raw(base, xp)
+    y = run(driver, tmp_path, n, base, xp, gr, pr, "upwind")
+    inner = (slice(1, n + 1),) * 3
+    for F in range(4):
+        r, g = ref[F][inner], y[F][inner]
+        m = np.abs(r).max()
+        assert m > 0
+        assert np.abs(g - r).max() <= TOL * m, (F, np.abs(g - r).max() / m)
+    central = Oracle(n, n, n, bc=bc, gr=gr, pr=pr, tproj=tproj).jx_raw(base, xp)
+    assert np.abs(central - ref).max() > 1e-6 * np.abs(ref).max()
+
+
 def test_grid_conversion_is_exact_where_it_should_be(driver, tmp_path):
     """A base state and an input whose values are small integers times powers of two: their
     conversions to the fixed-point grids are exact and so is every integer sum and product, which

@@ -1,7 +1,7 @@
 """GPU parity of the optional first-order upwind advection (KV_ADV_UPWIND) against the FP64
-oracle's upwind branch: every FP64 block shape and every double-float operator variant at
-ragged sizes, the Newton residual, the transpose, an autotuned mixed grid, and the refusals
-(fixed-point operator, base-flow gradient). Per-field max-abs bars as in the central tests:
+oracle's upwind branch: every FP64 block shape and every mixed operator variant (double-float
+and fixed-point) at ragged sizes, the Newton residual, the transpose, an autotuned mixed grid,
+and the refusal of the base-flow gradient. Per-field max-abs bars as in the central tests:
 1e-12 of max |y_ref_F| for FP64, 1e-9 for mixed precision."""
 import numpy as np
 import pytest
@@ -16,9 +16,13 @@ UP = 1
 
 FP64_BLOCKS = [(32, 8), (64, 4), (128, 2), (32, 4), (16, 16), (256, 1)]
 DF_VARIANTS = [(0, 32, 1), (0, 32, 2), (0, 64, 1), (0, 32, 4), (0, 64, 2), (0, 128, 1), (1, 0, 16), (1, 0, 32),
-               (1, 0, 64)]
+               (1, 0, 64), (2, 0, 8), (2, 0, 16), (2, 0, 32), (2, 0, 64)]
 CASES = [((70, 65, 67), synth.CC, 2e6, 0), ((33, 18, 20), synth.AA, 3e6, 1), ((9, 130, 12), synth.AA, 3e6, 0),
          ((37, 37, 37), synth.CC, 3.3e6, 0), ((2, 3, 2), synth.CC, 1e6, 0)]
+# the fixed-point operator (variant 2) serves cubes: ragged cubes against its tiles, and cubes
+# whose every cell touches a wall
+CUBES = [((33, 33, 33), synth.AA, 3e6, 1), ((20, 20, 20), synth.AA, 3e6, 0), ((2, 2, 2), synth.CC, 1e6, 0),
+         ((3, 3, 3), synth.AA, 1e6, 1)]
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -77,22 +81,24 @@ def test_upwind_every_fp64_block_shape_matches_oracle(n, bc, gr, tproj):
     assert np.linalg.norm(yc - y_ref) > 1e-4 * np.linalg.norm(y_ref)
 
 
-@pytest.mark.parametrize("n,bc,gr,tproj", CASES + [((128, 128, 128), synth.AA, 3e6, 0)])
-def test_upwind_every_double_float_variant_matches_oracle(n, bc, gr, tproj):
+@pytest.mark.parametrize("n,bc,gr,tproj", CASES + CUBES + [((128, 128, 128), synth.AA, 3e6, 0)])
+def test_upwind_every_mixed_operator_variant_matches_oracle(n, bc, gr, tproj):
     kv = kvmod()
     base, x, y_ref = reference(n, bc, gr, tproj)
     g = kv.Grid(*n, bc=bc, gr=gr, pr=0.71, tproj=tproj, precision=kv.KV_PREC_MIXED, advection=kv.KV_ADV_UPWIND)
     g.set_tuning(apply_block=(32, 8), df_variant=1, df_block=(0, 32))
     g.set_base_flow(torch.from_numpy(base).cuda())
     xt = torch.from_numpy(x).cuda()
+    cubic = n[0] == n[1] == n[2]
     for v, bx, by in DF_VARIANTS:
+        if v == 2 and not cubic:
+            with pytest.raises(kv.KvError):
+                g.set_tuning(apply_block=(32, 8), df_variant=v, df_block=(bx, by))
+            continue
         g.set_tuning(apply_block=(32, 8), df_variant=v, df_block=(bx, by))
         y, st = g.krylov_vector(xt, stats=True)
         assert st.device_error == 0
         check(y.cpu().numpy(), y_ref, TOLMIX, (v, bx, by))
-    # the fixed-point operator is central only, also on a cube
-    with pytest.raises(kv.KvError):
-        g.set_tuning(apply_block=(32, 8), df_variant=2, df_block=(0, 32))
 
 
 def test_upwind_autotuned_mixed_grid_matches_oracle():
@@ -101,7 +107,7 @@ def test_upwind_autotuned_mixed_grid_matches_oracle():
     base, x, y_ref = reference(n, bc, gr, 0)
     g = kv.Grid(*n, bc=bc, gr=gr, pr=0.71, precision=kv.KV_PREC_MIXED, advection=kv.KV_ADV_UPWIND)
     g.set_base_flow(torch.from_numpy(base).cuda())  # the autotuner runs here
-    assert g.tuning()["df_variant"] in (0, 1)
+    assert g.tuning()["df_variant"] in (0, 1, 2)
     check(g.krylov_vector(torch.from_numpy(x).cuda()).cpu().numpy(), y_ref, TOLMIX, "autotuned")
 
 
