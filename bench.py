@@ -708,6 +708,33 @@ def run_ours(args):
         ph = out["phases"].get(k)
         if ph and ph["ms_per_step"] > 0:
             ph["hbm_frac"] = byts / (ph["ms_per_step"] / 1e3) / 1e9 / hbm_peak
+    # The whole step against its bounds: the sum over phases of the time at the bound, over the
+    # measured step time. Algorithmic work: the Krylov vector's streaming steps move 13 fields
+    # (read x and the base state, write y and p); the Poisson solves are 12 N^4 flops per solve
+    # for each of the 6 BF16 slice products, at the sustained tensor rate; the Gram-Schmidt
+    # sweeps stream the basis and w as they run (first sweep nq + 1 vectors, fused sweep nq + 2,
+    # third sweep nq + 2 in the steps that take the second update, else the 2 of the
+    # normalisation). The refinement residual and the other intermediates are implementation
+    # traffic, with no time at the bound.
+    bf16, bf16_src = bf16_peak()
+    tpd = out["phases"].get("tpd", {})
+    sweeps = tpd.get("launches_per_step", 12.0) / 6.0
+    su = mx["second_updates"]
+    f2 = su[0] / su[1] if su[1] else 0.0
+    t_min = {"operator + divergence + correction (HBM, 13 fields x 8 B x N^3)": 13 * 8.0 * n3 / (hbm_peak * 1e9),
+             "Poisson contractions (tensor, 6 x 12 N^4 flops x sweeps)":
+                 6 * 12.0 * w.nx * w.ny * w.nz * (w.nx + w.ny + w.nz) / 3.0 * sweeps / (bf16 * 1e12),
+             "Gram-Schmidt sweeps (HBM, basis and w streams)":
+                 8.0 * L * ((nqm + 1) + (nqm + 2) + f2 * (nqm + 2) + (1 - f2) * 2) / (hbm_peak * 1e9)}
+    t_sum = sum(t_min.values())
+    kv_min = t_sum - t_min["Gram-Schmidt sweeps (HBM, basis and w streams)"]
+    out["roofline_step"] = {
+        "frac": t_sum / (out["ms_per_step"] / 1e3),
+        "t_min_ms": {k: v * 1e3 for k, v in t_min.items()}, "t_measured_ms": out["ms_per_step"],
+        "krylov_vector_frac": kv_min / (mx["kv_ms"] / 1e3), "krylov_vector_ms": mx["kv_ms"],
+        "peaks": {"hbm_gbs": hbm_peak, "bf16_tflops": bf16, "source": bf16_src},
+        "what": "sum over phases of (algorithmic work / peak) over the measured time; the Krylov vector's "
+                "intermediates (v*, b, phi and the refinement residual) count as implementation traffic"}
     out["fp64_plain"] = {"value": fp["value"], "ms_per_step": fp["ms"] / args.steps,
                          "krylov_vector_ms": fp["kv_ms"],
                          "roofline": roofline(fp["phases"], w, "fp64", args.steps, fp["nq"]),
