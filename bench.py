@@ -639,24 +639,31 @@ def run_ours(args):
     # End to end through the host-buffer entry points (pinned host memory, every vector's copies
     # inside the timed region): the streamed form (copies overlapping the evaluations) is the
     # e2e value; one kv_krylov_vector_host call per vector is reported beside it.
+    # (one untimed pass over every buffer first; the median of three timed passes is the value,
+    # all three are reported: the host link's rate varies with what else the host is doing)
     ne = args.e2e_steps
     Xh = torch.from_numpy(np.stack([x_np[0]] * ne).reshape(ne, -1)).pin_memory()
     Yh = torch.empty_like(Xh).pin_memory()
-    g.krylov_vector_host_stream(Xh[:2], Yh[:2])
-    torch.cuda.synchronize()
-    if dist:
-        dist.barrier()
-    t0 = time.perf_counter()
     g.krylov_vector_host_stream(Xh, Yh)
-    e2e_s = max_over_ranks(time.perf_counter() - t0, dist)
-    e2e_value = whole_job_rate(ne, world, e2e_s)
+    torch.cuda.synchronize()
+    e2e_runs = []
+    for _ in range(3):
+        if dist:
+            dist.barrier()
+        t0 = time.perf_counter()
+        g.krylov_vector_host_stream(Xh, Yh)
+        e2e_runs.append(whole_job_rate(ne, world, max_over_ranks(time.perf_counter() - t0, dist)))
+    e2e_value = sorted(e2e_runs)[1]
     xh, yh = Xh[0], Yh[0]
     g.krylov_vector_host(xh, yh)
     torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    for _ in range(ne):
-        g.krylov_vector_host(xh, yh)
-    e2e_single = whole_job_rate(ne, world, max_over_ranks(time.perf_counter() - t0, dist))
+    single_runs = []
+    for _ in range(3):
+        t0 = time.perf_counter()
+        for _ in range(ne):
+            g.krylov_vector_host(xh, yh)
+        single_runs.append(whole_job_rate(ne, world, max_over_ranks(time.perf_counter() - t0, dist)))
+    e2e_single = sorted(single_runs)[1]
     vec_bytes = xh.numel() * 8
 
     mx = results["mixed"]
@@ -679,7 +686,8 @@ def run_ours(args):
                    "d2h_bytes_per_step": vec_bytes,
                    "path": f"kv_krylov_vector_host_stream over {ne} vectors, mixed precision (pinned host X and Y; "
                            f"copy-in of the next and copy-out of the previous vector overlap each evaluation)",
-                   "single_call_value": e2e_single},
+                   "single_call_value": e2e_single, "runs": e2e_runs, "single_call_runs": single_runs,
+                   "statistic": "median of 3 timed passes after one untimed pass"},
            "gpu_launches": launches, "roofline": roof, "clocks": mx["clocks"], "tuning": mx["g"].tuning()}
     if not args.no_extras:
         out.update(extras(base_np, x_np, w, kv, synth))
