@@ -241,6 +241,25 @@ const char* kv_plan_last_error(kv_plan_handle p);
    KV_PREC_MIXED on both the FP64 and FP32 pipes) is a sweep of its own. */
 kv_status kv_arnoldi_step(kv_handle h, double* V, int j, double* h_col);
 
+/* m Arnoldi steps in one call (Section 3.1; the same basis and Hessenberg matrix as m calls of
+   kv_arnoldi_step with classical Gram-Schmidt applied twice, up to rounding), with the second
+   projection of each new vector deferred to the next step, where it shares that step's sweeps
+   over the basis (delayed classical Gram-Schmidt, after Swirydowicz et al., "Low
+   synchronization Gram-Schmidt and generalized minimal residual algorithms", 2021): two sweeps
+   over the basis per step instead of two to three. V holds at least j0 + m + 1 packed vectors
+   (device), V_0..V_{j0} orthonormal on entry; on return V_0..V_{j0+m} are orthonormal. The
+   Arnoldi operator is applied to each new vector before its second projection and
+   normalisation (A is linear; the corrections use the Arnoldi relation of the final columns).
+   H: HOST, column-major, leading dimension ldh >= j0 + m + 1. Columns 0..j0-1 (rows 0..c+1)
+   are read: the Hessenberg matrix of the basis V_0..V_{j0} (needed by the deferred corrections);
+   columns j0..j0+m-1 (rows 0..c+1) are written. Requires j0 >= 0, m >= 1 and
+   j0 + m <= 24 (else KV_ERR_ARG; larger bases: kv_arnoldi_step). Synchronises the stream once, at
+   the end. KV_PREC_MIXED: the sweeps' arithmetic as kv_arnoldi_step's double-float sweeps (FP64
+   for the first basis vectors of each sweep, double-float for the rest); a vector with an entry
+   of magnitude >= 2^48, NaN or Inf, or one in the span of the basis, gives KV_ERR_ARG (V and H
+   undefined). While the call runs, V_{j+1} holds intermediate vectors. */
+kv_status kv_arnoldi_run(kv_handle h, double* V, int j0, int m, double* H, int ldh);
+
 /* Transpose of the Krylov map: z = A^T y with A = (Pi_v (+) P_T) J P_BC (the adjoint eigenvalue
    problem of Eq (10) uses it). With the orthogonal reading of Eq (21) the three projections are
    symmetric, so A^T = P_BC J^T (Pi_v (+) P_T); J^T is applied from the same assembled

@@ -1033,6 +1033,89 @@ kv_status kv_arnoldi_step(kv_handle h, double* V, int j, double* h_col) {
   return KV_OK;
 }
 
+kv_status kv_arnoldi_run(kv_handle h, double* V, int j0, int m, double* H, int ldh) {
+  if (!h) return KV_ERR_ARG;
+  if (!V || !H || j0 < 0 || m < 1 || j0 + m > kv_dcgs_max() || ldh < j0 + m + 1)
+    return fail(h, KV_ERR_ARG, "kv_arnoldi_run: bad argument (j0 >= 0, m >= 1, j0 + m <= " +
+                                   std::to_string(kv_dcgs_max()) + ", ldh >= j0 + m + 1)");
+  const size_t L = 4 * h->P;
+  const int J = j0 + m, ldd = J + 1;
+  const size_t need_p = (size_t)(2 * J + 3) * kv_reduce_blocks();
+  if (h->partials_cap < need_p) {
+    cudaFree(h->partials);
+    h->partials = nullptr;
+    h->partials_cap = 0;
+    kv_status s = dalloc(h, &h->partials, need_p);
+    if (s != KV_OK) return s;
+    h->partials_cap = need_p;
+  }
+  // device scratch: the inner products (2J + 3), the Hessenberg matrix (ldd x J, column-major),
+  // the update coefficients (2J + 3) and an error flag
+  const size_t n_dots = 2 * (size_t)J + 3, n_h = (size_t)ldd * J, n_c = 2 * (size_t)J + 3;
+  const size_t need_h = n_dots + n_h + n_c + 1;
+  if (h->hdev_cap < need_h) {
+    cudaFree(h->hdev);
+    h->hdev = nullptr;
+    h->hdev_cap = 0;
+    kv_status s = dalloc(h, &h->hdev, need_h);
+    if (s != KV_OK) return s;
+    h->hdev_cap = need_h;
+  }
+  double* dots = h->hdev;
+  double* Hd = dots + n_dots;
+  double* coef = Hd + n_h;
+  int* err = reinterpret_cast<int*>(coef + n_c);
+  // the columns of H before the run (those of the existing basis) go to the device; the
+  // corrections of the deferred projections use them
+  std::vector<double> hd(n_h, 0.0);
+  for (int c = 0; c < j0; ++c)
+    for (int r = 0; r <= c + 1; ++r) hd[r + (size_t)ldd * c] = H[r + (size_t)ldh * c];
+  KV_CHECK_CUDA(h, cudaMemcpyAsync(Hd, hd.data(), n_h * sizeof(double), cudaMemcpyHostToDevice, h->s));
+  KV_CHECK_CUDA(h, cudaMemsetAsync(err, 0, sizeof(int), h->s));
+  const int df = h->d.precision == KV_PREC_MIXED;
+  for (int j = j0; j < J; ++j) {
+    double* u = V + (size_t)j * L;
+    double* w = V + (size_t)(j + 1) * L;
+    kv_status s = kv_krylov_vector(h, u, w, nullptr, nullptr);  // w = A u_j (u_j provisional)
+    if (s != KV_OK) return s;
+    {
+      KvPhase ph(h, KV_PH_GS_DOTS, 2);
+      kv_launch_dots2(V, L, j, u, w, L, h->partials, dots, df, h->s);
+    }
+    {
+      KvPhase ph(h, KV_PH_ARNOLDI, 1);
+      kv_launch_dcgs_coef(dots, Hd, ldd, j, j == j0, 0, coef, err, h->s);
+    }
+    {
+      KvPhase ph(h, KV_PH_GS_UPDATE, 1);
+      kv_launch_update2(V, L, j, coef, u, w, L, j != j0, 1, df, h->s);
+    }
+  }
+  {
+    // the last vector's deferred second projection and its normalisation
+    KvPhase ph(h, KV_PH_ARNOLDI, 4);
+    double* u = V + (size_t)J * L;
+    kv_launch_dots_norm(V, L, J, u, L, h->partials, dots, dots + J, df, h->s);
+    kv_launch_dcgs_coef(dots, Hd, ldd, J, 0, 1, coef, err, h->s);
+    kv_launch_update2(V, L, J, coef, u, nullptr, L, 1, 0, df, h->s);
+  }
+  kv_status s = check_launch(h, "arnoldi run");
+  if (s != KV_OK) return s;
+  int herr = 0;
+  KV_CHECK_CUDA(h, cudaMemcpyAsync(hd.data(), Hd, n_h * sizeof(double), cudaMemcpyDeviceToHost, h->s));
+  KV_CHECK_CUDA(h, cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, h->s));
+  KV_CHECK_CUDA(h, cudaStreamSynchronize(h->s));
+  if (herr)
+    return fail(h, KV_ERR_ARG,
+                "kv_arnoldi_run: a vector of the run has entries outside the Gram-Schmidt sweeps' range or "
+                "lies in the span of the basis; V and H are undefined");
+  for (int c = j0; c < J; ++c)
+    for (int r = 0; r <= c + 1; ++r) H[r + (size_t)ldh * c] = hd[r + (size_t)ldd * c];
+  h->gs_steps += m;
+  h->gs_second += m;
+  return KV_OK;
+}
+
 kv_status kv_newton_residual(kv_handle h, const double* S, double* F, double* norm_out) {
   if (!h) return KV_ERR_ARG;
   if (!S) return fail(h, KV_ERR_ARG, "kv_newton_residual: S is NULL");

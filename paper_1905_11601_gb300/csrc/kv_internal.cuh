@@ -313,6 +313,26 @@ void kv_launch_poisson(kv_grid* h, double* b, double* phi, cudaStream_t s);
 // partial sums of <V_q, w> for q = 0..nq-1 (vectors of length len, stride between V_q = ld),
 // then out[q] = sum of partials. If accumulate, out[q] += result.
 int kv_reduce_blocks();
+// out[r] = sum of the nb block partials of row r (rows laid out kv_reduce_blocks() apart)
+void kv_launch_finalize(const double* partials, int rows, int nb, double* out, cudaStream_t s);
+// kv_dcgs.cu: the sweeps of the delayed classical Gram-Schmidt (kv_arnoldi_run).
+// Inner products of the basis V_0..V_{q-1} with two vectors u and w, and u.w, u.u, w.w:
+// out[0, q) = <V, u>, out[q, 2q) = <V, w>, out[2q] = <u, w>, out[2q + 1] = ||u||^2 (NaN if a
+// double-float sweep meets an entry of u or w outside its range), out[2q + 2] = ||w||^2.
+// q <= kv_dcgs_max() - 1; partials: (2q + 3) kv_reduce_blocks() doubles.
+int kv_dcgs_max();
+void kv_launch_dots2(const double* V, size_t ld, int q, const double* u, const double* w, size_t len,
+                     double* partials, double* out, int df, cudaStream_t s);
+// The coefficients of a step from those inner products and the Hessenberg matrix Hd (device,
+// column-major, leading dimension ldh): column j-1 finalised (unless first), column j
+// provisional; coef laid out for kv_launch_update2. final_only: finalise column j-1 from
+// a = out[0, j), ||u||^2 = out[j] (the run's last vector), no w. err: set on a failure.
+void kv_launch_dcgs_coef(const double* dots, double* Hd, int ldh, int j, int first, int final_only, double* coef,
+                         int* err, cudaStream_t s);
+// u <- coef[0] u + sum_q coef[1 + q] V_q (unless first), w <- coef[q + 1] w + coef[q + 2] u +
+// sum_r coef[q + 3 + r] V_r (unless no_w), both from the entering u.
+void kv_launch_update2(const double* V, size_t ld, int q, const double* coef, double* u, double* w, size_t len,
+                       int write_u, int write_w, int df, cudaStream_t s);
 void kv_launch_multidot(const double* V, size_t ld, int nq, const double* w, size_t len, double* partials,
                         double* out, int accumulate, cudaStream_t s);
 // w -= sum_q c[q] V_q

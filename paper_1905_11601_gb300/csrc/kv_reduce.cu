@@ -486,6 +486,11 @@ int aligned16(const double* V, size_t ld, const double* w) {
 }  // namespace
 
 int kv_reduce_blocks() { return RB; }
+
+// out[r] = sum of partials[r * RB + b] over the nb blocks, r < rows (fixed order)
+void kv_launch_finalize(const double* partials, int rows, int nb, double* out, cudaStream_t s) {
+  k_finalize<<<rows, RT, 0, s>>>(partials, nb, out, 0);
+}
 int kv_fused_cgs_max() { return QF; }
 
 void kv_launch_dots_norm(const double* V, size_t ld, int nq, const double* w, size_t len, double* partials,

@@ -24,7 +24,8 @@ _STATUS = {0: "KV_OK", -1: "KV_ERR_ARG", -2: "KV_ERR_CUDA", -3: "KV_ERR_NOT_CONV
 
 # every symbol include/kv.h declares
 EXPORTS = ("kv_create_grid", "kv_destroy_grid", "kv_set_stream", "kv_field_len", "kv_set_base_flow",
-           "kv_krylov_vector", "kv_krylov_vector_host", "kv_arnoldi_step", "kv_newton_residual", "kv_last_error",
+           "kv_krylov_vector", "kv_krylov_vector_host", "kv_arnoldi_step", "kv_arnoldi_run", "kv_newton_residual",
+           "kv_last_error",
            "kv_profile_enable", "kv_profile_get", "kv_krylov_vector_noalloc", "kv_krylov_vector_adjoint",
            "kv_base_flow_gradient", "kv_krylov_vector_batch", "kv_plan_create", "kv_plan_add", "kv_plan_launch",
            "kv_plan_destroy", "kv_plan_last_error", "kv_selftest_wait_timeout", "kv_tuning",
@@ -125,6 +126,7 @@ def load_library(path: str = LIB_PATH):
     lib.kv_krylov_vector.argtypes = [H, D, D, D, ctypes.POINTER(Stats)]
     lib.kv_krylov_vector_host.argtypes = [H, D, D, ctypes.POINTER(Stats)]
     lib.kv_arnoldi_step.argtypes = [H, D, ctypes.c_int, ctypes.POINTER(ctypes.c_double)]
+    lib.kv_arnoldi_run.argtypes = [H, D, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_double), ctypes.c_int]
     lib.kv_newton_residual.argtypes = [H, D, D, ctypes.POINTER(ctypes.c_double)]
     lib.kv_profile_enable.argtypes = [H, ctypes.c_int]
     lib.kv_profile_get.argtypes = [H, ctypes.c_int, ctypes.POINTER(ctypes.c_double),
@@ -369,6 +371,23 @@ class Grid:
         self._check(self.lib.kv_combine(self.h, _dev_ptr(V, self.torch, "V", len(c) * L), len(c),
                                         c.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
                                         _dev_ptr(y, self.torch, "y", L)))
+
+    def arnoldi_run(self, V, j0, m, H=None):
+        """kv_arnoldi_run: m Arnoldi steps from the orthonormal V[0..j0] (delayed classical
+        Gram-Schmidt). H: the Hessenberg matrix so far (at least j0 columns used), or None when
+        j0 == 0. Returns the (j0 + m + 1) x (j0 + m) Hessenberg matrix (numpy)."""
+        import numpy as np
+
+        self._sync_stream()
+        J = j0 + m
+        Hf = np.zeros((J + 1, J), order="F")
+        if H is not None and j0 > 0:
+            H = np.asarray(H, dtype=np.float64)
+            Hf[: min(H.shape[0], J + 1), :j0] = H[: J + 1, :j0]
+        L = 4 * self.field_len
+        self._check(self.lib.kv_arnoldi_run(self.h, _dev_ptr(V, self.torch, "V", (J + 1) * L), j0, m,
+                                            Hf.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), J + 1))
+        return np.ascontiguousarray(Hf)
 
     def arnoldi_step(self, V, j):
         self._sync_stream()

@@ -75,6 +75,7 @@ def test_null_arguments_rejected(lib):
     assert lib.kv_destroy_grid(None) == 0
     assert lib.kv_krylov_vector(None, None, None, None, None) == -1
     assert lib.kv_arnoldi_step(None, None, 0, None) == -1
+    assert lib.kv_arnoldi_run(None, None, 0, 1, None, 2) == -1
     assert lib.kv_newton_residual(None, None, None, None) == -1
     assert lib.kv_set_base_flow(None, None, None, None, None) == -1
     assert lib.kv_set_base_flow_packed(None, None) == -1
