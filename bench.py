@@ -53,9 +53,11 @@ def parse_args():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the 16-vector block and the 12-grid plan measurements")
-    ap.add_argument("--single", choices=["fp64", "mixed", "mixed-arnoldi", "mixed-newton"], default=None,
-                    help="profiling case: two untimed Krylov-vector evaluations (or 8 Arnoldi steps, or two "
-                         "Newton corrections at 64^3 with one GMRES(30) cycle each), no JSON line")
+    ap.add_argument("--single", choices=["fp64", "mixed", "mixed-arnoldi", "mixed-arnoldi-run", "mixed-newton"],
+                    default=None,
+                    help="profiling case: two untimed Krylov-vector evaluations (or 8 Arnoldi steps, step by step "
+                         "or as one kv_arnoldi_run, or two Newton corrections at 64^3 with one GMRES(30) cycle "
+                         "each), no JSON line")
     ap.add_argument("--operator", default=None, metavar="VARIANT,PLANES",
                     help="with --single: pin the mixed path's operator (kv_set_tuning), e.g. 2,16 for the "
                          "fixed-point march with 16 planes per block, 1,32 for the double-float march")
@@ -822,11 +824,14 @@ def run_single(args):
     x = torch.from_numpy(x_np[0]).cuda()
     y, st = g.krylov_vector(x, stats=True)  # statistics for the line printed below
     y = g.krylov_vector(x)                   # the evaluation a profiler captures (no statistics)
-    if args.single == "mixed-arnoldi":
+    if args.single in ("mixed-arnoldi", "mixed-arnoldi-run"):
         V = torch.zeros((9, 4) + g.shape, dtype=torch.float64, device="cuda")
         V[0] = y / torch.linalg.vector_norm(y)
-        for j in range(8):
-            g.arnoldi_step(V, j)
+        if args.single == "mixed-arnoldi-run":
+            g.arnoldi_run(V, 0, 8)
+        else:
+            for j in range(8):
+                g.arnoldi_step(V, j)
     torch.cuda.synchronize()
     print(f"single {args.single} {w.name}: rel_div {st.rel_div:.2e} device_error {st.device_error}")
 
