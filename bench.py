@@ -234,24 +234,38 @@ def whole_job_rate(units_per_rank, world, seconds_max):
     return world * units_per_rank / seconds_max
 
 
-def arnoldi_run(g, V, m, steps, warmup, dist, clocks_index=None):
-    """Times `steps` Arnoldi steps (after `warmup`) on the current stream; restart every m."""
+def arnoldi_run(g, V, m, steps, warmup, dist, clocks_index=None, delayed=True):
+    """Times `steps` Arnoldi steps (after `warmup`) on the current stream; restart every m.
+    delayed: the steps between restarts as one kv_arnoldi_run call (delayed classical
+    Gram-Schmidt, one synchronisation per call); else one kv_arnoldi_step call per step."""
+    import numpy as np
     import torch
 
-    state = {"j": 0, "nq": []}
+    state = {"j": 0, "nq": [], "runs": 0}
+    H = np.zeros((m + 1, m))
 
-    def step():
-        j = state["j"]
-        if j == m:  # restart the basis from the last vector
-            V[0].copy_(V[m])
-            j = 0
-        g.arnoldi_step(V, j)
-        state["nq"].append(j + 1)
-        state["j"] = j + 1
+    def run_steps(n):
+        left = n
+        while left > 0:
+            j = state["j"]
+            if j == m:  # restart the basis from the last vector
+                V[0].copy_(V[m])
+                j = 0
+            k = min(left, m - j)
+            if delayed:
+                Hn = g.arnoldi_run(V, j, k, H)
+                H[: j + k + 1, : j + k] = Hn
+            else:
+                for jj in range(j, j + k):
+                    H[: jj + 2, jj] = g.arnoldi_step(V, jj)
+            state["nq"].extend(range(j + 1, j + k + 1))
+            state["runs"] += 1
+            state["j"] = j + k
+            left -= k
 
-    for _ in range(warmup):
-        step()
+    run_steps(warmup)
     state["nq"].clear()
+    state["runs"] = 0
     stream = torch.cuda.current_stream()
     torch.cuda.synchronize()
     if dist:
@@ -261,8 +275,7 @@ def arnoldi_run(g, V, m, steps, warmup, dist, clocks_index=None):
     j0 = state["j"]
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
-    for _ in range(steps):
-        step()
+    run_steps(steps)
     e1.record(stream)
     torch.cuda.synchronize()
     if dist:
@@ -273,11 +286,11 @@ def arnoldi_run(g, V, m, steps, warmup, dist, clocks_index=None):
     # phase breakdown from a second pass over the same basis sizes with the library's per-phase
     # CUDA events on (kept out of the timed region above)
     nq_timed = list(state["nq"])
+    runs = state["runs"]
     state["nq"].clear()
     state["j"] = j0
     g.profile_enable(True)
-    for _ in range(steps):
-        step()
+    run_steps(steps)
     torch.cuda.synchronize()
     prof = g.profile()
     counts = g.arnoldi_counts()  # (fused steps, of them with the second update) of this pass
@@ -287,7 +300,7 @@ def arnoldi_run(g, V, m, steps, warmup, dist, clocks_index=None):
     for p in phases.values():
         p["share"] = p["ms"] / total if total else None
     assert state["nq"] == nq_timed
-    return ms, phases, clk, nq_timed, counts
+    return ms, phases, clk, nq_timed, counts, runs
 
 
 def roofline(phases, w, precision, steps, nqs=(), tuning=None):
@@ -343,16 +356,25 @@ def roofline(phases, w, precision, steps, nqs=(), tuning=None):
                                f"DRAM bytes per launch, about 2.7x the algorithmic bytes), to keep the FP64-accurate "
                                f"operator off GB300's FP64 pipe"}
     if dom in ("gs_update", "gs_dots", "arnoldi") and nqs:
-        # streams per launch: the first sweep reads nq + 1 vectors; the fused sweep and the third
-        # sweep read nq + 1 and write 1
-        per = [(nq + 1) if dom == "gs_dots" else (nq + 2) for nq in nqs]
+        # The delayed classical Gram-Schmidt (kv_arnoldi_run): per step (basis size nq after it),
+        # the inner-product sweep streams nq + 1 vectors (the nq - 1 final ones, the provisional
+        # vector and its image) and the update sweep reads nq + 1 and writes 2; per run, the last
+        # vector's two sweeps stream (J + 1) + (J + 2) vectors, J the run's final basis size.
+        ends = [nq for i, nq in enumerate(nqs) if i + 1 == len(nqs) or nqs[i + 1] <= nq]
+        if dom == "arnoldi":
+            units = L * sum((J + 1) + (J + 2) for J in ends) / len(nqs)
+            byts = 8.0 * units * len(nqs)
+            ach = byts / (phases[dom]["ms"] / 1e3) / 1e9
+            return {"kernel": "k_dcgs_coef + the last vector's sweeps (k_dots_df, k_update2)", "bound": "hbm",
+                    "achieved": ach, "peak": hbm_peak, "unit": "GB/s", "frac": ach / hbm_peak, "traffic": None,
+                    "peak_source": hbm_src,
+                    "algorithmic": "(J + 1) + (J + 2) vectors x 8 B per entry per run, J the run's basis size"}
+        per = [(nq + 1) if dom == "gs_dots" else (nq + 3) for nq in nqs]
         units = L * sum(per) / len(per)
-        kern = {"gs_dots": "k_dots", "gs_update": "k_update_dot", "arnoldi": "k_update_small_scale"}[dom]
-        if precision == "fp64" and dom != "arnoldi":
-            # per element: first sweep nq + 1 multiply-adds (inner products and ||w||^2); fused sweep
-            # 2 nq + 1 (update, second-pass inner products, ||w||^2); FP64
-            fl = [(nq + 1) if dom == "gs_dots" else (2 * nq + 1) for nq in nqs]
-            flops = 2.0 * L * sum(fl)
+        kern = {"gs_dots": "k_dots2", "gs_update": "k_update2"}[dom]
+        if precision == "fp64":
+            # per entry and step: 2 (nq - 1) + 3 multiply-adds in either sweep, FP64
+            flops = 2.0 * L * sum(2 * nq + 1 for nq in nqs)
             ach = flops / (phases[dom]["ms"] / 1e3) / 1e12
             return {"kernel": kern + " (FP64 Gram-Schmidt sweep)", "bound": "alu", "achieved": ach,
                     "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": ach / FP64_PEAK_TFLOPS,
@@ -361,13 +383,12 @@ def roofline(phases, w, precision, steps, nqs=(), tuning=None):
                                    f"mean nq {sum(nqs) / len(nqs):.1f}"}
         byts = 8.0 * L * sum(per)
         ach = byts / (phases[dom]["ms"] / 1e3) / 1e9
-        name = {"gs_dots": "k_dots_df (Gram-Schmidt inner products, double-float)",
-                "gs_update": "k_update_dot_df (update fused with second-pass inner products, double-float)",
-                "arnoldi": "k_update_small_scale (third sweep fused with the normalisation)"}[dom]
+        name = {"gs_dots": "k_dots2 (inner products of the basis with the provisional vector and its image, "
+                           "double-float and FP64)",
+                "gs_update": "k_update2 (final vector and next provisional vector, double-float and FP64)"}[dom]
         return {"kernel": name, "bound": "hbm", "achieved": ach, "peak": hbm_peak, "unit": "GB/s",
-                "frac": ach / hbm_peak, "traffic": traffic_for(kern + ("_df" if dom != "arnoldi" else ""), units),
-                "peak_source": hbm_src,
-                "algorithmic": f"(nq + 1) or (nq + 2) vectors x 8 B per entry per launch, "
+                "frac": ach / hbm_peak, "traffic": traffic_for(kern, units), "peak_source": hbm_src,
+                "algorithmic": f"(nq + 1) or (nq + 3) vectors x 8 B per entry per launch, "
                                f"mean nq {sum(nqs) / len(nqs):.1f}"}
     # b = D v*: read 3 fields, write 1; v = v* - G phi: read v* (3) and phi (1), write 3; residual:
     # read b and phi, write three BF16 slices
@@ -454,11 +475,12 @@ def extras(base_np, x_np, w, kv, synth):
     Vm = V[:14].reshape(14, -1)
     orth = (Vm @ Vm.T - torch.eye(14, dtype=torch.float64, device="cuda")).abs().max().item()
     ts, tr = sorted(t_step)[1], sorted(t_run)[1]
-    out["arnoldi_run"] = {"workload": f"{w.name}, 10 Arnoldi steps at basis sizes 4..13, mixed precision",
-                          "value": 1.0 / tr, "unit": "Arnoldi steps/s", "ms_per_step": tr * 1e3,
-                          "stepwise_ms_per_step": ts * 1e3, "orthogonality": orth,
-                          "what": "kv_arnoldi_run (delayed classical Gram-Schmidt) against the same steps by "
-                                  "kv_arnoldi_step; median of 3"}
+    out["arnoldi_stepwise"] = {"workload": f"{w.name}, 10 Arnoldi steps at basis sizes 4..13, mixed precision",
+                               "value": 1.0 / ts, "unit": "Arnoldi steps/s", "ms_per_step": ts * 1e3,
+                               "delayed_ms_per_step": tr * 1e3, "orthogonality_delayed": orth,
+                               "what": "the headline's steps one kv_arnoldi_step call each (classical Gram-Schmidt "
+                                       "with the measured second pass, one synchronisation per step) beside one "
+                                       "kv_arnoldi_run over the same steps; median of 3"}
     del V, Vm, V0, g
     torch.cuda.empty_cache()
     # a 100-vector Arnoldi run at 256^3 (a 55 GB FP64 basis), mixed precision
@@ -649,7 +671,7 @@ def run_ours(args):
         V[0] = y0 / torch.linalg.vector_norm(y0)
         del y0
         g.guard(reset=True)
-        ms, phases, clk, nqs, (steps_seen, second) = arnoldi_run(
+        ms, phases, clk, nqs, (steps_seen, second), runs = arnoldi_run(
             g, V, m, args.steps, args.warmup, dist, clocks_index=local if (rank == 0 and prec == "mixed") else None)
         # the device-side SIMPLE test of every Krylov vector of the run (warm-up, timed and
         # phase-timing passes), read after the timed region
@@ -660,7 +682,7 @@ def run_ours(args):
         del yk
         results[prec] = {"g": g, "ms": ms, "phases": phases, "clocks": clk, "err": err, "nq": nqs,
                          "rel_div": st.rel_div, "value": whole_job_rate(args.steps, world, ms / 1000.0),
-                         "guard": guard, "second_updates": [second, steps_seen], "kv_ms": kv_ms}
+                         "guard": guard, "second_updates": [second, steps_seen], "kv_ms": kv_ms, "runs": runs}
         del V
         if prec == "fp64":
             del g
@@ -711,9 +733,10 @@ def run_ours(args):
            "scaling": "weak", "vs_baseline": None, "dtype": DTYPE_MIXED,
            "data": "synthetic (seeded base flow and vectors)", "config": workload_desc(w, m, "mixed"),
            "impl": "ours",
-           "step": "one Arnoldi step = one Krylov-vector evaluation + classical Gram-Schmidt (second update when "
-                   "measured above rounding) + normalisation; value = steps/s = Krylov vectors/s including their "
-                   "orthogonalisation",
+           "step": "one Arnoldi step = one Krylov-vector evaluation + classical Gram-Schmidt applied twice, the "
+                   "second projection and the normalisation of each new vector deferred to the next step "
+                   "(kv_arnoldi_run over the steps between restarts, one synchronisation per call); value = "
+                   "steps/s = Krylov vectors/s including their orthogonalisation",
            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": vec_bytes,
                    "d2h_bytes_per_step": vec_bytes,
                    "path": f"kv_krylov_vector_host_stream over {ne} vectors, mixed precision (pinned host X and Y; "
@@ -730,7 +753,8 @@ def run_ours(args):
                                note="device-side SIMPLE test (max|Dv| h_min / max|v|) of every Krylov vector in the "
                                     "mixed run, timed steps included; read after the timed region")
     out["second_gs_update"] = {"steps": mx["second_updates"][1], "with_second_update": mx["second_updates"][0],
-                               "note": "the phase-timing pass over the timed basis sizes"}
+                               "note": "the phase-timing pass over the timed basis sizes; the delayed form applies "
+                                       "every step's second projection (in the next step's sweeps)"}
     # the operator phase's own roofline (the line's roofline object is the dominant phase's)
     out["roofline_operator"] = roofline({"stencil": mx["phases"]["stencil"]}, w, "mixed", args.steps,
                                         mx["nq"], mx["g"].tuning())
@@ -743,7 +767,7 @@ def run_ours(args):
     n3 = w.nx * w.ny * w.nz
     nqm = sum(mx["nq"]) / len(mx["nq"]) if mx["nq"] else 0.0
     algo = {"stencil": 12 * 8.0 * n3, "divergence": (4 * 8.0 + 6.0) * n3, "correct": 7 * 8.0 * n3,
-            "refine": (2 * 8.0 + 6.0) * n3, "gs_dots": 8.0 * L * (nqm + 1), "gs_update": 8.0 * L * (nqm + 2)}
+            "refine": (2 * 8.0 + 6.0) * n3, "gs_dots": 8.0 * L * (nqm + 1), "gs_update": 8.0 * L * (nqm + 3)}
     for k, byts in algo.items():
         ph = out["phases"].get(k)
         if ph and ph["ms_per_step"] > 0:
@@ -752,22 +776,23 @@ def run_ours(args):
     # measured step time. Algorithmic work: the Krylov vector's streaming steps move 13 fields
     # (read x and the base state, write y and p); the Poisson solves are 12 N^4 flops per solve
     # for each of the 6 BF16 slice products, at the sustained tensor rate; the Gram-Schmidt
-    # sweeps stream the basis and w as they run (first sweep nq + 1 vectors, fused sweep nq + 2,
-    # third sweep nq + 2 in the steps that take the second update, else the 2 of the
-    # normalisation). The refinement residual and the other intermediates are implementation
-    # traffic, with no time at the bound.
+    # sweeps stream the basis, the provisional vector and its image as they run (the delayed form:
+    # nq + 1 vectors for the inner products and nq + 3 for the update per step, and the last
+    # vector's two sweeps, (J + 1) + (J + 2), once per run). The refinement residual and the other
+    # intermediates are implementation traffic, with no time at the bound.
     bf16, bf16_src = bf16_peak()
     tpd = out["phases"].get("tpd", {})
     sweeps = tpd.get("launches_per_step", 12.0) / 6.0
-    su = mx["second_updates"]
-    f2 = su[0] / su[1] if su[1] else 0.0
+    nqs_t = mx["nq"]
+    ends = [nq for i, nq in enumerate(nqs_t) if i + 1 == len(nqs_t) or nqs_t[i + 1] <= nq]
+    final_per_step = sum((J + 1) + (J + 2) for J in ends) / max(len(nqs_t), 1)
     t_min = {"operator + divergence + correction (HBM, 13 fields x 8 B x N^3)": 13 * 8.0 * n3 / (hbm_peak * 1e9),
              "Poisson contractions (tensor, 6 x 12 N^4 flops x sweeps)":
                  6 * 12.0 * w.nx * w.ny * w.nz * (w.nx + w.ny + w.nz) / 3.0 * sweeps / (bf16 * 1e12),
-             "Gram-Schmidt sweeps (HBM, basis and w streams)":
-                 8.0 * L * ((nqm + 1) + (nqm + 2) + f2 * (nqm + 2) + (1 - f2) * 2) / (hbm_peak * 1e9)}
+             "Gram-Schmidt sweeps (HBM, basis and vector streams)":
+                 8.0 * L * ((nqm + 1) + (nqm + 3) + final_per_step) / (hbm_peak * 1e9)}
     t_sum = sum(t_min.values())
-    kv_min = t_sum - t_min["Gram-Schmidt sweeps (HBM, basis and w streams)"]
+    kv_min = t_sum - t_min["Gram-Schmidt sweeps (HBM, basis and vector streams)"]
     out["roofline_step"] = {
         "frac": t_sum / (out["ms_per_step"] / 1e3),
         "t_min_ms": {k: v * 1e3 for k, v in t_min.items()}, "t_measured_ms": out["ms_per_step"],
