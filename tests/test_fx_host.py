@@ -95,6 +95,31 @@ def test_fixed_point_upwind_equations_match_oracle(driver, tmp_path, n, bc, gr, 
     assert np.abs(central - ref).max() > 1e-6 * np.abs(ref).max()
 
 
+_rng = np.random.default_rng(1905)
+RANDOM_CASES = [(int(_rng.integers(2, 19)), int(_rng.integers(0, 2)), float(10 ** _rng.uniform(4, 7)),
+                 int(_rng.integers(0, 2)), int(_rng.integers(0, 2)), int(_rng.integers(100, 10000)))
+                for _ in range(8)]
+
+
+@pytest.mark.parametrize("n,bc,gr,tproj,adv,seed", RANDOM_CASES)
+def test_fixed_point_equations_on_seeded_random_cubes(driver, tmp_path, n, bc, gr, tproj, adv, seed):
+    """Seeded random cube sizes, Grashof numbers, boundary types, projection readings and both
+    advection schemes, with a base state scaled by a random power of ten (the grids follow it)."""
+    pr = 0.71
+    scale = 10.0 ** np.random.default_rng(seed).integers(-3, 4)
+    base = np.stack(synth.base_flow(n, n, n, bc, seed)) * scale
+    x = synth.krylov_input(n, n, n, seed + 1)[0]
+    o = Oracle(n, n, n, bc=bc, gr=gr, pr=pr, tproj=tproj, adv=adv)
+    xp = o.project_input(x)
+    ref = o.jx_raw(base, xp)
+    y = run(driver, tmp_path, n, base, xp, gr, pr, "upwind" if adv else "auto")
+    inner = (slice(1, n + 1),) * 3
+    for F in range(4):
+        r, g = ref[F][inner], y[F][inner]
+        m = np.abs(r).max()
+        assert np.abs(g - r).max() <= TOL * m, (F, np.abs(g - r).max() / m)
+
+
 def test_grid_conversion_is_exact_where_it_should_be(driver, tmp_path):
     """A base state and an input whose values are small integers times powers of two: their
     conversions to the fixed-point grids are exact and so is every integer sum and product, which
