@@ -252,9 +252,9 @@ kv_status kv_arnoldi_step(kv_handle h, double* V, int j, double* h_col);
    normalisation (A is linear; the corrections use the Arnoldi relation of the final columns).
    H: HOST, column-major, leading dimension ldh >= j0 + m + 1. Columns 0..j0-1 (rows 0..c+1)
    are read: the Hessenberg matrix of the basis V_0..V_{j0} (needed by the deferred corrections);
-   columns j0..j0+m-1 (rows 0..c+1) are written. Requires j0 >= 0, m >= 1 and
-   j0 + m <= 24 (else KV_ERR_ARG; larger bases: kv_arnoldi_step). Synchronises the stream once, at
-   the end. KV_PREC_MIXED: the sweeps' arithmetic as kv_arnoldi_step's double-float sweeps (FP64
+   columns j0..j0+m-1 (rows 0..c+1) are written. Requires j0 >= 0, m >= 1 and j0 + m <= 4096
+   (else KV_ERR_ARG); the sweeps take the basis in chunks of 24 vectors. Synchronises the stream
+   once, at the end. KV_PREC_MIXED: the sweeps' arithmetic as kv_arnoldi_step's double-float sweeps (FP64
    for the first basis vectors of each sweep, double-float for the rest); a vector with an entry
    of magnitude >= 2^48, NaN or Inf, or one in the span of the basis, gives KV_ERR_ARG (V and H
    undefined). While the call runs, V_{j+1} holds intermediate vectors. */

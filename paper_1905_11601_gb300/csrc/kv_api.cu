@@ -1035,12 +1035,13 @@ kv_status kv_arnoldi_step(kv_handle h, double* V, int j, double* h_col) {
 
 kv_status kv_arnoldi_run(kv_handle h, double* V, int j0, int m, double* H, int ldh) {
   if (!h) return KV_ERR_ARG;
-  if (!V || !H || j0 < 0 || m < 1 || j0 + m > kv_dcgs_max() || ldh < j0 + m + 1)
-    return fail(h, KV_ERR_ARG, "kv_arnoldi_run: bad argument (j0 >= 0, m >= 1, j0 + m <= " +
-                                   std::to_string(kv_dcgs_max()) + ", ldh >= j0 + m + 1)");
+  if (!V || !H || j0 < 0 || m < 1 || j0 + m > 4096 || ldh < j0 + m + 1)
+    return fail(h, KV_ERR_ARG, "kv_arnoldi_run: bad argument (j0 >= 0, m >= 1, j0 + m <= 4096, ldh >= j0 + m + 1)");
   const size_t L = 4 * h->P;
   const int J = j0 + m, ldd = J + 1;
-  const size_t need_p = (size_t)(2 * J + 3) * kv_reduce_blocks();
+  const int QC = kv_dcgs_chunk(), DSs = kv_dcgs_dots_stride();
+  const int nch = (J + QC - 1) / QC;
+  const size_t need_p = (size_t)(2 * QC + 3) * kv_reduce_blocks();
   if (h->partials_cap < need_p) {
     cudaFree(h->partials);
     h->partials = nullptr;
@@ -1049,10 +1050,11 @@ kv_status kv_arnoldi_run(kv_handle h, double* V, int j0, int m, double* H, int l
     if (s != KV_OK) return s;
     h->partials_cap = need_p;
   }
-  // device scratch: the inner products (2J + 3), the Hessenberg matrix (ldd x J, column-major),
-  // the update coefficients (2J + 3) and an error flag
-  const size_t n_dots = 2 * (size_t)J + 3, n_h = (size_t)ldd * J, n_c = 2 * (size_t)J + 3;
-  const size_t need_h = n_dots + n_h + n_c + 1;
+  // device scratch: the inner products (a block per chunk), the Hessenberg matrix (ldd x J,
+  // column-major), the update's scalars (3) and the constant (1, 1, 0) of later chunks, its two
+  // coefficient vectors (J each), the coefficient kernel's scratch (2 (J + 1)), an error flag
+  const size_t n_dots = (size_t)DSs * (nch > 0 ? nch : 1), n_h = (size_t)ldd * J;
+  const size_t need_h = n_dots + n_h + 6 + 2 * (size_t)J + 2 * (size_t)(J + 1) + 1;
   if (h->hdev_cap < need_h) {
     cudaFree(h->hdev);
     h->hdev = nullptr;
@@ -1063,14 +1065,20 @@ kv_status kv_arnoldi_run(kv_handle h, double* V, int j0, int m, double* H, int l
   }
   double* dots = h->hdev;
   double* Hd = dots + n_dots;
-  double* coef = Hd + n_h;
-  int* err = reinterpret_cast<int*>(coef + n_c);
+  double* s3 = Hd + n_h;
+  double* one3 = s3 + 3;
+  double* cuv = one3 + 3;
+  double* cwv = cuv + J;
+  double* scr = cwv + J;
+  int* err = reinterpret_cast<int*>(scr + 2 * (size_t)(J + 1));
   // the columns of H before the run (those of the existing basis) go to the device; the
   // corrections of the deferred projections use them
-  std::vector<double> hd(n_h, 0.0);
+  std::vector<double> hd(n_h + 6, 0.0);
   for (int c = 0; c < j0; ++c)
     for (int r = 0; r <= c + 1; ++r) hd[r + (size_t)ldd * c] = H[r + (size_t)ldh * c];
-  KV_CHECK_CUDA(h, cudaMemcpyAsync(Hd, hd.data(), n_h * sizeof(double), cudaMemcpyHostToDevice, h->s));
+  hd[n_h + 3] = 1.0;
+  hd[n_h + 4] = 1.0;
+  KV_CHECK_CUDA(h, cudaMemcpyAsync(Hd, hd.data(), (n_h + 6) * sizeof(double), cudaMemcpyHostToDevice, h->s));
   KV_CHECK_CUDA(h, cudaMemsetAsync(err, 0, sizeof(int), h->s));
   const int df = h->d.precision == KV_PREC_MIXED;
   for (int j = j0; j < J; ++j) {
@@ -1078,26 +1086,28 @@ kv_status kv_arnoldi_run(kv_handle h, double* V, int j0, int m, double* H, int l
     double* w = V + (size_t)(j + 1) * L;
     kv_status s = kv_krylov_vector(h, u, w, nullptr, nullptr);  // w = A u_j (u_j provisional)
     if (s != KV_OK) return s;
+    const int nc = j > 0 ? (j + QC - 1) / QC : 1;
     {
-      KvPhase ph(h, KV_PH_GS_DOTS, 2);
+      KvPhase ph(h, KV_PH_GS_DOTS, 2 * nc);
       kv_launch_dots2(V, L, j, u, w, L, h->partials, dots, df, h->s);
     }
     {
       KvPhase ph(h, KV_PH_ARNOLDI, 1);
-      kv_launch_dcgs_coef(dots, Hd, ldd, j, j == j0, 0, coef, err, h->s);
+      kv_launch_dcgs_coef(dots, Hd, ldd, j, j == j0, 0, s3, cuv, cwv, scr, err, h->s);
     }
     {
-      KvPhase ph(h, KV_PH_GS_UPDATE, 1);
-      kv_launch_update2(V, L, j, coef, u, w, L, j != j0, 1, df, h->s);
+      KvPhase ph(h, KV_PH_GS_UPDATE, nc);
+      kv_launch_update2(V, L, j, s3, one3, cuv, cwv, u, w, L, j != j0, 1, df, h->s);
     }
   }
   {
     // the last vector's deferred second projection and its normalisation
-    KvPhase ph(h, KV_PH_ARNOLDI, 4);
+    const int nc = (J + QC - 1) / QC;
+    KvPhase ph(h, KV_PH_ARNOLDI, 3 * nc + 1);
     double* u = V + (size_t)J * L;
-    kv_launch_dots_norm(V, L, J, u, L, h->partials, dots, dots + J, df, h->s);
-    kv_launch_dcgs_coef(dots, Hd, ldd, J, 0, 1, coef, err, h->s);
-    kv_launch_update2(V, L, J, coef, u, nullptr, L, 1, 0, df, h->s);
+    kv_launch_dots2(V, L, J, u, u, L, h->partials, dots, df, h->s);
+    kv_launch_dcgs_coef(dots, Hd, ldd, J, 0, 1, s3, cuv, cwv, scr, err, h->s);
+    kv_launch_update2(V, L, J, s3, one3, cuv, cwv, u, nullptr, L, 1, 0, df, h->s);
   }
   kv_status s = check_launch(h, "arnoldi run");
   if (s != KV_OK) return s;

@@ -21,7 +21,7 @@
 namespace {
 
 constexpr int RT = 256;  // threads per block
-constexpr int QD = 24;   // largest basis of a run (j0 + m)
+constexpr int QD = 24;   // basis vectors per chunk of a sweep
 #define KV_FOR_EACH_Q0(X)                                                                                       \
   X(0) X(1) X(2) X(3) X(4) X(5) X(6) X(7) X(8) X(9) X(10) X(11) X(12) X(13) X(14) X(15) X(16) X(17) X(18) X(19) \
       X(20) X(21) X(22) X(23) X(24)
@@ -150,10 +150,11 @@ __global__ void __launch_bounds__(RT) k_dots2(const double* __restrict__ V, size
 }
 
 // u <- c0 u + sum_q cu_q V_q, w <- cw w + cwu u + sum_q cw_q V_q, both from the entering u;
-// coef = [c0, cu_0 .. cu_{Q-1}, cw, cwu, cw_0 .. cw_{Q-1}]. Stored rounded to FP64.
+// s3 = (c0, cw, cwu). Stored rounded to FP64.
 template <int Q, bool DFM>
 __global__ void __launch_bounds__(RT) k_update2(const double* __restrict__ V, size_t ld,
-                                                const double* __restrict__ coef, double* __restrict__ u,
+                                                const double* __restrict__ s3, const double* __restrict__ cuv,
+                                                const double* __restrict__ cwv, double* __restrict__ u,
                                                 double* __restrict__ w, size_t len, int write_u, int write_w) {
   constexpr int K64 = DFM ? update2_k64<Q>() : Q;
   constexpr int QA = Q > 0 ? Q : 1;
@@ -161,17 +162,13 @@ __global__ void __launch_bounds__(RT) k_update2(const double* __restrict__ V, si
   __shared__ DF cud[QA], cwd[QA];
   const int t = threadIdx.x;
   if (t < Q) {
-    const double a = coef[1 + t], b = coef[Q + 3 + t];
+    const double a = cuv[t], b = cwv[t];
     cu64[t] = a;
     cw64[t] = b;
     cud[t] = df_split(a);
     cwd[t] = df_split(b);
   }
-  if (t == 0) {
-    c3[0] = coef[0];
-    c3[1] = coef[Q + 1];
-    c3[2] = coef[Q + 2];
-  }
+  if (t < 3) c3[t] = s3[t];
   __syncthreads();
   const double c0 = c3[0], cw = c3[1], cwu = c3[2];
   for (size_t e = (size_t)blockIdx.x * RT + threadIdx.x; e < len; e += (size_t)gridDim.x * RT) {
@@ -205,8 +202,13 @@ __global__ void __launch_bounds__(RT) k_update2(const double* __restrict__ V, si
   }
 }
 
-// One step's coefficients (one thread; j < QD). With a = <V, u>, b = <V, w>, bu = <u, w>,
-// nu = <u, u> (u = u_j, w = A u_j, V = the final V_0..V_{j-1}):
+// Inner products of a step, chunk c (vectors 24c .. 24c + q_c - 1) at dots + DS c:
+// [<V, u> (q_c), <V, w> (q_c), <u, w>, <u, u>, <w, w>] (the last three equal in every chunk).
+constexpr int DS = 2 * QD + 3;
+__host__ __device__ __forceinline__ int chunk_q(int j, int c) { return j - QD * c < QD ? j - QD * c : QD; }
+
+// One step's coefficients (one warp). With a = <V, u>, b = <V, w>, bu = <u, w>, nu = <u, u>
+// (u = u_j, w = A u_j, V = the final V_0..V_{j-1}):
 //   beta = sqrt(nu - a.a): column j-1 += a, its subdiagonal = beta (the deferred second
 //   projection of u_j), v_j = (u_j - V a) / beta;
 //   d = H[0..j, 0..j-1] a, so that A v_j = (w - [V, v_j] d) / beta;
@@ -214,48 +216,74 @@ __global__ void __launch_bounds__(RT) k_update2(const double* __restrict__ V, si
 //   h_j = ((bu - a.b) / beta - d_j) / beta; column j = h (provisional);
 //   u_{j+1} = A v_j - [V, v_j] h = w / beta - (kappa / beta) u_j - V e,
 //   kappa = d_j / beta + h_j, e = d / beta + h - a kappa / beta.
-// first (the run's first step, v_j final on entry): a = 0, beta = 1, column j-1 untouched.
-// final_only: column j-1 from a = dots[0, j), nu = dots[j], and v_j only.
+// Outputs: s3 = (1 / beta, 1 / beta, -kappa / beta), cuv = -a / beta, cwv = -e (the update
+// sweep's coefficients). first (the run's first step, v_j final on entry): a = 0, beta = 1,
+// column j-1 untouched. final_only: column j-1 and v_j only (the run's last vector). scr: 2 (j + 1)
+// doubles of scratch.
 __global__ void k_dcgs_coef(const double* __restrict__ dots, double* __restrict__ Hd, int ldh, int j, int first,
-                            int final_only, double* __restrict__ coef, int* __restrict__ err) {
-  if (threadIdx.x != 0 || blockIdx.x != 0) return;
-  const double* a = dots;
-  double aa = 0.0;
-  if (!first)
-    for (int q = 0; q < j; ++q) aa = fma(a[q], a[q], aa);
-  const double nu = final_only ? dots[j] : dots[2 * j + 1];
-  double beta = 1.0;
+                            int final_only, double* __restrict__ s3, double* __restrict__ cuv,
+                            double* __restrict__ cwv, double* __restrict__ scr, int* __restrict__ err) {
+  __shared__ double sh[4];  // beta, a.b, kappa
+  const int lane = threadIdx.x;
+  auto a_of = [&](int q) { return first ? 0.0 : dots[(size_t)DS * (q / QD) + q % QD]; };
+  auto b_of = [&](int q) { return dots[(size_t)DS * (q / QD) + chunk_q(j, q / QD) + q % QD]; };
+  const int q0 = j < QD ? j : QD;
+  const double bu = dots[2 * q0], nu = dots[2 * q0 + 1];
+  double aa = 0.0, ab = 0.0;
+  for (int q = lane; q < j; q += 32) {
+    const double a = a_of(q);
+    aa = fma(a, a, aa);
+    if (!final_only) ab = fma(a, b_of(q), ab);
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    aa += __shfl_xor_sync(0xffffffffu, aa, o);
+    ab += __shfl_xor_sync(0xffffffffu, ab, o);
+  }
+  if (lane == 0) {
+    double beta = 1.0;
+    if (!first) {
+      const double b2 = nu - aa;
+      if (!(b2 > 0.0) || !isfinite(b2)) *err = 1;
+      beta = sqrt(b2);
+    } else if (!isfinite(nu)) {
+      *err = 1;
+    }
+    sh[0] = beta;
+    sh[1] = ab;
+  }
+  __syncwarp();
+  const double beta = sh[0];
   if (!first) {
-    const double b2 = nu - aa;
-    if (!(b2 > 0.0) || !isfinite(b2)) *err = 1;
-    beta = sqrt(b2);
-    for (int q = 0; q < j; ++q) Hd[q + (size_t)ldh * (j - 1)] += a[q];
-    Hd[j + (size_t)ldh * (j - 1)] = beta;
-  } else if (!isfinite(nu)) {
-    *err = 1;
+    for (int q = lane; q < j; q += 32) Hd[q + (size_t)ldh * (j - 1)] += a_of(q);
+    if (lane == 0) Hd[j + (size_t)ldh * (j - 1)] = beta;
   }
-  coef[0] = 1.0 / beta;
-  for (int q = 0; q < j; ++q) coef[1 + q] = first ? 0.0 : -a[q] / beta;
+  for (int q = lane; q < j; q += 32) cuv[q] = -a_of(q) / beta;
+  if (lane == 0) s3[0] = 1.0 / beta;
   if (final_only) return;
-  const double* b = dots + j;
-  const double bu = dots[2 * j];
-  double d[QD + 1], hq[QD + 1];
-  double ab = 0.0;
-  for (int r = 0; r <= j; ++r) {
-    double s = 0.0;
+  __syncwarp();
+  // d = H[0..j, 0..j-1] a (the final columns, j - 1 included), one row per lane
+  double* d = scr;
+  double* hq = scr + j + 1;
+  for (int r = lane; r <= j; r += 32) {
+    double t = 0.0;
     if (!first)
-      for (int c = 0; c < j; ++c) s = fma(Hd[r + (size_t)ldh * c], a[c], s);
-    d[r] = s;
+      for (int c = (r > 0 ? r - 1 : 0); c < j; ++c) t = fma(Hd[r + (size_t)ldh * c], a_of(c), t);
+    d[r] = t;
   }
-  if (!first)
-    for (int q = 0; q < j; ++q) ab = fma(a[q], b[q], ab);
-  for (int q = 0; q < j; ++q) hq[q] = (b[q] - d[q]) / beta;
-  hq[j] = ((bu - ab) / beta - d[j]) / beta;
-  for (int q = 0; q <= j; ++q) Hd[q + (size_t)ldh * j] = hq[q];
-  const double kappa = d[j] / beta + hq[j];
-  coef[j + 1] = 1.0 / beta;
-  coef[j + 2] = -kappa / beta;
-  for (int q = 0; q < j; ++q) coef[j + 3 + q] = -(d[q] / beta + hq[q] - (first ? 0.0 : a[q]) * kappa / beta);
+  __syncwarp();
+  for (int q = lane; q < j; q += 32) hq[q] = (b_of(q) - d[q]) / beta;
+  if (lane == 0) {
+    hq[j] = ((bu - sh[1]) / beta - d[j]) / beta;
+    sh[2] = d[j] / beta + hq[j];
+  }
+  __syncwarp();
+  const double kappa = sh[2];
+  for (int q = lane; q <= j; q += 32) Hd[q + (size_t)ldh * j] = hq[q];
+  for (int q = lane; q < j; q += 32) cwv[q] = -(d[q] / beta + hq[q] - a_of(q) * kappa / beta);
+  if (lane == 0) {
+    s3[1] = 1.0 / beta;
+    s3[2] = -kappa / beta;
+  }
 }
 
 // Blocks of kernel K resident at once (at most cap): one wave.
@@ -273,19 +301,21 @@ int wave(int cap) {
 
 }  // namespace
 
-int kv_dcgs_max() { return QD; }
+int kv_dcgs_chunk() { return QD; }
+int kv_dcgs_dots_stride() { return DS; }
 
-void kv_launch_dots2(const double* V, size_t ld, int q, const double* u, const double* w, size_t len,
-                     double* partials, double* out, int df, cudaStream_t s) {
+namespace {
+void dots2_one(const double* V, size_t ld, int q, const double* u, const double* w, size_t len, double* partials,
+               double* out, int df, cudaStream_t s) {
   const int rb = kv_reduce_blocks();
   int nb = rb;
   // V_q, u and w all start on 16-byte boundaries
   const int vec = (uintptr_t)V % 16 == 0 && ld % 2 == 0 && (uintptr_t)u % 16 == 0 && (uintptr_t)w % 16 == 0;
   if (df) {
     switch (q) {
-#define KV_DOTS2_DF(Qn)                                                         \
-  case Qn:                                                                      \
-    nb = wave<k_dots2<Qn, true>>(rb);                                           \
+#define KV_DOTS2_DF(Qn)                                                              \
+  case Qn:                                                                           \
+    nb = wave<k_dots2<Qn, true>>(rb);                                                \
     k_dots2<Qn, true><<<nb, RT, 0, s>>>(V, ld, u, w, len, (size_t)rb, vec, partials); \
     break;
       KV_FOR_EACH_Q0(KV_DOTS2_DF)
@@ -293,9 +323,9 @@ void kv_launch_dots2(const double* V, size_t ld, int q, const double* u, const d
     }
   } else {
     switch (q) {
-#define KV_DOTS2_64(Qn)                                                          \
-  case Qn:                                                                       \
-    nb = wave<k_dots2<Qn, false>>(rb);                                           \
+#define KV_DOTS2_64(Qn)                                                               \
+  case Qn:                                                                            \
+    nb = wave<k_dots2<Qn, false>>(rb);                                                \
     k_dots2<Qn, false><<<nb, RT, 0, s>>>(V, ld, u, w, len, (size_t)rb, vec, partials); \
     break;
       KV_FOR_EACH_Q0(KV_DOTS2_64)
@@ -305,33 +335,56 @@ void kv_launch_dots2(const double* V, size_t ld, int q, const double* u, const d
   kv_launch_finalize(partials, 2 * q + 3, nb, out, s);
 }
 
-void kv_launch_dcgs_coef(const double* dots, double* Hd, int ldh, int j, int first, int final_only, double* coef,
-                         int* err, cudaStream_t s) {
-  k_dcgs_coef<<<1, 32, 0, s>>>(dots, Hd, ldh, j, first, final_only, coef, err);
-}
-
-void kv_launch_update2(const double* V, size_t ld, int q, const double* coef, double* u, double* w, size_t len,
-                       int write_u, int write_w, int df, cudaStream_t s) {
+void update2_one(const double* V, size_t ld, int q, const double* s3, const double* cuv, const double* cwv, double* u,
+                 double* w, size_t len, int write_u, int write_w, int df, cudaStream_t s) {
   const int rb = kv_reduce_blocks();
   if (df) {
     switch (q) {
-#define KV_UPD2_DF(Qn)                                                                            \
-  case Qn:                                                                                        \
-    k_update2<Qn, true><<<wave<k_update2<Qn, true>>(rb), RT, 0, s>>>(V, ld, coef, u, w, len, write_u, \
-                                                                      write_w);                   \
+#define KV_UPD2_DF(Qn)                                                                                    \
+  case Qn:                                                                                                \
+    k_update2<Qn, true><<<wave<k_update2<Qn, true>>(rb), RT, 0, s>>>(V, ld, s3, cuv, cwv, u, w, len, write_u, \
+                                                                      write_w);                           \
     break;
       KV_FOR_EACH_Q0(KV_UPD2_DF)
 #undef KV_UPD2_DF
     }
   } else {
     switch (q) {
-#define KV_UPD2_64(Qn)                                                                              \
-  case Qn:                                                                                          \
-    k_update2<Qn, false><<<wave<k_update2<Qn, false>>(rb), RT, 0, s>>>(V, ld, coef, u, w, len, write_u, \
-                                                                        write_w);                   \
+#define KV_UPD2_64(Qn)                                                                                      \
+  case Qn:                                                                                                  \
+    k_update2<Qn, false><<<wave<k_update2<Qn, false>>(rb), RT, 0, s>>>(V, ld, s3, cuv, cwv, u, w, len, write_u, \
+                                                                        write_w);                           \
     break;
       KV_FOR_EACH_Q0(KV_UPD2_64)
 #undef KV_UPD2_64
     }
   }
+}
+}  // namespace
+
+void kv_launch_dots2(const double* V, size_t ld, int q, const double* u, const double* w, size_t len,
+                     double* partials, double* dots, int df, cudaStream_t s) {
+  if (q == 0) {
+    dots2_one(V, ld, 0, u, w, len, partials, dots, df, s);
+    return;
+  }
+  for (int c = 0; QD * c < q; ++c)
+    dots2_one(V + (size_t)QD * c * ld, ld, chunk_q(q, c), u, w, len, partials, dots + (size_t)DS * c, df, s);
+}
+
+void kv_launch_dcgs_coef(const double* dots, double* Hd, int ldh, int j, int first, int final_only, double* s3,
+                         double* cuv, double* cwv, double* scr, int* err, cudaStream_t s) {
+  k_dcgs_coef<<<1, 32, 0, s>>>(dots, Hd, ldh, j, first, final_only, s3, cuv, cwv, scr, err);
+}
+
+void kv_launch_update2(const double* V, size_t ld, int q, const double* s3, const double* one3, const double* cuv,
+                       const double* cwv, double* u, double* w, size_t len, int write_u, int write_w, int df,
+                       cudaStream_t s) {
+  if (q == 0) {
+    update2_one(V, ld, 0, s3, cuv, cwv, u, w, len, write_u, write_w, df, s);
+    return;
+  }
+  for (int c = 0; QD * c < q; ++c)
+    update2_one(V + (size_t)QD * c * ld, ld, chunk_q(q, c), c == 0 ? s3 : one3, cuv + (size_t)QD * c,
+                cwv + (size_t)QD * c, u, w, len, write_u, write_w, df, s);
 }

@@ -315,24 +315,27 @@ void kv_launch_poisson(kv_grid* h, double* b, double* phi, cudaStream_t s);
 int kv_reduce_blocks();
 // out[r] = sum of the nb block partials of row r (rows laid out kv_reduce_blocks() apart)
 void kv_launch_finalize(const double* partials, int rows, int nb, double* out, cudaStream_t s);
-// kv_dcgs.cu: the sweeps of the delayed classical Gram-Schmidt (kv_arnoldi_run).
-// Inner products of the basis V_0..V_{q-1} with two vectors u and w, and u.w, u.u, w.w:
-// out[0, q) = <V, u>, out[q, 2q) = <V, w>, out[2q] = <u, w>, out[2q + 1] = ||u||^2 (NaN if a
-// double-float sweep meets an entry of u or w outside its range), out[2q + 2] = ||w||^2.
-// q <= kv_dcgs_max() - 1; partials: (2q + 3) kv_reduce_blocks() doubles.
-int kv_dcgs_max();
+// kv_dcgs.cu: the sweeps of the delayed classical Gram-Schmidt (kv_arnoldi_run), in chunks of
+// kv_dcgs_chunk() basis vectors. Inner products of the basis V_0..V_{q-1} with two vectors u and
+// w: chunk c (from vector c kv_dcgs_chunk() on) at dots + c kv_dcgs_dots_stride() holds [<V, u>, <V, w>, <u, w>,
+// ||u||^2 (NaN if a double-float sweep meets an entry of u or w outside its range), ||w||^2];
+// partials: (2 kv_dcgs_chunk() + 3) kv_reduce_blocks() doubles (reused chunk by chunk).
+int kv_dcgs_chunk();
+int kv_dcgs_dots_stride();
 void kv_launch_dots2(const double* V, size_t ld, int q, const double* u, const double* w, size_t len,
-                     double* partials, double* out, int df, cudaStream_t s);
+                     double* partials, double* dots, int df, cudaStream_t s);
 // The coefficients of a step from those inner products and the Hessenberg matrix Hd (device,
 // column-major, leading dimension ldh): column j-1 finalised (unless first), column j
-// provisional; coef laid out for kv_launch_update2. final_only: finalise column j-1 from
-// a = out[0, j), ||u||^2 = out[j] (the run's last vector), no w. err: set on a failure.
-void kv_launch_dcgs_coef(const double* dots, double* Hd, int ldh, int j, int first, int final_only, double* coef,
-                         int* err, cudaStream_t s);
-// u <- coef[0] u + sum_q coef[1 + q] V_q (unless first), w <- coef[q + 1] w + coef[q + 2] u +
-// sum_r coef[q + 3 + r] V_r (unless no_w), both from the entering u.
-void kv_launch_update2(const double* V, size_t ld, int q, const double* coef, double* u, double* w, size_t len,
-                       int write_u, int write_w, int df, cudaStream_t s);
+// provisional; s3, cuv, cwv for kv_launch_update2. final_only: column j-1 and v_j only (the
+// run's last vector; the inner products from kv_launch_dots2 with w = u). scr: 2 (j + 1)
+// doubles. err: set on a failure.
+void kv_launch_dcgs_coef(const double* dots, double* Hd, int ldh, int j, int first, int final_only, double* s3,
+                         double* cuv, double* cwv, double* scr, int* err, cudaStream_t s);
+// u <- s3[0] u + sum_q cuv_q V_q (if write_u), w <- s3[1] w + s3[2] u + sum_q cwv_q V_q (if
+// write_w), both from the entering u; chunks after the first use one3 = (1, 1, 0).
+void kv_launch_update2(const double* V, size_t ld, int q, const double* s3, const double* one3, const double* cuv,
+                       const double* cwv, double* u, double* w, size_t len, int write_u, int write_w, int df,
+                       cudaStream_t s);
 void kv_launch_multidot(const double* V, size_t ld, int nq, const double* w, size_t len, double* partials,
                         double* out, int accumulate, cudaStream_t s);
 // w -= sum_q c[q] V_q
