@@ -1,6 +1,6 @@
 """Arnoldi driver for the eigenvalue problem Eq (10) over the GPU Krylov map.
 
-The basis and every Krylov vector live on the GPU (kv_arnoldi_step); only the small Hessenberg
+The basis and every Krylov vector live on the GPU (kv_arnoldi_run); only the small Hessenberg
 matrix H comes back to the host, where its eigenvalues (the Ritz values) are computed. The
 residual of a Ritz pair (theta, X = V y) follows from the Arnoldi relation A V_k = V_k H_k +
 h_{k+1,k} v_{k+1} e_k^T as |h_{k+1,k}| |y_k| / ||y||, the quantity the paper monitors
@@ -10,6 +10,8 @@ from __future__ import annotations
 
 import numpy as np
 
+from .kv import KvError
+
 
 def arnoldi(grid, v0, k):
     """k Arnoldi steps from v0 (a packed vector, device): returns V ((k+1) x packed) and H."""
@@ -17,8 +19,7 @@ def arnoldi(grid, v0, k):
     V = torch.zeros((k + 1, 4) + grid.shape, dtype=torch.float64, device="cuda")
     V[0] = v0 / torch.linalg.vector_norm(v0)
     H = np.zeros((k + 1, k))
-    for j in range(k):
-        H[: j + 2, j] = grid.arnoldi_step(V, j)
+    H[:, :] = grid.arnoldi_run(V, 0, k)  # one call: the delayed classical Gram-Schmidt
     return V, H
 
 
@@ -82,7 +83,7 @@ def _wanted(theta, nev):
 
 def arnoldi_chebyshev(grid, v0, m=30, nev=1, k=20, tol=1e-10, max_cycles=100):
     """The leading eigenvalue(s) of Eq (10) by the Chebyshev-preconditioned Arnoldi iteration
-    (Section 3.1; Saad's Arnoldi-Chebyshev method): cycles of m Arnoldi steps (kv_arnoldi_step);
+    (Section 3.1; Saad's Arnoldi-Chebyshev method): cycles of m Arnoldi steps (kv_arnoldi_run);
     the unwanted Ritz values define an ellipse centred on the real axis; the wanted Ritz vectors'
     real and imaginary parts (kv_combine) are filtered by the degree-k Chebyshev polynomial of
     that ellipse, normalised at the rightmost wanted Ritz value (three-term recurrence over
@@ -109,15 +110,30 @@ def arnoldi_chebyshev(grid, v0, m=30, nev=1, k=20, tol=1e-10, max_cycles=100):
         info["cycles"] += 1
         nv = np.sqrt(grid.dot(v, v))
         grid.axpby(1.0 / nv, v, 0.0, V[0])
-        H = np.zeros((m + 1, m))
+        # the cycle's m steps as one kv_arnoldi_run (one synchronisation), cut at the first step
+        # whose new vector is negligible; a breakdown inside the run (an invariant subspace)
+        # repeats the cycle step by step, stopping there
+        try:
+            H = grid.arnoldi_run(V, 0, m)
+            info["matvecs"] += m
+        except KvError:
+            H = None
         kk = m
-        for j in range(m):
-            H[: j + 2, j] = grid.arnoldi_step(V, j)
-            info["matvecs"] += 1
-            hn, col = H[j + 1, j], np.linalg.norm(H[: j + 2, j])
-            if hn == 0.0 or (hn <= tol * col and j + 1 >= nev):
-                kk = j + 1
-                break
+        if H is not None:
+            for j in range(m):
+                hn, col = H[j + 1, j], np.linalg.norm(H[: j + 2, j])
+                if hn == 0.0 or (hn <= tol * col and j + 1 >= nev):
+                    kk = j + 1
+                    break
+        else:
+            H = np.zeros((m + 1, m))
+            for j in range(m):
+                H[: j + 2, j] = grid.arnoldi_step(V, j)
+                info["matvecs"] += 1
+                hn, col = H[j + 1, j], np.linalg.norm(H[: j + 2, j])
+                if hn == 0.0 or (hn <= tol * col and j + 1 >= nev):
+                    kk = j + 1
+                    break
         theta_all, Y, rs = ritz(H[: kk + 1, :kk], kk)
         nw = _wanted(theta_all, nev)
         theta, res, Yw = theta_all[:nw], rs[:nw], Y[:, :nw]
